@@ -1,0 +1,488 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics
+(brute force, closed forms, invariants, hand-worked examples), independent of
+the oracle's own formulas.  CPU only."""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import cp_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rand_factors(rng, dims, R):
+    return [rng.standard_normal((I, R)) for I in dims]
+
+
+# --------------------------------------------------------------------------
+# MTTKRP
+# --------------------------------------------------------------------------
+
+def explicit_matricize(T, n):
+    """T_(n) built element by element: column index runs over the other
+    modes in increasing order with the LAST one fastest (pure Python loops)."""
+    dims = T.shape
+    others = [m for m in range(T.ndim) if m != n]
+    cols = list(itertools.product(*[range(dims[m]) for m in others]))
+    Tn = np.zeros((dims[n], len(cols)))
+    for i in range(dims[n]):
+        for c, idx in enumerate(cols):
+            full = [0] * T.ndim
+            full[n] = i
+            for m, v in zip(others, idx):
+                full[m] = v
+            Tn[i, c] = T[tuple(full)]
+    return Tn, cols, others
+
+
+def explicit_khatri_rao(factors, cols, others, R):
+    """Phibar with rows in the same column order as explicit_matricize."""
+    Phi = np.ones((len(cols), R))
+    for c, idx in enumerate(cols):
+        for m, v in zip(others, idx):
+            for r in range(R):
+                Phi[c, r] *= factors[m][v, r]
+    return Phi
+
+
+@pytest.mark.parametrize("dims,R", [((3, 4), 2), ((2, 3, 4), 3), ((3, 2, 4, 2), 2), ((5, 1, 3), 4)])
+def test_mttkrp_equals_explicit_matricization_times_khatri_rao(dims, R):
+    rng = np.random.default_rng(1)
+    T = rng.standard_normal(dims)
+    factors = rand_factors(rng, dims, R)
+    for n in range(len(dims)):
+        Tn, cols, others = explicit_matricize(T, n)
+        Phi = explicit_khatri_rao(factors, cols, others, R)
+        np.testing.assert_allclose(O.mttkrp_dense(T, factors, n), Tn @ Phi, rtol=1e-13, atol=1e-13)
+
+
+def test_mttkrp_golden_hand_example():
+    g = json.load(open(os.path.join(GOLDEN, "mttkrp_2x2x2.json")))
+    T = np.array(g["T"], dtype=float)
+    F = [np.array(g[k], dtype=float) for k in ("A", "B", "C")]
+    for n in range(3):
+        np.testing.assert_array_equal(O.mttkrp_dense(T, F, n), np.array(g["M"][n], dtype=float))
+
+
+def test_mttkrp_rank_one_closed_form():
+    rng = np.random.default_rng(2)
+    a, b, c = rng.standard_normal(4), rng.standard_normal(5), rng.standard_normal(3)
+    T = np.multiply.outer(np.multiply.outer(a, b), c)
+    B, C = rng.standard_normal((5, 2)), rng.standard_normal((3, 2))
+    A = rng.standard_normal((4, 2))
+    M1 = O.mttkrp_dense(T, [A, B, C], 0)
+    expect = np.outer(a, (b @ B) * (c @ C))
+    np.testing.assert_allclose(M1, expect, rtol=1e-13)
+
+
+def test_mttkrp_two_way_is_matrix_product():
+    rng = np.random.default_rng(3)
+    T = rng.standard_normal((6, 4))
+    A, B = rng.standard_normal((6, 3)), rng.standard_normal((4, 3))
+    np.testing.assert_allclose(O.mttkrp_dense(T, [A, B], 0), T @ B, rtol=1e-13)
+    np.testing.assert_allclose(O.mttkrp_dense(T, [A, B], 1), T.T @ A, rtol=1e-13)
+
+
+def test_sparse_mttkrp_matches_loop_over_nonzeros():
+    rng = np.random.default_rng(4)
+    dims = (5, 4, 6)
+    coords = synth.distinct_coords(rng, dims, 40)
+    vals = rng.standard_normal(40)
+    F = rand_factors(rng, dims, 3)
+    for n in range(3):
+        ref = np.zeros((dims[n], 3))
+        for k in range(40):
+            for r in range(3):
+                p = vals[k]
+                for m in range(3):
+                    if m != n:
+                        p *= F[m][coords[k, m], r]
+                ref[coords[k, n], r] += p
+        np.testing.assert_allclose(O.mttkrp_sparse(coords, vals, dims, F, n), ref, rtol=1e-13, atol=1e-14)
+        dense = np.zeros(dims)
+        dense[tuple(coords.T)] = vals
+        np.testing.assert_allclose(O.mttkrp_dense(dense, F, n), ref, rtol=1e-12, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# f and g
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,R", [((4, 5, 3), 2), ((3, 3, 2, 4), 3), ((6, 7), 2)])
+def test_f_expansion_equals_bruteforce(dims, R):
+    rng = np.random.default_rng(5)
+    T = rng.standard_normal(dims)
+    u = synth.initial_guess(rng, dims, R)
+    X = O.DenseTensor(T)
+    f, _ = O.fg(X, u, R)
+    ref = 0.0
+    F = O.unpack(u, dims, R)
+    for idx in itertools.product(*[range(d) for d in dims]):
+        model = sum(math.prod(F[n][idx[n], r] for n in range(len(dims))) for r in range(R))
+        ref += 0.5 * (T[idx] - model) ** 2
+    assert abs(f - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("dims,R", [((4, 3, 5), 2), ((3, 2, 3, 2), 3)])
+def test_gradient_central_differences(dims, R):
+    rng = np.random.default_rng(6)
+    T = rng.standard_normal(dims)
+    X = O.DenseTensor(T)
+    u = synth.initial_guess(rng, dims, R)
+    _, g = O.fg(X, u, R)
+    fd = np.zeros_like(u)
+    for k in range(u.size):
+        h = 1e-6 * max(1.0, abs(u[k]))
+        up, um = u.copy(), u.copy()
+        up[k] += h
+        um[k] -= h
+        fd[k] = (O.f_bruteforce(T, O.unpack(up, dims, R)) - O.f_bruteforce(T, O.unpack(um, dims, R))) / (2 * h)
+    assert np.linalg.norm(fd - g) <= 1e-6 * np.linalg.norm(g)
+
+
+def test_exact_decomposition_has_zero_f_and_g():
+    rng = np.random.default_rng(7)
+    dims, R = (5, 4, 6), 3
+    F = rand_factors(rng, dims, R)
+    T = O.cp_full(F)
+    X = O.DenseTensor(T)
+    f, g = O.fg(X, O.pack(F), R)
+    assert abs(f) <= 1e-12 * X.norm2
+    assert np.linalg.norm(g) <= 1e-12 * X.norm2
+    for n in range(3):  # M^(n) = A^(n) Gammabar^(n) at an exact decomposition
+        np.testing.assert_allclose(O.mttkrp_dense(T, F, n), F[n] @ O.gamma_bar(F, n), rtol=1e-12, atol=1e-12)
+
+
+def test_sparse_fg_equals_dense_fg():
+    rng = np.random.default_rng(8)
+    dims, R = (6, 5, 7), 3
+    coords = synth.distinct_coords(rng, dims, 50)
+    vals = rng.standard_normal(50)
+    dense = np.zeros(dims)
+    dense[tuple(coords.T)] = vals
+    u = synth.initial_guess(rng, dims, R)
+    fs, gs = O.fg(O.SparseTensor(coords, vals, dims), u, R)
+    fd, gd = O.fg(O.DenseTensor(dense), u, R)
+    assert abs(fs - fd) <= 1e-12 * abs(fd)
+    np.testing.assert_allclose(gs, gd, rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# ALS
+# --------------------------------------------------------------------------
+
+def test_als_mode_updates_decrease_f_and_zero_the_mode_gradient():
+    rng = np.random.default_rng(9)
+    prob = synth.dense_problem(rng, (8, 7, 6), 3, 0.5, eta=0.1)
+    X = O.DenseTensor(prob.T)
+    R = 3
+    u = synth.initial_guess(rng, prob.dims, R)
+    F = [A.copy() for A in O.unpack(u, prob.dims, R)]
+    f_prev = O.f_bruteforce(prob.T, F)
+    for sweep in range(4):
+        for n in range(3):
+            M = O.mttkrp_dense(prob.T, F, n)
+            F[n] = O.als_mode_solve(M, O.gamma_bar(F, n))
+            f_now = O.f_bruteforce(prob.T, F)
+            assert f_now <= f_prev * (1 + 1e-12)
+            f_prev = f_now
+            _, g = O.fg(X, O.pack(F), R)
+            Gn = O.unpack(g, prob.dims, R)[n]
+            assert np.linalg.norm(Gn) <= 1e-9 * np.linalg.norm(M)
+    # the sweep function reproduces the hand-rolled sweep
+    u1 = O.als_sweep(X, u, R)
+    F2 = [A.copy() for A in O.unpack(u, prob.dims, R)]
+    for n in range(3):
+        F2[n] = O.als_mode_solve(O.mttkrp_dense(prob.T, F2, n), O.gamma_bar(F2, n))
+    np.testing.assert_allclose(u1, O.pack(F2), rtol=1e-12)
+
+
+def test_als_recovers_noise_free_planted_tensor():
+    rng = np.random.default_rng(10)
+    prob = synth.dense_problem(rng, (10, 9, 8), 3, 0.3)
+    X = O.DenseTensor(prob.T)
+    u = synth.initial_guess(rng, prob.dims, 3)
+    for _ in range(400):
+        u = O.als_sweep(X, u, 3)
+    f, g = O.fg(X, u, 3)
+    assert f <= 1e-16 * X.norm2 * 1e4
+    # congruence with the planted factors up to permutation and scaling
+    F = O.unpack(u, prob.dims, 3)
+    cong = np.ones((3, 3))
+    for A, B in zip(F, prob.planted):
+        An = A / np.linalg.norm(A, axis=0)
+        Bn = B / np.linalg.norm(B, axis=0)
+        cong *= np.abs(An.T @ Bn)
+    best = max(sum(cong[i, p[i]] for i in range(3)) for p in itertools.permutations(range(3)))
+    assert best >= 3 * (1 - 1e-8)
+
+
+# --------------------------------------------------------------------------
+# Normalisation
+# --------------------------------------------------------------------------
+
+def test_normalize_invariants_and_exact_gradient_rescale():
+    rng = np.random.default_rng(11)
+    dims, R = (5, 6, 4), 4
+    T = rng.standard_normal(dims)
+    X = O.DenseTensor(T)
+    u = synth.initial_guess(rng, dims, R) * np.repeat(rng.uniform(0.1, 3, size=R * 0 + 1), 1)
+    f, g = O.fg(X, u, R)
+    un, gn, lam = O.normalize(u, dims, R, g)
+    f2, g2 = O.fg(X, un, R)
+    assert abs(f2 - f) <= 1e-12 * abs(f)
+    np.testing.assert_allclose(gn, g2, rtol=1e-10, atol=1e-12)
+    assert np.all(np.diff(lam) <= 0)
+    F = O.unpack(un, dims, R)
+    for A in F:
+        np.testing.assert_allclose(np.linalg.norm(A, axis=0), lam ** (1 / 3), rtol=1e-12)
+
+
+def test_normalize_zero_column_left_unscaled():
+    dims, R = (3, 3), 2
+    u = np.arange(1.0, 13.0)
+    F = O.unpack(u.copy(), dims, R)
+    F[0][:, 1] = 0.0
+    un, _, lam = O.normalize(O.pack(F), dims, R)
+    assert lam[-1] == 0.0
+    Fn = O.unpack(un, dims, R)
+    np.testing.assert_array_equal(Fn[1][:, 1], F[1][:, 1])
+
+
+# --------------------------------------------------------------------------
+# N-GMRES Step II: in the linear case it is GMRES (Lemma 1)
+# --------------------------------------------------------------------------
+
+def arnoldi_gmres(A, b, x0, Minv, k):
+    """Right-preconditioned GMRES by Arnoldi: minimise ||b - A x|| over
+    x in x0 + Minv K_k(A Minv, r0) (textbook algorithm, independent of the oracle)."""
+    n = b.size
+    r0 = b - A @ x0
+    beta = np.linalg.norm(r0)
+    V = np.zeros((n, k + 1))
+    H = np.zeros((k + 1, k))
+    V[:, 0] = r0 / beta
+    for j in range(k):
+        w = A @ (Minv @ V[:, j])
+        for i in range(j + 1):
+            H[i, j] = V[:, i] @ w
+            w = w - H[i, j] * V[:, i]
+        H[j + 1, j] = np.linalg.norm(w)
+        V[:, j + 1] = w / H[j + 1, j]
+    e1 = np.zeros(k + 1)
+    e1[0] = beta
+    y = np.linalg.lstsq(H, e1, rcond=None)[0]
+    return x0 + Minv @ (V[:, :k] @ y)
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 7])
+def test_ngmres_step_is_gmres_in_the_linear_case(k):
+    rng = np.random.default_rng(12)
+    n = 30
+    Q = rng.standard_normal((n, n))
+    A = Q @ Q.T + n * np.eye(n)
+    b = rng.standard_normal(n)
+    Minv = np.diag(1.0 / np.diag(A))        # Jacobi preconditioner
+    grad = lambda x: A @ x - b               # g(u) of f = 1/2 u^T A u - b^T u
+    us = [rng.standard_normal(n)]
+    for _ in range(k):                       # stationary iteration (Eq. stat)
+        us.append(us[-1] + Minv @ (b - A @ us[-1]))
+    U = np.array(us[:k])
+    G = np.array([grad(x) for x in us[:k]])
+    ubar = us[k]
+    uhat, alpha = O.ngmres_step(U, G, ubar, grad(ubar), eps=0.0)
+    ref = arnoldi_gmres(A, b, us[0], Minv, k)
+    np.testing.assert_allclose(uhat, ref, rtol=1e-8, atol=1e-10)
+
+
+def test_ngmres_single_vector_closed_form():
+    rng = np.random.default_rng(13)
+    P = 50
+    u0, g0, ub, gb = (rng.standard_normal(P) for _ in range(4))
+    uhat, alpha = O.ngmres_step(u0[None], g0[None], ub, gb, eps=1e-12)
+    p = gb - g0
+    delta = 1e-12 * (p @ p)
+    a = -(p @ gb) / (p @ p + delta)
+    assert abs(alpha[0] - a) <= 1e-14 * abs(a)
+    np.testing.assert_allclose(uhat, ub + a * (ub - u0), rtol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# More-Thuente line search
+# --------------------------------------------------------------------------
+
+def quad_phi(g0, c):
+    return lambda a: (g0 * a + 0.5 * c * a * a, g0 + c * a, None)
+
+
+def test_linesearch_accepts_unit_step_on_matching_quadratic():
+    beta, f, g, _, nfev, info = O.more_thuente(quad_phi(-2.0, 2.0), 0.0, -2.0)
+    assert (beta, nfev, info) == (1.0, 1, 1)
+
+
+def strong_wolfe(phi, beta, f0, g0, mu, eta):
+    f, g, _ = phi(beta)
+    return f <= f0 + mu * beta * g0 + 1e-15 * abs(f0) and abs(g) <= eta * abs(g0)
+
+
+def mt_test_functions():
+    """Test functions of More and Thuente's Section 5 (definitions only)."""
+    def f1(a, b=2.0):
+        return -a / (a * a + b), (a * a - b) / (a * a + b) ** 2
+
+    def f2(a, b=0.004):
+        return (a + b) ** 5 - 2 * (a + b) ** 4, 5 * (a + b) ** 4 - 8 * (a + b) ** 3
+
+    def f3(a, b=0.01, l=39):
+        if a <= 1 - b:
+            p, dp = 1 - a, -1.0
+        elif a >= 1 + b:
+            p, dp = a - 1, 1.0
+        else:
+            p, dp = (a - 1) ** 2 / (2 * b) + b / 2, (a - 1) / b
+        return (p + 2 * (1 - b) / (l * math.pi) * math.sin(l * math.pi * a / 2),
+                dp + (1 - b) * math.cos(l * math.pi * a / 2))
+
+    def gamma(b):
+        return math.sqrt(1 + b * b) - b
+
+    def yanai(b1, b2):
+        def f(a):
+            v = gamma(b1) * math.sqrt((1 - a) ** 2 + b2 * b2) + gamma(b2) * math.sqrt(a * a + b1 * b1)
+            dv = -gamma(b1) * (1 - a) / math.sqrt((1 - a) ** 2 + b2 * b2) + gamma(b2) * a / math.sqrt(a * a + b1 * b1)
+            return v, dv
+        return f
+
+    return [(f1, 1e-3, 1e-1), (f2, 1e-1, 1e-1), (f3, 1e-1, 1e-1),
+            (yanai(1e-3, 1e-3), 1e-3, 1e-3), (yanai(1e-2, 1e-3), 1e-3, 1e-3),
+            (yanai(1e-3, 1e-2), 1e-3, 1e-3)]
+
+
+@pytest.mark.parametrize("case", range(6))
+@pytest.mark.parametrize("a0", [1e-3, 1e-1, 1e1, 1e3])
+def test_linesearch_strong_wolfe_on_published_test_functions(case, a0):
+    fn, mu, eta = mt_test_functions()[case]
+    phi = lambda a: (*fn(a), None)
+    f0, g0 = fn(0.0)
+    opts = O.LSOpts(ftol=mu, gtol=eta, stp0=a0, maxfev=40, xtol=1e-12)
+    beta, f, g, _, nfev, info = O.more_thuente(phi, f0, g0, opts)
+    assert info == 1, (case, a0, info, nfev)
+    assert strong_wolfe(phi, beta, f0, g0, mu, eta)
+    assert nfev <= 20
+
+
+def test_linesearch_rejects_ascent_direction():
+    assert O.more_thuente(quad_phi(1.0, 1.0), 0.0, 1.0)[-1] == -1
+
+
+# --------------------------------------------------------------------------
+# COO sort and segmentation
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [0, 1, 2])
+def test_coo_sort_matches_python_sorted(n):
+    rng = np.random.default_rng(14)
+    dims = (4, 5, 3)
+    coords = synth.distinct_coords(rng, dims, 45)
+    perm, seg_ptr, seg_row = O.coo_sort_mode(coords, n)
+    key = lambda k: tuple(int(coords[k, (n + j) % 3]) for j in range(3))
+    assert list(perm) == sorted(range(45), key=key)
+    assert seg_ptr[0] == 0 and seg_ptr[-1] == 45 and np.all(np.diff(seg_ptr) > 0)
+    rows = coords[perm, n]
+    for s in range(seg_row.size):
+        assert np.all(rows[seg_ptr[s]:seg_ptr[s + 1]] == seg_row[s])
+    assert len(set(seg_row.tolist())) == seg_row.size
+
+
+def test_coo_sort_empty():
+    perm, seg_ptr, seg_row = O.coo_sort_mode(np.zeros((0, 3), dtype=np.int64), 1)
+    assert perm.size == 0 and list(seg_ptr) == [0] and seg_row.size == 0
+
+
+# --------------------------------------------------------------------------
+# Generators
+# --------------------------------------------------------------------------
+
+def test_collinear_factor_has_exact_collinearity():
+    rng = synth.rng_for(99)
+    for c in (0.5, 0.9):
+        A = synth.collinear_factor(rng, 40, 5, c)
+        np.testing.assert_allclose(A.T @ A, synth.collinearity_matrix(5, c), atol=1e-12)
+
+
+def test_noise_scaled_to_eta_of_planted_norm():
+    rng = synth.rng_for(98)
+    prob = synth.dense_problem(rng, (6, 7, 8), 2, 0.5, eta=0.1)
+    TR = O.cp_full(prob.planted)
+    assert abs(np.linalg.norm(prob.T - TR) - 0.1 * np.linalg.norm(TR)) <= 1e-12 * np.linalg.norm(TR)
+
+
+def test_laplacian_matches_paper_worked_example():
+    g = json.load(open(os.path.join(GOLDEN, "laplacian_d2_s2.json")))
+    lap = synth.laplacian_tensor(g["d"], g["s"])
+    got = {tuple(int(x) for x in c): float(v) for c, v in zip(lap.coords, lap.vals)}
+    want = {tuple(c): float(v) for c, v in g["nonzeros"]}
+    assert got == want
+
+
+@pytest.mark.parametrize("d,s", [(1, 5), (2, 4), (3, 3)])
+def test_laplacian_nnz_count(d, s):
+    lap = synth.laplacian_tensor(d, s)
+    assert lap.coords.shape[0] == s ** d + 2 * d * (s - 1) * s ** (d - 1)
+    assert np.unique(lap.coords, axis=0).shape[0] == lap.coords.shape[0]
+
+
+# --------------------------------------------------------------------------
+# Whole N-GMRES solve
+# --------------------------------------------------------------------------
+
+def test_solve_two_way_laplacian_reaches_eckart_young_optimum():
+    """Test Problem II with d = 1 is the s x s tridiagonal Laplacian, an SPD
+    matrix with eigenvalues 2 - 2 cos(k pi / (s + 1)).  For N = 2 the CP problem
+    is best rank-R matrix approximation, whose optimum keeps the R largest
+    eigenvalues: f* = 1/2 sum of the other squared eigenvalues."""
+    s, R = 12, 3
+    lap = synth.laplacian_tensor(1, s)
+    X = O.SparseTensor(lap.coords, lap.vals, lap.dims)
+    lam = np.sort(2 - 2 * np.cos(np.arange(1, s + 1) * np.pi / (s + 1)))
+    fstar = 0.5 * float(np.sum(lam[: s - R] ** 2))
+    u0 = synth.initial_guess(synth.rng_for(97), lap.dims, R)
+    u, g, rep = O.cp_solve(X, u0, O.SolveOpts(R=R, tol=1e-10, maxit=2000))
+    assert rep.converged
+    assert abs(rep.f - fstar) <= 1e-8 * fstar
+
+
+def test_solve_monotone_and_recovers_planted():
+    rng = synth.rng_for(96)
+    prob = synth.dense_problem(rng, (9, 8, 10), 3, 0.9)
+    X = O.DenseTensor(prob.T)
+    u0 = synth.initial_guess(rng, prob.dims, 3)
+    u, g, rep = O.cp_solve(X, u0, O.SolveOpts(R=3, tol=1e-12, maxit=3000))
+    assert rep.converged
+    fs = [h[0] for h in rep.history]
+    assert all(b <= a * (1 + 1e-10) + 1e-14 for a, b in zip(fs, fs[1:]))
+    assert rep.f <= 1e-12 * X.norm2
+
+
+def test_ngmres_beats_als_on_collinear_problem():
+    rng = synth.rng_for(95)
+    prob = synth.dense_problem(rng, (15, 15, 15), 3, 0.9, paper_l1=1, paper_l2=1)
+    X = O.DenseTensor(prob.T)
+    u0 = synth.initial_guess(rng, prob.dims, 3)
+    tol = 1e-9
+    _, _, rep = O.cp_solve(X, u0, O.SolveOpts(R=3, tol=tol, maxit=3000))
+    assert rep.converged
+    u, _, _ = O.normalize(u0, prob.dims, 3)
+    P = O.n_params(prob.dims, 3)
+    als_it = 0
+    while als_it < 3000:
+        u, _, _ = O.normalize(O.als_sweep(X, u, 3), prob.dims, 3)
+        als_it += 1
+        if np.linalg.norm(O.fg(X, u, 3)[1]) / P < tol:
+            break
+    assert rep.iters < als_it
