@@ -1,0 +1,229 @@
+/*
+ * cp.h -- C ABI of the GB300 (sm_103a) library for rank-R canonical (CP)
+ * tensor approximation by N-GMRES-accelerated ALS (De Sterck, "A Nonlinear
+ * GMRES Optimization Algorithm for Canonical Tensor Decomposition").
+ *
+ * Problem (Optimization Problem I, Section 1, Eq. fA): given a tensor T of
+ * size I_1 x ... x I_N, find factor matrices A^(n) (I_n x R) minimising
+ *     f = 1/2 || T - [[A^(1), ..., A^(N)]] ||_F^2 .
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Iterate layout.  An iterate u is one FP64 vector of P = R * sum_n I_n
+ *    entries holding A^(1), ..., A^(N) back to back, each row-major I_n x R
+ *    (the R values of a row are contiguous).  Gradients use the same layout.
+ *  Dense tensors.  Row-major with the LAST index fastest.
+ *  Ownership.  Every array argument belongs to the caller and is only read or
+ *    written during the call (or, for asynchronous calls, by work enqueued on
+ *    the context stream).  The library never frees caller memory.  Handles
+ *    own their internal copies and workspace.
+ *  Pointers.  Unless stated otherwise, array arguments are DEVICE pointers
+ *    on the context's device.  Calls marked "host or device" accept either;
+ *    the library inspects the pointer.
+ *  Streams.  Work is enqueued on the context stream.  Calls whose outputs are
+ *    device arrays return without synchronising; calls with host outputs
+ *    synchronise the stream before returning.
+ *  Errors.  Every call returns a cp_status; nothing is thrown across the ABI.
+ *    cp_last_error() gives a message for the calling thread's last failure.
+ *    Arguments are validated before any work is enqueued.
+ *  Threads.  A context may be used by one thread at a time.
+ */
+#ifndef CP_GB300_H
+#define CP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CP_OK = 0,
+  CP_ERR_ARG = 1,          /* bad argument (null pointer, bad mode, R < 1 ...)   */
+  CP_ERR_SHAPE = 2,        /* inconsistent sizes, coordinates out of range        */
+  CP_ERR_OOM = 3,          /* device allocation failed or budget exceeded          */
+  CP_ERR_CUDA = 4,         /* a CUDA runtime/driver call failed                   */
+  CP_ERR_NOT_SPD = 5,      /* Gammabar^(n) not positive definite after one ridge  */
+  CP_ERR_NONFINITE = 6,    /* NaN or Inf met in f or g                            */
+  CP_ERR_LINESEARCH = 7,   /* line search could not start (not a descent dir.)    */
+  CP_ERR_MAXIT = 8,        /* cp_solve stopped at maxit without meeting tol       */
+  CP_ERR_TIMEOUT = 9,      /* a bounded device wait gave up                       */
+  CP_ERR_BUSY = 10,        /* server has no free slot / budget for a request      */
+  CP_ERR_UNSUPPORTED = 11  /* combination not provided (e.g. precision on COO)    */
+} cp_status;
+
+typedef enum {
+  CP_FP64 = 0,          /* every product and sum in FP64                               */
+  CP_MIXED_BF16X3 = 1   /* MTTKRP on tensor cores: T and the Khatri-Rao tile split   */
+                        /* into bf16 hi+lo, products hi*hi + hi*lo + lo*hi, FP32      */
+                        /* accumulation; everything else stays FP64                   */
+} cp_precision;
+
+typedef enum { CP_DTYPE_F32 = 0, CP_DTYPE_F64 = 1 } cp_dtype;
+
+typedef struct cp_ctx cp_ctx;
+typedef struct cp_tensor cp_tensor;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to enqueue on (borrowed, not destroyed; cudaStreamLegacy selects the legacy
+ * default stream), or NULL to create a private non-blocking stream.
+ * Errors: CP_ERR_ARG, CP_ERR_CUDA. */
+cp_status cp_ctx_create(int device, void* cuda_stream, cp_ctx** out);
+void cp_ctx_destroy(cp_ctx* ctx);
+/* Message of the calling thread's last failed call ("" if none).  The string
+ * stays valid until the thread's next failing call. */
+const char* cp_last_error(void);
+/* Wait for all work on the context stream; return any error that a kernel
+ * recorded in the context's device status word since the last sync. */
+cp_status cp_ctx_sync(cp_ctx* ctx);
+/* The context's cudaStream_t. */
+void* cp_ctx_stream(cp_ctx* ctx);
+
+/* ---------------------------------------------------------------- tensors */
+
+/* Dense tensor from `data` (host or device; row-major, last index fastest,
+ * prod(dims) elements of `dtype`).  The data are copied; the handle keeps one
+ * mode-n matricised copy T_(n) (I_n x prod_{m!=n} I_m, row-major) per mode
+ * (Section 2.3, "mode-n matricization") and ||T||_F^2 in FP64.  2 <= N <= 8,
+ * every dim >= 1.  Synchronous.  Errors: CP_ERR_ARG, CP_ERR_SHAPE, CP_ERR_OOM. */
+cp_status cp_tensor_dense(cp_ctx* ctx, int N, const int64_t* dims, cp_dtype dtype,
+                          const void* data, cp_tensor** out);
+
+/* Sparse tensor in coordinate form (Section 4, "sparse tensors").  coords is
+ * nnz x N int64 row-major (host or device), values FP32 (host or device);
+ * coordinates must be distinct and in range (checked: CP_ERR_SHAPE).  For each
+ * mode n the handle keeps the nonzeros stably sorted by the cyclic key
+ * (i_n, i_{n+1}, ..., i_{n-1}) with segment pointers over runs of equal i_n.
+ * nnz may be 0.  Synchronous. */
+cp_status cp_tensor_coo(cp_ctx* ctx, int N, const int64_t* dims, int64_t nnz,
+                        const int64_t* coords, const float* vals, cp_tensor** out);
+
+/* Order of the tensor, its dims (array of N, host) and ||T||_F^2 (host).
+ * Any output may be NULL. */
+cp_status cp_tensor_info(const cp_tensor* t, int* N, int64_t* dims, double* norm2);
+
+/* Copy mode `mode`'s sort permutation (nnz int64), segment pointers
+ * (nseg + 1 int64) and segment rows (nseg int64) to HOST arrays (any may be
+ * NULL; nseg is written if non-NULL).  COO tensors only; synchronous. */
+cp_status cp_tensor_sorted_mode(cp_ctx* ctx, const cp_tensor* t, int mode, int64_t* perm,
+                                int64_t* seg_ptr, int64_t* seg_row, int64_t* nseg);
+void cp_tensor_destroy(cp_tensor* t);
+
+/* ------------------------------------------------------ multilinear kernels */
+
+/* MTTKRP M^(n) = T_(n) Phibar^(n) (Section 2.3, Eq. Gn and Eq. Phi): for every
+ * i and r, M[i,r] = sum over all other indices of T[...] * prod_{m != n}
+ * A^(m)[i_m, r].  u: iterate (P doubles); out: I_mode x R doubles, row-major.
+ * CP_MIXED_BF16X3 is provided for dense tensors only.  Asynchronous. */
+cp_status cp_mttkrp(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, int mode,
+                    double* out, cp_precision prec);
+
+/* Objective and gradient (Eq. fA, Eq. Gn):
+ *   f = 1/2 (||T||^2 - 2 <T, A_R> + sum_{r,s} Gamma[r,s]),
+ *   G^(n) = -M^(n) + A^(n) Gammabar^(n),
+ * with Gamma, Gammabar^(n) the Hadamard products of the factor Grams (Eq.
+ * Gamma).  f: one device double; g: P device doubles or NULL.  All sums of
+ * f are FP64.  Asynchronous. */
+cp_status cp_fg(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, double* f,
+                double* g, cp_precision prec);
+
+/* One ALS iteration M(u) (Section 2.3, Eq. foopt): for n = 1..N,
+ * A^(n) <- M^(n) (Gammabar^(n))^{-1} by an R x R Cholesky factorisation, with
+ * the factors of modes < n already updated (block Gauss-Seidel).  If a
+ * Cholesky pivot is not positive, one retry with Gammabar + 1e-12 tr/R I;
+ * then CP_ERR_NOT_SPD is recorded (reported by the next sync).  If
+ * `normalize` is non-zero the result is normalised as cp_normalize does.
+ * u is updated in place.  Asynchronous. */
+cp_status cp_als_sweep(cp_ctx* ctx, const cp_tensor* t, int R, double* u, int normalize,
+                       cp_precision prec);
+
+/* Normalisation and reordering (Section 2.3): every column of every factor
+ * is scaled to norm lambda_r^(1/N), lambda_r = prod_n ||a_r^(n)||, and the
+ * terms are stably ordered by decreasing lambda_r.  A term with a zero column
+ * gets lambda_r = 0 and is left unscaled.  If g (same layout) is given it is
+ * rescaled exactly to the gradient at the normalised point (column r of mode
+ * n divided by the scale of that column) and permuted alike.  lambda: R
+ * doubles (sorted) or NULL.  Asynchronous. */
+cp_status cp_normalize(cp_ctx* ctx, int N, const int64_t* dims, int R, double* u, double* g,
+                       double* lambda);
+
+/* ------------------------------------------------------------------ N-GMRES */
+
+/* N-GMRES Step II (Section 2.1, Eq. accel, Eq. linearize, Eq. normal): with
+ * p_j = gbar - G_j, solve (P^T P + delta I) alpha = -P^T gbar by Cholesky,
+ * delta = eps * max_j (P^T P)_jj (alpha = 0 if that maximum is 0), and form
+ * uhat = ubar + sum_j alpha_j (ubar - U_j).
+ * U, G: m x Pn row-major (window iterates and their gradients, any order);
+ * ubar, gbar, uhat: Pn doubles; alpha: m doubles (may be NULL).
+ * 1 <= m <= 64.  Asynchronous. */
+cp_status ngmres_step(cp_ctx* ctx, int64_t Pn, int m, const double* U, const double* G,
+                      const double* ubar, const double* gbar, double eps, double* uhat,
+                      double* alpha);
+
+/* Line-search parameters (Section 2.4 and More & Thuente 1994).
+ * Defaults: ftol 1e-4, gtol 1e-2, xtol 1e-15, stpmin 1e-15, stpmax 1e15,
+ * stp0 1, maxfev 20. */
+typedef struct {
+  double ftol, gtol, xtol, stpmin, stpmax, stp0;
+  int maxfev;
+} cp_ls_opts;
+
+void cp_ls_opts_default(cp_ls_opts* o);
+
+/* More-Thuente line search on phi(beta) = f(x0 + beta d), phi'(beta) =
+ * g(x0 + beta d)^T d (Step III, Eq. linesearch), evaluating f and g with
+ * cp_fg.  x0, g0, d: device (P); f0: f(x0).  On return x = x0 + stp d and
+ * f, g are evaluated there (x, g device; f, stp, nfev, info host).  info as in
+ * More-Thuente: 1 strong Wolfe met, 2 xtol, 3 maxfev, 4 stpmin, 5 stpmax,
+ * 6 rounding; if g0^T d >= 0 returns CP_ERR_LINESEARCH.  Synchronous. */
+cp_status linesearch(cp_ctx* ctx, const cp_tensor* t, int R, const double* x0, double f0,
+                     const double* g0, const double* d, const cp_ls_opts* opts, double* x,
+                     double* f, double* g, double* stp, int* nfev, int* info,
+                     cp_precision prec);
+
+/* ---------------------------------------------------------------- the solve */
+
+typedef struct {
+  int R;               /* rank                                                   */
+  int w;               /* N-GMRES window (Section 2.4: 20)                       */
+  int maxit;           /* iteration limit                                        */
+  double tol;          /* stop when ||g||_2 / P < tol                            */
+  double eps;          /* delta = eps * max diag(P^T P) (Section 2.4: 1e-12)     */
+  cp_precision prec;   /* precision of MTTKRP in the iterations                  */
+  int polish;          /* mixed precision: finish with FP64 iterations until the */
+                       /* FP64 gradient meets tol (1 = on)                       */
+  double mixed_tol_factor; /* mixed phase stops at tol * factor before polishing */
+  cp_ls_opts ls;
+} cp_solve_opts;
+
+typedef struct {
+  int iters, fg_evals, als_sweeps, restarts, ls_failures, converged;
+  int mixed_iters, fp64_iters;
+  double f, gnorm_over_P, normT2;
+  double t_total_s;
+} cp_solve_report;
+
+void cp_solve_opts_default(cp_solve_opts* o, int R);
+
+/* N-GMRES optimisation algorithm (Algorithm 1; Steps I-III of Section 2.1;
+ * window start-up of Section 2.1; restart rule and delta I of Section 2.1):
+ *   u0 <- normalise(u0); window {(u0, g(u0))};
+ *   repeat: ubar = normalise(ALS(u_i)); uhat = ngmres(window; ubar);
+ *           uhat <- normalise(uhat); d = uhat - ubar; s = g(ubar)^T d;
+ *           s >= 0: restart (u_{i+1} = ubar, window {(ubar, g(ubar))});
+ *           else u_{i+1} = normalise(ubar + beta* d) by the line search;
+ *           push (u_{i+1}, g(u_{i+1})) keeping the last w;
+ *   until ||g(u_i)||_2 / P < tol or maxit.
+ * u: P doubles, host or device; initial guess in, solution out.  rep: host,
+ * may be NULL.  Synchronous.  Returns CP_ERR_MAXIT if tol was not met. */
+cp_status cp_solve(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* opts, double* u,
+                   cp_solve_report* rep);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CP_GB300_H */

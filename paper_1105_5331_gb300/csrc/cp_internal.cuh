@@ -1,0 +1,185 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here is part of the C ABI (include/cp.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/cp.h"
+
+#define CP_MAX_N 8
+#define CP_MAX_R 64       // largest rank the kernels accept
+#define CP_MAX_W 64       // largest N-GMRES window
+
+namespace cpg {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+cp_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define CP_CUDA(expr)                                                         \
+  do {                                                                        \
+    cudaError_t e__ = (expr);                                                 \
+    if (e__ != cudaSuccess) return cpg::cuda_fail(e__, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+#define CP_LAUNCH_CHECK()                                                     \
+  do {                                                                        \
+    cudaError_t e__ = cudaGetLastError();                                     \
+    if (e__ != cudaSuccess) return cpg::cuda_fail(e__, "kernel launch", __FILE__, __LINE__); \
+  } while (0)
+
+#define CP_TRY(expr)                                                          \
+  do {                                                                        \
+    cp_status s__ = (expr);                                                   \
+    if (s__ != CP_OK) return s__;                                             \
+  } while (0)
+
+// Device status word: kernels record the first error (cp_status value) they
+// meet with atomicCAS; the host reads and clears it at sync points.
+__device__ __forceinline__ void record_status(int* st, int code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+// Mode bookkeeping of an iterate u = [A^(1); ...; A^(N)].
+struct Layout {
+  int N = 0;
+  int R = 0;
+  int64_t dims[CP_MAX_N] = {0};
+  int64_t off[CP_MAX_N + 1] = {0};   // element offset of A^(n) in u; off[N] = P
+  int64_t P() const { return off[N]; }
+  void set(int N_, const int64_t* d, int R_) {
+    N = N_;
+    R = R_;
+    off[0] = 0;
+    for (int n = 0; n < N; ++n) {
+      dims[n] = d[n];
+      off[n + 1] = off[n] + d[n] * R;
+    }
+  }
+};
+
+// Pointers of the factor matrices of one iterate, passed to kernels by value.
+struct FactorPtrs {
+  const double* A[CP_MAX_N];
+  int64_t I[CP_MAX_N];
+  int N;
+  int R;
+};
+
+inline FactorPtrs factor_ptrs(const Layout& L, const double* u) {
+  FactorPtrs f;
+  f.N = L.N;
+  f.R = L.R;
+  for (int n = 0; n < CP_MAX_N; ++n) {
+    f.A[n] = n < L.N ? u + L.off[n] : nullptr;
+    f.I[n] = n < L.N ? L.dims[n] : 0;
+  }
+  return f;
+}
+
+}  // namespace cpg
+
+// ------------------------------------------------------------------ handles
+struct cp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  int* d_status = nullptr;          // device status word
+  double* h_pinned = nullptr;       // small pinned host scratch (64 doubles)
+  int* h_pinned_i = nullptr;        // small pinned host scratch (64 ints)
+};
+
+struct CooMode {
+  int64_t nseg = 0;
+  int64_t nunits = 0;
+  int64_t* perm = nullptr;       // nnz: position in the input order
+  int64_t* seg_ptr = nullptr;    // nseg + 1
+  int32_t* seg_row = nullptr;    // nseg: the i_n of each segment
+  int64_t* seg_unit = nullptr;   // nseg + 1: first work unit of each segment
+  int64_t* unit_start = nullptr; // nunits + 1: first nonzero of each work unit
+  int32_t* other = nullptr;      // (N-1) x nnz: other coordinates, cyclic order n+1..n-1
+  float* vals = nullptr;         // nnz values in sorted order
+};
+
+struct cp_tensor {
+  int kind = 0;                  // 0 dense, 1 coo
+  int N = 0;
+  int device = 0;
+  int64_t dims[CP_MAX_N] = {0};
+  int64_t K = 0;                 // prod dims (dense)
+  double norm2 = 0.0;            // ||T||_F^2
+  cp_dtype dtype = CP_DTYPE_F32;
+  // dense: per-mode matricised copies T_(n), row-major I_n x Kbar_n
+  void* Tn[CP_MAX_N] = {nullptr};
+  // dense mixed precision: per-mode bf16 hi/lo planes of T_(n) with a row
+  // pitch padded to a multiple of 64 elements (created on first use)
+  __nv_bfloat16* Thi[CP_MAX_N] = {nullptr};
+  __nv_bfloat16* Tlo[CP_MAX_N] = {nullptr};
+  int64_t pitch[CP_MAX_N] = {0};
+  // coo
+  int64_t nnz = 0;
+  CooMode modes[CP_MAX_N];
+};
+
+namespace cpg {
+
+inline int64_t kbar(const cp_tensor* t, int n) { return t->K / t->dims[n]; }
+
+// --------------------------------------------------------- kernel entry points
+// Dense MTTKRP, FP64 arithmetic.  Writes out (I_n x R).
+cp_status mttkrp_dense_f64(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u,
+                           int mode, double* out);
+// Dense MTTKRP, bf16x3 split products on tcgen05 tensor cores, FP32 accumulate.
+cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u,
+                             int mode, double* out);
+// Sparse MTTKRP from the mode-sorted copy (FP64 or FP32 products).
+cp_status mttkrp_sparse(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u,
+                        int mode, double* out, cp_precision prec);
+cp_status coo_build(cp_ctx* ctx, cp_tensor* t, const int64_t* d_coords, const float* d_vals);
+
+cp_status mttkrp_any(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, int mode,
+                     double* out, cp_precision prec);
+
+// Grams G_m = A_m^T A_m of all modes into grams (N x R x R).
+cp_status grams_all(cp_ctx* ctx, const Layout& L, const double* u, double* grams);
+// One ALS mode update: A_n <- M Gammabar^-1 (Gammabar from grams), then
+// refresh grams[n] from the new A_n.
+cp_status als_mode_solve(cp_ctx* ctx, const Layout& L, double* u, int mode, const double* M,
+                         double* grams);
+// f and g from M^(n) (all modes, packed like u) and grams.
+cp_status fg_assemble(cp_ctx* ctx, const Layout& L, const double* u, const double* M_all,
+                      const double* grams, double norm2, double* f, double* g);
+// Normalise src (and gsrc) into dst (and gdst); lambda (R) optional.
+cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double* dst,
+                         const double* gsrc, double* gdst, double* lambda);
+
+// Window-indexed N-GMRES Step II.  Window row j (oldest first) is at ring slot
+// (start + j) % wcap.
+cp_status ngmres_core(cp_ctx* ctx, int64_t P, int m, const double* U, const double* G,
+                      int start, int wcap, const double* ubar, const double* gbar, double eps,
+                      double* uhat, double* alpha);
+
+// Deterministic FP64 dot product: out = x . y (device scalar).
+cp_status dot(cp_ctx* ctx, int64_t n, const double* x, const double* y, double* out);
+// Device scalar helpers.
+cp_status axpy_scalar(cp_ctx* ctx, int64_t n, const double* x0, const double* d,
+                      const double* stp, double* x);  // x = x0 + (*stp) d
+cp_status sub(cp_ctx* ctx, int64_t n, const double* a, const double* b, double* out);  // a - b
+
+// Full cp_fg with workspace.
+cp_status fg_eval(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, double* f,
+                  double* g, cp_precision prec);
+
+// Workspace (stream-ordered).
+cp_status ws_alloc(cp_ctx* ctx, void** p, size_t bytes);
+void ws_free(cp_ctx* ctx, void* p);
+
+cp_status read_status(cp_ctx* ctx);
+
+}  // namespace cpg

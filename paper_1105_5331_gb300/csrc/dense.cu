@@ -1,0 +1,239 @@
+// Dense tensors: per-mode matricised copies, ||T||^2, and the FP64 MTTKRP.
+//
+// Layout decision: the handle keeps one row-major copy of T_(n) for every mode
+// n (I_n x Kbar_n, Kbar_n = prod_{m != n} I_m, column index over the other
+// modes in natural order with the last one fastest).  Every mode's MTTKRP
+// M^(n) = T_(n) Phibar^(n) (Section 2.3, Eq. Gn) is then the same row-major,
+// contiguous-in-the-contraction product, whatever n is.  The extra memory
+// (N copies) is small next to the GPU's HBM.
+#include "cp_internal.cuh"
+
+namespace cpg {
+
+namespace {
+
+// T_(n)[i, l*Q + q] = T[l, i, q] where L = prod_{m<n} I_m, Q = prod_{m>n} I_m.
+template <typename TT>
+__global__ void matricize_kernel(const TT* __restrict__ src, TT* __restrict__ dst, int64_t L,
+                                 int64_t I, int64_t Q) {
+  const int64_t Kbar = L * Q;
+  const int64_t total = I * Kbar;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = o / Kbar;
+    const int64_t kb = o - i * Kbar;
+    const int64_t l = kb / Q;
+    const int64_t q = kb - l * Q;
+    dst[o] = src[(l * I + i) * Q + q];
+  }
+}
+
+// Deterministic sum of squares: per-block tree partials.
+template <typename TT>
+__global__ void sumsq_partial_kernel(const TT* __restrict__ x, int64_t n, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)x[k];
+    acc = fma(v, v, acc);
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) acc += part[k];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// Factors of the modes other than n, in natural order (last one fastest in k).
+struct KRDesc {
+  const double* A[CP_MAX_N - 1];
+  int64_t I[CP_MAX_N - 1];
+  int cnt;
+};
+
+constexpr int kF64BK = 32;     // contraction elements per tile
+constexpr int kF64RSUB = 16;   // ranks per thread
+
+// FP64 MTTKRP, one CTA per contiguous range of the contraction index kbar.
+// Each CTA builds the Khatri-Rao tile KR[kbar, r] = prod_{m != n} A_m[i_m, r]
+// for kF64BK columns in shared memory (FP64), then every thread owns one row
+// i of T_(n) and up to kF64RSUB ranks and accumulates T[i, kbar] * KR[kbar, r].
+// The CTA writes its partial I x R sum; a second kernel adds the partials in
+// a fixed order, so results do not depend on scheduling.
+template <typename TT>
+__global__ void __launch_bounds__(256) mttkrp_f64_kernel(const TT* __restrict__ Tn, int64_t I,
+                                                          int64_t Kbar, KRDesc kr, int R,
+                                                          int64_t tiles_per_cta,
+                                                          double* __restrict__ partial) {
+  extern __shared__ double kr_tile[];  // [kF64BK][R]
+  const int nsplit = (R + kF64RSUB - 1) / kF64RSUB;
+  const int64_t k_begin = (int64_t)blockIdx.x * tiles_per_cta * kF64BK;
+  const int64_t k_end = min(Kbar, k_begin + tiles_per_cta * kF64BK);
+  const int rows_per_pass = blockDim.x / nsplit;
+  const int my_row = threadIdx.x / nsplit;
+  const int r0 = (threadIdx.x % nsplit) * kF64RSUB;
+  const int rcount = min(kF64RSUB, R - r0);
+  double* out = partial + (int64_t)blockIdx.x * I * R;
+
+  for (int64_t row_base = 0; row_base < I; row_base += rows_per_pass) {
+    const int64_t row = row_base + my_row;
+    const bool active = my_row < rows_per_pass && row < I;
+    double acc[kF64RSUB];
+#pragma unroll
+    for (int j = 0; j < kF64RSUB; ++j) acc[j] = 0.0;
+    for (int64_t k0 = k_begin; k0 < k_end; k0 += kF64BK) {
+      const int kt = (int)min((int64_t)kF64BK, k_end - k0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < kt * R; e += blockDim.x) {
+        const int kk = e / R;
+        const int r = e - kk * R;
+        int64_t rem = k0 + kk;
+        double v = 1.0;
+        for (int j = kr.cnt - 1; j >= 0; --j) {
+          const int64_t q = rem / kr.I[j];
+          const int64_t idx = rem - q * kr.I[j];
+          rem = q;
+          v *= kr.A[j][idx * R + r];
+        }
+        kr_tile[kk * R + r] = v;
+      }
+      __syncthreads();
+      if (active) {
+        const TT* trow = Tn + row * Kbar + k0;
+        for (int kk = 0; kk < kt; ++kk) {
+          const double x = (double)trow[kk];
+          const double* krow = kr_tile + kk * R + r0;
+#pragma unroll
+          for (int j = 0; j < kF64RSUB; ++j)
+            if (j < rcount) acc[j] = fma(x, krow[j], acc[j]);
+        }
+      }
+    }
+    if (active)
+      for (int j = 0; j < rcount; ++j) out[row * R + r0 + j] = acc[j];
+  }
+}
+
+// M[e] = sum_c partial[c][e], c in increasing order.
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nparts, int64_t n,
+                                       double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nparts; ++c) s += partial[(int64_t)c * n + e];
+    out[e] = s;
+  }
+}
+
+}  // namespace
+
+cp_status reduce_partials(cp_ctx* ctx, const double* partial, int nparts, int64_t n, double* out) {
+  const int threads = 256;
+  int64_t blocks = (n + threads - 1) / threads;
+  if (blocks > 4 * ctx->num_sms) blocks = 4 * ctx->num_sms;
+  if (blocks < 1) blocks = 1;
+  reduce_partials_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(partial, nparts, n, out);
+  CP_LAUNCH_CHECK();
+  return CP_OK;
+}
+
+cp_status sumsq(cp_ctx* ctx, const void* x, cp_dtype dt, int64_t n, double* d_out) {
+  const int threads = 256;
+  int nb = (int)std::min<int64_t>((n + threads - 1) / threads, 2 * ctx->num_sms);
+  if (nb < 1) nb = 1;
+  double* part = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&part, sizeof(double) * nb));
+  if (dt == CP_DTYPE_F64)
+    sumsq_partial_kernel<double><<<nb, threads, 0, ctx->stream>>>((const double*)x, n, part);
+  else
+    sumsq_partial_kernel<float><<<nb, threads, 0, ctx->stream>>>((const float*)x, n, part);
+  CP_LAUNCH_CHECK();
+  sum_partials_kernel<<<1, 256, 0, ctx->stream>>>(part, nb, d_out);
+  CP_LAUNCH_CHECK();
+  ws_free(ctx, part);
+  return CP_OK;
+}
+
+cp_status dense_build(cp_ctx* ctx, cp_tensor* t, const void* d_data) {
+  const size_t esz = t->dtype == CP_DTYPE_F64 ? 8 : 4;
+  for (int n = 0; n < t->N; ++n) {
+    CP_CUDA(cudaMalloc(&t->Tn[n], esz * (size_t)t->K));
+    int64_t L = 1, Q = 1;
+    for (int m = 0; m < n; ++m) L *= t->dims[m];
+    for (int m = n + 1; m < t->N; ++m) Q *= t->dims[m];
+    int64_t blocks = (t->K + 255) / 256;
+    if (blocks > 16 * ctx->num_sms) blocks = 16 * ctx->num_sms;
+    if (n == 0) {
+      CP_CUDA(cudaMemcpyAsync(t->Tn[0], d_data, esz * (size_t)t->K, cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+    } else if (t->dtype == CP_DTYPE_F64) {
+      matricize_kernel<double><<<(unsigned)blocks, 256, 0, ctx->stream>>>(
+          (const double*)d_data, (double*)t->Tn[n], L, t->dims[n], Q);
+    } else {
+      matricize_kernel<float><<<(unsigned)blocks, 256, 0, ctx->stream>>>(
+          (const float*)d_data, (float*)t->Tn[n], L, t->dims[n], Q);
+    }
+    CP_LAUNCH_CHECK();
+  }
+  double* d_norm = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&d_norm, sizeof(double)));
+  CP_TRY(sumsq(ctx, d_data, t->dtype, t->K, d_norm));
+  CP_CUDA(cudaMemcpyAsync(ctx->h_pinned, d_norm, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CP_CUDA(cudaStreamSynchronize(ctx->stream));
+  t->norm2 = ctx->h_pinned[0];
+  ws_free(ctx, d_norm);
+  return CP_OK;
+}
+
+cp_status mttkrp_dense_f64(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u,
+                           int mode, double* out) {
+  const int R = L.R;
+  const int64_t I = t->dims[mode];
+  const int64_t Kb = kbar(t, mode);
+  KRDesc kr;
+  kr.cnt = 0;
+  for (int m = 0; m < t->N; ++m) {
+    if (m == mode) continue;
+    kr.A[kr.cnt] = u + L.off[m];
+    kr.I[kr.cnt] = t->dims[m];
+    ++kr.cnt;
+  }
+  const int nsplit = (R + kF64RSUB - 1) / kF64RSUB;
+  int64_t want = ((I * nsplit + 31) / 32) * 32;
+  const int threads = (int)std::max<int64_t>(32, std::min<int64_t>(256, want));
+  const int64_t ntiles = (Kb + kF64BK - 1) / kF64BK;
+  const int64_t target = 2 * (int64_t)ctx->num_sms;
+  const int64_t tiles_per_cta = (ntiles + target - 1) / target;
+  const int grid = (int)((ntiles + tiles_per_cta - 1) / tiles_per_cta);
+  double* partial = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&partial, sizeof(double) * (size_t)grid * I * R));
+  const size_t smem = sizeof(double) * kF64BK * R;
+  if (t->dtype == CP_DTYPE_F64)
+    mttkrp_f64_kernel<double><<<grid, threads, smem, ctx->stream>>>(
+        (const double*)t->Tn[mode], I, Kb, kr, R, tiles_per_cta, partial);
+  else
+    mttkrp_f64_kernel<float><<<grid, threads, smem, ctx->stream>>>(
+        (const float*)t->Tn[mode], I, Kb, kr, R, tiles_per_cta, partial);
+  CP_LAUNCH_CHECK();
+  CP_TRY(reduce_partials(ctx, partial, grid, I * R, out));
+  ws_free(ctx, partial);
+  return CP_OK;
+}
+
+}  // namespace cpg

@@ -1,0 +1,28 @@
+// Device-resident state of the More-Thuente line search (Step III).
+#pragma once
+
+#include "cp_internal.cuh"
+
+namespace cpg {
+
+struct MTState {
+  double f0, g0;                  // phi(0), phi'(0)
+  double stp;                     // next trial step
+  double stp_eval;                // step of the last evaluation
+  double f, g;                    // phi, phi' at stp_eval
+  double lo_a, lo_f, lo_g;        // best point (a_l)
+  double hi_a, hi_f, hi_g;        // other end of the interval (a_u)
+  double width, width1, imin, imax;
+  double ftol, gtol, xtol, stpmin, stpmax;
+  int maxfev, nfev, info, done, brackt, stage;
+};
+
+cp_status mt_start(cp_ctx* ctx, MTState* st, const double* f0, const double* g0,
+                   const cp_ls_opts& o);
+cp_status mt_iterate(cp_ctx* ctx, MTState* st, const double* f, const double* g);
+cp_status run_linesearch(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* x0,
+                         const double* f0, const double* slope, const double* d,
+                         const cp_ls_opts& o, double* x, double* fx, double* gx, double* gd,
+                         MTState* st, cp_precision prec, MTState* host_out);
+
+}  // namespace cpg

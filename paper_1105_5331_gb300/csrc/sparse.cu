@@ -1,0 +1,556 @@
+// Sparse (COO) tensors (Section 4): per-mode sorted copies and the sparse
+// MTTKRP M^(n) = T_(n) Phibar^(n) over the nonzeros only (Section 2.3).
+//
+// Build, for every mode n (once per tensor):
+//   * stable LSD radix sort (4-bit digits, written here) of the nonzero
+//     indices by the cyclic key (i_n, i_{n+1}, ..., i_{n-1}): one stable pass
+//     per digit, components taken from least to most significant;
+//   * segments = runs of equal i_n (head flags + exclusive scan);
+//   * work units = segments cut into chunks of at most kUnit nonzeros;
+//   * the other coordinates as int32 planes and the values, in sorted order.
+// MTTKRP: one warp per unit; each lane takes nonzeros of the unit in turn,
+// gathers the factor rows of the other modes, multiplies, and accumulates R
+// partial sums; a butterfly shuffle reduction gives the unit's row sum
+// (fixed order, no atomics); a last kernel adds the units of each segment
+// in order into M.  Rows without nonzeros are zero.
+#include <algorithm>
+#include <vector>
+
+#include "cp_internal.cuh"
+
+namespace cpg {
+
+cp_status sumsq(cp_ctx* ctx, const void* x, cp_dtype dt, int64_t n, double* d_out);
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kBins = 16;
+constexpr int kUnit = 256;            // nonzeros per MTTKRP work unit
+
+// ------------------------------------------------------------- scans (int64)
+// Exclusive scan, tile of 2048 per block: block sums, then a one-block scan
+// of the sums, then the per-tile scans with the carried offset.
+__global__ void tile_sum_kernel(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ sums) {
+  __shared__ int64_t sh[kSortThreads];
+  const int64_t base = (int64_t)blockIdx.x * kSortTile + threadIdx.x * kSortItems;
+  int64_t s = 0;
+  for (int i = 0; i < kSortItems; ++i)
+    if (base + i < n) s += in[base + i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = kSortThreads / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = sh[0];
+}
+
+// In-place exclusive scan of x[0..n) by one block of 1024 threads; total to *total.
+__global__ void single_block_scan_kernel(int64_t* __restrict__ x, int64_t n, int64_t* total) {
+  __shared__ int64_t sh[1024];
+  const int64_t per = (n + 1023) / 1024;
+  const int64_t b = threadIdx.x * per;
+  const int64_t e = min(n, b + per);
+  int64_t s = 0;
+  for (int64_t k = b; k < e; ++k) s += x[k];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int64_t v = (int)threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t run = threadIdx.x ? sh[threadIdx.x - 1] : 0;
+  for (int64_t k = b; k < e; ++k) {
+    const int64_t v = x[k];
+    x[k] = run;
+    run += v;
+  }
+  if (threadIdx.x == 1023 && total) *total = sh[1023];
+}
+
+__global__ void tile_scan_kernel(const int64_t* __restrict__ in, int64_t n,
+                                 const int64_t* __restrict__ offs, int64_t* __restrict__ out) {
+  __shared__ int64_t sh[kSortThreads];
+  const int64_t base = (int64_t)blockIdx.x * kSortTile + threadIdx.x * kSortItems;
+  int64_t v[kSortItems];
+  int64_t s = 0;
+  for (int i = 0; i < kSortItems; ++i) {
+    v[i] = base + i < n ? in[base + i] : 0;
+    s += v[i];
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < kSortThreads; off <<= 1) {
+    int64_t t = (int)threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int64_t run = offs[blockIdx.x] + (threadIdx.x ? sh[threadIdx.x - 1] : 0);
+  for (int i = 0; i < kSortItems; ++i) {
+    if (base + i < n) out[base + i] = run;
+    run += v[i];
+  }
+}
+
+// ----------------------------------------------------------------- radix sort
+__device__ __forceinline__ int digit_of(const int64_t* coords, int N, int c, int shift, int64_t idx) {
+  return (int)((coords[idx * N + c] >> shift) & (kBins - 1));
+}
+
+__global__ void radix_hist_kernel(const int64_t* __restrict__ perm, const int64_t* __restrict__ coords,
+                                  int N, int c, int shift, int64_t n, int64_t* __restrict__ hist,
+                                  int64_t ntiles) {
+  __shared__ int cnt[kBins];
+  if (threadIdx.x < kBins) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile + threadIdx.x * kSortItems;
+  for (int i = 0; i < kSortItems; ++i)
+    if (base + i < n) atomicAdd(&cnt[digit_of(coords, N, c, shift, perm[base + i])], 1);
+  __syncthreads();
+  if (threadIdx.x < kBins) hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter: thread t owns items [t*8, t*8+8) of the tile, in order.
+__global__ void radix_scatter_kernel(const int64_t* __restrict__ perm_in,
+                                     const int64_t* __restrict__ coords, int N, int c, int shift,
+                                     int64_t n, const int64_t* __restrict__ hist_scan,
+                                     int64_t ntiles, int64_t* __restrict__ perm_out) {
+  __shared__ int cnt[kBins * kSortThreads];   // [bin][thread]
+  __shared__ int tsum[kSortThreads];
+  const int64_t base = (int64_t)blockIdx.x * kSortTile + threadIdx.x * kSortItems;
+  int64_t item[kSortItems];
+  int dig[kSortItems];
+  int local[kBins];
+#pragma unroll
+  for (int b = 0; b < kBins; ++b) local[b] = 0;
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    if (base + i < n) {
+      item[i] = perm_in[base + i];
+      dig[i] = digit_of(coords, N, c, shift, item[i]);
+      local[dig[i]]++;
+    } else {
+      dig[i] = -1;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < kBins; ++b) cnt[b * kSortThreads + threadIdx.x] = local[b];
+  __syncthreads();
+  // exclusive scan of cnt in (bin, thread) order: thread t scans entries
+  // [t*16, t*16+16), then a block scan of the per-thread sums.
+  int run = 0;
+  int vals[kBins];
+#pragma unroll
+  for (int k = 0; k < kBins; ++k) {
+    vals[k] = cnt[threadIdx.x * kBins + k];
+    run += vals[k];
+  }
+  tsum[threadIdx.x] = run;
+  __syncthreads();
+  for (int off = 1; off < kSortThreads; off <<= 1) {
+    int t = (int)threadIdx.x >= off ? tsum[threadIdx.x - off] : 0;
+    __syncthreads();
+    tsum[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int ex = threadIdx.x ? tsum[threadIdx.x - 1] : 0;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kBins; ++k) {
+    cnt[threadIdx.x * kBins + k] = ex;
+    ex += vals[k];
+  }
+  __syncthreads();
+  int pos[kBins];
+#pragma unroll
+  for (int b = 0; b < kBins; ++b)
+    pos[b] = cnt[b * kSortThreads + threadIdx.x] - cnt[b * kSortThreads];
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    if (dig[i] >= 0) {
+      const int b = dig[i];
+      const int64_t dst = hist_scan[(int64_t)b * ntiles + blockIdx.x] + pos[b];
+      pos[b]++;
+      perm_out[dst] = item[i];
+    }
+  }
+}
+
+__global__ void iota_kernel(int64_t* __restrict__ p, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    p[k] = k;
+}
+
+__global__ void range_check_kernel(const int64_t* __restrict__ coords, int64_t nnz, int N,
+                                   const int64_t* __restrict__ dims, int* status) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz * N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(k % N);
+    const int64_t v = coords[k];
+    if (v < 0 || v >= dims[n]) record_status(status, CP_ERR_SHAPE);
+  }
+}
+
+// Segment heads of the sorted order: flag[e] = 1 if i_n changes at e.
+__global__ void head_flags_kernel(const int64_t* __restrict__ perm, const int64_t* __restrict__ coords,
+                                  int N, int n, int64_t nnz, int64_t* __restrict__ flag) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = coords[perm[e] * N + n];
+    flag[e] = (e == 0 || coords[perm[e - 1] * N + n] != r) ? 1 : 0;
+  }
+}
+
+// Duplicate check on a fully sorted order: neighbours must differ somewhere.
+__global__ void dup_check_kernel(const int64_t* __restrict__ perm, const int64_t* __restrict__ coords,
+                                 int N, int64_t nnz, int* status) {
+  for (int64_t e = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t* a = coords + perm[e - 1] * N;
+    const int64_t* b = coords + perm[e] * N;
+    bool same = true;
+    for (int k = 0; k < N; ++k) same = same && (a[k] == b[k]);
+    if (same) record_status(status, CP_ERR_SHAPE);
+  }
+}
+
+__global__ void segments_kernel(const int64_t* __restrict__ perm, const int64_t* __restrict__ coords, int N,
+                                int n, int64_t nnz, const int64_t* __restrict__ flag,
+                                const int64_t* __restrict__ segidx, int64_t* __restrict__ seg_ptr,
+                                int32_t* __restrict__ seg_row) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    if (flag[e]) {
+      const int64_t s = segidx[e];
+      seg_ptr[s] = e;
+      seg_row[s] = (int32_t)coords[perm[e] * N + n];
+    }
+  }
+}
+
+__global__ void units_count_kernel(const int64_t* __restrict__ seg_ptr, int64_t nseg, int64_t* __restrict__ cnt) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg; s += (int64_t)gridDim.x * blockDim.x)
+    cnt[s] = (seg_ptr[s + 1] - seg_ptr[s] + kUnit - 1) / kUnit;
+}
+
+__global__ void units_fill_kernel(const int64_t* __restrict__ seg_ptr, int64_t nseg,
+                                  const int64_t* __restrict__ ubase, int64_t* __restrict__ unit_start,
+                                  int64_t nunits, int64_t nnz) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = seg_ptr[s], e = seg_ptr[s + 1];
+    int64_t u = ubase[s];
+    for (int64_t k = b; k < e; k += kUnit) unit_start[u++] = k;
+    if (s == nseg - 1) unit_start[nunits] = nnz;
+  }
+}
+
+__global__ void gather_sorted_kernel(const int64_t* __restrict__ perm, const int64_t* __restrict__ coords,
+                                     const float* __restrict__ vals, int N, int n, int64_t nnz,
+                                     int32_t* __restrict__ other, float* __restrict__ svals) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = perm[e];
+    svals[e] = vals[p];
+    for (int j = 0; j < N - 1; ++j) other[(int64_t)j * nnz + e] = (int32_t)coords[p * N + (n + 1 + j) % N];
+  }
+}
+
+// ------------------------------------------------------------------- MTTKRP
+struct Tables {
+  const void* A[CP_MAX_N - 1];   // factor of the j-th other mode (cyclic order), row stride RP
+};
+
+// Copy factor m of u into a padded table (row stride RP) of type TT.
+template <typename TT>
+__global__ void table_kernel(const double* __restrict__ A, int64_t I, int R, int RP, TT* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < I * RP; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = k / RP;
+    const int r = (int)(k - i * RP);
+    out[k] = r < R ? (TT)A[i * R + r] : (TT)0;
+  }
+}
+
+template <typename TT, int RB>
+__global__ void __launch_bounds__(256) mttkrp_coo_kernel(const int32_t* __restrict__ other,
+                                                         const float* __restrict__ vals, int64_t nnz,
+                                                         int nothers, const int64_t* __restrict__ unit_start,
+                                                         int64_t nunits, Tables tab, int R, int RP,
+                                                         double* __restrict__ partial) {
+  const int lane = threadIdx.x & 31;
+  const int64_t unit = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (unit >= nunits) return;
+  const int64_t b = unit_start[unit], e = unit_start[unit + 1];
+  TT acc[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) acc[r] = (TT)0;
+  for (int64_t k = b + lane; k < e; k += 32) {
+    TT prod[RB];
+    const TT v = (TT)vals[k];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) prod[r] = v;
+    for (int j = 0; j < nothers; ++j) {
+      const int64_t idx = other[(int64_t)j * nnz + k];
+      const TT* row = (const TT*)tab.A[j] + idx * RP;
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        if (r < RP) prod[r] *= row[r];
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] += prod[r];
+  }
+  // butterfly reduction: every lane ends with the same, fixed-order sum
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    double s = (double)acc[r];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0 && r < R) partial[unit * R + r] = s;
+  }
+}
+
+// M[seg_row[s], :] = sum of the partials of the units of segment s.
+__global__ void coo_finalize_kernel(const int64_t* __restrict__ seg_unit, int64_t nseg,
+                                    const int32_t* __restrict__ seg_row, const double* __restrict__ partial,
+                                    int R, double* __restrict__ M) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nseg * R; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = k / R;
+    const int r = (int)(k - s * R);
+    double v = 0.0;
+    for (int64_t u = seg_unit[s]; u < seg_unit[s + 1]; ++u) v += partial[u * R + r];
+    M[(int64_t)seg_row[s] * R + r] = v;
+  }
+}
+
+inline int blocks_for(cp_ctx* ctx, int64_t n, int threads = 256) {
+  int64_t b = (n + threads - 1) / threads;
+  b = std::min<int64_t>(b, 16 * (int64_t)ctx->num_sms);
+  return (int)std::max<int64_t>(b, 1);
+}
+
+cp_status exclusive_scan(cp_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, int64_t* d_total) {
+  const int64_t ntiles = std::max<int64_t>(1, (n + kSortTile - 1) / kSortTile);
+  int64_t* sums = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&sums, sizeof(int64_t) * (size_t)ntiles));
+  tile_sum_kernel<<<(unsigned)ntiles, kSortThreads, 0, ctx->stream>>>(in, n, sums);
+  CP_LAUNCH_CHECK();
+  single_block_scan_kernel<<<1, 1024, 0, ctx->stream>>>(sums, ntiles, d_total);
+  CP_LAUNCH_CHECK();
+  tile_scan_kernel<<<(unsigned)ntiles, kSortThreads, 0, ctx->stream>>>(in, n, sums, out);
+  CP_LAUNCH_CHECK();
+  ws_free(ctx, sums);
+  return CP_OK;
+}
+
+int bits_for(int64_t dim) {
+  int b = 0;
+  while (b < 63 && (((int64_t)1 << b) < dim)) ++b;
+  return b;
+}
+
+// Stable sort of perm (identity on entry) by the cyclic key starting at mode n.
+cp_status sort_mode(cp_ctx* ctx, const cp_tensor* t, const int64_t* coords, int n, int64_t* perm,
+                    int64_t* tmp) {
+  const int64_t nnz = t->nnz;
+  const int64_t ntiles = (nnz + kSortTile - 1) / kSortTile;
+  int64_t* hist = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&hist, sizeof(int64_t) * (size_t)kBins * ntiles));
+  iota_kernel<<<blocks_for(ctx, nnz), 256, 0, ctx->stream>>>(perm, nnz);
+  CP_LAUNCH_CHECK();
+  int64_t* a = perm;
+  int64_t* b = tmp;
+  for (int k = t->N - 1; k >= 0; --k) {
+    const int c = (n + k) % t->N;
+    const int bits = bits_for(t->dims[c]);
+    for (int shift = 0; shift < bits; shift += 4) {
+      radix_hist_kernel<<<(unsigned)ntiles, kSortThreads, 0, ctx->stream>>>(a, coords, t->N, c, shift, nnz,
+                                                                            hist, ntiles);
+      CP_LAUNCH_CHECK();
+      CP_TRY(exclusive_scan(ctx, hist, hist, (int64_t)kBins * ntiles, nullptr));
+      radix_scatter_kernel<<<(unsigned)ntiles, kSortThreads, 0, ctx->stream>>>(a, coords, t->N, c, shift, nnz,
+                                                                               hist, ntiles, b);
+      CP_LAUNCH_CHECK();
+      std::swap(a, b);
+    }
+  }
+  if (a != perm)
+    CP_CUDA(cudaMemcpyAsync(perm, a, sizeof(int64_t) * nnz, cudaMemcpyDeviceToDevice, ctx->stream));
+  ws_free(ctx, hist);
+  return CP_OK;
+}
+
+}  // namespace
+
+cp_status coo_build(cp_ctx* ctx, cp_tensor* t, const int64_t* coords, const float* vals) {
+  const int64_t nnz = t->nnz;
+  const int N = t->N;
+  // ||T||^2 over the nonzeros
+  {
+    double* d = nullptr;
+    CP_TRY(ws_alloc(ctx, (void**)&d, sizeof(double)));
+    if (nnz > 0) {
+      CP_TRY(sumsq(ctx, vals, CP_DTYPE_F32, nnz, d));
+      CP_CUDA(cudaMemcpyAsync(ctx->h_pinned, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      CP_CUDA(cudaStreamSynchronize(ctx->stream));
+      t->norm2 = ctx->h_pinned[0];
+    } else {
+      t->norm2 = 0.0;
+    }
+    ws_free(ctx, d);
+  }
+  int64_t* d_dims = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&d_dims, sizeof(int64_t) * CP_MAX_N));
+  for (int n = 0; n < N; ++n) ((int64_t*)ctx->h_pinned)[n] = t->dims[n];
+  CP_CUDA(cudaMemcpyAsync(d_dims, ctx->h_pinned, sizeof(int64_t) * N, cudaMemcpyHostToDevice, ctx->stream));
+  if (nnz > 0) {
+    range_check_kernel<<<blocks_for(ctx, nnz * N), 256, 0, ctx->stream>>>(coords, nnz, N, d_dims, ctx->d_status);
+    CP_LAUNCH_CHECK();
+    CP_TRY(read_status(ctx));
+  }
+  int64_t* tmp = nullptr;
+  int64_t* flag = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&tmp, sizeof(int64_t) * (size_t)(nnz + 1)));
+  CP_TRY(ws_alloc(ctx, (void**)&flag, sizeof(int64_t) * (size_t)(2 * nnz + 2)));
+  int64_t* segidx = flag + nnz + 1;
+  for (int n = 0; n < N; ++n) {
+    CooMode& md = t->modes[n];
+    CP_CUDA(cudaMalloc(&md.perm, sizeof(int64_t) * (size_t)std::max<int64_t>(nnz, 1)));
+    CP_CUDA(cudaMalloc(&md.vals, sizeof(float) * (size_t)std::max<int64_t>(nnz, 1)));
+    CP_CUDA(cudaMalloc(&md.other, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz * (N - 1), 1)));
+    if (nnz == 0) {
+      md.nseg = 0;
+      md.nunits = 0;
+      CP_CUDA(cudaMalloc(&md.seg_ptr, sizeof(int64_t)));
+      CP_CUDA(cudaMemsetAsync(md.seg_ptr, 0, sizeof(int64_t), ctx->stream));
+      CP_CUDA(cudaMalloc(&md.seg_row, sizeof(int32_t)));
+      CP_CUDA(cudaMalloc(&md.seg_unit, sizeof(int64_t)));
+      CP_CUDA(cudaMemsetAsync(md.seg_unit, 0, sizeof(int64_t), ctx->stream));
+      CP_CUDA(cudaMalloc(&md.unit_start, sizeof(int64_t)));
+      CP_CUDA(cudaMemsetAsync(md.unit_start, 0, sizeof(int64_t), ctx->stream));
+      continue;
+    }
+    CP_TRY(sort_mode(ctx, t, coords, n, md.perm, tmp));
+    if (n == 0) {
+      dup_check_kernel<<<blocks_for(ctx, nnz), 256, 0, ctx->stream>>>(md.perm, coords, N, nnz, ctx->d_status);
+      CP_LAUNCH_CHECK();
+      CP_TRY(read_status(ctx));
+    }
+    head_flags_kernel<<<blocks_for(ctx, nnz), 256, 0, ctx->stream>>>(md.perm, coords, N, n, nnz, flag);
+    CP_LAUNCH_CHECK();
+    int64_t* d_total = tmp + nnz;
+    CP_TRY(exclusive_scan(ctx, flag, segidx, nnz, d_total));
+    CP_CUDA(cudaMemcpyAsync(ctx->h_pinned, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CP_CUDA(cudaStreamSynchronize(ctx->stream));
+    md.nseg = ((int64_t*)ctx->h_pinned)[0];
+    CP_CUDA(cudaMalloc(&md.seg_ptr, sizeof(int64_t) * (size_t)(md.nseg + 1)));
+    CP_CUDA(cudaMalloc(&md.seg_row, sizeof(int32_t) * (size_t)md.nseg));
+    segments_kernel<<<blocks_for(ctx, nnz), 256, 0, ctx->stream>>>(md.perm, coords, N, n, nnz, flag, segidx,
+                                                                   md.seg_ptr, md.seg_row);
+    CP_LAUNCH_CHECK();
+    ((int64_t*)ctx->h_pinned)[0] = nnz;
+    CP_CUDA(cudaMemcpyAsync(md.seg_ptr + md.nseg, ctx->h_pinned, sizeof(int64_t), cudaMemcpyHostToDevice,
+                            ctx->stream));
+    // work units
+    CP_CUDA(cudaMalloc(&md.seg_unit, sizeof(int64_t) * (size_t)(md.nseg + 1)));
+    units_count_kernel<<<blocks_for(ctx, md.nseg), 256, 0, ctx->stream>>>(md.seg_ptr, md.nseg, flag);
+    CP_LAUNCH_CHECK();
+    CP_TRY(exclusive_scan(ctx, flag, md.seg_unit, md.nseg, md.seg_unit + md.nseg));
+    CP_CUDA(cudaMemcpyAsync(ctx->h_pinned, md.seg_unit + md.nseg, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    CP_CUDA(cudaStreamSynchronize(ctx->stream));
+    md.nunits = ((int64_t*)ctx->h_pinned)[0];
+    CP_CUDA(cudaMalloc(&md.unit_start, sizeof(int64_t) * (size_t)(md.nunits + 1)));
+    units_fill_kernel<<<blocks_for(ctx, md.nseg), 256, 0, ctx->stream>>>(md.seg_ptr, md.nseg, md.seg_unit,
+                                                                         md.unit_start, md.nunits, nnz);
+    CP_LAUNCH_CHECK();
+    gather_sorted_kernel<<<blocks_for(ctx, nnz), 256, 0, ctx->stream>>>(md.perm, coords, vals, N, n, nnz,
+                                                                        md.other, md.vals);
+    CP_LAUNCH_CHECK();
+  }
+  CP_CUDA(cudaStreamSynchronize(ctx->stream));
+  ws_free(ctx, flag);
+  ws_free(ctx, tmp);
+  ws_free(ctx, d_dims);
+  return read_status(ctx);
+}
+
+void tensor_free_coo(cp_tensor* t) {
+  for (int n = 0; n < CP_MAX_N; ++n) {
+    CooMode& md = t->modes[n];
+    cudaFree(md.perm);
+    cudaFree(md.seg_ptr);
+    cudaFree(md.seg_row);
+    cudaFree(md.other);
+    cudaFree(md.vals);
+    cudaFree(md.seg_unit);
+    cudaFree(md.unit_start);
+    md = CooMode();
+  }
+}
+
+template <typename TT, int RB>
+static cp_status launch_coo(cp_ctx* ctx, const cp_tensor* t, const CooMode& md, const Tables& tab, int R,
+                            int RP, double* partial) {
+  const int64_t threads = 256;
+  const int64_t blocks = (md.nunits * 32 + threads - 1) / threads;
+  if (blocks == 0) return CP_OK;
+  mttkrp_coo_kernel<TT, RB><<<(unsigned)blocks, (unsigned)threads, 0, ctx->stream>>>(
+      md.other, md.vals, t->nnz, t->N - 1, md.unit_start, md.nunits, tab, R, RP, partial);
+  CP_LAUNCH_CHECK();
+  return CP_OK;
+}
+
+template <typename TT>
+static cp_status dispatch_coo(cp_ctx* ctx, const cp_tensor* t, const CooMode& md, const Tables& tab, int R,
+                              int RP, double* partial) {
+  if (RP <= 4) return launch_coo<TT, 4>(ctx, t, md, tab, R, RP, partial);
+  if (RP <= 8) return launch_coo<TT, 8>(ctx, t, md, tab, R, RP, partial);
+  if (RP <= 16) return launch_coo<TT, 16>(ctx, t, md, tab, R, RP, partial);
+  if (RP <= 32) return launch_coo<TT, 32>(ctx, t, md, tab, R, RP, partial);
+  return launch_coo<TT, 64>(ctx, t, md, tab, R, RP, partial);
+}
+
+cp_status mttkrp_sparse(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, int mode,
+                        double* out, cp_precision prec) {
+  const int R = L.R;
+  const int N = t->N;
+  const CooMode& md = t->modes[mode];
+  CP_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)t->dims[mode] * R, ctx->stream));
+  if (t->nnz == 0) return CP_OK;
+  const bool f32 = prec != CP_FP64;
+  const size_t esz = f32 ? sizeof(float) : sizeof(double);
+  const int RP = R;   // tables keep the rank as row stride
+  size_t tab_elems = 0;
+  for (int j = 0; j < N - 1; ++j) tab_elems += (size_t)t->dims[(mode + 1 + j) % N] * RP;
+  char* tabmem = nullptr;
+  double* partial = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&tabmem, esz * tab_elems + 256));
+  CP_TRY(ws_alloc(ctx, (void**)&partial, sizeof(double) * (size_t)md.nunits * R + 16));
+  Tables tab;
+  size_t off = 0;
+  for (int j = 0; j < N - 1; ++j) {
+    const int m = (mode + 1 + j) % N;
+    void* dst = tabmem + off * esz;
+    const int64_t I = t->dims[m];
+    if (f32)
+      table_kernel<float><<<blocks_for(ctx, I * RP), 256, 0, ctx->stream>>>(u + L.off[m], I, R, RP, (float*)dst);
+    else
+      table_kernel<double><<<blocks_for(ctx, I * RP), 256, 0, ctx->stream>>>(u + L.off[m], I, R, RP, (double*)dst);
+    CP_LAUNCH_CHECK();
+    tab.A[j] = dst;
+    off += (size_t)I * RP;
+  }
+  if (f32)
+    CP_TRY(dispatch_coo<float>(ctx, t, md, tab, R, RP, partial));
+  else
+    CP_TRY(dispatch_coo<double>(ctx, t, md, tab, R, RP, partial));
+  coo_finalize_kernel<<<blocks_for(ctx, md.nseg * R), 256, 0, ctx->stream>>>(md.seg_unit, md.nseg, md.seg_row,
+                                                                             partial, R, out);
+  CP_LAUNCH_CHECK();
+  ws_free(ctx, partial);
+  ws_free(ctx, tabmem);
+  return CP_OK;
+}
+
+}  // namespace cpg
