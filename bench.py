@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark: CP solves per second to ||grad f|| / #params < 1e-7 on the dense
+256 x 256 x 256 FP32 tensor (planted rank 16, collinearity 0.9, 10 %
+homoscedastic + 10 % heteroscedastic noise), solved at R = 16 by N-GMRES
+(w = 20) accelerated ALS with the More-Thuente line search.
+
+One step = one complete solve from the same seeded N(0,1) initial guess with
+the tensor already resident in HBM; L2 is flushed (512 MiB write) before
+every timed step, outside the timed interval.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+
+With more than one process (torchrun), every rank solves its own replica
+(no collective on the data path); value = all ranks' solves / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CP solves/s & p99 latency to rel-grad 1e-7; MTTKRP %roofline, mixed vs FP64"
+UNIT = "solves/s"
+WORKLOAD = ("dense 256x256x256 fp32, planted R=16, collinearity 0.9, 10% homoscedastic + "
+            "10% heteroscedastic noise; N-GMRES w=20 + More-Thuente, R=16, stop ||g||/P < 1e-7")
+DIMS = (256, 256, 256)
+R = 16
+TOL = 1e-7
+# FP64 FMA issue rate of the part: 2 FP64 FMA per clock per SM (152 SMs at
+# 2070 MHz max) -> 2 * 2 * 152 * 2.07e9 flop/s.  cuBLAS DGEMM measured 1.10.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--cpu-iters", type=int, default=1, help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_iters(name="dense_256"):
+    path = os.path.join(ROOT, "oracle", "workload_iters.json")
+    try:
+        return json.load(open(path))[name]["iters"]
+    except Exception:
+        return None
+
+
+def cpu_sample(n_iters: int) -> dict:
+    """Time the oracle on the workload: the start-up (normalise + f/g) and
+    n_iters N-GMRES iterations; a full solve is start-up + iters x per-iteration."""
+    import numpy as np  # noqa: F401
+    import synth
+    from oracle import cp_oracle as O
+    prob, u0 = synth.workload_dense_256()
+    X = O.DenseTensor(prob.T)
+    t0 = time.perf_counter()
+    O.cp_solve(X, u0, O.SolveOpts(R=R, tol=TOL), max_iters=0)
+    t_init = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, _, rep = O.cp_solve(X, u0, O.SolveOpts(R=R, tol=TOL), max_iters=n_iters)
+    t_run = time.perf_counter() - t0
+    per_iter = max(t_run - t_init, 1e-9) / max(rep.iters, 1)
+    full = oracle_iters()
+    est = t_init + (full if full else float("nan")) * per_iter
+    return dict(t_init_s=t_init, per_iter_s=per_iter, iters_sampled=rep.iters, oracle_iters=full,
+                est_solve_s=est)
+
+
+def run_cpu_baseline_subprocess(n_iters: int) -> dict | None:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample",
+                              "--cpu-iters", str(n_iters)], capture_output=True, text=True, env=env,
+                             timeout=900)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # noqa: BLE001
+        return {"error": str(exc)[:200]}
+
+
+def cpu_baseline_obj(s: dict) -> dict:
+    val = 1.0 / s["est_solve_s"] if s.get("est_solve_s") and s["est_solve_s"] == s["est_solve_s"] else None
+    return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle start-up + {s.get('iters_sampled')} N-GMRES iteration(s) of this workload "
+                       f"timed ({s.get('t_init_s', 0):.2f} s + {s.get('per_iter_s', 0):.2f} s/iter, numpy "
+                       f"single thread), extrapolated to the oracle's own {s.get('oracle_iters')} "
+                       f"iterations to tolerance (oracle/workload_iters.json)")}
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[4:8]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1105_5331_gb300 as cp
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline_subprocess(args.cpu_iters)   # before any GPU work
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(dev)
+    prob, u0 = synth.workload_dense_256()
+    T_host = torch.from_numpy(prob.T).pin_memory()
+    u0_host = torch.from_numpy(u0).pin_memory()
+    P = u0.size
+    ctx = cp.cp_ctx_create(local_rank, stream)
+    prec = cp.CP_MIXED_BF16X3 if args.prec == "mixed" else cp.CP_FP64
+    with torch.cuda.stream(stream):
+        T_dev = T_host.to(dev, non_blocking=True)
+        u0_dev = u0_host.to(dev, non_blocking=True)
+        u = torch.empty_like(u0_dev)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream.synchronize()
+    t = cp.cp_tensor_dense(ctx, T_dev)
+
+    def opts_for(p):
+        o = cp.cp_solve_opts_default(R)
+        o.tol = TOL
+        o.prec = p
+        return o
+
+    def timed_solves(p, n_warm, n_timed):
+        o = opts_for(p)
+        times, reps = [], []
+        for k in range(n_warm + n_timed):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                u.copy_(u0_dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rep = cp.cp_solve(ctx, t, o, u)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= n_warm:
+                times.append(e0.elapsed_time(e1) / 1e3)
+                reps.append(rep)
+        return times, reps
+
+    # headline precision
+    launches0 = cp.cp_kernel_launches()
+    barrier(world)
+    with ClockSampler(local_rank) as clk:
+        times, reps = timed_solves(prec, args.warmup, args.steps)
+    launches = cp.cp_kernel_launches() - launches0
+    total = sum(times)
+    total_max = allreduce_max(total, world)
+    value = world * args.steps / total_max
+    # the other precision at the same tolerance, for the mixed-vs-FP64 figure
+    other = cp.CP_FP64 if prec != cp.CP_FP64 else None
+    other_obj = None
+    if other is not None:
+        ot, orp = timed_solves(other, 1, 1)
+        other_obj = {"precision": "fp64", "solves_per_s": 1.0 / ot[0], "ms_per_solve": ot[0] * 1e3,
+                     "iters": orp[0]["iters"], "gnorm_over_P": orp[0]["gnorm_over_P"], "f": orp[0]["f"]}
+
+    # roofline of the dominant kernel (the MTTKRP), timed live on the ctx stream
+    roof = mttkrp_roofline(cp, ctx, t, u0_dev, stream, flush, prec)
+
+    # end to end through the public API with host buffers
+    e2e = e2e_run(cp, ctx, prob, u0, prec, min(args.steps, 3), T_host)
+
+    clocks = clk.summary()
+    lat = sorted(times)
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3(fp32 acc)+f64" if prec != cp.CP_FP64 else "f64",
+        "data": "synthetic (seeded generator; no dataset)",
+        "config": {"workload": WORKLOAD, "dims": list(DIMS), "R": R, "tol": TOL, "w": 20,
+                   "precision": args.prec, "l2": "flushed by a 512 MiB write before every timed step",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "solve": {"iters": reps[-1]["iters"], "fg_evals": reps[-1]["fg_evals"],
+                  "restarts": reps[-1]["restarts"], "ls_failures": reps[-1]["ls_failures"],
+                  "mixed_iters": reps[-1]["mixed_iters"], "fp64_iters": reps[-1]["fp64_iters"],
+                  "gnorm_over_P": reps[-1]["gnorm_over_P"], "f": reps[-1]["f"]},
+        "vs_fp64_path": other_obj,
+        "roofline": roof,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    if cpu is not None:
+        if "error" in cpu:
+            res["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu["error"]}
+        else:
+            res["cpu_baseline"] = cpu_baseline_obj(cpu)
+    t.close()
+    ctx.close()
+    return res
+
+
+def mttkrp_roofline(cp, ctx, t, u, stream, flush, prec):
+    import torch
+    out = torch.empty(DIMS[0] * R, dtype=torch.float64, device=u.device)
+    K = DIMS[0] * DIMS[1] * DIMS[2]
+    durs = []
+    for n in range(3):
+        for k in range(7):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cp.cp_mttkrp(ctx, t, R, u, n, out, prec)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 2:
+                durs.append(e0.elapsed_time(e1) / 1e3)
+    d = sum(durs) / len(durs)
+    peaks = measured_peaks()
+    if prec == cp.CP_FP64:
+        flops = 2.0 * K * R
+        ach = flops / d / 1e12
+        return {"kernel": "mttkrp_f64_kernel (+ partial-sum reduction)", "bound": "alu",
+                "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": None, "per_launch": {"flops": flops, "avg_ms": d * 1e3},
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
+    # mixed: HBM-bound stream of the bf16 hi/lo planes of T_(n) (4 B per element)
+    bytes_ = 4.0 * K + 8.0 * DIMS[0] * R + 4.0 * 2 * DIMS[1] * R
+    ach = bytes_ / d / 1e9
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    return {"kernel": "mttkrp_tc_kernel (tcgen05 bf16x3, + partial-sum reduction)", "bound": "hbm",
+            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+            "per_launch": {"bytes": bytes_, "avg_ms": d * 1e3},
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+
+
+def e2e_run(cp, ctx, prob, u0, prec, n, T_host):
+    """Solves through the public C-ABI with HOST buffers: tensor upload,
+    solve with a host iterate (uploaded and read back inside the call)."""
+    import numpy as np
+    o = cp.cp_solve_opts_default(R)
+    o.tol = TOL
+    o.prec = prec
+    times = []
+    for k in range(n + 1):
+        u = np.array(u0, copy=True)
+        t0 = time.perf_counter()
+        tt = cp.cp_tensor_dense(ctx, T_host.numpy())
+        cp.cp_solve(ctx, tt, o, u)
+        tt.close()
+        dt = time.perf_counter() - t0
+        if k > 0:
+            times.append(dt)
+    return {"value": len(times) / sum(times), "unit": UNIT,
+            "h2d_bytes_per_step": int(prob.T.nbytes + u0.nbytes), "d2h_bytes_per_step": int(u0.nbytes),
+            "note": "host-clock wall time per solve incl. tensor upload, per-mode copies and iterate H2D/D2H"}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    times = []
+    last = None
+    for k in range(args.warmup + args.steps):
+        s = cpu_sample(args.cpu_iters)
+        if k >= args.warmup:
+            times.append(s["est_solve_s"])
+            last = s
+    mean = sum(times) / len(times)
+    value = 1.0 / mean if mean == mean else None
+    cb = cpu_baseline_obj(last)
+    cb["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * mean,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator; no dataset)",
+            "config": {"workload": WORKLOAD, "dims": list(DIMS), "R": R, "tol": TOL, "w": 20,
+                       "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# -------------------------------------------------------------- distributed
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    v = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v.item())
+
+
+def main():
+    args = parse()
+    if args.cpu_sample:
+        print(json.dumps(cpu_sample(args.cpu_iters)))
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -81,6 +81,9 @@ const char* cp_last_error(void);
 cp_status cp_ctx_sync(cp_ctx* ctx);
 /* The context's cudaStream_t. */
 void* cp_ctx_stream(cp_ctx* ctx);
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all contexts; for accounting in benchmarks). */
+unsigned long long cp_kernel_launches(void);
 
 /* ---------------------------------------------------------------- tensors */
 

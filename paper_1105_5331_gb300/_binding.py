@@ -29,6 +29,7 @@ STATUS_NAMES = {
 # Every symbol include/cp.h declares (checked by the tests).
 EXPORTED = [
     "cp_ctx_create", "cp_ctx_destroy", "cp_last_error", "cp_ctx_sync", "cp_ctx_stream",
+    "cp_kernel_launches",
     "cp_tensor_dense", "cp_tensor_coo", "cp_tensor_info", "cp_tensor_sorted_mode",
     "cp_tensor_destroy", "cp_mttkrp", "cp_fg", "cp_als_sweep", "cp_normalize", "ngmres_step",
     "cp_ls_opts_default", "linesearch", "cp_solve_opts_default", "cp_solve",
@@ -77,6 +78,7 @@ def _load():
         "cp_last_error": (C.c_char_p, []),
         "cp_ctx_sync": (I, [VP]),
         "cp_ctx_stream": (VP, [VP]),
+        "cp_kernel_launches": (C.c_ulonglong, []),
         "cp_tensor_dense": (I, [VP, I, P, I, VP, C.POINTER(VP)]),
         "cp_tensor_coo": (I, [VP, I, P, I64, VP, VP, C.POINTER(VP)]),
         "cp_tensor_info": (I, [VP, C.POINTER(I), P, C.POINTER(D)]),
@@ -207,6 +209,10 @@ def cp_ctx_sync(ctx):
 
 def cp_ctx_stream(ctx) -> int:
     return _lib.cp_ctx_stream(_h(ctx))
+
+
+def cp_kernel_launches() -> int:
+    return int(_lib.cp_kernel_launches())
 
 
 def cp_tensor_dense(ctx, data, dims=None, dtype=None) -> Tensor:

@@ -11,6 +11,7 @@
 namespace cpg {
 
 static thread_local char g_err[1024] = "";
+std::atomic<unsigned long long> g_launches{0};
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -98,6 +99,8 @@ using namespace cpg;
 extern "C" {
 
 const char* cp_last_error(void) { return cpg::g_err; }
+
+unsigned long long cp_kernel_launches(void) { return cpg::g_launches.load(); }
 
 cp_status cp_ctx_create(int device, void* cuda_stream, cp_ctx** out) {
   CP_NULLCHECK(out);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <vector>
@@ -27,8 +28,11 @@ cp_status cuda_fail(cudaError_t e, const char* what, const char* file, int line)
     if (e__ != cudaSuccess) return cpg::cuda_fail(e__, #expr, __FILE__, __LINE__); \
   } while (0)
 
+extern std::atomic<unsigned long long> g_launches;
+
 #define CP_LAUNCH_CHECK()                                                     \
   do {                                                                        \
+    cpg::g_launches.fetch_add(1, std::memory_order_relaxed);                  \
     cudaError_t e__ = cudaGetLastError();                                     \
     if (e__ != cudaSuccess) return cpg::cuda_fail(e__, "kernel launch", __FILE__, __LINE__); \
   } while (0)
@@ -122,6 +126,7 @@ struct cp_tensor {
   __nv_bfloat16* Thi[CP_MAX_N] = {nullptr};
   __nv_bfloat16* Tlo[CP_MAX_N] = {nullptr};
   int64_t pitch[CP_MAX_N] = {0};
+  void* tc_state = nullptr;      // tensor maps of the planes (dense_tc.cu)
   // coo
   int64_t nnz = 0;
   CooMode modes[CP_MAX_N];

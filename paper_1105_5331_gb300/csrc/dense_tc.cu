@@ -1,13 +1,528 @@
-// Dense MTTKRP on tcgen05 tensor cores (bf16x3 split products).
+// Dense MTTKRP on the sm_103a tensor cores (tcgen05), bf16x3 split products
+// with FP32 accumulation in tensor memory.
+//
+// M^(n) = T_(n) Phibar^(n) (Section 2.3, Eq. Gn) is a GEMM with rows i of
+// T_(n) (I_n of them), contraction over kbar (prod of the other dims) and R
+// columns.  T_(n) is kept as two bf16 planes, hi = bf16(T) and
+// lo = bf16(T - hi), so that T ~= hi + lo to about 2^-17 relative.  The
+// Khatri-Rao tile KR[kbar, r] = prod_{m != n} A_m[i_m, r] is formed on the fly
+// in shared memory from FP32 copies of the factors and split the same way.
+// Each 16-deep step issues three MMAs, hi*hi + hi*lo + lo*hi, into one FP32
+// accumulator (the lo*lo term, ~2^-18 relative, is dropped).
+//
+// CTA layout (192 threads, one CTA per SM):
+//   warp 0     TMA producer: 128 x 64 bf16 tiles of both planes, 128-byte
+//              swizzle, into a ring of `stages` shared-memory stages.
+//   warp 1     TMEM allocation and the MMA issuer (one thread).
+//   warps 2-5  build the Khatri-Rao hi/lo tiles of each stage (SW128,
+//              K-major), then drain the accumulators (tcgen05.ld) and write
+//              the CTA's partial I x R sums.
+// The grid splits the contraction range (split-K) and, for I_n > 256, the row
+// tiles.  A second kernel adds the per-CTA partials in a fixed order in FP64.
+// Every mbarrier wait is bounded; on a timeout the CTA records
+// CP_ERR_TIMEOUT in the device status word and winds down.
+#include <cuda.h>
+
+#include <algorithm>
+
 #include "cp_internal.cuh"
 
 namespace cpg {
 
-cp_status mttkrp_dense_mixed(cp_ctx*, cp_tensor*, const Layout&, const double*, int, double*) {
-  set_error("mixed precision MTTKRP: not built yet");
-  return CP_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int kBM = 128;                 // rows per M tile = TMEM lanes
+constexpr int kBK = 64;                  // contraction elements per tile (128 bytes of bf16)
+constexpr int kThreads = 192;
+constexpr uint32_t kTileBytes = kBM * kBK * 2;   // one plane, one M tile: 16 KB
+constexpr int kMaxTilesPerCta = 2;       // M tiles handled by one CTA
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
+
+struct TcParams {
+  int64_t I;
+  int64_t Kbar;
+  int R, RP;
+  int ntm;                    // M tiles per CTA (1 or 2)
+  int stages;
+  int64_t ktiles;             // total contraction tiles
+  int64_t ktiles_per_cta;
+  int nother;
+  const float* tab[CP_MAX_N - 1];    // FP32 factors of the other modes, row stride R
+  int64_t dimo[CP_MAX_N - 1];
+  float* partial;             // [gridDim.x][I][R]
+  int* status;
+  uint32_t ncols;             // TMEM columns allocated
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-void tensor_free_mixed(cp_tensor* t) { (void)t; }
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* status) {
+  if (mbar_try(a, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(a, parity)) {
+    if (gtimer() - t0 > kWaitNs) {
+      record_status(status, CP_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // version
+  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    mttkrp_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+                     const TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const int S = p.stages;
+  const uint32_t b_bytes = (uint32_t)p.RP * 128u;
+  const uint32_t stage_bytes = (uint32_t)p.ntm * 2u * kTileBytes + 2u * b_bytes;
+  const uint32_t bars = base + (uint32_t)S * stage_bytes;
+  auto full_bar = [&](int s) { return bars + 8u * (uint32_t)s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (uint32_t)(S + s); };
+  const uint32_t done_bar = bars + 16u * (uint32_t)S;
+  const uint32_t tmem_slot = done_bar + 8u;
+  volatile uint32_t* tmem_slot_ptr = (volatile uint32_t*)(gbase + (tmem_slot - base));
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t kt0 = (int64_t)blockIdx.x * p.ktiles_per_cta;
+  const int64_t kt1 = min(p.ktiles, kt0 + p.ktiles_per_cta);
+  const int nk = (int)max((int64_t)0, kt1 - kt0);
+  const int64_t row0 = (int64_t)blockIdx.y * (kBM * kMaxTilesPerCta);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full_bar(s), 2);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_proxy_async();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tmem_slot),
+                 "r"(p.ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot_ptr;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % S;
+        const uint32_t ph = (uint32_t)((i / S) & 1);
+        if (!mbar_wait(empty_bar(s), ph ^ 1u, p.status)) break;
+        mbar_arrive_tx(full_bar(s), (uint32_t)p.ntm * 2u * kTileBytes);
+        const int x = (int)((kt0 + i) * kBK);
+        const uint32_t st = base + (uint32_t)s * stage_bytes;
+        for (int mt = 0; mt < p.ntm; ++mt) {
+          const int y = (int)(row0 + mt * kBM);
+          tma_load_2d(st + (uint32_t)mt * kTileBytes, &tm_hi, x, y, full_bar(s));
+          tma_load_2d(st + (uint32_t)(p.ntm + mt) * kTileBytes, &tm_lo, x, y, full_bar(s));
+        }
+        ++issued;
+      }
+      // let copies still in flight land before the CTA can exit
+      for (int i = max(0, issued - S); i < issued; ++i)
+        mbar_wait(full_bar(i % S), (uint32_t)((i / S) & 1), p.status);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kBM, p.RP);
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % S;
+        const uint32_t ph = (uint32_t)((i / S) & 1);
+        if (!mbar_wait(full_bar(s), ph, p.status)) break;
+        tc_fence_after();
+        const uint32_t st = base + (uint32_t)s * stage_bytes;
+        const uint32_t bhi = st + 2u * (uint32_t)p.ntm * kTileBytes;
+        const uint32_t blo = bhi + b_bytes;
+        for (int mt = 0; mt < p.ntm; ++mt) {
+          const uint32_t d = tmem + (uint32_t)(mt * p.RP);
+          const uint32_t ahi = st + (uint32_t)mt * kTileBytes;
+          const uint32_t alo = st + (uint32_t)(p.ntm + mt) * kTileBytes;
+#pragma unroll
+          for (int j = 0; j < kBK / 16; ++j) {
+            const uint32_t off = (uint32_t)j * 32u;
+            mma_bf16(d, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, (i > 0 || j > 0) ? 1u : 0u);
+            mma_bf16(d, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
+            mma_bf16(d, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, 1u);
+          }
+        }
+        mma_commit(empty_bar(s));
+      }
+      mma_commit(done_bar);
+    }
+  } else {
+    // ------------------------------------------------- Khatri-Rao tile builders
+    const int t = threadIdx.x - 64;            // 0..127
+    const int kk = t & (kBK - 1);              // contraction element within the tile
+    const int half = t >> 6;                   // which half of the padded ranks
+    const int rh = p.RP >> 1;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % S;
+      const uint32_t ph = (uint32_t)((i / S) & 1);
+      const bool ok = mbar_wait(empty_bar(s), ph ^ 1u, p.status);
+      if (ok) {
+        uint8_t* st = gbase + (size_t)s * stage_bytes;
+        uint8_t* bhi = st + 2u * (uint32_t)p.ntm * kTileBytes;
+        uint8_t* blo = bhi + b_bytes;
+        const int64_t kb = (kt0 + i) * kBK + kk;
+        int64_t idx[CP_MAX_N - 1];
+        const bool in = kb < p.Kbar;
+        if (in) {
+          int64_t rem = kb;
+          for (int j = p.nother - 1; j >= 0; --j) {
+            const int64_t q = rem / p.dimo[j];
+            idx[j] = rem - q * p.dimo[j];
+            rem = q;
+          }
+        }
+        for (int r = half * rh; r < (half + 1) * rh; ++r) {
+          float v = 0.f;
+          if (in && r < p.R) {
+            v = 1.f;
+            for (int j = 0; j < p.nother; ++j) v *= p.tab[j][idx[j] * p.R + r];
+          }
+          const __nv_bfloat16 h = __float2bfloat16_rn(v);
+          const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+          const uint32_t off = (uint32_t)r * 128u + ((((uint32_t)kk >> 3) ^ ((uint32_t)r & 7u)) << 4) +
+                               ((uint32_t)kk & 7u) * 2u;
+          *(__nv_bfloat16*)(bhi + off) = h;
+          *(__nv_bfloat16*)(blo + off) = l;
+        }
+      }
+      fence_proxy_async();
+      // all 128 builders agree on success before the stage is published, so
+      // a timeout in one thread stops every builder at the same tile
+      uint32_t all_ok;
+      asm volatile(
+          "{\n\t.reg .pred pin, pout;\n\t"
+          "setp.ne.u32 pin, %1, 0;\n\t"
+          "bar.red.and.pred pout, 1, 128, pin;\n\t"
+          "selp.u32 %0, 1, 0, pout;\n\t}"
+          : "=r"(all_ok)
+          : "r"((uint32_t)ok)
+          : "memory");
+      if (!all_ok) break;
+      if (t == 0) mbar_arrive(full_bar(s));
+    }
+    // ------------------------------------------------------------ epilogue
+    const bool done = mbar_wait(done_bar, 0u, p.status);
+    tc_fence_after();
+    const int q = warp & 3;                    // TMEM lane quarter of this warp
+    const int64_t rin = q * 32 + lane;
+    for (int mt = 0; mt < p.ntm; ++mt) {
+      const int64_t row = row0 + mt * kBM + rin;
+      for (int c = 0; c < p.RP; c += 16) {
+        uint32_t v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * p.RP + c), v);
+        if (done && row < p.I) {
+          float* out = p.partial + ((int64_t)blockIdx.x * p.I + row) * p.R;
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (c + e < p.R) out[c + e] = __uint_as_float(v[e]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.ncols) : "memory");
+  }
+}
+
+// hi = bf16(x), lo = bf16(x - hi); row pitch `pitch` (zero padding).
+template <typename TT>
+__global__ void split_planes_kernel(const TT* __restrict__ src, int64_t I, int64_t Kbar, int64_t pitch,
+                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int64_t total = I * pitch;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = o / pitch;
+    const int64_t k = o - i * pitch;
+    double x = k < Kbar ? (double)src[i * Kbar + k] : 0.0;
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    const __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
+    hi[o] = h;
+    lo[o] = l;
+  }
+}
+
+__global__ void f32_table_kernel(const double* __restrict__ A, int64_t n, float* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = (float)A[k];
+}
+
+// M[e] = sum_c partial[c][e] in FP64, c increasing.
+__global__ void reduce_f32_partials_kernel(const float* __restrict__ partial, int nparts, int64_t n,
+                                           double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nparts; ++c) s += (double)partial[(int64_t)c * n + e];
+    out[e] = s;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+struct MixedMode {
+  CUtensorMap hi, lo;
+  bool ready = false;
+};
+
+}  // namespace
+
+// Per-tensor mixed-precision state lives beside the handle (indexed by mode).
+struct TcState {
+  MixedMode mode[CP_MAX_N];
+};
+
+static TcState* tc_state(cp_tensor* t) {
+  return reinterpret_cast<TcState*>(t->tc_state);
+}
+
+void tensor_free_mixed(cp_tensor* t) {
+  for (int n = 0; n < CP_MAX_N; ++n) {
+    if (t->Thi[n]) cudaFree(t->Thi[n]);
+    if (t->Tlo[n]) cudaFree(t->Tlo[n]);
+    t->Thi[n] = t->Tlo[n] = nullptr;
+  }
+  delete tc_state(t);
+  t->tc_state = nullptr;
+}
+
+static cp_status ensure_planes(cp_ctx* ctx, cp_tensor* t, int n) {
+  if (!t->tc_state) t->tc_state = new TcState();
+  MixedMode& mm = tc_state(t)->mode[n];
+  if (mm.ready) return CP_OK;
+  const int64_t I = t->dims[n];
+  const int64_t Kb = kbar(t, n);
+  const int64_t pitch = (Kb + 7) / 8 * 8;
+  if (Kb > ((int64_t)1 << 31) - 64 || I > ((int64_t)1 << 31) - 256) {
+    set_error("mixed MTTKRP: matricisation %lld x %lld too large for 32-bit TMA coordinates",
+              (long long)I, (long long)Kb);
+    return CP_ERR_UNSUPPORTED;
+  }
+  CP_CUDA(cudaMalloc(&t->Thi[n], sizeof(__nv_bfloat16) * (size_t)(I * pitch)));
+  CP_CUDA(cudaMalloc(&t->Tlo[n], sizeof(__nv_bfloat16) * (size_t)(I * pitch)));
+  t->pitch[n] = pitch;
+  int64_t blocks = std::min<int64_t>((I * pitch + 255) / 256, 16 * (int64_t)ctx->num_sms);
+  if (t->dtype == CP_DTYPE_F64)
+    split_planes_kernel<double><<<(unsigned)blocks, 256, 0, ctx->stream>>>((const double*)t->Tn[n], I, Kb, pitch,
+                                                                          t->Thi[n], t->Tlo[n]);
+  else
+    split_planes_kernel<float><<<(unsigned)blocks, 256, 0, ctx->stream>>>((const float*)t->Tn[n], I, Kb, pitch,
+                                                                         t->Thi[n], t->Tlo[n]);
+  CP_LAUNCH_CHECK();
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return CP_ERR_CUDA;
+  }
+  cuuint64_t gdim[2] = {(cuuint64_t)Kb, (cuuint64_t)I};
+  cuuint64_t gstride[1] = {(cuuint64_t)(pitch * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  cuuint32_t estr[2] = {1, 1};
+  for (int pl = 0; pl < 2; ++pl) {
+    CUresult r = enc(pl == 0 ? &mm.hi : &mm.lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                     pl == 0 ? (void*)t->Thi[n] : (void*)t->Tlo[n], gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_error("cuTensorMapEncodeTiled failed (%d) for mode %d", (int)r, n);
+      return CP_ERR_CUDA;
+    }
+  }
+  mm.ready = true;
+  return CP_OK;
+}
+
+cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, int mode, double* out) {
+  CP_TRY(ensure_planes(ctx, t, mode));
+  const MixedMode& mm = tc_state(t)->mode[mode];
+  const int R = L.R;
+  const int RP = std::max(16, (R + 15) / 16 * 16);
+  const int64_t I = t->dims[mode];
+  const int64_t Kb = kbar(t, mode);
+  TcParams p{};
+  p.I = I;
+  p.Kbar = Kb;
+  p.R = R;
+  p.RP = RP;
+  const int64_t mtiles = (I + kBM - 1) / kBM;
+  p.ntm = (int)std::min<int64_t>(mtiles, kMaxTilesPerCta);
+  const int mgroups = (int)((mtiles + kMaxTilesPerCta - 1) / kMaxTilesPerCta);
+  const uint32_t stage_bytes = (uint32_t)p.ntm * 2u * kTileBytes + 2u * (uint32_t)RP * 128u;
+  const uint32_t budget = 200u * 1024u;
+  p.stages = (int)std::min<uint32_t>(6u, budget / stage_bytes);
+  if (p.stages < 2) {
+    set_error("mixed MTTKRP: rank %d too large for the shared-memory pipeline", R);
+    return CP_ERR_UNSUPPORTED;
+  }
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(p.ntm * RP)) cols <<= 1;
+  p.ncols = cols;
+  p.ktiles = (Kb + kBK - 1) / kBK;
+  const int64_t target = std::max<int64_t>(1, ctx->num_sms / mgroups);
+  p.ktiles_per_cta = (p.ktiles + target - 1) / target;
+  const int gx = (int)((p.ktiles + p.ktiles_per_cta - 1) / p.ktiles_per_cta);
+  // FP32 tables of the other modes' factors
+  size_t tab_elems = 0;
+  for (int m = 0; m < t->N; ++m)
+    if (m != mode) tab_elems += (size_t)t->dims[m] * R;
+  float* tabs = nullptr;
+  float* partial = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&tabs, sizeof(float) * tab_elems + 64));
+  CP_TRY(ws_alloc(ctx, (void**)&partial, sizeof(float) * (size_t)gx * I * R));
+  size_t off = 0;
+  p.nother = 0;
+  for (int m = 0; m < t->N; ++m) {
+    if (m == mode) continue;
+    const int64_t n_el = t->dims[m] * R;
+    f32_table_kernel<<<(unsigned)std::min<int64_t>((n_el + 255) / 256, 4 * ctx->num_sms), 256, 0, ctx->stream>>>(
+        u + L.off[m], n_el, tabs + off);
+    CP_LAUNCH_CHECK();
+    p.tab[p.nother] = tabs + off;
+    p.dimo[p.nother] = t->dims[m];
+    ++p.nother;
+    off += (size_t)n_el;
+  }
+  p.partial = partial;
+  p.status = ctx->d_status;
+  const size_t smem = (size_t)p.stages * stage_bytes + 1024 + 256;
+  static bool attr_set = false;
+  if (!attr_set) {
+    CP_CUDA(cudaFuncSetAttribute(mttkrp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr_set = true;
+  }
+  mttkrp_tc_kernel<<<dim3(gx, mgroups), kThreads, smem, ctx->stream>>>(mm.hi, mm.lo, p);
+  CP_LAUNCH_CHECK();
+  const int64_t n_out = I * R;
+  reduce_f32_partials_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n_out + 255) / 256, 4 * ctx->num_sms)),
+                               256, 0, ctx->stream>>>(partial, gx, n_out, out);
+  CP_LAUNCH_CHECK();
+  ws_free(ctx, partial);
+  ws_free(ctx, tabs);
+  return CP_OK;
+}
 
 }  // namespace cpg
