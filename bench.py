@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--mttkrp-only", default=None, choices=["dense_256", "dense_4way"],
+                   help="time only cp_mttkrp on that workload (profiling driver)")
+    p.add_argument("--reps", type=int, default=3)
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--cpu-iters", type=int, default=1, help=argparse.SUPPRESS)
     return p.parse_args()
@@ -373,10 +376,54 @@ def allreduce_max(x, world):
     return float(v.item())
 
 
+def run_mttkrp_only(args):
+    """cp_mttkrp on every mode of a workload, `reps` launches per mode with an
+    L2 flush before each; prints per-mode average times (profiling driver)."""
+    import torch
+
+    import synth
+    import paper_1105_5331_gb300 as cp
+    if args.mttkrp_only == "dense_256":
+        prob, u0 = synth.workload_dense_256()
+    else:
+        prob, u0 = synth.workload_dense_4way()
+    Rk = prob.R
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    ctx = cp.cp_ctx_create(0, stream)
+    prec = cp.CP_MIXED_BF16X3 if args.prec == "mixed" else cp.CP_FP64
+    with torch.cuda.stream(stream):
+        T = torch.from_numpy(prob.T).to(dev)
+        u = torch.from_numpy(u0).to(dev)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream.synchronize()
+    t = cp.cp_tensor_dense(ctx, T)
+    res = {}
+    for n in range(len(prob.dims)):
+        out = torch.empty(prob.dims[n] * Rk, dtype=torch.float64, device=dev)
+        ms = []
+        for k in range(args.reps + 1):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cp.cp_mttkrp(ctx, t, Rk, u, n, out, prec)
+            e1.record(stream)
+            e1.synchronize()
+            if k > 0:
+                ms.append(e0.elapsed_time(e1))
+        res[f"mode{n}_ms"] = sum(ms) / len(ms)
+    cp.cp_ctx_sync(ctx)
+    print(json.dumps({"mttkrp_only": args.mttkrp_only, "prec": args.prec, **res}))
+
+
 def main():
     args = parse()
     if args.cpu_sample:
         print(json.dumps(cpu_sample(args.cpu_iters)))
+        return
+    if args.mttkrp_only:
+        run_mttkrp_only(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

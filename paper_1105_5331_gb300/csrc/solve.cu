@@ -118,6 +118,9 @@ cp_status solve_impl(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* o, do
   cp_precision prec = o->prec;
   bool polish_pending = (o->prec != CP_FP64) && o->polish;
   const double tol_now_mixed = o->tol * (o->mixed_tol_factor > 0 ? o->mixed_tol_factor : 1.0);
+  constexpr int kMixedStall = 50;   // mixed iterations without a new best ||g|| before FP64
+  double best_mixed = INFINITY;
+  int since_best = 0;
 
   auto body = [&]() -> cp_status {
     CP_CUDA(cudaMemcpyAsync(s.work, u_user, sizeof(double) * P,
@@ -137,7 +140,16 @@ cp_status solve_impl(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* o, do
       r.gnorm_over_P = gn;
       if (!std::isfinite(gn)) return CP_ERR_NONFINITE;
       const double tol_now = (prec != CP_FP64 && polish_pending) ? tol_now_mixed : o->tol;
-      if (gn < tol_now) {
+      // a mixed phase that stops improving hands over to FP64 early
+      if (prec != CP_FP64 && polish_pending) {
+        if (gn < best_mixed) {
+          best_mixed = gn;
+          since_best = 0;
+        } else if (++since_best >= kMixedStall) {
+          best_mixed = 0.0;   // forces the switch below
+        }
+      }
+      if (gn < tol_now || (prec != CP_FP64 && polish_pending && best_mixed == 0.0)) {
         if (prec != CP_FP64 && polish_pending) {
           // switch to FP64: exact gradient at u, fresh window
           prec = CP_FP64;

@@ -1,0 +1,114 @@
+"""GPU checks of the mixed-precision dense MTTKRP (tcgen05, bf16x3 split
+products, FP32 accumulation) against the FP64 oracle, through the C ABI.
+
+Stated bound: relative Frobenius error of M^(n) <= 5e-5 (each split product
+carries ~2^-17 relative error, the accumulation is FP32); f and g built from
+these MTTKRPs are held to the same relative bound against their FP64 values
+(g is compared relative to ||M||, the scale at which its terms cancel)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import cp_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 5e-5
+
+
+@pytest.fixture(scope="module")
+def cp():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1105_5331_gb300 as cp
+    return cp
+
+
+@pytest.fixture(scope="module")
+def ctx(cp):
+    c = cp.cp_ctx_create(0, torch.cuda.current_stream())
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0)
+
+
+SHAPES = [
+    ((20, 20, 20), 3, np.float64),        # tiny, one k-tile group per CTA
+    ((7, 5, 3), 1, np.float32),           # K-bar below one tile
+    ((130, 33, 17), 16, np.float32),      # two M tiles, ragged rows and k
+    ((96, 40, 30, 5), 32, np.float32),    # 4-way, R = 32
+    ((300, 20, 9), 20, np.float32),       # 3 M tiles -> two row groups
+    ((64, 64, 64), 48, np.float32),       # padded rank 48
+    ((17, 256, 12), 64, np.float32),      # R = 64
+]
+
+
+@pytest.mark.parametrize("shape,R,dtype", SHAPES)
+def test_mixed_mttkrp_error_bound(cp, ctx, shape, R, dtype):
+    rng = np.random.default_rng(R)
+    T = rng.standard_normal(shape).astype(dtype)
+    u = synth.initial_guess(rng, shape, R)
+    F = O.unpack(u, shape, R)
+    t = cp.cp_tensor_dense(ctx, dev(T))
+    ud = dev(u)
+    for n in range(len(shape)):
+        out = torch.empty(shape[n] * R, dtype=torch.float64, device="cuda")
+        cp.cp_mttkrp(ctx, t, R, ud, n, out, cp.CP_MIXED_BF16X3)
+        cp.cp_ctx_sync(ctx)
+        ref = O.mttkrp_dense(T.astype(np.float64), F, n)
+        err = rel(out.cpu().numpy().reshape(ref.shape), ref)
+        assert err <= MIXED_TOL, (shape, R, n, err)
+
+
+def test_mixed_mttkrp_deterministic(cp, ctx):
+    rng = np.random.default_rng(3)
+    T = rng.standard_normal((130, 70, 33)).astype(np.float32)
+    u = dev(synth.initial_guess(rng, T.shape, 16))
+    t = cp.cp_tensor_dense(ctx, dev(T))
+    outs = []
+    for _ in range(2):
+        out = torch.empty(70 * 16, dtype=torch.float64, device="cuda")
+        cp.cp_mttkrp(ctx, t, 16, u, 1, out, cp.CP_MIXED_BF16X3)
+        cp.cp_ctx_sync(ctx)
+        outs.append(out.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_mixed_fg_error_bound(cp, ctx):
+    prob, u0 = synth.workload_dense_small()
+    X = O.DenseTensor(prob.T)
+    t = cp.cp_tensor_dense(ctx, dev(prob.T))
+    ud = dev(u0)
+    f = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(ud)
+    cp.cp_fg(ctx, t, 3, ud, f, g, cp.CP_MIXED_BF16X3)
+    cp.cp_ctx_sync(ctx)
+    fo, go = O.fg(X, u0, 3)
+    F = O.unpack(u0, prob.dims, 3)
+    Mscale = np.sqrt(sum(np.sum(O.mttkrp_dense(prob.T, F, n) ** 2) for n in range(3)))
+    assert abs(f.item() - fo) <= MIXED_TOL * (X.norm2 + abs(fo))
+    assert np.linalg.norm(g.cpu().numpy() - go) <= MIXED_TOL * Mscale
+
+
+def test_full_size_dense_256_mixed_mttkrp(cp, ctx):
+    """The 256^3, R=16 workload at full size in the launch configuration the
+    bench times: every mode against the FP64 oracle."""
+    prob, u0 = synth.workload_dense_256()
+    t = cp.cp_tensor_dense(ctx, dev(prob.T))
+    ud = dev(u0)
+    F = O.unpack(u0, prob.dims, 16)
+    for n in range(3):
+        out = torch.empty(256 * 16, dtype=torch.float64, device="cuda")
+        cp.cp_mttkrp(ctx, t, 16, ud, n, out, cp.CP_MIXED_BF16X3)
+        cp.cp_ctx_sync(ctx)
+        ref = O.mttkrp_dense(prob.T, F, n)
+        assert rel(out.cpu().numpy().reshape(ref.shape), ref) <= MIXED_TOL
