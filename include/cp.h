@@ -200,6 +200,9 @@ typedef struct {
                        /* FP64 gradient meets tol (1 = on)                       */
   double mixed_tol_factor; /* mixed phase stops at tol * factor before polishing */
   cp_ls_opts ls;
+  int mixed_maxfev;    /* mixed precision phase: at most this many f/g        */
+                       /* evaluations per line search (f is resolved only to  */
+                       /* ~1e-9 relative there); FP64 iterations use ls.maxfev */
 } cp_solve_opts;
 
 typedef struct {

@@ -51,7 +51,8 @@ class cp_ls_opts(C.Structure):
 class cp_solve_opts(C.Structure):
     _fields_ = [("R", C.c_int), ("w", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
                 ("eps", C.c_double), ("prec", C.c_int), ("polish", C.c_int),
-                ("mixed_tol_factor", C.c_double), ("ls", cp_ls_opts)]
+                ("mixed_tol_factor", C.c_double), ("ls", cp_ls_opts),
+                ("mixed_maxfev", C.c_int)]
 
 
 class cp_solve_report(C.Structure):

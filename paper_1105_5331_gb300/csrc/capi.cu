@@ -451,7 +451,16 @@ cp_status ngmres_step(cp_ctx* ctx, int64_t Pn, int m, const double* U, const dou
     return CP_ERR_ARG;
   }
   CP_TRY(use_device(ctx));
-  return ngmres_core(ctx, Pn, m, U, G, 0, m, ubar, gbar, eps, uhat, alpha);
+  int* win = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&win, sizeof(int) * 2));
+  ctx->h_pinned_i[8] = 0;
+  ctx->h_pinned_i[9] = m;
+  CP_CUDA(cudaMemcpyAsync(win, ctx->h_pinned_i + 8, sizeof(int) * 2, cudaMemcpyHostToDevice, ctx->stream));
+  const cp_status st = ngmres_core(ctx, Pn, win, m, U, G, ubar, gbar, eps, uhat, alpha);
+  ws_free(ctx, win);
+  // the pinned staging slot must not be reused before the copy has run
+  CP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return st;
 }
 
 void cp_ls_opts_default(cp_ls_opts* o) {
@@ -522,6 +531,7 @@ void cp_solve_opts_default(cp_solve_opts* o, int R) {
   o->polish = 1;
   o->mixed_tol_factor = 1.0;
   cp_ls_opts_default(&o->ls);
+  o->mixed_maxfev = 5;
 }
 
 cp_status cp_solve(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* opts, double* u,

@@ -164,11 +164,16 @@ cp_status fg_assemble(cp_ctx* ctx, const Layout& L, const double* u, const doubl
 cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double* dst,
                          const double* gsrc, double* gdst, double* lambda);
 
-// Window-indexed N-GMRES Step II.  Window row j (oldest first) is at ring slot
-// (start + j) % wcap.
-cp_status ngmres_core(cp_ctx* ctx, int64_t P, int m, const double* U, const double* G,
-                      int start, int wcap, const double* ubar, const double* gbar, double eps,
+// Window-indexed N-GMRES Step II.  win (device) = {start, m}; window row j
+// (oldest first) is ring slot (start + j) % cap.
+cp_status ngmres_core(cp_ctx* ctx, int64_t P, const int* win, int cap, const double* U,
+                      const double* G, const double* ubar, const double* gbar, double eps,
                       double* uhat, double* alpha);
+// Push (u, g) into the window ring (or reset it to {(u, g)}).
+cp_status window_update(cp_ctx* ctx, int* win, int cap, bool reset, int64_t P, const double* u,
+                        const double* g, double* U, double* G);
+// Create the bf16 planes of every mode before graph capture.
+cp_status prepare_mixed(cp_ctx* ctx, cp_tensor* t);
 
 // Deterministic FP64 dot product: out = x . y (device scalar).
 cp_status dot(cp_ctx* ctx, int64_t n, const double* x, const double* y, double* out);

@@ -7,6 +7,9 @@
 // contiguous-in-the-contraction product, whatever n is.  The extra memory
 // (N copies) is small next to the GPU's HBM.
 #include "cp_internal.cuh"
+#include "reduce.cuh"
+
+#include <mutex>
 
 namespace cpg {
 
@@ -130,27 +133,10 @@ __global__ void __launch_bounds__(256) mttkrp_f64_kernel(const TT* __restrict__ 
   }
 }
 
-// M[e] = sum_c partial[c][e], c in increasing order.
-__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nparts, int64_t n,
-                                       double* __restrict__ out) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += partial[(int64_t)c * n + e];
-    out[e] = s;
-  }
-}
-
 }  // namespace
 
 cp_status reduce_partials(cp_ctx* ctx, const double* partial, int nparts, int64_t n, double* out) {
-  const int threads = 256;
-  int64_t blocks = (n + threads - 1) / threads;
-  if (blocks > 4 * ctx->num_sms) blocks = 4 * ctx->num_sms;
-  if (blocks < 1) blocks = 1;
-  reduce_partials_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(partial, nparts, n, out);
-  CP_LAUNCH_CHECK();
-  return CP_OK;
+  return reduce_parts<double>(ctx, partial, nparts, n, out);
 }
 
 cp_status sumsq(cp_ctx* ctx, const void* x, cp_dtype dt, int64_t n, double* d_out) {

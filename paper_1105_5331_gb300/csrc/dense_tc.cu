@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "cp_internal.cuh"
+#include "reduce.cuh"
 
 namespace cpg {
 
@@ -37,6 +38,7 @@ constexpr int kThreads = 192;
 constexpr uint32_t kTileBytes = kBM * kBK * 2;   // one plane, one M tile: 16 KB
 constexpr int kMaxTilesPerCta = 2;       // M tiles handled by one CTA
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
+constexpr int kMaxDynSmem = 227 * 1024;
 
 struct TcParams {
   int64_t I;
@@ -49,6 +51,8 @@ struct TcParams {
   int nother;
   const float* tab[CP_MAX_N - 1];    // FP32 factors of the other modes, row stride R
   int64_t dimo[CP_MAX_N - 1];
+  uint32_t tab_soff[CP_MAX_N - 1];   // offsets (floats) of the tables in shared memory
+  int tab_smem;                      // 1: builders read the tables from shared memory
   float* partial;             // [gridDim.x][I][R]
   int* status;
   uint32_t ncols;             // TMEM columns allocated
@@ -161,6 +165,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+template <int NO>
 __global__ void __launch_bounds__(kThreads, 1)
     mttkrp_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
                      const TcParams p) {
@@ -261,6 +266,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int kk = t & (kBK - 1);              // contraction element within the tile
     const int half = t >> 6;                   // which half of the padded ranks
     const int rh = p.RP >> 1;
+    // factor tables of the other modes, staged once in shared memory
+    float* tabs = (float*)(gbase + (((tmem_slot + 8u - base) + 15u) & ~15u));
+    const float* tb[NO];
+    uint32_t dim32[NO];
+#pragma unroll
+    for (int j = 0; j < NO; ++j) {
+      dim32[j] = (uint32_t)p.dimo[j];
+      if (p.tab_smem) {
+        float* dst = tabs + p.tab_soff[j];
+        const int64_t n_el = p.dimo[j] * p.R;
+        for (int64_t e = t; e < n_el; e += 128) dst[e] = p.tab[j][e];
+        tb[j] = dst;
+      } else {
+        tb[j] = p.tab[j];
+      }
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
     for (int i = 0; i < nk; ++i) {
       const int s = i % S;
       const uint32_t ph = (uint32_t)((i / S) & 1);
@@ -269,22 +291,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint8_t* st = gbase + (size_t)s * stage_bytes;
         uint8_t* bhi = st + 2u * (uint32_t)p.ntm * kTileBytes;
         uint8_t* blo = bhi + b_bytes;
-        const int64_t kb = (kt0 + i) * kBK + kk;
-        int64_t idx[CP_MAX_N - 1];
-        const bool in = kb < p.Kbar;
-        if (in) {
-          int64_t rem = kb;
-          for (int j = p.nother - 1; j >= 0; --j) {
-            const int64_t q = rem / p.dimo[j];
-            idx[j] = rem - q * p.dimo[j];
-            rem = q;
-          }
+        const int64_t kb64 = (kt0 + i) * kBK + kk;
+        const bool in = kb64 < p.Kbar;
+        const float* rows[NO];
+        uint32_t rem = (uint32_t)(in ? kb64 : 0);
+#pragma unroll
+        for (int j = NO - 1; j >= 0; --j) {
+          const uint32_t q = rem / dim32[j];
+          rows[j] = tb[j] + (size_t)(rem - q * dim32[j]) * p.R;
+          rem = q;
         }
         for (int r = half * rh; r < (half + 1) * rh; ++r) {
           float v = 0.f;
           if (in && r < p.R) {
-            v = 1.f;
-            for (int j = 0; j < p.nother; ++j) v *= p.tab[j][idx[j] * p.R + r];
+            v = rows[0][r];
+#pragma unroll
+            for (int j = 1; j < NO; ++j) v *= rows[j][r];
           }
           const __nv_bfloat16 h = __float2bfloat16_rn(v);
           const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
@@ -356,16 +378,6 @@ __global__ void split_planes_kernel(const TT* __restrict__ src, int64_t I, int64
 __global__ void f32_table_kernel(const double* __restrict__ A, int64_t n, float* __restrict__ out) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
     out[k] = (float)A[k];
-}
-
-// M[e] = sum_c partial[c][e] in FP64, c increasing.
-__global__ void reduce_f32_partials_kernel(const float* __restrict__ partial, int nparts, int64_t n,
-                                           double* __restrict__ out) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += (double)partial[(int64_t)c * n + e];
-    out[e] = s;
-  }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -456,6 +468,39 @@ static cp_status ensure_planes(cp_ctx* ctx, cp_tensor* t, int n) {
   return CP_OK;
 }
 
+typedef void (*TcKernel)(CUtensorMap, CUtensorMap, TcParams);
+
+static TcKernel tc_kernel_for(int nother) {
+  switch (nother) {
+    case 1: return mttkrp_tc_kernel<1>;
+    case 2: return mttkrp_tc_kernel<2>;
+    case 3: return mttkrp_tc_kernel<3>;
+    case 4: return mttkrp_tc_kernel<4>;
+    case 5: return mttkrp_tc_kernel<5>;
+    case 6: return mttkrp_tc_kernel<6>;
+    default: return mttkrp_tc_kernel<7>;
+  }
+}
+
+static cp_status set_smem_attr() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    for (int no = 1; no <= CP_MAX_N - 1; ++no)
+      CP_CUDA(cudaFuncSetAttribute(tc_kernel_for(no), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kMaxDynSmem));
+    attr_set = true;
+  }
+  return CP_OK;
+}
+
+cp_status prepare_mixed(cp_ctx* ctx, cp_tensor* t) {
+  if (t->kind != 0) return CP_OK;
+  for (int n = 0; n < t->N; ++n) CP_TRY(ensure_planes(ctx, t, n));
+  CP_TRY(set_smem_attr());
+  CP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return CP_OK;
+}
+
 cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, int mode, double* out) {
   CP_TRY(ensure_planes(ctx, t, mode));
   const MixedMode& mm = tc_state(t)->mode[mode];
@@ -472,8 +517,16 @@ cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const d
   p.ntm = (int)std::min<int64_t>(mtiles, kMaxTilesPerCta);
   const int mgroups = (int)((mtiles + kMaxTilesPerCta - 1) / kMaxTilesPerCta);
   const uint32_t stage_bytes = (uint32_t)p.ntm * 2u * kTileBytes + 2u * (uint32_t)RP * 128u;
-  const uint32_t budget = 200u * 1024u;
-  p.stages = (int)std::min<uint32_t>(6u, budget / stage_bytes);
+  // FP32 tables of the other modes' factors (in shared memory when they fit)
+  size_t tab_elems = 0;
+  for (int m = 0; m < t->N; ++m)
+    if (m != mode) tab_elems += (size_t)t->dims[m] * R;
+  const size_t fixed = 1024 + 256 + 64;          // alignment slack, barriers, TMEM slot
+  const size_t tab_bytes = sizeof(float) * tab_elems;
+  p.tab_smem = (tab_bytes <= 96 * 1024 &&
+                (size_t)kMaxDynSmem >= fixed + tab_bytes + 2 * (size_t)stage_bytes) ? 1 : 0;
+  const size_t avail = (size_t)kMaxDynSmem - fixed - (p.tab_smem ? tab_bytes : 0);
+  p.stages = (int)std::min<size_t>(6, avail / stage_bytes);
   if (p.stages < 2) {
     set_error("mixed MTTKRP: rank %d too large for the shared-memory pipeline", R);
     return CP_ERR_UNSUPPORTED;
@@ -485,13 +538,9 @@ cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const d
   const int64_t target = std::max<int64_t>(1, ctx->num_sms / mgroups);
   p.ktiles_per_cta = (p.ktiles + target - 1) / target;
   const int gx = (int)((p.ktiles + p.ktiles_per_cta - 1) / p.ktiles_per_cta);
-  // FP32 tables of the other modes' factors
-  size_t tab_elems = 0;
-  for (int m = 0; m < t->N; ++m)
-    if (m != mode) tab_elems += (size_t)t->dims[m] * R;
   float* tabs = nullptr;
   float* partial = nullptr;
-  CP_TRY(ws_alloc(ctx, (void**)&tabs, sizeof(float) * tab_elems + 64));
+  CP_TRY(ws_alloc(ctx, (void**)&tabs, tab_bytes + 64));
   CP_TRY(ws_alloc(ctx, (void**)&partial, sizeof(float) * (size_t)gx * I * R));
   size_t off = 0;
   p.nother = 0;
@@ -503,23 +552,17 @@ cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const d
     CP_LAUNCH_CHECK();
     p.tab[p.nother] = tabs + off;
     p.dimo[p.nother] = t->dims[m];
+    p.tab_soff[p.nother] = (uint32_t)off;
     ++p.nother;
     off += (size_t)n_el;
   }
   p.partial = partial;
   p.status = ctx->d_status;
-  const size_t smem = (size_t)p.stages * stage_bytes + 1024 + 256;
-  static bool attr_set = false;
-  if (!attr_set) {
-    CP_CUDA(cudaFuncSetAttribute(mttkrp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr_set = true;
-  }
-  mttkrp_tc_kernel<<<dim3(gx, mgroups), kThreads, smem, ctx->stream>>>(mm.hi, mm.lo, p);
+  const size_t smem = (size_t)p.stages * stage_bytes + fixed + (p.tab_smem ? tab_bytes : 0);
+  CP_TRY(set_smem_attr());
+  tc_kernel_for(p.nother)<<<dim3(gx, mgroups), kThreads, smem, ctx->stream>>>(mm.hi, mm.lo, p);
   CP_LAUNCH_CHECK();
-  const int64_t n_out = I * R;
-  reduce_f32_partials_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n_out + 255) / 256, 4 * ctx->num_sms)),
-                               256, 0, ctx->stream>>>(partial, gx, n_out, out);
-  CP_LAUNCH_CHECK();
+  CP_TRY(reduce_parts<float>(ctx, partial, gx, I * R, out));
   ws_free(ctx, partial);
   ws_free(ctx, tabs);
   return CP_OK;

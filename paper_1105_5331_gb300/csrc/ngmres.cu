@@ -7,6 +7,11 @@
 // are formed per element, never stored); one block reduces the per-CTA sums in
 // a fixed order, factors the m x m system by Cholesky and solves for alpha; a
 // last pass forms uhat.
+//
+// The window is a ring of `cap` slots in device memory; its state
+// win = {start, m} also lives in device memory (window row j, oldest first, is
+// slot (start + j) % cap), so the whole step can be replayed from a CUDA graph
+// while the window grows and rotates (window size w of Section 2.1).
 #include <algorithm>
 
 #include "cp_internal.cuh"
@@ -30,11 +35,13 @@ __device__ __forceinline__ void pair_of(int o, int m, int* j, int* l) {
   *l = jj + (o - base);
 }
 
-__global__ void ngmres_dots_kernel(const double* __restrict__ G, int start, int wcap, int m,
+__global__ void ngmres_dots_kernel(const double* __restrict__ G, const int* __restrict__ win, int cap,
                                    int64_t P, const double* __restrict__ gbar, int64_t chunk,
-                                   double* __restrict__ part) {
+                                   int nout_max, double* __restrict__ part) {
   __shared__ double pt[CP_MAX_W * (kTile + 1)];
   __shared__ double gt[kTile];
+  const int start = win[0];
+  const int m = win[1];
   const int npairs = m * (m + 1) / 2;
   const int nout = npairs + m;
   int oj[kMaxOutPerThread], ol[kMaxOutPerThread];
@@ -60,7 +67,7 @@ __global__ void ngmres_dots_kernel(const double* __restrict__ G, int start, int 
     for (int e = threadIdx.x; e < kt; e += blockDim.x) gt[e] = gbar[k0 + e];
     for (int e = threadIdx.x; e < m * kt; e += blockDim.x) {
       const int j = e / kt, kk = e - (e / kt) * kt;
-      const int slot = (start + j) % wcap;
+      const int slot = (start + j) % cap;
       pt[j * (kTile + 1) + kk] = gbar[k0 + kk] - G[(int64_t)slot * P + k0 + kk];
     }
     __syncthreads();
@@ -77,21 +84,23 @@ __global__ void ngmres_dots_kernel(const double* __restrict__ G, int start, int 
 #pragma unroll
   for (int q = 0; q < kMaxOutPerThread; ++q) {
     const int o = threadIdx.x + q * blockDim.x;
-    if (o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[q];
+    if (o < nout) part[(int64_t)blockIdx.x * nout_max + o] = acc[q];
   }
 }
 
-__global__ void ngmres_solve_kernel(const double* __restrict__ part, int nparts, int m, double eps,
-                                    double* __restrict__ alpha, int* status) {
+__global__ void ngmres_solve_kernel(const double* __restrict__ part, int nparts, int nout_max,
+                                    const int* __restrict__ win, double eps, double* __restrict__ alpha,
+                                    int* status) {
   __shared__ double H[CP_MAX_W * CP_MAX_W];
   __shared__ double rhs[CP_MAX_W];
   __shared__ double dmax;
   __shared__ int flag;
+  const int m = win[1];
   const int npairs = m * (m + 1) / 2;
   const int nout = npairs + m;
   for (int o = threadIdx.x; o < nout; o += blockDim.x) {
     double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * nout + o];
+    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * nout_max + o];
     if (o < npairs) {
       int j, l;
       pair_of(o, m, &j, &l);
@@ -136,10 +145,12 @@ __global__ void ngmres_solve_kernel(const double* __restrict__ part, int nparts,
   }
 }
 
-__global__ void ngmres_combine_kernel(const double* __restrict__ U, int start, int wcap, int m,
+__global__ void ngmres_combine_kernel(const double* __restrict__ U, const int* __restrict__ win, int cap,
                                       int64_t P, const double* __restrict__ ubar,
                                       const double* __restrict__ alpha, double* __restrict__ uhat) {
   __shared__ double a[CP_MAX_W];
+  const int start = win[0];
+  const int m = win[1];
   for (int j = threadIdx.x; j < m; j += blockDim.x) a[j] = alpha[j];
   __syncthreads();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
@@ -147,41 +158,76 @@ __global__ void ngmres_combine_kernel(const double* __restrict__ U, int start, i
     const double ub = ubar[k];
     double acc = 0.0;
     for (int j = 0; j < m; ++j) {
-      const int slot = (start + j) % wcap;
+      const int slot = (start + j) % cap;
       acc += a[j] * (ub - U[(int64_t)slot * P + k]);
     }
     uhat[k] = ub + acc;
   }
 }
 
+// Copy (u, g) into the slot the window update will use; win is read only.
+__global__ void window_copy_kernel(const int* __restrict__ win, int cap, int reset, int64_t P,
+                                   const double* __restrict__ u, const double* __restrict__ g,
+                                   double* __restrict__ U, double* __restrict__ G) {
+  const int start = win[0], m = win[1];
+  const int slot = reset ? 0 : (m < cap ? (start + m) % cap : start);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    U[(int64_t)slot * P + k] = u[k];
+    G[(int64_t)slot * P + k] = g[k];
+  }
+}
+
+// Window bookkeeping after the copy: reset -> {0, 1}; push grows to cap,
+// then drops the oldest.
+__global__ void window_index_kernel(int* win, int cap, int reset) {
+  if (reset) {
+    win[0] = 0;
+    win[1] = 1;
+  } else if (win[1] < cap) {
+    win[1] += 1;
+  } else {
+    win[0] = (win[0] + 1) % cap;
+  }
+}
+
 }  // namespace
 
-cp_status ngmres_core(cp_ctx* ctx, int64_t P, int m, const double* U, const double* G, int start,
-                      int wcap, const double* ubar, const double* gbar, double eps, double* uhat,
-                      double* alpha) {
-  if (m < 1 || m > CP_MAX_W) {
-    set_error("ngmres: window size %d outside [1, %d]", m, CP_MAX_W);
+cp_status ngmres_core(cp_ctx* ctx, int64_t P, const int* win, int cap, const double* U, const double* G,
+                      const double* ubar, const double* gbar, double eps, double* uhat, double* alpha) {
+  if (cap < 1 || cap > CP_MAX_W) {
+    set_error("ngmres: window capacity %d outside [1, %d]", cap, CP_MAX_W);
     return CP_ERR_ARG;
   }
-  const int nout = m * (m + 1) / 2 + m;
+  const int nout_max = cap * (cap + 1) / 2 + cap;
   int64_t nb = std::min<int64_t>((P + 255) / 256, 2 * (int64_t)ctx->num_sms);
   nb = std::max<int64_t>(nb, 1);
   const int64_t chunk = (P + nb - 1) / nb;
-  nb = (P + chunk - 1) / chunk;
-  if (nb < 1) nb = 1;
+  nb = std::max<int64_t>((P + chunk - 1) / chunk, 1);
   double* part = nullptr;
   double* a = alpha;
-  CP_TRY(ws_alloc(ctx, (void**)&part, sizeof(double) * ((size_t)nb * nout + CP_MAX_W)));
-  if (!a) a = part + (size_t)nb * nout;
-  ngmres_dots_kernel<<<(unsigned)nb, 256, 0, ctx->stream>>>(G, start, wcap, m, P, gbar, chunk, part);
+  CP_TRY(ws_alloc(ctx, (void**)&part, sizeof(double) * ((size_t)nb * nout_max + CP_MAX_W)));
+  if (!a) a = part + (size_t)nb * nout_max;
+  ngmres_dots_kernel<<<(unsigned)nb, 256, 0, ctx->stream>>>(G, win, cap, P, gbar, chunk, nout_max, part);
   CP_LAUNCH_CHECK();
-  ngmres_solve_kernel<<<1, 256, 0, ctx->stream>>>(part, (int)nb, m, eps, a, ctx->d_status);
+  ngmres_solve_kernel<<<1, 256, 0, ctx->stream>>>(part, (int)nb, nout_max, win, eps, a, ctx->d_status);
   CP_LAUNCH_CHECK();
   int64_t cb = std::min<int64_t>((P + 255) / 256, 8 * (int64_t)ctx->num_sms);
-  ngmres_combine_kernel<<<(unsigned)std::max<int64_t>(cb, 1), 256, 0, ctx->stream>>>(
-      U, start, wcap, m, P, ubar, a, uhat);
+  ngmres_combine_kernel<<<(unsigned)std::max<int64_t>(cb, 1), 256, 0, ctx->stream>>>(U, win, cap, P, ubar, a,
+                                                                                      uhat);
   CP_LAUNCH_CHECK();
   ws_free(ctx, part);
+  return CP_OK;
+}
+
+cp_status window_update(cp_ctx* ctx, int* win, int cap, bool reset, int64_t P, const double* u,
+                        const double* g, double* U, double* G) {
+  int64_t cb = std::min<int64_t>((P + 255) / 256, 8 * (int64_t)ctx->num_sms);
+  window_copy_kernel<<<(unsigned)std::max<int64_t>(cb, 1), 256, 0, ctx->stream>>>(win, cap, reset ? 1 : 0, P, u,
+                                                                                   g, U, G);
+  CP_LAUNCH_CHECK();
+  window_index_kernel<<<1, 1, 0, ctx->stream>>>(win, cap, reset ? 1 : 0);
+  CP_LAUNCH_CHECK();
   return CP_OK;
 }
 
