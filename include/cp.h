@@ -124,6 +124,24 @@ void cp_tensor_destroy(cp_tensor* t);
 cp_status cp_mttkrp(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, int mode,
                     double* out, cp_precision prec);
 
+/* FP64 dense MTTKRP that allocates no device memory (no counterpart in the
+ * paper; it exists for callers that cannot allocate while they run: code that
+ * enqueues work inside a stream capture it does not own, serving loops with a
+ * fixed memory budget in which cudaMalloc may stall or fail, or programs
+ * whose device memory is owned by another allocator).  Same arguments and
+ * result as cp_mttkrp with CP_FP64 on a dense tensor (t must be dense; t and
+ * ctx are created beforehand).  The split-K partial sums go to one 8 MiB
+ * scratch array inside the library, which every GPU that loads the library
+ * holds until the process exits.  Rejected with CP_ERR_SHAPE when
+ * I_mode * R * 8 bytes exceeds that scratch.  The first call on a device
+ * looks up the scratch's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the one scratch
+ * array: calls that may overlap on the GPU (other streams, other contexts on
+ * the same device) race and must be serialised by the caller.  The scratch
+ * needs no clearing: every call overwrites the part it reads.  Asynchronous. */
+cp_status cp_mttkrp_noalloc(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, int mode,
+                            double* out);
+
 /* Objective and gradient (Eq. fA, Eq. Gn):
  *   f = 1/2 (||T||^2 - 2 <T, A_R> + sum_{r,s} Gamma[r,s]),
  *   G^(n) = -M^(n) + A^(n) Gammabar^(n),

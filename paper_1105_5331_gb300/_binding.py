@@ -31,7 +31,8 @@ EXPORTED = [
     "cp_ctx_create", "cp_ctx_destroy", "cp_last_error", "cp_ctx_sync", "cp_ctx_stream",
     "cp_kernel_launches",
     "cp_tensor_dense", "cp_tensor_coo", "cp_tensor_info", "cp_tensor_sorted_mode",
-    "cp_tensor_destroy", "cp_mttkrp", "cp_fg", "cp_als_sweep", "cp_normalize", "ngmres_step",
+    "cp_tensor_destroy", "cp_mttkrp", "cp_mttkrp_noalloc", "cp_fg", "cp_als_sweep", "cp_normalize",
+    "ngmres_step",
     "cp_ls_opts_default", "linesearch", "cp_solve_opts_default", "cp_solve",
 ]
 
@@ -86,6 +87,7 @@ def _load():
         "cp_tensor_sorted_mode": (I, [VP, VP, I, P, P, P, C.POINTER(I64)]),
         "cp_tensor_destroy": (None, [VP]),
         "cp_mttkrp": (I, [VP, VP, I, VP, I, VP, I]),
+        "cp_mttkrp_noalloc": (I, [VP, VP, I, VP, I, VP]),
         "cp_fg": (I, [VP, VP, I, VP, VP, VP, I]),
         "cp_als_sweep": (I, [VP, VP, I, VP, I, I]),
         "cp_normalize": (I, [VP, I, P, I, VP, VP, VP]),
@@ -267,6 +269,13 @@ def cp_tensor_destroy(t):
 
 def cp_mttkrp(ctx, t, R: int, u, mode: int, out, prec: int = CP_FP64):
     _check(_lib.cp_mttkrp(_h(ctx), _h(t), int(R), _ptr(u), int(mode), _ptr(out), int(prec)))
+    return out
+
+
+def cp_mttkrp_noalloc(ctx, t, R: int, u, mode: int, out):
+    """FP64 dense MTTKRP that allocates no device memory (fixed 8 MiB library
+    scratch shared by all calls; see include/cp.h)."""
+    _check(_lib.cp_mttkrp_noalloc(_h(ctx), _h(t), int(R), _ptr(u), int(mode), _ptr(out)))
     return out
 
 

@@ -222,4 +222,101 @@ cp_status mttkrp_dense_f64(cp_ctx* ctx, const cp_tensor* t, const Layout& L, con
   return CP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 dense MTTKRP that allocates nothing (cp_mttkrp_noalloc).
+//
+// Callers that cannot allocate device memory while they run -- code that
+// enqueues work inside someone else's stream capture, real-time or serving
+// loops with a fixed memory budget in which cudaMalloc may stall or fail,
+// or host programs whose device memory is owned by another allocator -- can
+// still run the MTTKRP: its split-K partial sums go to this file-scope device
+// array instead of workspace memory.  The array is part of the library image:
+// every GPU that loads the library holds it until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;   // 8 MiB
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchBytes / sizeof(double)];
+
+// Device address of g_noalloc_scratch, looked up once per device (with that
+// device current); the host-side symbol is not a device address.
+constexpr int kMaxDevices = 64;
+void* g_noalloc_addr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+cp_status noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) {
+    set_error("cp_mttkrp_noalloc: device %d out of range", device);
+    return CP_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    CP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[device] = p;
+  }
+  *out = g_noalloc_addr[device];
+  return CP_OK;
+}
+
+}  // namespace
+
 }  // namespace cpg
+
+extern "C" cp_status cp_mttkrp_noalloc(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, int mode,
+                                       double* out) {
+  using namespace cpg;
+  if (!ctx || !t || !u || !out) {
+    set_error("cp_mttkrp_noalloc: null argument");
+    return CP_ERR_ARG;
+  }
+  if (t->kind != 0) {
+    set_error("cp_mttkrp_noalloc: dense tensors only");
+    return CP_ERR_UNSUPPORTED;
+  }
+  if (R < 1 || R > CP_MAX_R || mode < 0 || mode >= t->N) {
+    set_error("cp_mttkrp_noalloc: R = %d or mode = %d out of range", R, mode);
+    return CP_ERR_ARG;
+  }
+  const int64_t I = t->dims[mode];
+  const size_t per_cta = sizeof(double) * (size_t)I * R;
+  if (per_cta > kNoAllocScratchBytes) {
+    set_error("cp_mttkrp_noalloc: I_mode x R x 8 bytes = %zu exceeds the %zu-byte scratch", per_cta,
+              kNoAllocScratchBytes);
+    return CP_ERR_SHAPE;
+  }
+  int cur = -1;
+  CP_CUDA(cudaGetDevice(&cur));
+  if (cur != ctx->device) CP_CUDA(cudaSetDevice(ctx->device));
+  void* scratch = nullptr;
+  CP_TRY(noalloc_scratch(ctx->device, &scratch));
+  Layout L;
+  L.set(t->N, t->dims, R);
+  const int64_t Kb = kbar(t, mode);
+  KRDesc kr;
+  kr.cnt = 0;
+  for (int m = 0; m < t->N; ++m) {
+    if (m == mode) continue;
+    kr.A[kr.cnt] = u + L.off[m];
+    kr.I[kr.cnt] = t->dims[m];
+    ++kr.cnt;
+  }
+  const int nsplit = (R + kF64RSUB - 1) / kF64RSUB;
+  const int64_t want = ((I * nsplit + 31) / 32) * 32;
+  const int threads = (int)std::max<int64_t>(32, std::min<int64_t>(256, want));
+  const int64_t ntiles = (Kb + kF64BK - 1) / kF64BK;
+  const int64_t fit = (int64_t)(kNoAllocScratchBytes / per_cta);   // partial blocks that fit
+  const int64_t target = std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)ctx->num_sms, fit));
+  const int64_t tiles_per_cta = (ntiles + target - 1) / target;
+  const int grid = (int)((ntiles + tiles_per_cta - 1) / tiles_per_cta);
+  double* partial = (double*)scratch;
+  const size_t smem = sizeof(double) * kF64BK * R;
+  if (t->dtype == CP_DTYPE_F64)
+    mttkrp_f64_kernel<double><<<grid, threads, smem, ctx->stream>>>((const double*)t->Tn[mode], I, Kb, kr, R,
+                                                                     tiles_per_cta, partial);
+  else
+    mttkrp_f64_kernel<float><<<grid, threads, smem, ctx->stream>>>((const float*)t->Tn[mode], I, Kb, kr, R,
+                                                                    tiles_per_cta, partial);
+  CP_LAUNCH_CHECK();
+  return reduce_parts<double>(ctx, partial, grid, I * R, out);
+}
