@@ -442,8 +442,13 @@ cp_status fg_eval(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double
   CP_TRY(ws_alloc(ctx, (void**)&grams, sizeof(double) * L.N * RR));
   CP_TRY(grams_all(ctx, L, u, grams));
   // Without g only the last mode's MTTKRP is needed for <T, A_R>.
-  for (int n = g ? 0 : L.N - 1; n < L.N; ++n)
-    CP_TRY(mttkrp_any(ctx, t, L, u, n, M + L.off[n], prec));
+  if (t->kind == 0 && prec == CP_MIXED_BF16X3) {
+    // one FP32 copy of the factors serves every mode
+    CP_TRY(mttkrp_dense_mixed_modes(ctx, const_cast<cp_tensor*>(t), L, u, g ? 0 : L.N - 1, M));
+  } else {
+    for (int n = g ? 0 : L.N - 1; n < L.N; ++n)
+      CP_TRY(mttkrp_any(ctx, t, L, u, n, M + L.off[n], prec));
+  }
   CP_TRY(fg_assemble(ctx, L, u, M, grams, t->norm2, f, g));
   ws_free(ctx, grams);
   ws_free(ctx, M);

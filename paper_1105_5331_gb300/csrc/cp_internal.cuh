@@ -143,6 +143,9 @@ cp_status mttkrp_dense_f64(cp_ctx* ctx, const cp_tensor* t, const Layout& L, con
 // Dense MTTKRP, bf16x3 split products on tcgen05 tensor cores, FP32 accumulate.
 cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u,
                              int mode, double* out);
+// Mixed MTTKRP of modes first..N-1 into M_all (packed like u).
+cp_status mttkrp_dense_mixed_modes(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u,
+                                   int first, double* M_all);
 // Sparse MTTKRP from the mode-sorted copy (FP64 or FP32 products).
 cp_status mttkrp_sparse(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u,
                         int mode, double* out, cp_precision prec);

@@ -52,6 +52,8 @@ struct TcParams {
   const float* tab[CP_MAX_N - 1];    // FP32 factors of the other modes, row stride R
   int64_t dimo[CP_MAX_N - 1];
   uint32_t tab_soff[CP_MAX_N - 1];   // offsets (floats) of the tables in shared memory
+  uint32_t tab_cpy[CP_MAX_N - 1];    // bytes copied per table (multiple of 16)
+  uint32_t tab_bytes;                // sum of tab_cpy
   int tab_smem;                      // 1: builders read the tables from shared memory
   float* partial;             // [gridDim.x][I][R]
   int* status;
@@ -110,6 +112,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm,
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
       ::"r"(dst), "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned addresses, size a
+// multiple of 16), completing on an mbarrier.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"((unsigned long long)src), "r"(bytes), "r"(bar)
       : "memory");
 }
 
@@ -180,7 +191,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto full_bar = [&](int s) { return bars + 8u * (uint32_t)s; };
   auto empty_bar = [&](int s) { return bars + 8u * (uint32_t)(S + s); };
   const uint32_t done_bar = bars + 16u * (uint32_t)S;
-  const uint32_t tmem_slot = done_bar + 8u;
+  const uint32_t tab_bar = done_bar + 8u;
+  const uint32_t tmem_slot = tab_bar + 8u;
+  const uint32_t tab_saddr = (tmem_slot + 8u + 15u) & ~15u;   // factor tables (16-byte aligned)
   volatile uint32_t* tmem_slot_ptr = (volatile uint32_t*)(gbase + (tmem_slot - base));
 
   const int warp = threadIdx.x >> 5;
@@ -196,6 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(empty_bar(s), 1);
     }
     mbar_init(done_bar, 1);
+    mbar_init(tab_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fence_proxy_async();
   }
@@ -213,6 +227,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
+      // the factor tables of the other modes: one bulk copy each, overlapped
+      // with the first tile loads
+      if (p.tab_smem) {
+        mbar_arrive_tx(tab_bar, p.tab_bytes);
+#pragma unroll
+        for (int j = 0; j < NO; ++j)
+          bulk_load(tab_saddr + 4u * p.tab_soff[j], p.tab[j], p.tab_cpy[j], tab_bar);
+      }
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
         const int s = i % S;
@@ -231,6 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // let copies still in flight land before the CTA can exit
       for (int i = max(0, issued - S); i < issued; ++i)
         mbar_wait(full_bar(i % S), (uint32_t)((i / S) & 1), p.status);
+      if (p.tab_smem) mbar_wait(tab_bar, 0u, p.status);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -266,27 +289,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int kk = t & (kBK - 1);              // contraction element within the tile
     const int half = t >> 6;                   // which half of the padded ranks
     const int rh = p.RP >> 1;
-    // factor tables of the other modes, staged once in shared memory
-    float* tabs = (float*)(gbase + (((tmem_slot + 8u - base) + 15u) & ~15u));
+    // factor tables of the other modes (shared memory when they fit)
+    const float* tabs = (const float*)(gbase + (tab_saddr - base));
     const float* tb[NO];
     uint32_t dim32[NO];
 #pragma unroll
     for (int j = 0; j < NO; ++j) {
       dim32[j] = (uint32_t)p.dimo[j];
-      if (p.tab_smem) {
-        float* dst = tabs + p.tab_soff[j];
-        const int64_t n_el = p.dimo[j] * p.R;
-        for (int64_t e = t; e < n_el; e += 128) dst[e] = p.tab[j][e];
-        tb[j] = dst;
-      } else {
-        tb[j] = p.tab[j];
-      }
+      tb[j] = p.tab_smem ? tabs + p.tab_soff[j] : p.tab[j];
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    const bool tabs_ok = !p.tab_smem || mbar_wait(tab_bar, 0u, p.status);
     for (int i = 0; i < nk; ++i) {
       const int s = i % S;
       const uint32_t ph = (uint32_t)((i / S) & 1);
-      const bool ok = mbar_wait(empty_bar(s), ph ^ 1u, p.status);
+      const bool ok = tabs_ok && mbar_wait(empty_bar(s), ph ^ 1u, p.status);
       if (ok) {
         uint8_t* st = gbase + (size_t)s * stage_bytes;
         uint8_t* bhi = st + 2u * (uint32_t)p.ntm * kTileBytes;
@@ -375,9 +391,19 @@ __global__ void split_planes_kernel(const TT* __restrict__ src, int64_t I, int64
   }
 }
 
-__global__ void f32_table_kernel(const double* __restrict__ A, int64_t n, float* __restrict__ out) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    out[k] = (float)A[k];
+// FP32 copy of every factor of u; factor n starts at float offset off32[n]
+// (multiples of 4, so each factor is 16-byte aligned for bulk copies).
+struct F32Off {
+  int64_t off[CP_MAX_N];
+};
+
+__global__ void u_to_f32_kernel(Layout L, const double* __restrict__ u, F32Off o, float* __restrict__ out) {
+  const int64_t P = L.off[L.N];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
+    int n = 0;
+    while (n + 1 < L.N && e >= L.off[n + 1]) ++n;
+    out[o.off[n] + (e - L.off[n])] = (float)u[e];
+  }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -501,7 +527,24 @@ cp_status prepare_mixed(cp_ctx* ctx, cp_tensor* t) {
   return CP_OK;
 }
 
-cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, int mode, double* out) {
+// FP32 copy of the factors of u (one launch for all modes).
+static cp_status factors_f32(cp_ctx* ctx, const Layout& L, const double* u, float** buf, F32Off* o) {
+  int64_t acc = 0;
+  for (int n = 0; n < L.N; ++n) {
+    o->off[n] = acc;
+    acc += (L.dims[n] * L.R + 3) / 4 * 4;
+  }
+  CP_TRY(ws_alloc(ctx, (void**)buf, sizeof(float) * (size_t)acc + 64));
+  const int64_t P = L.P();
+  u_to_f32_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 8 * ctx->num_sms)), 256, 0,
+                    ctx->stream>>>(L, u, *o, *buf);
+  CP_LAUNCH_CHECK();
+  return CP_OK;
+}
+
+// One mode's MTTKRP from FP32 factors (u32 at offsets o).
+static cp_status mttkrp_tc_core(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o,
+                                int mode, double* out) {
   CP_TRY(ensure_planes(ctx, t, mode));
   const MixedMode& mm = tc_state(t)->mode[mode];
   const int R = L.R;
@@ -517,12 +560,21 @@ cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const d
   p.ntm = (int)std::min<int64_t>(mtiles, kMaxTilesPerCta);
   const int mgroups = (int)((mtiles + kMaxTilesPerCta - 1) / kMaxTilesPerCta);
   const uint32_t stage_bytes = (uint32_t)p.ntm * 2u * kTileBytes + 2u * (uint32_t)RP * 128u;
-  // FP32 tables of the other modes' factors (in shared memory when they fit)
-  size_t tab_elems = 0;
-  for (int m = 0; m < t->N; ++m)
-    if (m != mode) tab_elems += (size_t)t->dims[m] * R;
+  // factor tables of the other modes: bulk-copied to shared memory when they fit
+  size_t tab_bytes = 0;
+  p.nother = 0;
+  for (int m = 0; m < t->N; ++m) {
+    if (m == mode) continue;
+    const uint32_t cpy = (uint32_t)(((size_t)t->dims[m] * R * sizeof(float) + 15) / 16 * 16);
+    p.tab[p.nother] = u32 + o.off[m];
+    p.dimo[p.nother] = t->dims[m];
+    p.tab_soff[p.nother] = (uint32_t)(tab_bytes / sizeof(float));
+    p.tab_cpy[p.nother] = cpy;
+    tab_bytes += cpy;
+    ++p.nother;
+  }
+  p.tab_bytes = (uint32_t)tab_bytes;
   const size_t fixed = 1024 + 256 + 64;          // alignment slack, barriers, TMEM slot
-  const size_t tab_bytes = sizeof(float) * tab_elems;
   p.tab_smem = (tab_bytes <= 96 * 1024 &&
                 (size_t)kMaxDynSmem >= fixed + tab_bytes + 2 * (size_t)stage_bytes) ? 1 : 0;
   const size_t avail = (size_t)kMaxDynSmem - fixed - (p.tab_smem ? tab_bytes : 0);
@@ -538,24 +590,8 @@ cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const d
   const int64_t target = std::max<int64_t>(1, ctx->num_sms / mgroups);
   p.ktiles_per_cta = (p.ktiles + target - 1) / target;
   const int gx = (int)((p.ktiles + p.ktiles_per_cta - 1) / p.ktiles_per_cta);
-  float* tabs = nullptr;
   float* partial = nullptr;
-  CP_TRY(ws_alloc(ctx, (void**)&tabs, tab_bytes + 64));
   CP_TRY(ws_alloc(ctx, (void**)&partial, sizeof(float) * (size_t)gx * I * R));
-  size_t off = 0;
-  p.nother = 0;
-  for (int m = 0; m < t->N; ++m) {
-    if (m == mode) continue;
-    const int64_t n_el = t->dims[m] * R;
-    f32_table_kernel<<<(unsigned)std::min<int64_t>((n_el + 255) / 256, 4 * ctx->num_sms), 256, 0, ctx->stream>>>(
-        u + L.off[m], n_el, tabs + off);
-    CP_LAUNCH_CHECK();
-    p.tab[p.nother] = tabs + off;
-    p.dimo[p.nother] = t->dims[m];
-    p.tab_soff[p.nother] = (uint32_t)off;
-    ++p.nother;
-    off += (size_t)n_el;
-  }
   p.partial = partial;
   p.status = ctx->d_status;
   const size_t smem = (size_t)p.stages * stage_bytes + fixed + (p.tab_smem ? tab_bytes : 0);
@@ -564,7 +600,26 @@ cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const d
   CP_LAUNCH_CHECK();
   CP_TRY(reduce_parts<float>(ctx, partial, gx, I * R, out));
   ws_free(ctx, partial);
-  ws_free(ctx, tabs);
+  return CP_OK;
+}
+
+cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, int mode, double* out) {
+  float* u32 = nullptr;
+  F32Off o;
+  CP_TRY(factors_f32(ctx, L, u, &u32, &o));
+  CP_TRY(mttkrp_tc_core(ctx, t, L, u32, o, mode, out));
+  ws_free(ctx, u32);
+  return CP_OK;
+}
+
+// Modes first..N-1 into M_all (packed like u), one FP32 conversion of u.
+cp_status mttkrp_dense_mixed_modes(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, int first,
+                                   double* M_all) {
+  float* u32 = nullptr;
+  F32Off o;
+  CP_TRY(factors_f32(ctx, L, u, &u32, &o));
+  for (int n = first; n < L.N; ++n) CP_TRY(mttkrp_tc_core(ctx, t, L, u32, o, n, M_all + L.off[n]));
+  ws_free(ctx, u32);
   return CP_OK;
 }
 
