@@ -419,7 +419,7 @@ cp_status axpy_scalar(cp_ctx* ctx, int64_t n, const double* x0, const double* d,
   return CP_OK;
 }
 
-cp_status sub(cp_ctx* ctx, int64_t n, const double* a, const double* b, double* out) {
+cp_status sub_vec(cp_ctx* ctx, int64_t n, const double* a, const double* b, double* out) {
   sub_kernel<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(n, a, b, out);
   CP_LAUNCH_CHECK();
   return CP_OK;

@@ -27,13 +27,23 @@ cp_status cuda_fail(cudaError_t e, const char* what, const char* file, int line)
 
 cp_status ws_alloc(cp_ctx* ctx, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  if (ctx->arena_on) {
+    const size_t off = (ctx->arena_off + 255) & ~(size_t)255;
+    if (!ctx->arena_measure && off + bytes > ctx->arena_cap) {
+      set_error("workspace arena too small (%zu + %zu > %zu)", off, bytes, ctx->arena_cap);
+      return CP_ERR_OOM;
+    }
+    *p = (ctx->arena_measure ? (char*)(uintptr_t)4096 : ctx->arena_base) + off;
+    ctx->arena_off = off + bytes;
+    return CP_OK;
+  }
   cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(workspace)", __FILE__, __LINE__);
   return CP_OK;
 }
 
 void ws_free(cp_ctx* ctx, void* p) {
-  if (p) cudaFreeAsync(p, ctx->stream);
+  if (p && !ctx->arena_on) cudaFreeAsync(p, ctx->stream);
 }
 
 cp_status read_status(cp_ctx* ctx) {

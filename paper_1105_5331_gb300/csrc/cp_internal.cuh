@@ -95,8 +95,17 @@ struct cp_ctx {
   bool own_stream = false;
   int num_sms = 0;
   int* d_status = nullptr;          // device status word
-  double* h_pinned = nullptr;       // small pinned host scratch (64 doubles)
+  double* h_pinned = nullptr;       // small pinned host scratch (1024 doubles)
   int* h_pinned_i = nullptr;        // small pinned host scratch (64 ints)
+  // Bump arena for workspace while capturing graphs whose bodies may hold
+  // only kernel nodes: ws_alloc hands out arena space, ws_free does nothing.
+  // With arena_measure set, pointers are placeholders and only the peak
+  // offset is recorded.
+  bool arena_on = false;
+  bool arena_measure = false;
+  char* arena_base = nullptr;
+  size_t arena_cap = 0;
+  size_t arena_off = 0;
 };
 
 struct CooMode {
@@ -183,7 +192,7 @@ cp_status dot(cp_ctx* ctx, int64_t n, const double* x, const double* y, double* 
 // Device scalar helpers.
 cp_status axpy_scalar(cp_ctx* ctx, int64_t n, const double* x0, const double* d,
                       const double* stp, double* x);  // x = x0 + (*stp) d
-cp_status sub(cp_ctx* ctx, int64_t n, const double* a, const double* b, double* out);  // a - b
+cp_status sub_vec(cp_ctx* ctx, int64_t n, const double* a, const double* b, double* out);  // a - b
 
 // Full cp_fg with workspace.
 cp_status fg_eval(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, double* f,

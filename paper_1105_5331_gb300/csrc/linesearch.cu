@@ -147,7 +147,21 @@ __global__ void mt_start_kernel(MTState* st, const double* f0, const double* g0,
 }
 
 // Consume phi(stp), phi'(stp); decide termination or the next trial.
+__device__ void mt_advance(MTState* st, const double* fval, const double* gval);
+
 __global__ void mt_iterate_kernel(MTState* st, const double* fval, const double* gval) {
+  mt_advance(st, fval, gval);
+}
+
+// The same step inside a graph: the enclosing WHILE node repeats the
+// evaluation while the search is not done.
+__global__ void mt_iterate_cond_kernel(MTState* st, const double* fval, const double* gval,
+                                       cudaGraphConditionalHandle h) {
+  mt_advance(st, fval, gval);
+  cudaGraphSetConditional(h, st->done ? 0u : 1u);
+}
+
+__device__ void mt_advance(MTState* st, const double* fval, const double* gval) {
   MTState s = *st;
   if (s.done) return;
   const double f = *fval, g = *gval;
@@ -218,6 +232,13 @@ cp_status mt_start(cp_ctx* ctx, MTState* st, const double* f0, const double* g0,
 
 cp_status mt_iterate(cp_ctx* ctx, MTState* st, const double* f, const double* g) {
   mt_iterate_kernel<<<1, 1, 0, ctx->stream>>>(st, f, g);
+  CP_LAUNCH_CHECK();
+  return CP_OK;
+}
+
+cp_status mt_iterate_cond(cp_ctx* ctx, MTState* st, const double* f, const double* g,
+                          cudaGraphConditionalHandle h) {
+  mt_iterate_cond_kernel<<<1, 1, 0, ctx->stream>>>(st, f, g, h);
   CP_LAUNCH_CHECK();
   return CP_OK;
 }

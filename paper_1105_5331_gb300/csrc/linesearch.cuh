@@ -20,6 +20,8 @@ struct MTState {
 cp_status mt_start(cp_ctx* ctx, MTState* st, const double* f0, const double* g0,
                    const cp_ls_opts& o);
 cp_status mt_iterate(cp_ctx* ctx, MTState* st, const double* f, const double* g);
+cp_status mt_iterate_cond(cp_ctx* ctx, MTState* st, const double* f, const double* g,
+                          cudaGraphConditionalHandle h);
 cp_status run_linesearch(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* x0,
                          const double* f0, const double* slope, const double* d,
                          const cp_ls_opts& o, double* x, double* fx, double* gx, double* gd,

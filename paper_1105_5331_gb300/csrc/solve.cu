@@ -3,30 +3,37 @@
 // and window size w (Section 2.1), the restart rule of Section 2.1 and the
 // delta I regularisation with eps = 1e-12 (Section 2.4).
 //
-// All state (iterates, gradients, the window ring and its indices, the line
-// search) lives on the device.  Each stretch of work between two host
-// decisions is captured once as a CUDA graph and replayed:
-//   head     Step I (ALS sweep, normalise), f and g at ubar, Step II (window
-//            dots, normal equations, uhat, normalise), d = uhat - ubar,
-//            slope = g(ubar)^T d, line-search start
-//   ls_eval  x = ubar + stp d, f and g at x, phi'(stp) = g(x)^T d, one
-//            More-Thuente update
-//   accept   u = normalise(x) with the gradient rescaled, push to the window
-//   reject   u = ubar (line search without sufficient decrease), push
-//   restart  u = ubar, window reset to {(ubar, g(ubar))}
-// The host reads a few pinned scalars after each replay (the slope, the line
-// search's done flag, ||g||) to choose the next graph.
+// The whole iteration runs on the device.  Each precision phase of a solve is
+// ONE CUDA graph built from conditional nodes:
 //
-// Mixed precision: iterations run with bf16x3 MTTKRPs until ||g||/P drops
-// below tol * mixed_tol_factor (or stops improving for 50 iterations); then
-// the window is reset and FP64 iterations continue until the FP64 gradient
-// meets tol (the polish).
+//   start   f, g at u; window <- {(u, g(u))}; ||g||; set `outer`
+//   WHILE outer:
+//     head      Step I (ALS sweep, normalise), f and g at ubar, Step II
+//               (window dots, normal equations, uhat, normalise),
+//               d = uhat - ubar, slope = g(ubar)^T d, line-search start;
+//               set `restart` = (slope >= 0)
+//     IF restart:  u = ubar, window <- {(ubar, g(ubar))}
+//     ELSE:        WHILE ls:  x = ubar + stp d, f and g at x, phi'(stp),
+//                             one More-Thuente update, set `ls` = !done
+//                  set `accept`;  IF accept: u = normalise(x) (g rescaled)
+//                                 ELSE: u = ubar;   push (u, g) to the window
+//     tail      ||g||, counters, stopping test; set `outer`
+//
+// The host launches one graph per phase and reads a small control block at
+// its end.  Workspace inside the graph comes from a bump arena (sized by a
+// first, measuring capture), so every conditional body holds kernel nodes only.
+//
+// Mixed precision: the bf16x3 phase stops at ||g||/P < tol * mixed_tol_factor
+// or after 50 iterations without a new best ||g||; then the FP64 phase (the
+// polish) restarts the window from the FP64 gradient and runs to tol.
 #include <chrono>
 #include <cmath>
 #include <functional>
+#include <vector>
 
 #include "cp_internal.cuh"
 #include "linesearch.cuh"
+#include "solver.cuh"
 
 namespace cpg {
 
@@ -43,270 +50,501 @@ cp_status als_sweep_inplace(cp_ctx* ctx, const cp_tensor* t, const Layout& L, do
 
 namespace {
 
-struct Graph {
-  cudaGraphExec_t exec = nullptr;
-  unsigned long long kernels = 0;
-  ~Graph() {
-    if (exec) cudaGraphExecDestroy(exec);
-  }
-};
-
-cp_status capture(cp_ctx* ctx, const std::function<cp_status()>& body, Graph& out) {
-  const unsigned long long before = g_launches.load();
-  cudaGraph_t graph = nullptr;
-  CP_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-  const cp_status st = body();
-  const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
-  const unsigned long long n = g_launches.load() - before;
-  g_launches.fetch_sub(n);   // captured, not launched
-  if (st != CP_OK) {
-    if (graph) cudaGraphDestroy(graph);
-    return st;
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
-  const cudaError_t ei = cudaGraphInstantiate(&out.exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate", __FILE__, __LINE__);
-  out.kernels = n;
-  return CP_OK;
-}
-
-cp_status replay(cp_ctx* ctx, const Graph& g) {
-  CP_CUDA(cudaGraphLaunch(g.exec, ctx->stream));
-  g_launches.fetch_add(g.kernels);
-  return CP_OK;
-}
-
-struct Mem {
-  double *u, *g, *ubar, *gbar, *uhat, *d, *x, *gx, *work, *M, *grams, *scal, *U, *G;
-  int* win;
-  MTState* st;
-  void* base = nullptr;
-};
-
-// Scalars (device scal[] and its pinned mirror).
 enum { F = 0, FBAR = 1, FX = 2, SLOPE = 3, GD = 4, GG = 5, NSCAL = 8 };
+enum { STOP_RUN = 0, STOP_TOL = 1, STOP_MAXIT = 2, STOP_STALL = 3, STOP_NONFINITE = 4 };
 
-struct PrecGraphs {
-  Graph head, ls_eval, accept, reject, restart;
-  bool ready = false;
-};
+__global__ void copy_kernel(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    b[k] = a[k];
+}
+
+// Stopping test on ||g||/P (shared by the phase start and the loop tail).
+__device__ void ctl_eval(SolveCtl* c, const double* scal, double P, double tol, int maxit, int mixed,
+                         int stall, cudaGraphConditionalHandle outer) {
+  const double gn = sqrt(scal[GG]) / P;
+  c->gn = gn;
+  c->f = scal[F];
+  int stop = STOP_RUN;
+  if (!isfinite(gn))
+    stop = STOP_NONFINITE;
+  else if (gn < tol)
+    stop = STOP_TOL;
+  else if (c->iters >= maxit)
+    stop = STOP_MAXIT;
+  else if (mixed) {
+    if (gn < c->best) {
+      c->best = gn;
+      c->since_best = 0;
+    } else if (++c->since_best >= stall) {
+      stop = STOP_STALL;
+    }
+  }
+  c->stop = stop;
+  cudaGraphSetConditional(outer, stop == STOP_RUN ? 1u : 0u);
+}
+
+__global__ void ctl_begin_kernel(SolveCtl* c, const double* scal, double P, double tol, int maxit, int mixed,
+                                 int stall, cudaGraphConditionalHandle outer) {
+  c->best = INFINITY;
+  c->since_best = 0;
+  c->fg_evals += 1;
+  ctl_eval(c, scal, P, tol, maxit, mixed, stall, outer);
+}
+
+__global__ void ctl_tail_kernel(SolveCtl* c, const double* scal, double P, double tol, int maxit, int mixed,
+                                int stall, cudaGraphConditionalHandle outer) {
+  c->iters += 1;
+  if (mixed)
+    c->mixed_iters += 1;
+  else
+    c->fp64_iters += 1;
+  ctl_eval(c, scal, P, tol, maxit, mixed, stall, outer);
+}
+
+__global__ void ctl_after_head_kernel(SolveCtl* c, const double* scal, cudaGraphConditionalHandle restart) {
+  c->als_sweeps += 1;
+  c->fg_evals += 1;
+  const bool r = !(scal[SLOPE] < 0.0);
+  if (r) c->restarts += 1;
+  cudaGraphSetConditional(restart, r ? 1u : 0u);
+}
+
+__global__ void ctl_ls_begin_kernel(const MTState* st, cudaGraphConditionalHandle ls) {
+  cudaGraphSetConditional(ls, st->done ? 0u : 1u);
+}
+
+__global__ void ctl_after_ls_kernel(SolveCtl* c, const MTState* st, cudaGraphConditionalHandle accept) {
+  c->fg_evals += st->nfev;
+  if (st->info != 1) c->ls_failures += 1;
+  const bool a = st->nfev > 0 && (st->info == 1 || st->f <= st->f0 + st->ftol * st->stp_eval * st->g0);
+  c->ls_evals += st->nfev;
+  if (a) c->accepts += 1;
+  cudaGraphSetConditional(accept, a ? 1u : 0u);
+}
+
+int64_t grid_for(cp_ctx* ctx, int64_t n) {
+  const int64_t b = std::min<int64_t>((n + 255) / 256, 8 * (int64_t)ctx->num_sms);
+  return std::max<int64_t>(b, 1);
+}
+
+cp_status dcopy(cp_ctx* ctx, int64_t n, const double* a, double* b) {
+  copy_kernel<<<(unsigned)grid_for(ctx, n), 256, 0, ctx->stream>>>(n, a, b);
+  CP_LAUNCH_CHECK();
+  return CP_OK;
+}
+
+// Append a conditional node after the capture frontier of `s`; body i is
+// captured on stream `bs` by fill(i).  The graph that owns the node is the
+// one `s` is capturing into.
+cp_status add_conditional(cudaStream_t s, cudaStream_t bs, cudaGraphConditionalHandle h,
+                          cudaGraphConditionalNodeType type, unsigned size,
+                          const std::function<cp_status(int)>& fill) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CP_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams prm{};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h;
+  prm.conditional.type = type;
+  prm.conditional.size = size;
+  cudaGraphNode_t node;
+  CP_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &prm));
+  for (unsigned i = 0; i < size; ++i) {
+    CP_CUDA(cudaStreamBeginCaptureToGraph(bs, prm.conditional.phGraph_out[i], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed));
+    const cp_status st = fill((int)i);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(bs, &out);
+    CP_TRY(st);
+    CP_CUDA(e);
+  }
+  CP_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return CP_OK;
+}
+
+cp_status new_handle(cudaStream_t s, unsigned dflt, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  CP_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  CP_CUDA(cudaGraphConditionalHandleCreate(h, g, dflt, cudaGraphCondAssignDefault));
+  return CP_OK;
+}
 
 }  // namespace
 
-cp_status solve_impl(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts* o, double* u_user,
-                     bool user_on_device, cp_solve_report* rep) {
-  const auto t0 = std::chrono::steady_clock::now();
-  cp_tensor* t = const_cast<cp_tensor*>(t_in);
-  Layout L;
-  L.set(t->N, t->dims, o->R);
-  const int64_t P = L.P();
+Solver::~Solver() { release(); }
+
+void Solver::release() {
+  for (auto& e : exec)
+    if (e) {
+      cudaGraphExecDestroy(e);
+      e = nullptr;
+    }
+  if (sub.stream) cudaStreamSynchronize(sub.stream);
+  if (base) cudaFree(base);
+  base = nullptr;
+  if (arena) cudaFree(arena);
+  arena = nullptr;
+  for (auto& s : side)
+    if (s) {
+      cudaStreamDestroy(s);
+      s = nullptr;
+    }
+  if (done_ev) cudaEventDestroy(done_ev);
+  done_ev = nullptr;
+  if (sub.stream && own_stream) cudaStreamDestroy(sub.stream);
+  sub.stream = nullptr;
+  if (sub.d_status) cudaFree(sub.d_status);
+  sub.d_status = nullptr;
+  if (sub.h_pinned) cudaFreeHost(sub.h_pinned);
+  sub.h_pinned = nullptr;
+  if (sub.h_pinned_i) cudaFreeHost(sub.h_pinned_i);
+  sub.h_pinned_i = nullptr;
+  if (hctl) cudaFreeHost(hctl);
+  hctl = nullptr;
+}
+
+cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts& opts) {
+  t = const_cast<cp_tensor*>(t_in);
+  o = opts;
+  L.set(t->N, t->dims, o.R);
+  P = L.P();
+  sub = cp_ctx();
+  sub.device = ctx->device;
+  sub.num_sms = ctx->num_sms;
+  CP_CUDA(cudaStreamCreateWithFlags(&sub.stream, cudaStreamNonBlocking));
+  own_stream = true;
+  for (auto& s : side) CP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  CP_CUDA(cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming));
+  CP_CUDA(cudaMalloc(&sub.d_status, sizeof(int)));
+  CP_CUDA(cudaMemsetAsync(sub.d_status, 0, sizeof(int), sub.stream));
+  CP_CUDA(cudaMallocHost(&sub.h_pinned, sizeof(double) * 64));
+  CP_CUDA(cudaMallocHost(&sub.h_pinned_i, sizeof(int) * 64));
+  CP_CUDA(cudaMallocHost(&hctl, sizeof(SolveCtl)));
+  *hctl = SolveCtl{};
   int64_t Imax = 1;
   for (int n = 0; n < L.N; ++n) Imax = std::max(Imax, L.dims[n]);
-  const size_t RR = (size_t)o->R * o->R;
-  const int cap = o->w;
+  const size_t RR = (size_t)o.R * o.R;
+  const int cap = o.w;
+  const size_t bytes = sizeof(double) * (9 * (size_t)P + 2 * (size_t)cap * P + (size_t)Imax * o.R +
+                                         (size_t)L.N * RR + 16) +
+                       sizeof(MTState) + sizeof(SolveCtl) + 512;
+  CP_CUDA(cudaMalloc(&base, bytes));
+  double* p = (double*)base;
+  m.u = p; p += P;
+  m.g = p; p += P;
+  m.ubar = p; p += P;
+  m.gbar = p; p += P;
+  m.uhat = p; p += P;
+  m.d = p; p += P;
+  m.x = p; p += P;
+  m.gx = p; p += P;
+  m.work = p; p += P;
+  m.U = p; p += (size_t)cap * P;
+  m.G = p; p += (size_t)cap * P;
+  m.M = p; p += (size_t)Imax * o.R;
+  m.grams = p; p += (size_t)L.N * RR;
+  m.scal = p; p += 16;
+  m.win = (int*)p; p += 8;
+  uintptr_t q = ((uintptr_t)p + 63) & ~(uintptr_t)63;
+  m.st = (MTState*)q;
+  q = (q + sizeof(MTState) + 63) & ~(uintptr_t)63;
+  m.ctl = (SolveCtl*)q;
+  CP_CUDA(cudaMemsetAsync(m.ctl, 0, sizeof(SolveCtl), sub.stream));
+  if (o.prec != CP_FP64) CP_TRY(prepare_mixed(&sub, t));
+  return CP_OK;
+}
 
-  // The solve runs on a private capturable stream ordered after the
-  // context stream's earlier work.
-  cudaStream_t user_stream = ctx->stream;
-  cudaStream_t ss = nullptr;
-  cudaEvent_t ev = nullptr;
-  CP_CUDA(cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking));
-  CP_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-  CP_CUDA(cudaEventRecord(ev, user_stream));
-  CP_CUDA(cudaStreamWaitEvent(ss, ev, 0));
-  ctx->stream = ss;
-
-  Mem s;
-  double* h = ctx->h_pinned;                       // NSCAL doubles
-  MTState* hst = (MTState*)(ctx->h_pinned + 16);   // line-search state mirror
-  cp_solve_report r{};
-  r.normT2 = t->norm2;
-  cp_precision prec = o->prec;
-  bool polish_pending = (o->prec != CP_FP64) && o->polish;
-  const double tol_mixed = o->tol * (o->mixed_tol_factor > 0 ? o->mixed_tol_factor : 1.0);
-  constexpr int kMixedStall = 50;   // mixed iterations without a new best ||g|| before FP64
-  double best_mixed = INFINITY;
-  int since_best = 0;
-  PrecGraphs graphs[2];
-
-  auto body = [&]() -> cp_status {
-    const size_t bytes = sizeof(double) * (9 * (size_t)P + 2 * (size_t)cap * P + (size_t)Imax * o->R +
-                                           (size_t)L.N * RR + 16) +
-                         sizeof(MTState) + 256 + 64;
-    CP_CUDA(cudaMallocAsync(&s.base, bytes, ctx->stream));
-    double* p = (double*)s.base;
-    s.u = p; p += P;
-    s.g = p; p += P;
-    s.ubar = p; p += P;
-    s.gbar = p; p += P;
-    s.uhat = p; p += P;
-    s.d = p; p += P;
-    s.x = p; p += P;
-    s.gx = p; p += P;
-    s.work = p; p += P;
-    s.U = p; p += (size_t)cap * P;
-    s.G = p; p += (size_t)cap * P;
-    s.M = p; p += (size_t)Imax * o->R;
-    s.grams = p; p += (size_t)L.N * RR;
-    s.scal = p; p += 16;
-    s.win = (int*)p; p += 8;
-    s.st = (MTState*)(((uintptr_t)p + 63) & ~(uintptr_t)63);
-    if (o->prec != CP_FP64) CP_TRY(prepare_mixed(ctx, t));
-
-    auto to_host = [&]() -> cp_status {
-      CP_CUDA(cudaMemcpyAsync(h, s.scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, ctx->stream));
-      return CP_OK;
-    };
-    auto st_to_host = [&]() -> cp_status {
-      CP_CUDA(cudaMemcpyAsync(hst, s.st, sizeof(MTState), cudaMemcpyDeviceToHost, ctx->stream));
-      return CP_OK;
-    };
-    auto sync = [&]() -> cp_status {
-      CP_CUDA(cudaStreamSynchronize(ctx->stream));
-      return CP_OK;
-    };
-    auto build = [&](cp_precision pr) -> cp_status {
-      PrecGraphs& G = graphs[pr == CP_FP64 ? 0 : 1];
-      if (G.ready) return CP_OK;
-      CP_TRY(capture(ctx, [&]() -> cp_status {
-        CP_CUDA(cudaMemcpyAsync(s.work, s.u, sizeof(double) * P, cudaMemcpyDeviceToDevice, ctx->stream));
-        CP_TRY(grams_all(ctx, L, s.work, s.grams));
-        CP_TRY(als_sweep_inplace(ctx, t, L, s.work, s.grams, s.M, pr));
-        CP_TRY(normalize_into(ctx, L, s.work, s.ubar, nullptr, nullptr, nullptr));
-        CP_TRY(fg_eval(ctx, t, L, s.ubar, s.scal + FBAR, s.gbar, pr));
-        CP_TRY(ngmres_core(ctx, P, s.win, cap, s.U, s.G, s.ubar, s.gbar, o->eps, s.work, nullptr));
-        CP_TRY(normalize_into(ctx, L, s.work, s.uhat, nullptr, nullptr, nullptr));
-        CP_TRY(sub(ctx, P, s.uhat, s.ubar, s.d));
-        CP_TRY(dot(ctx, P, s.gbar, s.d, s.scal + SLOPE));
-        cp_ls_opts lso = o->ls;
-        if (pr != CP_FP64 && o->mixed_maxfev > 0 && o->mixed_maxfev < lso.maxfev) lso.maxfev = o->mixed_maxfev;
-        CP_TRY(mt_start(ctx, s.st, s.scal + FBAR, s.scal + SLOPE, lso));
-        CP_TRY(to_host());
-        return st_to_host();
-      }, G.head));
-      CP_TRY(capture(ctx, [&]() -> cp_status {
-        CP_TRY(axpy_scalar(ctx, P, s.ubar, s.d, &s.st->stp, s.x));
-        CP_TRY(fg_eval(ctx, t, L, s.x, s.scal + FX, s.gx, pr));
-        CP_TRY(dot(ctx, P, s.gx, s.d, s.scal + GD));
-        CP_TRY(mt_iterate(ctx, s.st, s.scal + FX, s.scal + GD));
-        return st_to_host();
-      }, G.ls_eval));
-      CP_TRY(capture(ctx, [&]() -> cp_status {
-        CP_TRY(normalize_into(ctx, L, s.x, s.u, s.gx, s.g, nullptr));
-        CP_CUDA(cudaMemcpyAsync(s.scal + F, s.scal + FX, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-        CP_TRY(window_update(ctx, s.win, cap, false, P, s.u, s.g, s.U, s.G));
-        CP_TRY(dot(ctx, P, s.g, s.g, s.scal + GG));
-        return to_host();
-      }, G.accept));
-      for (int reset = 0; reset < 2; ++reset) {
-        CP_TRY(capture(ctx, [&]() -> cp_status {
-          CP_CUDA(cudaMemcpyAsync(s.u, s.ubar, sizeof(double) * P, cudaMemcpyDeviceToDevice, ctx->stream));
-          CP_CUDA(cudaMemcpyAsync(s.g, s.gbar, sizeof(double) * P, cudaMemcpyDeviceToDevice, ctx->stream));
-          CP_CUDA(cudaMemcpyAsync(s.scal + F, s.scal + FBAR, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-          CP_TRY(window_update(ctx, s.win, cap, reset != 0, P, s.u, s.g, s.U, s.G));
-          CP_TRY(dot(ctx, P, s.g, s.g, s.scal + GG));
-          return to_host();
-        }, reset ? G.restart : G.reject));
-      }
-      G.ready = true;
-      return CP_OK;
-    };
-    // start-up: u0 normalised, f and g at u0, window {(u0, g0)}
-    auto start = [&](cp_precision pr, bool from_user) -> cp_status {
-      if (from_user) {
-        CP_CUDA(cudaMemcpyAsync(s.work, u_user, sizeof(double) * P,
-                                user_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
-        CP_TRY(normalize_into(ctx, L, s.work, s.u, nullptr, nullptr, nullptr));
-      }
-      CP_TRY(fg_eval(ctx, t, L, s.u, s.scal + F, s.g, pr));
-      CP_TRY(window_update(ctx, s.win, cap, true, P, s.u, s.g, s.U, s.G));
-      CP_TRY(dot(ctx, P, s.g, s.g, s.scal + GG));
-      CP_TRY(to_host());
-      return sync();
-    };
-
-    CP_TRY(start(prec, true));
-    r.fg_evals++;
-    CP_TRY(build(prec));
-    for (;;) {
-      CP_TRY(read_status(ctx));
-      const double gn = std::sqrt(h[GG]) / (double)P;
-      r.f = h[F];
-      r.gnorm_over_P = gn;
-      if (!std::isfinite(gn)) {
-        set_error("cp_solve: non-finite gradient");
-        return CP_ERR_NONFINITE;
-      }
-      const bool mixed_phase = prec != CP_FP64 && polish_pending;
-      bool stalled = false;
-      if (mixed_phase) {
-        if (gn < best_mixed) {
-          best_mixed = gn;
-          since_best = 0;
-        } else if (++since_best >= kMixedStall) {
-          stalled = true;
-        }
-      }
-      if (mixed_phase && (gn < tol_mixed || stalled)) {
-        // polish: exact FP64 gradient at u, fresh window, FP64 graphs
-        prec = CP_FP64;
-        polish_pending = false;
-        CP_TRY(start(prec, false));
-        r.fg_evals++;
-        CP_TRY(build(prec));
-        continue;
-      }
-      if (gn < o->tol && (prec == CP_FP64 || !o->polish)) {
-        r.converged = 1;
-        break;
-      }
-      if (r.iters >= o->maxit) break;
-      PrecGraphs& G = graphs[prec == CP_FP64 ? 0 : 1];
-      CP_TRY(replay(ctx, G.head));
-      CP_TRY(sync());
-      r.als_sweeps++;
-      r.fg_evals++;
-      if (!(h[SLOPE] < 0.0)) {
-        r.restarts++;
-        CP_TRY(replay(ctx, G.restart));
-        CP_TRY(sync());
-      } else {
-        for (int k = 0; k <= o->ls.maxfev && !hst->done; ++k) {
-          CP_TRY(replay(ctx, G.ls_eval));
-          CP_TRY(sync());
-        }
-        const MTState ms = *hst;
-        r.fg_evals += ms.nfev;
-        if (ms.info != 1) r.ls_failures++;
-        const bool accept = ms.nfev > 0 && (ms.info == 1 || ms.f <= ms.f0 + ms.ftol * ms.stp_eval * ms.g0);
-        CP_TRY(replay(ctx, accept ? G.accept : G.reject));
-        CP_TRY(sync());
-      }
-      r.iters++;
-      if (prec == CP_FP64)
-        r.fp64_iters++;
-      else
-        r.mixed_iters++;
-    }
-    CP_CUDA(cudaMemcpyAsync(u_user, s.u, sizeof(double) * P,
-                            user_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
-    CP_TRY(sync());
-    return read_status(ctx);
+// Capture one phase graph on the solver's stream.  first: the phase starts
+// from the user's (normalised) initial guess.
+cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
+  cp_ctx* ctx = &sub;
+  cudaStream_t s0 = sub.stream;
+  const bool mixed = pr != CP_FP64 && o.polish;
+  const double tol = mixed ? o.tol * (o.mixed_tol_factor > 0 ? o.mixed_tol_factor : 1.0) : o.tol;
+  const int maxit = o.maxit;
+  const int stall = 50;
+  const double Pd = (double)P;
+  const int cap = o.w;
+  cp_ls_opts lso = o.ls;
+  if (pr != CP_FP64 && o.mixed_maxfev > 0 && o.mixed_maxfev < lso.maxfev) lso.maxfev = o.mixed_maxfev;
+  unsigned long long k0 = g_launches.load();
+  kcount = KernelCounts();
+  auto with_stream = [&](cudaStream_t st, const std::function<cp_status()>& f) -> cp_status {
+    cudaStream_t keep = ctx->stream;
+    ctx->stream = st;
+    const cp_status r = f();
+    ctx->stream = keep;
+    return r;
   };
-  cp_status result = body();
-  if (s.base) cudaFreeAsync(s.base, ctx->stream);
-  cudaStreamSynchronize(ctx->stream);
-  ctx->stream = user_stream;
-  cudaEventDestroy(ev);
-  cudaStreamDestroy(ss);
-  r.t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (rep) *rep = r;
-  if (result == CP_OK && !r.converged) {
-    set_error("cp_solve: tol not met after %d iterations (||g||/P = %.3e)", r.iters, r.gnorm_over_P);
+  auto counted = [&](unsigned long long* slot, const std::function<cp_status()>& f) -> cp_status {
+    const unsigned long long a = g_launches.load();
+    const cp_status r = f();
+    *slot += g_launches.load() - a;
+    return r;
+  };
+  CP_CUDA(cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed));
+  cp_status st = [&]() -> cp_status {
+    CP_TRY(counted(&kcount.top, [&]() -> cp_status {
+      if (first) CP_TRY(normalize_into(ctx, L, m.work, m.u, nullptr, nullptr, nullptr));
+      CP_TRY(fg_eval(ctx, t, L, m.u, m.scal + F, m.g, pr));
+      CP_TRY(window_update(ctx, m.win, cap, true, P, m.u, m.g, m.U, m.G));
+      return dot(ctx, P, m.g, m.g, m.scal + GG);
+    }));
+    cudaGraphConditionalHandle h_outer;
+    CP_TRY(new_handle(s0, 0, &h_outer));
+    ctl_begin_kernel<<<1, 1, 0, s0>>>(m.ctl, m.scal, Pd, tol, maxit, mixed ? 1 : 0, stall, h_outer);
+    CP_LAUNCH_CHECK();
+    kcount.top += 1;
+    CP_TRY(add_conditional(s0, side[0], h_outer, cudaGraphCondTypeWhile, 1, [&](int) -> cp_status {
+      return with_stream(side[0], [&]() -> cp_status {
+        CP_TRY(counted(&kcount.head, [&]() -> cp_status {
+          CP_TRY(dcopy(ctx, P, m.u, m.work));
+          CP_TRY(grams_all(ctx, L, m.work, m.grams));
+          CP_TRY(als_sweep_inplace(ctx, t, L, m.work, m.grams, m.M, pr));
+          CP_TRY(normalize_into(ctx, L, m.work, m.ubar, nullptr, nullptr, nullptr));
+          CP_TRY(fg_eval(ctx, t, L, m.ubar, m.scal + FBAR, m.gbar, pr));
+          CP_TRY(ngmres_core(ctx, P, m.win, cap, m.U, m.G, m.ubar, m.gbar, o.eps, m.work, nullptr));
+          CP_TRY(normalize_into(ctx, L, m.work, m.uhat, nullptr, nullptr, nullptr));
+          CP_TRY(sub_vec(ctx, P, m.uhat, m.ubar, m.d));
+          CP_TRY(dot(ctx, P, m.gbar, m.d, m.scal + SLOPE));
+          return mt_start(ctx, m.st, m.scal + FBAR, m.scal + SLOPE, lso);
+        }));
+        cudaGraphConditionalHandle h_restart;
+        CP_TRY(new_handle(side[0], 0, &h_restart));
+        ctl_after_head_kernel<<<1, 1, 0, side[0]>>>(m.ctl, m.scal, h_restart);
+        CP_LAUNCH_CHECK();
+        kcount.head += 1;
+        CP_TRY(add_conditional(side[0], side[1], h_restart, cudaGraphCondTypeIf, 2, [&](int br) -> cp_status {
+          return with_stream(side[1], [&]() -> cp_status {
+            if (br == 0) {
+              // restart: u = ubar, window <- {(ubar, g(ubar))}
+              return counted(&kcount.restart, [&]() -> cp_status {
+                CP_TRY(dcopy(ctx, P, m.ubar, m.u));
+                CP_TRY(dcopy(ctx, P, m.gbar, m.g));
+                CP_TRY(dcopy(ctx, 1, m.scal + FBAR, m.scal + F));
+                return window_update(ctx, m.win, cap, true, P, m.u, m.g, m.U, m.G);
+              });
+            }
+            cudaGraphConditionalHandle h_ls, h_acc;
+            CP_TRY(new_handle(side[1], 0, &h_ls));
+            CP_TRY(new_handle(side[1], 0, &h_acc));
+            ctl_ls_begin_kernel<<<1, 1, 0, side[1]>>>(m.st, h_ls);
+            CP_LAUNCH_CHECK();
+            kcount.ls_fixed += 1;
+            CP_TRY(add_conditional(side[1], side[2], h_ls, cudaGraphCondTypeWhile, 1, [&](int) -> cp_status {
+              return with_stream(side[2], [&]() -> cp_status {
+                return counted(&kcount.ls_eval, [&]() -> cp_status {
+                  CP_TRY(axpy_scalar(ctx, P, m.ubar, m.d, &m.st->stp, m.x));
+                  CP_TRY(fg_eval(ctx, t, L, m.x, m.scal + FX, m.gx, pr));
+                  CP_TRY(dot(ctx, P, m.gx, m.d, m.scal + GD));
+                  return mt_iterate_cond(ctx, m.st, m.scal + FX, m.scal + GD, h_ls);
+                });
+              });
+            }));
+            ctl_after_ls_kernel<<<1, 1, 0, side[1]>>>(m.ctl, m.st, h_acc);
+            CP_LAUNCH_CHECK();
+            kcount.ls_fixed += 1;
+            return add_conditional(side[1], side[2], h_acc, cudaGraphCondTypeIf, 2, [&](int ab) -> cp_status {
+              return with_stream(side[2], [&]() -> cp_status {
+                return counted(ab == 0 ? &kcount.accept : &kcount.reject, [&]() -> cp_status {
+                  if (ab == 0) {
+                    CP_TRY(normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr));
+                    CP_TRY(dcopy(ctx, 1, m.scal + FX, m.scal + F));
+                  } else {
+                    CP_TRY(dcopy(ctx, P, m.ubar, m.u));
+                    CP_TRY(dcopy(ctx, P, m.gbar, m.g));
+                    CP_TRY(dcopy(ctx, 1, m.scal + FBAR, m.scal + F));
+                  }
+                  return window_update(ctx, m.win, cap, false, P, m.u, m.g, m.U, m.G);
+                });
+              });
+            });
+          });
+        }));
+        CP_TRY(counted(&kcount.head, [&]() { return dot(ctx, P, m.g, m.g, m.scal + GG); }));
+        ctl_tail_kernel<<<1, 1, 0, side[0]>>>(m.ctl, m.scal, Pd, tol, maxit, mixed ? 1 : 0, stall, h_outer);
+        CP_LAUNCH_CHECK();
+        kcount.head += 1;
+        return CP_OK;
+      });
+    }));
+    CP_CUDA(cudaMemcpyAsync(hctl, m.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s0));
+    return CP_OK;
+  }();
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s0, &g);
+  g_launches.fetch_sub(g_launches.load() - k0);   // captured, not launched
+  if (st != CP_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  CP_CUDA(e);
+  *out = g;
+  return CP_OK;
+}
+
+cp_status Solver::build_phase(cp_precision pr, bool first) {
+  const int slot = pr == CP_FP64 ? 0 : 1;
+  if (exec[slot] && !first) return CP_OK;
+  if (exec[slot]) {
+    cudaGraphExecDestroy(exec[slot]);
+    exec[slot] = nullptr;
+  }
+  // measuring capture: size of the workspace arena
+  sub.arena_on = true;
+  sub.arena_measure = true;
+  sub.arena_off = 0;
+  cudaGraph_t g = nullptr;
+  cp_status st = capture_phase(pr, first, &g);
+  if (g) cudaGraphDestroy(g);
+  const size_t need = sub.arena_off + 4096;
+  sub.arena_measure = false;
+  if (st != CP_OK) {
+    sub.arena_on = false;
+    return st;
+  }
+  if (need > sub.arena_cap) {
+    if (arena) cudaFree(arena);
+    arena = nullptr;
+    cudaError_t e = cudaMalloc(&arena, need);
+    if (e != cudaSuccess) {
+      sub.arena_on = false;
+      return cuda_fail(e, "cudaMalloc(arena)", __FILE__, __LINE__);
+    }
+    sub.arena_base = (char*)arena;
+    sub.arena_cap = need;
+  }
+  sub.arena_off = 0;
+  g = nullptr;
+  st = capture_phase(pr, first, &g);
+  sub.arena_on = false;
+  if (st != CP_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&exec[slot], g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate", __FILE__, __LINE__);
+  phase_counts[slot] = kcount;
+  return CP_OK;
+}
+
+cp_status Solver::launch_phase(cp_precision pr, bool first) {
+  CP_TRY(build_phase(pr, first));
+  cur = pr;
+  const int slot = pr == CP_FP64 ? 0 : 1;
+  ctl_before = *hctl;   // counters before this phase (for the launch count)
+  CP_CUDA(cudaGraphLaunch(exec[slot], sub.stream));
+  CP_CUDA(cudaEventRecord(done_ev, sub.stream));
+  return CP_OK;
+}
+
+void Solver::account_phase() {
+  const KernelCounts& k = phase_counts[cur == CP_FP64 ? 0 : 1];
+  const SolveCtl& a = ctl_before;
+  const SolveCtl& b = *hctl;
+  const unsigned long long iters = (unsigned long long)(b.iters - a.iters);
+  const unsigned long long restarts = (unsigned long long)(b.restarts - a.restarts);
+  const unsigned long long lsrch = iters - restarts;
+  const unsigned long long evals = (unsigned long long)(b.ls_evals - a.ls_evals);
+  const unsigned long long acc = (unsigned long long)(b.accepts - a.accepts);
+  g_launches.fetch_add(k.top + iters * k.head + restarts * k.restart + lsrch * k.ls_fixed + evals * k.ls_eval +
+                       acc * k.accept + (lsrch - acc) * k.reject);
+}
+
+cp_status Solver::start(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts& opts, const double* u0,
+                        bool u0_on_device) {
+  t0 = std::chrono::steady_clock::now();
+  CP_TRY(setup(ctx, t_in, opts));
+  CP_CUDA(cudaMemcpyAsync(m.work, u0, sizeof(double) * P,
+                          u0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, sub.stream));
+  polish_pending = (o.prec != CP_FP64) && o.polish;
+  phase = 1;
+  return launch_phase(o.prec, true);
+}
+
+// Non-blocking: advance when the running phase has finished.  Returns true
+// when the solve is complete (result holds the status).
+bool Solver::poll(bool block) {
+  if (finished) return true;
+  cudaError_t q = block ? cudaEventSynchronize(done_ev) : cudaEventQuery(done_ev);
+  if (q == cudaErrorNotReady) return false;
+  auto finish = [&](cp_status s) {
+    result = s;
+    finished = true;
+    rep_fill();
+    return true;
+  };
+  if (q != cudaSuccess) return finish(cuda_fail(q, "solve phase", __FILE__, __LINE__));
+  account_phase();
+  {
+    const cp_status s = read_status(&sub);
+    if (s != CP_OK) return finish(s);
+  }
+  const SolveCtl& c = *hctl;
+  if (c.stop == STOP_NONFINITE) {
+    set_error("cp_solve: non-finite gradient");
+    return finish(CP_ERR_NONFINITE);
+  }
+  if (cur != CP_FP64 && polish_pending && (c.stop == STOP_TOL || c.stop == STOP_STALL)) {
+    polish_pending = false;
+    phase = 2;
+    const cp_status s = launch_phase(CP_FP64, false);
+    if (s != CP_OK) return finish(s);
+    return false;
+  }
+  converged = c.stop == STOP_TOL;
+  return finish(CP_OK);
+}
+
+void Solver::rep_fill() {
+  const SolveCtl& c = *hctl;
+  rep = cp_solve_report{};
+  rep.iters = c.iters;
+  rep.fg_evals = c.fg_evals;
+  rep.als_sweeps = c.als_sweeps;
+  rep.restarts = c.restarts;
+  rep.ls_failures = c.ls_failures;
+  rep.converged = converged ? 1 : 0;
+  rep.mixed_iters = c.mixed_iters;
+  rep.fp64_iters = c.fp64_iters;
+  rep.f = c.f;
+  rep.gnorm_over_P = c.gn;
+  rep.normT2 = t ? t->norm2 : 0.0;
+  rep.t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+cp_status Solver::copy_out(double* u_user, bool on_device) {
+  CP_CUDA(cudaMemcpyAsync(u_user, m.u, sizeof(double) * P, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          sub.stream));
+  CP_CUDA(cudaStreamSynchronize(sub.stream));
+  return CP_OK;
+}
+
+cp_status solve_impl(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* o, double* u_user, bool user_on_device,
+                     cp_solve_report* rep) {
+  // order after the caller's earlier work on the context stream
+  CP_CUDA(cudaStreamSynchronize(ctx->stream));
+  Solver s;
+  cp_status st = s.start(ctx, t, *o, u_user, user_on_device);
+  if (st == CP_OK) {
+    while (!s.poll(true)) {
+    }
+    st = s.result;
+  }
+  if (st == CP_OK) st = s.copy_out(u_user, user_on_device);
+  if (s.finished || st != CP_OK) {
+    s.rep_fill();
+    if (rep) *rep = s.rep;
+  }
+  if (st == CP_OK && !s.converged) {
+    set_error("cp_solve: tol not met after %d iterations (||g||/P = %.3e)", s.rep.iters, s.rep.gnorm_over_P);
     return CP_ERR_MAXIT;
   }
-  return result;
+  return st;
 }
 
 }  // namespace cpg

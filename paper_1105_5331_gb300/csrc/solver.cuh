@@ -1,0 +1,72 @@
+// Device-resident N-GMRES solve (one CUDA graph per precision phase); used
+// synchronously by cp_solve and concurrently by the request server.
+#pragma once
+
+#include <chrono>
+
+#include "cp_internal.cuh"
+#include "linesearch.cuh"
+
+namespace cpg {
+
+// Control block written by the graph's control kernels.
+struct SolveCtl {
+  int iters, fg_evals, als_sweeps, restarts, ls_failures;
+  int mixed_iters, fp64_iters;
+  int ls_evals, accepts;
+  int stop;          // 0 running, 1 tol met, 2 maxit, 3 mixed phase stalled, 4 non-finite
+  int since_best;
+  double gn, best, f;
+};
+
+// Kernels per graph stretch (captured once), to count replayed launches.
+struct KernelCounts {
+  unsigned long long top = 0, head = 0, restart = 0, ls_fixed = 0, ls_eval = 0, accept = 0, reject = 0;
+};
+
+struct SolverMem {
+  double *u, *g, *ubar, *gbar, *uhat, *d, *x, *gx, *work, *M, *grams, *scal, *U, *G;
+  int* win;
+  MTState* st;
+  SolveCtl* ctl;
+};
+
+struct Solver {
+  cp_ctx sub;                       // device, own stream, status word, pinned scratch, arena
+  bool own_stream = false;
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // capture streams of nested bodies
+  cudaEvent_t done_ev = nullptr;
+  cp_tensor* t = nullptr;
+  cp_solve_opts o{};
+  Layout L;
+  int64_t P = 0;
+  void* base = nullptr;
+  void* arena = nullptr;
+  SolverMem m{};
+  SolveCtl* hctl = nullptr;         // pinned mirror, written at the end of each phase
+  SolveCtl ctl_before{};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};   // [0] FP64, [1] mixed
+  KernelCounts kcount, phase_counts[2];
+  cp_precision cur = CP_FP64;
+  bool polish_pending = false;
+  int phase = 0;
+  bool finished = false;
+  bool converged = false;
+  cp_status result = CP_OK;
+  cp_solve_report rep{};
+  std::chrono::steady_clock::time_point t0;
+
+  ~Solver();
+  void release();
+  cp_status setup(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts& opts);
+  cp_status capture_phase(cp_precision pr, bool first, cudaGraph_t* out);
+  cp_status build_phase(cp_precision pr, bool first);
+  cp_status launch_phase(cp_precision pr, bool first);
+  void account_phase();
+  cp_status start(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts& opts, const double* u0, bool on_device);
+  bool poll(bool block);
+  void rep_fill();
+  cp_status copy_out(double* u_user, bool on_device);
+};
+
+}  // namespace cpg

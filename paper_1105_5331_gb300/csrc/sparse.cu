@@ -310,6 +310,11 @@ __global__ void __launch_bounds__(256) mttkrp_coo_kernel(const int32_t* __restri
   }
 }
 
+__global__ void zero_kernel(double* __restrict__ x, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    x[k] = 0.0;
+}
+
 // M[seg_row[s], :] = sum of the partials of the units of segment s.
 __global__ void coo_finalize_kernel(const int64_t* __restrict__ seg_unit, int64_t nseg,
                                     const int32_t* __restrict__ seg_row, const double* __restrict__ partial,
@@ -516,7 +521,9 @@ cp_status mttkrp_sparse(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const 
   const int R = L.R;
   const int N = t->N;
   const CooMode& md = t->modes[mode];
-  CP_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)t->dims[mode] * R, ctx->stream));
+  // rows without nonzeros are zero (a kernel, so that graph bodies hold kernel nodes only)
+  zero_kernel<<<blocks_for(ctx, t->dims[mode] * R), 256, 0, ctx->stream>>>(out, t->dims[mode] * R);
+  CP_LAUNCH_CHECK();
   if (t->nnz == 0) return CP_OK;
   const bool f32 = prec != CP_FP64;
   const size_t esz = f32 ? sizeof(float) : sizeof(double);
