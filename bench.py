@@ -51,6 +51,11 @@ def parse():
     p.add_argument("--mttkrp-only", default=None, choices=["dense_256", "dense_4way"],
                    help="time only cp_mttkrp on that workload (profiling driver)")
     p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--serve-requests", type=int, default=128,
+                   help="requests of the 200/s Poisson serving stream replayed (0: skip)")
+    p.add_argument("--serve-fp64-requests", type=int, default=32,
+                   help="requests solved by the FP64 path in saturation for the mixed-vs-FP64 figure")
+    p.add_argument("--serve-slots", type=int, default=48)
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--cpu-iters", type=int, default=1, help=argparse.SUPPRESS)
     return p.parse_args()
@@ -246,6 +251,8 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the public API with host buffers
     e2e = e2e_run(cp, ctx, prob, u0, prec, min(args.steps, 3), T_host)
 
+    serving = serving_run(cp, ctx, args) if rank == 0 else None
+
     clocks = clk.summary()
     lat = sorted(times)
     res = {
@@ -263,6 +270,7 @@ def run_ours(args, rank, world, local_rank):
                   "mixed_iters": reps[-1]["mixed_iters"], "fp64_iters": reps[-1]["fp64_iters"],
                   "gnorm_over_P": reps[-1]["gnorm_over_P"], "f": reps[-1]["f"]},
         "vs_fp64_path": other_obj,
+        "serving": serving,
         "roofline": roof,
         "e2e": e2e,
         "clocks": clocks,
@@ -312,6 +320,57 @@ def mttkrp_roofline(cp, ctx, t, u, stream, flush, prec):
             "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
             "per_launch": {"bytes": bytes_, "avg_ms": d * 1e3},
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+
+
+def serving_run(cp, ctx, args):
+    """The serving stream (dense 3-way requests, sides U{16..192}, R U{2..32},
+    collinearity {0.5, 0.9}, 1-10 % noise, tol {1e-5, 1e-7}, Poisson arrivals
+    at 200/s): the first `serve_requests` requests replayed open-loop through
+    the request server (p50/p99 time to tolerance), then the same requests all
+    submitted at t=0 (saturation solves/s), mixed and FP64."""
+    import numpy as np
+    import synth
+    n = args.serve_requests
+    if n <= 0:
+        return None
+    reqs = synth.request_stream(n, rate_per_s=200.0, config=5)
+    probs = [synth.request_problem(r, config=5) for r in reqs]   # generated before timing
+
+    def opts(r, prec):
+        o = cp.cp_solve_opts_default(r.R)
+        o.tol = r.tol
+        o.prec = prec
+        return o
+
+    def run(prec, count, open_loop):
+        srv = cp.cp_server_create(ctx, 64 << 30, args.serve_slots)
+        outs = [np.zeros_like(u0) for _, u0 in probs[:count]]
+        t0 = time.perf_counter()
+        ids = []
+        for r, (prob, u0), out in zip(reqs[:count], probs[:count], outs):
+            if open_loop:
+                delay = r.arrival_s - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            ids.append(cp.cp_server_submit(srv, prob.T, opts(r, prec), u0, out))
+        cp.cp_server_drain(srv, 1800.0)
+        wall = time.perf_counter() - t0
+        st = cp.cp_server_stats(srv)
+        conv = sum(1 for i in ids if cp.cp_server_poll(srv, i)[1]["converged"])
+        srv.close()
+        return {"requests": count, "converged": conv, "wall_s": wall, "p50_ms": st["p50_s"] * 1e3,
+                "p99_ms": st["p99_s"] * 1e3, "solves_per_s": count / wall,
+                "peak_admitted_bytes": st["peak_bytes"]}
+
+    res = {"stream": "Poisson 200/s, sides U{16..192}, R U{2..32}, c {0.5,0.9}, noise U(1%,10%), tol {1e-5,1e-7}",
+           "slots": args.serve_slots}
+    res["open_loop_mixed"] = run(cp.CP_MIXED_BF16X3, n, True)
+    res["saturation_mixed"] = run(cp.CP_MIXED_BF16X3, n, False)
+    if args.serve_fp64_requests > 0:
+        m = min(n, args.serve_fp64_requests)
+        res["saturation_fp64"] = run(cp.CP_FP64, m, False)
+        res["saturation_mixed_same_requests"] = run(cp.CP_MIXED_BF16X3, m, False)
+    return res
 
 
 def e2e_run(cp, ctx, prob, u0, prec, n, T_host):

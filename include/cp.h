@@ -246,6 +246,57 @@ void cp_solve_opts_default(cp_solve_opts* o, int R);
 cp_status cp_solve(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* opts, double* u,
                    cp_solve_report* rep);
 
+/* ------------------------------------------------- batching and serving */
+
+/* Solve nreq independent problems at once (host-side batching of
+ * Algorithm 1): every problem runs its own device-resident solve on its own
+ * stream, so their iterations overlap on the GPU.  tensors[i], opts[i], u[i]
+ * (host or device, in: initial guess, out: solution) as for cp_solve; reps
+ * (may be NULL) receives nreq reports.  Returns the first failing status
+ * (CP_ERR_MAXIT if a problem did not meet its tol).  Synchronous. */
+cp_status cp_solve_batch(cp_ctx* ctx, int nreq, const cp_tensor* const* tensors,
+                         const cp_solve_opts* opts, double* const* u, cp_solve_report* reps);
+
+/* Request server (continuous batching).  Requests (dense tensors, each with
+ * its own shape, rank, tolerance and precision) wait in arrival order and are
+ * admitted while one of `max_active` slots is free and the sum of the device
+ * footprints of the running requests stays within hbm_budget_bytes.  Each
+ * admitted request keeps its tensor, factors, N-GMRES window and line-search
+ * state on the device and runs on its own stream; requests that arrive while
+ * others run are admitted as slots and memory free up.  A worker thread inside
+ * the server admits, polls and retires requests. */
+typedef struct cp_server cp_server;
+
+cp_status cp_server_create(cp_ctx* ctx, size_t hbm_budget_bytes, int max_active, cp_server** out);
+
+/* Submit a dense request: data (host, row-major, prod(dims) elements of
+ * dtype) and u0 (host, P doubles) are copied at submission; the solution is
+ * written to the host array u_out (P doubles), which must stay valid until
+ * the request is done.  CP_ERR_BUSY if the request alone exceeds the budget. */
+cp_status cp_server_submit(cp_server* s, int N, const int64_t* dims, cp_dtype dtype, const void* data,
+                           const cp_solve_opts* opts, const double* u0, double* u_out,
+                           uint64_t* req_id);
+
+/* done: 1 once the request finished (or was cancelled); then req_status,
+ * rep and latency_s (submission to completion) are filled (each may be NULL). */
+cp_status cp_server_poll(cp_server* s, uint64_t req_id, int* done, cp_status* req_status,
+                         cp_solve_report* rep, double* latency_s);
+
+/* Cancel a request that is still waiting (CP_ERR_ARG otherwise). */
+cp_status cp_server_cancel(cp_server* s, uint64_t req_id);
+
+/* Wait until no request is waiting or running; CP_ERR_TIMEOUT after timeout_s. */
+cp_status cp_server_drain(cp_server* s, double timeout_s);
+
+/* p50/p99 latency (nearest rank) of finished requests, finished requests per
+ * second since the first submission, number finished, peak admitted footprint.
+ * Any output may be NULL. */
+cp_status cp_server_stats(cp_server* s, double* p50_s, double* p99_s, double* solves_per_s, int* completed,
+                          size_t* peak_bytes);
+
+/* Stop the worker after the running requests finish; free everything. */
+void cp_server_destroy(cp_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,6 +34,8 @@ EXPORTED = [
     "cp_tensor_destroy", "cp_mttkrp", "cp_mttkrp_noalloc", "cp_fg", "cp_als_sweep", "cp_normalize",
     "ngmres_step",
     "cp_ls_opts_default", "linesearch", "cp_solve_opts_default", "cp_solve",
+    "cp_solve_batch", "cp_server_create", "cp_server_submit", "cp_server_poll", "cp_server_cancel",
+    "cp_server_drain", "cp_server_stats", "cp_server_destroy",
 ]
 
 
@@ -97,6 +99,17 @@ def _load():
                            C.POINTER(D), C.POINTER(I), C.POINTER(I), I]),
         "cp_solve_opts_default": (None, [C.POINTER(cp_solve_opts), I]),
         "cp_solve": (I, [VP, VP, C.POINTER(cp_solve_opts), VP, C.POINTER(cp_solve_report)]),
+        "cp_solve_batch": (I, [VP, I, C.POINTER(VP), C.POINTER(cp_solve_opts), C.POINTER(VP),
+                               C.POINTER(cp_solve_report)]),
+        "cp_server_create": (I, [VP, C.c_size_t, I, C.POINTER(VP)]),
+        "cp_server_submit": (I, [VP, I, P, I, VP, C.POINTER(cp_solve_opts), VP, VP, C.POINTER(C.c_uint64)]),
+        "cp_server_poll": (I, [VP, C.c_uint64, C.POINTER(I), C.POINTER(I), C.POINTER(cp_solve_report),
+                               C.POINTER(D)]),
+        "cp_server_cancel": (I, [VP, C.c_uint64]),
+        "cp_server_drain": (I, [VP, D]),
+        "cp_server_stats": (I, [VP, C.POINTER(D), C.POINTER(D), C.POINTER(D), C.POINTER(I),
+                                C.POINTER(C.c_size_t)]),
+        "cp_server_destroy": (None, [VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -328,3 +341,82 @@ def cp_solve(ctx, t, opts: cp_solve_opts, u) -> dict:
     rep = cp_solve_report()
     _check(_lib.cp_solve(_h(ctx), _h(t), C.byref(opts), _ptr(u), C.byref(rep)), allow=(8,))
     return rep.as_dict()
+
+
+def cp_solve_batch(ctx, tensors, opts_list, us) -> list:
+    """Solve several problems at once (each on its own stream); returns the
+    reports.  A problem that stops at maxit is not an exception."""
+    n = len(tensors)
+    th = (C.c_void_p * n)(*[_h(t) for t in tensors])
+    op = (cp_solve_opts * n)(*opts_list)
+    up = (C.c_void_p * n)(*[_ptr(u) for u in us])
+    reps = (cp_solve_report * n)()
+    _check(_lib.cp_solve_batch(_h(ctx), n, th, op, up, reps), allow=(8,))
+    return [r.as_dict() for r in reps]
+
+
+class Server:
+    """Owning wrapper of a cp_server*."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            _lib.cp_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cp_server_create(ctx, hbm_budget_bytes: int, max_active: int) -> Server:
+    out = C.c_void_p()
+    _check(_lib.cp_server_create(_h(ctx), int(hbm_budget_bytes), int(max_active), C.byref(out)))
+    return Server(out.value)
+
+
+def cp_server_submit(server, data, opts: cp_solve_opts, u0, u_out) -> int:
+    """data: host numpy array (float32/float64); u0, u_out: host float64 arrays."""
+    dims = tuple(data.shape)
+    dtype = CP_DTYPE_F64 if "float64" in str(data.dtype) else CP_DTYPE_F32
+    rid = C.c_uint64()
+    _check(_lib.cp_server_submit(_h(server), len(dims), _dims(dims), dtype, _ptr(data), C.byref(opts),
+                                 _ptr(u0), _ptr(u_out), C.byref(rid)))
+    return rid.value
+
+
+def cp_server_poll(server, req_id: int):
+    """Returns None while running, else (status, report dict, latency_s)."""
+    done = C.c_int()
+    st = C.c_int()
+    rep = cp_solve_report()
+    lat = C.c_double()
+    _check(_lib.cp_server_poll(_h(server), int(req_id), C.byref(done), C.byref(st), C.byref(rep), C.byref(lat)))
+    if not done.value:
+        return None
+    return st.value, rep.as_dict(), lat.value
+
+
+def cp_server_cancel(server, req_id: int):
+    _check(_lib.cp_server_cancel(_h(server), int(req_id)))
+
+
+def cp_server_drain(server, timeout_s: float = 600.0):
+    _check(_lib.cp_server_drain(_h(server), float(timeout_s)))
+
+
+def cp_server_stats(server) -> dict:
+    p50, p99, sps = C.c_double(), C.c_double(), C.c_double()
+    n = C.c_int()
+    peak = C.c_size_t()
+    _check(_lib.cp_server_stats(_h(server), C.byref(p50), C.byref(p99), C.byref(sps), C.byref(n), C.byref(peak)))
+    return {"p50_s": p50.value, "p99_s": p99.value, "solves_per_s": sps.value, "completed": n.value,
+            "peak_bytes": peak.value}
+
+
+def cp_server_destroy(server):
+    server.close() if hasattr(server, "close") else _lib.cp_server_destroy(server)

@@ -68,9 +68,19 @@ cp_status als_sweep_inplace(cp_ctx* ctx, const cp_tensor* t, const Layout& L, do
                             double* grams, double* M, cp_precision prec);
 cp_status grams_all(cp_ctx* ctx, const Layout& L, const double* u, double* grams);
 void tensor_free_coo(cp_tensor* t);
-void tensor_free_mixed(cp_tensor* t);
+void tensor_free_mixed(cp_tensor* t, cudaStream_t s);
 
-static bool on_device(const void* p) {
+// Free every buffer of t in stream order on `s` (no device-wide sync) and
+// delete the handle.  The caller guarantees no queued work still uses t.
+void tensor_release(cp_tensor* t, cudaStream_t s) {
+  for (int n = 0; n < CP_MAX_N; ++n)
+    if (t->Tn[n]) cudaFreeAsync(t->Tn[n], s);
+  tensor_free_mixed(t, s);
+  tensor_free_coo(t);
+  delete t;
+}
+
+bool on_device(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -206,20 +216,17 @@ cp_status cp_tensor_dense(cp_ctx* ctx, int N, const int64_t* dims, cp_dtype dtyp
   void* tmp = nullptr;
   cp_status st = CP_OK;
   if (!on_device(data)) {
-    cudaError_t e = cudaMalloc(&tmp, bytes);
+    cudaError_t e = cudaMallocAsync(&tmp, bytes, ctx->stream);
     if (e != cudaSuccess) {
       cp_tensor_destroy(t);
-      return cuda_fail(e, "cudaMalloc(upload)", __FILE__, __LINE__);
+      return cuda_fail(e, "cudaMallocAsync(upload)", __FILE__, __LINE__);
     }
     e = cudaMemcpyAsync(tmp, data, bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) st = cuda_fail(e, "upload", __FILE__, __LINE__);
     src = tmp;
   }
   if (st == CP_OK) st = dense_build(ctx, t, src);
-  if (tmp) {
-    cudaStreamSynchronize(ctx->stream);
-    cudaFree(tmp);
-  }
+  if (tmp) cudaFreeAsync(tmp, ctx->stream);
   if (st != CP_OK) {
     cp_tensor_destroy(t);
     return st;
@@ -338,12 +345,8 @@ void cp_tensor_destroy(cp_tensor* t) {
   cudaGetDevice(&cur);
   if (cur != t->device) cudaSetDevice(t->device);
   cudaDeviceSynchronize();
-  for (int n = 0; n < CP_MAX_N; ++n) {
-    if (t->Tn[n]) cudaFree(t->Tn[n]);
-  }
-  tensor_free_mixed(t);
-  tensor_free_coo(t);
-  delete t;
+  cpg::tensor_release(t, cudaStreamLegacy);
+  cudaStreamSynchronize(cudaStreamLegacy);
 }
 
 static cp_status check_tensor_R(const cp_tensor* t, int R) {

@@ -186,6 +186,10 @@ cp_status window_update(cp_ctx* ctx, int* win, int cap, bool reset, int64_t P, c
                         const double* g, double* U, double* G);
 // Create the bf16 planes of every mode before graph capture.
 cp_status prepare_mixed(cp_ctx* ctx, cp_tensor* t);
+// Free every buffer of t in stream order on s and delete the handle.
+void tensor_release(cp_tensor* t, cudaStream_t s);
+bool on_device(const void* p);
+cp_status dense_build(cp_ctx* ctx, cp_tensor* t, const void* d_data);
 
 // Deterministic FP64 dot product: out = x . y (device scalar).
 cp_status dot(cp_ctx* ctx, int64_t n, const double* x, const double* y, double* out);

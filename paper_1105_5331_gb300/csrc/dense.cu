@@ -159,7 +159,7 @@ cp_status sumsq(cp_ctx* ctx, const void* x, cp_dtype dt, int64_t n, double* d_ou
 cp_status dense_build(cp_ctx* ctx, cp_tensor* t, const void* d_data) {
   const size_t esz = t->dtype == CP_DTYPE_F64 ? 8 : 4;
   for (int n = 0; n < t->N; ++n) {
-    CP_CUDA(cudaMalloc(&t->Tn[n], esz * (size_t)t->K));
+    CP_CUDA(cudaMallocAsync(&t->Tn[n], esz * (size_t)t->K, ctx->stream));
     int64_t L = 1, Q = 1;
     for (int m = 0; m < n; ++m) L *= t->dims[m];
     for (int m = n + 1; m < t->N; ++m) Q *= t->dims[m];

@@ -438,10 +438,10 @@ static TcState* tc_state(cp_tensor* t) {
   return reinterpret_cast<TcState*>(t->tc_state);
 }
 
-void tensor_free_mixed(cp_tensor* t) {
+void tensor_free_mixed(cp_tensor* t, cudaStream_t s) {
   for (int n = 0; n < CP_MAX_N; ++n) {
-    if (t->Thi[n]) cudaFree(t->Thi[n]);
-    if (t->Tlo[n]) cudaFree(t->Tlo[n]);
+    if (t->Thi[n]) cudaFreeAsync(t->Thi[n], s);
+    if (t->Tlo[n]) cudaFreeAsync(t->Tlo[n], s);
     t->Thi[n] = t->Tlo[n] = nullptr;
   }
   delete tc_state(t);
@@ -460,8 +460,8 @@ static cp_status ensure_planes(cp_ctx* ctx, cp_tensor* t, int n) {
               (long long)I, (long long)Kb);
     return CP_ERR_UNSUPPORTED;
   }
-  CP_CUDA(cudaMalloc(&t->Thi[n], sizeof(__nv_bfloat16) * (size_t)(I * pitch)));
-  CP_CUDA(cudaMalloc(&t->Tlo[n], sizeof(__nv_bfloat16) * (size_t)(I * pitch)));
+  CP_CUDA(cudaMallocAsync(&t->Thi[n], sizeof(__nv_bfloat16) * (size_t)(I * pitch), ctx->stream));
+  CP_CUDA(cudaMallocAsync(&t->Tlo[n], sizeof(__nv_bfloat16) * (size_t)(I * pitch), ctx->stream));
   t->pitch[n] = pitch;
   int64_t blocks = std::min<int64_t>((I * pitch + 255) / 256, 16 * (int64_t)ctx->num_sms);
   if (t->dtype == CP_DTYPE_F64)

@@ -1,0 +1,407 @@
+// Continuous batching of CP decompositions on one GPU.
+//
+// A server owns `max_active` slots; each slot has its own streams, event,
+// status word and pinned buffers (SolverRes).  Requests wait in arrival order
+// and are admitted while a slot is free and the sum of the device footprints
+// of running requests plus the new one stays within the HBM budget.  An
+// admitted request uploads its tensor (per-mode copies, bf16 planes) and
+// launches its own device-resident solve (one CUDA graph per precision phase,
+// see solve.cu) on its slot's stream, so the iterations of all running
+// requests overlap on the device.  A worker thread polls the slots without
+// blocking, retires finished requests (result copied to the caller's host
+// buffer, latency stamped) and admits waiting ones as slots and memory free
+// up.  Every allocation on this path is stream-ordered, so admitting or
+// retiring one request never waits for the others.
+//
+// Each request's result depends only on its own data (no cross-request
+// reduction, fixed launch shapes), so it is the same alone and in a mix.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "cp_internal.cuh"
+#include "solver.cuh"
+
+namespace cpg {
+
+cp_status solve_impl(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* o, double* u_user, bool user_on_device,
+                     cp_solve_report* rep);
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double seconds_since(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double>(b - a).count();
+}
+
+enum ReqState { REQ_PENDING = 0, REQ_RUNNING = 1, REQ_DONE = 2, REQ_CANCELLED = 3 };
+
+struct Request {
+  uint64_t id = 0;
+  int N = 0;
+  int64_t dims[CP_MAX_N] = {0};
+  cp_dtype dtype = CP_DTYPE_F32;
+  std::vector<char> data;          // host copy of the tensor
+  std::vector<double> u0;          // host copy of the initial guess
+  double* u_out = nullptr;         // caller's host buffer for the result
+  cp_solve_opts opts{};
+  size_t footprint = 0;
+  Clock::time_point t_submit, t_admit, t_done;
+  int state = REQ_PENDING;
+  cp_status status = CP_OK;
+  cp_solve_report rep{};
+};
+
+struct Slot {
+  SolverRes res;
+  std::unique_ptr<Solver> solver;
+  cp_tensor* t = nullptr;
+  Request* req = nullptr;
+};
+
+}  // namespace
+
+// Device bytes a request needs while it runs (tensor copies, bf16 planes,
+// solver state, graph workspace): an estimate used for admission.
+size_t request_footprint(int N, const int64_t* dims, cp_dtype dtype, const cp_solve_opts& o) {
+  size_t K = 1, sumI = 0, Imax = 1;
+  for (int n = 0; n < N; ++n) {
+    K *= (size_t)dims[n];
+    sumI += (size_t)dims[n];
+    Imax = std::max(Imax, (size_t)dims[n]);
+  }
+  const size_t esz = dtype == CP_DTYPE_F64 ? 8 : 4;
+  const size_t P = sumI * (size_t)o.R;
+  size_t bytes = (size_t)N * K * esz + K * esz;                 // per-mode copies + upload
+  if (o.prec != CP_FP64) bytes += (size_t)N * (K + 8 * Imax) * 4;  // bf16 hi/lo planes
+  bytes += sizeof(double) * ((9 + 2 * (size_t)o.w) * P + Imax * o.R + (size_t)N * o.R * o.R);
+  bytes += sizeof(double) * 12 * P + (size_t)4 * 152 * Imax * o.R * 6 + ((size_t)8 << 20);   // workspace
+  return bytes;
+}
+
+}  // namespace cpg
+
+using namespace cpg;
+
+struct cp_server {
+  cp_ctx* ctx = nullptr;        // caller's context (device)
+  cp_ctx* wctx = nullptr;       // worker's own context (stream for uploads)
+  size_t budget = 0, used = 0, peak = 0;
+  int max_active = 0;
+  std::vector<Slot> slots;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request*> pending;
+  std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+  std::vector<double> latencies;
+  bool any_submit = false;
+  Clock::time_point t_first, t_last;
+  uint64_t next_id = 1;
+  int running = 0, completed = 0;
+  std::atomic<bool> stop{false};
+  std::thread worker;
+  cp_status worker_error = CP_OK;
+
+  void admit(Slot& sl, Request* r) {
+    sl.req = r;
+    r->t_admit = Clock::now();
+    cp_tensor* t = nullptr;
+    cp_status st = cp_tensor_dense(wctx, r->N, r->dims, r->dtype, r->data.data(), &t);
+    if (st == CP_OK) {
+      sl.t = t;
+      // the slot's stream must see the finished upload
+      cudaEvent_t ev;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(ev, wctx->stream);
+        cudaStreamWaitEvent(sl.res.stream, ev, 0);
+        cudaEventDestroy(ev);
+      }
+      sl.solver.reset(new Solver());
+      st = sl.solver->start(ctx, t, r->opts, r->u0.data(), false, &sl.res);
+    }
+    if (st != CP_OK) {
+      if (sl.solver) {
+        sl.solver->finished = true;
+        sl.solver->result = st;
+      }
+      finish(sl, st);
+      return;
+    }
+    r->state = REQ_RUNNING;
+  }
+
+  void finish(Slot& sl, cp_status st) {
+    Request* r = sl.req;
+    if (sl.solver) {
+      if (st == CP_OK) st = sl.solver->result;
+      if (st == CP_OK || st == CP_ERR_MAXIT) {
+        const cp_status c = sl.solver->copy_out(r->u_out, false);
+        if (c != CP_OK) st = c;
+      }
+      sl.solver->rep_fill();
+      r->rep = sl.solver->rep;
+      if (st == CP_OK && !sl.solver->converged) st = CP_ERR_MAXIT;
+      sl.solver.reset();   // stream-ordered frees on the slot stream
+    }
+    if (sl.t) {
+      tensor_release(sl.t, sl.res.stream);
+      sl.t = nullptr;
+    }
+    r->t_done = Clock::now();
+    std::lock_guard<std::mutex> lock(mu);
+    r->status = st;
+    r->state = REQ_DONE;
+    used -= r->footprint;
+    --running;
+    ++completed;
+    latencies.push_back(seconds_since(r->t_submit, r->t_done));
+    t_last = r->t_done;
+    sl.req = nullptr;
+    cv.notify_all();
+  }
+
+  void loop() {
+    cudaSetDevice(ctx->device);
+    while (!stop.load()) {
+      bool progress = false;
+      for (auto& sl : slots) {
+        if (sl.req && sl.solver && sl.solver->poll(false)) {
+          finish(sl, CP_OK);
+          progress = true;
+        }
+      }
+      for (auto& sl : slots) {
+        if (sl.req) continue;
+        Request* r = nullptr;
+        {
+          std::lock_guard<std::mutex> lock(mu);
+          while (!pending.empty() && pending.front()->state == REQ_CANCELLED) pending.pop_front();
+          if (!pending.empty() && used + pending.front()->footprint <= budget) {
+            r = pending.front();
+            pending.pop_front();
+            used += r->footprint;
+            peak = std::max(peak, used);
+            ++running;
+          }
+        }
+        if (!r) break;
+        admit(sl, r);
+        progress = true;
+      }
+      if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
+};
+
+extern "C" {
+
+cp_status cp_server_create(cp_ctx* ctx, size_t hbm_budget_bytes, int max_active, cp_server** out) {
+  if (!ctx || !out || max_active < 1 || max_active > 1024 || hbm_budget_bytes == 0) {
+    set_error("cp_server_create: bad arguments");
+    return CP_ERR_ARG;
+  }
+  *out = nullptr;
+  CP_CUDA(cudaSetDevice(ctx->device));
+  std::unique_ptr<cp_server> s(new cp_server());
+  s->ctx = ctx;
+  s->budget = hbm_budget_bytes;
+  s->max_active = max_active;
+  CP_TRY(cp_ctx_create(ctx->device, nullptr, &s->wctx));
+  s->slots.resize((size_t)max_active);
+  for (auto& sl : s->slots) CP_TRY(sl.res.create());
+  cp_server* raw = s.release();
+  raw->worker = std::thread([raw]() { raw->loop(); });
+  *out = raw;
+  return CP_OK;
+}
+
+cp_status cp_server_submit(cp_server* s, int N, const int64_t* dims, cp_dtype dtype, const void* data,
+                           const cp_solve_opts* opts, const double* u0, double* u_out, uint64_t* req_id) {
+  if (!s || !dims || !data || !opts || !u0 || !u_out || !req_id || N < 2 || N > CP_MAX_N) {
+    set_error("cp_server_submit: bad arguments");
+    return CP_ERR_ARG;
+  }
+  if (opts->R < 1 || opts->R > CP_MAX_R || opts->w < 1 || opts->w > CP_MAX_W || !(opts->tol > 0)) {
+    set_error("cp_server_submit: bad options");
+    return CP_ERR_ARG;
+  }
+  std::unique_ptr<Request> r(new Request());
+  size_t K = 1, sumI = 0;
+  for (int n = 0; n < N; ++n) {
+    if (dims[n] < 1) {
+      set_error("cp_server_submit: dim %d < 1", n);
+      return CP_ERR_SHAPE;
+    }
+    r->dims[n] = dims[n];
+    K *= (size_t)dims[n];
+    sumI += (size_t)dims[n];
+  }
+  r->N = N;
+  r->dtype = dtype;
+  r->opts = *opts;
+  const size_t esz = dtype == CP_DTYPE_F64 ? 8 : 4;
+  r->data.assign((const char*)data, (const char*)data + K * esz);
+  r->u0.assign(u0, u0 + sumI * (size_t)opts->R);
+  r->u_out = u_out;
+  r->footprint = request_footprint(N, dims, dtype, *opts);
+  if (r->footprint > s->budget) {
+    set_error("cp_server_submit: request needs ~%zu bytes, budget %zu", r->footprint, s->budget);
+    return CP_ERR_BUSY;
+  }
+  r->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (!s->any_submit) {
+    s->any_submit = true;
+    s->t_first = r->t_submit;
+  }
+  r->id = s->next_id++;
+  *req_id = r->id;
+  s->pending.push_back(r.get());
+  s->reqs[r->id] = std::move(r);
+  return CP_OK;
+}
+
+cp_status cp_server_poll(cp_server* s, uint64_t req_id, int* done, cp_status* req_status, cp_solve_report* rep,
+                         double* latency_s) {
+  if (!s || !done) {
+    set_error("cp_server_poll: bad arguments");
+    return CP_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(req_id);
+  if (it == s->reqs.end()) {
+    set_error("cp_server_poll: unknown request %llu", (unsigned long long)req_id);
+    return CP_ERR_ARG;
+  }
+  Request* r = it->second.get();
+  *done = (r->state == REQ_DONE || r->state == REQ_CANCELLED) ? 1 : 0;
+  if (*done) {
+    if (req_status) *req_status = r->status;
+    if (rep) *rep = r->rep;
+    if (latency_s) *latency_s = r->state == REQ_DONE ? seconds_since(r->t_submit, r->t_done) : 0.0;
+  }
+  return CP_OK;
+}
+
+cp_status cp_server_cancel(cp_server* s, uint64_t req_id) {
+  if (!s) return CP_ERR_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(req_id);
+  if (it == s->reqs.end() || it->second->state != REQ_PENDING) {
+    set_error("cp_server_cancel: request %llu is not waiting", (unsigned long long)req_id);
+    return CP_ERR_ARG;
+  }
+  it->second->state = REQ_CANCELLED;
+  it->second->status = CP_ERR_ARG;
+  s->cv.notify_all();
+  return CP_OK;
+}
+
+cp_status cp_server_drain(cp_server* s, double timeout_s) {
+  if (!s) return CP_ERR_ARG;
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto all_done = [&]() {
+    for (auto& kv : s->reqs)
+      if (kv.second->state == REQ_PENDING || kv.second->state == REQ_RUNNING) return false;
+    return true;
+  };
+  if (!s->cv.wait_for(lock, std::chrono::duration<double>(timeout_s), all_done)) {
+    set_error("cp_server_drain: timed out");
+    return CP_ERR_TIMEOUT;
+  }
+  return CP_OK;
+}
+
+cp_status cp_server_stats(cp_server* s, double* p50_s, double* p99_s, double* solves_per_s, int* completed,
+                          size_t* peak_bytes) {
+  if (!s) return CP_ERR_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  std::vector<double> l = s->latencies;
+  std::sort(l.begin(), l.end());
+  auto pct = [&](double q) {
+    if (l.empty()) return 0.0;
+    size_t i = (size_t)std::ceil(q * (double)l.size()) - 1;
+    return l[std::min(i, l.size() - 1)];
+  };
+  if (p50_s) *p50_s = pct(0.50);
+  if (p99_s) *p99_s = pct(0.99);
+  if (solves_per_s) {
+    const double span = s->completed ? seconds_since(s->t_first, s->t_last) : 0.0;
+    *solves_per_s = span > 0 ? (double)s->completed / span : 0.0;
+  }
+  if (completed) *completed = s->completed;
+  if (peak_bytes) *peak_bytes = s->peak;
+  return CP_OK;
+}
+
+void cp_server_destroy(cp_server* s) {
+  if (!s) return;
+  s->stop.store(true);
+  if (s->worker.joinable()) s->worker.join();
+  cudaSetDevice(s->ctx->device);
+  for (auto& sl : s->slots) {
+    if (sl.solver)
+      while (!sl.solver->poll(true)) {
+      }
+    sl.solver.reset();
+    if (sl.t) tensor_release(sl.t, sl.res.stream);
+    sl.t = nullptr;
+    sl.res.destroy();
+  }
+  cp_ctx_destroy(s->wctx);
+  delete s;
+}
+
+cp_status cp_solve_batch(cp_ctx* ctx, int nreq, const cp_tensor* const* tensors, const cp_solve_opts* opts,
+                         double* const* u, cp_solve_report* reps) {
+  if (!ctx || nreq < 0 || (nreq > 0 && (!tensors || !opts || !u))) {
+    set_error("cp_solve_batch: bad arguments");
+    return CP_ERR_ARG;
+  }
+  CP_CUDA(cudaSetDevice(ctx->device));
+  CP_CUDA(cudaStreamSynchronize(ctx->stream));
+  std::vector<std::unique_ptr<Solver>> sv((size_t)nreq);
+  std::vector<bool> dev((size_t)nreq);
+  cp_status first = CP_OK;
+  for (int i = 0; i < nreq; ++i) {
+    if (!tensors[i] || !u[i]) {
+      if (first == CP_OK) first = CP_ERR_ARG;
+      continue;
+    }
+    dev[i] = on_device(u[i]);
+    sv[i].reset(new Solver());
+    const cp_status st = sv[i]->start(ctx, tensors[i], opts[i], u[i], dev[i]);
+    if (st != CP_OK) {
+      sv[i]->finished = true;
+      sv[i]->result = st;
+    }
+  }
+  bool all = false;
+  while (!all) {
+    all = true;
+    for (int i = 0; i < nreq; ++i)
+      if (sv[i] && !sv[i]->finished && !sv[i]->poll(false)) all = false;
+    if (!all) std::this_thread::sleep_for(std::chrono::microseconds(10));
+  }
+  for (int i = 0; i < nreq; ++i) {
+    if (!sv[i]) continue;
+    cp_status st = sv[i]->result;
+    if (st == CP_OK) st = sv[i]->copy_out(u[i], dev[i]);
+    sv[i]->rep_fill();
+    if (reps) reps[i] = sv[i]->rep;
+    if (st == CP_OK && !sv[i]->converged) st = CP_ERR_MAXIT;
+    if (st != CP_OK && first == CP_OK) first = st;
+  }
+  return first;
+}
+
+}  // extern "C"

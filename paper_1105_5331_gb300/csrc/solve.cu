@@ -174,56 +174,72 @@ cp_status new_handle(cudaStream_t s, unsigned dflt, cudaGraphConditionalHandle* 
 
 }  // namespace
 
+cp_status SolverRes::create() {
+  CP_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+  for (auto& s : side) CP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  CP_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CP_CUDA(cudaMalloc(&d_status, sizeof(int)));
+  CP_CUDA(cudaMemset(d_status, 0, sizeof(int)));
+  CP_CUDA(cudaMallocHost(&h_pinned, sizeof(double) * 64));
+  CP_CUDA(cudaMallocHost(&h_pinned_i, sizeof(int) * 64));
+  CP_CUDA(cudaMallocHost(&hctl, sizeof(SolveCtl)));
+  return CP_OK;
+}
+
+void SolverRes::destroy() {
+  if (stream) cudaStreamSynchronize(stream);
+  for (auto& s : side)
+    if (s) cudaStreamDestroy(s);
+  if (stream) cudaStreamDestroy(stream);
+  if (ev) cudaEventDestroy(ev);
+  if (d_status) cudaFree(d_status);
+  if (h_pinned) cudaFreeHost(h_pinned);
+  if (h_pinned_i) cudaFreeHost(h_pinned_i);
+  if (hctl) cudaFreeHost(hctl);
+  *this = SolverRes();
+}
+
 Solver::~Solver() { release(); }
 
+// Frees in stream order on the solver's stream; no device-wide sync.
 void Solver::release() {
   for (auto& e : exec)
     if (e) {
       cudaGraphExecDestroy(e);
       e = nullptr;
     }
-  if (sub.stream) cudaStreamSynchronize(sub.stream);
-  if (base) cudaFree(base);
+  if (base && sub.stream) cudaFreeAsync(base, sub.stream);
   base = nullptr;
-  if (arena) cudaFree(arena);
+  if (arena && sub.stream) cudaFreeAsync(arena, sub.stream);
   arena = nullptr;
-  for (auto& s : side)
-    if (s) {
-      cudaStreamDestroy(s);
-      s = nullptr;
-    }
-  if (done_ev) cudaEventDestroy(done_ev);
-  done_ev = nullptr;
-  if (sub.stream && own_stream) cudaStreamDestroy(sub.stream);
+  if (res == &own) own.destroy();
+  res = nullptr;
   sub.stream = nullptr;
-  if (sub.d_status) cudaFree(sub.d_status);
-  sub.d_status = nullptr;
-  if (sub.h_pinned) cudaFreeHost(sub.h_pinned);
-  sub.h_pinned = nullptr;
-  if (sub.h_pinned_i) cudaFreeHost(sub.h_pinned_i);
-  sub.h_pinned_i = nullptr;
-  if (hctl) cudaFreeHost(hctl);
-  hctl = nullptr;
 }
 
-cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts& opts) {
+cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts& opts, SolverRes* r) {
   t = const_cast<cp_tensor*>(t_in);
   o = opts;
   L.set(t->N, t->dims, o.R);
   P = L.P();
+  if (r) {
+    res = r;
+  } else {
+    res = &own;
+    CP_TRY(own.create());
+  }
   sub = cp_ctx();
   sub.device = ctx->device;
   sub.num_sms = ctx->num_sms;
-  CP_CUDA(cudaStreamCreateWithFlags(&sub.stream, cudaStreamNonBlocking));
-  own_stream = true;
-  for (auto& s : side) CP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-  CP_CUDA(cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming));
-  CP_CUDA(cudaMalloc(&sub.d_status, sizeof(int)));
-  CP_CUDA(cudaMemsetAsync(sub.d_status, 0, sizeof(int), sub.stream));
-  CP_CUDA(cudaMallocHost(&sub.h_pinned, sizeof(double) * 64));
-  CP_CUDA(cudaMallocHost(&sub.h_pinned_i, sizeof(int) * 64));
-  CP_CUDA(cudaMallocHost(&hctl, sizeof(SolveCtl)));
+  sub.stream = res->stream;
+  for (int i = 0; i < 3; ++i) side[i] = res->side[i];
+  done_ev = res->ev;
+  sub.d_status = res->d_status;
+  sub.h_pinned = res->h_pinned;
+  sub.h_pinned_i = res->h_pinned_i;
+  hctl = res->hctl;
   *hctl = SolveCtl{};
+  CP_CUDA(cudaMemsetAsync(sub.d_status, 0, sizeof(int), sub.stream));
   int64_t Imax = 1;
   for (int n = 0; n < L.N; ++n) Imax = std::max(Imax, L.dims[n]);
   const size_t RR = (size_t)o.R * o.R;
@@ -231,7 +247,7 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   const size_t bytes = sizeof(double) * (9 * (size_t)P + 2 * (size_t)cap * P + (size_t)Imax * o.R +
                                          (size_t)L.N * RR + 16) +
                        sizeof(MTState) + sizeof(SolveCtl) + 512;
-  CP_CUDA(cudaMalloc(&base, bytes));
+  CP_CUDA(cudaMallocAsync(&base, bytes, sub.stream));
   double* p = (double*)base;
   m.u = p; p += P;
   m.g = p; p += P;
@@ -407,9 +423,9 @@ cp_status Solver::build_phase(cp_precision pr, bool first) {
     return st;
   }
   if (need > sub.arena_cap) {
-    if (arena) cudaFree(arena);
+    if (arena) cudaFreeAsync(arena, sub.stream);
     arena = nullptr;
-    cudaError_t e = cudaMalloc(&arena, need);
+    cudaError_t e = cudaMallocAsync(&arena, need, sub.stream);
     if (e != cudaSuccess) {
       sub.arena_on = false;
       return cuda_fail(e, "cudaMalloc(arena)", __FILE__, __LINE__);
@@ -456,9 +472,9 @@ void Solver::account_phase() {
 }
 
 cp_status Solver::start(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts& opts, const double* u0,
-                        bool u0_on_device) {
+                        bool u0_on_device, SolverRes* r) {
   t0 = std::chrono::steady_clock::now();
-  CP_TRY(setup(ctx, t_in, opts));
+  CP_TRY(setup(ctx, t_in, opts, r));
   CP_CUDA(cudaMemcpyAsync(m.work, u0, sizeof(double) * P,
                           u0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, sub.stream));
   polish_pending = (o.prec != CP_FP64) && o.polish;

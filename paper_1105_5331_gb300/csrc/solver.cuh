@@ -31,10 +31,26 @@ struct SolverMem {
   SolveCtl* ctl;
 };
 
-struct Solver {
-  cp_ctx sub;                       // device, own stream, status word, pinned scratch, arena
-  bool own_stream = false;
+// Streams, event, status word and pinned buffers of one solve; reusable by a
+// server slot so that admitting a request allocates no host-pinned memory
+// and creates no streams.
+struct SolverRes {
+  cudaStream_t stream = nullptr;
   cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // capture streams of nested bodies
+  cudaEvent_t ev = nullptr;
+  int* d_status = nullptr;
+  double* h_pinned = nullptr;
+  int* h_pinned_i = nullptr;
+  SolveCtl* hctl = nullptr;
+  cp_status create();
+  void destroy();
+};
+
+struct Solver {
+  cp_ctx sub;                       // device, the slot's stream, status word, pinned scratch, arena
+  SolverRes own;                    // used when no slot resources are given
+  SolverRes* res = nullptr;
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t done_ev = nullptr;
   cp_tensor* t = nullptr;
   cp_solve_opts o{};
@@ -58,12 +74,13 @@ struct Solver {
 
   ~Solver();
   void release();
-  cp_status setup(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts& opts);
+  cp_status setup(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts& opts, SolverRes* r);
   cp_status capture_phase(cp_precision pr, bool first, cudaGraph_t* out);
   cp_status build_phase(cp_precision pr, bool first);
   cp_status launch_phase(cp_precision pr, bool first);
   void account_phase();
-  cp_status start(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts& opts, const double* u0, bool on_device);
+  cp_status start(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts& opts, const double* u0, bool on_device,
+                  SolverRes* r = nullptr);
   bool poll(bool block);
   void rep_fill();
   cp_status copy_out(double* u_user, bool on_device);
