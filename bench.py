@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mttkrp-only", default=None, choices=["dense_256", "dense_4way"],
+    p.add_argument("--mttkrp-only", default=None, choices=["dense_256", "dense_4way", "sparse"],
                    help="time only cp_mttkrp on that workload (profiling driver)")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--serve-requests", type=int, default=128,
@@ -442,21 +442,28 @@ def run_mttkrp_only(args):
 
     import synth
     import paper_1105_5331_gb300 as cp
+    sparse = args.mttkrp_only == "sparse"
     if args.mttkrp_only == "dense_256":
         prob, u0 = synth.workload_dense_256()
-    else:
+    elif args.mttkrp_only == "dense_4way":
         prob, u0 = synth.workload_dense_4way()
+    else:
+        prob, u0 = synth.workload_sparse()
     Rk = prob.R
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
     ctx = cp.cp_ctx_create(0, stream)
     prec = cp.CP_MIXED_BF16X3 if args.prec == "mixed" else cp.CP_FP64
     with torch.cuda.stream(stream):
-        T = torch.from_numpy(prob.T).to(dev)
         u = torch.from_numpy(u0).to(dev)
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        if sparse:
+            coords = torch.from_numpy(prob.coords).to(dev)
+            vals = torch.from_numpy(prob.vals).to(dev)
+        else:
+            T = torch.from_numpy(prob.T).to(dev)
     stream.synchronize()
-    t = cp.cp_tensor_dense(ctx, T)
+    t = cp.cp_tensor_coo(ctx, prob.dims, coords, vals) if sparse else cp.cp_tensor_dense(ctx, T)
     res = {}
     for n in range(len(prob.dims)):
         out = torch.empty(prob.dims[n] * Rk, dtype=torch.float64, device=dev)
@@ -472,6 +479,13 @@ def run_mttkrp_only(args):
             if k > 0:
                 ms.append(e0.elapsed_time(e1))
         res[f"mode{n}_ms"] = sum(ms) / len(ms)
+        if sparse:
+            nnz = prob.coords.shape[0]
+            sf = 4 if args.prec == "mixed" else 8
+            comp = nnz * (4 + 4 * (len(prob.dims) - 1))          # values + other coordinates
+            access = comp + nnz * (len(prob.dims) - 1) * Rk * sf   # + gathered factor rows
+            res[f"mode{n}_compulsory_GBps"] = comp / (res[f"mode{n}_ms"] / 1e3) / 1e9
+            res[f"mode{n}_access_GBps"] = access / (res[f"mode{n}_ms"] / 1e3) / 1e9
     cp.cp_ctx_sync(ctx)
     print(json.dumps({"mttkrp_only": args.mttkrp_only, "prec": args.prec, **res}))
 
