@@ -435,24 +435,9 @@ cp_status mttkrp_any(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const dou
 
 cp_status fg_eval(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, double* f,
                   double* g, cp_precision prec) {
-  double* M = nullptr;
-  double* grams = nullptr;
-  const size_t RR = (size_t)L.R * L.R;
-  CP_TRY(ws_alloc(ctx, (void**)&M, sizeof(double) * (size_t)L.P()));
-  CP_TRY(ws_alloc(ctx, (void**)&grams, sizeof(double) * L.N * RR));
-  CP_TRY(grams_all(ctx, L, u, grams));
-  // Without g only the last mode's MTTKRP is needed for <T, A_R>.
-  if (t->kind == 0 && prec == CP_MIXED_BF16X3) {
-    // one FP32 copy of the factors serves every mode
-    CP_TRY(mttkrp_dense_mixed_modes(ctx, const_cast<cp_tensor*>(t), L, u, g ? 0 : L.N - 1, M));
-  } else {
-    for (int n = g ? 0 : L.N - 1; n < L.N; ++n)
-      CP_TRY(mttkrp_any(ctx, t, L, u, n, M + L.off[n], prec));
-  }
-  CP_TRY(fg_assemble(ctx, L, u, M, grams, t->norm2, f, g));
-  ws_free(ctx, grams);
-  ws_free(ctx, M);
-  return CP_OK;
+  // prep (Grams, FP32 copy) -> MTTKRP partial sums -> fused finish
+  return fg_eval_ex(ctx, t, L, u, nullptr, nullptr, nullptr, f, g, prec, nullptr, nullptr,
+                    cudaGraphConditionalHandle{}, 0);
 }
 
 }  // namespace cpg

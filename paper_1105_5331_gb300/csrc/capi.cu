@@ -143,6 +143,8 @@ cp_status cp_ctx_create(int device, void* cuda_stream, cp_ctx** out) {
     c->own_stream = true;
   }
   CP_CUDA(cudaMalloc(&c->d_status, sizeof(int)));
+  CP_CUDA(cudaMalloc(&c->d_counter, sizeof(unsigned)));
+  CP_CUDA(cudaMemset(c->d_counter, 0, sizeof(unsigned)));
   CP_CUDA(cudaMemset(c->d_status, 0, sizeof(int)));
   CP_CUDA(cudaMallocHost(&c->h_pinned, sizeof(double) * 1024));
   CP_CUDA(cudaMallocHost(&c->h_pinned_i, sizeof(int) * 64));
@@ -161,6 +163,7 @@ void cp_ctx_destroy(cp_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   cudaFree(c->d_status);
+  cudaFree(c->d_counter);
   cudaFreeHost(c->h_pinned);
   cudaFreeHost(c->h_pinned_i);
   delete c;
@@ -400,8 +403,7 @@ cp_status cp_als_sweep(cp_ctx* ctx, const cp_tensor* t, int R, double* u, int no
   double* M = nullptr;
   CP_TRY(ws_alloc(ctx, (void**)&grams, sizeof(double) * (size_t)t->N * R * R));
   CP_TRY(ws_alloc(ctx, (void**)&M, sizeof(double) * (size_t)Imax * R));
-  CP_TRY(grams_all(ctx, L, u, grams));
-  CP_TRY(als_sweep_inplace(ctx, t, L, u, grams, M, prec));
+  CP_TRY(als_sweep_fused(ctx, t, L, u, prec));
   if (normalize) {
     double* tmp = nullptr;
     CP_TRY(ws_alloc(ctx, (void**)&tmp, sizeof(double) * (size_t)L.P()));

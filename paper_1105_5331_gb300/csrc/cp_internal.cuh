@@ -75,6 +75,20 @@ struct FactorPtrs {
   int R;
 };
 
+// Split-K partial sums of one mode's MTTKRP: M[e] = sum_{c < count} p[c * n + e]
+// (n = I_mode * R), FP32 or FP64.
+struct Parts {
+  const void* p = nullptr;
+  int count = 0;
+  int f32 = 0;
+};
+
+// Offsets (in floats) of the factors inside an FP32 copy of an iterate;
+// multiples of 4 so each factor starts 16-byte aligned.
+struct F32Off {
+  int64_t off[CP_MAX_N];
+};
+
 inline FactorPtrs factor_ptrs(const Layout& L, const double* u) {
   FactorPtrs f;
   f.N = L.N;
@@ -95,6 +109,7 @@ struct cp_ctx {
   bool own_stream = false;
   int num_sms = 0;
   int* d_status = nullptr;          // device status word
+  unsigned* d_counter = nullptr;    // last-block counter of fused kernels (zero between kernels)
   double* h_pinned = nullptr;       // small pinned host scratch (1024 doubles)
   int* h_pinned_i = nullptr;        // small pinned host scratch (64 ints)
   // Bump arena for workspace while capturing graphs whose bodies may hold
@@ -201,6 +216,21 @@ cp_status sub_vec(cp_ctx* ctx, int64_t n, const double* a, const double* b, doub
 // Full cp_fg with workspace.
 cp_status fg_eval(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, double* f,
                   double* g, cp_precision prec);
+// MTTKRP of one mode as split-K partial sums (u32: FP32 copy of u for the
+// tensor-core path, may be null otherwise).
+cp_status mttkrp_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, const float* u32,
+                       const F32Off& o32, int mode, cp_precision prec, Parts* out);
+struct MTState;
+// One ALS sweep in place on u with fused kernels (1 + 2N launches).
+cp_status als_sweep_fused(cp_ctx* ctx, const cp_tensor* t, const Layout& L, double* u,
+                          cp_precision prec);
+// Fused f/g at x = base (+ (*stp) d when d is given; x written).  With d, also
+// g . d into gd; with st, one More-Thuente update (and, with use_h, the graph
+// condition h set to "not done").
+cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* base,
+                     const double* d, const double* stp, double* x, double* f, double* g,
+                     cp_precision prec, double* gd, MTState* st, cudaGraphConditionalHandle h,
+                     int use_h);
 
 // Workspace (stream-ordered).
 cp_status ws_alloc(cp_ctx* ctx, void** p, size_t bytes);

@@ -187,8 +187,22 @@ cp_status dense_build(cp_ctx* ctx, cp_tensor* t, const void* d_data) {
   return CP_OK;
 }
 
+static cp_status mttkrp_f64_impl(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u,
+                                 int mode, double* out, Parts* parts_out);
+
 cp_status mttkrp_dense_f64(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u,
                            int mode, double* out) {
+  return mttkrp_f64_impl(ctx, t, L, u, mode, out, nullptr);
+}
+
+// Split-K partial sums only (grid x I x R doubles), for a fused consumer.
+cp_status mttkrp_f64_parts(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, int mode,
+                           Parts* out) {
+  return mttkrp_f64_impl(ctx, t, L, u, mode, nullptr, out);
+}
+
+static cp_status mttkrp_f64_impl(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u,
+                                 int mode, double* out, Parts* parts_out) {
   const int R = L.R;
   const int64_t I = t->dims[mode];
   const int64_t Kb = kbar(t, mode);
@@ -217,6 +231,10 @@ cp_status mttkrp_dense_f64(cp_ctx* ctx, const cp_tensor* t, const Layout& L, con
     mttkrp_f64_kernel<float><<<grid, threads, smem, ctx->stream>>>(
         (const float*)t->Tn[mode], I, Kb, kr, R, tiles_per_cta, partial);
   CP_LAUNCH_CHECK();
+  if (parts_out) {
+    *parts_out = Parts{partial, grid, 0};
+    return CP_OK;
+  }
   CP_TRY(reduce_partials(ctx, partial, grid, I * R, out));
   ws_free(ctx, partial);
   return CP_OK;

@@ -393,10 +393,6 @@ __global__ void split_planes_kernel(const TT* __restrict__ src, int64_t I, int64
 
 // FP32 copy of every factor of u; factor n starts at float offset off32[n]
 // (multiples of 4, so each factor is 16-byte aligned for bulk copies).
-struct F32Off {
-  int64_t off[CP_MAX_N];
-};
-
 __global__ void u_to_f32_kernel(Layout L, const double* __restrict__ u, F32Off o, float* __restrict__ out) {
   const int64_t P = L.off[L.N];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
@@ -543,8 +539,9 @@ static cp_status factors_f32(cp_ctx* ctx, const Layout& L, const double* u, floa
 }
 
 // One mode's MTTKRP from FP32 factors (u32 at offsets o).
-static cp_status mttkrp_tc_core(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o,
-                                int mode, double* out) {
+// Launch the tensor-core kernel; partial sums (gx x I x R floats) in *parts.
+static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o,
+                                  int mode, Parts* parts) {
   CP_TRY(ensure_planes(ctx, t, mode));
   const MixedMode& mm = tc_state(t)->mode[mode];
   const int R = L.R;
@@ -598,9 +595,22 @@ static cp_status mttkrp_tc_core(cp_ctx* ctx, cp_tensor* t, const Layout& L, cons
   CP_TRY(set_smem_attr());
   tc_kernel_for(p.nother)<<<dim3(gx, mgroups), kThreads, smem, ctx->stream>>>(mm.hi, mm.lo, p);
   CP_LAUNCH_CHECK();
-  CP_TRY(reduce_parts<float>(ctx, partial, gx, I * R, out));
-  ws_free(ctx, partial);
+  *parts = Parts{partial, gx, 1};
   return CP_OK;
+}
+
+static cp_status mttkrp_tc_core(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o,
+                                int mode, double* out) {
+  Parts pt;
+  CP_TRY(mttkrp_tc_launch(ctx, t, L, u32, o, mode, &pt));
+  CP_TRY(reduce_parts<float>(ctx, (const float*)pt.p, pt.count, L.dims[mode] * L.R, out));
+  ws_free(ctx, const_cast<void*>(pt.p));
+  return CP_OK;
+}
+
+cp_status mttkrp_tc_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o, int mode,
+                          Parts* out) {
+  return mttkrp_tc_launch(ctx, t, L, u32, o, mode, out);
 }
 
 cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, int mode, double* out) {

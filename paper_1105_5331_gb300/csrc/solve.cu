@@ -180,6 +180,8 @@ cp_status SolverRes::create() {
   CP_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   CP_CUDA(cudaMalloc(&d_status, sizeof(int)));
   CP_CUDA(cudaMemset(d_status, 0, sizeof(int)));
+  CP_CUDA(cudaMalloc(&d_counter, sizeof(unsigned)));
+  CP_CUDA(cudaMemset(d_counter, 0, sizeof(unsigned)));
   CP_CUDA(cudaMallocHost(&h_pinned, sizeof(double) * 64));
   CP_CUDA(cudaMallocHost(&h_pinned_i, sizeof(int) * 64));
   CP_CUDA(cudaMallocHost(&hctl, sizeof(SolveCtl)));
@@ -193,6 +195,7 @@ void SolverRes::destroy() {
   if (stream) cudaStreamDestroy(stream);
   if (ev) cudaEventDestroy(ev);
   if (d_status) cudaFree(d_status);
+  if (d_counter) cudaFree(d_counter);
   if (h_pinned) cudaFreeHost(h_pinned);
   if (h_pinned_i) cudaFreeHost(h_pinned_i);
   if (hctl) cudaFreeHost(hctl);
@@ -235,6 +238,7 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   for (int i = 0; i < 3; ++i) side[i] = res->side[i];
   done_ev = res->ev;
   sub.d_status = res->d_status;
+  sub.d_counter = res->d_counter;
   sub.h_pinned = res->h_pinned;
   sub.h_pinned_i = res->h_pinned_i;
   hctl = res->hctl;
@@ -318,8 +322,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
       return with_stream(side[0], [&]() -> cp_status {
         CP_TRY(counted(&kcount.head, [&]() -> cp_status {
           CP_TRY(dcopy(ctx, P, m.u, m.work));
-          CP_TRY(grams_all(ctx, L, m.work, m.grams));
-          CP_TRY(als_sweep_inplace(ctx, t, L, m.work, m.grams, m.M, pr));
+          CP_TRY(als_sweep_fused(ctx, t, L, m.work, pr));
           CP_TRY(normalize_into(ctx, L, m.work, m.ubar, nullptr, nullptr, nullptr));
           CP_TRY(fg_eval(ctx, t, L, m.ubar, m.scal + FBAR, m.gbar, pr));
           CP_TRY(ngmres_core(ctx, P, m.win, cap, m.U, m.G, m.ubar, m.gbar, o.eps, m.work, nullptr));
@@ -352,11 +355,11 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
             kcount.ls_fixed += 1;
             CP_TRY(add_conditional(side[1], side[2], h_ls, cudaGraphCondTypeWhile, 1, [&](int) -> cp_status {
               return with_stream(side[2], [&]() -> cp_status {
+                // x = ubar + stp d; f, g at x; phi' = g . d; one More-Thuente
+                // update that also sets `ls` -- prep, MTTKRPs, finish
                 return counted(&kcount.ls_eval, [&]() -> cp_status {
-                  CP_TRY(axpy_scalar(ctx, P, m.ubar, m.d, &m.st->stp, m.x));
-                  CP_TRY(fg_eval(ctx, t, L, m.x, m.scal + FX, m.gx, pr));
-                  CP_TRY(dot(ctx, P, m.gx, m.d, m.scal + GD));
-                  return mt_iterate_cond(ctx, m.st, m.scal + FX, m.scal + GD, h_ls);
+                  return fg_eval_ex(ctx, t, L, m.ubar, m.d, &m.st->stp, m.x, m.scal + FX, m.gx, pr,
+                                    m.scal + GD, m.st, h_ls, 1);
                 });
               });
             }));

@@ -39,6 +39,7 @@ struct SolverRes {
   cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // capture streams of nested bodies
   cudaEvent_t ev = nullptr;
   int* d_status = nullptr;
+  unsigned* d_counter = nullptr;
   double* h_pinned = nullptr;
   int* h_pinned_i = nullptr;
   SolveCtl* hctl = nullptr;

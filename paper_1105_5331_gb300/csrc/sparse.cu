@@ -272,42 +272,54 @@ __global__ void table_kernel(const double* __restrict__ A, int64_t I, int R, int
   }
 }
 
-template <typename TT, int RB>
+// One warp per work unit.  Lanes map to ranks: with R <= 32 the warp holds
+// G = 32 / R groups of R lanes, group g takes the unit's nonzeros g, g + G,
+// ..., and lane r of a group multiplies the r-th entries of the gathered
+// factor rows (so each row is one coalesced R-wide load and the value and
+// coordinates are broadcast within the group).  The G group sums are added
+// in a fixed order at the end.  For R > 32 one group covers the ranks in
+// chunks of 32.
+template <typename TT, int NO>
 __global__ void __launch_bounds__(256) mttkrp_coo_kernel(const int32_t* __restrict__ other,
                                                          const float* __restrict__ vals, int64_t nnz,
-                                                         int nothers, const int64_t* __restrict__ unit_start,
-                                                         int64_t nunits, Tables tab, int R, int RP,
+                                                         const int64_t* __restrict__ unit_start,
+                                                         int64_t nunits, Tables tab, int R,
                                                          double* __restrict__ partial) {
   const int lane = threadIdx.x & 31;
   const int64_t unit = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (unit >= nunits) return;
   const int64_t b = unit_start[unit], e = unit_start[unit + 1];
-  TT acc[RB];
+  const int G = R <= 32 ? 32 / R : 1;
+  const int g = R <= 32 ? lane / R : 0;
+  const int r0 = R <= 32 ? lane - g * R : lane;
+  const bool active = g < G;
+  const int nch = (R + 31) / 32;            // rank chunks handled by this lane (R > 32)
+  TT acc0 = (TT)0, acc1 = (TT)0;
+  const TT* rows[NO];
+  if (active) {
+    for (int64_t k = b + g; k < e; k += G) {
+      const TT v = (TT)vals[k];
 #pragma unroll
-  for (int r = 0; r < RB; ++r) acc[r] = (TT)0;
-  for (int64_t k = b + lane; k < e; k += 32) {
-    TT prod[RB];
-    const TT v = (TT)vals[k];
+      for (int j = 0; j < NO; ++j) rows[j] = (const TT*)tab.A[j] + (int64_t)other[(int64_t)j * nnz + k] * R;
+      if (r0 < R) {
+        TT p = v;
 #pragma unroll
-    for (int r = 0; r < RB; ++r) prod[r] = v;
-    for (int j = 0; j < nothers; ++j) {
-      const int64_t idx = other[(int64_t)j * nnz + k];
-      const TT* row = (const TT*)tab.A[j] + idx * RP;
+        for (int j = 0; j < NO; ++j) p *= rows[j][r0];
+        acc0 += p;
+      }
+      if (nch > 1 && r0 + 32 < R) {
+        TT p = v;
 #pragma unroll
-      for (int r = 0; r < RB; ++r)
-        if (r < RP) prod[r] *= row[r];
+        for (int j = 0; j < NO; ++j) p *= rows[j][r0 + 32];
+        acc1 += p;
+      }
     }
-#pragma unroll
-    for (int r = 0; r < RB; ++r) acc[r] += prod[r];
   }
-  // butterfly reduction: every lane ends with the same, fixed-order sum
-#pragma unroll
-  for (int r = 0; r < RB; ++r) {
-    double s = (double)acc[r];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0 && r < R) partial[unit * R + r] = s;
-  }
+  // add the group sums in order: lane r (group 0) gathers groups 1..G-1
+  double s0 = (double)acc0;
+  for (int q = 1; q < G; ++q) s0 += (double)__shfl_sync(0xffffffffu, acc0, (lane + q * R) & 31);
+  if (g == 0 && r0 < R) partial[unit * R + r0] = s0;
+  if (nch > 1 && r0 + 32 < R) partial[unit * R + r0 + 32] = (double)acc1;
 }
 
 __global__ void zero_kernel(double* __restrict__ x, int64_t n) {
@@ -494,14 +506,14 @@ void tensor_free_coo(cp_tensor* t) {
   }
 }
 
-template <typename TT, int RB>
+template <typename TT, int NO>
 static cp_status launch_coo(cp_ctx* ctx, const cp_tensor* t, const CooMode& md, const Tables& tab, int R,
-                            int RP, double* partial) {
+                            double* partial) {
   const int64_t threads = 256;
   const int64_t blocks = (md.nunits * 32 + threads - 1) / threads;
   if (blocks == 0) return CP_OK;
-  mttkrp_coo_kernel<TT, RB><<<(unsigned)blocks, (unsigned)threads, 0, ctx->stream>>>(
-      md.other, md.vals, t->nnz, t->N - 1, md.unit_start, md.nunits, tab, R, RP, partial);
+  mttkrp_coo_kernel<TT, NO><<<(unsigned)blocks, (unsigned)threads, 0, ctx->stream>>>(
+      md.other, md.vals, t->nnz, md.unit_start, md.nunits, tab, R, partial);
   CP_LAUNCH_CHECK();
   return CP_OK;
 }
@@ -509,11 +521,16 @@ static cp_status launch_coo(cp_ctx* ctx, const cp_tensor* t, const CooMode& md, 
 template <typename TT>
 static cp_status dispatch_coo(cp_ctx* ctx, const cp_tensor* t, const CooMode& md, const Tables& tab, int R,
                               int RP, double* partial) {
-  if (RP <= 4) return launch_coo<TT, 4>(ctx, t, md, tab, R, RP, partial);
-  if (RP <= 8) return launch_coo<TT, 8>(ctx, t, md, tab, R, RP, partial);
-  if (RP <= 16) return launch_coo<TT, 16>(ctx, t, md, tab, R, RP, partial);
-  if (RP <= 32) return launch_coo<TT, 32>(ctx, t, md, tab, R, RP, partial);
-  return launch_coo<TT, 64>(ctx, t, md, tab, R, RP, partial);
+  (void)RP;
+  switch (t->N - 1) {
+    case 1: return launch_coo<TT, 1>(ctx, t, md, tab, R, partial);
+    case 2: return launch_coo<TT, 2>(ctx, t, md, tab, R, partial);
+    case 3: return launch_coo<TT, 3>(ctx, t, md, tab, R, partial);
+    case 4: return launch_coo<TT, 4>(ctx, t, md, tab, R, partial);
+    case 5: return launch_coo<TT, 5>(ctx, t, md, tab, R, partial);
+    case 6: return launch_coo<TT, 6>(ctx, t, md, tab, R, partial);
+    default: return launch_coo<TT, 7>(ctx, t, md, tab, R, partial);
+  }
 }
 
 cp_status mttkrp_sparse(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, int mode,
