@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--mttkrp-only", default=None, choices=["dense_256", "dense_4way", "sparse"],
                    help="time only cp_mttkrp on that workload (profiling driver)")
     p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--solve-only", action="store_true",
+                   help="time only the headline solves (profiling driver; no side reports)")
     p.add_argument("--serve-requests", type=int, default=128,
                    help="requests of the 200/s Poisson serving stream replayed (0: skip)")
     p.add_argument("--serve-fp64-requests", type=int, default=32,
@@ -184,7 +186,7 @@ def run_ours(args, rank, world, local_rank):
     import paper_1105_5331_gb300 as cp
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and not args.solve_only:
         cpu = run_cpu_baseline_subprocess(args.cpu_iters)   # before any GPU work
 
     torch.cuda.set_device(local_rank)
@@ -210,10 +212,12 @@ def run_ours(args, rank, world, local_rank):
         o.prec = p
         return o
 
-    def timed_solves(p, n_warm, n_timed):
+    def timed_solves(p, n_warm, n_timed, launch_count=None):
         o = opts_for(p)
         times, reps = [], []
         for k in range(n_warm + n_timed):
+            if k == n_warm and launch_count is not None:
+                launch_count.append(cp.cp_kernel_launches())
             with torch.cuda.stream(stream):
                 flush.fill_(float(k))
                 u.copy_(u0_dev)
@@ -229,16 +233,16 @@ def run_ours(args, rank, world, local_rank):
         return times, reps
 
     # headline precision
-    launches0 = cp.cp_kernel_launches()
+    lc = []
     barrier(world)
     with ClockSampler(local_rank) as clk:
-        times, reps = timed_solves(prec, args.warmup, args.steps)
-    launches = cp.cp_kernel_launches() - launches0
+        times, reps = timed_solves(prec, args.warmup, args.steps, lc)
+    launches = cp.cp_kernel_launches() - lc[0]   # the K timed solves only
     total = sum(times)
     total_max = allreduce_max(total, world)
     value = world * args.steps / total_max
     # the other precision at the same tolerance, for the mixed-vs-FP64 figure
-    other = cp.CP_FP64 if prec != cp.CP_FP64 else None
+    other = cp.CP_FP64 if prec != cp.CP_FP64 and not args.solve_only else None
     other_obj = None
     if other is not None:
         ot, orp = timed_solves(other, 1, 1)
@@ -246,12 +250,12 @@ def run_ours(args, rank, world, local_rank):
                      "iters": orp[0]["iters"], "gnorm_over_P": orp[0]["gnorm_over_P"], "f": orp[0]["f"]}
 
     # roofline of the dominant kernel (the MTTKRP), timed live on the ctx stream
-    roof = mttkrp_roofline(cp, ctx, t, u0_dev, stream, flush, prec)
+    roof = None if args.solve_only else mttkrp_roofline(cp, ctx, t, u0_dev, stream, flush, prec)
 
     # end to end through the public API with host buffers
-    e2e = e2e_run(cp, ctx, prob, u0, prec, min(args.steps, 3), T_host)
+    e2e = None if args.solve_only else e2e_run(cp, ctx, prob, u0, prec, min(args.steps, 3), T_host)
 
-    serving = serving_run(cp, ctx, args) if rank == 0 else None
+    serving = serving_run(cp, ctx, args) if rank == 0 and not args.solve_only else None
 
     clocks = clk.summary()
     lat = sorted(times)
@@ -286,40 +290,61 @@ def run_ours(args, rank, world, local_rank):
     return res
 
 
+# DRAM bytes (read + write) per launch of mttkrp_tc_kernel, mode 0 of the
+# 256^3 R=16 workload, from one ncu --set full capture of the current kernel
+# (profiles/mttkrp_tc_dense256.md); None until such a capture exists.
+TC_NCU_TRAFFIC = None
+
+
 def mttkrp_roofline(cp, ctx, t, u, stream, flush, prec):
+    """Dominant kernel: the MTTKRP kernel itself, timed live with CUDA events
+    around each of its launches on the context stream (library kernel
+    timers), L2 flushed before every call; the whole cp_mttkrp call (FP32
+    factor copy, kernel, split-K reduction) is reported beside it."""
     import torch
     out = torch.empty(DIMS[0] * R, dtype=torch.float64, device=u.device)
     K = DIMS[0] * DIMS[1] * DIMS[2]
-    durs = []
-    for n in range(3):
-        for k in range(7):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(k))
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            cp.cp_mttkrp(ctx, t, R, u, n, out, prec)
-            e1.record(stream)
-            e1.synchronize()
-            if k >= 2:
-                durs.append(e0.elapsed_time(e1) / 1e3)
-    d = sum(durs) / len(durs)
+    fam = cp.TIMER_F64 if prec == cp.CP_FP64 else cp.TIMER_TC
+    call = []
+    for warm in (True, False):
+        cp.cp_ctx_timer_enable(ctx, True)
+        for n in range(3):
+            for k in range(2 if warm else 5):
+                with torch.cuda.stream(stream):
+                    flush.fill_(float(k))
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                cp.cp_mttkrp(ctx, t, R, u, n, out, prec)
+                e1.record(stream)
+                e1.synchronize()
+                if not warm:
+                    call.append(e0.elapsed_time(e1) / 1e3)
+    total_ms, launches = cp.cp_ctx_timer_read(ctx, fam)
+    cp.cp_ctx_timer_enable(ctx, False)
+    d = total_ms / 1e3 / max(launches, 1)
+    dc = sum(call) / len(call)
     peaks = measured_peaks()
     if prec == cp.CP_FP64:
         flops = 2.0 * K * R
         ach = flops / d / 1e12
-        return {"kernel": "mttkrp_f64_kernel (+ partial-sum reduction)", "bound": "alu",
-                "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": None, "per_launch": {"flops": flops, "avg_ms": d * 1e3},
+        return {"kernel": "mttkrp_f64_kernel", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "per_launch": {"flops": flops, "avg_kernel_ms": d * 1e3, "launches_timed": launches,
+                               "avg_cp_mttkrp_call_ms": dc * 1e3},
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
-    # mixed: HBM-bound stream of the bf16 hi/lo planes of T_(n) (4 B per element)
-    bytes_ = 4.0 * K + 8.0 * DIMS[0] * R + 4.0 * 2 * DIMS[1] * R
+    # HBM-bound stream of the bf16 hi/lo planes of T_(n): 4 B per element, plus
+    # the FP32 factor tables read and the split-K partials written
+    bytes_ = 4.0 * K + 4.0 * 2 * DIMS[1] * R + 4.0 * 152 * DIMS[0] * R
     ach = bytes_ / d / 1e9
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    return {"kernel": "mttkrp_tc_kernel (tcgen05 bf16x3, + partial-sum reduction)", "bound": "hbm",
-            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
-            "per_launch": {"bytes": bytes_, "avg_ms": d * 1e3},
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+    return {"kernel": "mttkrp_tc_kernel (tcgen05 bf16x3)", "bound": "hbm", "achieved": ach, "peak": peak,
+            "unit": "GB/s", "frac": ach / peak, "traffic": TC_NCU_TRAFFIC,
+            "per_launch": {"bytes": bytes_, "avg_kernel_ms": d * 1e3, "launches_timed": launches,
+                           "avg_cp_mttkrp_call_ms": dc * 1e3,
+                           "call_achieved_GBps": bytes_ / dc / 1e9},
+            "peak_source": ("MEASURED_PEAKS.json hbm_gbs (burst copy) - of measured" if peaks
+                            else "fallback 6.8 TB/s - of fallback")}
 
 
 def serving_run(cp, ctx, args):

@@ -84,6 +84,14 @@ void* cp_ctx_stream(cp_ctx* ctx);
 /* Number of CUDA kernels this library has launched in the process so far
  * (all contexts; for accounting in benchmarks). */
 unsigned long long cp_kernel_launches(void);
+/* Kernel timers (profiling aid).  While enabled, every launch of an MTTKRP
+ * kernel on this context's stream (outside stream capture) is bracketed by
+ * CUDA events.  Enabling (or disabling) resets the sums.  cp_ctx_timer_read
+ * synchronises the stream and returns the summed device time and the number
+ * of launches of family `which`: 0 tensor-core (bf16x3) dense MTTKRP kernel,
+ * 1 FP64 dense MTTKRP kernel, 2 sparse MTTKRP kernel. */
+cp_status cp_ctx_timer_enable(cp_ctx* ctx, int enable);
+cp_status cp_ctx_timer_read(cp_ctx* ctx, int which, double* total_ms, int* launches);
 
 /* ---------------------------------------------------------------- tensors */
 

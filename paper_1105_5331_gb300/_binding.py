@@ -29,7 +29,7 @@ STATUS_NAMES = {
 # Every symbol include/cp.h declares (checked by the tests).
 EXPORTED = [
     "cp_ctx_create", "cp_ctx_destroy", "cp_last_error", "cp_ctx_sync", "cp_ctx_stream",
-    "cp_kernel_launches",
+    "cp_kernel_launches", "cp_ctx_timer_enable", "cp_ctx_timer_read",
     "cp_tensor_dense", "cp_tensor_coo", "cp_tensor_info", "cp_tensor_sorted_mode",
     "cp_tensor_destroy", "cp_mttkrp", "cp_mttkrp_noalloc", "cp_fg", "cp_als_sweep", "cp_normalize",
     "ngmres_step",
@@ -83,6 +83,8 @@ def _load():
         "cp_ctx_sync": (I, [VP]),
         "cp_ctx_stream": (VP, [VP]),
         "cp_kernel_launches": (C.c_ulonglong, []),
+        "cp_ctx_timer_enable": (I, [VP, I]),
+        "cp_ctx_timer_read": (I, [VP, I, C.POINTER(D), C.POINTER(I)]),
         "cp_tensor_dense": (I, [VP, I, P, I, VP, C.POINTER(VP)]),
         "cp_tensor_coo": (I, [VP, I, P, I64, VP, VP, C.POINTER(VP)]),
         "cp_tensor_info": (I, [VP, C.POINTER(I), P, C.POINTER(D)]),
@@ -229,6 +231,21 @@ def cp_ctx_stream(ctx) -> int:
 
 def cp_kernel_launches() -> int:
     return int(_lib.cp_kernel_launches())
+
+
+TIMER_TC, TIMER_F64, TIMER_COO = 0, 1, 2
+
+
+def cp_ctx_timer_enable(ctx, enable: bool = True):
+    _check(_lib.cp_ctx_timer_enable(_h(ctx), int(bool(enable))))
+
+
+def cp_ctx_timer_read(ctx, which: int):
+    """(total_ms, launches) of one MTTKRP kernel family since enabling."""
+    ms = C.c_double()
+    n = C.c_int()
+    _check(_lib.cp_ctx_timer_read(_h(ctx), int(which), C.byref(ms), C.byref(n)))
+    return ms.value, n.value
 
 
 def cp_tensor_dense(ctx, data, dims=None, dtype=None) -> Tensor:

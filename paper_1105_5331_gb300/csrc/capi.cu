@@ -178,6 +178,39 @@ cp_status cp_ctx_sync(cp_ctx* c) {
 
 void* cp_ctx_stream(cp_ctx* c) { return c ? (void*)c->stream : nullptr; }
 
+cp_status cp_ctx_timer_enable(cp_ctx* c, int enable) {
+  CP_NULLCHECK(c);
+  CP_TRY(use_device(c));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  c->timing = enable != 0;
+  for (auto& t : c->ktimer) {
+    t.n = 0;
+    t.ms = 0.0;
+    t.count = 0;
+  }
+  return CP_OK;
+}
+
+cp_status cp_ctx_timer_read(cp_ctx* c, int which, double* total_ms, int* launches) {
+  CP_NULLCHECK(c);
+  if (which < 0 || which > 2) {
+    set_error("cp_ctx_timer_read: kernel family %d unknown", which);
+    return CP_ERR_ARG;
+  }
+  CP_TRY(use_device(c));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  cp_ctx::KTimer& t = c->ktimer[which];
+  for (int i = 0; i < t.n; ++i) {
+    float ms = 0.f;
+    CP_CUDA(cudaEventElapsedTime(&ms, t.a[i], t.b[i]));
+    t.ms += ms;
+  }
+  t.n = 0;
+  if (total_ms) *total_ms = t.ms;
+  if (launches) *launches = t.count;
+  return CP_OK;
+}
+
 cp_status cp_tensor_dense(cp_ctx* ctx, int N, const int64_t* dims, cp_dtype dtype, const void* data,
                           cp_tensor** out) {
   CP_NULLCHECK(ctx);

@@ -121,7 +121,62 @@ struct cp_ctx {
   char* arena_base = nullptr;
   size_t arena_cap = 0;
   size_t arena_off = 0;
+  // Kernel timers (cp_ctx_timer_*): CUDA events around the MTTKRP kernels.
+  struct KTimer {
+    cudaEvent_t a[64], b[64];
+    int n = 0;
+    double ms = 0.0;
+    int count = 0;
+    bool made = false;
+  };
+  bool timing = false;
+  KTimer ktimer[3];
 };
+
+namespace cpg {
+
+// Brackets one kernel launch on ctx->stream with events when timing is on
+// (never inside a stream capture).
+struct TimerScope {
+  cp_ctx* c;
+  int kind;
+  bool on = false;
+  TimerScope(cp_ctx* ctx, int k) : c(ctx), kind(k) {
+    if (!c->timing) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    cp_ctx::KTimer& t = c->ktimer[kind];
+    if (!t.made) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEventCreate(&t.a[i]);
+        cudaEventCreate(&t.b[i]);
+      }
+      t.made = true;
+    }
+    if (t.n == 64) {
+      for (int i = 0; i < 64; ++i) {
+        float ms = 0.f;
+        cudaEventSynchronize(t.b[i]);
+        cudaEventElapsedTime(&ms, t.a[i], t.b[i]);
+        t.ms += ms;
+      }
+      t.n = 0;
+    }
+    cudaEventRecord(t.a[t.n], c->stream);
+    on = true;
+  }
+  ~TimerScope() {
+    if (!on) return;
+    cp_ctx::KTimer& t = c->ktimer[kind];
+    cudaEventRecord(t.b[t.n], c->stream);
+    ++t.n;
+    ++t.count;
+  }
+};
+
+}  // namespace cpg
+
+struct cp_ctx_timer_tag {};
 
 struct CooMode {
   int64_t nseg = 0;

@@ -224,12 +224,15 @@ static cp_status mttkrp_f64_impl(cp_ctx* ctx, const cp_tensor* t, const Layout& 
   double* partial = nullptr;
   CP_TRY(ws_alloc(ctx, (void**)&partial, sizeof(double) * (size_t)grid * I * R));
   const size_t smem = sizeof(double) * kF64BK * R;
-  if (t->dtype == CP_DTYPE_F64)
-    mttkrp_f64_kernel<double><<<grid, threads, smem, ctx->stream>>>(
-        (const double*)t->Tn[mode], I, Kb, kr, R, tiles_per_cta, partial);
-  else
-    mttkrp_f64_kernel<float><<<grid, threads, smem, ctx->stream>>>(
-        (const float*)t->Tn[mode], I, Kb, kr, R, tiles_per_cta, partial);
+  {
+    TimerScope ts(ctx, 1);
+    if (t->dtype == CP_DTYPE_F64)
+      mttkrp_f64_kernel<double><<<grid, threads, smem, ctx->stream>>>(
+          (const double*)t->Tn[mode], I, Kb, kr, R, tiles_per_cta, partial);
+    else
+      mttkrp_f64_kernel<float><<<grid, threads, smem, ctx->stream>>>(
+          (const float*)t->Tn[mode], I, Kb, kr, R, tiles_per_cta, partial);
+  }
   CP_LAUNCH_CHECK();
   if (parts_out) {
     *parts_out = Parts{partial, grid, 0};

@@ -593,7 +593,10 @@ static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, co
   p.status = ctx->d_status;
   const size_t smem = (size_t)p.stages * stage_bytes + fixed + (p.tab_smem ? tab_bytes : 0);
   CP_TRY(set_smem_attr());
-  tc_kernel_for(p.nother)<<<dim3(gx, mgroups), kThreads, smem, ctx->stream>>>(mm.hi, mm.lo, p);
+  {
+    TimerScope ts(ctx, 0);
+    tc_kernel_for(p.nother)<<<dim3(gx, mgroups), kThreads, smem, ctx->stream>>>(mm.hi, mm.lo, p);
+  }
   CP_LAUNCH_CHECK();
   *parts = Parts{partial, gx, 1};
   return CP_OK;

@@ -512,8 +512,11 @@ static cp_status launch_coo(cp_ctx* ctx, const cp_tensor* t, const CooMode& md, 
   const int64_t threads = 256;
   const int64_t blocks = (md.nunits * 32 + threads - 1) / threads;
   if (blocks == 0) return CP_OK;
-  mttkrp_coo_kernel<TT, NO><<<(unsigned)blocks, (unsigned)threads, 0, ctx->stream>>>(
-      md.other, md.vals, t->nnz, md.unit_start, md.nunits, tab, R, partial);
+  {
+    TimerScope ts(ctx, 2);
+    mttkrp_coo_kernel<TT, NO><<<(unsigned)blocks, (unsigned)threads, 0, ctx->stream>>>(
+        md.other, md.vals, t->nnz, md.unit_start, md.nunits, tab, R, partial);
+  }
   CP_LAUNCH_CHECK();
   return CP_OK;
 }
