@@ -1,0 +1,409 @@
+// ALS sweep (Section 2.3, Eq. foopt) and factor Grams, laid out for a GPU
+// whose FP64 units are scarce: a dependent FP64 FMA costs ~64 clocks and a
+// divide or square root ~650 on sm_103a, so no kernel here runs a long
+// serial FP64 chain and no single block reduces a large FP64 sum.
+//
+//   Grams       one warp per (Gram, entry): lanes stride the rows, a
+//               butterfly shuffle adds the lane sums; no cross-block
+//               reduction unless a factor is taller than one row chunk.
+//   inverse     Gammabar^(n) = Hadamard product of the other modes' Grams,
+//               inverted by symmetric Gauss-Jordan elimination (no pivoting,
+//               which is stable for SPD matrices and fails exactly when a
+//               Cholesky factorisation would), one ridge retry; pivot
+//               reciprocals by Newton's iteration from an FP32 seed.  It runs
+//               on the context's aux stream, overlapped with the MTTKRP of
+//               the same mode, which does not depend on it.
+//   update      A_n = M Gammabar^-1: rows spread over blocks; M rows from the
+//               MTTKRP partial sums (FP32 partials added in FP32, FP64 ones in
+//               FP64, in a fixed order), then one FP64 dot per output.
+#include <algorithm>
+
+#include "cp_internal.cuh"
+
+namespace cpg {
+
+cp_status mttkrp_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, const float* u32,
+                       const F32Off& o32, int mode, cp_precision prec, Parts* out);
+
+namespace {
+
+constexpr int kGramChunk = 4096;      // rows per warp item before the row range is split
+
+struct GramParams {
+  GramJob job[kMaxGramJobs];
+  int64_t item_off[kMaxGramJobs + 1];  // prefix of (entries x chunks) per job
+  int njobs;
+  int R;
+  double* partial;                     // [items] when any job is chunked
+  int chunked;
+  unsigned* counter;
+};
+
+__device__ __forceinline__ void upper_pair(int e, int R, int* r, int* s) {
+  // e enumerates (r, s), r <= s, row by row
+  int rr = 0, base = 0;
+  while (e >= base + (R - rr)) {
+    base += R - rr;
+    ++rr;
+  }
+  *r = rr;
+  *s = rr + (e - base);
+}
+
+__device__ __forceinline__ void job_entry(const GramParams& p, int64_t item, int* j, int* r, int* s, int64_t* chunk) {
+  int jj = 0;
+  while (jj + 1 < p.njobs && item >= p.item_off[jj + 1]) ++jj;
+  const GramJob& g = p.job[jj];
+  const int64_t nch = (g.I + kGramChunk - 1) / kGramChunk;
+  const int64_t local = item - p.item_off[jj];
+  const int64_t e = local / (nch > 0 ? nch : 1);
+  *chunk = local - e * (nch > 0 ? nch : 1);
+  if (g.sym) {
+    upper_pair((int)e, p.R, r, s);
+  } else {
+    *r = (int)(e / p.R);
+    *s = (int)(e - (e / p.R) * p.R);
+  }
+  *j = jj;
+}
+
+__global__ void __launch_bounds__(256) gram_kernel(const GramParams p) {
+  __shared__ bool is_last;
+  const int lane = threadIdx.x & 31;
+  const int64_t item = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t nitems = p.item_off[p.njobs];
+  if (item < nitems) {
+    int j, r, s;
+    int64_t ch;
+    job_entry(p, item, &j, &r, &s, &ch);
+    const GramJob& g = p.job[j];
+    const int R = p.R;
+    const int64_t i0 = ch * kGramChunk, i1 = min(g.I, i0 + kGramChunk);
+    double a0 = 0.0, a1 = 0.0;
+    int64_t i = i0 + lane;
+    for (; i + 32 < i1; i += 64) {
+      a0 = fma(g.X[i * R + r], g.Y[i * R + s], a0);
+      a1 = fma(g.X[(i + 32) * R + r], g.Y[(i + 32) * R + s], a1);
+    }
+    if (i < i1) a0 = fma(g.X[i * R + r], g.Y[i * R + s], a0);
+    double v = a0 + a1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) {
+      if (p.chunked) {
+        p.partial[item] = v;
+      } else {
+        g.out[r * R + s] = v;
+        if (g.sym) g.out[s * R + r] = v;
+      }
+    }
+  }
+  if (!p.chunked) return;
+  // chunked: the last block adds each entry's chunk sums in chunk order
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(p.counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const int R = p.R;
+  for (int j = 0; j < p.njobs; ++j) {
+    const GramJob& g = p.job[j];
+    const int64_t nch = (g.I + kGramChunk - 1) / kGramChunk;
+    const int ne = g.sym ? R * (R + 1) / 2 : R * R;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      double v = 0.0;
+      for (int64_t c = 0; c < nch; ++c) v += __ldcg(&p.partial[p.item_off[j] + (int64_t)e * nch + c]);
+      int r, s;
+      if (g.sym) {
+        upper_pair(e, R, &r, &s);
+      } else {
+        r = e / R;
+        s = e - r * R;
+      }
+      g.out[r * R + s] = v;
+      if (g.sym) g.out[s * R + r] = v;
+    }
+  }
+  if (threadIdx.x == 0) *p.counter = 0u;
+}
+
+// 1/d by Newton's iteration r <- r (2 - d r) from an FP32 reciprocal, two
+// steps (each doubles the correct bits: ~23 -> 46 -> full precision); the
+// FP64 divide is used outside the FP32 exponent range.
+__device__ __forceinline__ double recip_newton(double d) {
+  const double ad = fabs(d);
+  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+  double r = (double)__frcp_rn((float)d);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
+struct InvParams {
+  const double* grams;   // N x R*R
+  int N, R, n;
+  double* Xinv;          // R*R out: Gammabar^(n)^-1
+  int* ok;               // out: 1 on success
+  int* status;
+};
+
+// In-place symmetric Gauss-Jordan inverse of the R x R SPD matrix S (shared
+// memory, all threads); false if a pivot is not positive and finite.
+__device__ bool gj_inverse(double* S, int R, double* piv_sh, int* flag) {
+  for (int k = 0; k < R; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = S[k * R + k];
+      if (!(d > 0.0) || !isfinite(d)) *flag = 1;
+      else *piv_sh = recip_newton(d);
+    }
+    __syncthreads();
+    if (*flag) return false;
+    const double pinv = *piv_sh;
+    // rows i != k, columns j != k: S_ij -= S_ik S_kj / S_kk
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+      const int i = e / R, j = e - (e / R) * R;
+      if (i != k && j != k) S[e] = fma(-S[i * R + k] * pinv, S[k * R + j], S[e]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+      if (i != k) {
+        S[i * R + k] *= -pinv;
+        S[k * R + i] *= -pinv;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) S[k * R + k] = -pinv;
+    __syncthreads();
+  }
+  // the elimination above leaves -S^-1
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) S[e] = -S[e];
+  __syncthreads();
+  return true;
+}
+
+__global__ void __launch_bounds__(256) gram_inverse_kernel(const InvParams p) {
+  __shared__ double S[CP_MAX_R * CP_MAX_R];
+  __shared__ double piv;
+  __shared__ int flag;
+  const int R = p.R, RR = R * R;
+  auto build = [&](double ridge) {
+    for (int k = threadIdx.x; k < RR; k += blockDim.x) {
+      double v = 1.0;
+      for (int m = 0; m < p.N; ++m)
+        if (m != p.n) v *= p.grams[(int64_t)m * RR + k];
+      S[k] = v;
+    }
+    __syncthreads();
+    if (ridge > 0.0 && threadIdx.x == 0) {
+      double tr = 0.0;
+      for (int r = 0; r < R; ++r) tr += S[r * R + r];
+      for (int r = 0; r < R; ++r) S[r * R + r] += ridge * tr / R;
+    }
+    if (threadIdx.x == 0) flag = 0;
+    __syncthreads();
+  };
+  build(0.0);
+  bool ok = gj_inverse(S, R, &piv, &flag);
+  if (!ok) {
+    build(1e-12);
+    ok = gj_inverse(S, R, &piv, &flag);
+  }
+  for (int k = threadIdx.x; k < RR; k += blockDim.x) p.Xinv[k] = ok ? S[k] : 0.0;
+  if (threadIdx.x == 0) {
+    *p.ok = ok ? 1 : 0;
+    if (!ok) record_status(p.status, CP_ERR_NOT_SPD);
+  }
+}
+
+struct UpdParams {
+  Parts parts;
+  int64_t I;
+  int R;
+  int rows;              // rows per block
+  const double* Xinv;
+  const int* ok;
+  double* An;            // I x R, updated in place
+  float* An32;           // nullable
+};
+
+__global__ void __launch_bounds__(256) als_update_kernel(const UpdParams p) {
+  __shared__ double X[CP_MAX_R * CP_MAX_R];
+  __shared__ double Mt[2 * CP_MAX_R];
+  __shared__ float redf[8][33];
+  __shared__ double redd[8][33];
+  const int R = p.R, RR = R * R;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t rb = (int64_t)blockIdx.x * p.rows;
+  const int nr = (int)min((int64_t)p.rows, p.I - rb);
+  const int nout = nr * R;
+  const int64_t nel = p.I * R;
+  if (!*p.ok) return;
+  for (int k = threadIdx.x; k < RR; k += blockDim.x) X[k] = p.Xinv[k];
+  // M rows of this block: warp w adds partials c = w, w + 8, ... for 32
+  // consecutive outputs; warp 0 adds the eight warp sums in order
+  for (int e0 = 0; e0 < nout; e0 += 32) {
+    const int64_t e = rb * R + e0 + lane;
+    const bool in = e0 + lane < nout;
+    if (p.parts.f32) {
+      const float* q = (const float*)p.parts.p;
+      float s = 0.f;
+      if (in)
+#pragma unroll 4
+        for (int c = w; c < p.parts.count; c += 8) s += __ldcg(&q[(int64_t)c * nel + e]);
+      redf[w][lane] = s;
+    } else {
+      const double* q = (const double*)p.parts.p;
+      double s = 0.0;
+      if (in)
+#pragma unroll 4
+        for (int c = w; c < p.parts.count; c += 8) s += __ldcg(&q[(int64_t)c * nel + e]);
+      redd[w][lane] = s;
+    }
+    __syncthreads();
+    if (w == 0 && in) {
+      if (p.parts.f32) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += redf[q][lane];
+        Mt[e0 + lane] = (double)t;
+      } else {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += redd[q][lane];
+        Mt[e0 + lane] = t;
+      }
+    }
+    __syncthreads();
+  }
+  // a_i = m_i Gammabar^-1: one output per thread, two partial chains
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    const int q = o / R, r = o - (o / R) * R;
+    const double* m = Mt + q * R;
+    double s0 = 0.0, s1 = 0.0;
+    int k = 0;
+    for (; k + 1 < R; k += 2) {
+      s0 = fma(m[k], X[k * R + r], s0);
+      s1 = fma(m[k + 1], X[(k + 1) * R + r], s1);
+    }
+    if (k < R) s0 = fma(m[k], X[k * R + r], s0);
+    const double a = s0 + s1;
+    const int64_t idx = (rb + q) * R + r;
+    p.An[idx] = a;
+    if (p.An32) p.An32[idx] = (float)a;
+  }
+}
+
+__global__ void f64_to_f32_kernel(Layout L, const double* __restrict__ u, F32Off o, float* __restrict__ out) {
+  const int64_t P = L.off[L.N];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
+    int n = 0;
+    while (n + 1 < L.N && e >= L.off[n + 1]) ++n;
+    out[o.off[n] + (e - L.off[n])] = (float)u[e];
+  }
+}
+
+}  // namespace
+
+cp_status grams_jobs(cp_ctx* ctx, cudaStream_t s, unsigned* counter, int R, const GramJob* jobs, int njobs) {
+  if (njobs < 1 || njobs > kMaxGramJobs) {
+    set_error("grams: %d jobs outside [1, %d]", njobs, kMaxGramJobs);
+    return CP_ERR_ARG;
+  }
+  GramParams p{};
+  p.njobs = njobs;
+  p.R = R;
+  int64_t items = 0;
+  for (int j = 0; j < njobs; ++j) {
+    p.job[j] = jobs[j];
+    p.item_off[j] = items;
+    const int64_t nch = std::max<int64_t>(1, (jobs[j].I + kGramChunk - 1) / kGramChunk);
+    if (nch > 1) p.chunked = 1;
+    items += (int64_t)(jobs[j].sym ? R * (R + 1) / 2 : R * R) * nch;
+  }
+  p.item_off[njobs] = items;
+  p.counter = counter;
+  if (p.chunked) {
+    // chunked jobs need every job's item layout to carry its chunk count;
+    // jobs that fit one chunk still index as nch = 1
+    CP_TRY(ws_alloc(ctx, (void**)&p.partial, sizeof(double) * (size_t)items));
+  }
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, (items + 7) / 8);
+  gram_kernel<<<blocks, 256, 0, s>>>(p);
+  CP_LAUNCH_CHECK();
+  if (p.partial) ws_free(ctx, p.partial);
+  return CP_OK;
+}
+
+cp_status grams_of(cp_ctx* ctx, cudaStream_t s, unsigned* counter, const Layout& L, const double* u, int mode_lo,
+                   int nmodes, double* grams) {
+  GramJob jobs[kMaxGramJobs];
+  for (int k = 0; k < nmodes; ++k) {
+    const int m = mode_lo + k;
+    jobs[k] = GramJob{u + L.off[m], u + L.off[m], L.dims[m], grams + (size_t)m * L.R * L.R, 1};
+  }
+  return grams_jobs(ctx, s, counter, L.R, jobs, nmodes);
+}
+
+// One ALS sweep in place on u (Section 2.3): every mode n in turn takes
+// A_n = M^(n) Gammabar^(n)^-1.  grams (N x R x R) receives the Grams of the
+// updated factors; with grams_valid it already holds those of u on entry.
+cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, double* u, cp_precision prec,
+                       double* grams, bool grams_valid) {
+  cp_tensor* t = const_cast<cp_tensor*>(t_in);
+  const int R = L.R, N = L.N, RR = R * R;
+  const bool want_f32 = t->kind == 0 && prec == CP_MIXED_BF16X3;
+  F32Off o32{};
+  int64_t acc32 = 0;
+  for (int n = 0; n < N; ++n) {
+    o32.off[n] = acc32;
+    acc32 += (L.dims[n] * R + 3) / 4 * 4;
+  }
+  float* u32 = nullptr;
+  double* Xinv = nullptr;
+  int* ok = nullptr;
+  if (want_f32) CP_TRY(ws_alloc(ctx, (void**)&u32, sizeof(float) * (size_t)acc32 + 64));
+  CP_TRY(ws_alloc(ctx, (void**)&Xinv, sizeof(double) * (size_t)RR + 64));
+  ok = (int*)(Xinv + RR);
+  if (want_f32) {
+    const int64_t P = L.P();
+    f64_to_f32_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 4 * ctx->num_sms)), 256, 0,
+                        ctx->stream>>>(L, u, o32, u32);
+    CP_LAUNCH_CHECK();
+  }
+  if (!grams_valid) CP_TRY(grams_of(ctx, ctx->stream, ctx->d_counter, L, u, 0, N, grams));
+  const int rows = std::max(1, 32 / R);
+  for (int n = 0; n < N; ++n) {
+    // aux: (Gram of the mode updated last) -> inverse of Gammabar^(n),
+    // overlapped with this mode's MTTKRP on the main stream
+    CP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    CP_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    if (n > 0) CP_TRY(grams_of(ctx, ctx->aux, ctx->d_counter + 1, L, u, n - 1, 1, grams));
+    InvParams ip{grams, N, R, n, Xinv, ok, ctx->d_status};
+    gram_inverse_kernel<<<1, 256, 0, ctx->aux>>>(ip);
+    CP_LAUNCH_CHECK();
+    CP_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
+    Parts pt;
+    CP_TRY(mttkrp_parts(ctx, t, L, u, u32, o32, n, prec, &pt));
+    CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    UpdParams up;
+    up.parts = pt;
+    up.I = L.dims[n];
+    up.R = R;
+    up.rows = rows;
+    up.Xinv = Xinv;
+    up.ok = ok;
+    up.An = u + L.off[n];
+    up.An32 = u32 ? u32 + o32.off[n] : nullptr;
+    als_update_kernel<<<(unsigned)((L.dims[n] + rows - 1) / rows), 256, 0, ctx->stream>>>(up);
+    CP_LAUNCH_CHECK();
+    ws_free(ctx, const_cast<void*>(pt.p));
+  }
+  CP_TRY(grams_of(ctx, ctx->stream, ctx->d_counter, L, u, N - 1, 1, grams));
+  ws_free(ctx, Xinv);
+  if (u32) ws_free(ctx, u32);
+  return CP_OK;
+}
+
+}  // namespace cpg

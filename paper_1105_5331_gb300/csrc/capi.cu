@@ -143,8 +143,11 @@ cp_status cp_ctx_create(int device, void* cuda_stream, cp_ctx** out) {
     c->own_stream = true;
   }
   CP_CUDA(cudaMalloc(&c->d_status, sizeof(int)));
-  CP_CUDA(cudaMalloc(&c->d_counter, sizeof(unsigned)));
-  CP_CUDA(cudaMemset(c->d_counter, 0, sizeof(unsigned)));
+  CP_CUDA(cudaMalloc(&c->d_counter, 4 * sizeof(unsigned)));
+  CP_CUDA(cudaMemset(c->d_counter, 0, 4 * sizeof(unsigned)));
+  CP_CUDA(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+  CP_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  CP_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   CP_CUDA(cudaMemset(c->d_status, 0, sizeof(int)));
   CP_CUDA(cudaMallocHost(&c->h_pinned, sizeof(double) * 1024));
   CP_CUDA(cudaMallocHost(&c->h_pinned_i, sizeof(int) * 64));
@@ -162,6 +165,9 @@ void cp_ctx_destroy(cp_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   if (c->own_stream) cudaStreamDestroy(c->stream);
+  if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   cudaFree(c->d_status);
   cudaFree(c->d_counter);
   cudaFreeHost(c->h_pinned);
@@ -430,13 +436,9 @@ cp_status cp_als_sweep(cp_ctx* ctx, const cp_tensor* t, int R, double* u, int no
   CP_TRY(use_device(ctx));
   Layout L;
   L.set(t->N, t->dims, R);
-  int64_t Imax = 1;
-  for (int n = 0; n < t->N; ++n) Imax = std::max(Imax, t->dims[n]);
   double* grams = nullptr;
-  double* M = nullptr;
   CP_TRY(ws_alloc(ctx, (void**)&grams, sizeof(double) * (size_t)t->N * R * R));
-  CP_TRY(ws_alloc(ctx, (void**)&M, sizeof(double) * (size_t)Imax * R));
-  CP_TRY(als_sweep_fused(ctx, t, L, u, prec));
+  CP_TRY(als_sweep_v2(ctx, t, L, u, prec, grams, false));
   if (normalize) {
     double* tmp = nullptr;
     CP_TRY(ws_alloc(ctx, (void**)&tmp, sizeof(double) * (size_t)L.P()));
@@ -444,7 +446,6 @@ cp_status cp_als_sweep(cp_ctx* ctx, const cp_tensor* t, int R, double* u, int no
     CP_TRY(normalize_into(ctx, L, tmp, u, nullptr, nullptr, nullptr));
     ws_free(ctx, tmp);
   }
-  ws_free(ctx, M);
   ws_free(ctx, grams);
   return CP_OK;
 }

@@ -109,7 +109,12 @@ struct cp_ctx {
   bool own_stream = false;
   int num_sms = 0;
   int* d_status = nullptr;          // device status word
-  unsigned* d_counter = nullptr;    // last-block counter of fused kernels (zero between kernels)
+  unsigned* d_counter = nullptr;    // last-block counters (zero between kernels): [0] stream, [1] aux
+  // Second stream for work that overlaps the MTTKRP (the Gram inverse of
+  // the next ALS mode), and the events that fork it from / join it to
+  // `stream`; inside a stream capture they become graph edges.
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* h_pinned = nullptr;       // small pinned host scratch (1024 doubles)
   int* h_pinned_i = nullptr;        // small pinned host scratch (64 ints)
   // Bump arena for workspace while capturing graphs whose bodies may hold
@@ -279,6 +284,26 @@ struct MTState;
 // One ALS sweep in place on u with fused kernels (1 + 2N launches).
 cp_status als_sweep_fused(cp_ctx* ctx, const cp_tensor* t, const Layout& L, double* u,
                           cp_precision prec);
+// Gram jobs out = X^T Y (X, Y: I x R row-major; sym: X == Y, both triangles
+// written), one launch on stream s; counter: a zeroed last-block counter
+// owned by s.
+struct GramJob {
+  const double* X;
+  const double* Y;
+  int64_t I;
+  double* out;
+  int sym;
+};
+constexpr int kMaxGramJobs = 3 * CP_MAX_N;
+cp_status grams_jobs(cp_ctx* ctx, cudaStream_t s, unsigned* counter, int R, const GramJob* jobs, int njobs);
+// Grams A_m^T A_m of modes mode_lo .. mode_lo + nmodes - 1 of u into grams[m].
+cp_status grams_of(cp_ctx* ctx, cudaStream_t s, unsigned* counter, const Layout& L, const double* u, int mode_lo,
+                   int nmodes, double* grams);
+// ALS sweep in place on u: per mode, the Gram inverse on ctx->aux overlapped
+// with the MTTKRP, then a row-parallel update.  grams (N x R x R) ends with
+// the Grams of the updated factors (grams_valid: it holds u's on entry).
+cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t, const Layout& L, double* u, cp_precision prec,
+                       double* grams, bool grams_valid);
 // Fused f/g at x = base (+ (*stp) d when d is given; x written).  With d, also
 // g . d into gd; with st, one More-Thuente update (and, with use_h, the graph
 // condition h set to "not done").

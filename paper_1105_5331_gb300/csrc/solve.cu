@@ -180,8 +180,11 @@ cp_status SolverRes::create() {
   CP_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   CP_CUDA(cudaMalloc(&d_status, sizeof(int)));
   CP_CUDA(cudaMemset(d_status, 0, sizeof(int)));
-  CP_CUDA(cudaMalloc(&d_counter, sizeof(unsigned)));
-  CP_CUDA(cudaMemset(d_counter, 0, sizeof(unsigned)));
+  CP_CUDA(cudaMalloc(&d_counter, 4 * sizeof(unsigned)));
+  CP_CUDA(cudaMemset(d_counter, 0, 4 * sizeof(unsigned)));
+  CP_CUDA(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
+  CP_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+  CP_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
   CP_CUDA(cudaMallocHost(&h_pinned, sizeof(double) * 64));
   CP_CUDA(cudaMallocHost(&h_pinned_i, sizeof(int) * 64));
   CP_CUDA(cudaMallocHost(&hctl, sizeof(SolveCtl)));
@@ -196,6 +199,9 @@ void SolverRes::destroy() {
   if (ev) cudaEventDestroy(ev);
   if (d_status) cudaFree(d_status);
   if (d_counter) cudaFree(d_counter);
+  if (aux) cudaStreamDestroy(aux);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
   if (h_pinned) cudaFreeHost(h_pinned);
   if (h_pinned_i) cudaFreeHost(h_pinned_i);
   if (hctl) cudaFreeHost(hctl);
@@ -239,6 +245,9 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   done_ev = res->ev;
   sub.d_status = res->d_status;
   sub.d_counter = res->d_counter;
+  sub.aux = res->aux;
+  sub.ev_fork = res->ev_fork;
+  sub.ev_join = res->ev_join;
   sub.h_pinned = res->h_pinned;
   sub.h_pinned_i = res->h_pinned_i;
   hctl = res->hctl;
@@ -322,7 +331,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
       return with_stream(side[0], [&]() -> cp_status {
         CP_TRY(counted(&kcount.head, [&]() -> cp_status {
           CP_TRY(dcopy(ctx, P, m.u, m.work));
-          CP_TRY(als_sweep_fused(ctx, t, L, m.work, pr));
+          CP_TRY(als_sweep_v2(ctx, t, L, m.work, pr, m.grams, false));
           CP_TRY(normalize_into(ctx, L, m.work, m.ubar, nullptr, nullptr, nullptr));
           CP_TRY(fg_eval(ctx, t, L, m.ubar, m.scal + FBAR, m.gbar, pr));
           CP_TRY(ngmres_core(ctx, P, m.win, cap, m.U, m.G, m.ubar, m.gbar, o.eps, m.work, nullptr));

@@ -40,6 +40,8 @@ struct SolverRes {
   cudaEvent_t ev = nullptr;
   int* d_status = nullptr;
   unsigned* d_counter = nullptr;
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* h_pinned = nullptr;
   int* h_pinned_i = nullptr;
   SolveCtl* hctl = nullptr;

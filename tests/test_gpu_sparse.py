@@ -162,6 +162,26 @@ def test_sparse_fg_parity(cp, ctx):
     assert rel(g.cpu().numpy(), go) <= TOL
 
 
+def test_sparse_als_sweep_tall_factor(cp, ctx):
+    """A factor taller than one Gram row chunk (9000 rows): the Grams take
+    the chunked path with its fixed-order cross-block sum."""
+    dims, nnz, R = (9000, 50, 40), 40000, 6
+    rng = np.random.default_rng(17)
+    coords = synth.distinct_coords(rng, dims, nnz)
+    vals = rng.standard_normal(nnz).astype(np.float32)
+    u = synth.initial_guess(rng, dims, R)
+    X = O.SparseTensor(coords, vals, dims)
+    try:
+        ref = O.als_sweep(X, u, R)
+    except O.NotSPD:
+        pytest.skip("Gammabar singular for this draw")
+    t = cp.cp_tensor_coo(ctx, dims, dev(coords), dev(vals))
+    ud = dev(u)
+    cp.cp_als_sweep(ctx, t, R, ud, False)
+    cp.cp_ctx_sync(ctx)
+    assert rel(ud.cpu().numpy(), ref) <= 1e-8
+
+
 def test_two_way_laplacian_solve_reaches_eckart_young_optimum(cp, ctx):
     """Test Problem II with d = 1: f* = 1/2 sum of the s - R smallest squared
     eigenvalues 2 - 2 cos(k pi / (s + 1)) of the tridiagonal Laplacian."""
