@@ -203,11 +203,18 @@ typedef struct {
 void cp_ls_opts_default(cp_ls_opts* o);
 
 /* More-Thuente line search on phi(beta) = f(x0 + beta d), phi'(beta) =
- * g(x0 + beta d)^T d (Step III, Eq. linesearch), evaluating f and g with
- * cp_fg.  x0, g0, d: device (P); f0: f(x0).  On return x = x0 + stp d and
- * f, g are evaluated there (x, g device; f, stp, nfev, info host).  info as in
- * More-Thuente: 1 strong Wolfe met, 2 xtol, 3 maxfev, 4 stpmin, 5 stpmax,
- * 6 rounding; if g0^T d >= 0 returns CP_ERR_LINESEARCH.  Synchronous. */
+ * g(x0 + beta d)^T d (Step III, Eq. linesearch).  phi is a polynomial of
+ * degree 2N in beta (the model is multilinear in the factors); its
+ * coefficients come from one MTTKRP pass (the last mode against the 2^(N-1)
+ * mixes of x0's and d's factors) and factor Grams, and every trial evaluates
+ * phi and phi' from them; f and g are then evaluated with cp_fg at the final
+ * point.  x0, g0, d: device (P).  f0 = f(x0) and g0 are accepted for
+ * interface stability; the search starts from phi(0) and phi'(0) of the
+ * polynomial, equal to f0 and g0^T d up to rounding.  On return
+ * x = x0 + stp d and f, g are evaluated there (x, g device; f, stp, nfev,
+ * info host; nfev counts trials).  info as in More-Thuente: 1 strong Wolfe
+ * met, 2 xtol, 3 maxfev, 4 stpmin, 5 stpmax, 6 rounding; if phi'(0) >= 0
+ * returns CP_ERR_LINESEARCH.  Synchronous. */
 cp_status linesearch(cp_ctx* ctx, const cp_tensor* t, int R, const double* x0, double f0,
                      const double* g0, const double* d, const cp_ls_opts* opts, double* x,
                      double* f, double* g, double* stp, int* nfev, int* info,
@@ -226,9 +233,8 @@ typedef struct {
                        /* FP64 gradient meets tol (1 = on)                       */
   double mixed_tol_factor; /* mixed phase stops at tol * factor before polishing */
   cp_ls_opts ls;
-  int mixed_maxfev;    /* mixed precision phase: at most this many f/g        */
-                       /* evaluations per line search (f is resolved only to  */
-                       /* ~1e-9 relative there); FP64 iterations use ls.maxfev */
+  int mixed_maxfev;    /* mixed precision phase: at most this many trials    */
+                       /* per line search when > 0 (default 0: ls.maxfev)     */
 } cp_solve_opts;
 
 typedef struct {

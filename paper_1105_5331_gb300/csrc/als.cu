@@ -327,12 +327,12 @@ cp_status grams_jobs(cp_ctx* ctx, cudaStream_t s, unsigned* counter, int R, cons
   if (p.chunked) {
     // chunked jobs need every job's item layout to carry its chunk count;
     // jobs that fit one chunk still index as nch = 1
-    CP_TRY(ws_alloc(ctx, (void**)&p.partial, sizeof(double) * (size_t)items));
+    CP_TRY(ws_alloc_on(ctx, s, (void**)&p.partial, sizeof(double) * (size_t)items));
   }
   const unsigned blocks = (unsigned)std::max<int64_t>(1, (items + 7) / 8);
   gram_kernel<<<blocks, 256, 0, s>>>(p);
   CP_LAUNCH_CHECK();
-  if (p.partial) ws_free(ctx, p.partial);
+  if (p.partial) ws_free_on(ctx, s, p.partial);
   return CP_OK;
 }
 

@@ -25,7 +25,11 @@ cp_status cuda_fail(cudaError_t e, const char* what, const char* file, int line)
   return e == cudaErrorMemoryAllocation ? CP_ERR_OOM : CP_ERR_CUDA;
 }
 
-cp_status ws_alloc(cp_ctx* ctx, void** p, size_t bytes) {
+cp_status ws_alloc(cp_ctx* ctx, void** p, size_t bytes) { return ws_alloc_on(ctx, ctx->stream, p, bytes); }
+
+void ws_free(cp_ctx* ctx, void* p) { ws_free_on(ctx, ctx->stream, p); }
+
+cp_status ws_alloc_on(cp_ctx* ctx, cudaStream_t s, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (ctx->arena_on) {
     const size_t off = (ctx->arena_off + 255) & ~(size_t)255;
@@ -37,13 +41,13 @@ cp_status ws_alloc(cp_ctx* ctx, void** p, size_t bytes) {
     ctx->arena_off = off + bytes;
     return CP_OK;
   }
-  cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(workspace)", __FILE__, __LINE__);
   return CP_OK;
 }
 
-void ws_free(cp_ctx* ctx, void* p) {
-  if (p && !ctx->arena_on) cudaFreeAsync(p, ctx->stream);
+void ws_free_on(cp_ctx* ctx, cudaStream_t s, void* p) {
+  if (p && !ctx->arena_on) cudaFreeAsync(p, s);
 }
 
 cp_status read_status(cp_ctx* ctx) {
@@ -546,23 +550,28 @@ cp_status linesearch(cp_ctx* ctx, const cp_tensor* t, int R, const double* x0, d
   Layout L;
   L.set(t->N, t->dims, R);
   const int64_t P = L.P();
+  (void)f0;
+  (void)g0;
   double* sc = nullptr;
-  CP_TRY(ws_alloc(ctx, (void**)&sc, sizeof(double) * 8 + sizeof(MTState) + 64));
-  MTState* st = (MTState*)(((uintptr_t)(sc + 8) + 63) & ~(uintptr_t)63);
-  ctx->h_pinned[0] = f0;
-  CP_CUDA(cudaMemcpyAsync(sc, ctx->h_pinned, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  CP_TRY(dot(ctx, P, g0, d, sc + 1));
+  CP_TRY(ws_alloc(ctx, (void**)&sc, sizeof(double) * 40 + sizeof(MTState) + 64));
+  MTState* st = (MTState*)(((uintptr_t)(sc + 40) + 63) & ~(uintptr_t)63);
+  CP_TRY(ls_poly(ctx, t, L, x0, d, prec, o, st, sc + 4, nullptr, cudaGraphConditionalHandle{}, 0));
+  // the final point, evaluated directly
+  CP_TRY(axpy_scalar(ctx, P, x0, d, &st->stp_eval, x));
+  CP_TRY(fg_eval(ctx, t, L, x, sc, g, prec));
   MTState* hs = (MTState*)(ctx->h_pinned + 16);
-  CP_TRY(run_linesearch(ctx, t, L, x0, sc, sc + 1, d, o, x, sc + 2, g, sc + 3, st, prec, hs));
+  CP_CUDA(cudaMemcpyAsync(hs, st, sizeof(MTState), cudaMemcpyDeviceToHost, ctx->stream));
+  CP_CUDA(cudaMemcpyAsync(ctx->h_pinned, sc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CP_CUDA(cudaStreamSynchronize(ctx->stream));
   const MTState ms = *hs;
+  const double fx = ctx->h_pinned[0];
   ws_free(ctx, sc);
   CP_TRY(read_status(ctx));
   if (ms.info == -1) {
-    set_error("linesearch: g0^T d = %g is not negative", ms.g0);
+    set_error("linesearch: phi'(0) = g0^T d = %g is not negative", ms.g0);
     return CP_ERR_LINESEARCH;
   }
-  if (f) *f = ms.f;
+  if (f) *f = fx;
   if (stp) *stp = ms.stp_eval;
   if (nfev) *nfev = ms.nfev;
   if (info) *info = ms.info;
@@ -580,7 +589,7 @@ void cp_solve_opts_default(cp_solve_opts* o, int R) {
   o->polish = 1;
   o->mixed_tol_factor = 1.0;
   cp_ls_opts_default(&o->ls);
-  o->mixed_maxfev = 5;
+  o->mixed_maxfev = 0;
 }
 
 cp_status cp_solve(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* opts, double* u,

@@ -312,9 +312,11 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const dou
                      cp_precision prec, double* gd, MTState* st, cudaGraphConditionalHandle h,
                      int use_h);
 
-// Workspace (stream-ordered).
+// Workspace (stream-ordered on ctx->stream, or on s for the _on forms).
 cp_status ws_alloc(cp_ctx* ctx, void** p, size_t bytes);
 void ws_free(cp_ctx* ctx, void* p);
+cp_status ws_alloc_on(cp_ctx* ctx, cudaStream_t s, void** p, size_t bytes);
+void ws_free_on(cp_ctx* ctx, cudaStream_t s, void* p);
 
 cp_status read_status(cp_ctx* ctx);
 

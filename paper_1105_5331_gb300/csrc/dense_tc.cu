@@ -49,13 +49,20 @@ struct TcParams {
   int64_t ktiles;             // total contraction tiles
   int64_t ktiles_per_cta;
   int nother;
+  // Khatri-Rao variants: 1, or 2^nother when the other modes' factors are
+  // each either A (bit clear) or D (bit set): column v R + r of the result
+  // is T_(n) times prod_j (bit j of v ? D_j : A_j)[:, r]
+  int nvar;
+  int outc;                          // nvar * R output columns
   const float* tab[CP_MAX_N - 1];    // FP32 factors of the other modes, row stride R
+  const float* tabd[CP_MAX_N - 1];   // FP32 D factors (nvar > 1)
   int64_t dimo[CP_MAX_N - 1];
   uint32_t tab_soff[CP_MAX_N - 1];   // offsets (floats) of the tables in shared memory
+  uint32_t tabd_soff[CP_MAX_N - 1];
   uint32_t tab_cpy[CP_MAX_N - 1];    // bytes copied per table (multiple of 16)
-  uint32_t tab_bytes;                // sum of tab_cpy
+  uint32_t tab_bytes;                // sum of the copies
   int tab_smem;                      // 1: builders read the tables from shared memory
-  float* partial;             // [gridDim.x][I][R]
+  float* partial;             // [gridDim.x][I][outc]
   int* status;
   uint32_t ncols;             // TMEM columns allocated
 };
@@ -232,8 +239,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (p.tab_smem) {
         mbar_arrive_tx(tab_bar, p.tab_bytes);
 #pragma unroll
-        for (int j = 0; j < NO; ++j)
+        for (int j = 0; j < NO; ++j) {
           bulk_load(tab_saddr + 4u * p.tab_soff[j], p.tab[j], p.tab_cpy[j], tab_bar);
+          if (p.nvar > 1) bulk_load(tab_saddr + 4u * p.tabd_soff[j], p.tabd[j], p.tab_cpy[j], tab_bar);
+        }
       }
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
@@ -292,11 +301,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     // factor tables of the other modes (shared memory when they fit)
     const float* tabs = (const float*)(gbase + (tab_saddr - base));
     const float* tb[NO];
+    const float* tbd[NO];
     uint32_t dim32[NO];
 #pragma unroll
     for (int j = 0; j < NO; ++j) {
       dim32[j] = (uint32_t)p.dimo[j];
       tb[j] = p.tab_smem ? tabs + p.tab_soff[j] : p.tab[j];
+      tbd[j] = p.tab_smem ? tabs + p.tabd_soff[j] : p.tabd[j];
+    }
+    if (p.nvar > 1) {
+      // padding columns outc .. RP-1 stay zero in every stage
+      for (int s = 0; s < S; ++s) {
+        uint8_t* bhi = gbase + (size_t)s * stage_bytes + 2u * (uint32_t)p.ntm * kTileBytes;
+        uint8_t* blo = bhi + b_bytes;
+        for (int r = p.outc + half; r < p.RP; r += 2) {
+          const uint32_t off = (uint32_t)r * 128u + ((((uint32_t)kk >> 3) ^ ((uint32_t)r & 7u)) << 4) +
+                               ((uint32_t)kk & 7u) * 2u;
+          *(__nv_bfloat16*)(bhi + off) = __float2bfloat16_rn(0.f);
+          *(__nv_bfloat16*)(blo + off) = __float2bfloat16_rn(0.f);
+        }
+      }
     }
     const bool tabs_ok = !p.tab_smem || mbar_wait(tab_bar, 0u, p.status);
     for (int i = 0; i < nk; ++i) {
@@ -310,13 +334,47 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t kb64 = (kt0 + i) * kBK + kk;
         const bool in = kb64 < p.Kbar;
         const float* rows[NO];
+        uint32_t rowi[NO];
         uint32_t rem = (uint32_t)(in ? kb64 : 0);
 #pragma unroll
         for (int j = NO - 1; j >= 0; --j) {
           const uint32_t q = rem / dim32[j];
-          rows[j] = tb[j] + (size_t)(rem - q * dim32[j]) * p.R;
+          rowi[j] = rem - q * dim32[j];
+          rows[j] = tb[j] + (size_t)rowi[j] * p.R;
           rem = q;
         }
+        if (NO <= 3 && p.nvar > 1) {
+          // all 2^NO products of one rank r by doubling: after mode j the
+          // list index holds the A/D choice of modes 0..j in its bits
+          // (variants are built for up to 4-way tensors)
+          constexpr int V = 1 << (NO <= 3 ? NO : 0);
+          const int rh2 = (p.R + 1) >> 1;
+          const int r1 = min(p.R, (half + 1) * rh2);
+          for (int r = half * rh2; r < r1; ++r) {
+            float vals[V];
+            vals[0] = in ? 1.f : 0.f;
+#pragma unroll
+            for (int j = 0; j < (NO <= 3 ? NO : 0); ++j) {
+              const float a = rows[j][r];
+              const float dd = tbd[j][(size_t)rowi[j] * p.R + r];
+#pragma unroll
+              for (int q = 0; q < (1 << j); ++q) {
+                vals[q + (1 << j)] = vals[q] * dd;
+                vals[q] *= a;
+              }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              const float x = vals[v];
+              const __nv_bfloat16 h = __float2bfloat16_rn(x);
+              const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+              const uint32_t c = (uint32_t)(v * p.R + r);
+              const uint32_t off = c * 128u + ((((uint32_t)kk >> 3) ^ (c & 7u)) << 4) + ((uint32_t)kk & 7u) * 2u;
+              *(__nv_bfloat16*)(bhi + off) = h;
+              *(__nv_bfloat16*)(blo + off) = l;
+            }
+          }
+        } else
         for (int r = half * rh; r < (half + 1) * rh; ++r) {
           float v = 0.f;
           if (in && r < p.R) {
@@ -358,10 +416,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * p.RP + c), v);
         if (done && row < p.I) {
-          float* out = p.partial + ((int64_t)blockIdx.x * p.I + row) * p.R;
+          float* out = p.partial + ((int64_t)blockIdx.x * p.I + row) * p.outc;
 #pragma unroll
           for (int e = 0; e < 16; ++e)
-            if (c + e < p.R) out[c + e] = __uint_as_float(v[e]);
+            if (c + e < p.outc) out[c + e] = __uint_as_float(v[e]);
         }
       }
     }
@@ -541,11 +599,15 @@ static cp_status factors_f32(cp_ctx* ctx, const Layout& L, const double* u, floa
 // One mode's MTTKRP from FP32 factors (u32 at offsets o).
 // Launch the tensor-core kernel; partial sums (gx x I x R floats) in *parts.
 static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o,
-                                  int mode, Parts* parts) {
+                                  int mode, Parts* parts, const float* d32 = nullptr, int nvar = 1) {
   CP_TRY(ensure_planes(ctx, t, mode));
   const MixedMode& mm = tc_state(t)->mode[mode];
   const int R = L.R;
-  const int RP = std::max(16, (R + 15) / 16 * 16);
+  const int RP = std::max(16, (nvar * R + 15) / 16 * 16);
+  if (RP > 256 || (nvar > 1 && (nvar != (1 << (t->N - 1)) || !d32))) {
+    set_error("mixed MTTKRP: %d Khatri-Rao variants of rank %d not supported", nvar, R);
+    return CP_ERR_UNSUPPORTED;
+  }
   const int64_t I = t->dims[mode];
   const int64_t Kb = kbar(t, mode);
   TcParams p{};
@@ -553,6 +615,8 @@ static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, co
   p.Kbar = Kb;
   p.R = R;
   p.RP = RP;
+  p.nvar = nvar;
+  p.outc = nvar * R;
   const int64_t mtiles = (I + kBM - 1) / kBM;
   p.ntm = (int)std::min<int64_t>(mtiles, kMaxTilesPerCta);
   const int mgroups = (int)((mtiles + kMaxTilesPerCta - 1) / kMaxTilesPerCta);
@@ -568,6 +632,11 @@ static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, co
     p.tab_soff[p.nother] = (uint32_t)(tab_bytes / sizeof(float));
     p.tab_cpy[p.nother] = cpy;
     tab_bytes += cpy;
+    if (nvar > 1) {
+      p.tabd[p.nother] = d32 + o.off[m];
+      p.tabd_soff[p.nother] = (uint32_t)(tab_bytes / sizeof(float));
+      tab_bytes += cpy;
+    }
     ++p.nother;
   }
   p.tab_bytes = (uint32_t)tab_bytes;
@@ -588,7 +657,7 @@ static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, co
   p.ktiles_per_cta = (p.ktiles + target - 1) / target;
   const int gx = (int)((p.ktiles + p.ktiles_per_cta - 1) / p.ktiles_per_cta);
   float* partial = nullptr;
-  CP_TRY(ws_alloc(ctx, (void**)&partial, sizeof(float) * (size_t)gx * I * R));
+  CP_TRY(ws_alloc(ctx, (void**)&partial, sizeof(float) * (size_t)gx * I * p.outc));
   p.partial = partial;
   p.status = ctx->d_status;
   const size_t smem = (size_t)p.stages * stage_bytes + fixed + (p.tab_smem ? tab_bytes : 0);
@@ -614,6 +683,16 @@ static cp_status mttkrp_tc_core(cp_ctx* ctx, cp_tensor* t, const Layout& L, cons
 cp_status mttkrp_tc_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o, int mode,
                           Parts* out) {
   return mttkrp_tc_launch(ctx, t, L, u32, o, mode, out);
+}
+
+cp_status mttkrp_tc_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* a32, const float* d32,
+                             const F32Off& o, int mode, Parts* out) {
+  return mttkrp_tc_launch(ctx, t, L, a32, o, mode, out, d32, 1 << (L.N - 1));
+}
+
+bool tc_variants_supported(const Layout& L) {
+  if (L.N < 2 || L.N > 4) return false;
+  return ((1 << (L.N - 1)) * L.R + 15) / 16 * 16 <= 256;
 }
 
 cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, int mode, double* out) {

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) fg_finish_kernel(const FinishParams p) {
     const double fv = 0.5 * (p.norm2 - 2.0 * inner_sum + tr[0][0]);
     *p.f = fv;
     if (!isfinite(fv)) record_status(p.status, CP_ERR_NONFINITE);
-    if (p.d) *p.gd = gd_sum;
+    if (p.d && p.gd) *p.gd = gd_sum;
     if (p.st) {
       mtdev::mt_advance(p.st, p.f, p.gd);
       if (p.use_h) cudaGraphSetConditional(p.h, p.st->done ? 0u : 1u);
@@ -503,7 +503,7 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   fp.norm2 = t->norm2;
   fp.g = g;
   fp.f = f;
-  fp.d = d;
+  fp.d = gd ? d : nullptr;   // g . d only when asked for
   fp.gd = gd;
   fp.st = st;
   fp.h = h;

@@ -1,0 +1,406 @@
+// Step III of N-GMRES (Section 2.1, Eq. linesearch) on the exact polynomial
+// phi(beta) = f(ubar + beta d).
+//
+// The CP model is multilinear in the factors, so along the search line
+//   phi(beta) = 1/2 ||T||^2 - C(beta) + 1/2 E(beta)
+// with (Eq. fA written out along the line)
+//   C(beta) = sum_r T x_1 (a1_r + beta d1_r) ... x_N (aN_r + beta dN_r)
+//           = sum over subsets S of the modes of beta^|S| <T, rank-1 terms>,
+//   E(beta) = sum_{r,s} prod_n (A_n^T A_n + beta (A_n^T D_n + D_n^T A_n)
+//                               + beta^2 D_n^T D_n)[r, s],
+// a polynomial of degree 2N whose coefficients need one pass over T: the
+// MTTKRP of the last mode against the 2^(N-1) Khatri-Rao products in which
+// every other mode contributes either its A or its D factor, contracted with
+// A and D of the last mode, plus three Grams per mode.  The More-Thuente
+// search then evaluates phi and phi' = dphi/dbeta (= g(ubar + beta d) . d)
+// by Horner's rule at no further cost per trial, in one thread.  Every trial
+// sees the same function the paper's search sees; only the arithmetic that
+// produces its values differs.
+#include <algorithm>
+
+#include "cp_internal.cuh"
+#include "linesearch.cuh"
+#include "mt_device.cuh"
+#include "solver.cuh"
+
+namespace cpg {
+
+cp_status mttkrp_tc_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* a32, const float* d32,
+                             const F32Off& o, int mode, Parts* out);
+bool tc_variants_supported(const Layout& L);
+
+namespace {
+
+constexpr int kMaxVar = 1 << (CP_MAX_N - 1);
+constexpr int kMaxDeg = 2 * CP_MAX_N;
+
+struct CoefParams {
+  const void* pp[kMaxVar];      // partial sums of variant v
+  int count[kMaxVar];
+  int f32;
+  int col_stride;               // columns per row of the partials
+  int col_off[kMaxVar];         // first column of variant v
+  int nvar;
+  int64_t I;                    // rows of the last mode
+  int64_t chunks;               // 32-output chunks per variant
+  int R, N;
+  const double* Alast;
+  const double* Dlast;
+  const double* epoly;          // 2N + 1 coefficients of E(beta)
+  double norm2;
+  double* blk;                  // [2][gridDim.x]
+  double* poly;                 // 2N + 1 coefficients out
+  MTState* st;
+  cp_ls_opts o;
+  SolveCtl* ctl;                // nullable: solver counters
+  cudaGraphConditionalHandle h;
+  int use_h;
+  unsigned* counter;
+  int* status;
+};
+
+__device__ void mt_init(MTState& s, double f0, double g0, const cp_ls_opts& o) {
+  s.ftol = o.ftol;
+  s.gtol = o.gtol;
+  s.xtol = o.xtol;
+  s.stpmin = o.stpmin;
+  s.stpmax = o.stpmax;
+  s.maxfev = o.maxfev;
+  s.f0 = f0;
+  s.g0 = g0;
+  s.nfev = 0;
+  s.info = 0;
+  s.done = 0;
+  s.brackt = 0;
+  s.stage = 1;
+  s.lo_a = 0.0; s.lo_f = f0; s.lo_g = g0;
+  s.hi_a = 0.0; s.hi_f = f0; s.hi_g = g0;
+  s.width = o.stpmax - o.stpmin;
+  s.width1 = 2.0 * s.width;
+  s.stp = fmin(fmax(o.stp0, o.stpmin), o.stpmax);
+  s.imin = 0.0;
+  s.imax = s.stp + 4.0 * s.stp;
+  s.stp_eval = s.stp;
+  s.f = f0;
+  s.g = g0;
+  if (!(g0 < 0.0)) {
+    s.info = -1;
+    s.done = 1;
+    s.stp_eval = 0.0;
+  }
+}
+
+// E(beta) coefficients: thread per (r, s), the product of the N quadratics
+// of that entry; block sums, then the last block adds them in block order.
+__global__ void __launch_bounds__(256) ls_epoly_kernel(const double* __restrict__ grams, int N, int R,
+                                                       double* __restrict__ blk, double* __restrict__ e_out,
+                                                       unsigned* counter) {
+  __shared__ double epart[8][kMaxDeg + 1];
+  __shared__ bool is_last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int RR = R * R, D = 2 * N;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  double c[kMaxDeg + 1];
+#pragma unroll
+  for (int q = 0; q <= kMaxDeg; ++q) c[q] = 0.0;
+  if (k < RR) {
+    const int rr = k / R, ss = k - (k / R) * R;
+    c[0] = 1.0;
+    int deg = 0;
+    for (int n = 0; n < N; ++n) {
+      const double q0 = grams[(int64_t)(0 * N + n) * RR + k];
+      const double q1 = grams[(int64_t)(1 * N + n) * RR + k] + grams[(int64_t)(1 * N + n) * RR + ss * R + rr];
+      const double q2 = grams[(int64_t)(2 * N + n) * RR + k];
+      for (int q = deg + 2; q >= 0; --q) {
+        double t = q <= deg ? c[q] * q0 : 0.0;
+        if (q >= 1 && q - 1 <= deg) t = fma(c[q - 1], q1, t);
+        if (q >= 2) t = fma(c[q - 2], q2, t);
+        c[q] = t;
+      }
+      deg += 2;
+    }
+  }
+  for (int q = 0; q <= D; ++q) {
+    double s = c[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) epart[w][q] = s;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x <= D) {
+    double s = 0.0;
+    for (int ww = 0; ww < 8; ++ww) s += epart[ww][threadIdx.x];
+    blk[(int64_t)blockIdx.x * (kMaxDeg + 1) + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  if ((int)threadIdx.x <= D) {
+    double s = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&blk[(int64_t)b * (kMaxDeg + 1) + threadIdx.x]);
+    e_out[threadIdx.x] = s;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+__global__ void __launch_bounds__(256) ls_coef_kernel(const CoefParams p) {
+  __shared__ float redf[8][33];
+  __shared__ double redd[8][33];
+  __shared__ double sums[2 * kMaxVar];
+  __shared__ bool is_last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int R = p.R, N = p.N;
+  const int v = (int)(blockIdx.x / p.chunks);
+  const int64_t e = (blockIdx.x - (int64_t)v * p.chunks) * 32 + lane;
+  const int64_t nout = p.I * R;
+  const bool in = e < nout;
+  const int64_t i = in ? e / R : 0;
+  const int r = in ? (int)(e - i * R) : 0;
+  const int64_t nel = p.I * p.col_stride;
+  const int64_t idx = i * p.col_stride + p.col_off[v] + r;
+  // M_v[i][r]: warp w adds partials c = w, w + 8, ...; warp 0 the warp sums
+  if (p.f32) {
+    const float* q = (const float*)p.pp[v];
+    float s = 0.f;
+    if (in)
+#pragma unroll 4
+      for (int c = w; c < p.count[v]; c += 8) s += __ldcg(&q[(int64_t)c * nel + idx]);
+    redf[w][lane] = s;
+  } else {
+    const double* q = (const double*)p.pp[v];
+    double s = 0.0;
+    if (in)
+#pragma unroll 4
+      for (int c = w; c < p.count[v]; c += 8) s += __ldcg(&q[(int64_t)c * nel + idx]);
+    redd[w][lane] = s;
+  }
+  __syncthreads();
+  if (w == 0) {
+    double m = 0.0;
+    if (p.f32) {
+      float t = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) t += redf[q][lane];
+      m = (double)t;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) m += redd[q][lane];
+    }
+    double a = in ? m * p.Alast[e] : 0.0;
+    double b = in ? m * p.Dlast[e] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      p.blk[blockIdx.x] = a;
+      p.blk[gridDim.x + blockIdx.x] = b;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(p.counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // <M_v, A_last> and <M_v, D_last>: one warp per sum, lanes stride the chunks
+  for (int k = w; k < 2 * p.nvar; k += 8) {
+    const int vv = k >> 1, which = k & 1;
+    const double* src = p.blk + (which ? gridDim.x : 0) + (int64_t)vv * p.chunks;
+    double s = 0.0;
+    for (int64_t c = lane; c < p.chunks; c += 32) s += __ldcg(&src[c]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sums[k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double poly[kMaxDeg + 1];
+  for (int q = 0; q <= 2 * N; ++q) poly[q] = 0.5 * __ldcg(&p.epoly[q]);
+  // C(beta): variant v (bit m: mode m uses D) with the last mode's A adds to
+  // beta^popc(v), with its D to beta^(popc(v) + 1)
+  for (int vv = 0; vv < p.nvar; ++vv) {
+    const int k = __popc(vv);
+    poly[k] -= sums[2 * vv];
+    poly[k + 1] -= sums[2 * vv + 1];
+  }
+  poly[0] += 0.5 * p.norm2;
+  for (int q = 0; q <= 2 * N; ++q) p.poly[q] = poly[q];
+  // More-Thuente on phi, phi' by Horner's rule
+  MTState s;
+  mt_init(s, poly[0], poly[1], p.o);
+  while (!s.done) {
+    const double b = s.stp;
+    double f = poly[2 * N], g = 2 * N * poly[2 * N];
+    for (int q = 2 * N - 1; q >= 1; --q) {
+      f = fma(f, b, poly[q]);
+      g = fma(g, b, q * poly[q]);
+    }
+    f = fma(f, b, poly[0]);
+    mtdev::mt_advance(&s, &f, &g);
+  }
+  *p.st = s;
+  const bool accept = s.nfev > 0 && (s.info == 1 || s.f <= s.f0 + s.ftol * s.stp_eval * s.g0);
+  if (p.ctl) {
+    SolveCtl* c = p.ctl;
+    c->ls_evals += s.nfev;
+    if (s.info != 1) c->ls_failures += 1;
+    if (accept) {
+      c->accepts += 1;
+      c->fg_evals += 1;
+    }
+  }
+  if (p.use_h) cudaGraphSetConditional(p.h, accept ? 1u : 0u);
+  *p.counter = 0u;
+}
+
+// FP32 copies of a and d (same packing), for the tensor-core variants.
+__global__ void pair_f32_kernel(Layout L, const double* __restrict__ a, const double* __restrict__ d, F32Off o,
+                                float* __restrict__ a32, float* __restrict__ d32) {
+  const int64_t P = L.off[L.N];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
+    int n = 0;
+    while (n + 1 < L.N && e >= L.off[n + 1]) ++n;
+    const int64_t q = o.off[n] + (e - L.off[n]);
+    a32[q] = (float)a[e];
+    d32[q] = (float)d[e];
+  }
+}
+
+// Mixed iterates w_v (v < nvar): factor m < N-1 is d's when bit m of v is
+// set, else a's; the last factor is a's.  FP32 copies when w32 is given.
+__global__ void mix_kernel(Layout L, const double* __restrict__ a, const double* __restrict__ d, int nvar,
+                           double* __restrict__ w, F32Off o, int64_t p32, float* __restrict__ w32) {
+  const int64_t P = L.off[L.N];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
+    int n = 0;
+    while (n + 1 < L.N && e >= L.off[n + 1]) ++n;
+    const double av = a[e], dv = d[e];
+    for (int v = 0; v < nvar; ++v) {
+      const double x = (n < L.N - 1 && ((v >> n) & 1)) ? dv : av;
+      w[(int64_t)v * P + e] = x;
+      if (w32) w32[(int64_t)v * p32 + o.off[n] + (e - L.off[n])] = (float)x;
+    }
+  }
+}
+
+}  // namespace
+
+cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const double* base, const double* d,
+                  cp_precision prec, const cp_ls_opts& o, MTState* st, double* poly, SolveCtl* ctl,
+                  cudaGraphConditionalHandle h, int use_h) {
+  cp_tensor* t = const_cast<cp_tensor*>(t_in);
+  const int N = L.N, R = L.R, RR = R * R;
+  const int last = N - 1;
+  const int nvar = 1 << (N - 1);
+  if (N > CP_MAX_N) return CP_ERR_ARG;
+  const bool tc = t->kind == 0 && prec == CP_MIXED_BF16X3;
+  const bool tc_var = tc && tc_variants_supported(L);
+  F32Off o32{};
+  int64_t acc32 = 0;
+  for (int n = 0; n < N; ++n) {
+    o32.off[n] = acc32;
+    acc32 += (L.dims[n] * R + 3) / 4 * 4;
+  }
+  const int64_t P = L.P();
+  const unsigned eblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 4 * ctx->num_sms));
+  // Grams on the aux stream, overlapped with the MTTKRP
+  double* grams = nullptr;
+  const size_t eblocks_n = (size_t)((RR + 255) / 256);
+  CP_TRY(ws_alloc(ctx, (void**)&grams,
+                  sizeof(double) * (3 * (size_t)N * RR + (eblocks_n + 1) * (kMaxDeg + 1))));
+  double* eblk = grams + 3 * (size_t)N * RR;
+  double* epoly = eblk + eblocks_n * (kMaxDeg + 1);
+  CP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream));
+  CP_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+  {
+    GramJob jobs[kMaxGramJobs];
+    int nj = 0;
+    for (int n = 0; n < N; ++n) {
+      const double* A = base + L.off[n];
+      const double* D = d + L.off[n];
+      jobs[nj++] = GramJob{A, A, L.dims[n], grams + (size_t)(0 * N + n) * RR, 1};
+      jobs[nj++] = GramJob{A, D, L.dims[n], grams + (size_t)(1 * N + n) * RR, 0};
+      jobs[nj++] = GramJob{D, D, L.dims[n], grams + (size_t)(2 * N + n) * RR, 1};
+    }
+    CP_TRY(grams_jobs(ctx, ctx->aux, ctx->d_counter + 1, R, jobs, nj));
+    const unsigned eb = (unsigned)((RR + 255) / 256);
+    ls_epoly_kernel<<<eb, 256, 0, ctx->aux>>>(grams, N, R, eblk, epoly, ctx->d_counter + 1);
+    CP_LAUNCH_CHECK();
+  }
+  CP_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
+  // the variant MTTKRPs of the last mode
+  CoefParams cp{};
+  Parts parts[kMaxVar];
+  float *a32 = nullptr, *d32 = nullptr, *w32 = nullptr;
+  double* wv = nullptr;
+  if (tc_var) {
+    CP_TRY(ws_alloc(ctx, (void**)&a32, sizeof(float) * (size_t)acc32 + 64));
+    CP_TRY(ws_alloc(ctx, (void**)&d32, sizeof(float) * (size_t)acc32 + 64));
+    pair_f32_kernel<<<eblocks, 256, 0, ctx->stream>>>(L, base, d, o32, a32, d32);
+    CP_LAUNCH_CHECK();
+    Parts pt;
+    CP_TRY(mttkrp_tc_variants(ctx, t, L, a32, d32, o32, last, &pt));
+    for (int v = 0; v < nvar; ++v) {
+      parts[v] = pt;
+      cp.col_off[v] = v * R;
+    }
+    cp.col_stride = nvar * R;
+  } else {
+    CP_TRY(ws_alloc(ctx, (void**)&wv, sizeof(double) * (size_t)nvar * P));
+    if (tc) CP_TRY(ws_alloc(ctx, (void**)&w32, sizeof(float) * (size_t)nvar * acc32 + 64));
+    mix_kernel<<<eblocks, 256, 0, ctx->stream>>>(L, base, d, nvar, wv, o32, acc32, w32);
+    CP_LAUNCH_CHECK();
+    for (int v = 0; v < nvar; ++v) {
+      CP_TRY(mttkrp_parts(ctx, t, L, wv + (size_t)v * P, w32 ? w32 + (size_t)v * acc32 : nullptr, o32, last, prec,
+                          &parts[v]));
+      cp.col_off[v] = 0;
+    }
+    cp.col_stride = R;
+  }
+  for (int v = 0; v < nvar; ++v) {
+    cp.pp[v] = parts[v].p;
+    cp.count[v] = parts[v].count;
+  }
+  cp.f32 = parts[0].f32;
+  cp.nvar = nvar;
+  cp.I = L.dims[last];
+  cp.chunks = (L.dims[last] * R + 31) / 32;
+  cp.R = R;
+  cp.N = N;
+  cp.Alast = base + L.off[last];
+  cp.Dlast = d + L.off[last];
+  cp.epoly = epoly;
+  cp.norm2 = t->norm2;
+  cp.poly = poly;
+  cp.st = st;
+  cp.o = o;
+  cp.ctl = ctl;
+  cp.h = h;
+  cp.use_h = use_h;
+  cp.counter = ctx->d_counter;
+  cp.status = ctx->d_status;
+  const int64_t nblocks = (int64_t)nvar * cp.chunks;
+  CP_TRY(ws_alloc(ctx, (void**)&cp.blk, sizeof(double) * 2 * (size_t)nblocks + 16));
+  CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+  ls_coef_kernel<<<(unsigned)nblocks, 256, 0, ctx->stream>>>(cp);
+  CP_LAUNCH_CHECK();
+  ws_free(ctx, cp.blk);
+  if (tc_var) {
+    ws_free(ctx, const_cast<void*>(parts[0].p));
+  } else {
+    for (int v = 0; v < nvar; ++v) ws_free(ctx, const_cast<void*>(parts[v].p));
+  }
+  if (a32) ws_free(ctx, a32);
+  if (d32) ws_free(ctx, d32);
+  if (w32) ws_free(ctx, w32);
+  if (wv) ws_free(ctx, wv);
+  ws_free(ctx, grams);
+  return CP_OK;
+}
+
+}  // namespace cpg

@@ -109,19 +109,6 @@ __global__ void ctl_after_head_kernel(SolveCtl* c, const double* scal, cudaGraph
   cudaGraphSetConditional(restart, r ? 1u : 0u);
 }
 
-__global__ void ctl_ls_begin_kernel(const MTState* st, cudaGraphConditionalHandle ls) {
-  cudaGraphSetConditional(ls, st->done ? 0u : 1u);
-}
-
-__global__ void ctl_after_ls_kernel(SolveCtl* c, const MTState* st, cudaGraphConditionalHandle accept) {
-  c->fg_evals += st->nfev;
-  if (st->info != 1) c->ls_failures += 1;
-  const bool a = st->nfev > 0 && (st->info == 1 || st->f <= st->f0 + st->ftol * st->stp_eval * st->g0);
-  c->ls_evals += st->nfev;
-  if (a) c->accepts += 1;
-  cudaGraphSetConditional(accept, a ? 1u : 0u);
-}
-
 int64_t grid_for(cp_ctx* ctx, int64_t n) {
   const int64_t b = std::min<int64_t>((n + 255) / 256, 8 * (int64_t)ctx->num_sms);
   return std::max<int64_t>(b, 1);
@@ -185,6 +172,11 @@ cp_status SolverRes::create() {
   CP_CUDA(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
   CP_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
   CP_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+  for (int i = 0; i < 3; ++i) {
+    CP_CUDA(cudaStreamCreateWithFlags(&aux_side[i], cudaStreamNonBlocking));
+    CP_CUDA(cudaEventCreateWithFlags(&fork_side[i], cudaEventDisableTiming));
+    CP_CUDA(cudaEventCreateWithFlags(&join_side[i], cudaEventDisableTiming));
+  }
   CP_CUDA(cudaMallocHost(&h_pinned, sizeof(double) * 64));
   CP_CUDA(cudaMallocHost(&h_pinned_i, sizeof(int) * 64));
   CP_CUDA(cudaMallocHost(&hctl, sizeof(SolveCtl)));
@@ -202,6 +194,11 @@ void SolverRes::destroy() {
   if (aux) cudaStreamDestroy(aux);
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
+  for (int i = 0; i < 3; ++i) {
+    if (aux_side[i]) cudaStreamDestroy(aux_side[i]);
+    if (fork_side[i]) cudaEventDestroy(fork_side[i]);
+    if (join_side[i]) cudaEventDestroy(join_side[i]);
+  }
   if (h_pinned) cudaFreeHost(h_pinned);
   if (h_pinned_i) cudaFreeHost(h_pinned_i);
   if (hctl) cudaFreeHost(hctl);
@@ -258,7 +255,7 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   const size_t RR = (size_t)o.R * o.R;
   const int cap = o.w;
   const size_t bytes = sizeof(double) * (9 * (size_t)P + 2 * (size_t)cap * P + (size_t)Imax * o.R +
-                                         (size_t)L.N * RR + 16) +
+                                         (size_t)L.N * RR + 16 + 40) +
                        sizeof(MTState) + sizeof(SolveCtl) + 512;
   CP_CUDA(cudaMallocAsync(&base, bytes, sub.stream));
   double* p = (double*)base;
@@ -276,6 +273,7 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   m.M = p; p += (size_t)Imax * o.R;
   m.grams = p; p += (size_t)L.N * RR;
   m.scal = p; p += 16;
+  m.poly = p; p += 40;
   m.win = (int*)p; p += 8;
   uintptr_t q = ((uintptr_t)p + 63) & ~(uintptr_t)63;
   m.st = (MTState*)q;
@@ -302,10 +300,19 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
   unsigned long long k0 = g_launches.load();
   kcount = KernelCounts();
   auto with_stream = [&](cudaStream_t st, const std::function<cp_status()>& f) -> cp_status {
-    cudaStream_t keep = ctx->stream;
+    const cp_ctx keep = *ctx;
     ctx->stream = st;
+    for (int i = 0; i < 3; ++i)
+      if (side[i] == st) {
+        ctx->aux = res->aux_side[i];
+        ctx->ev_fork = res->fork_side[i];
+        ctx->ev_join = res->join_side[i];
+      }
     const cp_status r = f();
-    ctx->stream = keep;
+    ctx->stream = keep.stream;
+    ctx->aux = keep.aux;
+    ctx->ev_fork = keep.ev_fork;
+    ctx->ev_join = keep.ev_join;
     return r;
   };
   auto counted = [&](unsigned long long* slot, const std::function<cp_status()>& f) -> cp_status {
@@ -337,8 +344,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
           CP_TRY(ngmres_core(ctx, P, m.win, cap, m.U, m.G, m.ubar, m.gbar, o.eps, m.work, nullptr));
           CP_TRY(normalize_into(ctx, L, m.work, m.uhat, nullptr, nullptr, nullptr));
           CP_TRY(sub_vec(ctx, P, m.uhat, m.ubar, m.d));
-          CP_TRY(dot(ctx, P, m.gbar, m.d, m.scal + SLOPE));
-          return mt_start(ctx, m.st, m.scal + FBAR, m.scal + SLOPE, lso);
+          return dot(ctx, P, m.gbar, m.d, m.scal + SLOPE);
         }));
         cudaGraphConditionalHandle h_restart;
         CP_TRY(new_handle(side[0], 0, &h_restart));
@@ -356,29 +362,20 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
                 return window_update(ctx, m.win, cap, true, P, m.u, m.g, m.U, m.G);
               });
             }
-            cudaGraphConditionalHandle h_ls, h_acc;
-            CP_TRY(new_handle(side[1], 0, &h_ls));
+            // Step III: More-Thuente on the polynomial phi(beta) (one MTTKRP
+            // pass), which also sets `accept`
+            cudaGraphConditionalHandle h_acc;
             CP_TRY(new_handle(side[1], 0, &h_acc));
-            ctl_ls_begin_kernel<<<1, 1, 0, side[1]>>>(m.st, h_ls);
-            CP_LAUNCH_CHECK();
-            kcount.ls_fixed += 1;
-            CP_TRY(add_conditional(side[1], side[2], h_ls, cudaGraphCondTypeWhile, 1, [&](int) -> cp_status {
-              return with_stream(side[2], [&]() -> cp_status {
-                // x = ubar + stp d; f, g at x; phi' = g . d; one More-Thuente
-                // update that also sets `ls` -- prep, MTTKRPs, finish
-                return counted(&kcount.ls_eval, [&]() -> cp_status {
-                  return fg_eval_ex(ctx, t, L, m.ubar, m.d, &m.st->stp, m.x, m.scal + FX, m.gx, pr,
-                                    m.scal + GD, m.st, h_ls, 1);
-                });
-              });
+            CP_TRY(counted(&kcount.ls_fixed, [&]() -> cp_status {
+              return ls_poly(ctx, t, L, m.ubar, m.d, pr, lso, m.st, m.poly, m.ctl, h_acc, 1);
             }));
-            ctl_after_ls_kernel<<<1, 1, 0, side[1]>>>(m.ctl, m.st, h_acc);
-            CP_LAUNCH_CHECK();
-            kcount.ls_fixed += 1;
             return add_conditional(side[1], side[2], h_acc, cudaGraphCondTypeIf, 2, [&](int ab) -> cp_status {
               return with_stream(side[2], [&]() -> cp_status {
                 return counted(ab == 0 ? &kcount.accept : &kcount.reject, [&]() -> cp_status {
                   if (ab == 0) {
+                    // x = ubar + beta d, f and g there
+                    CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, m.d, &m.st->stp_eval, m.x, m.scal + FX, m.gx, pr,
+                                      nullptr, nullptr, cudaGraphConditionalHandle{}, 0));
                     CP_TRY(normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr));
                     CP_TRY(dcopy(ctx, 1, m.scal + FX, m.scal + F));
                   } else {

@@ -25,7 +25,7 @@ struct KernelCounts {
 };
 
 struct SolverMem {
-  double *u, *g, *ubar, *gbar, *uhat, *d, *x, *gx, *work, *M, *grams, *scal, *U, *G;
+  double *u, *g, *ubar, *gbar, *uhat, *d, *x, *gx, *work, *M, *grams, *scal, *poly, *U, *G;
   int* win;
   MTState* st;
   SolveCtl* ctl;
@@ -42,6 +42,10 @@ struct SolverRes {
   unsigned* d_counter = nullptr;
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // one aux stream and event pair per nested capture level (a stream that
+  // joined a capture stays in it until that capture ends)
+  cudaStream_t aux_side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fork_side[3] = {nullptr, nullptr, nullptr}, join_side[3] = {nullptr, nullptr, nullptr};
   double* h_pinned = nullptr;
   int* h_pinned_i = nullptr;
   SolveCtl* hctl = nullptr;
