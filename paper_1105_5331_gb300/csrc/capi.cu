@@ -68,9 +68,8 @@ cp_status read_status(cp_ctx* ctx) {
 cp_status dense_build(cp_ctx* ctx, cp_tensor* t, const void* d_data);
 cp_status solve_impl(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* o, double* u_user,
                      bool user_on_device, cp_solve_report* rep);
-cp_status als_sweep_inplace(cp_ctx* ctx, const cp_tensor* t, const Layout& L, double* u,
-                            double* grams, double* M, cp_precision prec);
-cp_status grams_all(cp_ctx* ctx, const Layout& L, const double* u, double* grams);
+
+
 void tensor_free_coo(cp_tensor* t);
 void tensor_free_mixed(cp_tensor* t, cudaStream_t s);
 
@@ -447,7 +446,7 @@ cp_status cp_als_sweep(cp_ctx* ctx, const cp_tensor* t, int R, double* u, int no
     double* tmp = nullptr;
     CP_TRY(ws_alloc(ctx, (void**)&tmp, sizeof(double) * (size_t)L.P()));
     CP_CUDA(cudaMemcpyAsync(tmp, u, sizeof(double) * L.P(), cudaMemcpyDeviceToDevice, ctx->stream));
-    CP_TRY(normalize_into(ctx, L, tmp, u, nullptr, nullptr, nullptr));
+    CP_TRY(normalize_into(ctx, L, tmp, u, nullptr, nullptr, nullptr, grams));
     ws_free(ctx, tmp);
   }
   ws_free(ctx, grams);

@@ -238,18 +238,11 @@ cp_status coo_build(cp_ctx* ctx, cp_tensor* t, const int64_t* d_coords, const fl
 cp_status mttkrp_any(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, int mode,
                      double* out, cp_precision prec);
 
-// Grams G_m = A_m^T A_m of all modes into grams (N x R x R).
-cp_status grams_all(cp_ctx* ctx, const Layout& L, const double* u, double* grams);
-// One ALS mode update: A_n <- M Gammabar^-1 (Gammabar from grams), then
-// refresh grams[n] from the new A_n.
-cp_status als_mode_solve(cp_ctx* ctx, const Layout& L, double* u, int mode, const double* M,
-                         double* grams);
-// f and g from M^(n) (all modes, packed like u) and grams.
-cp_status fg_assemble(cp_ctx* ctx, const Layout& L, const double* u, const double* M_all,
-                      const double* grams, double norm2, double* f, double* g);
-// Normalise src (and gsrc) into dst (and gdst); lambda (R) optional.
+// Normalise src (and gsrc) into dst (and gdst); lambda (R) optional.  With
+// grams (N x R x R, the Grams of src) the column norms come from their
+// diagonals instead of a pass over src.
 cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double* dst,
-                         const double* gsrc, double* gdst, double* lambda);
+                         const double* gsrc, double* gdst, double* lambda, const double* grams = nullptr);
 
 // Window-indexed N-GMRES Step II.  win (device) = {start, m}; window row j
 // (oldest first) is ring slot (start + j) % cap.
@@ -280,10 +273,6 @@ cp_status fg_eval(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double
 // tensor-core path, may be null otherwise).
 cp_status mttkrp_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, const float* u32,
                        const F32Off& o32, int mode, cp_precision prec, Parts* out);
-struct MTState;
-// One ALS sweep in place on u with fused kernels (1 + 2N launches).
-cp_status als_sweep_fused(cp_ctx* ctx, const cp_tensor* t, const Layout& L, double* u,
-                          cp_precision prec);
 // Gram jobs out = X^T Y (X, Y: I x R row-major; sym: X == Y, both triangles
 // written), one launch on stream s; counter: a zeroed last-block counter
 // owned by s.
@@ -304,13 +293,11 @@ cp_status grams_of(cp_ctx* ctx, cudaStream_t s, unsigned* counter, const Layout&
 // the Grams of the updated factors (grams_valid: it holds u's on entry).
 cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t, const Layout& L, double* u, cp_precision prec,
                        double* grams, bool grams_valid);
-// Fused f/g at x = base (+ (*stp) d when d is given; x written).  With d, also
-// g . d into gd; with st, one More-Thuente update (and, with use_h, the graph
-// condition h set to "not done").
+// Fused f/g at x = base (+ (*stp) d when d is given; x written); with gd
+// (and d) also g . d.
 cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* base,
                      const double* d, const double* stp, double* x, double* f, double* g,
-                     cp_precision prec, double* gd, MTState* st, cudaGraphConditionalHandle h,
-                     int use_h);
+                     cp_precision prec, double* gd, double* grams_out = nullptr);
 
 // Workspace (stream-ordered on ctx->stream, or on s for the _on forms).
 cp_status ws_alloc(cp_ctx* ctx, void** p, size_t bytes);

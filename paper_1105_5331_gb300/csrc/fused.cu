@@ -6,8 +6,7 @@
 //   MTTKRP   per mode, split-K partial sums (tcgen05 / FP64 / sparse)
 //   finish   per 32 gradient entries: M = sum of the partials (fixed order),
 //            G = A Gammabar - M; <A^(N), M^(N)> and g . d as block partials;
-//            the last block forms f = 1/2(||T||^2 - 2<T,A> + sum Gamma), g . d,
-//            and (in a line search) advances the More-Thuente state.
+//            the last block forms f = 1/2(||T||^2 - 2<T,A> + sum Gamma) and g . d.
 //
 // "Last block" reductions: each block writes its partial, fences, and bumps a
 // per-stream counter; the block that sees the final count reads all partials
@@ -15,8 +14,6 @@
 #include <algorithm>
 
 #include "cp_internal.cuh"
-#include "dev_linalg.cuh"
-#include "mt_device.cuh"
 
 namespace cpg {
 
@@ -119,9 +116,6 @@ struct FinishParams {
   double* f;
   const double* d;        // nullable: also g . d
   double* gd;
-  MTState* st;            // nullable: advance the line search with (f, g . d)
-  cudaGraphConditionalHandle h;
-  int use_h;
   double* blk;            // 2 x gridDim.x block partials
   unsigned* counter;
   int* status;
@@ -149,9 +143,12 @@ __global__ void __launch_bounds__(256) fg_finish_kernel(const FinishParams p) {
   double s = 0.0;
   if (e < nel) {
     if (pt.f32) {
+      // FP32 partial sums of the mixed MTTKRP are added in FP32
       const float* q = (const float*)pt.p;
+      float sf = 0.f;
 #pragma unroll 4
-      for (int c = w; c < pt.count; c += 8) s += (double)__ldcg(&q[(int64_t)c * nel + e]);
+      for (int c = w; c < pt.count; c += 8) sf += __ldcg(&q[(int64_t)c * nel + e]);
+      s = (double)sf;
     } else {
       const double* q = (const double*)pt.p;
 #pragma unroll 4
@@ -221,219 +218,11 @@ __global__ void __launch_bounds__(256) fg_finish_kernel(const FinishParams p) {
     *p.f = fv;
     if (!isfinite(fv)) record_status(p.status, CP_ERR_NONFINITE);
     if (p.d && p.gd) *p.gd = gd_sum;
-    if (p.st) {
-      mtdev::mt_advance(p.st, p.f, p.gd);
-      if (p.use_h) cudaGraphSetConditional(p.h, p.st->done ? 0u : 1u);
-    }
     *p.counter = 0u;
   }
 }
 
-// ALS mode update (Section 2.3, Eq. foopt) fused with its inputs and outputs:
-// M rows from the MTTKRP partial sums, A_n = M Gammabar^-1 (Cholesky with
-// one ridge retry), the new rows in FP64 (and FP32 for the next modes'
-// tensor-core MTTKRPs), and the new Gram A_n^T A_n (last-block reduction).
-struct AlsParams {
-  Layout L;
-  int n;
-  Parts parts;
-  double* u;              // A_n updated in place
-  float* u32;             // nullable: FP32 copy updated too
-  F32Off o32;
-  double* grams;          // all modes; mode n refreshed
-  double* part;           // [S][R*R] Gram partials
-  int S;
-  unsigned* counter;
-  int* status;
-};
-
-constexpr int kAlsRows = 16;
-
-__global__ void __launch_bounds__(256) als_fused_kernel(const AlsParams p) {
-  __shared__ double Lc[CP_MAX_R * CP_MAX_R];
-  __shared__ double Mt[kAlsRows * CP_MAX_R];
-  __shared__ double red[8][33];
-  __shared__ int flag;
-  __shared__ bool is_last;
-  const int R = p.L.R, N = p.L.N, RR = R * R, n = p.n;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t I = p.L.dims[n];
-  const int64_t chunk = (I + p.S - 1) / p.S;
-  const int64_t rb = (int64_t)blockIdx.x * chunk;
-  const int64_t re = min(I, rb + chunk);
-  const int64_t nel = I * R;
-  // Gammabar^(n) and its Cholesky factor (identical in every block)
-  auto build = [&]() {
-    for (int k = threadIdx.x; k < RR; k += blockDim.x) {
-      double v = 1.0;
-      for (int m = 0; m < N; ++m)
-        if (m != n) v *= p.grams[(int64_t)m * RR + k];
-      Lc[k] = v;
-    }
-  };
-  build();
-  if (threadIdx.x == 0) flag = 0;
-  __syncthreads();
-  bool ok = chol_block(Lc, R, &flag);
-  if (!ok) {
-    __syncthreads();
-    build();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double tr = 0.0;
-      for (int r = 0; r < R; ++r) tr += Lc[r * R + r];
-      for (int r = 0; r < R; ++r) Lc[r * R + r] += 1e-12 * tr / R;
-      flag = 0;
-    }
-    __syncthreads();
-    ok = chol_block(Lc, R, &flag);
-    if (!ok && threadIdx.x == 0 && blockIdx.x == 0) record_status(p.status, CP_ERR_NOT_SPD);
-  }
-  double acc[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) acc[k] = 0.0;
-  double* An = p.u + p.L.off[n];
-  for (int64_t r0 = rb; r0 < re; r0 += kAlsRows) {
-    const int nr = (int)min((int64_t)kAlsRows, re - r0);
-    // M rows: warp w adds partials c = w, w + 8, ... for 32 entries at a time
-    for (int e0 = 0; e0 < nr * R; e0 += 32) {
-      const int64_t e = r0 * R + e0 + lane;
-      double s = 0.0;
-      if (e0 + lane < nr * R) {
-        if (p.parts.f32) {
-          const float* q = (const float*)p.parts.p;
-#pragma unroll 4
-          for (int c = w; c < p.parts.count; c += 8) s += (double)__ldcg(&q[(int64_t)c * nel + e]);
-        } else {
-          const double* q = (const double*)p.parts.p;
-#pragma unroll 4
-          for (int c = w; c < p.parts.count; c += 8) s += __ldcg(&q[(int64_t)c * nel + e]);
-        }
-      }
-      red[w][lane] = s;
-      __syncthreads();
-      if (w == 0 && e0 + lane < nr * R) {
-        double t = 0.0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) t += red[q][lane];
-        Mt[e0 + lane] = t;
-      }
-      __syncthreads();
-    }
-    // forward / back substitution, one thread per row
-    if (ok && (int)threadIdx.x < nr) {
-      double y[CP_MAX_R];
-      const double* mrow = Mt + threadIdx.x * R;
-      for (int r = 0; r < R; ++r) {
-        double v = mrow[r];
-        for (int s2 = 0; s2 < r; ++s2) v -= Lc[r * R + s2] * y[s2];
-        y[r] = v / Lc[r * R + r];
-      }
-      for (int r = R - 1; r >= 0; --r) {
-        double v = y[r];
-        for (int s2 = r + 1; s2 < R; ++s2) v -= Lc[s2 * R + r] * y[s2];
-        y[r] = v / Lc[r * R + r];
-      }
-      const int64_t i = r0 + threadIdx.x;
-      for (int r = 0; r < R; ++r) {
-        An[i * R + r] = y[r];
-        Mt[threadIdx.x * R + r] = y[r];
-        if (p.u32) p.u32[p.o32.off[n] + i * R + r] = (float)y[r];
-      }
-    }
-    __syncthreads();
-    // Gram contribution of the new rows (Mt now holds them)
-    if (ok) {
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int e = threadIdx.x + k * blockDim.x;
-        if (e < RR) {
-          const int r = e / R, s2 = e - (e / R) * R;
-          double t = acc[k];
-          for (int q = 0; q < nr; ++q) t = fma(Mt[q * R + r], Mt[q * R + s2], t);
-          acc[k] = t;
-        }
-      }
-    }
-    __syncthreads();
-  }
-  double* out = p.part + (int64_t)blockIdx.x * RR;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const int e = threadIdx.x + k * blockDim.x;
-    if (e < RR) out[e] = acc[k];
-  }
-  if (!last_block(p.counter, gridDim.x, &is_last)) return;
-  if (ok) {
-    for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-      double s = 0.0;
-      for (int c = 0; c < p.S; ++c) s += __ldcg(&p.part[(int64_t)c * RR + e]);
-      p.grams[(int64_t)n * RR + e] = s;
-    }
-  }
-  if (threadIdx.x == 0) *p.counter = 0u;
-}
-
 }  // namespace
-
-// One ALS sweep (Section 2.3) in place on u with the fused kernels: prep
-// (Grams, FP32 copy), then per mode the MTTKRP partial sums and the fused
-// mode update.
-cp_status als_sweep_fused(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, double* u, cp_precision prec) {
-  cp_tensor* t = const_cast<cp_tensor*>(t_in);
-  const int R = L.R, N = L.N, RR = R * R;
-  const bool want_f32 = t->kind == 0 && prec == CP_MIXED_BF16X3;
-  F32Off o32{};
-  int64_t acc32 = 0, Imax = 1;
-  for (int n = 0; n < N; ++n) {
-    o32.off[n] = acc32;
-    acc32 += (L.dims[n] * R + 3) / 4 * 4;
-    Imax = std::max(Imax, L.dims[n]);
-  }
-  const int S = (int)std::max<int64_t>(1, std::min<int64_t>((Imax + 15) / 16, 2 * (int64_t)ctx->num_sms));
-  float* u32 = nullptr;
-  double *grams = nullptr, *gpart = nullptr;
-  if (want_f32) CP_TRY(ws_alloc(ctx, (void**)&u32, sizeof(float) * (size_t)acc32 + 64));
-  CP_TRY(ws_alloc(ctx, (void**)&grams, sizeof(double) * (size_t)N * RR));
-  CP_TRY(ws_alloc(ctx, (void**)&gpart, sizeof(double) * (size_t)N * S * RR));
-  PrepParams pp;
-  pp.L = L;
-  pp.base = u;
-  pp.d = nullptr;
-  pp.stp = nullptr;
-  pp.x = nullptr;
-  pp.x32 = u32;
-  pp.o32 = o32;
-  pp.part = gpart;
-  pp.grams = grams;
-  pp.S = S;
-  pp.counter = ctx->d_counter;
-  prep_kernel<<<dim3(S, N), 256, 0, ctx->stream>>>(pp);
-  CP_LAUNCH_CHECK();
-  for (int n = 0; n < N; ++n) {
-    Parts pt;
-    CP_TRY(mttkrp_parts(ctx, t, L, u, u32, o32, n, prec, &pt));
-    AlsParams ap;
-    ap.L = L;
-    ap.n = n;
-    ap.parts = pt;
-    ap.u = u;
-    ap.u32 = u32;
-    ap.o32 = o32;
-    ap.grams = grams;
-    ap.part = gpart;
-    ap.S = (int)std::max<int64_t>(1, std::min<int64_t>((L.dims[n] + 15) / 16, 2 * (int64_t)ctx->num_sms));
-    ap.counter = ctx->d_counter;
-    ap.status = ctx->d_status;
-    als_fused_kernel<<<ap.S, 256, 0, ctx->stream>>>(ap);
-    CP_LAUNCH_CHECK();
-    ws_free(ctx, const_cast<void*>(pt.p));
-  }
-  ws_free(ctx, gpart);
-  ws_free(ctx, grams);
-  if (u32) ws_free(ctx, u32);
-  return CP_OK;
-}
 
 cp_status mttkrp_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, const float* u32,
                        const F32Off& o32, int mode, cp_precision prec, Parts* out) {
@@ -450,7 +239,7 @@ cp_status mttkrp_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double*
 
 cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const double* base, const double* d,
                      const double* stp, double* x, double* f, double* g, cp_precision prec, double* gd,
-                     MTState* st, cudaGraphConditionalHandle h, int use_h) {
+                     double* grams_out) {
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int R = L.R, N = L.N, RR = R * R;
   const double* u = d ? x : base;
@@ -469,7 +258,10 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   double* grams = nullptr;
   double* gpart = nullptr;
   if (want_f32) CP_TRY(ws_alloc(ctx, (void**)&x32, sizeof(float) * (size_t)acc32 + 64));
-  CP_TRY(ws_alloc(ctx, (void**)&grams, sizeof(double) * (size_t)N * RR));
+  if (grams_out)
+    grams = grams_out;
+  else
+    CP_TRY(ws_alloc(ctx, (void**)&grams, sizeof(double) * (size_t)N * RR));
   CP_TRY(ws_alloc(ctx, (void**)&gpart, sizeof(double) * (size_t)N * S * RR));
   PrepParams pp;
   pp.L = L;
@@ -505,9 +297,6 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   fp.f = f;
   fp.d = gd ? d : nullptr;   // g . d only when asked for
   fp.gd = gd;
-  fp.st = st;
-  fp.h = h;
-  fp.use_h = use_h;
   fp.counter = ctx->d_counter;
   fp.status = ctx->d_status;
   CP_TRY(ws_alloc(ctx, (void**)&fp.blk, sizeof(double) * 2 * (size_t)chunks + 16));
@@ -516,7 +305,7 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   ws_free(ctx, fp.blk);
   for (int n = first; n < N; ++n) ws_free(ctx, const_cast<void*>(fp.parts[n].p));
   ws_free(ctx, gpart);
-  ws_free(ctx, grams);
+  if (!grams_out) ws_free(ctx, grams);
   if (x32) ws_free(ctx, x32);
   return CP_OK;
 }

@@ -17,11 +17,6 @@ struct MTState {
   int maxfev, nfev, info, done, brackt, stage;
 };
 
-cp_status mt_start(cp_ctx* ctx, MTState* st, const double* f0, const double* g0,
-                   const cp_ls_opts& o);
-cp_status mt_iterate(cp_ctx* ctx, MTState* st, const double* f, const double* g);
-cp_status mt_iterate_cond(cp_ctx* ctx, MTState* st, const double* f, const double* g,
-                          cudaGraphConditionalHandle h);
 struct SolveCtl;
 // Line search on the polynomial phi(beta) = f(base + beta d) (degree 2N):
 // one MTTKRP pass for its coefficients (Grams on ctx->aux), then the whole
@@ -32,9 +27,6 @@ struct SolveCtl;
 cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* base, const double* d,
                   cp_precision prec, const cp_ls_opts& o, MTState* st, double* poly, SolveCtl* ctl,
                   cudaGraphConditionalHandle h, int use_h);
-cp_status run_linesearch(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* x0,
-                         const double* f0, const double* slope, const double* d,
-                         const cp_ls_opts& o, double* x, double* fx, double* gx, double* gd,
-                         MTState* st, cp_precision prec, MTState* host_out);
+
 
 }  // namespace cpg

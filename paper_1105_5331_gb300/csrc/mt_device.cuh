@@ -1,5 +1,14 @@
-// More-Thuente step logic as device functions (shared by the line-search
-// kernels and the fused f/g finish kernel).
+// The More-Thuente line search the paper uses for Step III (Section 2.1,
+// Eq. linesearch; Section 2.4 parameters; method of J. J. More and
+// D. J. Thuente, ACM TOMS 20(3), 1994), as device functions:
+//  * sufficient decrease  phi(a) <= phi(0) + ftol a phi'(0),
+//    curvature            |phi'(a)| <= gtol |phi'(0)|;
+//  * stage 1 works on psi(a) = phi(a) - phi(0) - ftol a phi'(0) until a trial
+//    has psi <= 0 and phi' >= min(ftol, gtol) phi'(0);
+//  * trial selection by the four cases of cubic / quadratic / secant
+//    interpolation, the interval update rules, extrapolation into
+//    [a_t + 1.1 (a_t - a_l), a_t + 4 (a_t - a_l)] while unbracketed, and
+//    bisection when a bracketed interval fails to shrink by 0.66 in two trials.
 #pragma once
 
 #include "linesearch.cuh"

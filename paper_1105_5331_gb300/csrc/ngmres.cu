@@ -15,7 +15,6 @@
 #include <algorithm>
 
 #include "cp_internal.cuh"
-#include "dev_linalg.cuh"
 
 namespace cpg {
 
@@ -88,80 +87,134 @@ __global__ void ngmres_dots_kernel(const double* __restrict__ G, const int* __re
   }
 }
 
-__global__ void ngmres_solve_kernel(const double* __restrict__ part, int nparts, int nout_max,
-                                    const int* __restrict__ win, double eps, double* __restrict__ alpha,
-                                    int* status) {
-  __shared__ double H[CP_MAX_W * CP_MAX_W];
-  __shared__ double rhs[CP_MAX_W];
-  __shared__ double dmax;
+// 1/d by Newton's iteration from an FP32 reciprocal (FP64 divide outside
+// the FP32 exponent range).
+__device__ __forceinline__ double recip_nr(double d) {
+  const double ad = fabs(d);
+  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+  double r = (double)__frcp_rn((float)d);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Block b adds the per-CTA partial sums of outputs 32b .. 32b+31 (warp w
+// takes CTAs w, w + 8, ...; fixed order).  The last block assembles
+// H = P^T P + delta I and the right-hand side -P^T gbar and solves by
+// Gauss-Jordan elimination on [H | rhs] (no pivoting: H is SPD, and a
+// non-positive pivot reports CP_ERR_NOT_SPD with alpha = 0).
+__global__ void __launch_bounds__(256) ngmres_reduce_solve_kernel(const double* __restrict__ part, int nparts,
+                                                                  int nout_max, const int* __restrict__ win,
+                                                                  double eps, double* __restrict__ sums,
+                                                                  double* __restrict__ alpha, unsigned* counter,
+                                                                  int* status) {
+  __shared__ double red[8][33];
+  __shared__ double Ab[CP_MAX_W * (CP_MAX_W + 1)];
+  __shared__ double piv, dmax;
   __shared__ int flag;
+  __shared__ bool is_last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int m = win[1];
   const int npairs = m * (m + 1) / 2;
   const int nout = npairs + m;
-  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * nout_max + o];
-    if (o < npairs) {
+  const int o = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (o < nout)
+    for (int c = w; c < nparts; c += 8) s += __ldcg(&part[(int64_t)c * nout_max + o]);
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && o < nout) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += red[q][lane];
+    sums[o] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const int W = m + 1;   // row stride of [H | rhs]
+  for (int q = threadIdx.x; q < nout; q += blockDim.x) {
+    const double v = __ldcg(&sums[q]);
+    if (q < npairs) {
       int j, l;
-      pair_of(o, m, &j, &l);
-      H[j * m + l] = s;
-      H[l * m + j] = s;
+      pair_of(q, m, &j, &l);
+      Ab[j * W + l] = v;
+      Ab[l * W + j] = v;
     } else {
-      rhs[o - npairs] = -s;
+      Ab[(q - npairs) * W + m] = -v;
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double d = 0.0;
-    for (int j = 0; j < m; ++j) d = fmax(d, H[j * m + j]);
+    for (int j = 0; j < m; ++j) d = fmax(d, Ab[j * W + j]);
     dmax = d;
     flag = 0;
     if (d > 0.0)
-      for (int j = 0; j < m; ++j) H[j * m + j] += eps * d;
+      for (int j = 0; j < m; ++j) Ab[j * W + j] += eps * d;
   }
   __syncthreads();
   if (!(dmax > 0.0)) {
     for (int j = threadIdx.x; j < m; j += blockDim.x) alpha[j] = 0.0;
+    if (threadIdx.x == 0) *counter = 0u;
     return;
   }
-  if (!chol_block(H, m, &flag)) {
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = Ab[k * W + k];
+      if (!(d > 0.0) || !isfinite(d)) flag = 1;
+      else piv = recip_nr(d);
+    }
+    __syncthreads();
+    if (flag) break;
+    const double pinv = piv;
+    // eliminate column k from every other row (columns > k and the rhs)
+    for (int e = threadIdx.x; e < m * (W - k - 1); e += blockDim.x) {
+      const int i = e / (W - k - 1), j = k + 1 + e % (W - k - 1);
+      if (i != k) Ab[i * W + j] = fma(-Ab[i * W + k] * pinv, Ab[k * W + j], Ab[i * W + j]);
+    }
+    __syncthreads();
+  }
+  if (flag) {
     if (threadIdx.x == 0) record_status(status, CP_ERR_NOT_SPD);
     for (int j = threadIdx.x; j < m; j += blockDim.x) alpha[j] = 0.0;
-    return;
+  } else {
+    // the system is now diagonal: alpha_j = rhs_j / H_jj
+    for (int j = threadIdx.x; j < m; j += blockDim.x) alpha[j] = Ab[j * W + m] * recip_nr(Ab[j * W + j]);
   }
-  if (threadIdx.x == 0) {
-    double y[CP_MAX_W];
-    for (int r = 0; r < m; ++r) {
-      double v = rhs[r];
-      for (int s = 0; s < r; ++s) v -= H[r * m + s] * y[s];
-      y[r] = v / H[r * m + r];
-    }
-    for (int r = m - 1; r >= 0; --r) {
-      double v = y[r];
-      for (int s = r + 1; s < m; ++s) v -= H[s * m + r] * y[s];
-      y[r] = v / H[r * m + r];
-    }
-    for (int r = 0; r < m; ++r) alpha[r] = y[r];
-  }
+  if (threadIdx.x == 0) *counter = 0u;
 }
 
 __global__ void ngmres_combine_kernel(const double* __restrict__ U, const int* __restrict__ win, int cap,
                                       int64_t P, const double* __restrict__ ubar,
                                       const double* __restrict__ alpha, double* __restrict__ uhat) {
   __shared__ double a[CP_MAX_W];
+  __shared__ int slot[CP_MAX_W];
   const int start = win[0];
   const int m = win[1];
-  for (int j = threadIdx.x; j < m; j += blockDim.x) a[j] = alpha[j];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    a[j] = alpha[j];
+    slot[j] = (start + j) % cap;
+  }
   __syncthreads();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
        k += (int64_t)gridDim.x * blockDim.x) {
     const double ub = ubar[k];
-    double acc = 0.0;
-    for (int j = 0; j < m; ++j) {
-      const int slot = (start + j) % cap;
-      acc += a[j] * (ub - U[(int64_t)slot * P + k]);
+    // four independent chains over the window, added in a fixed order
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+    int j = 0;
+    for (; j + 3 < m; j += 4) {
+      c0 = fma(a[j], ub - U[(int64_t)slot[j] * P + k], c0);
+      c1 = fma(a[j + 1], ub - U[(int64_t)slot[j + 1] * P + k], c1);
+      c2 = fma(a[j + 2], ub - U[(int64_t)slot[j + 2] * P + k], c2);
+      c3 = fma(a[j + 3], ub - U[(int64_t)slot[j + 3] * P + k], c3);
     }
-    uhat[k] = ub + acc;
+    for (; j < m; ++j) c0 = fma(a[j], ub - U[(int64_t)slot[j] * P + k], c0);
+    uhat[k] = ub + ((c0 + c1) + (c2 + c3));
   }
 }
 
@@ -200,17 +253,21 @@ cp_status ngmres_core(cp_ctx* ctx, int64_t P, const int* win, int cap, const dou
     return CP_ERR_ARG;
   }
   const int nout_max = cap * (cap + 1) / 2 + cap;
-  int64_t nb = std::min<int64_t>((P + 255) / 256, 2 * (int64_t)ctx->num_sms);
+  // one CTA per SM (at most): the P (m(m+1)/2 + m) FP64 FMAs of the dots
+  // spread over the whole chip
+  int64_t nb = std::min<int64_t>((P + kTile - 1) / kTile, (int64_t)ctx->num_sms);
   nb = std::max<int64_t>(nb, 1);
   const int64_t chunk = (P + nb - 1) / nb;
   nb = std::max<int64_t>((P + chunk - 1) / chunk, 1);
   double* part = nullptr;
   double* a = alpha;
-  CP_TRY(ws_alloc(ctx, (void**)&part, sizeof(double) * ((size_t)nb * nout_max + CP_MAX_W)));
-  if (!a) a = part + (size_t)nb * nout_max;
+  CP_TRY(ws_alloc(ctx, (void**)&part, sizeof(double) * ((size_t)nb * nout_max + nout_max + CP_MAX_W)));
+  double* sums = part + (size_t)nb * nout_max;
+  if (!a) a = sums + nout_max;
   ngmres_dots_kernel<<<(unsigned)nb, 256, 0, ctx->stream>>>(G, win, cap, P, gbar, chunk, nout_max, part);
   CP_LAUNCH_CHECK();
-  ngmres_solve_kernel<<<1, 256, 0, ctx->stream>>>(part, (int)nb, nout_max, win, eps, a, ctx->d_status);
+  ngmres_reduce_solve_kernel<<<(unsigned)((nout_max + 31) / 32), 256, 0, ctx->stream>>>(
+      part, (int)nb, nout_max, win, eps, sums, a, ctx->d_counter, ctx->d_status);
   CP_LAUNCH_CHECK();
   int64_t cb = std::min<int64_t>((P + 255) / 256, 8 * (int64_t)ctx->num_sms);
   ngmres_combine_kernel<<<(unsigned)std::max<int64_t>(cb, 1), 256, 0, ctx->stream>>>(U, win, cap, P, ubar, a,

@@ -37,17 +37,6 @@
 
 namespace cpg {
 
-// One ALS sweep in place on u (grams must hold the Grams of u on entry and
-// hold those of the result on exit); M is I_max x R scratch.
-cp_status als_sweep_inplace(cp_ctx* ctx, const cp_tensor* t, const Layout& L, double* u,
-                            double* grams, double* M, cp_precision prec) {
-  for (int n = 0; n < L.N; ++n) {
-    CP_TRY(mttkrp_any(ctx, t, L, u, n, M, prec));
-    CP_TRY(als_mode_solve(ctx, L, u, n, M, grams));
-  }
-  return CP_OK;
-}
-
 namespace {
 
 enum { F = 0, FBAR = 1, FX = 2, SLOPE = 3, GD = 4, GG = 5, NSCAL = 8 };
@@ -339,7 +328,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
         CP_TRY(counted(&kcount.head, [&]() -> cp_status {
           CP_TRY(dcopy(ctx, P, m.u, m.work));
           CP_TRY(als_sweep_v2(ctx, t, L, m.work, pr, m.grams, false));
-          CP_TRY(normalize_into(ctx, L, m.work, m.ubar, nullptr, nullptr, nullptr));
+          CP_TRY(normalize_into(ctx, L, m.work, m.ubar, nullptr, nullptr, nullptr, m.grams));
           CP_TRY(fg_eval(ctx, t, L, m.ubar, m.scal + FBAR, m.gbar, pr));
           CP_TRY(ngmres_core(ctx, P, m.win, cap, m.U, m.G, m.ubar, m.gbar, o.eps, m.work, nullptr));
           CP_TRY(normalize_into(ctx, L, m.work, m.uhat, nullptr, nullptr, nullptr));
@@ -375,8 +364,8 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
                   if (ab == 0) {
                     // x = ubar + beta d, f and g there
                     CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, m.d, &m.st->stp_eval, m.x, m.scal + FX, m.gx, pr,
-                                      nullptr, nullptr, cudaGraphConditionalHandle{}, 0));
-                    CP_TRY(normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr));
+                                      nullptr, m.grams));
+                    CP_TRY(normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr, m.grams));
                     CP_TRY(dcopy(ctx, 1, m.scal + FX, m.scal + F));
                   } else {
                     CP_TRY(dcopy(ctx, P, m.ubar, m.u));
