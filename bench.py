@@ -490,10 +490,13 @@ def run_mttkrp_only(args):
     stream.synchronize()
     t = cp.cp_tensor_coo(ctx, prob.dims, coords, vals) if sparse else cp.cp_tensor_dense(ctx, T)
     res = {}
+    fam = cp.TIMER_COO if sparse else (cp.TIMER_TC if prec == cp.CP_MIXED_BF16X3 else cp.TIMER_F64)
     for n in range(len(prob.dims)):
         out = torch.empty(prob.dims[n] * Rk, dtype=torch.float64, device=dev)
         ms = []
         for k in range(args.reps + 1):
+            if k == 1:
+                cp.cp_ctx_timer_enable(ctx, True)
             with torch.cuda.stream(stream):
                 flush.fill_(float(k))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -503,7 +506,15 @@ def run_mttkrp_only(args):
             e1.synchronize()
             if k > 0:
                 ms.append(e0.elapsed_time(e1))
+        kms, kl = cp.cp_ctx_timer_read(ctx, fam)
+        cp.cp_ctx_timer_enable(ctx, False)
         res[f"mode{n}_ms"] = sum(ms) / len(ms)
+        res[f"mode{n}_kernel_ms"] = kms / max(kl, 1)
+        if not sparse and prec == cp.CP_MIXED_BF16X3:
+            K = 1
+            for d in prob.dims:
+                K *= d
+            res[f"mode{n}_kernel_GBps"] = 4.0 * K / (res[f"mode{n}_kernel_ms"] / 1e3) / 1e9
         if sparse:
             nnz = prob.coords.shape[0]
             sf = 4 if args.prec == "mixed" else 8

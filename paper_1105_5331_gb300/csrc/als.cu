@@ -225,7 +225,8 @@ struct UpdParams {
   const double* Xinv;
   const int* ok;
   double* An;            // I x R, updated in place
-  float* An32;           // nullable
+  float* An32;           // nullable: padded FP32 rows (stride rs)
+  int rs;
 };
 
 __global__ void __launch_bounds__(256) als_update_kernel(const UpdParams p) {
@@ -291,20 +292,31 @@ __global__ void __launch_bounds__(256) als_update_kernel(const UpdParams p) {
     const double a = s0 + s1;
     const int64_t idx = (rb + q) * R + r;
     p.An[idx] = a;
-    if (p.An32) p.An32[idx] = (float)a;
+    if (p.An32) p.An32[(rb + q) * p.rs + r] = (float)a;
   }
 }
 
-__global__ void f64_to_f32_kernel(Layout L, const double* __restrict__ u, F32Off o, float* __restrict__ out) {
-  const int64_t P = L.off[L.N];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
+// Padded FP32 copy: every float of the layout is written (padding as 0).
+__global__ void f32_copy_kernel(Layout L, const double* __restrict__ u, F32Off o, int64_t total,
+                                float* __restrict__ out) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     int n = 0;
-    while (n + 1 < L.N && e >= L.off[n + 1]) ++n;
-    out[o.off[n] + (e - L.off[n])] = (float)u[e];
+    while (n + 1 < L.N && q >= o.off[n + 1]) ++n;
+    const int64_t within = q - o.off[n];
+    const int64_t i = within / o.rs;
+    const int r = (int)(within - i * o.rs);
+    out[q] = r < L.R ? (float)u[L.off[n] + i * L.R + r] : 0.f;
   }
 }
 
 }  // namespace
+
+cp_status f32_copy(cp_ctx* ctx, const Layout& L, const double* u, const F32Off& o, int64_t total, float* out) {
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4 * ctx->num_sms));
+  f32_copy_kernel<<<blocks, 256, 0, ctx->stream>>>(L, u, o, total, out);
+  CP_LAUNCH_CHECK();
+  return CP_OK;
+}
 
 cp_status grams_jobs(cp_ctx* ctx, cudaStream_t s, unsigned* counter, int R, const GramJob* jobs, int njobs) {
   if (njobs < 1 || njobs > kMaxGramJobs) {
@@ -354,24 +366,15 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int R = L.R, N = L.N, RR = R * R;
   const bool want_f32 = t->kind == 0 && prec == CP_MIXED_BF16X3;
-  F32Off o32{};
   int64_t acc32 = 0;
-  for (int n = 0; n < N; ++n) {
-    o32.off[n] = acc32;
-    acc32 += (L.dims[n] * R + 3) / 4 * 4;
-  }
+  const F32Off o32 = f32_layout(L, &acc32);
   float* u32 = nullptr;
   double* Xinv = nullptr;
   int* ok = nullptr;
   if (want_f32) CP_TRY(ws_alloc(ctx, (void**)&u32, sizeof(float) * (size_t)acc32 + 64));
   CP_TRY(ws_alloc(ctx, (void**)&Xinv, sizeof(double) * (size_t)RR + 64));
   ok = (int*)(Xinv + RR);
-  if (want_f32) {
-    const int64_t P = L.P();
-    f64_to_f32_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 4 * ctx->num_sms)), 256, 0,
-                        ctx->stream>>>(L, u, o32, u32);
-    CP_LAUNCH_CHECK();
-  }
+  if (want_f32) CP_TRY(f32_copy(ctx, L, u, o32, acc32, u32));
   if (!grams_valid) CP_TRY(grams_of(ctx, ctx->stream, ctx->d_counter, L, u, 0, N, grams));
   const int rows = std::max(1, 32 / R);
   for (int n = 0; n < N; ++n) {
@@ -396,6 +399,7 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
     up.ok = ok;
     up.An = u + L.off[n];
     up.An32 = u32 ? u32 + o32.off[n] : nullptr;
+    up.rs = o32.rs;
     als_update_kernel<<<(unsigned)((L.dims[n] + rows - 1) / rows), 256, 0, ctx->stream>>>(up);
     CP_LAUNCH_CHECK();
     ws_free(ctx, const_cast<void*>(pt.p));

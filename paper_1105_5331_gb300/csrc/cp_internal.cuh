@@ -83,11 +83,25 @@ struct Parts {
   int f32 = 0;
 };
 
-// Offsets (in floats) of the factors inside an FP32 copy of an iterate;
-// multiples of 4 so each factor starts 16-byte aligned.
+// FP32 copy of an iterate for the tensor-core MTTKRP: factor n starts at
+// float offset off[n]; its rows are rs = R rounded up to 4 floats apart (16
+// bytes, for vector loads) with zero padding.
 struct F32Off {
   int64_t off[CP_MAX_N];
+  int rs;
 };
+
+inline F32Off f32_layout(const Layout& L, int64_t* total) {
+  F32Off o{};
+  o.rs = (L.R + 3) & ~3;
+  int64_t acc = 0;
+  for (int n = 0; n < L.N; ++n) {
+    o.off[n] = acc;
+    acc += L.dims[n] * o.rs;
+  }
+  *total = acc;
+  return o;
+}
 
 inline FactorPtrs factor_ptrs(const Layout& L, const double* u) {
   FactorPtrs f;
@@ -298,6 +312,9 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t, const Layout& L, double*
 cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* base,
                      const double* d, const double* stp, double* x, double* f, double* g,
                      cp_precision prec, double* gd, double* grams_out = nullptr);
+
+// Padded FP32 copy (f32_layout) of the packed FP64 iterate u, on ctx->stream.
+cp_status f32_copy(cp_ctx* ctx, const Layout& L, const double* u, const F32Off& o, int64_t total, float* out);
 
 // Workspace (stream-ordered on ctx->stream, or on s for the _on forms).
 cp_status ws_alloc(cp_ctx* ctx, void** p, size_t bytes);

@@ -36,7 +36,7 @@ constexpr int kBM = 128;                 // rows per M tile = TMEM lanes
 constexpr int kBK = 64;                  // contraction elements per tile (128 bytes of bf16)
 constexpr int kThreads = 192;
 constexpr uint32_t kTileBytes = kBM * kBK * 2;   // one plane, one M tile: 16 KB
-constexpr int kMaxTilesPerCta = 2;       // M tiles handled by one CTA
+constexpr int kMaxTilesPerCta = 1;       // M tiles handled by one CTA
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
 constexpr int kMaxDynSmem = 227 * 1024;
 
@@ -62,6 +62,7 @@ struct TcParams {
   uint32_t tab_cpy[CP_MAX_N - 1];    // bytes copied per table (multiple of 16)
   uint32_t tab_bytes;                // sum of the copies
   int tab_smem;                      // 1: builders read the tables from shared memory
+  int rs;                            // table row stride in floats (R rounded up to 4)
   float* partial;             // [gridDim.x][I][outc]
   int* status;
   uint32_t ncols;             // TMEM columns allocated
@@ -296,30 +297,38 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------- Khatri-Rao tile builders
     const int t = threadIdx.x - 64;            // 0..127
     const int kk = t & (kBK - 1);              // contraction element within the tile
-    const int half = t >> 6;                   // which half of the padded ranks
-    const int rh = p.RP >> 1;
-    // factor tables of the other modes (shared memory when they fit)
-    const float* tabs = (const float*)(gbase + (tab_saddr - base));
-    const float* tb[NO];
-    const float* tbd[NO];
+    const int half = t >> 6;                   // which half of the column groups
+    const int rs = p.rs;                       // FP32 table row stride (multiple of 4)
     uint32_t dim32[NO];
 #pragma unroll
-    for (int j = 0; j < NO; ++j) {
-      dim32[j] = (uint32_t)p.dimo[j];
-      tb[j] = p.tab_smem ? tabs + p.tab_soff[j] : p.tab[j];
-      tbd[j] = p.tab_smem ? tabs + p.tabd_soff[j] : p.tabd[j];
-    }
+    for (int j = 0; j < NO; ++j) dim32[j] = (uint32_t)p.dimo[j];
+    // four consecutive ranks of table row `ro` (float offset) of mode j: 16-byte
+    // loads from shared memory (or through the read-only path when the tables
+    // stay in global memory)
+    auto ld4 = [&](int j, bool dtab, uint32_t ro) -> float4 {
+      if (p.tab_smem) {
+        float4 v;
+        const uint32_t a = tab_saddr + 4u * ((dtab ? p.tabd_soff[j] : p.tab_soff[j]) + ro);
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "r"(a));
+        return v;
+      }
+      return __ldg(reinterpret_cast<const float4*>((dtab ? p.tabd[j] : p.tab[j]) + ro));
+    };
+    // column c of the B tile, SW128 K-major: hi = bf16(x), lo = bf16(x - hi)
+    auto put = [&](uint8_t* bhi, uint8_t* blo, uint32_t c, float x) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+      const uint32_t off = c * 128u + ((((uint32_t)kk >> 3) ^ (c & 7u)) << 4) + ((uint32_t)kk & 7u) * 2u;
+      *(__nv_bfloat16*)(bhi + off) = h;
+      *(__nv_bfloat16*)(blo + off) = l;
+    };
     if (p.nvar > 1) {
       // padding columns outc .. RP-1 stay zero in every stage
       for (int s = 0; s < S; ++s) {
         uint8_t* bhi = gbase + (size_t)s * stage_bytes + 2u * (uint32_t)p.ntm * kTileBytes;
-        uint8_t* blo = bhi + b_bytes;
-        for (int r = p.outc + half; r < p.RP; r += 2) {
-          const uint32_t off = (uint32_t)r * 128u + ((((uint32_t)kk >> 3) ^ ((uint32_t)r & 7u)) << 4) +
-                               ((uint32_t)kk & 7u) * 2u;
-          *(__nv_bfloat16*)(bhi + off) = __float2bfloat16_rn(0.f);
-          *(__nv_bfloat16*)(blo + off) = __float2bfloat16_rn(0.f);
-        }
+        for (int r = p.outc + half; r < p.RP; r += 2) put(bhi, bhi + b_bytes, (uint32_t)r, 0.f);
       }
     }
     const bool tabs_ok = !p.tab_smem || mbar_wait(tab_bar, 0u, p.status);
@@ -333,61 +342,66 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint8_t* blo = bhi + b_bytes;
         const int64_t kb64 = (kt0 + i) * kBK + kk;
         const bool in = kb64 < p.Kbar;
-        const float* rows[NO];
-        uint32_t rowi[NO];
+        uint32_t rowo[NO];                     // float offset of each factor row
         uint32_t rem = (uint32_t)(in ? kb64 : 0);
 #pragma unroll
         for (int j = NO - 1; j >= 0; --j) {
           const uint32_t q = rem / dim32[j];
-          rowi[j] = rem - q * dim32[j];
-          rows[j] = tb[j] + (size_t)rowi[j] * p.R;
+          rowo[j] = (rem - q * dim32[j]) * (uint32_t)rs;
           rem = q;
         }
         if (NO <= 3 && p.nvar > 1) {
-          // all 2^NO products of one rank r by doubling: after mode j the
-          // list index holds the A/D choice of modes 0..j in its bits
-          // (variants are built for up to 4-way tensors)
+          // all 2^NO products of four ranks by doubling: after mode j the list
+          // index holds the A/D choice of modes 0..j in its bits (variants
+          // are built for up to 4-way tensors); variant v fills columns
+          // v rs .. v rs + rs - 1
           constexpr int V = 1 << (NO <= 3 ? NO : 0);
-          const int rh2 = (p.R + 1) >> 1;
-          const int r1 = min(p.R, (half + 1) * rh2);
-          for (int r = half * rh2; r < r1; ++r) {
-            float vals[V];
-            vals[0] = in ? 1.f : 0.f;
+          const int G = rs >> 2, gh = (G + 1) >> 1;
+          const int g1 = min(G, (half + 1) * gh);
+          for (int g = half * gh; g < g1; ++g) {
+            float4 vals[V];
+            vals[0] = in ? make_float4(1.f, 1.f, 1.f, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < (NO <= 3 ? NO : 0); ++j) {
-              const float a = rows[j][r];
-              const float dd = tbd[j][(size_t)rowi[j] * p.R + r];
+              const float4 a = ld4(j, false, rowo[j] + 4u * g);
+              const float4 dd = ld4(j, true, rowo[j] + 4u * g);
 #pragma unroll
               for (int q = 0; q < (1 << j); ++q) {
-                vals[q + (1 << j)] = vals[q] * dd;
-                vals[q] *= a;
+                float4& lo = vals[q];
+                float4& up = vals[q + (1 << j)];
+                up = make_float4(lo.x * dd.x, lo.y * dd.y, lo.z * dd.z, lo.w * dd.w);
+                lo = make_float4(lo.x * a.x, lo.y * a.y, lo.z * a.z, lo.w * a.w);
               }
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-              const float x = vals[v];
-              const __nv_bfloat16 h = __float2bfloat16_rn(x);
-              const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-              const uint32_t c = (uint32_t)(v * p.R + r);
-              const uint32_t off = c * 128u + ((((uint32_t)kk >> 3) ^ (c & 7u)) << 4) + ((uint32_t)kk & 7u) * 2u;
-              *(__nv_bfloat16*)(bhi + off) = h;
-              *(__nv_bfloat16*)(blo + off) = l;
+              const uint32_t c = (uint32_t)(v * rs + 4 * g);
+              put(bhi, blo, c, vals[v].x);
+              put(bhi, blo, c + 1, vals[v].y);
+              put(bhi, blo, c + 2, vals[v].z);
+              put(bhi, blo, c + 3, vals[v].w);
             }
           }
-        } else
-        for (int r = half * rh; r < (half + 1) * rh; ++r) {
-          float v = 0.f;
-          if (in && r < p.R) {
-            v = rows[0][r];
+        } else {
+          // columns in groups of four; groups past the table rows are zero
+          const int gh = p.RP >> 3;
+#pragma unroll 2
+          for (int g = half * gh; g < (half + 1) * gh; ++g) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (in && 4 * g < rs) {
+              v = ld4(0, false, rowo[0] + 4u * g);
 #pragma unroll
-            for (int j = 1; j < NO; ++j) v *= rows[j][r];
+              for (int j = 1; j < NO; ++j) {
+                const float4 w = ld4(j, false, rowo[j] + 4u * g);
+                v = make_float4(v.x * w.x, v.y * w.y, v.z * w.z, v.w * w.w);
+              }
+            }
+            const uint32_t c = 4u * g;
+            put(bhi, blo, c, v.x);
+            put(bhi, blo, c + 1, v.y);
+            put(bhi, blo, c + 2, v.z);
+            put(bhi, blo, c + 3, v.w);
           }
-          const __nv_bfloat16 h = __float2bfloat16_rn(v);
-          const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-          const uint32_t off = (uint32_t)r * 128u + ((((uint32_t)kk >> 3) ^ ((uint32_t)r & 7u)) << 4) +
-                               ((uint32_t)kk & 7u) * 2u;
-          *(__nv_bfloat16*)(bhi + off) = h;
-          *(__nv_bfloat16*)(blo + off) = l;
         }
       }
       fence_proxy_async();
@@ -446,17 +460,6 @@ __global__ void split_planes_kernel(const TT* __restrict__ src, int64_t I, int64
     const __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
     hi[o] = h;
     lo[o] = l;
-  }
-}
-
-// FP32 copy of every factor of u; factor n starts at float offset off32[n]
-// (multiples of 4, so each factor is 16-byte aligned for bulk copies).
-__global__ void u_to_f32_kernel(Layout L, const double* __restrict__ u, F32Off o, float* __restrict__ out) {
-  const int64_t P = L.off[L.N];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
-    int n = 0;
-    while (n + 1 < L.N && e >= L.off[n + 1]) ++n;
-    out[o.off[n] + (e - L.off[n])] = (float)u[e];
   }
 }
 
@@ -581,19 +584,12 @@ cp_status prepare_mixed(cp_ctx* ctx, cp_tensor* t) {
   return CP_OK;
 }
 
-// FP32 copy of the factors of u (one launch for all modes).
+// Padded FP32 copy of the factors of u (one launch for all modes).
 static cp_status factors_f32(cp_ctx* ctx, const Layout& L, const double* u, float** buf, F32Off* o) {
-  int64_t acc = 0;
-  for (int n = 0; n < L.N; ++n) {
-    o->off[n] = acc;
-    acc += (L.dims[n] * L.R + 3) / 4 * 4;
-  }
-  CP_TRY(ws_alloc(ctx, (void**)buf, sizeof(float) * (size_t)acc + 64));
-  const int64_t P = L.P();
-  u_to_f32_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 8 * ctx->num_sms)), 256, 0,
-                    ctx->stream>>>(L, u, *o, *buf);
-  CP_LAUNCH_CHECK();
-  return CP_OK;
+  int64_t total = 0;
+  *o = f32_layout(L, &total);
+  CP_TRY(ws_alloc(ctx, (void**)buf, sizeof(float) * (size_t)total + 64));
+  return f32_copy(ctx, L, u, *o, total, *buf);
 }
 
 // One mode's MTTKRP from FP32 factors (u32 at offsets o).
@@ -603,7 +599,8 @@ static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, co
   CP_TRY(ensure_planes(ctx, t, mode));
   const MixedMode& mm = tc_state(t)->mode[mode];
   const int R = L.R;
-  const int RP = std::max(16, (nvar * R + 15) / 16 * 16);
+  const int outc = nvar > 1 ? nvar * o.rs : R;
+  const int RP = std::max(16, (outc + 15) / 16 * 16);
   if (RP > 256 || (nvar > 1 && (nvar != (1 << (t->N - 1)) || !d32))) {
     set_error("mixed MTTKRP: %d Khatri-Rao variants of rank %d not supported", nvar, R);
     return CP_ERR_UNSUPPORTED;
@@ -616,7 +613,8 @@ static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, co
   p.R = R;
   p.RP = RP;
   p.nvar = nvar;
-  p.outc = nvar * R;
+  p.outc = outc;
+  p.rs = o.rs;
   const int64_t mtiles = (I + kBM - 1) / kBM;
   p.ntm = (int)std::min<int64_t>(mtiles, kMaxTilesPerCta);
   const int mgroups = (int)((mtiles + kMaxTilesPerCta - 1) / kMaxTilesPerCta);
@@ -626,7 +624,7 @@ static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, co
   p.nother = 0;
   for (int m = 0; m < t->N; ++m) {
     if (m == mode) continue;
-    const uint32_t cpy = (uint32_t)(((size_t)t->dims[m] * R * sizeof(float) + 15) / 16 * 16);
+    const uint32_t cpy = (uint32_t)((size_t)t->dims[m] * o.rs * sizeof(float));   // multiple of 16
     p.tab[p.nother] = u32 + o.off[m];
     p.dimo[p.nother] = t->dims[m];
     p.tab_soff[p.nother] = (uint32_t)(tab_bytes / sizeof(float));
@@ -692,7 +690,7 @@ cp_status mttkrp_tc_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L, const f
 
 bool tc_variants_supported(const Layout& L) {
   if (L.N < 2 || L.N > 4) return false;
-  return ((1 << (L.N - 1)) * L.R + 15) / 16 * 16 <= 256;
+  return ((1 << (L.N - 1)) * ((L.R + 3) & ~3) + 15) / 16 * 16 <= 256;
 }
 
 cp_status mttkrp_dense_mixed(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, int mode, double* out) {

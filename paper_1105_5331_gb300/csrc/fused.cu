@@ -74,9 +74,14 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepParams p) {
         v = v + a * p.d[gi];
         p.x[gi] = v;
       }
-      if (p.x32) p.x32[p.o32.off[m] + r0 * R + e] = (float)v;
+      if (p.x32) p.x32[p.o32.off[m] + (r0 + e / R) * p.o32.rs + e % R] = (float)v;
       tile[e] = v;
     }
+    if (p.x32)   // zero padding of the FP32 rows
+      for (int e = threadIdx.x; e < nr * (p.o32.rs - R); e += blockDim.x) {
+        const int q = e / (p.o32.rs - R);
+        p.x32[p.o32.off[m] + (r0 + q) * p.o32.rs + R + (e - q * (p.o32.rs - R))] = 0.f;
+      }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -245,12 +250,8 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   const double* u = d ? x : base;
   const bool want_f32 = t->kind == 0 && prec == CP_MIXED_BF16X3;
   // prep: x, FP32 copy, Grams
-  F32Off o32{};
   int64_t acc32 = 0;
-  for (int n = 0; n < N; ++n) {
-    o32.off[n] = acc32;
-    acc32 += (L.dims[n] * R + 3) / 4 * 4;
-  }
+  const F32Off o32 = f32_layout(L, &acc32);
   int64_t Imax = 1;
   for (int n = 0; n < N; ++n) Imax = std::max(Imax, L.dims[n]);
   const int S = (int)std::max<int64_t>(1, std::min<int64_t>((Imax + 15) / 16, 2 * (int64_t)ctx->num_sms));

@@ -258,33 +258,16 @@ __global__ void __launch_bounds__(256) ls_coef_kernel(const CoefParams p) {
   *p.counter = 0u;
 }
 
-// FP32 copies of a and d (same packing), for the tensor-core variants.
-__global__ void pair_f32_kernel(Layout L, const double* __restrict__ a, const double* __restrict__ d, F32Off o,
-                                float* __restrict__ a32, float* __restrict__ d32) {
-  const int64_t P = L.off[L.N];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
-    int n = 0;
-    while (n + 1 < L.N && e >= L.off[n + 1]) ++n;
-    const int64_t q = o.off[n] + (e - L.off[n]);
-    a32[q] = (float)a[e];
-    d32[q] = (float)d[e];
-  }
-}
-
 // Mixed iterates w_v (v < nvar): factor m < N-1 is d's when bit m of v is
-// set, else a's; the last factor is a's.  FP32 copies when w32 is given.
+// set, else a's; the last factor is a's.
 __global__ void mix_kernel(Layout L, const double* __restrict__ a, const double* __restrict__ d, int nvar,
-                           double* __restrict__ w, F32Off o, int64_t p32, float* __restrict__ w32) {
+                           double* __restrict__ w) {
   const int64_t P = L.off[L.N];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
     int n = 0;
     while (n + 1 < L.N && e >= L.off[n + 1]) ++n;
     const double av = a[e], dv = d[e];
-    for (int v = 0; v < nvar; ++v) {
-      const double x = (n < L.N - 1 && ((v >> n) & 1)) ? dv : av;
-      w[(int64_t)v * P + e] = x;
-      if (w32) w32[(int64_t)v * p32 + o.off[n] + (e - L.off[n])] = (float)x;
-    }
+    for (int v = 0; v < nvar; ++v) w[(int64_t)v * P + e] = (n < L.N - 1 && ((v >> n) & 1)) ? dv : av;
   }
 }
 
@@ -300,12 +283,8 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
   if (N > CP_MAX_N) return CP_ERR_ARG;
   const bool tc = t->kind == 0 && prec == CP_MIXED_BF16X3;
   const bool tc_var = tc && tc_variants_supported(L);
-  F32Off o32{};
   int64_t acc32 = 0;
-  for (int n = 0; n < N; ++n) {
-    o32.off[n] = acc32;
-    acc32 += (L.dims[n] * R + 3) / 4 * 4;
-  }
+  const F32Off o32 = f32_layout(L, &acc32);
   const int64_t P = L.P();
   const unsigned eblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 4 * ctx->num_sms));
   // Grams on the aux stream, overlapped with the MTTKRP
@@ -341,20 +320,23 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
   if (tc_var) {
     CP_TRY(ws_alloc(ctx, (void**)&a32, sizeof(float) * (size_t)acc32 + 64));
     CP_TRY(ws_alloc(ctx, (void**)&d32, sizeof(float) * (size_t)acc32 + 64));
-    pair_f32_kernel<<<eblocks, 256, 0, ctx->stream>>>(L, base, d, o32, a32, d32);
-    CP_LAUNCH_CHECK();
+    CP_TRY(f32_copy(ctx, L, base, o32, acc32, a32));
+    CP_TRY(f32_copy(ctx, L, d, o32, acc32, d32));
     Parts pt;
     CP_TRY(mttkrp_tc_variants(ctx, t, L, a32, d32, o32, last, &pt));
+    // variant v occupies columns v rs .. v rs + R - 1 of the partial sums
     for (int v = 0; v < nvar; ++v) {
       parts[v] = pt;
-      cp.col_off[v] = v * R;
+      cp.col_off[v] = v * o32.rs;
     }
-    cp.col_stride = nvar * R;
+    cp.col_stride = nvar * o32.rs;
   } else {
     CP_TRY(ws_alloc(ctx, (void**)&wv, sizeof(double) * (size_t)nvar * P));
     if (tc) CP_TRY(ws_alloc(ctx, (void**)&w32, sizeof(float) * (size_t)nvar * acc32 + 64));
-    mix_kernel<<<eblocks, 256, 0, ctx->stream>>>(L, base, d, nvar, wv, o32, acc32, w32);
+    mix_kernel<<<eblocks, 256, 0, ctx->stream>>>(L, base, d, nvar, wv);
     CP_LAUNCH_CHECK();
+    if (w32)
+      for (int v = 0; v < nvar; ++v) CP_TRY(f32_copy(ctx, L, wv + (size_t)v * P, o32, acc32, w32 + (size_t)v * acc32));
     for (int v = 0; v < nvar; ++v) {
       CP_TRY(mttkrp_parts(ctx, t, L, wv + (size_t)v * P, w32 ? w32 + (size_t)v * acc32 : nullptr, o32, last, prec,
                           &parts[v]));
