@@ -221,9 +221,7 @@ struct cp_tensor {
   void* Tn[CP_MAX_N] = {nullptr};
   // dense mixed precision: per-mode bf16 hi/lo planes of T_(n) with a row
   // pitch padded to a multiple of 64 elements (created on first use)
-  __nv_bfloat16* Thi[CP_MAX_N] = {nullptr};
-  __nv_bfloat16* Tlo[CP_MAX_N] = {nullptr};
-  int64_t pitch[CP_MAX_N] = {0};
+  void* Ttile[CP_MAX_N] = {nullptr};   // mixed precision: pre-tiled bf16 hi / lo planes of T_(n)
   void* tc_state = nullptr;      // tensor maps of the planes (dense_tc.cu)
   // coo
   int64_t nnz = 0;

@@ -10,9 +10,17 @@
 // Each 16-deep step issues three MMAs, hi*hi + hi*lo + lo*hi, into one FP32
 // accumulator (the lo*lo term, ~2^-18 relative, is dropped).
 //
+// T_(n) is stored pre-tiled: every 128-row x 64-column tile of each plane is
+// one contiguous block of rows x 128 bytes, already in the 128-byte-swizzled
+// K-major order the tensor cores read (16-byte chunk c of row r at chunk
+// c ^ (r & 7)), hi block then lo block, tiles of one column range for all
+// row tiles next to each other.  A stage is then filled by two plain bulk
+// copies of contiguous memory, which keeps whole DRAM pages in use (a 2-D
+// box of 128 rows x 128 bytes from a row-major matrix touches 128 pages).
+//
 // CTA layout (192 threads, one CTA per SM):
-//   warp 0     TMA producer: 128 x 64 bf16 tiles of both planes, 128-byte
-//              swizzle, into a ring of `stages` shared-memory stages.
+//   warp 0     producer: bulk copies of the hi / lo blocks of one tile per
+//              stage into a ring of `stages` shared-memory stages.
 //   warp 1     TMEM allocation and the MMA issuer (one thread).
 //   warps 2-5  build the Khatri-Rao hi/lo tiles of each stage (SW128,
 //              K-major), then drain the accumulators (tcgen05.ld) and write
@@ -21,7 +29,6 @@
 // tiles.  A second kernel adds the per-CTA partials in a fixed order in FP64.
 // Every mbarrier wait is bounded; on a timeout the CTA records
 // CP_ERR_TIMEOUT in the device status word and winds down.
-#include <cuda.h>
 
 #include <algorithm>
 
@@ -41,6 +48,7 @@ constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
 constexpr int kMaxDynSmem = 227 * 1024;
 
 struct TcParams {
+  const uint8_t* tiles;       // pre-tiled hi / lo planes of T_(n)
   int64_t I;
   int64_t Kbar;
   int R, RP;
@@ -115,14 +123,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* stat
   return true;
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
 // Untiled bulk copy global -> shared (16-byte aligned addresses, size a
 // multiple of 16), completing on an mbarrier.
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -186,8 +186,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 
 template <int NO>
 __global__ void __launch_bounds__(kThreads, 1)
-    mttkrp_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
-                     const TcParams p) {
+    mttkrp_tc_kernel(const TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -250,13 +249,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = i % S;
         const uint32_t ph = (uint32_t)((i / S) & 1);
         if (!mbar_wait(empty_bar(s), ph ^ 1u, p.status)) break;
-        mbar_arrive_tx(full_bar(s), (uint32_t)p.ntm * 2u * kTileBytes);
-        const int x = (int)((kt0 + i) * kBK);
+        // tile kt of row tile m: hi block (rows x 128 bytes) then lo block,
+        // at kt (2 I 128) + m (2 128 128) bytes
+        const int64_t kt = kt0 + i;
         const uint32_t st = base + (uint32_t)s * stage_bytes;
+        uint32_t bytes = 0;
+        for (int mt = 0; mt < p.ntm; ++mt)
+          bytes += 2u * 128u * (uint32_t)max((int64_t)0, min((int64_t)kBM, p.I - (row0 + mt * kBM)));
+        mbar_arrive_tx(full_bar(s), bytes);
         for (int mt = 0; mt < p.ntm; ++mt) {
-          const int y = (int)(row0 + mt * kBM);
-          tma_load_2d(st + (uint32_t)mt * kTileBytes, &tm_hi, x, y, full_bar(s));
-          tma_load_2d(st + (uint32_t)(p.ntm + mt) * kTileBytes, &tm_lo, x, y, full_bar(s));
+          const int64_t r0 = row0 + mt * kBM;
+          if (r0 >= p.I) break;
+          const uint32_t blk = 128u * (uint32_t)min((int64_t)kBM, p.I - r0);
+          const uint8_t* src = p.tiles + kt * (2 * p.I * 128) + r0 * 256;
+          bulk_load(st + (uint32_t)mt * kTileBytes, src, blk, full_bar(s));
+          bulk_load(st + (uint32_t)(p.ntm + mt) * kTileBytes, src + blk, blk, full_bar(s));
         }
         ++issued;
       }
@@ -447,40 +454,43 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// hi = bf16(x), lo = bf16(x - hi); row pitch `pitch` (zero padding).
+// Pre-tiled planes: one thread per (column tile kt, row i, 16-byte chunk c)
+// writes eight hi and eight lo values, hi = bf16(x), lo = bf16(x - hi),
+// zero past Kbar.  Tile (kt, m) starts at kt (2 I 128) + m (2 128 128)
+// bytes; its hi block has rows x 128 bytes with chunk c of row r at
+// position c ^ (r & 7), and the lo block follows.
 template <typename TT>
-__global__ void split_planes_kernel(const TT* __restrict__ src, int64_t I, int64_t Kbar, int64_t pitch,
-                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
-  const int64_t total = I * pitch;
+__global__ void split_tiles_kernel(const TT* __restrict__ src, int64_t I, int64_t Kbar, int64_t ktiles,
+                                   uint8_t* __restrict__ out) {
+  const int64_t total = ktiles * I * 8;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = o / pitch;
-    const int64_t k = o - i * pitch;
-    double x = k < Kbar ? (double)src[i * Kbar + k] : 0.0;
-    const __nv_bfloat16 h = __double2bfloat16(x);
-    const __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
-    hi[o] = h;
-    lo[o] = l;
+    const int c = (int)(o & 7);
+    const int64_t ri = o >> 3;
+    const int64_t i = ri % I;
+    const int64_t kt = ri / I;
+    const int64_t m = i / kBM;
+    const int r = (int)(i - m * kBM);
+    const int64_t rows = min((int64_t)kBM, I - m * kBM);
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      const int64_t k = kt * kBK + c * 8 + q;
+      const double x0 = k < Kbar ? (double)src[i * Kbar + k] : 0.0;
+      const double x1 = k + 1 < Kbar ? (double)src[i * Kbar + k + 1] : 0.0;
+      const __nv_bfloat16 h0 = __double2bfloat16(x0), h1 = __double2bfloat16(x1);
+      const __nv_bfloat16 l0 = __double2bfloat16(x0 - (double)__bfloat162float(h0));
+      const __nv_bfloat16 l1 = __double2bfloat16(x1 - (double)__bfloat162float(h1));
+      h[q / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      l[q / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    uint8_t* tile = out + kt * (2 * I * 128) + m * (2 * kBM * 128);
+    const int64_t pos = (int64_t)r * 128 + (int64_t)((c ^ (r & 7)) << 4);
+    *reinterpret_cast<uint4*>(tile + pos) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(tile + rows * 128 + pos) = make_uint4(l[0], l[1], l[2], l[3]);
   }
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
-  return fn;
 }
 
 struct MixedMode {
-  CUtensorMap hi, lo;
   bool ready = false;
 };
 
@@ -497,9 +507,8 @@ static TcState* tc_state(cp_tensor* t) {
 
 void tensor_free_mixed(cp_tensor* t, cudaStream_t s) {
   for (int n = 0; n < CP_MAX_N; ++n) {
-    if (t->Thi[n]) cudaFreeAsync(t->Thi[n], s);
-    if (t->Tlo[n]) cudaFreeAsync(t->Tlo[n], s);
-    t->Thi[n] = t->Tlo[n] = nullptr;
+    if (t->Ttile[n]) cudaFreeAsync(t->Ttile[n], s);
+    t->Ttile[n] = nullptr;
   }
   delete tc_state(t);
   t->tc_state = nullptr;
@@ -511,47 +520,23 @@ static cp_status ensure_planes(cp_ctx* ctx, cp_tensor* t, int n) {
   if (mm.ready) return CP_OK;
   const int64_t I = t->dims[n];
   const int64_t Kb = kbar(t, n);
-  const int64_t pitch = (Kb + 7) / 8 * 8;
-  if (Kb > ((int64_t)1 << 31) - 64 || I > ((int64_t)1 << 31) - 256) {
-    set_error("mixed MTTKRP: matricisation %lld x %lld too large for 32-bit TMA coordinates",
-              (long long)I, (long long)Kb);
-    return CP_ERR_UNSUPPORTED;
-  }
-  CP_CUDA(cudaMallocAsync(&t->Thi[n], sizeof(__nv_bfloat16) * (size_t)(I * pitch), ctx->stream));
-  CP_CUDA(cudaMallocAsync(&t->Tlo[n], sizeof(__nv_bfloat16) * (size_t)(I * pitch), ctx->stream));
-  t->pitch[n] = pitch;
-  int64_t blocks = std::min<int64_t>((I * pitch + 255) / 256, 16 * (int64_t)ctx->num_sms);
+  const int64_t ktiles = (Kb + kBK - 1) / kBK;
+  const size_t bytes = (size_t)ktiles * 2 * (size_t)I * 128;
+  CP_CUDA(cudaMallocAsync(&t->Ttile[n], bytes, ctx->stream));
+  const int64_t work = ktiles * I * 8;
+  const int64_t blocks = std::min<int64_t>((work + 255) / 256, 16 * (int64_t)ctx->num_sms);
   if (t->dtype == CP_DTYPE_F64)
-    split_planes_kernel<double><<<(unsigned)blocks, 256, 0, ctx->stream>>>((const double*)t->Tn[n], I, Kb, pitch,
-                                                                          t->Thi[n], t->Tlo[n]);
+    split_tiles_kernel<double><<<(unsigned)blocks, 256, 0, ctx->stream>>>((const double*)t->Tn[n], I, Kb, ktiles,
+                                                                         (uint8_t*)t->Ttile[n]);
   else
-    split_planes_kernel<float><<<(unsigned)blocks, 256, 0, ctx->stream>>>((const float*)t->Tn[n], I, Kb, pitch,
-                                                                         t->Thi[n], t->Tlo[n]);
+    split_tiles_kernel<float><<<(unsigned)blocks, 256, 0, ctx->stream>>>((const float*)t->Tn[n], I, Kb, ktiles,
+                                                                        (uint8_t*)t->Ttile[n]);
   CP_LAUNCH_CHECK();
-  EncodeTiledFn enc = encode_fn();
-  if (!enc) {
-    set_error("cuTensorMapEncodeTiled is not available from the driver");
-    return CP_ERR_CUDA;
-  }
-  cuuint64_t gdim[2] = {(cuuint64_t)Kb, (cuuint64_t)I};
-  cuuint64_t gstride[1] = {(cuuint64_t)(pitch * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
-  cuuint32_t estr[2] = {1, 1};
-  for (int pl = 0; pl < 2; ++pl) {
-    CUresult r = enc(pl == 0 ? &mm.hi : &mm.lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                     pl == 0 ? (void*)t->Thi[n] : (void*)t->Tlo[n], gdim, gstride, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-      set_error("cuTensorMapEncodeTiled failed (%d) for mode %d", (int)r, n);
-      return CP_ERR_CUDA;
-    }
-  }
   mm.ready = true;
   return CP_OK;
 }
 
-typedef void (*TcKernel)(CUtensorMap, CUtensorMap, TcParams);
+typedef void (*TcKernel)(TcParams);
 
 static TcKernel tc_kernel_for(int nother) {
   switch (nother) {
@@ -597,7 +582,6 @@ static cp_status factors_f32(cp_ctx* ctx, const Layout& L, const double* u, floa
 static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o,
                                   int mode, Parts* parts, const float* d32 = nullptr, int nvar = 1) {
   CP_TRY(ensure_planes(ctx, t, mode));
-  const MixedMode& mm = tc_state(t)->mode[mode];
   const int R = L.R;
   const int outc = nvar > 1 ? nvar * o.rs : R;
   const int RP = std::max(16, (outc + 15) / 16 * 16);
@@ -608,6 +592,7 @@ static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, co
   const int64_t I = t->dims[mode];
   const int64_t Kb = kbar(t, mode);
   TcParams p{};
+  p.tiles = (const uint8_t*)t->Ttile[mode];
   p.I = I;
   p.Kbar = Kb;
   p.R = R;
@@ -662,7 +647,7 @@ static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, co
   CP_TRY(set_smem_attr());
   {
     TimerScope ts(ctx, 0);
-    tc_kernel_for(p.nother)<<<dim3(gx, mgroups), kThreads, smem, ctx->stream>>>(mm.hi, mm.lo, p);
+    tc_kernel_for(p.nother)<<<dim3(gx, mgroups), kThreads, smem, ctx->stream>>>(p);
   }
   CP_LAUNCH_CHECK();
   *parts = Parts{partial, gx, 1};
