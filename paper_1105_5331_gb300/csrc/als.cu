@@ -12,7 +12,8 @@
 //               Cholesky factorisation would), one ridge retry; pivot
 //               reciprocals by Newton's iteration from an FP32 seed.  It runs
 //               on the context's aux stream, overlapped with the MTTKRP of
-//               the same mode, which does not depend on it.
+//               the same mode, which does not depend on it; one barrier per
+//               pivot (double-buffered), every thread forms the reciprocal.
 //   update      A_n = M Gammabar^-1: rows spread over blocks; M rows from the
 //               MTTKRP partial sums (FP32 partials added in FP32, FP64 ones in
 //               FP64, in a fixed order), then one FP64 dot per output.
@@ -79,13 +80,17 @@ __global__ void __launch_bounds__(256) gram_kernel(const GramParams p) {
     const GramJob& g = p.job[j];
     const int R = p.R;
     const int64_t i0 = ch * kGramChunk, i1 = min(g.I, i0 + kGramChunk);
+    const double a = g.D ? *g.stp : 0.0;
+    // element of an operand, shifted by a D when the job has one (the same
+    // fma as the kernel that forms x = base + stp d)
+    auto xv = [&](const double* M, int64_t idx) { return g.D ? fma(a, g.D[idx], M[idx]) : M[idx]; };
     double a0 = 0.0, a1 = 0.0;
     int64_t i = i0 + lane;
     for (; i + 32 < i1; i += 64) {
-      a0 = fma(g.X[i * R + r], g.Y[i * R + s], a0);
-      a1 = fma(g.X[(i + 32) * R + r], g.Y[(i + 32) * R + s], a1);
+      a0 = fma(xv(g.X, i * R + r), xv(g.Y, i * R + s), a0);
+      a1 = fma(xv(g.X, (i + 32) * R + r), xv(g.Y, (i + 32) * R + s), a1);
     }
-    if (i < i1) a0 = fma(g.X[i * R + r], g.Y[i * R + s], a0);
+    if (i < i1) a0 = fma(xv(g.X, i * R + r), xv(g.Y, i * R + s), a0);
     double v = a0 + a1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -149,72 +154,87 @@ struct InvParams {
   int* status;
 };
 
-// In-place symmetric Gauss-Jordan inverse of the R x R SPD matrix S (shared
-// memory, all threads); false if a pivot is not positive and finite.
-__device__ bool gj_inverse(double* S, int R, double* piv_sh, int* flag) {
+// One pivot step of in-place Gauss-Jordan inversion from `src` into `dst`
+// (every new entry from old ones only, so one barrier per pivot; every
+// thread forms the pivot reciprocal itself).  With p = 1 / S_kk:
+//   S_ij -= S_ik p S_kj (i, j != k),  S_ik = -S_ik p,  S_kj = -S_kj p,
+//   S_kk = -p;  after all pivots the matrix holds -S^-1.
+__device__ bool gj_inverse2(double* A, double* B, int R, double** out) {
+  double* src = A;
+  double* dst = B;
   for (int k = 0; k < R; ++k) {
-    if (threadIdx.x == 0) {
-      const double d = S[k * R + k];
-      if (!(d > 0.0) || !isfinite(d)) *flag = 1;
-      else *piv_sh = recip_newton(d);
-    }
-    __syncthreads();
-    if (*flag) return false;
-    const double pinv = *piv_sh;
-    // rows i != k, columns j != k: S_ij -= S_ik S_kj / S_kk
+    const double d = src[k * R + k];
+    if (!(d > 0.0) || !isfinite(d)) return false;   // uniform: every thread reads the same d
+    const double pinv = recip_newton(d);
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
       const int i = e / R, j = e - (e / R) * R;
-      if (i != k && j != k) S[e] = fma(-S[i * R + k] * pinv, S[k * R + j], S[e]);
+      double v;
+      if (i == k && j == k)
+        v = -pinv;
+      else if (j == k)
+        v = -src[e] * pinv;
+      else if (i == k)
+        v = -src[e] * pinv;
+      else
+        v = fma(-src[i * R + k] * pinv, src[k * R + j], src[e]);
+      dst[e] = v;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < R; i += blockDim.x) {
-      if (i != k) {
-        S[i * R + k] *= -pinv;
-        S[k * R + i] *= -pinv;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) S[k * R + k] = -pinv;
-    __syncthreads();
+    double* t = src;
+    src = dst;
+    dst = t;
   }
-  // the elimination above leaves -S^-1
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) S[e] = -S[e];
-  __syncthreads();
+  *out = src;
   return true;
 }
 
+// Dynamic shared memory: two R x R FP64 buffers.
 __global__ void __launch_bounds__(256) gram_inverse_kernel(const InvParams p) {
-  __shared__ double S[CP_MAX_R * CP_MAX_R];
-  __shared__ double piv;
-  __shared__ int flag;
+  extern __shared__ double dsm[];
   const int R = p.R, RR = R * R;
+  double* A = dsm;
+  double* B = dsm + RR;
   auto build = [&](double ridge) {
     for (int k = threadIdx.x; k < RR; k += blockDim.x) {
       double v = 1.0;
       for (int m = 0; m < p.N; ++m)
         if (m != p.n) v *= p.grams[(int64_t)m * RR + k];
-      S[k] = v;
+      A[k] = v;
     }
     __syncthreads();
-    if (ridge > 0.0 && threadIdx.x == 0) {
+    if (ridge > 0.0) {
       double tr = 0.0;
-      for (int r = 0; r < R; ++r) tr += S[r * R + r];
-      for (int r = 0; r < R; ++r) S[r * R + r] += ridge * tr / R;
+      for (int r = 0; r < R; ++r) tr += A[r * R + r];
+      __syncthreads();
+      for (int r = threadIdx.x; r < R; r += blockDim.x) A[r * R + r] += ridge * tr / R;
+      __syncthreads();
     }
-    if (threadIdx.x == 0) flag = 0;
-    __syncthreads();
   };
+  double* res = nullptr;
   build(0.0);
-  bool ok = gj_inverse(S, R, &piv, &flag);
+  bool ok = gj_inverse2(A, B, R, &res);
   if (!ok) {
+    __syncthreads();
     build(1e-12);
-    ok = gj_inverse(S, R, &piv, &flag);
+    ok = gj_inverse2(A, B, R, &res);
   }
-  for (int k = threadIdx.x; k < RR; k += blockDim.x) p.Xinv[k] = ok ? S[k] : 0.0;
+  for (int k = threadIdx.x; k < RR; k += blockDim.x) p.Xinv[k] = ok ? -res[k] : 0.0;
   if (threadIdx.x == 0) {
     *p.ok = ok ? 1 : 0;
     if (!ok) record_status(p.status, CP_ERR_NOT_SPD);
   }
+}
+
+size_t inverse_smem(int R) { return 2 * (size_t)R * R * sizeof(double); }
+
+cp_status inverse_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    CP_CUDA(cudaFuncSetAttribute(gram_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)inverse_smem(CP_MAX_R)));
+    done = true;
+  }
+  return CP_OK;
 }
 
 struct UpdParams {
@@ -374,6 +394,7 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
   if (want_f32) CP_TRY(ws_alloc(ctx, (void**)&u32, sizeof(float) * (size_t)acc32 + 64));
   CP_TRY(ws_alloc(ctx, (void**)&Xinv, sizeof(double) * (size_t)RR + 64));
   ok = (int*)(Xinv + RR);
+  CP_TRY(inverse_smem_attr());
   if (want_f32) CP_TRY(f32_copy(ctx, L, u, o32, acc32, u32));
   if (!grams_valid) CP_TRY(grams_of(ctx, ctx->stream, ctx->d_counter, L, u, 0, N, grams));
   const int rows = std::max(1, 32 / R);
@@ -384,7 +405,7 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
     CP_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
     if (n > 0) CP_TRY(grams_of(ctx, ctx->aux, ctx->d_counter + 1, L, u, n - 1, 1, grams));
     InvParams ip{grams, N, R, n, Xinv, ok, ctx->d_status};
-    gram_inverse_kernel<<<1, 256, 0, ctx->aux>>>(ip);
+    gram_inverse_kernel<<<1, 256, inverse_smem(R), ctx->aux>>>(ip);
     CP_LAUNCH_CHECK();
     CP_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
     Parts pt;

@@ -294,6 +294,8 @@ struct GramJob {
   int64_t I;
   double* out;
   int sym;
+  const double* D = nullptr;     // optional: both operands read as fma(*stp, D, .)
+  const double* stp = nullptr;
 };
 constexpr int kMaxGramJobs = 3 * CP_MAX_N;
 cp_status grams_jobs(cp_ctx* ctx, cudaStream_t s, unsigned* counter, int R, const GramJob* jobs, int njobs);

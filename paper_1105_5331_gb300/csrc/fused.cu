@@ -24,8 +24,6 @@ cp_status mttkrp_f64_parts(cp_ctx* ctx, const cp_tensor* t, const Layout& L, con
 
 namespace {
 
-constexpr int kPrepRows = 16;
-
 __device__ __forceinline__ bool last_block(unsigned* counter, unsigned nblocks, bool* flag) {
   __threadfence();
   __syncthreads();
@@ -35,79 +33,32 @@ __device__ __forceinline__ bool last_block(unsigned* counter, unsigned nblocks, 
   return *flag;
 }
 
-struct PrepParams {
-  Layout L;
-  const double* base;
-  const double* d;        // nullable: x = base + (*stp) d
-  const double* stp;
-  double* x;              // written when d != nullptr
-  float* x32;             // nullable
-  F32Off o32;
-  double* part;           // [N][S][R*R]
-  double* grams;          // out, N x R*R
-  int S;
-  unsigned* counter;
-};
-
-__global__ void __launch_bounds__(256) prep_kernel(const PrepParams p) {
-  __shared__ double tile[kPrepRows * CP_MAX_R];
-  __shared__ bool is_last;
-  const int m = blockIdx.y;
-  const int R = p.L.R;
-  const int RR = R * R;
-  const int64_t I = p.L.dims[m];
-  const int64_t chunk = (I + p.S - 1) / p.S;
-  const int64_t rb = (int64_t)blockIdx.x * chunk;
-  const int64_t re = min(I, rb + chunk);
-  const double a = p.d ? *p.stp : 0.0;
-  const int64_t off = p.L.off[m];
-  double acc[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) acc[k] = 0.0;
-  for (int64_t r0 = rb; r0 < re; r0 += kPrepRows) {
-    const int nr = (int)min((int64_t)kPrepRows, re - r0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < nr * R; e += blockDim.x) {
-      const int64_t gi = off + r0 * R + e;
-      double v = p.base[gi];
-      if (p.d) {
-        v = v + a * p.d[gi];
-        p.x[gi] = v;
+// x = base + (*stp) d (written when d is given) and its padded FP32 copy
+// (when x32 is given), one pass over the FP32 layout.
+__global__ void __launch_bounds__(256) xprep_kernel(Layout L, const double* __restrict__ base,
+                                                    const double* __restrict__ d, const double* __restrict__ stp,
+                                                    double* __restrict__ x, float* __restrict__ x32, F32Off o,
+                                                    int64_t total) {
+  const double a = d ? *stp : 0.0;
+  const int R = L.R;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    int n = 0;
+    while (n + 1 < L.N && q >= o.off[n + 1]) ++n;
+    const int64_t within = q - o.off[n];
+    const int64_t i = within / o.rs;
+    const int r = (int)(within - i * o.rs);
+    float v32 = 0.f;
+    if (r < R) {
+      const int64_t e = L.off[n] + i * R + r;
+      double v = base[e];
+      if (d) {
+        v = fma(a, d[e], v);
+        x[e] = v;
       }
-      if (p.x32) p.x32[p.o32.off[m] + (r0 + e / R) * p.o32.rs + e % R] = (float)v;
-      tile[e] = v;
+      v32 = (float)v;
     }
-    if (p.x32)   // zero padding of the FP32 rows
-      for (int e = threadIdx.x; e < nr * (p.o32.rs - R); e += blockDim.x) {
-        const int q = e / (p.o32.rs - R);
-        p.x32[p.o32.off[m] + (r0 + q) * p.o32.rs + R + (e - q * (p.o32.rs - R))] = 0.f;
-      }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int e = threadIdx.x + k * blockDim.x;
-      if (e < RR) {
-        const int r = e / R, s = e - (e / R) * R;
-        double t = acc[k];
-        for (int q = 0; q < nr; ++q) t = fma(tile[q * R + r], tile[q * R + s], t);
-        acc[k] = t;
-      }
-    }
+    if (x32) x32[q] = v32;
   }
-  double* out = p.part + ((int64_t)m * p.S + blockIdx.x) * RR;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const int e = threadIdx.x + k * blockDim.x;
-    if (e < RR) out[e] = acc[k];
-  }
-  if (!last_block(p.counter, gridDim.x * gridDim.y, &is_last)) return;
-  for (int idx = threadIdx.x; idx < p.L.N * RR; idx += blockDim.x) {
-    const int mm = idx / RR, e = idx - (idx / RR) * RR;
-    double s = 0.0;
-    for (int c = 0; c < p.S; ++c) s += __ldcg(&p.part[((int64_t)mm * p.S + c) * RR + e]);
-    p.grams[idx] = s;
-  }
-  if (threadIdx.x == 0) *p.counter = 0u;
 }
 
 struct FinishParams {
@@ -249,35 +200,38 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   const int R = L.R, N = L.N, RR = R * R;
   const double* u = d ? x : base;
   const bool want_f32 = t->kind == 0 && prec == CP_MIXED_BF16X3;
-  // prep: x, FP32 copy, Grams
+  // x and its FP32 copy on the main stream; the Grams of x on the aux
+  // stream, overlapped with the MTTKRPs (which do not need them)
   int64_t acc32 = 0;
   const F32Off o32 = f32_layout(L, &acc32);
-  int64_t Imax = 1;
-  for (int n = 0; n < N; ++n) Imax = std::max(Imax, L.dims[n]);
-  const int S = (int)std::max<int64_t>(1, std::min<int64_t>((Imax + 15) / 16, 2 * (int64_t)ctx->num_sms));
   float* x32 = nullptr;
   double* grams = nullptr;
-  double* gpart = nullptr;
   if (want_f32) CP_TRY(ws_alloc(ctx, (void**)&x32, sizeof(float) * (size_t)acc32 + 64));
   if (grams_out)
     grams = grams_out;
   else
     CP_TRY(ws_alloc(ctx, (void**)&grams, sizeof(double) * (size_t)N * RR));
-  CP_TRY(ws_alloc(ctx, (void**)&gpart, sizeof(double) * (size_t)N * S * RR));
-  PrepParams pp;
-  pp.L = L;
-  pp.base = base;
-  pp.d = d;
-  pp.stp = stp;
-  pp.x = x;
-  pp.x32 = x32;
-  pp.o32 = o32;
-  pp.part = gpart;
-  pp.grams = grams;
-  pp.S = S;
-  pp.counter = ctx->d_counter;
-  prep_kernel<<<dim3(S, N), 256, 0, ctx->stream>>>(pp);
-  CP_LAUNCH_CHECK();
+  CP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream));
+  CP_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+  {
+    GramJob jobs[kMaxGramJobs];
+    for (int n = 0; n < N; ++n) {
+      jobs[n] = GramJob{base + L.off[n], base + L.off[n], L.dims[n], grams + (size_t)n * RR, 1};
+      if (d) {
+        jobs[n].D = d + L.off[n];
+        jobs[n].stp = stp;
+      }
+    }
+    CP_TRY(grams_jobs(ctx, ctx->aux, ctx->d_counter + 1, R, jobs, N));
+  }
+  CP_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
+  if (d || x32) {
+    const int64_t total = x32 ? acc32 : L.P();
+    const F32Off o = x32 ? o32 : [&]() { F32Off q{}; q.rs = R; for (int n = 0; n < N; ++n) q.off[n] = L.off[n]; return q; }();
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4 * ctx->num_sms));
+    xprep_kernel<<<blocks, 256, 0, ctx->stream>>>(L, base, d, stp, x, x32, o, total);
+    CP_LAUNCH_CHECK();
+  }
   // MTTKRPs (all modes for g; the last one alone for f)
   FinishParams fp{};
   const int first = g || d ? 0 : N - 1;
@@ -290,7 +244,6 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
     if (n >= first) chunks += (L.dims[n] * R + 31) / 32;
   }
   fp.chunk_off[N] = chunks;
-  // modes before `first` own no chunks: point their offsets past them
   fp.u = u;
   fp.grams = grams;
   fp.norm2 = t->norm2;
@@ -301,11 +254,11 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   fp.counter = ctx->d_counter;
   fp.status = ctx->d_status;
   CP_TRY(ws_alloc(ctx, (void**)&fp.blk, sizeof(double) * 2 * (size_t)chunks + 16));
+  CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
   fg_finish_kernel<<<(unsigned)chunks, 256, 0, ctx->stream>>>(fp);
   CP_LAUNCH_CHECK();
   ws_free(ctx, fp.blk);
   for (int n = first; n < N; ++n) ws_free(ctx, const_cast<void*>(fp.parts[n].p));
-  ws_free(ctx, gpart);
   if (!grams_out) ws_free(ctx, grams);
   if (x32) ws_free(ctx, x32);
   return CP_OK;
