@@ -96,7 +96,9 @@ __global__ void __launch_bounds__(256) norm_apply_kernel(Layout L, const double*
                                                          double* __restrict__ dst, const double* __restrict__ gsrc,
                                                          double* __restrict__ gdst, const double* __restrict__ part,
                                                          int S, const double* __restrict__ grams,
-                                                         double* __restrict__ lambda_out, int* status) {
+                                                         double* __restrict__ lambda_out, int* status,
+                                                         const double* __restrict__ m0_src,
+                                                         double* __restrict__ m0_dst) {
   __shared__ double nu[CP_MAX_N * CP_MAX_R];
   __shared__ double scale[CP_MAX_N * CP_MAX_R];
   __shared__ double key[CP_MAX_R];
@@ -158,6 +160,19 @@ __global__ void __launch_bounds__(256) norm_apply_kernel(Layout L, const double*
     dst[e] = src[srcidx] * sc;
     if (gdst) gdst[e] = gsrc[srcidx] / sc;
   }
+  if (m0_dst) {
+    // M^(1)[i][p] of the normalised point: column order[p] of src's M^(1)
+    // times the scales of modes 2..N of that column
+    const int64_t n0 = L.dims[0] * R;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n0; e += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = e / R;
+      const int pcol = (int)(e - i * R);
+      const int q = order[pcol];
+      double sc = 1.0;
+      for (int n = 1; n < N; ++n) sc *= scale[n * R + q];
+      m0_dst[e] = m0_src[i * R + q] * sc;
+    }
+  }
 }
 
 inline int grid_for(cp_ctx* ctx, int64_t n, int threads) {
@@ -190,7 +205,8 @@ cp_status dot(cp_ctx* ctx, int64_t n, const double* x, const double* y, double* 
 }
 
 cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double* dst,
-                         const double* gsrc, double* gdst, double* lambda, const double* grams) {
+                         const double* gsrc, double* gdst, double* lambda, const double* grams,
+                         const double* m0_src, double* m0_dst) {
   const int R = L.R;
   double* part = nullptr;
   int S = 1;
@@ -205,7 +221,7 @@ cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double
     CP_LAUNCH_CHECK();
   }
   norm_apply_kernel<<<grid_for(ctx, L.P(), 256), 256, 0, ctx->stream>>>(L, src, dst, gsrc, gdst, part, S, grams,
-                                                                        lambda, ctx->d_status);
+                                                                        lambda, ctx->d_status, m0_src, m0_dst);
   CP_LAUNCH_CHECK();
   if (part) ws_free(ctx, part);
   return CP_OK;

@@ -382,7 +382,7 @@ cp_status grams_of(cp_ctx* ctx, cudaStream_t s, unsigned* counter, const Layout&
 // A_n = M^(n) Gammabar^(n)^-1.  grams (N x R x R) receives the Grams of the
 // updated factors; with grams_valid it already holds those of u on entry.
 cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, double* u, cp_precision prec,
-                       double* grams, bool grams_valid) {
+                       double* grams, bool grams_valid, const double* m0) {
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int R = L.R, N = L.N, RR = R * R;
   const bool want_f32 = t->kind == 0 && prec == CP_MIXED_BF16X3;
@@ -409,7 +409,10 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
     CP_LAUNCH_CHECK();
     CP_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
     Parts pt;
-    CP_TRY(mttkrp_parts(ctx, t, L, u, u32, o32, n, prec, &pt));
+    if (n == 0 && m0)
+      pt = Parts{m0, 1, 0};
+    else
+      CP_TRY(mttkrp_parts(ctx, t, L, u, u32, o32, n, prec, &pt));
     CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     UpdParams up;
     up.parts = pt;
@@ -423,7 +426,7 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
     up.rs = o32.rs;
     als_update_kernel<<<(unsigned)((L.dims[n] + rows - 1) / rows), 256, 0, ctx->stream>>>(up);
     CP_LAUNCH_CHECK();
-    ws_free(ctx, const_cast<void*>(pt.p));
+    if (!(n == 0 && m0)) ws_free(ctx, const_cast<void*>(pt.p));
   }
   CP_TRY(grams_of(ctx, ctx->stream, ctx->d_counter, L, u, N - 1, 1, grams));
   ws_free(ctx, Xinv);

@@ -253,8 +253,11 @@ cp_status mttkrp_any(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const dou
 // Normalise src (and gsrc) into dst (and gdst); lambda (R) optional.  With
 // grams (N x R x R, the Grams of src) the column norms come from their
 // diagonals instead of a pass over src.
+// With m0_src the M^(1) of src follows the normalisation into m0_dst (its
+// columns reordered and scaled by the other modes' scales).
 cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double* dst,
-                         const double* gsrc, double* gdst, double* lambda, const double* grams = nullptr);
+                         const double* gsrc, double* gdst, double* lambda, const double* grams = nullptr,
+                         const double* m0_src = nullptr, double* m0_dst = nullptr);
 
 // Window-indexed N-GMRES Step II.  win (device) = {start, m}; window row j
 // (oldest first) is ring slot (start + j) % cap.
@@ -305,13 +308,18 @@ cp_status grams_of(cp_ctx* ctx, cudaStream_t s, unsigned* counter, const Layout&
 // ALS sweep in place on u: per mode, the Gram inverse on ctx->aux overlapped
 // with the MTTKRP, then a row-parallel update.  grams (N x R x R) ends with
 // the Grams of the updated factors (grams_valid: it holds u's on entry).
+// m0 (nullable): M^(1) of u, used for the first mode instead of an MTTKRP.
 cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t, const Layout& L, double* u, cp_precision prec,
-                       double* grams, bool grams_valid);
+                       double* grams, bool grams_valid, const double* m0 = nullptr);
 // Fused f/g at x = base (+ (*stp) d when d is given; x written); with gd
 // (and d) also g . d.
+// grams_out: the Grams of the point (N x R x R); m0_out: its M^(1) (I_1 x R);
+// mv_last (with d): the last mode's M as sum_v beta^popc(v) mv_last[v] from the
+// line-search variants instead of an MTTKRP pass (beta = *mv_beta).
 cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* base,
                      const double* d, const double* stp, double* x, double* f, double* g,
-                     cp_precision prec, double* gd, double* grams_out = nullptr);
+                     cp_precision prec, double* gd, double* grams_out = nullptr, double* m0_out = nullptr,
+                     const double* mv_last = nullptr, const double* mv_beta = nullptr);
 
 // Padded FP32 copy (f32_layout) of the packed FP64 iterate u, on ctx->stream.
 cp_status f32_copy(cp_ctx* ctx, const Layout& L, const double* u, const F32Off& o, int64_t total, float* out);

@@ -72,6 +72,12 @@ struct FinishParams {
   double* f;
   const double* d;        // nullable: also g . d
   double* gd;
+  double* m0_out;         // nullable: M^(1) (mode 0) of the evaluation point
+  // nullable: the last mode's M from the line-search variants,
+  // M = sum_v beta^popc(v) mv[v] (x = base + beta d is multilinear in beta)
+  const double* mv;
+  int mv_nvar;
+  const double* mv_beta;
   double* blk;            // 2 x gridDim.x block partials
   unsigned* counter;
   int* status;
@@ -117,8 +123,17 @@ __global__ void __launch_bounds__(256) fg_finish_kernel(const FinishParams p) {
     double inner = 0.0, gdv = 0.0;
     if (e < nel) {
       double mval = 0.0;
+      if (p.mv && n == N - 1) {
+        const double beta = *p.mv_beta;
+        double pw[CP_MAX_N];
+        pw[0] = 1.0;
+        for (int k = 1; k < N; ++k) pw[k] = pw[k - 1] * beta;
+        for (int v = 0; v < p.mv_nvar; ++v) mval = fma(pw[__popc(v)], p.mv[(int64_t)v * nel + e], mval);
+      } else {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) mval += sh[q][lane];
+        for (int q = 0; q < 8; ++q) mval += sh[q][lane];
+      }
+      if (p.m0_out && n == 0) p.m0_out[e] = mval;
       const int64_t off = p.L.off[n];
       const int64_t i = e / R;
       const int r = (int)(e - i * R);
@@ -195,7 +210,7 @@ cp_status mttkrp_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double*
 
 cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const double* base, const double* d,
                      const double* stp, double* x, double* f, double* g, cp_precision prec, double* gd,
-                     double* grams_out) {
+                     double* grams_out, double* m0_out, const double* mv_last, const double* mv_beta) {
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int R = L.R, N = L.N, RR = R * R;
   const double* u = d ? x : base;
@@ -235,7 +250,8 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   // MTTKRPs (all modes for g; the last one alone for f)
   FinishParams fp{};
   const int first = g || d ? 0 : N - 1;
-  for (int n = first; n < N; ++n) CP_TRY(mttkrp_parts(ctx, t, L, u, x32, o32, n, prec, &fp.parts[n]));
+  const int last_pass = mv_last ? N - 1 : N;   // the last mode may come from the line-search variants
+  for (int n = first; n < last_pass; ++n) CP_TRY(mttkrp_parts(ctx, t, L, u, x32, o32, n, prec, &fp.parts[n]));
   // finish
   fp.L = L;
   int64_t chunks = 0;
@@ -251,6 +267,10 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   fp.f = f;
   fp.d = gd ? d : nullptr;   // g . d only when asked for
   fp.gd = gd;
+  fp.m0_out = m0_out;
+  fp.mv = mv_last;
+  fp.mv_nvar = 1 << (N - 1);
+  fp.mv_beta = mv_beta;
   fp.counter = ctx->d_counter;
   fp.status = ctx->d_status;
   CP_TRY(ws_alloc(ctx, (void**)&fp.blk, sizeof(double) * 2 * (size_t)chunks + 16));
@@ -258,7 +278,7 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   fg_finish_kernel<<<(unsigned)chunks, 256, 0, ctx->stream>>>(fp);
   CP_LAUNCH_CHECK();
   ws_free(ctx, fp.blk);
-  for (int n = first; n < N; ++n) ws_free(ctx, const_cast<void*>(fp.parts[n].p));
+  for (int n = first; n < last_pass; ++n) ws_free(ctx, const_cast<void*>(fp.parts[n].p));
   if (!grams_out) ws_free(ctx, grams);
   if (x32) ws_free(ctx, x32);
   return CP_OK;

@@ -23,10 +23,11 @@ struct SolveCtl;
 // More-Thuente search in one thread.  st receives the final state (stp_eval,
 // f = phi there, nfev, info); poly the 2N + 1 coefficients.  With ctl the
 // solver counters are updated, and with use_h the graph condition h is set to
-// "accept" (info 1, or sufficient decrease at the last trial).
+// "accept" (info 1, or sufficient decrease at the last trial).  mv_out
+// (nullable, 2^(N-1) x I_N x R): the variant MTTKRPs M_v of the last mode.
 cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* base, const double* d,
                   cp_precision prec, const cp_ls_opts& o, MTState* st, double* poly, SolveCtl* ctl,
-                  cudaGraphConditionalHandle h, int use_h);
+                  cudaGraphConditionalHandle h, int use_h, double* mv_out = nullptr);
 
 
 }  // namespace cpg

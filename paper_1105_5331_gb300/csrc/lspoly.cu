@@ -50,6 +50,7 @@ struct CoefParams {
   double norm2;
   double* blk;                  // [2][gridDim.x]
   double* poly;                 // 2N + 1 coefficients out
+  double* mv_out;               // nullable: M_v (nvar x I x R, FP64)
   MTState* st;
   cp_ls_opts o;
   SolveCtl* ctl;                // nullable: solver counters
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(256) ls_coef_kernel(const CoefParams p) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) m += redd[q][lane];
     }
+    if (p.mv_out && in) p.mv_out[(int64_t)v * nout + e] = m;
     double a = in ? m * p.Alast[e] : 0.0;
     double b = in ? m * p.Dlast[e] : 0.0;
 #pragma unroll
@@ -275,7 +277,7 @@ __global__ void mix_kernel(Layout L, const double* __restrict__ a, const double*
 
 cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const double* base, const double* d,
                   cp_precision prec, const cp_ls_opts& o, MTState* st, double* poly, SolveCtl* ctl,
-                  cudaGraphConditionalHandle h, int use_h) {
+                  cudaGraphConditionalHandle h, int use_h, double* mv_out) {
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int N = L.N, R = L.R, RR = R * R;
   const int last = N - 1;
@@ -359,6 +361,7 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
   cp.epoly = epoly;
   cp.norm2 = t->norm2;
   cp.poly = poly;
+  cp.mv_out = mv_out;
   cp.st = st;
   cp.o = o;
   cp.ctl = ctl;

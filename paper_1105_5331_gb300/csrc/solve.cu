@@ -243,8 +243,10 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   for (int n = 0; n < L.N; ++n) Imax = std::max(Imax, L.dims[n]);
   const size_t RR = (size_t)o.R * o.R;
   const int cap = o.w;
+  const size_t n0 = (size_t)L.dims[0] * o.R;                                  // M^(1) of u, ubar, x
+  const size_t nmv = ((size_t)1 << (L.N - 1)) * (size_t)L.dims[L.N - 1] * o.R;  // line-search variants
   const size_t bytes = sizeof(double) * (9 * (size_t)P + 2 * (size_t)cap * P + (size_t)Imax * o.R +
-                                         (size_t)L.N * RR + 16 + 40) +
+                                         (size_t)L.N * RR + 16 + 40 + 3 * n0 + nmv) +
                        sizeof(MTState) + sizeof(SolveCtl) + 512;
   CP_CUDA(cudaMallocAsync(&base, bytes, sub.stream));
   double* p = (double*)base;
@@ -263,6 +265,10 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   m.grams = p; p += (size_t)L.N * RR;
   m.scal = p; p += 16;
   m.poly = p; p += 40;
+  m.M0 = p; p += n0;
+  m.M0bar = p; p += n0;
+  m.M0x = p; p += n0;
+  m.Mv = p; p += nmv;
   m.win = (int*)p; p += 8;
   uintptr_t q = ((uintptr_t)p + 63) & ~(uintptr_t)63;
   m.st = (MTState*)q;
@@ -314,7 +320,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
   cp_status st = [&]() -> cp_status {
     CP_TRY(counted(&kcount.top, [&]() -> cp_status {
       if (first) CP_TRY(normalize_into(ctx, L, m.work, m.u, nullptr, nullptr, nullptr));
-      CP_TRY(fg_eval(ctx, t, L, m.u, m.scal + F, m.g, pr));
+      CP_TRY(fg_eval_ex(ctx, t, L, m.u, nullptr, nullptr, nullptr, m.scal + F, m.g, pr, nullptr, nullptr, m.M0));
       CP_TRY(window_update(ctx, m.win, cap, true, P, m.u, m.g, m.U, m.G));
       return dot(ctx, P, m.g, m.g, m.scal + GG);
     }));
@@ -327,9 +333,10 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
       return with_stream(side[0], [&]() -> cp_status {
         CP_TRY(counted(&kcount.head, [&]() -> cp_status {
           CP_TRY(dcopy(ctx, P, m.u, m.work));
-          CP_TRY(als_sweep_v2(ctx, t, L, m.work, pr, m.grams, false));
+          CP_TRY(als_sweep_v2(ctx, t, L, m.work, pr, m.grams, false, m.M0));
           CP_TRY(normalize_into(ctx, L, m.work, m.ubar, nullptr, nullptr, nullptr, m.grams));
-          CP_TRY(fg_eval(ctx, t, L, m.ubar, m.scal + FBAR, m.gbar, pr));
+          CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, nullptr, nullptr, nullptr, m.scal + FBAR, m.gbar, pr, nullptr,
+                            nullptr, m.M0bar));
           CP_TRY(ngmres_core(ctx, P, m.win, cap, m.U, m.G, m.ubar, m.gbar, o.eps, m.work, nullptr));
           CP_TRY(normalize_into(ctx, L, m.work, m.uhat, nullptr, nullptr, nullptr));
           CP_TRY(sub_vec(ctx, P, m.uhat, m.ubar, m.d));
@@ -348,6 +355,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
                 CP_TRY(dcopy(ctx, P, m.ubar, m.u));
                 CP_TRY(dcopy(ctx, P, m.gbar, m.g));
                 CP_TRY(dcopy(ctx, 1, m.scal + FBAR, m.scal + F));
+                CP_TRY(dcopy(ctx, (int64_t)L.dims[0] * L.R, m.M0bar, m.M0));
                 return window_update(ctx, m.win, cap, true, P, m.u, m.g, m.U, m.G);
               });
             }
@@ -356,21 +364,23 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
             cudaGraphConditionalHandle h_acc;
             CP_TRY(new_handle(side[1], 0, &h_acc));
             CP_TRY(counted(&kcount.ls_fixed, [&]() -> cp_status {
-              return ls_poly(ctx, t, L, m.ubar, m.d, pr, lso, m.st, m.poly, m.ctl, h_acc, 1);
+              return ls_poly(ctx, t, L, m.ubar, m.d, pr, lso, m.st, m.poly, m.ctl, h_acc, 1, m.Mv);
             }));
             return add_conditional(side[1], side[2], h_acc, cudaGraphCondTypeIf, 2, [&](int ab) -> cp_status {
               return with_stream(side[2], [&]() -> cp_status {
                 return counted(ab == 0 ? &kcount.accept : &kcount.reject, [&]() -> cp_status {
                   if (ab == 0) {
                     // x = ubar + beta d, f and g there
+                    // (the last mode's M from the line-search variants)
                     CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, m.d, &m.st->stp_eval, m.x, m.scal + FX, m.gx, pr,
-                                      nullptr, m.grams));
-                    CP_TRY(normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr, m.grams));
+                                      nullptr, m.grams, m.M0x, m.Mv, &m.st->stp_eval));
+                    CP_TRY(normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr, m.grams, m.M0x, m.M0));
                     CP_TRY(dcopy(ctx, 1, m.scal + FX, m.scal + F));
                   } else {
                     CP_TRY(dcopy(ctx, P, m.ubar, m.u));
                     CP_TRY(dcopy(ctx, P, m.gbar, m.g));
                     CP_TRY(dcopy(ctx, 1, m.scal + FBAR, m.scal + F));
+                    CP_TRY(dcopy(ctx, (int64_t)L.dims[0] * L.R, m.M0bar, m.M0));
                   }
                   return window_update(ctx, m.win, cap, false, P, m.u, m.g, m.U, m.G);
                 });

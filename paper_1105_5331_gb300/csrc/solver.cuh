@@ -26,6 +26,9 @@ struct KernelCounts {
 
 struct SolverMem {
   double *u, *g, *ubar, *gbar, *uhat, *d, *x, *gx, *work, *M, *grams, *scal, *poly, *U, *G;
+  // M^(1) of u, ubar and x (the next ALS sweep starts from u's), and the
+  // line-search variant MTTKRPs of the last mode
+  double *M0, *M0bar, *M0x, *Mv;
   int* win;
   MTState* st;
   SolveCtl* ctl;
