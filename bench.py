@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--solve-only", action="store_true",
                    help="time only the headline solves (profiling driver; no side reports)")
+    p.add_argument("--kernel-breakdown", action="store_true",
+                   help="one headline solve under the CUDA profiler (CUPTI): per-kernel launches, device "
+                        "time and critical-path share (ncu does not see kernels inside conditional graph bodies)")
     p.add_argument("--serve-requests", type=int, default=128,
                    help="requests of the 200/s Poisson serving stream replayed (0: skip)")
     p.add_argument("--serve-fp64-requests", type=int, default=32,
@@ -292,8 +295,8 @@ def run_ours(args, rank, world, local_rank):
 
 # DRAM bytes (read + write) per launch of mttkrp_tc_kernel, mode 0 of the
 # 256^3 R=16 workload, from one ncu --set full capture of the current kernel
-# (profiles/mttkrp_tc_dense256.md); None until such a capture exists.
-TC_NCU_TRAFFIC = None
+# (profiles/mttkrp_tc_dense256.md: 67.173888 MB read + 0.314880 MB written).
+TC_NCU_TRAFFIC = 67488768
 
 
 def mttkrp_roofline(cp, ctx, t, u, stream, flush, prec):
@@ -333,9 +336,10 @@ def mttkrp_roofline(cp, ctx, t, u, stream, flush, prec):
                 "per_launch": {"flops": flops, "avg_kernel_ms": d * 1e3, "launches_timed": launches,
                                "avg_cp_mttkrp_call_ms": dc * 1e3},
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
-    # HBM-bound stream of the bf16 hi/lo planes of T_(n): 4 B per element, plus
-    # the FP32 factor tables read and the split-K partials written
-    bytes_ = 4.0 * K + 4.0 * 2 * DIMS[1] * R + 4.0 * 152 * DIMS[0] * R
+    # compulsory traffic of one launch: the bf16 hi/lo planes of T_(n) (4 B
+    # per element), the FP32 factor tables of the other modes and one FP32
+    # I x R result (the split-K partials beyond it stay in L2)
+    bytes_ = 4.0 * K + 4.0 * R * (DIMS[1] + DIMS[2]) + 4.0 * DIMS[0] * R
     ach = bytes_ / d / 1e9
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     return {"kernel": "mttkrp_tc_kernel (tcgen05 bf16x3)", "bound": "hbm", "achieved": ach, "peak": peak,
@@ -526,10 +530,84 @@ def run_mttkrp_only(args):
     print(json.dumps({"mttkrp_only": args.mttkrp_only, "prec": args.prec, **res}))
 
 
+def run_kernel_breakdown(args):
+    """One warm headline solve, then one under torch.profiler (CUPTI activity
+    records, which include kernels launched by CUDA graphs and their
+    conditional bodies).  Prints per-kernel launches, total device time and
+    the time during which each kernel ran alone or shared the GPU."""
+    import collections
+
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+
+    import synth
+    import paper_1105_5331_gb300 as cp
+    prec = cp.CP_MIXED_BF16X3 if args.prec == "mixed" else cp.CP_FP64
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    prob, u0 = synth.workload_dense_256()
+    ctx = cp.cp_ctx_create(0, stream)
+    with torch.cuda.stream(stream):
+        T = torch.from_numpy(prob.T).to(dev)
+        u0d = torch.from_numpy(u0).to(dev)
+        u = torch.empty_like(u0d)
+    stream.synchronize()
+    t = cp.cp_tensor_dense(ctx, T)
+    o = cp.cp_solve_opts_default(R)
+    o.tol = TOL
+    o.prec = prec
+
+    def solve():
+        with torch.cuda.stream(stream):
+            u.copy_(u0d)
+        stream.synchronize()
+        return cp.cp_solve(ctx, t, o, u)
+
+    solve()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        rep = solve()
+        stream.synchronize()
+    kern = [e for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA
+            and "memcpy" not in e.name.lower() and "memset" not in e.name.lower()]
+
+    def short(name):
+        return name.replace("(anonymous namespace)::", "").split("(")[0].replace("cpg::", "").replace("void ", "")
+
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for e in kern:
+        a = agg[short(e.name)]
+        a[0] += 1
+        a[1] += e.time_range.end - e.time_range.start
+    ev = sorted([(e.time_range.start, 1, short(e.name)) for e in kern] + [(e.time_range.end, -1, short(e.name)) for e in kern])
+    active = collections.Counter()
+    alone = collections.defaultdict(float)
+    shared = collections.defaultdict(float)
+    last = ev[0][0]
+    for ts, kind, nm in ev:
+        dt = ts - last
+        names = [k for k, v in active.items() if v]
+        if len(names) == 1:
+            alone[names[0]] += dt
+        elif len(names) > 1:
+            for k in names:
+                shared[k] += dt / len(names)
+        active[nm] += kind
+        last = ts
+    tot = sum(v[1] for v in agg.values())
+    print(json.dumps({"kernel_breakdown": "mixed" if prec != cp.CP_FP64 else "fp64", "iters": rep["iters"],
+                      "fg_evals": rep["fg_evals"], "launches": len(kern), "device_time_ms": tot / 1e3}))
+    print(f"{'kernel':34s} {'launches':>9s} {'total ms':>9s} {'share':>6s} {'avg us':>8s} {'alone ms':>9s} {'shared ms':>9s}")
+    for k, (c, tt) in sorted(agg.items(), key=lambda x: -x[1][1]):
+        print(f"{k:34s} {c:9d} {tt / 1e3:9.3f} {100 * tt / tot:5.1f}% {tt / c:8.2f} {alone[k] / 1e3:9.3f} {shared[k] / 1e3:9.3f}")
+
+
 def main():
     args = parse()
     if args.cpu_sample:
         print(json.dumps(cpu_sample(args.cpu_iters)))
+        return
+    if args.kernel_breakdown:
+        run_kernel_breakdown(args)
         return
     if args.mttkrp_only:
         run_mttkrp_only(args)
