@@ -98,7 +98,10 @@ __global__ void __launch_bounds__(256) norm_apply_kernel(Layout L, const double*
                                                          int S, const double* __restrict__ grams,
                                                          double* __restrict__ lambda_out, int* status,
                                                          const double* __restrict__ m0_src,
-                                                         double* __restrict__ m0_dst) {
+                                                         double* __restrict__ m0_dst,
+                                                         double* __restrict__ grams_out,
+                                                         const double* __restrict__ xi_src,
+                                                         double* __restrict__ xi_dst) {
   __shared__ double nu[CP_MAX_N * CP_MAX_R];
   __shared__ double scale[CP_MAX_N * CP_MAX_R];
   __shared__ double key[CP_MAX_R];
@@ -173,6 +176,30 @@ __global__ void __launch_bounds__(256) norm_apply_kernel(Layout L, const double*
       m0_dst[e] = m0_src[i * R + q] * sc;
     }
   }
+  if (blockIdx.x == 0 && grams_out) {
+    // Grams of dst: G'[n][p][q] = G[n][o_p][o_q] s_n[o_p] s_n[o_q]
+    for (int e = threadIdx.x; e < N * R * R; e += blockDim.x) {
+      const int n = e / (R * R), pq = e - n * R * R;
+      const int pr = pq / R, qr = pq - (pq / R) * R;
+      const int op = order[pr], oq = order[qr];
+      grams_out[e] = grams[(int64_t)n * R * R + op * R + oq] * scale[n * R + op] * scale[n * R + oq];
+    }
+  }
+  if (blockIdx.x == 0 && xi_dst) {
+    // inverse of Gammabar^(1) of dst: Xi'[p][q] = Xi[o_p][o_q] / (S[o_p] S[o_q]),
+    // S[r] = prod_{n >= 2} s_n[r]; the ok flag follows
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+      const int pr = e / R, qr = e - (e / R) * R;
+      const int op = order[pr], oq = order[qr];
+      double sp = 1.0, sq = 1.0;
+      for (int n = 1; n < N; ++n) {
+        sp *= scale[n * R + op];
+        sq *= scale[n * R + oq];
+      }
+      xi_dst[e] = xi_src[op * R + oq] / (sp * sq);
+    }
+    if (threadIdx.x == 0) *(int*)(xi_dst + R * R) = *(const int*)(xi_src + R * R);
+  }
 }
 
 inline int grid_for(cp_ctx* ctx, int64_t n, int threads) {
@@ -206,7 +233,8 @@ cp_status dot(cp_ctx* ctx, int64_t n, const double* x, const double* y, double* 
 
 cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double* dst,
                          const double* gsrc, double* gdst, double* lambda, const double* grams,
-                         const double* m0_src, double* m0_dst) {
+                         const double* m0_src, double* m0_dst, double* grams_out, const double* xi_src,
+                         double* xi_dst) {
   const int R = L.R;
   double* part = nullptr;
   int S = 1;
@@ -221,7 +249,8 @@ cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double
     CP_LAUNCH_CHECK();
   }
   norm_apply_kernel<<<grid_for(ctx, L.P(), 256), 256, 0, ctx->stream>>>(L, src, dst, gsrc, gdst, part, S, grams,
-                                                                        lambda, ctx->d_status, m0_src, m0_dst);
+                                                                        lambda, ctx->d_status, m0_src, m0_dst,
+                                                                        grams ? grams_out : nullptr, xi_src, xi_dst);
   CP_LAUNCH_CHECK();
   if (part) ws_free(ctx, part);
   return CP_OK;

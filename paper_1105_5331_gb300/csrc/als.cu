@@ -154,30 +154,44 @@ struct InvParams {
   int* status;
 };
 
-// One pivot step of in-place Gauss-Jordan inversion from `src` into `dst`
-// (every new entry from old ones only, so one barrier per pivot; every
-// thread forms the pivot reciprocal itself).  With p = 1 / S_kk:
+// In-place Gauss-Jordan inversion of the SPD matrix in A (B: a second buffer).
+// One pivot step maps every entry from the old matrix to the new one, so the
+// two buffers alternate with one barrier per pivot.  With p = 1 / S_kk:
 //   S_ij -= S_ik p S_kj (i, j != k),  S_ik = -S_ik p,  S_kj = -S_kj p,
-//   S_kk = -p;  after all pivots the matrix holds -S^-1.
-__device__ bool gj_inverse2(double* A, double* B, int R, double** out) {
+//   S_kk = -p;  after all pivots the buffer holds -S^-1.  The matrix stays
+// symmetric, so only i <= j is computed (and mirrored), and the thread that
+// computes the next diagonal entry forms its reciprocal at once (look-ahead),
+// so the next pivot starts right after the barrier.
+__device__ bool gj_inverse2(double* A, double* B, int R, double** out, double* piv2, int* flag) {
+  if (threadIdx.x == 0) {
+    const double d = A[0];
+    if (!(d > 0.0) || !isfinite(d)) *flag = 1;
+    else piv2[0] = recip_newton(d);
+  }
+  __syncthreads();
   double* src = A;
   double* dst = B;
   for (int k = 0; k < R; ++k) {
-    const double d = src[k * R + k];
-    if (!(d > 0.0) || !isfinite(d)) return false;   // uniform: every thread reads the same d
-    const double pinv = recip_newton(d);
+    if (*flag) return false;                     // uniform: read after a barrier
+    const double pinv = piv2[k & 1];
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
       const int i = e / R, j = e - (e / R) * R;
+      if (i > j) continue;
       double v;
       if (i == k && j == k)
         v = -pinv;
-      else if (j == k)
-        v = -src[e] * pinv;
       else if (i == k)
-        v = -src[e] * pinv;
+        v = -src[k * R + j] * pinv;
+      else if (j == k)
+        v = -src[i * R + k] * pinv;
       else
-        v = fma(-src[i * R + k] * pinv, src[k * R + j], src[e]);
-      dst[e] = v;
+        v = fma(-src[i * R + k] * pinv, src[k * R + j], src[i * R + j]);
+      dst[i * R + j] = v;
+      dst[j * R + i] = v;
+      if (i == k + 1 && j == k + 1) {
+        if (!(v > 0.0) || !isfinite(v)) *flag = 1;
+        else piv2[(k + 1) & 1] = recip_newton(v);
+      }
     }
     __syncthreads();
     double* t = src;
@@ -210,13 +224,17 @@ __global__ void __launch_bounds__(256) gram_inverse_kernel(const InvParams p) {
       __syncthreads();
     }
   };
+  __shared__ double piv2[2];
+  __shared__ int flag;
   double* res = nullptr;
+  if (threadIdx.x == 0) flag = 0;
   build(0.0);
-  bool ok = gj_inverse2(A, B, R, &res);
+  bool ok = gj_inverse2(A, B, R, &res, piv2, &flag);
   if (!ok) {
     __syncthreads();
+    if (threadIdx.x == 0) flag = 0;
     build(1e-12);
-    ok = gj_inverse2(A, B, R, &res);
+    ok = gj_inverse2(A, B, R, &res, piv2, &flag);
   }
   for (int k = threadIdx.x; k < RR; k += blockDim.x) p.Xinv[k] = ok ? -res[k] : 0.0;
   if (threadIdx.x == 0) {
@@ -331,6 +349,14 @@ __global__ void f32_copy_kernel(Layout L, const double* __restrict__ u, F32Off o
 
 }  // namespace
 
+cp_status gram_inverse_launch(cp_ctx* ctx, cudaStream_t s, const double* grams, const Layout& L, int n, double* xi) {
+  CP_TRY(inverse_smem_attr());
+  InvParams ip{grams, L.N, L.R, n, xi, (int*)(xi + (size_t)L.R * L.R), ctx->d_status};
+  gram_inverse_kernel<<<1, 256, inverse_smem(L.R), s>>>(ip);
+  CP_LAUNCH_CHECK();
+  return CP_OK;
+}
+
 cp_status f32_copy(cp_ctx* ctx, const Layout& L, const double* u, const F32Off& o, int64_t total, float* out) {
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4 * ctx->num_sms));
   f32_copy_kernel<<<blocks, 256, 0, ctx->stream>>>(L, u, o, total, out);
@@ -382,7 +408,7 @@ cp_status grams_of(cp_ctx* ctx, cudaStream_t s, unsigned* counter, const Layout&
 // A_n = M^(n) Gammabar^(n)^-1.  grams (N x R x R) receives the Grams of the
 // updated factors; with grams_valid it already holds those of u on entry.
 cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, double* u, cp_precision prec,
-                       double* grams, bool grams_valid, const double* m0) {
+                       double* grams, bool grams_valid, const double* m0, const double* xi0) {
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int R = L.R, N = L.N, RR = R * R;
   const bool want_f32 = t->kind == 0 && prec == CP_MIXED_BF16X3;
@@ -400,27 +426,31 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
   const int rows = std::max(1, 32 / R);
   for (int n = 0; n < N; ++n) {
     // aux: (Gram of the mode updated last) -> inverse of Gammabar^(n),
-    // overlapped with this mode's MTTKRP on the main stream
-    CP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream));
-    CP_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
-    if (n > 0) CP_TRY(grams_of(ctx, ctx->aux, ctx->d_counter + 1, L, u, n - 1, 1, grams));
-    InvParams ip{grams, N, R, n, Xinv, ok, ctx->d_status};
-    gram_inverse_kernel<<<1, 256, inverse_smem(R), ctx->aux>>>(ip);
-    CP_LAUNCH_CHECK();
-    CP_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
+    // overlapped with this mode's MTTKRP on the main stream; the first mode's
+    // inverse may come precomputed (xi0)
+    const bool pre = n == 0 && xi0;
+    if (!pre) {
+      CP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream));
+      CP_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+      if (n > 0) CP_TRY(grams_of(ctx, ctx->aux, ctx->d_counter + 1, L, u, n - 1, 1, grams));
+      InvParams ip{grams, N, R, n, Xinv, ok, ctx->d_status};
+      gram_inverse_kernel<<<1, 256, inverse_smem(R), ctx->aux>>>(ip);
+      CP_LAUNCH_CHECK();
+      CP_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
+    }
     Parts pt;
     if (n == 0 && m0)
       pt = Parts{m0, 1, 0};
     else
       CP_TRY(mttkrp_parts(ctx, t, L, u, u32, o32, n, prec, &pt));
-    CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    if (!pre) CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     UpdParams up;
     up.parts = pt;
     up.I = L.dims[n];
     up.R = R;
     up.rows = rows;
-    up.Xinv = Xinv;
-    up.ok = ok;
+    up.Xinv = pre ? xi0 : Xinv;
+    up.ok = pre ? (const int*)(xi0 + RR) : ok;
     up.An = u + L.off[n];
     up.An32 = u32 ? u32 + o32.off[n] : nullptr;
     up.rs = o32.rs;

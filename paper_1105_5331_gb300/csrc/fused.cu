@@ -210,7 +210,8 @@ cp_status mttkrp_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double*
 
 cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const double* base, const double* d,
                      const double* stp, double* x, double* f, double* g, cp_precision prec, double* gd,
-                     double* grams_out, double* m0_out, const double* mv_last, const double* mv_beta) {
+                     double* grams_out, double* m0_out, const double* mv_last, const double* mv_beta,
+                     const double* grams_in, double* xi0_out) {
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int R = L.R, N = L.N, RR = R * R;
   const double* u = d ? x : base;
@@ -222,13 +223,15 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   float* x32 = nullptr;
   double* grams = nullptr;
   if (want_f32) CP_TRY(ws_alloc(ctx, (void**)&x32, sizeof(float) * (size_t)acc32 + 64));
-  if (grams_out)
+  if (grams_in)
+    grams = const_cast<double*>(grams_in);
+  else if (grams_out)
     grams = grams_out;
   else
     CP_TRY(ws_alloc(ctx, (void**)&grams, sizeof(double) * (size_t)N * RR));
   CP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream));
   CP_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
-  {
+  if (!grams_in) {
     GramJob jobs[kMaxGramJobs];
     for (int n = 0; n < N; ++n) {
       jobs[n] = GramJob{base + L.off[n], base + L.off[n], L.dims[n], grams + (size_t)n * RR, 1};
@@ -239,6 +242,7 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
     }
     CP_TRY(grams_jobs(ctx, ctx->aux, ctx->d_counter + 1, R, jobs, N));
   }
+  if (xi0_out) CP_TRY(gram_inverse_launch(ctx, ctx->aux, grams, L, 0, xi0_out));
   CP_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
   if (d || x32) {
     const int64_t total = x32 ? acc32 : L.P();
@@ -279,7 +283,7 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   CP_LAUNCH_CHECK();
   ws_free(ctx, fp.blk);
   for (int n = first; n < last_pass; ++n) ws_free(ctx, const_cast<void*>(fp.parts[n].p));
-  if (!grams_out) ws_free(ctx, grams);
+  if (!grams_out && !grams_in) ws_free(ctx, grams);
   if (x32) ws_free(ctx, x32);
   return CP_OK;
 }

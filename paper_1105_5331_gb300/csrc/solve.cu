@@ -98,9 +98,31 @@ __global__ void ctl_after_head_kernel(SolveCtl* c, const double* scal, cudaGraph
   cudaGraphSetConditional(restart, r ? 1u : 0u);
 }
 
+// Up to four copies in one launch (the branch that makes ubar the iterate).
+struct CopySeg {
+  const double* src[4];
+  double* dst[4];
+  int64_t n[4];
+  int nseg;
+};
+
+__global__ void copy_multi_kernel(const CopySeg c) {
+  for (int s = 0; s < c.nseg; ++s)
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < c.n[s]; k += (int64_t)gridDim.x * blockDim.x)
+      c.dst[s][k] = c.src[s][k];
+}
+
 int64_t grid_for(cp_ctx* ctx, int64_t n) {
   const int64_t b = std::min<int64_t>((n + 255) / 256, 8 * (int64_t)ctx->num_sms);
   return std::max<int64_t>(b, 1);
+}
+
+cp_status dcopy_multi(cp_ctx* ctx, const CopySeg& c) {
+  int64_t nmax = 1;
+  for (int s = 0; s < c.nseg; ++s) nmax = std::max(nmax, c.n[s]);
+  copy_multi_kernel<<<(unsigned)grid_for(ctx, nmax), 256, 0, ctx->stream>>>(c);
+  CP_LAUNCH_CHECK();
+  return CP_OK;
 }
 
 cp_status dcopy(cp_ctx* ctx, int64_t n, const double* a, double* b) {
@@ -246,7 +268,8 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   const size_t n0 = (size_t)L.dims[0] * o.R;                                  // M^(1) of u, ubar, x
   const size_t nmv = ((size_t)1 << (L.N - 1)) * (size_t)L.dims[L.N - 1] * o.R;  // line-search variants
   const size_t bytes = sizeof(double) * (9 * (size_t)P + 2 * (size_t)cap * P + (size_t)Imax * o.R +
-                                         (size_t)L.N * RR + 16 + 40 + 3 * n0 + nmv) +
+                                         (size_t)L.N * RR + 16 + 40 + 3 * n0 + nmv + 2 * (size_t)L.N * RR +
+                                         3 * (RR + 2)) +
                        sizeof(MTState) + sizeof(SolveCtl) + 512;
   CP_CUDA(cudaMallocAsync(&base, bytes, sub.stream));
   double* p = (double*)base;
@@ -269,6 +292,11 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   m.M0bar = p; p += n0;
   m.M0x = p; p += n0;
   m.Mv = p; p += nmv;
+  m.Gu = p; p += (size_t)L.N * RR;
+  m.Gbar = p; p += (size_t)L.N * RR;
+  m.Xi0 = p; p += RR + 2;
+  m.Xi0bar = p; p += RR + 2;
+  m.Xi0x = p; p += RR + 2;
   m.win = (int*)p; p += 8;
   uintptr_t q = ((uintptr_t)p + 63) & ~(uintptr_t)63;
   m.st = (MTState*)q;
@@ -316,11 +344,27 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
     *slot += g_launches.load() - a;
     return r;
   };
+  // ubar becomes the iterate: f, M^(1), Grams and Gammabar^(1) inverse follow
+  CopySeg ubar_state{};
+  ubar_state.nseg = 4;
+  ubar_state.src[0] = m.scal + FBAR;
+  ubar_state.dst[0] = m.scal + F;
+  ubar_state.n[0] = 1;
+  ubar_state.src[1] = m.M0bar;
+  ubar_state.dst[1] = m.M0;
+  ubar_state.n[1] = (int64_t)L.dims[0] * L.R;
+  ubar_state.src[2] = m.Gbar;
+  ubar_state.dst[2] = m.Gu;
+  ubar_state.n[2] = (int64_t)L.N * L.R * L.R;
+  ubar_state.src[3] = m.Xi0bar;
+  ubar_state.dst[3] = m.Xi0;
+  ubar_state.n[3] = (int64_t)L.R * L.R + 2;
   CP_CUDA(cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed));
   cp_status st = [&]() -> cp_status {
     CP_TRY(counted(&kcount.top, [&]() -> cp_status {
       if (first) CP_TRY(normalize_into(ctx, L, m.work, m.u, nullptr, nullptr, nullptr));
-      CP_TRY(fg_eval_ex(ctx, t, L, m.u, nullptr, nullptr, nullptr, m.scal + F, m.g, pr, nullptr, nullptr, m.M0));
+      CP_TRY(fg_eval_ex(ctx, t, L, m.u, nullptr, nullptr, nullptr, m.scal + F, m.g, pr, nullptr, m.Gu, m.M0,
+                        nullptr, nullptr, nullptr, m.Xi0));
       CP_TRY(window_update(ctx, m.win, cap, true, P, m.u, m.g, m.U, m.G));
       return dot(ctx, P, m.g, m.g, m.scal + GG);
     }));
@@ -333,10 +377,13 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
       return with_stream(side[0], [&]() -> cp_status {
         CP_TRY(counted(&kcount.head, [&]() -> cp_status {
           CP_TRY(dcopy(ctx, P, m.u, m.work));
-          CP_TRY(als_sweep_v2(ctx, t, L, m.work, pr, m.grams, false, m.M0));
-          CP_TRY(normalize_into(ctx, L, m.work, m.ubar, nullptr, nullptr, nullptr, m.grams));
+          // (u's Grams, M^(1) and Gammabar^(1) inverse carried over from the
+          // point u was made from)
+          CP_TRY(als_sweep_v2(ctx, t, L, m.work, pr, m.Gu, true, m.M0, m.Xi0));
+          CP_TRY(normalize_into(ctx, L, m.work, m.ubar, nullptr, nullptr, nullptr, m.Gu, nullptr, nullptr,
+                                m.Gbar));
           CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, nullptr, nullptr, nullptr, m.scal + FBAR, m.gbar, pr, nullptr,
-                            nullptr, m.M0bar));
+                            nullptr, m.M0bar, nullptr, nullptr, m.Gbar, m.Xi0bar));
           CP_TRY(ngmres_core(ctx, P, m.win, cap, m.U, m.G, m.ubar, m.gbar, o.eps, m.work, nullptr));
           CP_TRY(normalize_into(ctx, L, m.work, m.uhat, nullptr, nullptr, nullptr));
           CP_TRY(sub_vec(ctx, P, m.uhat, m.ubar, m.d));
@@ -354,8 +401,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
               return counted(&kcount.restart, [&]() -> cp_status {
                 CP_TRY(dcopy(ctx, P, m.ubar, m.u));
                 CP_TRY(dcopy(ctx, P, m.gbar, m.g));
-                CP_TRY(dcopy(ctx, 1, m.scal + FBAR, m.scal + F));
-                CP_TRY(dcopy(ctx, (int64_t)L.dims[0] * L.R, m.M0bar, m.M0));
+                CP_TRY(dcopy_multi(ctx, ubar_state));
                 return window_update(ctx, m.win, cap, true, P, m.u, m.g, m.U, m.G);
               });
             }
@@ -373,14 +419,14 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
                     // x = ubar + beta d, f and g there
                     // (the last mode's M from the line-search variants)
                     CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, m.d, &m.st->stp_eval, m.x, m.scal + FX, m.gx, pr,
-                                      nullptr, m.grams, m.M0x, m.Mv, &m.st->stp_eval));
-                    CP_TRY(normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr, m.grams, m.M0x, m.M0));
+                                      nullptr, m.grams, m.M0x, m.Mv, &m.st->stp_eval, nullptr, m.Xi0x));
+                    CP_TRY(normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr, m.grams, m.M0x, m.M0, m.Gu,
+                                          m.Xi0x, m.Xi0));
                     CP_TRY(dcopy(ctx, 1, m.scal + FX, m.scal + F));
                   } else {
                     CP_TRY(dcopy(ctx, P, m.ubar, m.u));
                     CP_TRY(dcopy(ctx, P, m.gbar, m.g));
-                    CP_TRY(dcopy(ctx, 1, m.scal + FBAR, m.scal + F));
-                    CP_TRY(dcopy(ctx, (int64_t)L.dims[0] * L.R, m.M0bar, m.M0));
+                    CP_TRY(dcopy_multi(ctx, ubar_state));
                   }
                   return window_update(ctx, m.win, cap, false, P, m.u, m.g, m.U, m.G);
                 });

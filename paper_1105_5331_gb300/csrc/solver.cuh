@@ -29,6 +29,9 @@ struct SolverMem {
   // M^(1) of u, ubar and x (the next ALS sweep starts from u's), and the
   // line-search variant MTTKRPs of the last mode
   double *M0, *M0bar, *M0x, *Mv;
+  // Grams of u and ubar (N x R x R); inverses of Gammabar^(1) of u, ubar and
+  // x with their ok flags (R*R + 2 doubles each)
+  double *Gu, *Gbar, *Xi0, *Xi0bar, *Xi0x;
   int* win;
   MTState* st;
   SolveCtl* ctl;
