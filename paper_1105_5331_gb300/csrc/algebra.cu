@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "cp_internal.cuh"
+#include "norm_dev.cuh"
 
 namespace cpg {
 
@@ -102,53 +103,11 @@ __global__ void __launch_bounds__(256) norm_apply_kernel(Layout L, const double*
                                                          double* __restrict__ grams_out,
                                                          const double* __restrict__ xi_src,
                                                          double* __restrict__ xi_dst) {
-  __shared__ double nu[CP_MAX_N * CP_MAX_R];
-  __shared__ double scale[CP_MAX_N * CP_MAX_R];
-  __shared__ double key[CP_MAX_R];
-  __shared__ double lam[CP_MAX_R];
-  __shared__ int order[CP_MAX_R];
+  __shared__ NormShared sh;
+  norm_prologue(L, part, S, grams, lambda_out, status, sh);
+  const double* scale = sh.scale;
+  const int* order = sh.order;
   const int N = L.N, R = L.R;
-  for (int t = threadIdx.x; t < N * R; t += blockDim.x) {
-    const int n = t / R, r = t - (t / R) * R;
-    double s;
-    if (grams) {
-      s = grams[(int64_t)n * R * R + r * R + r];
-    } else {
-      double s0 = 0.0, s1 = 0.0;
-      int c = 0;
-      for (; c + 1 < S; c += 2) {
-        s0 += part[((int64_t)n * S + c) * R + r];
-        s1 += part[((int64_t)n * S + c + 1) * R + r];
-      }
-      if (c < S) s0 += part[((int64_t)n * S + c) * R + r];
-      s = s0 + s1;
-    }
-    nu[t] = sqrt(s);
-  }
-  __syncthreads();
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    double l = 1.0;
-    bool zero = false;
-    for (int n = 0; n < N; ++n) {
-      l *= nu[n * R + r];
-      if (nu[n * R + r] == 0.0) zero = true;
-    }
-    if (zero) l = 0.0;
-    const double root = pow(l, 1.0 / N);
-    for (int n = 0; n < N; ++n) scale[n * R + r] = zero ? 1.0 : root / nu[n * R + r];
-    lam[r] = l;
-    key[r] = isnan(l) ? -INFINITY : l;
-    if (!isfinite(l) && blockIdx.x == 0) record_status(status, CP_ERR_NONFINITE);
-  }
-  __syncthreads();
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    int rank = 0;
-    for (int s = 0; s < R; ++s)
-      if (key[s] > key[r] || (key[s] == key[r] && s < r)) ++rank;
-    order[rank] = r;
-    if (lambda_out && blockIdx.x == 0) lambda_out[rank] = lam[r];
-  }
-  __syncthreads();
   const int64_t P = L.off[L.N];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P;
        e += (int64_t)gridDim.x * blockDim.x) {

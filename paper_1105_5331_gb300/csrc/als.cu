@@ -171,11 +171,19 @@ __device__ bool gj_inverse2(double* A, double* B, int R, double** out, double* p
   __syncthreads();
   double* src = A;
   double* dst = B;
+  // this thread's entries e = tid, tid + blockDim, ... as (i, j), stepped
+  // without divisions (the same entries at every pivot)
+  const int i0 = (int)threadIdx.x / R, j0 = (int)threadIdx.x - ((int)threadIdx.x / R) * R;
+  const int qi = (int)blockDim.x / R, qj = (int)blockDim.x - ((int)blockDim.x / R) * R;
   for (int k = 0; k < R; ++k) {
     if (*flag) return false;                     // uniform: read after a barrier
     const double pinv = piv2[k & 1];
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-      const int i = e / R, j = e - (e / R) * R;
+    int i = i0, j = j0;
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x, i += qi, j += qj) {
+      if (j >= R) {
+        j -= R;
+        ++i;
+      }
       if (i > j) continue;
       double v;
       if (i == k && j == k)

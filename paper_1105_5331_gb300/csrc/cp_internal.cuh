@@ -264,9 +264,13 @@ cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double
 
 // Window-indexed N-GMRES Step II.  win (device) = {start, m}; window row j
 // (oldest first) is ring slot (start + j) % cap.
+// With L and colsq, the combine pass also writes the column sums of squares
+// of uhat per block, colsq[n][S][R] (S blocks, returned in *S_out; colsq needs
+// N x (2 x SMs + 1) x R doubles).
 cp_status ngmres_core(cp_ctx* ctx, int64_t P, const int* win, int cap, const double* U,
                       const double* G, const double* ubar, const double* gbar, double eps,
-                      double* uhat, double* alpha);
+                      double* uhat, double* alpha, const Layout* L = nullptr, double* colsq = nullptr,
+                      int* S_out = nullptr);
 // Push (u, g) into the window ring (or reset it to {(u, g)}).
 cp_status window_update(cp_ctx* ctx, int* win, int cap, bool reset, int64_t P, const double* u,
                         const double* g, double* U, double* G);

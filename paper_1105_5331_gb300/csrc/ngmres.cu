@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) ngmres_reduce_solve_kernel(const double* 
                                                                   int* status) {
   __shared__ double red[8][33];
   __shared__ double Ab[CP_MAX_W * (CP_MAX_W + 1)];
-  __shared__ double piv, dmax;
+  __shared__ double dmax;
   __shared__ int flag;
   __shared__ bool is_last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -163,19 +163,36 @@ __global__ void __launch_bounds__(256) ngmres_reduce_solve_kernel(const double* 
     if (threadIdx.x == 0) *counter = 0u;
     return;
   }
+  // Elimination of column k from every other row touches columns > k only
+  // and never row k, so it runs in place with one barrier per pivot; the
+  // thread that updates the next diagonal entry forms its reciprocal at once
+  // (look-ahead).  Each thread keeps the same entries (i, j) of the m x W
+  // array at every pivot, stepped without divisions.
+  __shared__ double piv2[2];
+  if (threadIdx.x == 0) {
+    const double d = Ab[0];
+    if (!(d > 0.0) || !isfinite(d)) flag = 1;
+    else piv2[0] = recip_nr(d);
+  }
+  __syncthreads();
+  const int i0 = (int)threadIdx.x / W, j0 = (int)threadIdx.x - ((int)threadIdx.x / W) * W;
+  const int qi = (int)blockDim.x / W, qj = (int)blockDim.x - ((int)blockDim.x / W) * W;
   for (int k = 0; k < m; ++k) {
-    if (threadIdx.x == 0) {
-      const double d = Ab[k * W + k];
-      if (!(d > 0.0) || !isfinite(d)) flag = 1;
-      else piv = recip_nr(d);
-    }
-    __syncthreads();
-    if (flag) break;
-    const double pinv = piv;
-    // eliminate column k from every other row (columns > k and the rhs)
-    for (int e = threadIdx.x; e < m * (W - k - 1); e += blockDim.x) {
-      const int i = e / (W - k - 1), j = k + 1 + e % (W - k - 1);
-      if (i != k) Ab[i * W + j] = fma(-Ab[i * W + k] * pinv, Ab[k * W + j], Ab[i * W + j]);
+    if (flag) break;                             // uniform: read after a barrier
+    const double pinv = piv2[k & 1];
+    int i = i0, j = j0;
+    for (int e = threadIdx.x; e < m * W; e += blockDim.x, i += qi, j += qj) {
+      if (j >= W) {
+        j -= W;
+        ++i;
+      }
+      if (i == k || j <= k) continue;
+      const double v = fma(-Ab[i * W + k] * pinv, Ab[k * W + j], Ab[i * W + j]);
+      Ab[i * W + j] = v;
+      if (i == k + 1 && j == k + 1) {
+        if (!(v > 0.0) || !isfinite(v)) flag = 1;
+        else piv2[(k + 1) & 1] = recip_nr(v);
+      }
     }
     __syncthreads();
   }
@@ -189,11 +206,17 @@ __global__ void __launch_bounds__(256) ngmres_reduce_solve_kernel(const double* 
   if (threadIdx.x == 0) *counter = 0u;
 }
 
+// uhat = ubar + sum_j alpha_j (ubar - u_j) over contiguous chunks of `chunk`
+// entries (a multiple of R).  With colsq, the block size is a multiple of R so
+// every thread stays on one rank r, and the block's column sums of squares of
+// uhat per (mode, r) go to colsq[block][n][r] (fixed order).
 __global__ void ngmres_combine_kernel(const double* __restrict__ U, const int* __restrict__ win, int cap,
                                       int64_t P, const double* __restrict__ ubar,
-                                      const double* __restrict__ alpha, double* __restrict__ uhat) {
+                                      const double* __restrict__ alpha, double* __restrict__ uhat, Layout L,
+                                      int64_t chunk, double* __restrict__ colsq) {
   __shared__ double a[CP_MAX_W];
   __shared__ int slot[CP_MAX_W];
+  __shared__ double red[CP_MAX_N * 256];     // [N][blockDim] per-thread sums
   const int start = win[0];
   const int m = win[1];
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
@@ -201,10 +224,21 @@ __global__ void ngmres_combine_kernel(const double* __restrict__ U, const int* _
     slot[j] = (start + j) % cap;
   }
   __syncthreads();
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
-       k += (int64_t)gridDim.x * blockDim.x) {
+  const int R = L.R;
+  const int64_t kb = (int64_t)blockIdx.x * chunk;
+  const int64_t ke = min(P, kb + chunk);
+  int n = 0;
+  while (n + 1 < L.N && kb + (int64_t)threadIdx.x >= L.off[n + 1]) ++n;
+  double acc = 0.0;
+  int curn = n;
+  // per-thread sums of squares, flushed into shared memory when the mode changes
+  double* mine = red;
+  const bool want = colsq != nullptr;
+  if (want)
+    for (int q = threadIdx.x; q < L.N * (int)blockDim.x; q += blockDim.x) red[q] = 0.0;
+  __syncthreads();
+  for (int64_t k = kb + threadIdx.x; k < ke; k += blockDim.x) {
     const double ub = ubar[k];
-    // four independent chains over the window, added in a fixed order
     double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
     int j = 0;
     for (; j + 3 < m; j += 4) {
@@ -214,7 +248,27 @@ __global__ void ngmres_combine_kernel(const double* __restrict__ U, const int* _
       c3 = fma(a[j + 3], ub - U[(int64_t)slot[j + 3] * P + k], c3);
     }
     for (; j < m; ++j) c0 = fma(a[j], ub - U[(int64_t)slot[j] * P + k], c0);
-    uhat[k] = ub + ((c0 + c1) + (c2 + c3));
+    const double v = ub + ((c0 + c1) + (c2 + c3));
+    uhat[k] = v;
+    if (want) {
+      while (n + 1 < L.N && k >= L.off[n + 1]) ++n;
+      if (n != curn) {
+        mine[curn * blockDim.x + threadIdx.x] = acc;
+        acc = 0.0;
+        curn = n;
+      }
+      acc = fma(v, v, acc);
+    }
+  }
+  if (!want) return;
+  mine[curn * blockDim.x + threadIdx.x] = acc;
+  __syncthreads();
+  // thread t holds rank t % R; add the threads of each (mode, rank) in order
+  for (int q = threadIdx.x; q < L.N * R; q += blockDim.x) {
+    const int nn = q / R, r = q - (q / R) * R;
+    double s = 0.0;
+    for (int t = r; t < (int)blockDim.x; t += R) s += mine[nn * blockDim.x + t];
+    colsq[((int64_t)nn * gridDim.x + blockIdx.x) * R + r] = s;
   }
 }
 
@@ -247,7 +301,8 @@ __global__ void window_index_kernel(int* win, int cap, int reset) {
 }  // namespace
 
 cp_status ngmres_core(cp_ctx* ctx, int64_t P, const int* win, int cap, const double* U, const double* G,
-                      const double* ubar, const double* gbar, double eps, double* uhat, double* alpha) {
+                      const double* ubar, const double* gbar, double eps, double* uhat, double* alpha,
+                      const Layout* L, double* colsq, int* S_out) {
   if (cap < 1 || cap > CP_MAX_W) {
     set_error("ngmres: window capacity %d outside [1, %d]", cap, CP_MAX_W);
     return CP_ERR_ARG;
@@ -269,9 +324,27 @@ cp_status ngmres_core(cp_ctx* ctx, int64_t P, const int* win, int cap, const dou
   ngmres_reduce_solve_kernel<<<(unsigned)((nout_max + 31) / 32), 256, 0, ctx->stream>>>(
       part, (int)nb, nout_max, win, eps, sums, a, ctx->d_counter, ctx->d_status);
   CP_LAUNCH_CHECK();
-  int64_t cb = std::min<int64_t>((P + 255) / 256, 8 * (int64_t)ctx->num_sms);
-  ngmres_combine_kernel<<<(unsigned)std::max<int64_t>(cb, 1), 256, 0, ctx->stream>>>(U, win, cap, P, ubar, a,
-                                                                                      uhat);
+  if (L && colsq) {
+    // block size a multiple of R, chunks a multiple of the block size: every
+    // thread keeps one rank, and the chunks tile the modes' R-aligned rows
+    const int threads = std::max(L->R, (256 / L->R) * L->R);
+    const int64_t per = std::max<int64_t>(1, (P + 2 * (int64_t)ctx->num_sms - 1) / (2 * (int64_t)ctx->num_sms));
+    const int64_t chunk = (per + threads - 1) / threads * threads;
+    const int64_t cb = (P + chunk - 1) / chunk;
+    *S_out = (int)cb;
+    ngmres_combine_kernel<<<(unsigned)cb, threads, 0, ctx->stream>>>(U, win, cap, P, ubar, a, uhat, *L, chunk,
+                                                                     colsq);
+  } else {
+    Layout L1;
+    L1.N = 1;
+    L1.R = 1;
+    L1.off[0] = 0;
+    L1.off[1] = P;
+    int64_t cb = std::min<int64_t>((P + 255) / 256, 8 * (int64_t)ctx->num_sms);
+    cb = std::max<int64_t>(cb, 1);
+    const int64_t chunk = (P + cb - 1) / cb;
+    ngmres_combine_kernel<<<(unsigned)cb, 256, 0, ctx->stream>>>(U, win, cap, P, ubar, a, uhat, L1, chunk, nullptr);
+  }
   CP_LAUNCH_CHECK();
   ws_free(ctx, part);
   return CP_OK;

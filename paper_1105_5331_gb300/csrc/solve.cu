@@ -33,6 +33,7 @@
 
 #include "cp_internal.cuh"
 #include "linesearch.cuh"
+#include "norm_dev.cuh"
 #include "solver.cuh"
 
 namespace cpg {
@@ -98,11 +99,11 @@ __global__ void ctl_after_head_kernel(SolveCtl* c, const double* scal, cudaGraph
   cudaGraphSetConditional(restart, r ? 1u : 0u);
 }
 
-// Up to four copies in one launch (the branch that makes ubar the iterate).
+// Up to six copies in one launch (the branches that make ubar the iterate).
 struct CopySeg {
-  const double* src[4];
-  double* dst[4];
-  int64_t n[4];
+  const double* src[6];
+  double* dst[6];
+  int64_t n[6];
   int nseg;
 };
 
@@ -110,6 +111,137 @@ __global__ void copy_multi_kernel(const CopySeg c) {
   for (int s = 0; s < c.nseg; ++s)
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < c.n[s]; k += (int64_t)gridDim.x * blockDim.x)
       c.dst[s][k] = c.src[s][k];
+}
+
+// Block sum of one value per thread (fixed order); thread 0 returns it.
+__device__ double block_sum(double v, double* red8) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red8[w];
+  return s;
+}
+
+__device__ bool is_last_block(unsigned* counter, bool* flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (*flag) __threadfence();
+  return *flag;
+}
+
+// Sum of the per-block partials, in block order, by warp 0 (result in lane 0).
+__device__ double sum_blocks(const double* blk, int nb) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 32) s += __ldcg(&blk[b]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// After the N-GMRES combination (Section 2.1 Step II): normalise uhat with
+// the scales from the combine pass's column sums (R6), d = uhat - ubar, the
+// slope s = g(ubar)^T d, and the restart decision s >= 0 (R7).
+__global__ void __launch_bounds__(256) uhat_finish_kernel(Layout L, const double* __restrict__ uhat,
+                                                          const double* __restrict__ ubar,
+                                                          const double* __restrict__ gbar,
+                                                          const double* __restrict__ colsq, int S,
+                                                          double* __restrict__ d, double* blk, unsigned* counter,
+                                                          SolveCtl* c, double* scal, cudaGraphConditionalHandle restart,
+                                                          int* status) {
+  __shared__ NormShared sh;
+  __shared__ double red8[8];
+  __shared__ bool is_last;
+  norm_prologue(L, colsq, S, nullptr, nullptr, status, sh);
+  const int R = L.R;
+  const int64_t P = L.off[L.N];
+  double part = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
+    int n = 0;
+    while (n + 1 < L.N && e >= L.off[n + 1]) ++n;
+    const int64_t within = e - L.off[n];
+    const int64_t i = within / R;
+    const int p = (int)(within - i * R);
+    const int q = sh.order[p];
+    const double v = uhat[L.off[n] + i * R + q] * sh.scale[n * R + q];
+    const double dv = v - ubar[e];
+    d[e] = dv;
+    part = fma(gbar[e], dv, part);
+  }
+  const double bs = block_sum(part, red8);
+  if (threadIdx.x == 0) blk[blockIdx.x] = bs;
+  if (!is_last_block(counter, &is_last)) return;
+  if (threadIdx.x < 32) {
+    const double slope = sum_blocks(blk, gridDim.x);
+    if (threadIdx.x == 0) {
+      scal[SLOPE] = slope;
+      c->als_sweeps += 1;
+      c->fg_evals += 1;
+      const bool r = !(slope < 0.0);
+      c->restart_now = r ? 1 : 0;
+      if (r) c->restarts += 1;
+      cudaGraphSetConditional(restart, r ? 1u : 0u);
+      *counter = 0u;
+    }
+  }
+}
+
+// End of an iteration (or start of a phase): push (u, g) into the window ring
+// (reset to {(u, g)} at a phase start or after a restart), ||g||^2, and the
+// stopping test that sets the WHILE condition.
+__global__ void __launch_bounds__(256) tail_kernel(const double* __restrict__ u, const double* __restrict__ g,
+                                                   double* __restrict__ U, double* __restrict__ G, int* win, int cap,
+                                                   int64_t P, SolveCtl* c, double* scal, double Pd, double tol,
+                                                   int maxit, int mixed, int stall,
+                                                   cudaGraphConditionalHandle outer, double* blk, unsigned* counter,
+                                                   int begin) {
+  __shared__ double red8[8];
+  __shared__ bool is_last;
+  const int reset = begin ? 1 : c->restart_now;
+  const int start = win[0], m = win[1];
+  const int slot = reset ? 0 : (m < cap ? (start + m) % cap : start);
+  double part = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    const double gk = g[k];
+    U[(int64_t)slot * P + k] = u[k];
+    G[(int64_t)slot * P + k] = gk;
+    part = fma(gk, gk, part);
+  }
+  const double bs = block_sum(part, red8);
+  if (threadIdx.x == 0) blk[blockIdx.x] = bs;
+  if (!is_last_block(counter, &is_last)) return;
+  if (threadIdx.x < 32) {
+    const double gg = sum_blocks(blk, gridDim.x);
+    if (threadIdx.x == 0) {
+      scal[GG] = gg;
+      if (reset) {
+        win[0] = 0;
+        win[1] = 1;
+      } else if (win[1] < cap) {
+        win[1] += 1;
+      } else {
+        win[0] = (win[0] + 1) % cap;
+      }
+      if (begin) {
+        c->best = INFINITY;
+        c->since_best = 0;
+        c->fg_evals += 1;
+      } else {
+        c->iters += 1;
+        if (mixed)
+          c->mixed_iters += 1;
+        else
+          c->fp64_iters += 1;
+      }
+      c->restart_now = 0;
+      ctl_eval(c, scal, Pd, tol, maxit, mixed, stall, outer);
+      *counter = 0u;
+    }
+  }
 }
 
 int64_t grid_for(cp_ctx* ctx, int64_t n) {
@@ -344,66 +476,80 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
     *slot += g_launches.load() - a;
     return r;
   };
-  // ubar becomes the iterate: f, M^(1), Grams and Gammabar^(1) inverse follow
+  // ubar becomes the iterate: u, g, f, M^(1), Grams and Gammabar^(1) inverse follow
   CopySeg ubar_state{};
-  ubar_state.nseg = 4;
-  ubar_state.src[0] = m.scal + FBAR;
-  ubar_state.dst[0] = m.scal + F;
-  ubar_state.n[0] = 1;
-  ubar_state.src[1] = m.M0bar;
-  ubar_state.dst[1] = m.M0;
-  ubar_state.n[1] = (int64_t)L.dims[0] * L.R;
-  ubar_state.src[2] = m.Gbar;
-  ubar_state.dst[2] = m.Gu;
-  ubar_state.n[2] = (int64_t)L.N * L.R * L.R;
-  ubar_state.src[3] = m.Xi0bar;
-  ubar_state.dst[3] = m.Xi0;
-  ubar_state.n[3] = (int64_t)L.R * L.R + 2;
+  ubar_state.nseg = 6;
+  ubar_state.src[0] = m.ubar;
+  ubar_state.dst[0] = m.u;
+  ubar_state.n[0] = P;
+  ubar_state.src[1] = m.gbar;
+  ubar_state.dst[1] = m.g;
+  ubar_state.n[1] = P;
+  ubar_state.src[2] = m.scal + FBAR;
+  ubar_state.dst[2] = m.scal + F;
+  ubar_state.n[2] = 1;
+  ubar_state.src[3] = m.M0bar;
+  ubar_state.dst[3] = m.M0;
+  ubar_state.n[3] = (int64_t)L.dims[0] * L.R;
+  ubar_state.src[4] = m.Gbar;
+  ubar_state.dst[4] = m.Gu;
+  ubar_state.n[4] = (int64_t)L.N * L.R * L.R;
+  ubar_state.src[5] = m.Xi0bar;
+  ubar_state.dst[5] = m.Xi0;
+  ubar_state.n[5] = (int64_t)L.R * L.R + 2;
+  const unsigned vec_blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 2 * (int64_t)sub.num_sms));
+  auto tail = [&](cudaStream_t st, cudaGraphConditionalHandle h, int begin) -> cp_status {
+    double* blk = nullptr;
+    CP_TRY(ws_alloc(ctx, (void**)&blk, sizeof(double) * vec_blocks));
+    tail_kernel<<<vec_blocks, 256, 0, st>>>(m.u, m.g, m.U, m.G, m.win, cap, P, m.ctl, m.scal, Pd, tol, maxit,
+                                            mixed ? 1 : 0, stall, h, blk, ctx->d_counter, begin);
+    CP_LAUNCH_CHECK();
+    ws_free(ctx, blk);
+    return CP_OK;
+  };
   CP_CUDA(cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed));
   cp_status st = [&]() -> cp_status {
+    cudaGraphConditionalHandle h_outer;
+    CP_TRY(new_handle(s0, 0, &h_outer));
     CP_TRY(counted(&kcount.top, [&]() -> cp_status {
       if (first) CP_TRY(normalize_into(ctx, L, m.work, m.u, nullptr, nullptr, nullptr));
       CP_TRY(fg_eval_ex(ctx, t, L, m.u, nullptr, nullptr, nullptr, m.scal + F, m.g, pr, nullptr, m.Gu, m.M0,
                         nullptr, nullptr, nullptr, m.Xi0));
-      CP_TRY(window_update(ctx, m.win, cap, true, P, m.u, m.g, m.U, m.G));
-      return dot(ctx, P, m.g, m.g, m.scal + GG);
+      // window <- {(u, g)}, ||g||^2, the stopping test
+      return tail(s0, h_outer, 1);
     }));
-    cudaGraphConditionalHandle h_outer;
-    CP_TRY(new_handle(s0, 0, &h_outer));
-    ctl_begin_kernel<<<1, 1, 0, s0>>>(m.ctl, m.scal, Pd, tol, maxit, mixed ? 1 : 0, stall, h_outer);
-    CP_LAUNCH_CHECK();
-    kcount.top += 1;
     CP_TRY(add_conditional(s0, side[0], h_outer, cudaGraphCondTypeWhile, 1, [&](int) -> cp_status {
       return with_stream(side[0], [&]() -> cp_status {
-        CP_TRY(counted(&kcount.head, [&]() -> cp_status {
-          CP_TRY(dcopy(ctx, P, m.u, m.work));
-          // (u's Grams, M^(1) and Gammabar^(1) inverse carried over from the
-          // point u was made from)
-          CP_TRY(als_sweep_v2(ctx, t, L, m.work, pr, m.Gu, true, m.M0, m.Xi0));
-          CP_TRY(normalize_into(ctx, L, m.work, m.ubar, nullptr, nullptr, nullptr, m.Gu, nullptr, nullptr,
-                                m.Gbar));
-          CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, nullptr, nullptr, nullptr, m.scal + FBAR, m.gbar, pr, nullptr,
-                            nullptr, m.M0bar, nullptr, nullptr, m.Gbar, m.Xi0bar));
-          CP_TRY(ngmres_core(ctx, P, m.win, cap, m.U, m.G, m.ubar, m.gbar, o.eps, m.work, nullptr));
-          CP_TRY(normalize_into(ctx, L, m.work, m.uhat, nullptr, nullptr, nullptr));
-          CP_TRY(sub_vec(ctx, P, m.uhat, m.ubar, m.d));
-          return dot(ctx, P, m.gbar, m.d, m.scal + SLOPE);
-        }));
         cudaGraphConditionalHandle h_restart;
         CP_TRY(new_handle(side[0], 0, &h_restart));
-        ctl_after_head_kernel<<<1, 1, 0, side[0]>>>(m.ctl, m.scal, h_restart);
-        CP_LAUNCH_CHECK();
-        kcount.head += 1;
+        CP_TRY(counted(&kcount.head, [&]() -> cp_status {
+          // Step I on u in place (u itself is already in the window); u's
+          // Grams, M^(1) and Gammabar^(1) inverse were carried over from the
+          // point u was made from
+          CP_TRY(als_sweep_v2(ctx, t, L, m.u, pr, m.Gu, true, m.M0, m.Xi0));
+          CP_TRY(normalize_into(ctx, L, m.u, m.ubar, nullptr, nullptr, nullptr, m.Gu, nullptr, nullptr, m.Gbar));
+          CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, nullptr, nullptr, nullptr, m.scal + FBAR, m.gbar, pr, nullptr,
+                            nullptr, m.M0bar, nullptr, nullptr, m.Gbar, m.Xi0bar));
+          // Step II, then normalise uhat, d = uhat - ubar, slope, restart test
+          double* colsq = nullptr;
+          double* blk = nullptr;
+          int S = 1;
+          CP_TRY(ws_alloc(ctx, (void**)&colsq, sizeof(double) * (size_t)L.N * (2 * sub.num_sms + 2) * L.R));
+          CP_TRY(ws_alloc(ctx, (void**)&blk, sizeof(double) * vec_blocks));
+          CP_TRY(ngmres_core(ctx, P, m.win, cap, m.U, m.G, m.ubar, m.gbar, o.eps, m.work, nullptr, &L, colsq, &S));
+          uhat_finish_kernel<<<vec_blocks, 256, 0, side[0]>>>(L, m.work, m.ubar, m.gbar, colsq, S, m.d, blk,
+                                                              ctx->d_counter, m.ctl, m.scal, h_restart,
+                                                              ctx->d_status);
+          CP_LAUNCH_CHECK();
+          ws_free(ctx, blk);
+          ws_free(ctx, colsq);
+          return CP_OK;
+        }));
         CP_TRY(add_conditional(side[0], side[1], h_restart, cudaGraphCondTypeIf, 2, [&](int br) -> cp_status {
           return with_stream(side[1], [&]() -> cp_status {
             if (br == 0) {
-              // restart: u = ubar, window <- {(ubar, g(ubar))}
-              return counted(&kcount.restart, [&]() -> cp_status {
-                CP_TRY(dcopy(ctx, P, m.ubar, m.u));
-                CP_TRY(dcopy(ctx, P, m.gbar, m.g));
-                CP_TRY(dcopy_multi(ctx, ubar_state));
-                return window_update(ctx, m.win, cap, true, P, m.u, m.g, m.U, m.G);
-              });
+              // restart: u = ubar (the tail resets the window to {(ubar, g(ubar))})
+              return counted(&kcount.restart, [&]() -> cp_status { return dcopy_multi(ctx, ubar_state); });
             }
             // Step III: More-Thuente on the polynomial phi(beta) (one MTTKRP
             // pass), which also sets `accept`
@@ -422,23 +568,16 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
                                       nullptr, m.grams, m.M0x, m.Mv, &m.st->stp_eval, nullptr, m.Xi0x));
                     CP_TRY(normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr, m.grams, m.M0x, m.M0, m.Gu,
                                           m.Xi0x, m.Xi0));
-                    CP_TRY(dcopy(ctx, 1, m.scal + FX, m.scal + F));
-                  } else {
-                    CP_TRY(dcopy(ctx, P, m.ubar, m.u));
-                    CP_TRY(dcopy(ctx, P, m.gbar, m.g));
-                    CP_TRY(dcopy_multi(ctx, ubar_state));
+                    return dcopy(ctx, 1, m.scal + FX, m.scal + F);
                   }
-                  return window_update(ctx, m.win, cap, false, P, m.u, m.g, m.U, m.G);
+                  return dcopy_multi(ctx, ubar_state);
                 });
               });
             });
           });
         }));
-        CP_TRY(counted(&kcount.head, [&]() { return dot(ctx, P, m.g, m.g, m.scal + GG); }));
-        ctl_tail_kernel<<<1, 1, 0, side[0]>>>(m.ctl, m.scal, Pd, tol, maxit, mixed ? 1 : 0, stall, h_outer);
-        CP_LAUNCH_CHECK();
-        kcount.head += 1;
-        return CP_OK;
+        // window push (or reset after a restart), ||g||^2, stopping test
+        return counted(&kcount.head, [&]() { return tail(side[0], h_outer, 0); });
       });
     }));
     CP_CUDA(cudaMemcpyAsync(hctl, m.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s0));

@@ -15,6 +15,7 @@ struct SolveCtl {
   int mixed_iters, fp64_iters;
   int ls_evals, accepts;
   int stop;          // 0 running, 1 tol met, 2 maxit, 3 mixed phase stalled, 4 non-finite
+  int restart_now;   // this iteration restarted (the tail resets the window)
   int since_best;
   double gn, best, f;
 };
