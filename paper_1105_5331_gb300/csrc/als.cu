@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "cp_internal.cuh"
+#include "reduce.cuh"
 
 namespace cpg {
 
@@ -294,19 +295,9 @@ __global__ void __launch_bounds__(256) als_update_kernel(const UpdParams p) {
     const int64_t e = rb * R + e0 + lane;
     const bool in = e0 + lane < nout;
     if (p.parts.f32) {
-      const float* q = (const float*)p.parts.p;
-      float s = 0.f;
-      if (in)
-#pragma unroll 4
-        for (int c = w; c < p.parts.count; c += 8) s += __ldcg(&q[(int64_t)c * nel + e]);
-      redf[w][lane] = s;
+      redf[w][lane] = in ? strided_sum((const float*)p.parts.p + e, w, p.parts.count, 8, nel) : 0.f;
     } else {
-      const double* q = (const double*)p.parts.p;
-      double s = 0.0;
-      if (in)
-#pragma unroll 4
-        for (int c = w; c < p.parts.count; c += 8) s += __ldcg(&q[(int64_t)c * nel + e]);
-      redd[w][lane] = s;
+      redd[w][lane] = in ? strided_sum((const double*)p.parts.p + e, w, p.parts.count, 8, nel) : 0.0;
     }
     __syncthreads();
     if (w == 0 && in) {

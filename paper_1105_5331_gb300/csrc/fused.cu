@@ -14,6 +14,7 @@
 #include <algorithm>
 
 #include "cp_internal.cuh"
+#include "reduce.cuh"
 
 namespace cpg {
 
@@ -106,15 +107,9 @@ __global__ void __launch_bounds__(256) fg_finish_kernel(const FinishParams p) {
   if (e < nel) {
     if (pt.f32) {
       // FP32 partial sums of the mixed MTTKRP are added in FP32
-      const float* q = (const float*)pt.p;
-      float sf = 0.f;
-#pragma unroll 4
-      for (int c = w; c < pt.count; c += 8) sf += __ldcg(&q[(int64_t)c * nel + e]);
-      s = (double)sf;
+      s = (double)strided_sum((const float*)pt.p + e, w, pt.count, 8, nel);
     } else {
-      const double* q = (const double*)pt.p;
-#pragma unroll 4
-      for (int c = w; c < pt.count; c += 8) s += __ldcg(&q[(int64_t)c * nel + e]);
+      s = strided_sum((const double*)pt.p + e, w, pt.count, 8, nel);
     }
   }
   sh[w][lane] = s;

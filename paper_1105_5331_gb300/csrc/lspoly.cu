@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "cp_internal.cuh"
+#include "reduce.cuh"
 #include "linesearch.cuh"
 #include "mt_device.cuh"
 #include "solver.cuh"
@@ -164,19 +165,9 @@ __global__ void __launch_bounds__(256) ls_coef_kernel(const CoefParams p) {
   const int64_t idx = i * p.col_stride + p.col_off[v] + r;
   // M_v[i][r]: warp w adds partials c = w, w + 8, ...; warp 0 the warp sums
   if (p.f32) {
-    const float* q = (const float*)p.pp[v];
-    float s = 0.f;
-    if (in)
-#pragma unroll 4
-      for (int c = w; c < p.count[v]; c += 8) s += __ldcg(&q[(int64_t)c * nel + idx]);
-    redf[w][lane] = s;
+    redf[w][lane] = in ? strided_sum((const float*)p.pp[v] + idx, w, p.count[v], 8, nel) : 0.f;
   } else {
-    const double* q = (const double*)p.pp[v];
-    double s = 0.0;
-    if (in)
-#pragma unroll 4
-      for (int c = w; c < p.count[v]; c += 8) s += __ldcg(&q[(int64_t)c * nel + idx]);
-    redd[w][lane] = s;
+    redd[w][lane] = in ? strided_sum((const double*)p.pp[v] + idx, w, p.count[v], 8, nel) : 0.0;
   }
   __syncthreads();
   if (w == 0) {

@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "cp_internal.cuh"
+#include "reduce.cuh"
 
 namespace cpg {
 
@@ -119,10 +120,7 @@ __global__ void __launch_bounds__(256) ngmres_reduce_solve_kernel(const double* 
   const int npairs = m * (m + 1) / 2;
   const int nout = npairs + m;
   const int o = blockIdx.x * 32 + lane;
-  double s = 0.0;
-  if (o < nout)
-    for (int c = w; c < nparts; c += 8) s += __ldcg(&part[(int64_t)c * nout_max + o]);
-  red[w][lane] = s;
+  red[w][lane] = o < nout ? strided_sum(part + o, w, nparts, 8, (int64_t)nout_max) : 0.0;
   __syncthreads();
   if (w == 0 && o < nout) {
     double t = 0.0;

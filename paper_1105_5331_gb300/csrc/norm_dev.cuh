@@ -6,6 +6,7 @@
 #pragma once
 
 #include "cp_internal.cuh"
+#include "reduce.cuh"
 
 namespace cpg {
 
@@ -27,14 +28,7 @@ __device__ inline void norm_prologue(const Layout& L, const double* __restrict__
     if (grams) {
       s = grams[(int64_t)n * R * R + r * R + r];
     } else {
-      double s0 = 0.0, s1 = 0.0;
-      int c = 0;
-      for (; c + 1 < S; c += 2) {
-        s0 += part[((int64_t)n * S + c) * R + r];
-        s1 += part[((int64_t)n * S + c + 1) * R + r];
-      }
-      if (c < S) s0 += part[((int64_t)n * S + c) * R + r];
-      s = s0 + s1;
+      s = strided_sum(part + (int64_t)n * S * R + r, 0, S, 1, (int64_t)R);
     }
     sh.nu[t] = sqrt(s);
   }

@@ -43,3 +43,26 @@ inline cp_status reduce_parts(cp_ctx* ctx, const TP* partial, int nparts, int64_
 }
 
 }  // namespace cpg
+
+namespace cpg {
+
+// sum over c = c0, c0 + step, ... < count of q[c * stride], with four
+// independent accumulators so that up to 16 loads are in flight (the loads
+// are L2 hits; a single running sum would wait for each before issuing the
+// next).  Fixed order: ((a0 + a1) + (a2 + a3)).
+template <typename T>
+__device__ __forceinline__ T strided_sum(const T* __restrict__ q, int c0, int count, int step, int64_t stride) {
+  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+  int c = c0;
+#pragma unroll 4
+  for (; c + 3 * step < count; c += 4 * step) {
+    a0 += __ldcg(&q[(int64_t)c * stride]);
+    a1 += __ldcg(&q[(int64_t)(c + step) * stride]);
+    a2 += __ldcg(&q[(int64_t)(c + 2 * step) * stride]);
+    a3 += __ldcg(&q[(int64_t)(c + 3 * step) * stride]);
+  }
+  for (; c < count; c += step) a0 += __ldcg(&q[(int64_t)c * stride]);
+  return (a0 + a1) + (a2 + a3);
+}
+
+}  // namespace cpg
