@@ -61,6 +61,7 @@ __global__ void sub_kernel(int64_t n, const double* __restrict__ a, const double
 
 // Column sums of squares, partial over row chunks: part[mode][S][R].
 __global__ void colsq_partial_kernel(FactorPtrs F, int S, double* __restrict__ part) {
+  CP_PDL_ENTRY();
   const int m = blockIdx.y;
   const int R = F.R;
   const int64_t I = F.I[m];
@@ -103,6 +104,7 @@ __global__ void __launch_bounds__(256) norm_apply_kernel(Layout L, const double*
                                                          double* __restrict__ grams_out,
                                                          const double* __restrict__ xi_src,
                                                          double* __restrict__ xi_dst) {
+  CP_PDL_ENTRY();
   __shared__ NormShared sh;
   norm_prologue(L, part, S, grams, lambda_out, status, sh);
   const double* scale = sh.scale;
@@ -204,10 +206,10 @@ cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double
     S = chunks_for(ctx, Imax);
     CP_TRY(ws_alloc(ctx, (void**)&part, sizeof(double) * (size_t)L.N * S * R));
     const int threads = std::max(32, (256 / R) * R);
-    colsq_partial_kernel<<<dim3(S, L.N), threads, 0, ctx->stream>>>(F, S, part);
+    (void)launch_pdl(colsq_partial_kernel, dim3(dim3(S, L.N)), dim3(threads), 0, ctx->stream, F, S, part);
     CP_LAUNCH_CHECK();
   }
-  norm_apply_kernel<<<grid_for(ctx, L.P(), 256), 256, 0, ctx->stream>>>(L, src, dst, gsrc, gdst, part, S, grams,
+  (void)launch_pdl(norm_apply_kernel, dim3(grid_for(ctx, L.P(), 256)), dim3(256), 0, ctx->stream, L, src, dst, gsrc, gdst, part, S, grams,
                                                                         lambda, ctx->d_status, m0_src, m0_dst,
                                                                         grams ? grams_out : nullptr, xi_src, xi_dst);
   CP_LAUNCH_CHECK();

@@ -70,6 +70,7 @@ __device__ __forceinline__ void job_entry(const GramParams& p, int64_t item, int
 }
 
 __global__ void __launch_bounds__(256) gram_kernel(const GramParams p) {
+  CP_PDL_ENTRY();
   __shared__ bool is_last;
   const int lane = threadIdx.x & 31;
   const int64_t item = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -213,6 +214,7 @@ __device__ bool gj_inverse2(double* A, double* B, int R, double** out, double* p
 
 // Dynamic shared memory: two R x R FP64 buffers.
 __global__ void __launch_bounds__(256) gram_inverse_kernel(const InvParams p) {
+  CP_PDL_ENTRY();
   extern __shared__ double dsm[];
   const int R = p.R, RR = R * R;
   double* A = dsm;
@@ -277,6 +279,7 @@ struct UpdParams {
 };
 
 __global__ void __launch_bounds__(256) als_update_kernel(const UpdParams p) {
+  CP_PDL_ENTRY();
   __shared__ double X[CP_MAX_R * CP_MAX_R];
   __shared__ double Mt[2 * CP_MAX_R];
   __shared__ float redf[8][33];
@@ -336,6 +339,7 @@ __global__ void __launch_bounds__(256) als_update_kernel(const UpdParams p) {
 // Padded FP32 copy: every float of the layout is written (padding as 0).
 __global__ void f32_copy_kernel(Layout L, const double* __restrict__ u, F32Off o, int64_t total,
                                 float* __restrict__ out) {
+  CP_PDL_ENTRY();
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     int n = 0;
     while (n + 1 < L.N && q >= o.off[n + 1]) ++n;
@@ -351,14 +355,14 @@ __global__ void f32_copy_kernel(Layout L, const double* __restrict__ u, F32Off o
 cp_status gram_inverse_launch(cp_ctx* ctx, cudaStream_t s, const double* grams, const Layout& L, int n, double* xi) {
   CP_TRY(inverse_smem_attr());
   InvParams ip{grams, L.N, L.R, n, xi, (int*)(xi + (size_t)L.R * L.R), ctx->d_status};
-  gram_inverse_kernel<<<1, 256, inverse_smem(L.R), s>>>(ip);
+  (void)launch_pdl(gram_inverse_kernel, dim3(1), dim3(256), inverse_smem(L.R), s, ip);
   CP_LAUNCH_CHECK();
   return CP_OK;
 }
 
 cp_status f32_copy(cp_ctx* ctx, const Layout& L, const double* u, const F32Off& o, int64_t total, float* out) {
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4 * ctx->num_sms));
-  f32_copy_kernel<<<blocks, 256, 0, ctx->stream>>>(L, u, o, total, out);
+  (void)launch_pdl(f32_copy_kernel, dim3(blocks), dim3(256), 0, ctx->stream, L, u, o, total, out);
   CP_LAUNCH_CHECK();
   return CP_OK;
 }
@@ -387,7 +391,7 @@ cp_status grams_jobs(cp_ctx* ctx, cudaStream_t s, unsigned* counter, int R, cons
     CP_TRY(ws_alloc_on(ctx, s, (void**)&p.partial, sizeof(double) * (size_t)items));
   }
   const unsigned blocks = (unsigned)std::max<int64_t>(1, (items + 7) / 8);
-  gram_kernel<<<blocks, 256, 0, s>>>(p);
+  (void)launch_pdl(gram_kernel, dim3(blocks), dim3(256), 0, s, p);
   CP_LAUNCH_CHECK();
   if (p.partial) ws_free_on(ctx, s, p.partial);
   return CP_OK;
@@ -433,7 +437,7 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
       CP_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
       if (n > 0) CP_TRY(grams_of(ctx, ctx->aux, ctx->d_counter + 1, L, u, n - 1, 1, grams));
       InvParams ip{grams, N, R, n, Xinv, ok, ctx->d_status};
-      gram_inverse_kernel<<<1, 256, inverse_smem(R), ctx->aux>>>(ip);
+      (void)launch_pdl(gram_inverse_kernel, dim3(1), dim3(256), inverse_smem(R), ctx->aux, ip);
       CP_LAUNCH_CHECK();
       CP_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
     }
@@ -453,7 +457,7 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
     up.An = u + L.off[n];
     up.An32 = u32 ? u32 + o32.off[n] : nullptr;
     up.rs = o32.rs;
-    als_update_kernel<<<(unsigned)((L.dims[n] + rows - 1) / rows), 256, 0, ctx->stream>>>(up);
+    (void)launch_pdl(als_update_kernel, dim3((unsigned)((L.dims[n] + rows - 1) / rows)), dim3(256), 0, ctx->stream, up);
     CP_LAUNCH_CHECK();
     if (!(n == 0 && m0)) ws_free(ctx, const_cast<void*>(pt.p));
   }

@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 
+#include <cstdlib>
+
 #include "cp_internal.cuh"
 #include "linesearch.cuh"
 
@@ -12,6 +14,10 @@ namespace cpg {
 
 static thread_local char g_err[1024] = "";
 std::atomic<unsigned long long> g_launches{0};
+bool g_pdl = [] {
+  const char* e = getenv("CP_PDL");
+  return !(e && e[0] == '0');
+}();
 
 void set_error(const char* fmt, ...) {
   va_list ap;

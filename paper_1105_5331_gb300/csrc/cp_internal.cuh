@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <utility>
 #include <cuda_bf16.h>
 
 #include <atomic>
@@ -339,6 +340,38 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const dou
 
 // Padded FP32 copy (f32_layout) of the packed FP64 iterate u, on ctx->stream.
 cp_status f32_copy(cp_ctx* ctx, const Layout& L, const double* u, const F32Off& o, int64_t total, float* out);
+
+// Programmatic dependent launch.  Kernels of the solve start with
+// CP_PDL_ENTRY(): wait until the kernel before them in the stream has
+// completed and its writes are visible (a no-op when they were launched
+// without the attribute), then let the next kernel of the stream begin to
+// launch, so that its launch and block scheduling overlap this kernel's run.
+// Nothing before the wait touches global memory.
+#define CP_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+#define CP_PDL_TRIGGER() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
+#define CP_PDL_ENTRY() \
+  do {                 \
+    CP_PDL_WAIT();     \
+    CP_PDL_TRIGGER();  \
+  } while (0)
+
+extern bool g_pdl;   // launch with the programmatic attribute (CP_PDL=0 turns it off)
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = g_pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // Workspace (stream-ordered on ctx->stream, or on s for the _on forms).
 cp_status ws_alloc(cp_ctx* ctx, void** p, size_t bytes);

@@ -234,18 +234,25 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      // the factor tables of the other modes: one bulk copy each, overlapped
-      // with the first tile loads
-      if (p.tab_smem) {
-        mbar_arrive_tx(tab_bar, p.tab_bytes);
+      // The first `stages` tiles of T (static data) are requested before the
+      // wait for the preceding kernel; the factor tables (written by it) after.
+      bool waited = false;
+      auto after_wait = [&]() {
+        CP_PDL_WAIT();
+        CP_PDL_TRIGGER();
+        if (p.tab_smem) {
+          mbar_arrive_tx(tab_bar, p.tab_bytes);
 #pragma unroll
-        for (int j = 0; j < NO; ++j) {
-          bulk_load(tab_saddr + 4u * p.tab_soff[j], p.tab[j], p.tab_cpy[j], tab_bar);
-          if (p.nvar > 1) bulk_load(tab_saddr + 4u * p.tabd_soff[j], p.tabd[j], p.tab_cpy[j], tab_bar);
+          for (int j = 0; j < NO; ++j) {
+            bulk_load(tab_saddr + 4u * p.tab_soff[j], p.tab[j], p.tab_cpy[j], tab_bar);
+            if (p.nvar > 1) bulk_load(tab_saddr + 4u * p.tabd_soff[j], p.tabd[j], p.tab_cpy[j], tab_bar);
+          }
         }
-      }
+        waited = true;
+      };
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
+        if (i == S) after_wait();
         const int s = i % S;
         const uint32_t ph = (uint32_t)((i / S) & 1);
         if (!mbar_wait(empty_bar(s), ph ^ 1u, p.status)) break;
@@ -267,6 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ++issued;
       }
+      if (!waited) after_wait();
       // let copies still in flight land before the CTA can exit
       for (int i = max(0, issued - S); i < issued; ++i)
         mbar_wait(full_bar(i % S), (uint32_t)((i / S) & 1), p.status);
@@ -302,6 +310,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------- Khatri-Rao tile builders
+    CP_PDL_WAIT();      // the tables may be read from global memory; the epilogue writes it
+    CP_PDL_TRIGGER();
     const int t = threadIdx.x - 64;            // 0..127
     const int kk = t & (kBK - 1);              // contraction element within the tile
     const int half = t >> 6;                   // which half of the column groups
@@ -647,7 +657,7 @@ static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, co
   CP_TRY(set_smem_attr());
   {
     TimerScope ts(ctx, 0);
-    tc_kernel_for(p.nother)<<<dim3(gx, mgroups), kThreads, smem, ctx->stream>>>(p);
+    (void)launch_pdl(tc_kernel_for(p.nother), dim3(gx, mgroups), dim3(kThreads), smem, ctx->stream, p);
   }
   CP_LAUNCH_CHECK();
   *parts = Parts{partial, gx, 1};

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(256) xprep_kernel(Layout L, const double* __re
                                                     const double* __restrict__ d, const double* __restrict__ stp,
                                                     double* __restrict__ x, float* __restrict__ x32, F32Off o,
                                                     int64_t total) {
+  CP_PDL_ENTRY();
   const double a = d ? *stp : 0.0;
   const int R = L.R;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
@@ -85,6 +86,7 @@ struct FinishParams {
 };
 
 __global__ void __launch_bounds__(256) fg_finish_kernel(const FinishParams p) {
+  CP_PDL_ENTRY();
   __shared__ double Gb[CP_MAX_R * CP_MAX_R];
   __shared__ double sh[8][33];
   __shared__ double tr[2][256];
@@ -243,7 +245,7 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
     const int64_t total = x32 ? acc32 : L.P();
     const F32Off o = x32 ? o32 : [&]() { F32Off q{}; q.rs = R; for (int n = 0; n < N; ++n) q.off[n] = L.off[n]; return q; }();
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4 * ctx->num_sms));
-    xprep_kernel<<<blocks, 256, 0, ctx->stream>>>(L, base, d, stp, x, x32, o, total);
+    (void)launch_pdl(xprep_kernel, dim3(blocks), dim3(256), 0, ctx->stream, L, base, d, stp, x, x32, o, total);
     CP_LAUNCH_CHECK();
   }
   // MTTKRPs (all modes for g; the last one alone for f)
@@ -274,7 +276,7 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   fp.status = ctx->d_status;
   CP_TRY(ws_alloc(ctx, (void**)&fp.blk, sizeof(double) * 2 * (size_t)chunks + 16));
   CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-  fg_finish_kernel<<<(unsigned)chunks, 256, 0, ctx->stream>>>(fp);
+  (void)launch_pdl(fg_finish_kernel, dim3((unsigned)chunks), dim3(256), 0, ctx->stream, fp);
   CP_LAUNCH_CHECK();
   ws_free(ctx, fp.blk);
   for (int n = first; n < last_pass; ++n) ws_free(ctx, const_cast<void*>(fp.parts[n].p));

@@ -97,6 +97,7 @@ __device__ void mt_init(MTState& s, double f0, double g0, const cp_ls_opts& o) {
 __global__ void __launch_bounds__(256) ls_epoly_kernel(const double* __restrict__ grams, int N, int R,
                                                        double* __restrict__ blk, double* __restrict__ e_out,
                                                        unsigned* counter) {
+  CP_PDL_ENTRY();
   __shared__ double epart[8][kMaxDeg + 1];
   __shared__ bool is_last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(256) ls_epoly_kernel(const double* __restrict_
 }
 
 __global__ void __launch_bounds__(256) ls_coef_kernel(const CoefParams p) {
+  CP_PDL_ENTRY();
   __shared__ float redf[8][33];
   __shared__ double redd[8][33];
   __shared__ double sums[2 * kMaxVar];
@@ -255,6 +257,7 @@ __global__ void __launch_bounds__(256) ls_coef_kernel(const CoefParams p) {
 // set, else a's; the last factor is a's.
 __global__ void mix_kernel(Layout L, const double* __restrict__ a, const double* __restrict__ d, int nvar,
                            double* __restrict__ w) {
+  CP_PDL_ENTRY();
   const int64_t P = L.off[L.N];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
     int n = 0;
@@ -301,7 +304,7 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
     }
     CP_TRY(grams_jobs(ctx, ctx->aux, ctx->d_counter + 1, R, jobs, nj));
     const unsigned eb = (unsigned)((RR + 255) / 256);
-    ls_epoly_kernel<<<eb, 256, 0, ctx->aux>>>(grams, N, R, eblk, epoly, ctx->d_counter + 1);
+    (void)launch_pdl(ls_epoly_kernel, dim3(eb), dim3(256), 0, ctx->aux, grams, N, R, eblk, epoly, ctx->d_counter + 1);
     CP_LAUNCH_CHECK();
   }
   CP_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
@@ -326,7 +329,7 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
   } else {
     CP_TRY(ws_alloc(ctx, (void**)&wv, sizeof(double) * (size_t)nvar * P));
     if (tc) CP_TRY(ws_alloc(ctx, (void**)&w32, sizeof(float) * (size_t)nvar * acc32 + 64));
-    mix_kernel<<<eblocks, 256, 0, ctx->stream>>>(L, base, d, nvar, wv);
+    (void)launch_pdl(mix_kernel, dim3(eblocks), dim3(256), 0, ctx->stream, L, base, d, nvar, wv);
     CP_LAUNCH_CHECK();
     if (w32)
       for (int v = 0; v < nvar; ++v) CP_TRY(f32_copy(ctx, L, wv + (size_t)v * P, o32, acc32, w32 + (size_t)v * acc32));
@@ -363,7 +366,7 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
   const int64_t nblocks = (int64_t)nvar * cp.chunks;
   CP_TRY(ws_alloc(ctx, (void**)&cp.blk, sizeof(double) * 2 * (size_t)nblocks + 16));
   CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-  ls_coef_kernel<<<(unsigned)nblocks, 256, 0, ctx->stream>>>(cp);
+  (void)launch_pdl(ls_coef_kernel, dim3((unsigned)nblocks), dim3(256), 0, ctx->stream, cp);
   CP_LAUNCH_CHECK();
   ws_free(ctx, cp.blk);
   if (tc_var) {

@@ -38,6 +38,7 @@ __device__ __forceinline__ void pair_of(int o, int m, int* j, int* l) {
 __global__ void ngmres_dots_kernel(const double* __restrict__ G, const int* __restrict__ win, int cap,
                                    int64_t P, const double* __restrict__ gbar, int64_t chunk,
                                    int nout_max, double* __restrict__ part) {
+  CP_PDL_ENTRY();
   __shared__ double pt[CP_MAX_W * (kTile + 1)];
   __shared__ double gt[kTile];
   const int start = win[0];
@@ -110,6 +111,7 @@ __global__ void __launch_bounds__(256) ngmres_reduce_solve_kernel(const double* 
                                                                   double eps, double* __restrict__ sums,
                                                                   double* __restrict__ alpha, unsigned* counter,
                                                                   int* status) {
+  CP_PDL_ENTRY();
   __shared__ double red[8][33];
   __shared__ double Ab[CP_MAX_W * (CP_MAX_W + 1)];
   __shared__ double dmax;
@@ -212,6 +214,7 @@ __global__ void ngmres_combine_kernel(const double* __restrict__ U, const int* _
                                       int64_t P, const double* __restrict__ ubar,
                                       const double* __restrict__ alpha, double* __restrict__ uhat, Layout L,
                                       int64_t chunk, double* __restrict__ colsq) {
+  CP_PDL_ENTRY();
   __shared__ double a[CP_MAX_W];
   __shared__ int slot[CP_MAX_W];
   __shared__ double red[CP_MAX_N * 256];     // [N][blockDim] per-thread sums
@@ -317,9 +320,9 @@ cp_status ngmres_core(cp_ctx* ctx, int64_t P, const int* win, int cap, const dou
   CP_TRY(ws_alloc(ctx, (void**)&part, sizeof(double) * ((size_t)nb * nout_max + nout_max + CP_MAX_W)));
   double* sums = part + (size_t)nb * nout_max;
   if (!a) a = sums + nout_max;
-  ngmres_dots_kernel<<<(unsigned)nb, 256, 0, ctx->stream>>>(G, win, cap, P, gbar, chunk, nout_max, part);
+  (void)launch_pdl(ngmres_dots_kernel, dim3((unsigned)nb), dim3(256), 0, ctx->stream, G, win, cap, P, gbar, chunk, nout_max, part);
   CP_LAUNCH_CHECK();
-  ngmres_reduce_solve_kernel<<<(unsigned)((nout_max + 31) / 32), 256, 0, ctx->stream>>>(
+  (void)launch_pdl(ngmres_reduce_solve_kernel, dim3((unsigned)((nout_max + 31) / 32)), dim3(256), 0, ctx->stream, 
       part, (int)nb, nout_max, win, eps, sums, a, ctx->d_counter, ctx->d_status);
   CP_LAUNCH_CHECK();
   if (L && colsq) {
@@ -330,7 +333,7 @@ cp_status ngmres_core(cp_ctx* ctx, int64_t P, const int* win, int cap, const dou
     const int64_t chunk = (per + threads - 1) / threads * threads;
     const int64_t cb = (P + chunk - 1) / chunk;
     *S_out = (int)cb;
-    ngmres_combine_kernel<<<(unsigned)cb, threads, 0, ctx->stream>>>(U, win, cap, P, ubar, a, uhat, *L, chunk,
+    (void)launch_pdl(ngmres_combine_kernel, dim3((unsigned)cb), dim3(threads), 0, ctx->stream, U, win, cap, P, ubar, a, uhat, *L, chunk,
                                                                      colsq);
   } else {
     Layout L1;
@@ -341,7 +344,7 @@ cp_status ngmres_core(cp_ctx* ctx, int64_t P, const int* win, int cap, const dou
     int64_t cb = std::min<int64_t>((P + 255) / 256, 8 * (int64_t)ctx->num_sms);
     cb = std::max<int64_t>(cb, 1);
     const int64_t chunk = (P + cb - 1) / cb;
-    ngmres_combine_kernel<<<(unsigned)cb, 256, 0, ctx->stream>>>(U, win, cap, P, ubar, a, uhat, L1, chunk, nullptr);
+    (void)launch_pdl(ngmres_combine_kernel, dim3((unsigned)cb), dim3(256), 0, ctx->stream, U, win, cap, P, ubar, a, uhat, L1, chunk, nullptr);
   }
   CP_LAUNCH_CHECK();
   ws_free(ctx, part);

@@ -44,6 +44,7 @@ enum { F = 0, FBAR = 1, FX = 2, SLOPE = 3, GD = 4, GG = 5, NSCAL = 8 };
 enum { STOP_RUN = 0, STOP_TOL = 1, STOP_MAXIT = 2, STOP_STALL = 3, STOP_NONFINITE = 4 };
 
 __global__ void copy_kernel(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  CP_PDL_ENTRY();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
     b[k] = a[k];
 }
@@ -108,6 +109,7 @@ struct CopySeg {
 };
 
 __global__ void copy_multi_kernel(const CopySeg c) {
+  CP_PDL_ENTRY();
   for (int s = 0; s < c.nseg; ++s)
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < c.n[s]; k += (int64_t)gridDim.x * blockDim.x)
       c.dst[s][k] = c.src[s][k];
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(256) uhat_finish_kernel(Layout L, const double
                                                           double* __restrict__ d, double* blk, unsigned* counter,
                                                           SolveCtl* c, double* scal, cudaGraphConditionalHandle restart,
                                                           int* status) {
+  CP_PDL_ENTRY();
   __shared__ NormShared sh;
   __shared__ double red8[8];
   __shared__ bool is_last;
@@ -199,6 +202,7 @@ __global__ void __launch_bounds__(256) tail_kernel(const double* __restrict__ u,
                                                    int maxit, int mixed, int stall,
                                                    cudaGraphConditionalHandle outer, double* blk, unsigned* counter,
                                                    int begin) {
+  CP_PDL_ENTRY();
   __shared__ double red8[8];
   __shared__ bool is_last;
   const int reset = begin ? 1 : c->restart_now;
@@ -252,13 +256,13 @@ int64_t grid_for(cp_ctx* ctx, int64_t n) {
 cp_status dcopy_multi(cp_ctx* ctx, const CopySeg& c) {
   int64_t nmax = 1;
   for (int s = 0; s < c.nseg; ++s) nmax = std::max(nmax, c.n[s]);
-  copy_multi_kernel<<<(unsigned)grid_for(ctx, nmax), 256, 0, ctx->stream>>>(c);
+  (void)launch_pdl(copy_multi_kernel, dim3((unsigned)grid_for(ctx, nmax)), dim3(256), 0, ctx->stream, c);
   CP_LAUNCH_CHECK();
   return CP_OK;
 }
 
 cp_status dcopy(cp_ctx* ctx, int64_t n, const double* a, double* b) {
-  copy_kernel<<<(unsigned)grid_for(ctx, n), 256, 0, ctx->stream>>>(n, a, b);
+  (void)launch_pdl(copy_kernel, dim3((unsigned)grid_for(ctx, n)), dim3(256), 0, ctx->stream, n, a, b);
   CP_LAUNCH_CHECK();
   return CP_OK;
 }
@@ -501,7 +505,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
   auto tail = [&](cudaStream_t st, cudaGraphConditionalHandle h, int begin) -> cp_status {
     double* blk = nullptr;
     CP_TRY(ws_alloc(ctx, (void**)&blk, sizeof(double) * vec_blocks));
-    tail_kernel<<<vec_blocks, 256, 0, st>>>(m.u, m.g, m.U, m.G, m.win, cap, P, m.ctl, m.scal, Pd, tol, maxit,
+    (void)launch_pdl(tail_kernel, dim3(vec_blocks), dim3(256), 0, st, m.u, m.g, m.U, m.G, m.win, cap, P, m.ctl, m.scal, Pd, tol, maxit,
                                             mixed ? 1 : 0, stall, h, blk, ctx->d_counter, begin);
     CP_LAUNCH_CHECK();
     ws_free(ctx, blk);
@@ -537,7 +541,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
           CP_TRY(ws_alloc(ctx, (void**)&colsq, sizeof(double) * (size_t)L.N * (2 * sub.num_sms + 2) * L.R));
           CP_TRY(ws_alloc(ctx, (void**)&blk, sizeof(double) * vec_blocks));
           CP_TRY(ngmres_core(ctx, P, m.win, cap, m.U, m.G, m.ubar, m.gbar, o.eps, m.work, nullptr, &L, colsq, &S));
-          uhat_finish_kernel<<<vec_blocks, 256, 0, side[0]>>>(L, m.work, m.ubar, m.gbar, colsq, S, m.d, blk,
+          (void)launch_pdl(uhat_finish_kernel, dim3(vec_blocks), dim3(256), 0, side[0], L, m.work, m.ubar, m.gbar, colsq, S, m.d, blk,
                                                               ctx->d_counter, m.ctl, m.scal, h_restart,
                                                               ctx->d_status);
           CP_LAUNCH_CHECK();
