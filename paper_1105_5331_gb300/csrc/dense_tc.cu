@@ -234,25 +234,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      // The first `stages` tiles of T (static data) are requested before the
-      // wait for the preceding kernel; the factor tables (written by it) after.
-      bool waited = false;
-      auto after_wait = [&]() {
-        CP_PDL_WAIT();
-        CP_PDL_TRIGGER();
-        if (p.tab_smem) {
-          mbar_arrive_tx(tab_bar, p.tab_bytes);
+      // the factor tables (written by the preceding kernel) first, then the
+      // tiles of T, so that the builders can start on the first stage at once
+      CP_PDL_WAIT();
+      CP_PDL_TRIGGER();
+      if (p.tab_smem) {
+        mbar_arrive_tx(tab_bar, p.tab_bytes);
 #pragma unroll
-          for (int j = 0; j < NO; ++j) {
-            bulk_load(tab_saddr + 4u * p.tab_soff[j], p.tab[j], p.tab_cpy[j], tab_bar);
-            if (p.nvar > 1) bulk_load(tab_saddr + 4u * p.tabd_soff[j], p.tabd[j], p.tab_cpy[j], tab_bar);
-          }
+        for (int j = 0; j < NO; ++j) {
+          bulk_load(tab_saddr + 4u * p.tab_soff[j], p.tab[j], p.tab_cpy[j], tab_bar);
+          if (p.nvar > 1) bulk_load(tab_saddr + 4u * p.tabd_soff[j], p.tabd[j], p.tab_cpy[j], tab_bar);
         }
-        waited = true;
-      };
+      }
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
-        if (i == S) after_wait();
         const int s = i % S;
         const uint32_t ph = (uint32_t)((i / S) & 1);
         if (!mbar_wait(empty_bar(s), ph ^ 1u, p.status)) break;
@@ -274,7 +269,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ++issued;
       }
-      if (!waited) after_wait();
       // let copies still in flight land before the CTA can exit
       for (int i = max(0, issued - S); i < issued; ++i)
         mbar_wait(full_bar(i % S), (uint32_t)((i / S) & 1), p.status);
