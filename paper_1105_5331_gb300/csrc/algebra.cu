@@ -103,7 +103,9 @@ __global__ void __launch_bounds__(256) norm_apply_kernel(Layout L, const double*
                                                          double* __restrict__ m0_dst,
                                                          double* __restrict__ grams_out,
                                                          const double* __restrict__ xi_src,
-                                                         double* __restrict__ xi_dst) {
+                                                         double* __restrict__ xi_dst,
+                                                         const double* __restrict__ ml_src,
+                                                         double* __restrict__ ml_dst) {
   CP_PDL_ENTRY();
   __shared__ NormShared sh;
   norm_prologue(L, part, S, grams, lambda_out, status, sh);
@@ -135,6 +137,18 @@ __global__ void __launch_bounds__(256) norm_apply_kernel(Layout L, const double*
       double sc = 1.0;
       for (int n = 1; n < N; ++n) sc *= scale[n * R + q];
       m0_dst[e] = m0_src[i * R + q] * sc;
+    }
+  }
+  if (ml_dst) {
+    // M^(N) likewise, with the scales of modes 1..N-1
+    const int64_t nl = L.dims[N - 1] * R;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nl; e += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = e / R;
+      const int pcol = (int)(e - i * R);
+      const int q = order[pcol];
+      double sc = 1.0;
+      for (int n = 0; n + 1 < N; ++n) sc *= scale[n * R + q];
+      ml_dst[e] = ml_src[i * R + q] * sc;
     }
   }
   if (blockIdx.x == 0 && grams_out) {
@@ -195,7 +209,7 @@ cp_status dot(cp_ctx* ctx, int64_t n, const double* x, const double* y, double* 
 cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double* dst,
                          const double* gsrc, double* gdst, double* lambda, const double* grams,
                          const double* m0_src, double* m0_dst, double* grams_out, const double* xi_src,
-                         double* xi_dst) {
+                         double* xi_dst, const double* ml_src, double* ml_dst) {
   const int R = L.R;
   double* part = nullptr;
   int S = 1;
@@ -211,7 +225,8 @@ cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double
   }
   (void)launch_pdl(norm_apply_kernel, dim3(grid_for(ctx, L.P(), 256)), dim3(256), 0, ctx->stream, L, src, dst, gsrc, gdst, part, S, grams,
                                                                         lambda, ctx->d_status, m0_src, m0_dst,
-                                                                        grams ? grams_out : nullptr, xi_src, xi_dst);
+                                                                        grams ? grams_out : nullptr, xi_src, xi_dst,
+                                                                        ml_src, ml_dst);
   CP_LAUNCH_CHECK();
   if (part) ws_free(ctx, part);
   return CP_OK;

@@ -276,6 +276,7 @@ struct UpdParams {
   double* An;            // I x R, updated in place
   float* An32;           // nullable: padded FP32 rows (stride rs)
   int rs;
+  double* Mout;          // nullable: the summed M^(n) rows (I x R)
 };
 
 __global__ void __launch_bounds__(256) als_update_kernel(const UpdParams p) {
@@ -290,8 +291,10 @@ __global__ void __launch_bounds__(256) als_update_kernel(const UpdParams p) {
   const int nr = (int)min((int64_t)p.rows, p.I - rb);
   const int nout = nr * R;
   const int64_t nel = p.I * R;
-  if (!*p.ok) return;
-  for (int k = threadIdx.x; k < RR; k += blockDim.x) X[k] = p.Xinv[k];
+  const bool ok = *p.ok != 0;
+  if (!ok && !p.Mout) return;
+  if (ok)
+    for (int k = threadIdx.x; k < RR; k += blockDim.x) X[k] = p.Xinv[k];
   // M rows of this block: warp w adds partials c = w, w + 8, ... for 32
   // consecutive outputs; warp 0 adds the eight warp sums in order
   for (int e0 = 0; e0 < nout; e0 += 32) {
@@ -318,6 +321,11 @@ __global__ void __launch_bounds__(256) als_update_kernel(const UpdParams p) {
     }
     __syncthreads();
   }
+  // M^(n) depends on the other modes only, so it is kept even when the
+  // update itself is skipped (no inverse)
+  if (p.Mout)
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) p.Mout[rb * R + o] = Mt[o];
+  if (!ok) return;
   // a_i = m_i Gammabar^-1: one output per thread, two partial chains
   for (int o = threadIdx.x; o < nout; o += blockDim.x) {
     const int q = o / R, r = o - (o / R) * R;
@@ -410,8 +418,10 @@ cp_status grams_of(cp_ctx* ctx, cudaStream_t s, unsigned* counter, const Layout&
 // One ALS sweep in place on u (Section 2.3): every mode n in turn takes
 // A_n = M^(n) Gammabar^(n)^-1.  grams (N x R x R) receives the Grams of the
 // updated factors; with grams_valid it already holds those of u on entry.
+// With mlast_out the last mode's M^(N) (from the updated modes 1..N-1) is
+// kept: it is M^(N) of the swept point as well.
 cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, double* u, cp_precision prec,
-                       double* grams, bool grams_valid, const double* m0, const double* xi0) {
+                       double* grams, bool grams_valid, const double* m0, const double* xi0, double* mlast_out) {
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int R = L.R, N = L.N, RR = R * R;
   const bool want_f32 = t->kind == 0 && prec == CP_MIXED_BF16X3;
@@ -457,6 +467,7 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
     up.An = u + L.off[n];
     up.An32 = u32 ? u32 + o32.off[n] : nullptr;
     up.rs = o32.rs;
+    up.Mout = n == N - 1 ? mlast_out : nullptr;
     (void)launch_pdl(als_update_kernel, dim3((unsigned)((L.dims[n] + rows - 1) / rows)), dim3(256), 0, ctx->stream, up);
     CP_LAUNCH_CHECK();
     if (!(n == 0 && m0)) ws_free(ctx, const_cast<void*>(pt.p));

@@ -257,11 +257,13 @@ cp_status mttkrp_any(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const dou
 // With m0_src the M^(1) of src follows the normalisation into m0_dst (its
 // columns reordered and scaled by the other modes' scales).
 // With grams_out the Grams of dst (from grams), with xi_src / xi_dst the
-// inverse of Gammabar^(1) (and its ok flag) follow the normalisation too.
+// inverse of Gammabar^(1) (and its ok flag) follow the normalisation too;
+// with ml_src / ml_dst the last mode's M^(N), like M^(1).
 cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double* dst,
                          const double* gsrc, double* gdst, double* lambda, const double* grams = nullptr,
                          const double* m0_src = nullptr, double* m0_dst = nullptr, double* grams_out = nullptr,
-                         const double* xi_src = nullptr, double* xi_dst = nullptr);
+                         const double* xi_src = nullptr, double* xi_dst = nullptr, const double* ml_src = nullptr,
+                         double* ml_dst = nullptr);
 
 // Window-indexed N-GMRES Step II.  win (device) = {start, m}; window row j
 // (oldest first) is ring slot (start + j) % cap.
@@ -319,24 +321,39 @@ cp_status grams_of(cp_ctx* ctx, cudaStream_t s, unsigned* counter, const Layout&
 // m0 (nullable): M^(1) of u, used for the first mode instead of an MTTKRP;
 // xi0 (nullable): the inverse of u's Gammabar^(1) and its ok flag (R*R
 // doubles, then an int), used instead of forming it.
+// mlast_out (nullable): receives the last mode's M^(N) (I_N x R), formed
+// from the updated modes 1..N-1 and so also M^(N) of the swept point.
 cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t, const Layout& L, double* u, cp_precision prec,
-                       double* grams, bool grams_valid, const double* m0 = nullptr, const double* xi0 = nullptr);
+                       double* grams, bool grams_valid, const double* m0 = nullptr, const double* xi0 = nullptr,
+                       double* mlast_out = nullptr);
 // Inverse of Gammabar^(n) from grams (N x R x R) on stream s into xi (R*R
 // doubles, then an int ok flag).
 cp_status gram_inverse_launch(cp_ctx* ctx, cudaStream_t s, const double* grams, const Layout& L, int n, double* xi);
+// M^(n) supplied to fg_eval_ex instead of MTTKRP passes, per mode
+// (nullable): M^(n) itself (nvar = 1), or the Khatri-Rao variants of a
+// line search, M^(n)(base + beta d) = sum_v beta^popc(v) m[n][v I_n R + .]
+// with beta = *beta (the model is multilinear in the factors).
+struct MGiven {
+  const double* m[CP_MAX_N] = {};
+  int nvar = 1;
+  const double* beta = nullptr;
+};
+
 // Fused f/g at x = base (+ (*stp) d when d is given; x written); with gd
 // (and d) also g . d.
 // grams_out: the Grams of the point (N x R x R); m0_out: its M^(1) (I_1 x R);
-// mv_last (with d): the last mode's M as sum_v beta^popc(v) mv_last[v] from the
-// line-search variants instead of an MTTKRP pass (beta = *mv_beta).
+// mg: modes whose M is supplied instead of an MTTKRP pass (MGiven).
+// grams_ls (with d): the Grams of base and d from a line search (ls_poly's
+// grams_out); the Grams of x = base + stp d follow from them without a pass
+// over the factors.
 // grams_in: the Grams of the point when already known (no Gram pass);
 // xi0_out: the inverse of its Gammabar^(1) with the ok flag (as
 // gram_inverse_launch), formed on the aux stream beside the MTTKRPs.
 cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* base,
                      const double* d, const double* stp, double* x, double* f, double* g,
                      cp_precision prec, double* gd, double* grams_out = nullptr, double* m0_out = nullptr,
-                     const double* mv_last = nullptr, const double* mv_beta = nullptr,
-                     const double* grams_in = nullptr, double* xi0_out = nullptr);
+                     const MGiven* mg = nullptr, const double* grams_in = nullptr, double* xi0_out = nullptr,
+                     const double* grams_ls = nullptr);
 
 // Padded FP32 copy (f32_layout) of the packed FP64 iterate u, on ctx->stream.
 cp_status f32_copy(cp_ctx* ctx, const Layout& L, const double* u, const F32Off& o, int64_t total, float* out);

@@ -47,31 +47,40 @@ constexpr int kMaxTilesPerCta = 1;       // M tiles handled by one CTA
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
 constexpr int kMaxDynSmem = 227 * 1024;
 
-struct TcParams {
+// One MTTKRP of a launch (a launch may run the MTTKRPs of several modes:
+// CTAs cta0 .. cta0 + gx * mgroups - 1 are this job's, gx contraction
+// slices per row group).
+struct TcJob {
   const uint8_t* tiles;       // pre-tiled hi / lo planes of T_(n)
   int64_t I;
   int64_t Kbar;
-  int R, RP;
-  int ntm;                    // M tiles per CTA (1 or 2)
-  int stages;
   int64_t ktiles;             // total contraction tiles
   int64_t ktiles_per_cta;
-  int nother;
-  // Khatri-Rao variants: 1, or 2^nother when the other modes' factors are
-  // each either A (bit clear) or D (bit set): column v R + r of the result
-  // is T_(n) times prod_j (bit j of v ? D_j : A_j)[:, r]
-  int nvar;
-  int outc;                          // nvar * R output columns
-  const float* tab[CP_MAX_N - 1];    // FP32 factors of the other modes, row stride R
+  int cta0, gx;
+  const float* tab[CP_MAX_N - 1];    // FP32 factors of the other modes, row stride rs
   const float* tabd[CP_MAX_N - 1];   // FP32 D factors (nvar > 1)
   int64_t dimo[CP_MAX_N - 1];
   uint32_t tab_soff[CP_MAX_N - 1];   // offsets (floats) of the tables in shared memory
   uint32_t tabd_soff[CP_MAX_N - 1];
   uint32_t tab_cpy[CP_MAX_N - 1];    // bytes copied per table (multiple of 16)
   uint32_t tab_bytes;                // sum of the copies
+  float* partial;                    // [gx][I][outc]
+};
+
+struct TcParams {
+  int njobs;
+  TcJob job[CP_MAX_N];
+  int R, RP;
+  int ntm;                    // M tiles per CTA
+  int stages;
+  int nother;
+  // Khatri-Rao variants: 1, or 2^nother when the other modes' factors are
+  // each either A (bit clear) or D (bit set): column v rs + r of the result
+  // is T_(n) times prod_j (bit j of v ? D_j : A_j)[:, r]
+  int nvar;
+  int outc;                          // output columns: R, or nvar * rs
   int tab_smem;                      // 1: builders read the tables from shared memory
   int rs;                            // table row stride in floats (R rounded up to 4)
-  float* partial;             // [gridDim.x][I][outc]
   int* status;
   uint32_t ncols;             // TMEM columns allocated
 };
@@ -186,7 +195,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 
 template <int NO>
 __global__ void __launch_bounds__(kThreads, 1)
-    mttkrp_tc_kernel(const TcParams p) {
+    mttkrp_tc_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -205,10 +214,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int64_t kt0 = (int64_t)blockIdx.x * p.ktiles_per_cta;
-  const int64_t kt1 = min(p.ktiles, kt0 + p.ktiles_per_cta);
+  // this CTA's job, contraction slice and row group
+  int jb = 0;
+  while (jb + 1 < p.njobs && (int)blockIdx.x >= p.job[jb + 1].cta0) ++jb;
+  const TcJob& J = p.job[jb];
+  const int local = (int)blockIdx.x - J.cta0;
+  const int kslice = local % J.gx;
+  const int64_t kt0 = (int64_t)kslice * J.ktiles_per_cta;
+  const int64_t kt1 = min(J.ktiles, kt0 + J.ktiles_per_cta);
   const int nk = (int)max((int64_t)0, kt1 - kt0);
-  const int64_t row0 = (int64_t)blockIdx.y * (kBM * kMaxTilesPerCta);
+  const int64_t row0 = (int64_t)(local / J.gx) * (kBM * kMaxTilesPerCta);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -239,11 +254,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       CP_PDL_WAIT();
       CP_PDL_TRIGGER();
       if (p.tab_smem) {
-        mbar_arrive_tx(tab_bar, p.tab_bytes);
+        mbar_arrive_tx(tab_bar, J.tab_bytes);
 #pragma unroll
         for (int j = 0; j < NO; ++j) {
-          bulk_load(tab_saddr + 4u * p.tab_soff[j], p.tab[j], p.tab_cpy[j], tab_bar);
-          if (p.nvar > 1) bulk_load(tab_saddr + 4u * p.tabd_soff[j], p.tabd[j], p.tab_cpy[j], tab_bar);
+          bulk_load(tab_saddr + 4u * J.tab_soff[j], J.tab[j], J.tab_cpy[j], tab_bar);
+          if (p.nvar > 1) bulk_load(tab_saddr + 4u * J.tabd_soff[j], J.tabd[j], J.tab_cpy[j], tab_bar);
         }
       }
       int issued = 0;
@@ -257,13 +272,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t st = base + (uint32_t)s * stage_bytes;
         uint32_t bytes = 0;
         for (int mt = 0; mt < p.ntm; ++mt)
-          bytes += 2u * 128u * (uint32_t)max((int64_t)0, min((int64_t)kBM, p.I - (row0 + mt * kBM)));
+          bytes += 2u * 128u * (uint32_t)max((int64_t)0, min((int64_t)kBM, J.I - (row0 + mt * kBM)));
         mbar_arrive_tx(full_bar(s), bytes);
         for (int mt = 0; mt < p.ntm; ++mt) {
           const int64_t r0 = row0 + mt * kBM;
-          if (r0 >= p.I) break;
-          const uint32_t blk = 128u * (uint32_t)min((int64_t)kBM, p.I - r0);
-          const uint8_t* src = p.tiles + kt * (2 * p.I * 128) + r0 * 256;
+          if (r0 >= J.I) break;
+          const uint32_t blk = 128u * (uint32_t)min((int64_t)kBM, J.I - r0);
+          const uint8_t* src = J.tiles + kt * (2 * J.I * 128) + r0 * 256;
           bulk_load(st + (uint32_t)mt * kTileBytes, src, blk, full_bar(s));
           bulk_load(st + (uint32_t)(p.ntm + mt) * kTileBytes, src + blk, blk, full_bar(s));
         }
@@ -312,20 +327,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int rs = p.rs;                       // FP32 table row stride (multiple of 4)
     uint32_t dim32[NO];
 #pragma unroll
-    for (int j = 0; j < NO; ++j) dim32[j] = (uint32_t)p.dimo[j];
+    for (int j = 0; j < NO; ++j) dim32[j] = (uint32_t)J.dimo[j];
     // four consecutive ranks of table row `ro` (float offset) of mode j: 16-byte
     // loads from shared memory (or through the read-only path when the tables
     // stay in global memory)
     auto ld4 = [&](int j, bool dtab, uint32_t ro) -> float4 {
       if (p.tab_smem) {
         float4 v;
-        const uint32_t a = tab_saddr + 4u * ((dtab ? p.tabd_soff[j] : p.tab_soff[j]) + ro);
+        const uint32_t a = tab_saddr + 4u * ((dtab ? J.tabd_soff[j] : J.tab_soff[j]) + ro);
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                      : "r"(a));
         return v;
       }
-      return __ldg(reinterpret_cast<const float4*>((dtab ? p.tabd[j] : p.tab[j]) + ro));
+      return __ldg(reinterpret_cast<const float4*>((dtab ? J.tabd[j] : J.tab[j]) + ro));
     };
     // column c of the B tile, SW128 K-major: hi = bf16(x), lo = bf16(x - hi)
     auto put = [&](uint8_t* bhi, uint8_t* blo, uint32_t c, float x) {
@@ -352,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint8_t* bhi = st + 2u * (uint32_t)p.ntm * kTileBytes;
         uint8_t* blo = bhi + b_bytes;
         const int64_t kb64 = (kt0 + i) * kBK + kk;
-        const bool in = kb64 < p.Kbar;
+        const bool in = kb64 < J.Kbar;
         uint32_t rowo[NO];                     // float offset of each factor row
         uint32_t rem = (uint32_t)(in ? kb64 : 0);
 #pragma unroll
@@ -440,8 +455,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = 0; c < p.RP; c += 16) {
         uint32_t v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * p.RP + c), v);
-        if (done && row < p.I) {
-          float* out = p.partial + ((int64_t)blockIdx.x * p.I + row) * p.outc;
+        if (done && row < J.I) {
+          float* out = J.partial + ((int64_t)kslice * J.I + row) * p.outc;
 #pragma unroll
           for (int e = 0; e < 16; ++e)
             if (c + e < p.outc) out[c + e] = __uint_as_float(v[e]);
@@ -581,11 +596,19 @@ static cp_status factors_f32(cp_ctx* ctx, const Layout& L, const double* u, floa
   return f32_copy(ctx, L, u, *o, total, *buf);
 }
 
-// One mode's MTTKRP from FP32 factors (u32 at offsets o).
-// Launch the tensor-core kernel; partial sums (gx x I x R floats) in *parts.
-static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o,
-                                  int mode, Parts* parts, const float* d32 = nullptr, int nvar = 1) {
-  CP_TRY(ensure_planes(ctx, t, mode));
+// The MTTKRPs of modes[0..nmodes) in one launch of the tensor-core kernel
+// (FP32 factors u32 at offsets o; with nvar > 1 the Khatri-Rao variants of
+// u32 and d32); per mode the partial sums (gx x I x outc floats) in parts[k].
+// The CTAs (one per SM) are shared among the modes in proportion to their
+// tiles of T.
+static cp_status mttkrp_tc_multi(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o,
+                                 const int* modes, int nmodes, Parts* parts, const float* d32 = nullptr,
+                                 int nvar = 1) {
+  if (nmodes < 1 || nmodes > t->N) {
+    set_error("mixed MTTKRP: %d modes in one launch", nmodes);
+    return CP_ERR_ARG;
+  }
+  for (int k = 0; k < nmodes; ++k) CP_TRY(ensure_planes(ctx, t, modes[k]));
   const int R = L.R;
   const int outc = nvar > 1 ? nvar * o.rs : R;
   const int RP = std::max(16, (outc + 15) / 16 * 16);
@@ -593,44 +616,57 @@ static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, co
     set_error("mixed MTTKRP: %d Khatri-Rao variants of rank %d not supported", nvar, R);
     return CP_ERR_UNSUPPORTED;
   }
-  const int64_t I = t->dims[mode];
-  const int64_t Kb = kbar(t, mode);
   TcParams p{};
-  p.tiles = (const uint8_t*)t->Ttile[mode];
-  p.I = I;
-  p.Kbar = Kb;
+  p.njobs = nmodes;
   p.R = R;
   p.RP = RP;
   p.nvar = nvar;
   p.outc = outc;
   p.rs = o.rs;
-  const int64_t mtiles = (I + kBM - 1) / kBM;
-  p.ntm = (int)std::min<int64_t>(mtiles, kMaxTilesPerCta);
-  const int mgroups = (int)((mtiles + kMaxTilesPerCta - 1) / kMaxTilesPerCta);
+  p.nother = t->N - 1;
+  p.status = ctx->d_status;
+  int64_t mtiles_max = 1;
+  for (int k = 0; k < nmodes; ++k) mtiles_max = std::max<int64_t>(mtiles_max, (t->dims[modes[k]] + kBM - 1) / kBM);
+  p.ntm = (int)std::min<int64_t>(mtiles_max, kMaxTilesPerCta);
   const uint32_t stage_bytes = (uint32_t)p.ntm * 2u * kTileBytes + 2u * (uint32_t)RP * 128u;
-  // factor tables of the other modes: bulk-copied to shared memory when they fit
-  size_t tab_bytes = 0;
-  p.nother = 0;
-  for (int m = 0; m < t->N; ++m) {
-    if (m == mode) continue;
-    const uint32_t cpy = (uint32_t)((size_t)t->dims[m] * o.rs * sizeof(float));   // multiple of 16
-    p.tab[p.nother] = u32 + o.off[m];
-    p.dimo[p.nother] = t->dims[m];
-    p.tab_soff[p.nother] = (uint32_t)(tab_bytes / sizeof(float));
-    p.tab_cpy[p.nother] = cpy;
-    tab_bytes += cpy;
-    if (nvar > 1) {
-      p.tabd[p.nother] = d32 + o.off[m];
-      p.tabd_soff[p.nother] = (uint32_t)(tab_bytes / sizeof(float));
+  // factor tables of the other modes: bulk-copied to shared memory when they
+  // fit (the same choice for every job of the launch)
+  size_t tab_max = 0;
+  int64_t work[CP_MAX_N], work_sum = 0, mgroups[CP_MAX_N];
+  for (int k = 0; k < nmodes; ++k) {
+    const int mode = modes[k];
+    TcJob& J = p.job[k];
+    J.tiles = (const uint8_t*)t->Ttile[mode];
+    J.I = t->dims[mode];
+    J.Kbar = kbar(t, mode);
+    J.ktiles = (J.Kbar + kBK - 1) / kBK;
+    size_t tab_bytes = 0;
+    int j = 0;
+    for (int m = 0; m < t->N; ++m) {
+      if (m == mode) continue;
+      const uint32_t cpy = (uint32_t)((size_t)t->dims[m] * o.rs * sizeof(float));   // multiple of 16
+      J.tab[j] = u32 + o.off[m];
+      J.dimo[j] = t->dims[m];
+      J.tab_soff[j] = (uint32_t)(tab_bytes / sizeof(float));
+      J.tab_cpy[j] = cpy;
       tab_bytes += cpy;
+      if (nvar > 1) {
+        J.tabd[j] = d32 + o.off[m];
+        J.tabd_soff[j] = (uint32_t)(tab_bytes / sizeof(float));
+        tab_bytes += cpy;
+      }
+      ++j;
     }
-    ++p.nother;
+    J.tab_bytes = (uint32_t)tab_bytes;
+    tab_max = std::max(tab_max, tab_bytes);
+    const int64_t mt = (J.I + kBM - 1) / kBM;
+    mgroups[k] = (mt + kMaxTilesPerCta - 1) / kMaxTilesPerCta;
+    work[k] = J.ktiles * mt;
+    work_sum += work[k];
   }
-  p.tab_bytes = (uint32_t)tab_bytes;
   const size_t fixed = 1024 + 256 + 64;          // alignment slack, barriers, TMEM slot
-  p.tab_smem = (tab_bytes <= 96 * 1024 &&
-                (size_t)kMaxDynSmem >= fixed + tab_bytes + 2 * (size_t)stage_bytes) ? 1 : 0;
-  const size_t avail = (size_t)kMaxDynSmem - fixed - (p.tab_smem ? tab_bytes : 0);
+  p.tab_smem = (tab_max <= 96 * 1024 && (size_t)kMaxDynSmem >= fixed + tab_max + 2 * (size_t)stage_bytes) ? 1 : 0;
+  const size_t avail = (size_t)kMaxDynSmem - fixed - (p.tab_smem ? tab_max : 0);
   p.stages = (int)std::min<size_t>(6, avail / stage_bytes);
   if (p.stages < 2) {
     set_error("mixed MTTKRP: rank %d too large for the shared-memory pipeline", R);
@@ -639,23 +675,37 @@ static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, co
   uint32_t cols = 32;
   while (cols < (uint32_t)(p.ntm * RP)) cols <<= 1;
   p.ncols = cols;
-  p.ktiles = (Kb + kBK - 1) / kBK;
-  const int64_t target = std::max<int64_t>(1, ctx->num_sms / mgroups);
-  p.ktiles_per_cta = (p.ktiles + target - 1) / target;
-  const int gx = (int)((p.ktiles + p.ktiles_per_cta - 1) / p.ktiles_per_cta);
-  float* partial = nullptr;
-  CP_TRY(ws_alloc(ctx, (void**)&partial, sizeof(float) * (size_t)gx * I * p.outc));
-  p.partial = partial;
-  p.status = ctx->d_status;
-  const size_t smem = (size_t)p.stages * stage_bytes + fixed + (p.tab_smem ? tab_bytes : 0);
+  // contraction slices per row group: the job's share of the SMs
+  int cta = 0;
+  for (int k = 0; k < nmodes; ++k) {
+    TcJob& J = p.job[k];
+    const double share = (double)ctx->num_sms * (double)work[k] / (double)std::max<int64_t>(1, work_sum);
+    const int64_t target = std::max<int64_t>(1, (int64_t)(share / (double)mgroups[k]));
+    J.ktiles_per_cta = std::max<int64_t>(1, (J.ktiles + target - 1) / target);
+    J.gx = (int)((J.ktiles + J.ktiles_per_cta - 1) / J.ktiles_per_cta);
+    J.cta0 = cta;
+    cta += J.gx * (int)mgroups[k];
+  }
+  for (int k = 0; k < nmodes; ++k) {
+    TcJob& J = p.job[k];
+    float* partial = nullptr;
+    CP_TRY(ws_alloc(ctx, (void**)&partial, sizeof(float) * (size_t)J.gx * J.I * outc));
+    J.partial = partial;
+    parts[k] = Parts{partial, J.gx, 1};
+  }
+  const size_t smem = (size_t)p.stages * stage_bytes + fixed + (p.tab_smem ? tab_max : 0);
   CP_TRY(set_smem_attr());
   {
     TimerScope ts(ctx, 0);
-    (void)launch_pdl(tc_kernel_for(p.nother), dim3(gx, mgroups), dim3(kThreads), smem, ctx->stream, p);
+    (void)launch_pdl(tc_kernel_for(p.nother), dim3(cta), dim3(kThreads), smem, ctx->stream, p);
   }
   CP_LAUNCH_CHECK();
-  *parts = Parts{partial, gx, 1};
   return CP_OK;
+}
+
+static cp_status mttkrp_tc_launch(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o,
+                                  int mode, Parts* parts, const float* d32 = nullptr, int nvar = 1) {
+  return mttkrp_tc_multi(ctx, t, L, u32, o, &mode, 1, parts, d32, nvar);
 }
 
 static cp_status mttkrp_tc_core(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o,
@@ -673,8 +723,8 @@ cp_status mttkrp_tc_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const floa
 }
 
 cp_status mttkrp_tc_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* a32, const float* d32,
-                             const F32Off& o, int mode, Parts* out) {
-  return mttkrp_tc_launch(ctx, t, L, a32, o, mode, out, d32, 1 << (L.N - 1));
+                             const F32Off& o, const int* modes, int nmodes, Parts* out) {
+  return mttkrp_tc_multi(ctx, t, L, a32, o, modes, nmodes, out, d32, 1 << (L.N - 1));
 }
 
 bool tc_variants_supported(const Layout& L) {

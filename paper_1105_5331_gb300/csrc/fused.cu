@@ -63,6 +63,22 @@ __global__ void __launch_bounds__(256) xprep_kernel(Layout L, const double* __re
   }
 }
 
+// Grams of x = base + beta d from those of base and d (per mode: base^T base,
+// base^T d, d^T d):  X^T X = B^T B + beta (B^T D + D^T B) + beta^2 D^T D.
+__global__ void grams_from_ls_kernel(int N, int R, const double* __restrict__ ls, const double* __restrict__ stp,
+                                     double* __restrict__ out) {
+  CP_PDL_ENTRY();
+  const double b = *stp;
+  const int RR = R * R;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N * RR; e += gridDim.x * blockDim.x) {
+    const int n = e / RR, k = e - n * RR;
+    const int r = k / R, s = k - r * R;
+    const double* ad = ls + (int64_t)(N + n) * RR;
+    const double cross = ad[r * R + s] + ad[s * R + r];
+    out[e] = fma(b, fma(b, ls[(int64_t)(2 * N + n) * RR + k], cross), ls[(int64_t)n * RR + k]);
+  }
+}
+
 struct FinishParams {
   Layout L;
   Parts parts[CP_MAX_N];
@@ -75,9 +91,10 @@ struct FinishParams {
   const double* d;        // nullable: also g . d
   double* gd;
   double* m0_out;         // nullable: M^(1) (mode 0) of the evaluation point
-  // nullable: the last mode's M from the line-search variants,
-  // M = sum_v beta^popc(v) mv[v] (x = base + beta d is multilinear in beta)
-  const double* mv;
+  // per mode, nullable: M given (mv_nvar = 1) or from the line-search
+  // variants, M = sum_v beta^popc(v) mv[n][v I_n R + .] (x = base + beta d
+  // is multilinear in beta)
+  const double* mv[CP_MAX_N];
   int mv_nvar;
   const double* mv_beta;
   double* blk;            // 2 x gridDim.x block partials
@@ -120,12 +137,15 @@ __global__ void __launch_bounds__(256) fg_finish_kernel(const FinishParams p) {
     double inner = 0.0, gdv = 0.0;
     if (e < nel) {
       double mval = 0.0;
-      if (p.mv && n == N - 1) {
+      const double* mv = p.mv[n];
+      if (mv && p.mv_nvar == 1) {
+        mval = mv[e];
+      } else if (mv) {
         const double beta = *p.mv_beta;
         double pw[CP_MAX_N];
         pw[0] = 1.0;
         for (int k = 1; k < N; ++k) pw[k] = pw[k - 1] * beta;
-        for (int v = 0; v < p.mv_nvar; ++v) mval = fma(pw[__popc(v)], p.mv[(int64_t)v * nel + e], mval);
+        for (int v = 0; v < p.mv_nvar; ++v) mval = fma(pw[__popc(v)], mv[(int64_t)v * nel + e], mval);
       } else {
 #pragma unroll
         for (int q = 0; q < 8; ++q) mval += sh[q][lane];
@@ -205,14 +225,30 @@ cp_status mttkrp_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double*
   return mttkrp_f64_parts(ctx, t, L, u, mode, out);
 }
 
+// The MTTKRPs of several modes, one launch per mode.  (One tensor-core
+// launch for all of them streams T faster, but then each CTA accumulates a
+// longer contraction range in FP32 tensor memory, and the error of the
+// gradient grows with that length: about 2e-8 x P at 14 tiles of 64 per CTA,
+// 8e-8 x P at 43, which is close to the stopping tolerance of the solver.)
+static cp_status mttkrp_parts_multi(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, const float* u32,
+                                    const F32Off& o32, const int* modes, int nmodes, cp_precision prec, Parts* out) {
+  for (int k = 0; k < nmodes; ++k) CP_TRY(mttkrp_parts(ctx, t, L, u, u32, o32, modes[k], prec, &out[k]));
+  return CP_OK;
+}
+
 cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const double* base, const double* d,
                      const double* stp, double* x, double* f, double* g, cp_precision prec, double* gd,
-                     double* grams_out, double* m0_out, const double* mv_last, const double* mv_beta,
-                     const double* grams_in, double* xi0_out) {
+                     double* grams_out, double* m0_out, const MGiven* mg, const double* grams_in,
+                     double* xi0_out, const double* grams_ls) {
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int R = L.R, N = L.N, RR = R * R;
   const double* u = d ? x : base;
-  const bool want_f32 = t->kind == 0 && prec == CP_MIXED_BF16X3;
+  // MTTKRPs (all modes for g; the last one alone for f), less those supplied
+  const int first = g || d ? 0 : N - 1;
+  int modes[CP_MAX_N], nm = 0;
+  for (int n = first; n < N; ++n)
+    if (!(mg && mg->m[n])) modes[nm++] = n;
+  const bool want_f32 = t->kind == 0 && prec == CP_MIXED_BF16X3 && nm > 0;
   // x and its FP32 copy on the main stream; the Grams of x on the aux
   // stream, overlapped with the MTTKRPs (which do not need them)
   int64_t acc32 = 0;
@@ -226,9 +262,17 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
     grams = grams_out;
   else
     CP_TRY(ws_alloc(ctx, (void**)&grams, sizeof(double) * (size_t)N * RR));
+  // the Grams of x from a line search's Grams (main stream), else from the
+  // factors (aux stream, overlapped with the MTTKRPs)
+  const bool grams_on_aux = !grams_in && !(grams_ls && d);
+  if (!grams_in && !grams_on_aux) {
+    (void)launch_pdl(grams_from_ls_kernel, dim3((unsigned)((N * RR + 255) / 256)), dim3(256), 0, ctx->stream, N, R,
+                     grams_ls, stp, grams);
+    CP_LAUNCH_CHECK();
+  }
   CP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream));
   CP_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
-  if (!grams_in) {
+  if (grams_on_aux) {
     GramJob jobs[kMaxGramJobs];
     for (int n = 0; n < N; ++n) {
       jobs[n] = GramJob{base + L.off[n], base + L.off[n], L.dims[n], grams + (size_t)n * RR, 1};
@@ -248,11 +292,12 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
     (void)launch_pdl(xprep_kernel, dim3(blocks), dim3(256), 0, ctx->stream, L, base, d, stp, x, x32, o, total);
     CP_LAUNCH_CHECK();
   }
-  // MTTKRPs (all modes for g; the last one alone for f)
   FinishParams fp{};
-  const int first = g || d ? 0 : N - 1;
-  const int last_pass = mv_last ? N - 1 : N;   // the last mode may come from the line-search variants
-  for (int n = first; n < last_pass; ++n) CP_TRY(mttkrp_parts(ctx, t, L, u, x32, o32, n, prec, &fp.parts[n]));
+  {
+    Parts pm[CP_MAX_N];
+    CP_TRY(mttkrp_parts_multi(ctx, t, L, u, x32, o32, modes, nm, prec, pm));
+    for (int k = 0; k < nm; ++k) fp.parts[modes[k]] = pm[k];
+  }
   // finish
   fp.L = L;
   int64_t chunks = 0;
@@ -269,17 +314,23 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   fp.d = gd ? d : nullptr;   // g . d only when asked for
   fp.gd = gd;
   fp.m0_out = m0_out;
-  fp.mv = mv_last;
-  fp.mv_nvar = 1 << (N - 1);
-  fp.mv_beta = mv_beta;
+  if (mg) {
+    for (int n = 0; n < N; ++n) fp.mv[n] = mg->m[n];
+    fp.mv_nvar = mg->nvar;
+    fp.mv_beta = mg->beta;
+  } else {
+    fp.mv_nvar = 1;
+  }
   fp.counter = ctx->d_counter;
   fp.status = ctx->d_status;
   CP_TRY(ws_alloc(ctx, (void**)&fp.blk, sizeof(double) * 2 * (size_t)chunks + 16));
-  CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+  // the finish needs the Grams; the inverse alone may run on beside it
+  if (grams_on_aux) CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
   (void)launch_pdl(fg_finish_kernel, dim3((unsigned)chunks), dim3(256), 0, ctx->stream, fp);
   CP_LAUNCH_CHECK();
+  if (!grams_on_aux) CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
   ws_free(ctx, fp.blk);
-  for (int n = first; n < last_pass; ++n) ws_free(ctx, const_cast<void*>(fp.parts[n].p));
+  for (int k = 0; k < nm; ++k) ws_free(ctx, const_cast<void*>(fp.parts[modes[k]].p));
   if (!grams_out && !grams_in) ws_free(ctx, grams);
   if (x32) ws_free(ctx, x32);
   return CP_OK;

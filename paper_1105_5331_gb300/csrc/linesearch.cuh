@@ -24,10 +24,16 @@ struct SolveCtl;
 // f = phi there, nfev, info); poly the 2N + 1 coefficients.  With ctl the
 // solver counters are updated, and with use_h the graph condition h is set to
 // "accept" (info 1, or sufficient decrease at the last trial).  mv_out
-// (nullable, 2^(N-1) x I_N x R): the variant MTTKRPs M_v of the last mode.
+// (nullable, 2^(N-1) x P doubles; mode n's block of 2^(N-1) x I_n x R at
+// 2^(N-1) L.off[n]): the variant MTTKRPs M_v of the last mode, and, where
+// one tensor-core launch can make them alongside (dense, mixed precision),
+// those of every other mode too; *all_modes (nullable) tells which.
+// grams_out (nullable, 3 x N x R x R): keeps the Grams the polynomial is
+// built from, base^T base, base^T d and d^T d per mode (in that order).
 cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* base, const double* d,
                   cp_precision prec, const cp_ls_opts& o, MTState* st, double* poly, SolveCtl* ctl,
-                  cudaGraphConditionalHandle h, int use_h, double* mv_out = nullptr);
+                  cudaGraphConditionalHandle h, int use_h, double* mv_out = nullptr, bool* all_modes = nullptr,
+                  double* grams_out = nullptr);
 
 
 }  // namespace cpg

@@ -27,7 +27,7 @@
 namespace cpg {
 
 cp_status mttkrp_tc_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* a32, const float* d32,
-                             const F32Off& o, int mode, Parts* out);
+                             const F32Off& o, const int* modes, int nmodes, Parts* out);
 bool tc_variants_supported(const Layout& L);
 
 namespace {
@@ -52,6 +52,15 @@ struct CoefParams {
   double* blk;                  // [2][gridDim.x]
   double* poly;                 // 2N + 1 coefficients out
   double* mv_out;               // nullable: M_v (nvar x I x R, FP64)
+  // the other modes' variants (tensor-core layout, like the last mode's),
+  // summed into xout[k] (nvar x I x R, FP64) by the blocks past the last
+  // mode's nvar x chunks
+  int nx;
+  const float* xpp[CP_MAX_N - 1];
+  int xcount[CP_MAX_N - 1];
+  int64_t xI[CP_MAX_N - 1];
+  int64_t xblk_off[CP_MAX_N];   // prefix of nvar x chunks over those modes
+  double* xout[CP_MAX_N - 1];
   MTState* st;
   cp_ls_opts o;
   SolveCtl* ctl;                // nullable: solver counters
@@ -157,43 +166,67 @@ __global__ void __launch_bounds__(256) ls_coef_kernel(const CoefParams p) {
   __shared__ bool is_last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int R = p.R, N = p.N;
-  const int v = (int)(blockIdx.x / p.chunks);
-  const int64_t e = (blockIdx.x - (int64_t)v * p.chunks) * 32 + lane;
-  const int64_t nout = p.I * R;
-  const bool in = e < nout;
-  const int64_t i = in ? e / R : 0;
-  const int r = in ? (int)(e - i * R) : 0;
-  const int64_t nel = p.I * p.col_stride;
-  const int64_t idx = i * p.col_stride + p.col_off[v] + r;
-  // M_v[i][r]: warp w adds partials c = w, w + 8, ...; warp 0 the warp sums
-  if (p.f32) {
-    redf[w][lane] = in ? strided_sum((const float*)p.pp[v] + idx, w, p.count[v], 8, nel) : 0.f;
-  } else {
-    redd[w][lane] = in ? strided_sum((const double*)p.pp[v] + idx, w, p.count[v], 8, nel) : 0.0;
-  }
-  __syncthreads();
-  if (w == 0) {
-    double m = 0.0;
-    if (p.f32) {
+  if ((int64_t)blockIdx.x >= (int64_t)p.nvar * p.chunks) {
+    // another mode's variants: sum the partials into xout (no coefficient)
+    const int64_t b = (int64_t)blockIdx.x - (int64_t)p.nvar * p.chunks;
+    int k = 0;
+    while (k + 1 < p.nx && b >= p.xblk_off[k + 1]) ++k;
+    const int64_t xch = (p.xI[k] * R + 31) / 32;
+    const int64_t bb = b - p.xblk_off[k];
+    const int vx = (int)(bb / xch);
+    const int64_t ex = (bb - (int64_t)vx * xch) * 32 + lane;
+    const int64_t noutx = p.xI[k] * R;
+    const bool inx = ex < noutx;
+    const int64_t ix = inx ? ex / R : 0;
+    const int rx = inx ? (int)(ex - ix * R) : 0;
+    const int64_t idxx = ix * p.col_stride + p.col_off[vx] + rx;
+    redf[w][lane] = inx ? strided_sum(p.xpp[k] + idxx, w, p.xcount[k], 8, p.xI[k] * p.col_stride) : 0.f;
+    __syncthreads();
+    if (w == 0 && inx) {
       float t = 0.f;
 #pragma unroll
       for (int q = 0; q < 8; ++q) t += redf[q][lane];
-      m = (double)t;
+      p.xout[k][(int64_t)vx * noutx + ex] = (double)t;
+    }
+  } else {
+    const int v = (int)(blockIdx.x / p.chunks);
+    const int64_t e = (blockIdx.x - (int64_t)v * p.chunks) * 32 + lane;
+    const int64_t nout = p.I * R;
+    const bool in = e < nout;
+    const int64_t i = in ? e / R : 0;
+    const int r = in ? (int)(e - i * R) : 0;
+    const int64_t nel = p.I * p.col_stride;
+    const int64_t idx = i * p.col_stride + p.col_off[v] + r;
+    // M_v[i][r]: warp w adds partials c = w, w + 8, ...; warp 0 the warp sums
+    if (p.f32) {
+      redf[w][lane] = in ? strided_sum((const float*)p.pp[v] + idx, w, p.count[v], 8, nel) : 0.f;
     } else {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) m += redd[q][lane];
+      redd[w][lane] = in ? strided_sum((const double*)p.pp[v] + idx, w, p.count[v], 8, nel) : 0.0;
     }
-    if (p.mv_out && in) p.mv_out[(int64_t)v * nout + e] = m;
-    double a = in ? m * p.Alast[e] : 0.0;
-    double b = in ? m * p.Dlast[e] : 0.0;
+    __syncthreads();
+    if (w == 0) {
+      double m = 0.0;
+      if (p.f32) {
+        float t = 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    if (lane == 0) {
-      p.blk[blockIdx.x] = a;
-      p.blk[gridDim.x + blockIdx.x] = b;
+        for (int q = 0; q < 8; ++q) t += redf[q][lane];
+        m = (double)t;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) m += redd[q][lane];
+      }
+      if (p.mv_out && in) p.mv_out[(int64_t)v * nout + e] = m;
+      double a = in ? m * p.Alast[e] : 0.0;
+      double b = in ? m * p.Dlast[e] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+      }
+      if (lane == 0) {
+        p.blk[blockIdx.x] = a;
+        p.blk[gridDim.x + blockIdx.x] = b;
+      }
     }
   }
   __threadfence();
@@ -271,7 +304,7 @@ __global__ void mix_kernel(Layout L, const double* __restrict__ a, const double*
 
 cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const double* base, const double* d,
                   cp_precision prec, const cp_ls_opts& o, MTState* st, double* poly, SolveCtl* ctl,
-                  cudaGraphConditionalHandle h, int use_h, double* mv_out) {
+                  cudaGraphConditionalHandle h, int use_h, double* mv_out, bool* all_modes, double* grams_out) {
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int N = L.N, R = L.R, RR = R * R;
   const int last = N - 1;
@@ -281,14 +314,22 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
   const bool tc_var = tc && tc_variants_supported(L);
   int64_t acc32 = 0;
   const F32Off o32 = f32_layout(L, &acc32);
+  // every mode's variants in the same launch when they are kept and the
+  // Khatri-Rao tiles stay narrow (at most 64 variant columns per contraction
+  // element: wider ones make the tile builders, not the stream of T, the
+  // bound, and the variants of the other modes would cost more than the
+  // plain passes they replace)
+  const bool all = tc_var && mv_out && nvar * o32.rs <= 64;
+  if (all_modes) *all_modes = all;
   const int64_t P = L.P();
   const unsigned eblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 4 * ctx->num_sms));
   // Grams on the aux stream, overlapped with the MTTKRP
-  double* grams = nullptr;
+  double* work = nullptr;
   const size_t eblocks_n = (size_t)((RR + 255) / 256);
-  CP_TRY(ws_alloc(ctx, (void**)&grams,
+  CP_TRY(ws_alloc(ctx, (void**)&work,
                   sizeof(double) * (3 * (size_t)N * RR + (eblocks_n + 1) * (kMaxDeg + 1))));
-  double* eblk = grams + 3 * (size_t)N * RR;
+  double* grams = grams_out ? grams_out : work;
+  double* eblk = work + 3 * (size_t)N * RR;
   double* epoly = eblk + eblocks_n * (kMaxDeg + 1);
   CP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream));
   CP_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
@@ -311,6 +352,8 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
   // the variant MTTKRPs of the last mode
   CoefParams cp{};
   Parts parts[kMaxVar];
+  Parts pts[CP_MAX_N];
+  int nm = 0;
   float *a32 = nullptr, *d32 = nullptr, *w32 = nullptr;
   double* wv = nullptr;
   if (tc_var) {
@@ -318,14 +361,28 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
     CP_TRY(ws_alloc(ctx, (void**)&d32, sizeof(float) * (size_t)acc32 + 64));
     CP_TRY(f32_copy(ctx, L, base, o32, acc32, a32));
     CP_TRY(f32_copy(ctx, L, d, o32, acc32, d32));
-    Parts pt;
-    CP_TRY(mttkrp_tc_variants(ctx, t, L, a32, d32, o32, last, &pt));
+    // the last mode first, then (all) the others
+    int modes[CP_MAX_N];
+    modes[nm++] = last;
+    if (all)
+      for (int n = 0; n < last; ++n) modes[nm++] = n;
+    CP_TRY(mttkrp_tc_variants(ctx, t, L, a32, d32, o32, modes, nm, pts));
     // variant v occupies columns v rs .. v rs + R - 1 of the partial sums
     for (int v = 0; v < nvar; ++v) {
-      parts[v] = pt;
+      parts[v] = pts[0];
       cp.col_off[v] = v * o32.rs;
     }
     cp.col_stride = nvar * o32.rs;
+    cp.nx = nm - 1;
+    cp.xblk_off[0] = 0;
+    for (int k = 0; k + 1 < nm; ++k) {
+      const int n = modes[k + 1];
+      cp.xpp[k] = (const float*)pts[k + 1].p;
+      cp.xcount[k] = pts[k + 1].count;
+      cp.xI[k] = L.dims[n];
+      cp.xout[k] = mv_out + (size_t)nvar * L.off[n];
+      cp.xblk_off[k + 1] = cp.xblk_off[k] + (int64_t)nvar * ((L.dims[n] * R + 31) / 32);
+    }
   } else {
     CP_TRY(ws_alloc(ctx, (void**)&wv, sizeof(double) * (size_t)nvar * P));
     if (tc) CP_TRY(ws_alloc(ctx, (void**)&w32, sizeof(float) * (size_t)nvar * acc32 + 64));
@@ -355,7 +412,7 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
   cp.epoly = epoly;
   cp.norm2 = t->norm2;
   cp.poly = poly;
-  cp.mv_out = mv_out;
+  cp.mv_out = mv_out ? mv_out + (size_t)nvar * L.off[last] : nullptr;
   cp.st = st;
   cp.o = o;
   cp.ctl = ctl;
@@ -363,14 +420,14 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
   cp.use_h = use_h;
   cp.counter = ctx->d_counter;
   cp.status = ctx->d_status;
-  const int64_t nblocks = (int64_t)nvar * cp.chunks;
+  const int64_t nblocks = (int64_t)nvar * cp.chunks + cp.xblk_off[cp.nx];
   CP_TRY(ws_alloc(ctx, (void**)&cp.blk, sizeof(double) * 2 * (size_t)nblocks + 16));
   CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
   (void)launch_pdl(ls_coef_kernel, dim3((unsigned)nblocks), dim3(256), 0, ctx->stream, cp);
   CP_LAUNCH_CHECK();
   ws_free(ctx, cp.blk);
   if (tc_var) {
-    ws_free(ctx, const_cast<void*>(parts[0].p));
+    for (int k = 0; k < nm; ++k) ws_free(ctx, const_cast<void*>(pts[k].p));
   } else {
     for (int v = 0; v < nvar; ++v) ws_free(ctx, const_cast<void*>(parts[v].p));
   }
@@ -378,7 +435,7 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
   if (d32) ws_free(ctx, d32);
   if (w32) ws_free(ctx, w32);
   if (wv) ws_free(ctx, wv);
-  ws_free(ctx, grams);
+  ws_free(ctx, work);
   return CP_OK;
 }
 

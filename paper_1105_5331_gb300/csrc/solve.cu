@@ -402,9 +402,10 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   const size_t RR = (size_t)o.R * o.R;
   const int cap = o.w;
   const size_t n0 = (size_t)L.dims[0] * o.R;                                  // M^(1) of u, ubar, x
-  const size_t nmv = ((size_t)1 << (L.N - 1)) * (size_t)L.dims[L.N - 1] * o.R;  // line-search variants
+  const size_t nl = (size_t)L.dims[L.N - 1] * o.R;                           // M^(N) of the swept point, ubar
+  const size_t nmv = ((size_t)1 << (L.N - 1)) * (size_t)P;                   // line-search variants, every mode
   const size_t bytes = sizeof(double) * (9 * (size_t)P + 2 * (size_t)cap * P + (size_t)Imax * o.R +
-                                         (size_t)L.N * RR + 16 + 40 + 3 * n0 + nmv + 2 * (size_t)L.N * RR +
+                                         (size_t)L.N * RR + 16 + 40 + 3 * n0 + 2 * nl + nmv + 5 * (size_t)L.N * RR +
                                          3 * (RR + 2)) +
                        sizeof(MTState) + sizeof(SolveCtl) + 512;
   CP_CUDA(cudaMallocAsync(&base, bytes, sub.stream));
@@ -427,6 +428,9 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   m.M0 = p; p += n0;
   m.M0bar = p; p += n0;
   m.M0x = p; p += n0;
+  m.Ml = p; p += nl;
+  m.Mlbar = p; p += nl;
+  m.Gls = p; p += 3 * (size_t)L.N * RR;
   m.Mv = p; p += nmv;
   m.Gu = p; p += (size_t)L.N * RR;
   m.Gbar = p; p += (size_t)L.N * RR;
@@ -518,7 +522,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
     CP_TRY(counted(&kcount.top, [&]() -> cp_status {
       if (first) CP_TRY(normalize_into(ctx, L, m.work, m.u, nullptr, nullptr, nullptr));
       CP_TRY(fg_eval_ex(ctx, t, L, m.u, nullptr, nullptr, nullptr, m.scal + F, m.g, pr, nullptr, m.Gu, m.M0,
-                        nullptr, nullptr, nullptr, m.Xi0));
+                        nullptr, nullptr, m.Xi0));
       // window <- {(u, g)}, ||g||^2, the stopping test
       return tail(s0, h_outer, 1);
     }));
@@ -530,10 +534,15 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
           // Step I on u in place (u itself is already in the window); u's
           // Grams, M^(1) and Gammabar^(1) inverse were carried over from the
           // point u was made from
-          CP_TRY(als_sweep_v2(ctx, t, L, m.u, pr, m.Gu, true, m.M0, m.Xi0));
-          CP_TRY(normalize_into(ctx, L, m.u, m.ubar, nullptr, nullptr, nullptr, m.Gu, nullptr, nullptr, m.Gbar));
+          // (the sweep's last MTTKRP is M^(N) of the swept point: it follows
+          // the normalisation and stands in for that mode's pass at ubar)
+          CP_TRY(als_sweep_v2(ctx, t, L, m.u, pr, m.Gu, true, m.M0, m.Xi0, m.Ml));
+          CP_TRY(normalize_into(ctx, L, m.u, m.ubar, nullptr, nullptr, nullptr, m.Gu, nullptr, nullptr, m.Gbar,
+                                nullptr, nullptr, m.Ml, m.Mlbar));
+          MGiven mg_bar;
+          mg_bar.m[L.N - 1] = m.Mlbar;
           CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, nullptr, nullptr, nullptr, m.scal + FBAR, m.gbar, pr, nullptr,
-                            nullptr, m.M0bar, nullptr, nullptr, m.Gbar, m.Xi0bar));
+                            nullptr, m.M0bar, &mg_bar, m.Gbar, m.Xi0bar));
           // Step II, then normalise uhat, d = uhat - ubar, slope, restart test
           double* colsq = nullptr;
           double* blk = nullptr;
@@ -559,17 +568,22 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
             // pass), which also sets `accept`
             cudaGraphConditionalHandle h_acc;
             CP_TRY(new_handle(side[1], 0, &h_acc));
+            bool ls_all = false;
             CP_TRY(counted(&kcount.ls_fixed, [&]() -> cp_status {
-              return ls_poly(ctx, t, L, m.ubar, m.d, pr, lso, m.st, m.poly, m.ctl, h_acc, 1, m.Mv);
+              return ls_poly(ctx, t, L, m.ubar, m.d, pr, lso, m.st, m.poly, m.ctl, h_acc, 1, m.Mv, &ls_all, m.Gls);
             }));
             return add_conditional(side[1], side[2], h_acc, cudaGraphCondTypeIf, 2, [&](int ab) -> cp_status {
               return with_stream(side[2], [&]() -> cp_status {
                 return counted(ab == 0 ? &kcount.accept : &kcount.reject, [&]() -> cp_status {
                   if (ab == 0) {
-                    // x = ubar + beta d, f and g there
-                    // (the last mode's M from the line-search variants)
+                    // x = ubar + beta d, f and g there (the last mode's M,
+                    // or every mode's, from the line-search variants)
+                    MGiven mg_x;
+                    mg_x.nvar = 1 << (L.N - 1);
+                    mg_x.beta = &m.st->stp_eval;
+                    for (int n = ls_all ? 0 : L.N - 1; n < L.N; ++n) mg_x.m[n] = m.Mv + (size_t)mg_x.nvar * L.off[n];
                     CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, m.d, &m.st->stp_eval, m.x, m.scal + FX, m.gx, pr,
-                                      nullptr, m.grams, m.M0x, m.Mv, &m.st->stp_eval, nullptr, m.Xi0x));
+                                      nullptr, m.grams, m.M0x, &mg_x, nullptr, m.Xi0x, m.Gls));
                     CP_TRY(normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr, m.grams, m.M0x, m.M0, m.Gu,
                                           m.Xi0x, m.Xi0));
                     return dcopy(ctx, 1, m.scal + FX, m.scal + F);

@@ -27,9 +27,13 @@ struct KernelCounts {
 
 struct SolverMem {
   double *u, *g, *ubar, *gbar, *uhat, *d, *x, *gx, *work, *M, *grams, *scal, *poly, *U, *G;
-  // M^(1) of u, ubar and x (the next ALS sweep starts from u's), and the
-  // line-search variant MTTKRPs of the last mode
-  double *M0, *M0bar, *M0x, *Mv;
+  // M^(1) of u, ubar and x (the next ALS sweep starts from u's), M^(N) of
+  // the swept point and of ubar, and the line-search variant MTTKRPs of the
+  // last mode
+  double *M0, *M0bar, *M0x, *Ml, *Mlbar, *Mv;
+  // the line search's Grams (ubar^T ubar, ubar^T d, d^T d per mode), from
+  // which those of the accepted point follow
+  double* Gls;
   // Grams of u and ubar (N x R x R); inverses of Gammabar^(1) of u, ubar and
   // x with their ok flags (R*R + 2 doubles each)
   double *Gu, *Gbar, *Xi0, *Xi0bar, *Xi0x;
