@@ -105,7 +105,8 @@ __global__ void __launch_bounds__(256) norm_apply_kernel(Layout L, const double*
                                                          const double* __restrict__ xi_src,
                                                          double* __restrict__ xi_dst,
                                                          const double* __restrict__ ml_src,
-                                                         double* __restrict__ ml_dst) {
+                                                         double* __restrict__ ml_dst, float* __restrict__ dst32,
+                                                         F32Off o32) {
   CP_PDL_ENTRY();
   __shared__ NormShared sh;
   norm_prologue(L, part, S, grams, lambda_out, status, sh);
@@ -123,7 +124,9 @@ __global__ void __launch_bounds__(256) norm_apply_kernel(Layout L, const double*
     const int q = order[p];
     const int64_t srcidx = L.off[n] + i * R + q;
     const double sc = scale[n * R + q];
-    dst[e] = src[srcidx] * sc;
+    const double v = src[srcidx] * sc;
+    dst[e] = v;
+    if (dst32) dst32[o32.off[n] + i * o32.rs + p] = (float)v;
     if (gdst) gdst[e] = gsrc[srcidx] / sc;
   }
   if (m0_dst) {
@@ -209,7 +212,7 @@ cp_status dot(cp_ctx* ctx, int64_t n, const double* x, const double* y, double* 
 cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double* dst,
                          const double* gsrc, double* gdst, double* lambda, const double* grams,
                          const double* m0_src, double* m0_dst, double* grams_out, const double* xi_src,
-                         double* xi_dst, const double* ml_src, double* ml_dst) {
+                         double* xi_dst, const double* ml_src, double* ml_dst, float* dst32) {
   const int R = L.R;
   double* part = nullptr;
   int S = 1;
@@ -226,7 +229,7 @@ cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double
   (void)launch_pdl(norm_apply_kernel, dim3(grid_for(ctx, L.P(), 256)), dim3(256), 0, ctx->stream, L, src, dst, gsrc, gdst, part, S, grams,
                                                                         lambda, ctx->d_status, m0_src, m0_dst,
                                                                         grams ? grams_out : nullptr, xi_src, xi_dst,
-                                                                        ml_src, ml_dst);
+                                                                        ml_src, ml_dst, dst32, [&]() { int64_t a; return f32_layout(L, &a); }());
   CP_LAUNCH_CHECK();
   if (part) ws_free(ctx, part);
   return CP_OK;

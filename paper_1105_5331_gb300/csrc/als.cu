@@ -421,7 +421,8 @@ cp_status grams_of(cp_ctx* ctx, cudaStream_t s, unsigned* counter, const Layout&
 // With mlast_out the last mode's M^(N) (from the updated modes 1..N-1) is
 // kept: it is M^(N) of the swept point as well.
 cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, double* u, cp_precision prec,
-                       double* grams, bool grams_valid, const double* m0, const double* xi0, double* mlast_out) {
+                       double* grams, bool grams_valid, const double* m0, const double* xi0, double* mlast_out,
+                       float* u32_io) {
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int R = L.R, N = L.N, RR = R * R;
   const bool want_f32 = t->kind == 0 && prec == CP_MIXED_BF16X3;
@@ -430,11 +431,13 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
   float* u32 = nullptr;
   double* Xinv = nullptr;
   int* ok = nullptr;
-  if (want_f32) CP_TRY(ws_alloc(ctx, (void**)&u32, sizeof(float) * (size_t)acc32 + 64));
+  const bool own32 = want_f32 && !u32_io;
+  if (want_f32) u32 = u32_io;
+  if (own32) CP_TRY(ws_alloc(ctx, (void**)&u32, sizeof(float) * (size_t)acc32 + 64));
   CP_TRY(ws_alloc(ctx, (void**)&Xinv, sizeof(double) * (size_t)RR + 64));
   ok = (int*)(Xinv + RR);
   CP_TRY(inverse_smem_attr());
-  if (want_f32) CP_TRY(f32_copy(ctx, L, u, o32, acc32, u32));
+  if (own32) CP_TRY(f32_copy(ctx, L, u, o32, acc32, u32));
   if (!grams_valid) CP_TRY(grams_of(ctx, ctx->stream, ctx->d_counter, L, u, 0, N, grams));
   const int rows = std::max(1, 32 / R);
   for (int n = 0; n < N; ++n) {
@@ -474,7 +477,7 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
   }
   CP_TRY(grams_of(ctx, ctx->stream, ctx->d_counter, L, u, N - 1, 1, grams));
   ws_free(ctx, Xinv);
-  if (u32) ws_free(ctx, u32);
+  if (own32) ws_free(ctx, u32);
   return CP_OK;
 }
 

@@ -258,12 +258,13 @@ cp_status mttkrp_any(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const dou
 // columns reordered and scaled by the other modes' scales).
 // With grams_out the Grams of dst (from grams), with xi_src / xi_dst the
 // inverse of Gammabar^(1) (and its ok flag) follow the normalisation too;
-// with ml_src / ml_dst the last mode's M^(N), like M^(1).
+// with ml_src / ml_dst the last mode's M^(N), like M^(1).  dst32
+// (nullable): the padded FP32 copy of dst (f32_layout; padding untouched).
 cp_status normalize_into(cp_ctx* ctx, const Layout& L, const double* src, double* dst,
                          const double* gsrc, double* gdst, double* lambda, const double* grams = nullptr,
                          const double* m0_src = nullptr, double* m0_dst = nullptr, double* grams_out = nullptr,
                          const double* xi_src = nullptr, double* xi_dst = nullptr, const double* ml_src = nullptr,
-                         double* ml_dst = nullptr);
+                         double* ml_dst = nullptr, float* dst32 = nullptr);
 
 // Window-indexed N-GMRES Step II.  win (device) = {start, m}; window row j
 // (oldest first) is ring slot (start + j) % cap.
@@ -323,9 +324,11 @@ cp_status grams_of(cp_ctx* ctx, cudaStream_t s, unsigned* counter, const Layout&
 // doubles, then an int), used instead of forming it.
 // mlast_out (nullable): receives the last mode's M^(N) (I_N x R), formed
 // from the updated modes 1..N-1 and so also M^(N) of the swept point.
+// u32_io (nullable): the padded FP32 copy of u (f32_layout), used instead of
+// making one and kept up to date with the sweep.
 cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t, const Layout& L, double* u, cp_precision prec,
                        double* grams, bool grams_valid, const double* m0 = nullptr, const double* xi0 = nullptr,
-                       double* mlast_out = nullptr);
+                       double* mlast_out = nullptr, float* u32_io = nullptr);
 // Inverse of Gammabar^(n) from grams (N x R x R) on stream s into xi (R*R
 // doubles, then an int ok flag).
 cp_status gram_inverse_launch(cp_ctx* ctx, cudaStream_t s, const double* grams, const Layout& L, int n, double* xi);
@@ -345,7 +348,8 @@ struct MGiven {
 // mg: modes whose M is supplied instead of an MTTKRP pass (MGiven).
 // grams_ls (with d): the Grams of base and d from a line search (ls_poly's
 // grams_out); the Grams of x = base + stp d follow from them without a pass
-// over the factors.
+// over the factors.  x32_in (without d): the padded FP32 copy of base,
+// used instead of making one.
 // grams_in: the Grams of the point when already known (no Gram pass);
 // xi0_out: the inverse of its Gammabar^(1) with the ok flag (as
 // gram_inverse_launch), formed on the aux stream beside the MTTKRPs.
@@ -353,7 +357,7 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const dou
                      const double* d, const double* stp, double* x, double* f, double* g,
                      cp_precision prec, double* gd, double* grams_out = nullptr, double* m0_out = nullptr,
                      const MGiven* mg = nullptr, const double* grams_in = nullptr, double* xi0_out = nullptr,
-                     const double* grams_ls = nullptr);
+                     const double* grams_ls = nullptr, const float* x32_in = nullptr);
 
 // Padded FP32 copy (f32_layout) of the packed FP64 iterate u, on ctx->stream.
 cp_status f32_copy(cp_ctx* ctx, const Layout& L, const double* u, const F32Off& o, int64_t total, float* out);

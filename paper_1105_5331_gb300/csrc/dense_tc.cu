@@ -608,6 +608,11 @@ static cp_status mttkrp_tc_multi(cp_ctx* ctx, cp_tensor* t, const Layout& L, con
     set_error("mixed MTTKRP: %d modes in one launch", nmodes);
     return CP_ERR_ARG;
   }
+  // the factor tables are bulk-copied and read as float4: 16-byte aligned
+  if (((uintptr_t)u32 & 15u) || ((uintptr_t)d32 & 15u)) {
+    set_error("mixed MTTKRP: FP32 factor copies must be 16-byte aligned");
+    return CP_ERR_ARG;
+  }
   for (int k = 0; k < nmodes; ++k) CP_TRY(ensure_planes(ctx, t, modes[k]));
   const int R = L.R;
   const int outc = nvar > 1 ? nvar * o.rs : R;

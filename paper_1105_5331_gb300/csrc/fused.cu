@@ -239,7 +239,7 @@ static cp_status mttkrp_parts_multi(cp_ctx* ctx, cp_tensor* t, const Layout& L, 
 cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const double* base, const double* d,
                      const double* stp, double* x, double* f, double* g, cp_precision prec, double* gd,
                      double* grams_out, double* m0_out, const MGiven* mg, const double* grams_in,
-                     double* xi0_out, const double* grams_ls) {
+                     double* xi0_out, const double* grams_ls, const float* x32_in) {
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int R = L.R, N = L.N, RR = R * R;
   const double* u = d ? x : base;
@@ -255,7 +255,9 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   const F32Off o32 = f32_layout(L, &acc32);
   float* x32 = nullptr;
   double* grams = nullptr;
-  if (want_f32) CP_TRY(ws_alloc(ctx, (void**)&x32, sizeof(float) * (size_t)acc32 + 64));
+  const bool own32 = want_f32 && !(x32_in && !d);
+  if (want_f32 && !own32) x32 = const_cast<float*>(x32_in);
+  if (own32) CP_TRY(ws_alloc(ctx, (void**)&x32, sizeof(float) * (size_t)acc32 + 64));
   if (grams_in)
     grams = const_cast<double*>(grams_in);
   else if (grams_out)
@@ -285,11 +287,12 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   }
   if (xi0_out) CP_TRY(gram_inverse_launch(ctx, ctx->aux, grams, L, 0, xi0_out));
   CP_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
-  if (d || x32) {
-    const int64_t total = x32 ? acc32 : L.P();
-    const F32Off o = x32 ? o32 : [&]() { F32Off q{}; q.rs = R; for (int n = 0; n < N; ++n) q.off[n] = L.off[n]; return q; }();
+  if (d || own32) {
+    float* w32 = own32 ? x32 : nullptr;
+    const int64_t total = w32 ? acc32 : L.P();
+    const F32Off o = w32 ? o32 : [&]() { F32Off q{}; q.rs = R; for (int n = 0; n < N; ++n) q.off[n] = L.off[n]; return q; }();
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4 * ctx->num_sms));
-    (void)launch_pdl(xprep_kernel, dim3(blocks), dim3(256), 0, ctx->stream, L, base, d, stp, x, x32, o, total);
+    (void)launch_pdl(xprep_kernel, dim3(blocks), dim3(256), 0, ctx->stream, L, base, d, stp, x, w32, o, total);
     CP_LAUNCH_CHECK();
   }
   FinishParams fp{};
@@ -332,7 +335,7 @@ cp_status fg_eval_ex(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const 
   ws_free(ctx, fp.blk);
   for (int k = 0; k < nm; ++k) ws_free(ctx, const_cast<void*>(fp.parts[modes[k]].p));
   if (!grams_out && !grams_in) ws_free(ctx, grams);
-  if (x32) ws_free(ctx, x32);
+  if (own32) ws_free(ctx, x32);
   return CP_OK;
 }
 

@@ -30,10 +30,12 @@ struct SolveCtl;
 // those of every other mode too; *all_modes (nullable) tells which.
 // grams_out (nullable, 3 x N x R x R): keeps the Grams the polynomial is
 // built from, base^T base, base^T d and d^T d per mode (in that order).
+// base32 / d32 (nullable): padded FP32 copies of base and d (f32_layout),
+// used instead of making them.
 cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* base, const double* d,
                   cp_precision prec, const cp_ls_opts& o, MTState* st, double* poly, SolveCtl* ctl,
                   cudaGraphConditionalHandle h, int use_h, double* mv_out = nullptr, bool* all_modes = nullptr,
-                  double* grams_out = nullptr);
+                  double* grams_out = nullptr, const float* base32 = nullptr, const float* d32_in = nullptr);
 
 
 }  // namespace cpg

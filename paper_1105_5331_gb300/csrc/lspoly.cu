@@ -304,7 +304,8 @@ __global__ void mix_kernel(Layout L, const double* __restrict__ a, const double*
 
 cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const double* base, const double* d,
                   cp_precision prec, const cp_ls_opts& o, MTState* st, double* poly, SolveCtl* ctl,
-                  cudaGraphConditionalHandle h, int use_h, double* mv_out, bool* all_modes, double* grams_out) {
+                  cudaGraphConditionalHandle h, int use_h, double* mv_out, bool* all_modes, double* grams_out,
+                  const float* base32, const float* d32_in) {
   cp_tensor* t = const_cast<cp_tensor*>(t_in);
   const int N = L.N, R = L.R, RR = R * R;
   const int last = N - 1;
@@ -355,12 +356,21 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
   Parts pts[CP_MAX_N];
   int nm = 0;
   float *a32 = nullptr, *d32 = nullptr, *w32 = nullptr;
+  bool own_a32 = false, own_d32 = false;
   double* wv = nullptr;
   if (tc_var) {
-    CP_TRY(ws_alloc(ctx, (void**)&a32, sizeof(float) * (size_t)acc32 + 64));
-    CP_TRY(ws_alloc(ctx, (void**)&d32, sizeof(float) * (size_t)acc32 + 64));
-    CP_TRY(f32_copy(ctx, L, base, o32, acc32, a32));
-    CP_TRY(f32_copy(ctx, L, d, o32, acc32, d32));
+    own_a32 = !base32;
+    own_d32 = !d32_in;
+    a32 = const_cast<float*>(base32);
+    d32 = const_cast<float*>(d32_in);
+    if (own_a32) {
+      CP_TRY(ws_alloc(ctx, (void**)&a32, sizeof(float) * (size_t)acc32 + 64));
+      CP_TRY(f32_copy(ctx, L, base, o32, acc32, a32));
+    }
+    if (own_d32) {
+      CP_TRY(ws_alloc(ctx, (void**)&d32, sizeof(float) * (size_t)acc32 + 64));
+      CP_TRY(f32_copy(ctx, L, d, o32, acc32, d32));
+    }
     // the last mode first, then (all) the others
     int modes[CP_MAX_N];
     modes[nm++] = last;
@@ -431,8 +441,8 @@ cp_status ls_poly(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, const dou
   } else {
     for (int v = 0; v < nvar; ++v) ws_free(ctx, const_cast<void*>(parts[v].p));
   }
-  if (a32) ws_free(ctx, a32);
-  if (d32) ws_free(ctx, d32);
+  if (own_a32) ws_free(ctx, a32);
+  if (own_d32) ws_free(ctx, d32);
   if (w32) ws_free(ctx, w32);
   if (wv) ws_free(ctx, wv);
   ws_free(ctx, work);

@@ -102,9 +102,9 @@ __global__ void ctl_after_head_kernel(SolveCtl* c, const double* scal, cudaGraph
 
 // Up to six copies in one launch (the branches that make ubar the iterate).
 struct CopySeg {
-  const double* src[6];
-  double* dst[6];
-  int64_t n[6];
+  const double* src[8];
+  double* dst[8];
+  int64_t n[8];
   int nseg;
 };
 
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256) uhat_finish_kernel(Layout L, const double
                                                           const double* __restrict__ colsq, int S,
                                                           double* __restrict__ d, double* blk, unsigned* counter,
                                                           SolveCtl* c, double* scal, cudaGraphConditionalHandle restart,
-                                                          int* status) {
+                                                          int* status, float* __restrict__ d32, F32Off o32) {
   CP_PDL_ENTRY();
   __shared__ NormShared sh;
   __shared__ double red8[8];
@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(256) uhat_finish_kernel(Layout L, const double
     const double v = uhat[L.off[n] + i * R + q] * sh.scale[n * R + q];
     const double dv = v - ubar[e];
     d[e] = dv;
+    if (d32) d32[o32.off[n] + i * o32.rs + p] = (float)dv;
     part = fma(gbar[e], dv, part);
   }
   const double bs = block_sum(part, red8);
@@ -403,9 +404,14 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   const int cap = o.w;
   const size_t n0 = (size_t)L.dims[0] * o.R;                                  // M^(1) of u, ubar, x
   const size_t nl = (size_t)L.dims[L.N - 1] * o.R;                           // M^(N) of the swept point, ubar
+  int64_t acc32 = 0;
+  (void)f32_layout(L, &acc32);
+  // doubles per FP32 copy, a multiple of 128 bytes: the copies start 128-byte
+  // aligned (the tensor-core kernel bulk-copies and vector-loads them)
+  const size_t n32 = ((size_t)acc32 + 31) / 32 * 16;
   const size_t nmv = ((size_t)1 << (L.N - 1)) * (size_t)P;                   // line-search variants, every mode
   const size_t bytes = sizeof(double) * (9 * (size_t)P + 2 * (size_t)cap * P + (size_t)Imax * o.R +
-                                         (size_t)L.N * RR + 16 + 40 + 3 * n0 + 2 * nl + nmv + 5 * (size_t)L.N * RR +
+                                         (size_t)L.N * RR + 16 + 40 + 3 * n0 + 2 * nl + nmv + 5 * (size_t)L.N * RR + 3 * n32 + 16 +
                                          3 * (RR + 2)) +
                        sizeof(MTState) + sizeof(SolveCtl) + 512;
   CP_CUDA(cudaMallocAsync(&base, bytes, sub.stream));
@@ -431,6 +437,12 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   m.Ml = p; p += nl;
   m.Mlbar = p; p += nl;
   m.Gls = p; p += 3 * (size_t)L.N * RR;
+  // padded FP32 copies of u, ubar and d for the tensor-core MTTKRPs (the
+  // padding columns stay zero)
+  p = (double*)(((uintptr_t)p + 127) & ~(uintptr_t)127);
+  m.u32 = (float*)p; p += n32;
+  m.ubar32 = (float*)p; p += n32;
+  m.d32 = (float*)p; p += n32;
   m.Mv = p; p += nmv;
   m.Gu = p; p += (size_t)L.N * RR;
   m.Gbar = p; p += (size_t)L.N * RR;
@@ -443,6 +455,7 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   q = (q + sizeof(MTState) + 63) & ~(uintptr_t)63;
   m.ctl = (SolveCtl*)q;
   CP_CUDA(cudaMemsetAsync(m.ctl, 0, sizeof(SolveCtl), sub.stream));
+  CP_CUDA(cudaMemsetAsync(m.u32, 0, 3 * n32 * sizeof(double), sub.stream));
   if (o.prec != CP_FP64) CP_TRY(prepare_mixed(&sub, t));
   return CP_OK;
 }
@@ -453,6 +466,10 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
   cp_ctx* ctx = &sub;
   cudaStream_t s0 = sub.stream;
   const bool mixed = pr != CP_FP64 && o.polish;
+  // the tensor-core MTTKRPs read FP32 copies of u, ubar and d, kept beside them
+  const bool want32 = pr == CP_MIXED_BF16X3 && t->kind == 0;
+  int64_t acc32 = 0;
+  const F32Off o32 = f32_layout(L, &acc32);
   const double tol = mixed ? o.tol * (o.mixed_tol_factor > 0 ? o.mixed_tol_factor : 1.0) : o.tol;
   const int maxit = o.maxit;
   const int stall = 50;
@@ -505,6 +522,12 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
   ubar_state.src[5] = m.Xi0bar;
   ubar_state.dst[5] = m.Xi0;
   ubar_state.n[5] = (int64_t)L.R * L.R + 2;
+  if (want32) {
+    ubar_state.nseg = 7;
+    ubar_state.src[6] = (const double*)m.ubar32;
+    ubar_state.dst[6] = (double*)m.u32;
+    ubar_state.n[6] = (acc32 + 1) / 2;
+  }
   const unsigned vec_blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 2 * (int64_t)sub.num_sms));
   auto tail = [&](cudaStream_t st, cudaGraphConditionalHandle h, int begin) -> cp_status {
     double* blk = nullptr;
@@ -521,8 +544,9 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
     CP_TRY(new_handle(s0, 0, &h_outer));
     CP_TRY(counted(&kcount.top, [&]() -> cp_status {
       if (first) CP_TRY(normalize_into(ctx, L, m.work, m.u, nullptr, nullptr, nullptr));
+      if (want32) CP_TRY(f32_copy(ctx, L, m.u, o32, acc32, m.u32));
       CP_TRY(fg_eval_ex(ctx, t, L, m.u, nullptr, nullptr, nullptr, m.scal + F, m.g, pr, nullptr, m.Gu, m.M0,
-                        nullptr, nullptr, m.Xi0));
+                        nullptr, nullptr, m.Xi0, nullptr, want32 ? m.u32 : nullptr));
       // window <- {(u, g)}, ||g||^2, the stopping test
       return tail(s0, h_outer, 1);
     }));
@@ -536,13 +560,13 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
           // point u was made from
           // (the sweep's last MTTKRP is M^(N) of the swept point: it follows
           // the normalisation and stands in for that mode's pass at ubar)
-          CP_TRY(als_sweep_v2(ctx, t, L, m.u, pr, m.Gu, true, m.M0, m.Xi0, m.Ml));
+          CP_TRY(als_sweep_v2(ctx, t, L, m.u, pr, m.Gu, true, m.M0, m.Xi0, m.Ml, want32 ? m.u32 : nullptr));
           CP_TRY(normalize_into(ctx, L, m.u, m.ubar, nullptr, nullptr, nullptr, m.Gu, nullptr, nullptr, m.Gbar,
-                                nullptr, nullptr, m.Ml, m.Mlbar));
+                                nullptr, nullptr, m.Ml, m.Mlbar, want32 ? m.ubar32 : nullptr));
           MGiven mg_bar;
           mg_bar.m[L.N - 1] = m.Mlbar;
           CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, nullptr, nullptr, nullptr, m.scal + FBAR, m.gbar, pr, nullptr,
-                            nullptr, m.M0bar, &mg_bar, m.Gbar, m.Xi0bar));
+                            nullptr, m.M0bar, &mg_bar, m.Gbar, m.Xi0bar, nullptr, want32 ? m.ubar32 : nullptr));
           // Step II, then normalise uhat, d = uhat - ubar, slope, restart test
           double* colsq = nullptr;
           double* blk = nullptr;
@@ -552,7 +576,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
           CP_TRY(ngmres_core(ctx, P, m.win, cap, m.U, m.G, m.ubar, m.gbar, o.eps, m.work, nullptr, &L, colsq, &S));
           (void)launch_pdl(uhat_finish_kernel, dim3(vec_blocks), dim3(256), 0, side[0], L, m.work, m.ubar, m.gbar, colsq, S, m.d, blk,
                                                               ctx->d_counter, m.ctl, m.scal, h_restart,
-                                                              ctx->d_status);
+                                                              ctx->d_status, want32 ? m.d32 : nullptr, o32);
           CP_LAUNCH_CHECK();
           ws_free(ctx, blk);
           ws_free(ctx, colsq);
@@ -570,7 +594,8 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
             CP_TRY(new_handle(side[1], 0, &h_acc));
             bool ls_all = false;
             CP_TRY(counted(&kcount.ls_fixed, [&]() -> cp_status {
-              return ls_poly(ctx, t, L, m.ubar, m.d, pr, lso, m.st, m.poly, m.ctl, h_acc, 1, m.Mv, &ls_all, m.Gls);
+              return ls_poly(ctx, t, L, m.ubar, m.d, pr, lso, m.st, m.poly, m.ctl, h_acc, 1, m.Mv, &ls_all, m.Gls,
+                             want32 ? m.ubar32 : nullptr, want32 ? m.d32 : nullptr);
             }));
             return add_conditional(side[1], side[2], h_acc, cudaGraphCondTypeIf, 2, [&](int ab) -> cp_status {
               return with_stream(side[2], [&]() -> cp_status {
@@ -585,7 +610,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
                     CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, m.d, &m.st->stp_eval, m.x, m.scal + FX, m.gx, pr,
                                       nullptr, m.grams, m.M0x, &mg_x, nullptr, m.Xi0x, m.Gls));
                     CP_TRY(normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr, m.grams, m.M0x, m.M0, m.Gu,
-                                          m.Xi0x, m.Xi0));
+                                          m.Xi0x, m.Xi0, nullptr, nullptr, want32 ? m.u32 : nullptr));
                     return dcopy(ctx, 1, m.scal + FX, m.scal + F);
                   }
                   return dcopy_multi(ctx, ubar_state);

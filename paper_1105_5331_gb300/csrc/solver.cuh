@@ -34,6 +34,7 @@ struct SolverMem {
   // the line search's Grams (ubar^T ubar, ubar^T d, d^T d per mode), from
   // which those of the accepted point follow
   double* Gls;
+  float *u32, *ubar32, *d32;
   // Grams of u and ubar (N x R x R); inverses of Gammabar^(1) of u, ubar and
   // x with their ok flags (R*R + 2 doubles each)
   double *Gu, *Gbar, *Xi0, *Xi0bar, *Xi0x;
