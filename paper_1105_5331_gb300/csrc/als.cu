@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "cp_internal.cuh"
+#include "newton.cuh"
 #include "reduce.cuh"
 
 namespace cpg {
@@ -135,19 +136,6 @@ __global__ void __launch_bounds__(256) gram_kernel(const GramParams p) {
   if (threadIdx.x == 0) *p.counter = 0u;
 }
 
-// 1/d by Newton's iteration r <- r (2 - d r) from an FP32 reciprocal, two
-// steps (each doubles the correct bits: ~23 -> 46 -> full precision); the
-// FP64 divide is used outside the FP32 exponent range.
-__device__ __forceinline__ double recip_newton(double d) {
-  const double ad = fabs(d);
-  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
-  double r = (double)__frcp_rn((float)d);
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
-}
-
 struct InvParams {
   const double* grams;   // N x R*R
   int N, R, n;
@@ -168,7 +156,7 @@ __device__ bool gj_inverse2(double* A, double* B, int R, double** out, double* p
   if (threadIdx.x == 0) {
     const double d = A[0];
     if (!(d > 0.0) || !isfinite(d)) *flag = 1;
-    else piv2[0] = recip_newton(d);
+    else piv2[0] = recip_nr(d);
   }
   __syncthreads();
   double* src = A;
@@ -200,7 +188,7 @@ __device__ bool gj_inverse2(double* A, double* B, int R, double** out, double* p
       dst[j * R + i] = v;
       if (i == k + 1 && j == k + 1) {
         if (!(v > 0.0) || !isfinite(v)) *flag = 1;
-        else piv2[(k + 1) & 1] = recip_newton(v);
+        else piv2[(k + 1) & 1] = recip_nr(v);
       }
     }
     __syncthreads();

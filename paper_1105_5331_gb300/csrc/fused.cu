@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) fg_finish_kernel(const FinishParams p) {
   CP_PDL_ENTRY();
   __shared__ double Gb[CP_MAX_R * CP_MAX_R];
   __shared__ double sh[8][33];
-  __shared__ double tr[2][256];
+  __shared__ double tr[3][8];
   __shared__ bool is_last;
   const int R = p.L.R, N = p.L.N, RR = R * R;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -155,9 +155,17 @@ __global__ void __launch_bounds__(256) fg_finish_kernel(const FinishParams p) {
       const int64_t i = e / R;
       const int r = (int)(e - i * R);
       const double* A = p.u + off + i * R;
-      double v = 0.0;
-      for (int t = 0; t < R; ++t) v = fma(A[t], Gb[t * R + r], v);
-      const double gval = v - mval;
+      // (A Gammabar)[i][r] in four interleaved chains (FP64 FMA latency)
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      int t = 0;
+      for (; t + 3 < R; t += 4) {
+        v0 = fma(A[t], Gb[t * R + r], v0);
+        v1 = fma(A[t + 1], Gb[(t + 1) * R + r], v1);
+        v2 = fma(A[t + 2], Gb[(t + 2) * R + r], v2);
+        v3 = fma(A[t + 3], Gb[(t + 3) * R + r], v3);
+      }
+      for (; t < R; ++t) v0 = fma(A[t], Gb[t * R + r], v0);
+      const double gval = ((v0 + v1) + (v2 + v3)) - mval;
       if (p.g) p.g[off + e] = gval;
       if (n == N - 1) inner = p.u[off + e] * mval;
       if (p.d) gdv = gval * p.d[off + e];
@@ -183,26 +191,28 @@ __global__ void __launch_bounds__(256) fg_finish_kernel(const FinishParams p) {
     for (int m = 0; m < N; ++m) v *= p.grams[(int64_t)m * RR + k];
     gs += v;
   }
-  tr[0][threadIdx.x] = a;
-  tr[1][threadIdx.x] = b;
-  __syncthreads();
-  for (int st = 128; st > 0; st >>= 1) {
-    if ((int)threadIdx.x < st) {
-      tr[0][threadIdx.x] += tr[0][threadIdx.x + st];
-      tr[1][threadIdx.x] += tr[1][threadIdx.x + st];
-    }
-    __syncthreads();
+  // the three sums: warp shuffles, then the eight warp sums in order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    gs += __shfl_xor_sync(0xffffffffu, gs, o);
   }
-  const double inner_sum = tr[0][0], gd_sum = tr[1][0];
-  __syncthreads();
-  tr[0][threadIdx.x] = gs;
-  __syncthreads();
-  for (int st = 128; st > 0; st >>= 1) {
-    if ((int)threadIdx.x < st) tr[0][threadIdx.x] += tr[0][threadIdx.x + st];
-    __syncthreads();
+  if (lane == 0) {
+    tr[0][w] = a;
+    tr[1][w] = b;
+    tr[2][w] = gs;
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const double fv = 0.5 * (p.norm2 - 2.0 * inner_sum + tr[0][0]);
+    double inner_sum = 0.0, gd_sum = 0.0, gsum = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      inner_sum += tr[0][q];
+      gd_sum += tr[1][q];
+      gsum += tr[2][q];
+    }
+    const double fv = 0.5 * (p.norm2 - 2.0 * inner_sum + gsum);
     *p.f = fv;
     if (!isfinite(fv)) record_status(p.status, CP_ERR_NONFINITE);
     if (p.d && p.gd) *p.gd = gd_sum;

@@ -9,9 +9,14 @@
 //    interpolation, the interval update rules, extrapolation into
 //    [a_t + 1.1 (a_t - a_l), a_t + 4 (a_t - a_l)] while unbracketed, and
 //    bisection when a bracketed interval fails to shrink by 0.66 in two trials.
+//
+// The quotients and the square root of the interpolation formulas use the
+// Newton-refined FP64 operations (div_nr, sqrt_nr): the search runs in one
+// thread, where each IEEE divide or sqrt is a ~650-cycle serial chain.
 #pragma once
 
 #include "linesearch.cuh"
+#include "newton.cuh"
 
 namespace cpg {
 namespace mtdev {
@@ -21,13 +26,13 @@ struct Pt {
 
 // Local minimiser of the cubic with values/derivatives (a, fa, da), (b, fb, db).
 __device__ inline bool cubic_min(double a, double fa, double da, double b, double fb, double db, double* x) {
-  const double d1 = da + db - 3.0 * (fa - fb) / (a - b);
+  const double d1 = da + db - div_nr(3.0 * (fa - fb), a - b);
   const double disc = d1 * d1 - da * db;
   if (!(disc >= 0.0)) return false;
-  const double d2 = copysign(sqrt(disc), b - a);
+  const double d2 = copysign(sqrt_nr(disc), b - a);
   const double den = db - da + 2.0 * d2;
   if (den == 0.0) return false;
-  *x = b - (b - a) * (db + d2 - d1) / den;
+  *x = b - div_nr((b - a) * (db + d2 - d1), den);
   return true;
 }
 
@@ -36,14 +41,14 @@ __device__ inline bool quad_min(double a, double fa, double da, double b, double
   const double h = b - a;
   const double den = 2.0 * (fb - fa - da * h);
   if (den == 0.0) return false;
-  *x = a - da * h * h / den;
+  *x = a - div_nr(da * h * h, den);
   return true;
 }
 
 // Minimiser of the quadratic matching derivatives da at a and db at b.
 __device__ inline bool secant_min(double a, double da, double b, double db, double* x) {
   if (db == da) return false;
-  *x = b - db * (b - a) / (db - da);
+  *x = b - div_nr(db * (b - a), db - da);
   return true;
 }
 

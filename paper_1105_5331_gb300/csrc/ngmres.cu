@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "cp_internal.cuh"
+#include "newton.cuh"
 #include "reduce.cuh"
 
 namespace cpg {
@@ -87,18 +88,6 @@ __global__ void ngmres_dots_kernel(const double* __restrict__ G, const int* __re
     const int o = threadIdx.x + q * blockDim.x;
     if (o < nout) part[(int64_t)blockIdx.x * nout_max + o] = acc[q];
   }
-}
-
-// 1/d by Newton's iteration from an FP32 reciprocal (FP64 divide outside
-// the FP32 exponent range).
-__device__ __forceinline__ double recip_nr(double d) {
-  const double ad = fabs(d);
-  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
-  double r = (double)__frcp_rn((float)d);
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
 }
 
 // Block b adds the per-CTA partial sums of outputs 32b .. 32b+31 (warp w

@@ -3,9 +3,16 @@
 // scale = lambda^(1/N) / nu, order = stable sort by decreasing lambda.  The
 // column sums of squares come from the Gram diagonals (grams) or from
 // per-chunk partial sums part[n][S][R].
+//
+// FP64 divides, square roots and pow are slow, serial chains on this GPU
+// (pow about 5800 cycles, a divide or sqrt about 650), and every block waits
+// for this prologue.  So y = 1/nu comes from Newton's iteration for
+// 1/sqrt(s) (rsqrt_nr), nu = s y, scale = lambda^(1/N) y, and lambda^(1/N)
+// is cbrt / sqrt for N = 3, 2, 4 (pow otherwise).
 #pragma once
 
 #include "cp_internal.cuh"
+#include "newton.cuh"
 #include "reduce.cuh"
 
 namespace cpg {
@@ -30,7 +37,9 @@ __device__ inline void norm_prologue(const Layout& L, const double* __restrict__
     } else {
       s = strided_sum(part + (int64_t)n * S * R + r, 0, S, 1, (int64_t)R);
     }
-    sh.nu[t] = sqrt(s);
+    const double y = s > 0.0 ? rsqrt_nr(s) : 0.0;
+    sh.nu[t] = s * y;
+    sh.scale[t] = y;   // 1 / nu for now
   }
   __syncthreads();
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
@@ -41,8 +50,8 @@ __device__ inline void norm_prologue(const Layout& L, const double* __restrict__
       if (sh.nu[n * R + r] == 0.0) zero = true;
     }
     if (zero) l = 0.0;
-    const double root = pow(l, 1.0 / N);
-    for (int n = 0; n < N; ++n) sh.scale[n * R + r] = zero ? 1.0 : root / sh.nu[n * R + r];
+    const double root = N == 3 ? cbrt(l) : N == 2 ? sqrt(l) : N == 4 ? sqrt(sqrt(l)) : pow(l, 1.0 / N);
+    for (int n = 0; n < N; ++n) sh.scale[n * R + r] = zero ? 1.0 : root * sh.scale[n * R + r];
     sh.lam[r] = l;
     sh.key[r] = isnan(l) ? -INFINITY : l;
     if (!isfinite(l) && blockIdx.x == 0) record_status(status, CP_ERR_NONFINITE);
