@@ -46,6 +46,14 @@ constexpr uint32_t kTileBytes = kBM * kBK * 2;   // one plane, one M tile: 16 KB
 constexpr int kMaxTilesPerCta = 1;       // M tiles handled by one CTA
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
 constexpr int kMaxDynSmem = 227 * 1024;
+// Accumulators per row tile: the MMAs of contraction tile i go into TMEM
+// accumulator i % nacc, and the epilogue adds the nacc of them in FP32
+// registers (round-to-nearest).  The tensor-core FP32 accumulation loses
+// accuracy in proportion to the number of products added into one
+// accumulator: measured as ||g_mixed - g_FP64|| / P at a converged 256^3
+// R=16 point, the gradient error grew about linearly with a CTA's tiles
+// (1.1e-8 at 7, 2.4e-8 at 14, 7.5e-8 at 43 tiles, one accumulator).
+constexpr int kMaxAcc = 4;
 
 // One MTTKRP of a launch (a launch may run the MTTKRPs of several modes:
 // CTAs cta0 .. cta0 + gx * mgroups - 1 are this job's, gx contraction
@@ -83,6 +91,7 @@ struct TcParams {
   int rs;                            // table row stride in floats (R rounded up to 4)
   int* status;
   uint32_t ncols;             // TMEM columns allocated
+  int nacc;                   // accumulators per row tile (1 .. kMaxAcc)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -181,6 +190,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
+}
+
+// 16 columns of this warp's 32 TMEM lanes, without waiting for them
+// (tcgen05.wait::ld before the registers are read).
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
@@ -302,13 +322,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t bhi = st + 2u * (uint32_t)p.ntm * kTileBytes;
         const uint32_t blo = bhi + b_bytes;
         for (int mt = 0; mt < p.ntm; ++mt) {
-          const uint32_t d = tmem + (uint32_t)(mt * p.RP);
+          // accumulator i % nacc of row tile mt; its first tile starts it
+          const int a = i % p.nacc;
+          const uint32_t d = tmem + (uint32_t)((a * p.ntm + mt) * p.RP);
           const uint32_t ahi = st + (uint32_t)mt * kTileBytes;
           const uint32_t alo = st + (uint32_t)(p.ntm + mt) * kTileBytes;
 #pragma unroll
           for (int j = 0; j < kBK / 16; ++j) {
             const uint32_t off = (uint32_t)j * 32u;
-            mma_bf16(d, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, (i > 0 || j > 0) ? 1u : 0u);
+            mma_bf16(d, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, (i >= p.nacc || j > 0) ? 1u : 0u);
             mma_bf16(d, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
             mma_bf16(d, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, 1u);
           }
@@ -453,13 +475,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int mt = 0; mt < p.ntm; ++mt) {
       const int64_t row = row0 + mt * kBM + rin;
       for (int c = 0; c < p.RP; c += 16) {
-        uint32_t v[16];
-        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * p.RP + c), v);
-        if (done && row < J.I) {
+        // the accumulators that received tiles (all of them unless nk < nacc):
+        // their loads issued together, one wait
+        const int na = min(p.nacc, nk);
+        const uint32_t lane_col = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * p.RP + c);
+        const uint32_t astep = (uint32_t)(p.ntm * p.RP);
+        uint32_t v[kMaxAcc][16];
+#pragma unroll
+        for (int a = 0; a < kMaxAcc; ++a)
+          if (a < na) tmem_ld16_async(lane_col + (uint32_t)a * astep, v[a]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float sum[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          float s = 0.f;
+#pragma unroll
+          for (int a = 0; a < kMaxAcc; ++a)
+            if (a < na) s = a == 0 ? __uint_as_float(v[a][e]) : s + __uint_as_float(v[a][e]);
+          sum[e] = s;
+        }
+        if (done && row < J.I && nk > 0) {
           float* out = J.partial + ((int64_t)kslice * J.I + row) * p.outc;
 #pragma unroll
           for (int e = 0; e < 16; ++e)
-            if (c + e < p.outc) out[c + e] = __uint_as_float(v[e]);
+            if (c + e < p.outc) out[c + e] = sum[e];
         }
       }
     }
@@ -677,8 +716,11 @@ static cp_status mttkrp_tc_multi(cp_ctx* ctx, cp_tensor* t, const Layout& L, con
     set_error("mixed MTTKRP: rank %d too large for the shared-memory pipeline", R);
     return CP_ERR_UNSUPPORTED;
   }
+  // as many accumulators (up to kMaxAcc) as the 512 TMEM columns hold
+  p.nacc = 1;
+  while (p.nacc < kMaxAcc && 2 * p.nacc * p.ntm * RP <= 512) p.nacc *= 2;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(p.ntm * RP)) cols <<= 1;
+  while (cols < (uint32_t)(p.nacc * p.ntm * RP)) cols <<= 1;
   p.ncols = cols;
   // contraction slices per row group: the job's share of the SMs
   int cta = 0;

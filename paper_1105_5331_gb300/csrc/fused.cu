@@ -236,10 +236,10 @@ cp_status mttkrp_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double*
 }
 
 // The MTTKRPs of several modes, one launch per mode.  (One tensor-core
-// launch for all of them streams T faster, but then each CTA accumulates a
-// longer contraction range in FP32 tensor memory, and the error of the
-// gradient grows with that length: about 2e-8 x P at 14 tiles of 64 per CTA,
-// 8e-8 x P at 43, which is close to the stopping tolerance of the solver.)
+// launch shared among the modes streams T faster when timed alone, but in
+// the solve's stream of launches the next MTTKRP's CTAs already start on each
+// SM as the previous one's finish, programmatic dependent launch overlapping
+// their start-up, and the shared launch measured slower per iteration.)
 static cp_status mttkrp_parts_multi(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, const float* u32,
                                     const F32Off& o32, const int* modes, int nmodes, cp_precision prec, Parts* out) {
   for (int k = 0; k < nmodes; ++k) CP_TRY(mttkrp_parts(ctx, t, L, u, u32, o32, modes[k], prec, &out[k]));
