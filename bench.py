@@ -318,7 +318,7 @@ def run_ours(args, rank, world, local_rank):
 # DRAM bytes (read + write) per launch of mttkrp_tc_kernel, mode 0 of the
 # 256^3 R=16 workload, from one ncu --set full capture of the current kernel
 # (profiles/mttkrp_tc_dense256.md: 67.173888 MB read + 0.314880 MB written).
-TC_NCU_TRAFFIC = 67620096
+TC_NCU_TRAFFIC = 67571968
 
 
 def mttkrp_roofline(cp, ctx, t, u, stream, flush, prec):
