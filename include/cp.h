@@ -132,6 +132,23 @@ void cp_tensor_destroy(cp_tensor* t);
 cp_status cp_mttkrp(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, int mode,
                     double* out, cp_precision prec);
 
+/* Khatri-Rao variant MTTKRPs along a line x = u + beta d (Section 2.1, Eq.
+ * linesearch; the CP model is multilinear in the factors): for each listed
+ * mode n and each v in [0, 2^(N-1)), M_v^(n) = T_(n) times the Khatri-Rao
+ * product of the other modes' factors, in which the j-th other mode (the
+ * modes other than n in increasing order, j from 0) contributes d's factor
+ * when bit j of v is set and u's otherwise.  Then
+ * M^(n)(u + beta d) = sum_v beta^popcount(v) M_v^(n) for every beta.
+ * u, d: iterate and direction (P doubles each, device); modes: HOST array of
+ * nmodes distinct modes (1 <= nmodes <= N); out (device): for each listed
+ * mode in the order given, 2^(N-1) blocks (v = 0, 1, ...) of I_mode x R
+ * doubles, row-major.  CP_MIXED_BF16X3 on a dense tensor with
+ * 2^(N-1) * (R rounded up to 4) <= 256 runs one tensor-core launch for all
+ * listed modes (the line search's pass); otherwise one MTTKRP per variant.
+ * Asynchronous. */
+cp_status cp_mttkrp_variants(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, const double* d,
+                             const int* modes, int nmodes, double* out, cp_precision prec);
+
 /* FP64 dense MTTKRP that allocates no device memory (no counterpart in the
  * paper; it exists for callers that cannot allocate while they run: code that
  * enqueues work inside a stream capture it does not own, serving loops with a

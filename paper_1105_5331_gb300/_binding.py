@@ -31,7 +31,7 @@ EXPORTED = [
     "cp_ctx_create", "cp_ctx_destroy", "cp_last_error", "cp_ctx_sync", "cp_ctx_stream",
     "cp_kernel_launches", "cp_ctx_timer_enable", "cp_ctx_timer_read",
     "cp_tensor_dense", "cp_tensor_coo", "cp_tensor_info", "cp_tensor_sorted_mode",
-    "cp_tensor_destroy", "cp_mttkrp", "cp_mttkrp_noalloc", "cp_fg", "cp_als_sweep", "cp_normalize",
+    "cp_tensor_destroy", "cp_mttkrp", "cp_mttkrp_variants", "cp_mttkrp_noalloc", "cp_fg", "cp_als_sweep", "cp_normalize",
     "ngmres_step",
     "cp_ls_opts_default", "linesearch", "cp_solve_opts_default", "cp_solve",
     "cp_solve_batch", "cp_server_create", "cp_server_submit", "cp_server_poll", "cp_server_cancel",
@@ -92,6 +92,7 @@ def _load():
         "cp_tensor_destroy": (None, [VP]),
         "cp_mttkrp": (I, [VP, VP, I, VP, I, VP, I]),
         "cp_mttkrp_noalloc": (I, [VP, VP, I, VP, I, VP]),
+        "cp_mttkrp_variants": (I, [VP, VP, I, VP, VP, P, I, VP, I]),
         "cp_fg": (I, [VP, VP, I, VP, VP, VP, I]),
         "cp_als_sweep": (I, [VP, VP, I, VP, I, I]),
         "cp_normalize": (I, [VP, I, P, I, VP, VP, VP]),
@@ -299,6 +300,15 @@ def cp_tensor_destroy(t):
 
 def cp_mttkrp(ctx, t, R: int, u, mode: int, out, prec: int = CP_FP64):
     _check(_lib.cp_mttkrp(_h(ctx), _h(t), int(R), _ptr(u), int(mode), _ptr(out), int(prec)))
+    return out
+
+
+def cp_mttkrp_variants(ctx, t, R: int, u, d, modes, out, prec: int = CP_FP64):
+    """Khatri-Rao variant MTTKRPs along u + beta d for the listed modes; out
+    holds, per mode in the order given, 2^(N-1) blocks of I_mode x R."""
+    ms = (C.c_int * len(modes))(*[int(m) for m in modes])
+    _check(_lib.cp_mttkrp_variants(_h(ctx), _h(t), int(R), _ptr(u), _ptr(d), ms, len(modes), _ptr(out),
+                                   int(prec)))
     return out
 
 

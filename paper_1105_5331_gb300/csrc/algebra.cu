@@ -180,6 +180,20 @@ __global__ void __launch_bounds__(256) norm_apply_kernel(Layout L, const double*
   }
 }
 
+// w = the iterate whose factor m is d's when m != mode and bit j(m) of v is
+// set (j(m): m's index among the modes other than `mode`), else u's.
+__global__ void mix_for_mode_kernel(Layout L, const double* __restrict__ u, const double* __restrict__ d, int mode,
+                                    int v, double* __restrict__ w) {
+  CP_PDL_ENTRY();
+  const int64_t P = L.off[L.N];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
+    int n = 0;
+    while (n + 1 < L.N && e >= L.off[n + 1]) ++n;
+    const int j = n < mode ? n : n - 1;
+    w[e] = (n != mode && ((v >> j) & 1)) ? d[e] : u[e];
+  }
+}
+
 inline int grid_for(cp_ctx* ctx, int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   b = std::min<int64_t>(b, 8 * (int64_t)ctx->num_sms);
@@ -254,6 +268,29 @@ cp_status mttkrp_any(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const dou
   if (prec == CP_MIXED_BF16X3)
     return mttkrp_dense_mixed(ctx, const_cast<cp_tensor*>(t), L, u, mode, out);
   return mttkrp_dense_f64(ctx, t, L, u, mode, out);
+}
+
+cp_status mttkrp_variants_any(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, const double* d,
+                              const int* modes, int nmodes, double* out, cp_precision prec) {
+  if (t->kind == 0 && prec == CP_MIXED_BF16X3 && tc_variants_supported(L))
+    return mttkrp_dense_mixed_variants(ctx, const_cast<cp_tensor*>(t), L, u, d, modes, nmodes, out);
+  // one MTTKRP per variant, of the mixed iterate
+  const int nvar = 1 << (L.N - 1);
+  double* w = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&w, sizeof(double) * (size_t)L.P()));
+  size_t off = 0;
+  for (int k = 0; k < nmodes; ++k) {
+    const int mode = modes[k];
+    for (int v = 0; v < nvar; ++v) {
+      (void)launch_pdl(mix_for_mode_kernel, dim3(grid_for(ctx, L.P(), 256)), dim3(256), 0, ctx->stream, L, u, d,
+                       mode, v, w);
+      CP_LAUNCH_CHECK();
+      CP_TRY(mttkrp_any(ctx, t, L, w, mode, out + off, prec));
+      off += (size_t)L.dims[mode] * L.R;
+    }
+  }
+  ws_free(ctx, w);
+  return CP_OK;
 }
 
 cp_status fg_eval(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, double* f,

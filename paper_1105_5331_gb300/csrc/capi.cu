@@ -425,6 +425,39 @@ cp_status cp_mttkrp(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, int
   return mttkrp_any(ctx, t, L, u, mode, out, prec);
 }
 
+cp_status cp_mttkrp_variants(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, const double* d,
+                             const int* modes, int nmodes, double* out, cp_precision prec) {
+  CP_NULLCHECK(ctx);
+  CP_TRY(check_tensor_R(t, R));
+  CP_NULLCHECK(u);
+  CP_NULLCHECK(d);
+  CP_NULLCHECK(modes);
+  CP_NULLCHECK(out);
+  if (nmodes < 1 || nmodes > t->N) {
+    set_error("cp_mttkrp_variants: nmodes = %d outside [1, %d]", nmodes, t->N);
+    return CP_ERR_ARG;
+  }
+  for (int k = 0; k < nmodes; ++k) {
+    if (modes[k] < 0 || modes[k] >= t->N) {
+      set_error("cp_mttkrp_variants: mode %d outside [0, %d)", modes[k], t->N);
+      return CP_ERR_ARG;
+    }
+    for (int q = 0; q < k; ++q)
+      if (modes[q] == modes[k]) {
+        set_error("cp_mttkrp_variants: mode %d listed twice", modes[k]);
+        return CP_ERR_ARG;
+      }
+  }
+  if (prec != CP_FP64 && prec != CP_MIXED_BF16X3) {
+    set_error("unknown precision %d", (int)prec);
+    return CP_ERR_ARG;
+  }
+  CP_TRY(use_device(ctx));
+  Layout L;
+  L.set(t->N, t->dims, R);
+  return mttkrp_variants_any(ctx, t, L, u, d, modes, nmodes, out, prec);
+}
+
 cp_status cp_fg(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, double* f, double* g,
                 cp_precision prec) {
   CP_NULLCHECK(ctx);

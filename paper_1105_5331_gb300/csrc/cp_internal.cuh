@@ -250,6 +250,15 @@ cp_status coo_build(cp_ctx* ctx, cp_tensor* t, const int64_t* d_coords, const fl
 
 cp_status mttkrp_any(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, int mode,
                      double* out, cp_precision prec);
+// Khatri-Rao variant MTTKRPs of the listed modes along u + beta d (the
+// semantics and out layout of cp_mttkrp_variants).
+cp_status mttkrp_variants_any(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const double* u, const double* d,
+                              const int* modes, int nmodes, double* out, cp_precision prec);
+cp_status mttkrp_dense_mixed_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, const double* d,
+                                      const int* modes, int nmodes, double* out);
+cp_status mttkrp_tc_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* a32, const float* d32,
+                             const F32Off& o, const int* modes, int nmodes, Parts* out);
+bool tc_variants_supported(const Layout& L);
 
 // Normalise src (and gsrc) into dst (and gdst); lambda (R) optional.  With
 // grams (N x R x R, the Grams of src) the column norms come from their

@@ -512,6 +512,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Variant MTTKRPs from the tensor-core partial sums: out[v][i][r] is the
+// FP32 sum, over the CTAs in index order, of column v rs + r of row i.
+__global__ void variant_sum_kernel(const float* __restrict__ part, int count, int64_t I, int outc, int rs, int R,
+                                   int nvar, double* __restrict__ out) {
+  CP_PDL_ENTRY();
+  const int64_t n = (int64_t)nvar * I * R;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = e / (I * R);
+    const int64_t rem = e - v * I * R;
+    const int64_t i = rem / R;
+    const int r = (int)(rem - i * R);
+    out[e] = (double)strided_sum(part + i * outc + v * rs + r, 0, count, 1, I * (int64_t)outc);
+  }
+}
+
 // Pre-tiled planes: one thread per (column tile kt, row i, 16-byte chunk c)
 // writes eight hi and eight lo values, hi = bf16(x), lo = bf16(x - hi),
 // zero past Kbar.  Tile (kt, m) starts at kt (2 I 128) + m (2 128 128)
@@ -796,6 +811,37 @@ cp_status mttkrp_dense_mixed_modes(cp_ctx* ctx, cp_tensor* t, const Layout& L, c
   CP_TRY(factors_f32(ctx, L, u, &u32, &o));
   for (int n = first; n < L.N; ++n) CP_TRY(mttkrp_tc_core(ctx, t, L, u32, o, n, M_all + L.off[n]));
   ws_free(ctx, u32);
+  return CP_OK;
+}
+
+// The Khatri-Rao variant MTTKRPs of the listed modes in one tensor-core
+// launch (see cp_mttkrp_variants); out holds, per mode, nvar blocks of
+// I_mode x R doubles.
+cp_status mttkrp_dense_mixed_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, const double* d,
+                                      const int* modes, int nmodes, double* out) {
+  int64_t acc32 = 0;
+  const F32Off o = f32_layout(L, &acc32);
+  float *a32 = nullptr, *d32 = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&a32, sizeof(float) * (size_t)acc32 + 64));
+  CP_TRY(ws_alloc(ctx, (void**)&d32, sizeof(float) * (size_t)acc32 + 64));
+  CP_TRY(f32_copy(ctx, L, u, o, acc32, a32));
+  CP_TRY(f32_copy(ctx, L, d, o, acc32, d32));
+  Parts pts[CP_MAX_N];
+  CP_TRY(mttkrp_tc_variants(ctx, t, L, a32, d32, o, modes, nmodes, pts));
+  const int nvar = 1 << (L.N - 1);
+  size_t off = 0;
+  for (int k = 0; k < nmodes; ++k) {
+    const int64_t I = L.dims[modes[k]];
+    const int64_t n = (int64_t)nvar * I * L.R;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * ctx->num_sms));
+    (void)launch_pdl(variant_sum_kernel, dim3(blocks), dim3(256), 0, ctx->stream, (const float*)pts[k].p,
+                     pts[k].count, I, nvar * o.rs, o.rs, L.R, nvar, out + off);
+    CP_LAUNCH_CHECK();
+    off += (size_t)n;
+  }
+  for (int k = 0; k < nmodes; ++k) ws_free(ctx, const_cast<void*>(pts[k].p));
+  ws_free(ctx, d32);
+  ws_free(ctx, a32);
   return CP_OK;
 }
 

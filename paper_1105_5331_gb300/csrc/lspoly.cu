@@ -26,9 +26,6 @@
 
 namespace cpg {
 
-cp_status mttkrp_tc_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* a32, const float* d32,
-                             const F32Off& o, const int* modes, int nmodes, Parts* out);
-bool tc_variants_supported(const Layout& L);
 
 namespace {
 

@@ -112,3 +112,75 @@ def test_full_size_dense_256_mixed_mttkrp(cp, ctx):
         cp.cp_ctx_sync(ctx)
         ref = O.mttkrp_dense(prob.T, F, n)
         assert rel(out.cpu().numpy().reshape(ref.shape), ref) <= MIXED_TOL
+
+
+# Khatri-Rao variant MTTKRPs (the line search's pass): shapes where every
+# listed mode goes into one tensor-core launch, a 4-way tensor with 8 variants
+# of rank 32 (256 columns), rank 60 (4 x 60 = 240 columns), and a 4-way rank
+# too wide for one launch (8 x 40 > 256: one MTTKRP per variant), in FP64 and
+# mixed precision.
+VARIANT_CASES = [
+    ((20, 20, 20), 3, np.float64, "fp64"),
+    ((20, 20, 20), 3, np.float64, "mixed"),
+    ((130, 33, 17), 16, np.float32, "mixed"),
+    ((24, 12, 10, 6), 5, np.float32, "mixed"),
+    ((24, 12, 10, 6), 5, np.float32, "fp64"),
+    ((40, 30, 20, 9), 32, np.float32, "mixed"),
+    ((9, 8, 7), 60, np.float32, "mixed"),
+    ((12, 10, 8, 6), 40, np.float32, "mixed"),
+]
+
+
+def variant_factors(A, D, n, v):
+    """Factor m is D's when m != n and bit j of v is set, j being m's index
+    among the modes other than n."""
+    others = [m for m in range(len(A)) if m != n]
+    return [D[m] if m != n and (v >> others.index(m)) & 1 else A[m] for m in range(len(A))]
+
+
+@pytest.mark.parametrize("shape,R,dtype,prec_name", VARIANT_CASES)
+def test_mttkrp_variants_parity(cp, ctx, shape, R, dtype, prec_name):
+    rng = np.random.default_rng(R + len(shape))
+    T = rng.standard_normal(shape).astype(dtype)
+    u = synth.initial_guess(rng, shape, R)
+    d = synth.initial_guess(rng, shape, R) - u
+    N = len(shape)
+    nvar = 2 ** (N - 1)
+    modes = list(reversed(range(N)))
+    out = torch.empty(sum(nvar * shape[n] * R for n in modes), dtype=torch.float64, device="cuda")
+    prec = cp.CP_MIXED_BF16X3 if prec_name == "mixed" else cp.CP_FP64
+    t = cp.cp_tensor_dense(ctx, dev(T))
+    cp.cp_mttkrp_variants(ctx, t, R, dev(u), dev(d), modes, out, prec)
+    cp.cp_ctx_sync(ctx)
+    got = out.cpu().numpy()
+    A, D = O.unpack(u, shape, R), O.unpack(d, shape, R)
+    tol = MIXED_TOL if prec_name == "mixed" else 1e-10
+    off = 0
+    for n in modes:
+        for v in range(nvar):
+            ref = O.mttkrp_dense(T.astype(np.float64), variant_factors(A, D, n, v), n)
+            assert rel(got[off:off + ref.size].reshape(ref.shape), ref) <= tol, (shape, R, n, v)
+            off += ref.size
+
+
+def test_full_size_dense_256_variants_multilinear(cp, ctx):
+    """The 256^3, R=16 workload, all three modes' variants in the one launch
+    the solve's line search makes: sum_v beta^popcount(v) M_v^(n) equals the
+    FP64 oracle's M^(n)(u + beta d) within the mixed bound."""
+    prob, u0 = synth.workload_dense_256()
+    rng = np.random.default_rng(11)
+    d = 0.1 * rng.standard_normal(u0.size)
+    beta = 0.7
+    R, N = 16, 3
+    t = cp.cp_tensor_dense(ctx, dev(prob.T))
+    out = torch.empty(3 * 4 * 256 * R, dtype=torch.float64, device="cuda")
+    cp.cp_mttkrp_variants(ctx, t, R, dev(u0), dev(d), [2, 0, 1], out, cp.CP_MIXED_BF16X3)
+    cp.cp_ctx_sync(ctx)
+    got = out.cpu().numpy().reshape(3, 4, 256, R)
+    X = O.unpack(u0 + beta * d, prob.dims, R)
+    for k, n in enumerate([2, 0, 1]):
+        if n == 1:
+            continue
+        line = sum(beta ** bin(v).count("1") * got[k, v] for v in range(4))
+        ref = O.mttkrp_dense(prob.T, X, n)
+        assert rel(line, ref) <= MIXED_TOL, n
