@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--mttkrp-only", default=None, choices=["dense_256", "dense_4way", "sparse"],
                    help="time only cp_mttkrp on that workload (profiling driver)")
     p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--accuracy-report", default=None, choices=["dense_256", "dense_4way"],
+                   help="mixed (with FP64 polish) against FP64 solves of one workload; one JSON line")
     p.add_argument("--solve-only", action="store_true",
                    help="time only the headline solves (profiling driver; no side reports)")
     p.add_argument("--small-kernels", action="store_true",
@@ -550,6 +552,87 @@ def run_mttkrp_only(args):
     print(json.dumps({"mttkrp_only": args.mttkrp_only, "prec": args.prec, **res}))
 
 
+def run_accuracy_report(args):
+    """The mixed-precision solve (bf16x3 MTTKRP, FP64 polish) and the FP64
+    solve of one workload from the same starting point on the GPU: iterations,
+    time, f and ||grad f||/P of each; at the mixed solution, f and grad f of
+    the mixed evaluation against the FP64 one (the FP64 GPU path matches the
+    FP64 oracle within 1e-10 in the tests); and the mixed solution's factors
+    against the FP64 solution's (per mode, relative Frobenius error with the
+    column signs matched)."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1105_5331_gb300 as cp
+    prob, u0 = synth.workload_dense_4way() if args.accuracy_report == "dense_4way" else synth.workload_dense_256()
+    Rk = prob.R
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    ctx = cp.cp_ctx_create(0, stream)
+    with torch.cuda.stream(stream):
+        T = torch.from_numpy(prob.T).to(dev)
+    stream.synchronize()
+    t = cp.cp_tensor_dense(ctx, T)
+    out = {"accuracy_report": args.accuracy_report, "dims": list(prob.dims), "R": Rk, "tol": TOL}
+    sols = {}
+    for name, prec in (("mixed", cp.CP_MIXED_BF16X3), ("fp64", cp.CP_FP64)):
+        o = cp.cp_solve_opts_default(Rk)
+        o.tol = TOL
+        o.prec = prec
+        with torch.cuda.stream(stream):
+            u = torch.from_numpy(u0).to(dev)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        r = cp.cp_solve(ctx, t, o, u)
+        stream.synchronize()
+        dt = time.perf_counter() - t0
+        sols[name] = u
+        out[name] = {"s": dt, "iters": r["iters"], "mixed_iters": r["mixed_iters"], "fp64_iters": r["fp64_iters"],
+                     "converged": r["converged"], "f": r["f"], "gnorm_over_P": r["gnorm_over_P"]}
+    um = sols["mixed"]
+    P = um.numel()
+    ev = {}
+    for name, prec in (("mixed", cp.CP_MIXED_BF16X3), ("fp64", cp.CP_FP64)):
+        f = torch.zeros(1, dtype=torch.float64, device=dev)
+        g = torch.empty(P, dtype=torch.float64, device=dev)
+        cp.cp_fg(ctx, t, Rk, um, f, g, prec)
+        cp.cp_ctx_sync(ctx)
+        ev[name] = (f.item(), g.cpu().numpy())
+    f64, g64 = ev["fp64"]
+    fm, gm = ev["mixed"]
+    out["at_mixed_solution"] = {"f_fp64": f64, "f_mixed_rel_err": abs(fm - f64) / abs(f64),
+                                "g_fp64_over_P": float(np.linalg.norm(g64)) / P,
+                                "g_mixed_err_over_P": float(np.linalg.norm(gm - g64)) / P}
+    # rank-one terms matched greedily by congruence (product over modes of
+    # |cos| of the columns), then per mode the relative error, signs matched
+    a, b = um.cpu().numpy(), sols["fp64"].cpu().numpy()
+    As, Bs, off = [], [], 0
+    for n in prob.dims:
+        As.append(a[off:off + n * Rk].reshape(n, Rk))
+        Bs.append(b[off:off + n * Rk].reshape(n, Rk))
+        off += n * Rk
+    C = np.ones((Rk, Rk))
+    for A, Bf in zip(As, Bs):
+        C *= np.abs((A / np.linalg.norm(A, axis=0)).T @ (Bf / np.linalg.norm(Bf, axis=0)))
+    perm, used = [-1] * Rk, set()
+    for idx in np.argsort(-C, axis=None):
+        r, s = divmod(int(idx), Rk)
+        if perm[r] < 0 and s not in used:
+            perm[r] = s
+            used.add(s)
+    errs = []
+    for A, Bf in zip(As, Bs):
+        Bp = Bf[:, perm]
+        s = np.sign(np.sum(A * Bp, axis=0))
+        s[s == 0] = 1.0
+        errs.append(float(np.linalg.norm(A - Bp * s) / np.linalg.norm(Bf)))
+    out["factors_rel_err_vs_fp64_solve"] = errs
+    out["term_order_vs_fp64_solve"] = perm
+    out["f_rel_diff_vs_fp64_solve"] = abs(out["mixed"]["f"] - out["fp64"]["f"]) / abs(out["fp64"]["f"])
+    print(json.dumps(out))
+
+
 def run_small_kernels(args):
     """Three rounds of cp_fg, cp_als_sweep (normalising), ngmres_step (window
     of 20) and linesearch on the 256^3 R=16 workload, outside any graph."""
@@ -675,6 +758,9 @@ def main():
         return
     if args.kernel_breakdown:
         run_kernel_breakdown(args)
+        return
+    if args.accuracy_report:
+        run_accuracy_report(args)
         return
     if args.small_kernels:
         run_small_kernels(args)

@@ -184,3 +184,61 @@ def test_full_size_dense_256_variants_multilinear(cp, ctx):
         line = sum(beta ** bin(v).count("1") * got[k, v] for v in range(4))
         ref = O.mttkrp_dense(prob.T, X, n)
         assert rel(line, ref) <= MIXED_TOL, n
+
+
+def test_mixed_solve_4way_against_oracle(cp, ctx):
+    """A 4-way dense problem (planted R = 8, collinearity 0.5, 5 % noise, FP32
+    data) solved with the mixed-precision MTTKRP (every mode's line-search
+    variants in one launch: 8 x 8 columns) and the FP64 polish.  By the FP64
+    oracle's own evaluation at the result, the gradient meets the tolerance
+    and f is the one reported; f equals the FP64 solve's, and the rank-one
+    terms match the FP64 solve's up to order and sign (greedy matching by
+    congruence, the product over modes of the column cosines)."""
+    rng = synth.rng_for(60)
+    dims, R = (24, 20, 16, 12), 8
+    prob = synth.dense_problem(rng, dims, R, 0.5, eta=0.05, dtype=np.float32)
+    u0 = synth.initial_guess(rng, dims, R)
+    t = cp.cp_tensor_dense(ctx, dev(prob.T))
+    sols = {}
+    for name, prec in (("mixed", cp.CP_MIXED_BF16X3), ("fp64", cp.CP_FP64)):
+        opts = cp.cp_solve_opts_default(R)
+        opts.prec = prec
+        ud = dev(u0)
+        rep = cp.cp_solve(ctx, t, opts, ud)
+        assert rep["converged"], (name, rep)
+        sols[name] = (ud.cpu().numpy(), rep)
+    u, rep = sols["mixed"]
+    X = O.DenseTensor(prob.T)
+    f, g = O.fg(X, u, R)
+    P = O.n_params(dims, R)
+    assert np.linalg.norm(g) / P < 1.0001e-7
+    assert abs(rep["f"] - f) <= 1e-10 * abs(f) + 1e-14 * X.norm2
+    assert abs(rep["f"] - sols["fp64"][1]["f"]) <= 1e-6 * abs(f)
+    A, B = O.unpack(u, dims, R), O.unpack(sols["fp64"][0], dims, R)
+    perm = match_terms(A, B)
+    for a, b in zip(A, B):
+        bp = b[:, perm]
+        s = np.sign(np.sum(a * bp, axis=0))
+        s[s == 0] = 1.0
+        assert np.linalg.norm(a - bp * s) / np.linalg.norm(b) <= 1e-3
+    print("iterations mixed/fp64:", rep["iters"], sols["fp64"][1]["iters"], "fp64 polish", rep["fp64_iters"],
+          "order", perm)
+
+
+def match_terms(A, B):
+    """perm[r] = the term of B matched to term r of A, greedily by the largest
+    congruence prod_n |cos(a_r^(n), b_s^(n))|."""
+    R = A[0].shape[1]
+    C = np.ones((R, R))
+    for a, b in zip(A, B):
+        an = a / np.linalg.norm(a, axis=0)
+        bn = b / np.linalg.norm(b, axis=0)
+        C *= np.abs(an.T @ bn)
+    perm = [-1] * R
+    used = set()
+    for idx in np.argsort(-C, axis=None):
+        r, s = divmod(int(idx), R)
+        if perm[r] < 0 and s not in used:
+            perm[r] = s
+            used.add(s)
+    return perm
