@@ -7,8 +7,10 @@
 // lo = bf16(T - hi), so that T ~= hi + lo to about 2^-17 relative.  The
 // Khatri-Rao tile KR[kbar, r] = prod_{m != n} A_m[i_m, r] is formed on the fly
 // in shared memory from FP32 copies of the factors and split the same way.
-// Each 16-deep step issues three MMAs, hi*hi + hi*lo + lo*hi, into one FP32
-// accumulator (the lo*lo term, ~2^-18 relative, is dropped).
+// Each 16-deep step issues three MMAs, hi*hi + hi*lo + lo*hi, into an FP32
+// accumulator in tensor memory (the lo*lo term, ~2^-18 relative, is
+// dropped); successive contraction tiles rotate over up to four accumulators
+// that the epilogue adds in registers (see kMaxAcc).
 //
 // T_(n) is stored pre-tiled: every 128-row x 64-column tile of each plane is
 // one contiguous block of rows x 128 bytes, already in the 128-byte-swizzled
@@ -25,8 +27,12 @@
 //   warps 2-5  build the Khatri-Rao hi/lo tiles of each stage (SW128,
 //              K-major), then drain the accumulators (tcgen05.ld) and write
 //              the CTA's partial I x R sums.
-// The grid splits the contraction range (split-K) and, for I_n > 256, the row
-// tiles.  A second kernel adds the per-CTA partials in a fixed order in FP64.
+// The grid splits the contraction range (split-K) and the rows into 128-row
+// groups; one launch may hold the MTTKRPs of several modes (jobs), the CTAs
+// shared among them.  The consumers of the per-CTA partial sums add them in
+// a fixed order: in FP32 in the solver's kernels (ALS update, f/g finish,
+// line-search coefficients, variant sums), in FP64 in the stand-alone
+// MTTKRP's reduction.
 // Every mbarrier wait is bounded; on a timeout the CTA records
 // CP_ERR_TIMEOUT in the device status word and winds down.
 
