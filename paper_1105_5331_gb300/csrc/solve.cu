@@ -40,14 +40,8 @@ namespace cpg {
 
 namespace {
 
-enum { F = 0, FBAR = 1, FX = 2, SLOPE = 3, GD = 4, GG = 5, NSCAL = 8 };
+enum { F = 0, FBAR = 1, SLOPE = 3, GD = 4, GG = 5, NSCAL = 8 };
 enum { STOP_RUN = 0, STOP_TOL = 1, STOP_MAXIT = 2, STOP_STALL = 3, STOP_NONFINITE = 4 };
-
-__global__ void copy_kernel(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
-  CP_PDL_ENTRY();
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    b[k] = a[k];
-}
 
 // Stopping test on ||g||/P (shared by the phase start and the loop tail).
 __device__ void ctl_eval(SolveCtl* c, const double* scal, double P, double tol, int maxit, int mixed,
@@ -258,12 +252,6 @@ cp_status dcopy_multi(cp_ctx* ctx, const CopySeg& c) {
   int64_t nmax = 1;
   for (int s = 0; s < c.nseg; ++s) nmax = std::max(nmax, c.n[s]);
   (void)launch_pdl(copy_multi_kernel, dim3((unsigned)grid_for(ctx, nmax)), dim3(256), 0, ctx->stream, c);
-  CP_LAUNCH_CHECK();
-  return CP_OK;
-}
-
-cp_status dcopy(cp_ctx* ctx, int64_t n, const double* a, double* b) {
-  (void)launch_pdl(copy_kernel, dim3((unsigned)grid_for(ctx, n)), dim3(256), 0, ctx->stream, n, a, b);
   CP_LAUNCH_CHECK();
   return CP_OK;
 }
@@ -607,11 +595,11 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
                     mg_x.nvar = 1 << (L.N - 1);
                     mg_x.beta = &m.st->stp_eval;
                     for (int n = ls_all ? 0 : L.N - 1; n < L.N; ++n) mg_x.m[n] = m.Mv + (size_t)mg_x.nvar * L.off[n];
-                    CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, m.d, &m.st->stp_eval, m.x, m.scal + FX, m.gx, pr,
+                    // (f(x) goes straight to the iterate's f: nothing reads that in between)
+                    CP_TRY(fg_eval_ex(ctx, t, L, m.ubar, m.d, &m.st->stp_eval, m.x, m.scal + F, m.gx, pr,
                                       nullptr, m.grams, m.M0x, &mg_x, nullptr, m.Xi0x, m.Gls));
-                    CP_TRY(normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr, m.grams, m.M0x, m.M0, m.Gu,
-                                          m.Xi0x, m.Xi0, nullptr, nullptr, want32 ? m.u32 : nullptr));
-                    return dcopy(ctx, 1, m.scal + FX, m.scal + F);
+                    return normalize_into(ctx, L, m.x, m.u, m.gx, m.g, nullptr, m.grams, m.M0x, m.M0, m.Gu,
+                                          m.Xi0x, m.Xi0, nullptr, nullptr, want32 ? m.u32 : nullptr);
                   }
                   return dcopy_multi(ctx, ubar_state);
                 });
