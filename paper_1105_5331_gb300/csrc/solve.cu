@@ -6,18 +6,25 @@
 // The whole iteration runs on the device.  Each precision phase of a solve is
 // ONE CUDA graph built from conditional nodes:
 //
-//   start   f, g at u; window <- {(u, g(u))}; ||g||; set `outer`
+//   start   f, g at u (with u's Grams, M^(1) and Gammabar^(1) inverse);
+//           window <- {(u, g(u))}; ||g||; set `outer`
 //   WHILE outer:
-//     head      Step I (ALS sweep, normalise), f and g at ubar, Step II
-//               (window dots, normal equations, uhat, normalise),
-//               d = uhat - ubar, slope = g(ubar)^T d, line-search start;
+//     head      Step I: the ALS sweep on u (its first mode from the carried
+//               M^(1) and inverse), normalised into ubar (the sweep's last
+//               MTTKRP and the Grams follow); f and g at ubar; Step II
+//               (window dots, normal equations, uhat, normalised);
+//               d = uhat - ubar, slope = g(ubar)^T d;
 //               set `restart` = (slope >= 0)
-//     IF restart:  u = ubar, window <- {(ubar, g(ubar))}
-//     ELSE:        WHILE ls:  x = ubar + stp d, f and g at x, phi'(stp),
-//                             one More-Thuente update, set `ls` = !done
-//                  set `accept`;  IF accept: u = normalise(x) (g rescaled)
-//                                 ELSE: u = ubar;   push (u, g) to the window
-//     tail      ||g||, counters, stopping test; set `outer`
+//     IF restart:  u = ubar (with its f, g, M^(1), Grams and inverse)
+//     ELSE:        Step III: the polynomial phi(beta) = f(ubar + beta d)
+//                  from one MTTKRP launch (Khatri-Rao variants) and the
+//                  Grams of ubar and d, the More-Thuente search on it;
+//                  set `accept`
+//                  IF accept: x = ubar + beta d; f, g at x from the
+//                             variants; u = normalise(x)
+//                  ELSE:      u = ubar
+//     tail      push (u, g) to the window (reset it after a restart),
+//               ||g||, counters, stopping test; set `outer`
 //
 // The host launches one graph per phase and reads a small control block at
 // its end.  Workspace inside the graph comes from a bump arena (sized by a
@@ -68,33 +75,7 @@ __device__ void ctl_eval(SolveCtl* c, const double* scal, double P, double tol, 
   cudaGraphSetConditional(outer, stop == STOP_RUN ? 1u : 0u);
 }
 
-__global__ void ctl_begin_kernel(SolveCtl* c, const double* scal, double P, double tol, int maxit, int mixed,
-                                 int stall, cudaGraphConditionalHandle outer) {
-  c->best = INFINITY;
-  c->since_best = 0;
-  c->fg_evals += 1;
-  ctl_eval(c, scal, P, tol, maxit, mixed, stall, outer);
-}
-
-__global__ void ctl_tail_kernel(SolveCtl* c, const double* scal, double P, double tol, int maxit, int mixed,
-                                int stall, cudaGraphConditionalHandle outer) {
-  c->iters += 1;
-  if (mixed)
-    c->mixed_iters += 1;
-  else
-    c->fp64_iters += 1;
-  ctl_eval(c, scal, P, tol, maxit, mixed, stall, outer);
-}
-
-__global__ void ctl_after_head_kernel(SolveCtl* c, const double* scal, cudaGraphConditionalHandle restart) {
-  c->als_sweeps += 1;
-  c->fg_evals += 1;
-  const bool r = !(scal[SLOPE] < 0.0);
-  if (r) c->restarts += 1;
-  cudaGraphSetConditional(restart, r ? 1u : 0u);
-}
-
-// Up to six copies in one launch (the branches that make ubar the iterate).
+// Up to eight copies in one launch (the branches that make ubar the iterate).
 struct CopySeg {
   const double* src[8];
   double* dst[8];
