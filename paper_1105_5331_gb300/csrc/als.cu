@@ -13,10 +13,12 @@
 //               reciprocals by Newton's iteration from an FP32 seed.  It runs
 //               on the context's aux stream, overlapped with the MTTKRP of
 //               the same mode, which does not depend on it; one barrier per
-//               pivot (double-buffered), every thread forms the reciprocal.
+//               pivot (double-buffered), the thread that forms the next
+//               diagonal entry forming its reciprocal at once (look-ahead).
 //   update      A_n = M Gammabar^-1: rows spread over blocks; M rows from the
 //               MTTKRP partial sums (FP32 partials added in FP32, FP64 ones in
-//               FP64, in a fixed order), then one FP64 dot per output.
+//               FP64, in a fixed order), then one FP64 dot per output; the
+//               last mode's M can be kept (it is M^(N) of the swept point).
 #include <algorithm>
 
 #include "cp_internal.cuh"

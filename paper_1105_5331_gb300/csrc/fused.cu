@@ -1,12 +1,17 @@
 // Fused f / grad f evaluation (Eq. fA, Eq. Gn, Eq. Gamma) in three steps:
 //
-//   prep     x = base (+ stp d for a line-search trial), its FP32 copy for the
-//            tensor-core MTTKRP, and the factor Grams A_m^T A_m (per-block
-//            partial sums; the last block to finish adds them in a fixed order)
-//   MTTKRP   per mode, split-K partial sums (tcgen05 / FP64 / sparse)
-//   finish   per 32 gradient entries: M = sum of the partials (fixed order),
-//            G = A Gammabar - M; <A^(N), M^(N)> and g . d as block partials;
-//            the last block forms f = 1/2(||T||^2 - 2<T,A> + sum Gamma) and g . d.
+//   prep     x = base (+ stp d for a point on a search line) and its FP32
+//            copy for the tensor-core MTTKRP (unless one is given); the
+//            factor Grams on the aux stream beside the MTTKRPs (unless given,
+//            or formed from a line search's Grams), and the inverse of
+//            Gammabar^(1) when asked for
+//   MTTKRP   per mode whose M is not supplied, split-K partial sums
+//            (tcgen05 / FP64 / sparse)
+//   finish   per 32 gradient entries: M = the sum of the partials in a fixed
+//            order (or the supplied M, or sum_v beta^popc(v) M_v from a line
+//            search's Khatri-Rao variants), G = A Gammabar - M;
+//            <A^(N), M^(N)> and g . d as block partials; the last block forms
+//            f = 1/2(||T||^2 - 2<T,A> + sum Gamma) and g . d.
 //
 // "Last block" reductions: each block writes its partial, fences, and bumps a
 // per-stream counter; the block that sees the final count reads all partials

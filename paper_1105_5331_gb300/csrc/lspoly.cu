@@ -11,7 +11,10 @@
 // a polynomial of degree 2N whose coefficients need one pass over T: the
 // MTTKRP of the last mode against the 2^(N-1) Khatri-Rao products in which
 // every other mode contributes either its A or its D factor, contracted with
-// A and D of the last mode, plus three Grams per mode.  The More-Thuente
+// A and D of the last mode, plus three Grams per mode.  Where the variant
+// tiles are narrow, the same launch makes every other mode's variants too,
+// from which M^(n)(ubar + beta d) of every mode, and so f and g at the
+// accepted point, follow without another pass.  The More-Thuente
 // search then evaluates phi and phi' = dphi/dbeta (= g(ubar + beta d) . d)
 // by Horner's rule at no further cost per trial, in one thread.  Every trial
 // sees the same function the paper's search sees; only the arithmetic that
