@@ -4,9 +4,11 @@
 //     p_j = gbar - g(u_j),  (P^T P + delta I) alpha = -P^T gbar,
 //     delta = eps * max_j (P^T P)_jj,  uhat = ubar + sum_j alpha_j (ubar - u_j).
 // One pass over the window computes every p_j . p_l and p_j . gbar (the p_j
-// are formed per element, never stored); one block reduces the per-CTA sums in
-// a fixed order, factors the m x m system by Cholesky and solves for alpha; a
-// last pass forms uhat.
+// are formed per element, never stored); the last block of the reduction adds
+// the per-CTA sums in a fixed order and solves the m x m system by
+// Gauss-Jordan elimination (no pivoting: the matrix is SPD); a last pass
+// forms uhat (and, for the normalisation that follows, the column sums of
+// squares of its factors).
 //
 // The window is a ring of `cap` slots in device memory; its state
 // win = {start, m} also lives in device memory (window row j, oldest first, is
