@@ -145,6 +145,51 @@ def test_gradient_central_differences(dims, R):
     assert np.linalg.norm(fd - g) <= 1e-6 * np.linalg.norm(g)
 
 
+@pytest.mark.parametrize("dims,R", [((5, 4, 3), 2), ((4, 3, 3, 2), 3)])
+def test_f_along_a_line_is_a_polynomial_of_degree_2N(dims, R):
+    """phi(beta) = f(u + beta d) is a polynomial of degree 2N (the model is
+    multilinear in the factors; Section 2.1's line search sees this
+    function): the interpolant through 2N + 1 values predicts phi elsewhere,
+    its derivative is g(u + beta d) . d, and its leading coefficient is
+    1/2 sum_{r,s} prod_n (D_n^T D_n)[r, s]."""
+    rng = np.random.default_rng(13)
+    N = len(dims)
+    X = O.DenseTensor(rng.standard_normal(dims))
+    u = synth.initial_guess(rng, dims, R)
+    d = 0.3 * synth.initial_guess(rng, dims, R)
+    b = np.linspace(-1.0, 1.5, 2 * N + 1)
+    coef = np.polyfit(b, [O.fg(X, u + t * d, R)[0] for t in b], 2 * N)
+    D = O.unpack(d, dims, R)
+    lead = 0.5 * np.sum(np.prod([Dn.T @ Dn for Dn in D], axis=0))
+    assert abs(coef[0] - lead) <= 1e-6 * abs(lead)
+    for t in (-0.7, 0.2, 1.3):
+        f, g = O.fg(X, u + t * d, R)
+        assert abs(np.polyval(coef, t) - f) <= 1e-8 * (abs(f) + X.norm2)
+        assert abs(np.polyval(np.polyder(coef), t) - g @ d) <= 1e-6 * (abs(g @ d) + X.norm2)
+
+
+@pytest.mark.parametrize("dims,R", [((5, 4, 3), 2), ((4, 3, 3, 2), 3)])
+def test_mttkrp_is_multilinear_along_a_line(dims, R):
+    """M^(n)(u + beta d) = sum over the 2^(N-1) choices of A or D for the
+    other modes of beta^(number of D) times that MTTKRP (the Khatri-Rao
+    variants the line search's single pass makes), for every mode."""
+    rng = np.random.default_rng(17)
+    N = len(dims)
+    T = rng.standard_normal(dims)
+    A = rand_factors(rng, dims, R)
+    D = rand_factors(rng, dims, R)
+    beta = 0.37
+    X = [a + beta * dd for a, dd in zip(A, D)]
+    for n in range(N):
+        others = [m for m in range(N) if m != n]
+        acc = np.zeros((dims[n], R))
+        for v in range(2 ** (N - 1)):
+            F = [D[m] if m != n and (v >> others.index(m)) & 1 else A[m] for m in range(N)]
+            acc += beta ** bin(v).count("1") * O.mttkrp_dense(T, F, n)
+        ref = O.mttkrp_dense(T, X, n)
+        assert np.abs(acc - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 def test_exact_decomposition_has_zero_f_and_g():
     rng = np.random.default_rng(7)
     dims, R = (5, 4, 6), 3
