@@ -128,6 +128,9 @@ VARIANT_CASES = [
     ((40, 30, 20, 9), 32, np.float32, "mixed"),
     ((9, 8, 7), 60, np.float32, "mixed"),
     ((12, 10, 8, 6), 40, np.float32, "mixed"),
+    ((70, 90), 4, np.float32, "mixed"),       # 2-way: two variants, one other mode
+    ((70, 90), 4, np.float64, "fp64"),
+    ((33, 17, 9), 1, np.float32, "mixed"),    # rank 1
 ]
 
 
@@ -161,6 +164,28 @@ def test_mttkrp_variants_parity(cp, ctx, shape, R, dtype, prec_name):
             ref = O.mttkrp_dense(T.astype(np.float64), variant_factors(A, D, n, v), n)
             assert rel(got[off:off + ref.size].reshape(ref.shape), ref) <= tol, (shape, R, n, v)
             off += ref.size
+
+
+def test_mttkrp_variants_one_mode_and_argument_errors(cp, ctx):
+    """One listed mode gives that mode's variants alone (the same values as
+    when all modes are listed); a repeated mode, a mode out of range and an
+    empty list are argument errors."""
+    rng = np.random.default_rng(23)
+    shape, R = (30, 20, 10), 6
+    T = rng.standard_normal(shape).astype(np.float32)
+    u = dev(synth.initial_guess(rng, shape, R))
+    d = dev(0.5 * synth.initial_guess(rng, shape, R))
+    t = cp.cp_tensor_dense(ctx, dev(T))
+    one = torch.empty(4 * 20 * R, dtype=torch.float64, device="cuda")
+    cp.cp_mttkrp_variants(ctx, t, R, u, d, [1], one, cp.CP_FP64)
+    full = torch.empty(4 * sum(shape) * R, dtype=torch.float64, device="cuda")
+    cp.cp_mttkrp_variants(ctx, t, R, u, d, [0, 1, 2], full, cp.CP_FP64)
+    cp.cp_ctx_sync(ctx)
+    off = 4 * 30 * R
+    assert np.array_equal(one.cpu().numpy(), full.cpu().numpy()[off:off + 4 * 20 * R])
+    for modes in ([0, 0], [3], []):
+        with pytest.raises(cp.CpError):
+            cp.cp_mttkrp_variants(ctx, t, R, u, d, modes, full, cp.CP_FP64)
 
 
 def test_full_size_dense_256_variants_multilinear(cp, ctx):
