@@ -265,9 +265,7 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         times, reps = timed_solves(prec, args.warmup, args.steps, lc)
     launches = cp.cp_kernel_launches() - lc[0]   # the K timed solves only
-    total = sum(times)
-    total_max = allreduce_max(total, world)
-    value = world * args.steps / total_max
+    value, total_max = aggregate_replicas(times, world)
     # the other precision at the same tolerance, for the mixed-vs-FP64 figure
     other = cp.CP_FP64 if prec != cp.CP_FP64 and not args.solve_only else None
     other_obj = None
@@ -485,6 +483,14 @@ def allreduce_max(x, world):
     v = torch.tensor([x], dtype=torch.float64)
     dist.all_reduce(v, op=dist.ReduceOp.MAX)
     return float(v.item())
+
+
+def aggregate_replicas(times, world):
+    """Whole-job solves/s over `world` independent replicas, each of which
+    timed len(times) solves: every replica's total, the MAX over ranks (the
+    job ends when the slowest replica does), value = world x steps / max."""
+    total_max = allreduce_max(float(sum(times)), world)
+    return world * len(times) / total_max, total_max
 
 
 def run_mttkrp_only(args):
