@@ -83,7 +83,13 @@ size_t request_footprint(int N, const int64_t* dims, cp_dtype dtype, const cp_so
   const size_t P = sumI * (size_t)o.R;
   size_t bytes = (size_t)N * K * esz + K * esz;                 // per-mode copies + upload
   if (o.prec != CP_FP64) bytes += (size_t)N * (K + 8 * Imax) * 4;  // bf16 hi/lo planes
-  bytes += sizeof(double) * ((9 + 2 * (size_t)o.w) * P + Imax * o.R + (size_t)N * o.R * o.R);
+  // solver state: iterate-sized vectors and the window, M^(1) / M^(N) copies,
+  // the line-search variants of every mode, Grams, inverses, FP32 copies
+  const size_t RR = (size_t)o.R * o.R;
+  const size_t rs = ((size_t)o.R + 3) / 4 * 4;
+  const size_t n32 = (sumI * rs + 31) / 32 * 16;
+  bytes += sizeof(double) * ((9 + 2 * (size_t)o.w) * P + Imax * o.R + (size_t)N * RR + 5 * Imax * o.R +
+                             ((size_t)1 << (N - 1)) * P + 6 * (size_t)N * RR + 3 * (RR + 2) + 3 * n32 + 128);
   bytes += sizeof(double) * 12 * P + (size_t)4 * 152 * Imax * o.R * 6 + ((size_t)8 << 20);   // workspace
   return bytes;
 }
