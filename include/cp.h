@@ -177,10 +177,12 @@ cp_status cp_fg(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, double*
                 double* g, cp_precision prec);
 
 /* One ALS iteration M(u) (Section 2.3, Eq. foopt): for n = 1..N,
- * A^(n) <- M^(n) (Gammabar^(n))^{-1} by an R x R Cholesky factorisation, with
- * the factors of modes < n already updated (block Gauss-Seidel).  If a
- * Cholesky pivot is not positive, one retry with Gammabar + 1e-12 tr/R I;
- * then CP_ERR_NOT_SPD is recorded (reported by the next sync).  If
+ * A^(n) <- M^(n) (Gammabar^(n))^{-1} with the factors of modes < n already
+ * updated (block Gauss-Seidel); the SPD R x R matrix is inverted by
+ * Gauss-Jordan elimination without pivoting, which fails exactly when a
+ * Cholesky factorisation would.  If a pivot is not positive, one retry with
+ * Gammabar + 1e-12 tr/R I; then CP_ERR_NOT_SPD is recorded (reported by the
+ * next sync).  If
  * `normalize` is non-zero the result is normalised as cp_normalize does.
  * u is updated in place.  Asynchronous. */
 cp_status cp_als_sweep(cp_ctx* ctx, const cp_tensor* t, int R, double* u, int normalize,
@@ -199,7 +201,8 @@ cp_status cp_normalize(cp_ctx* ctx, int N, const int64_t* dims, int R, double* u
 /* ------------------------------------------------------------------ N-GMRES */
 
 /* N-GMRES Step II (Section 2.1, Eq. accel, Eq. linearize, Eq. normal): with
- * p_j = gbar - G_j, solve (P^T P + delta I) alpha = -P^T gbar by Cholesky,
+ * p_j = gbar - G_j, solve (P^T P + delta I) alpha = -P^T gbar (SPD; by
+ * Gauss-Jordan elimination without pivoting),
  * delta = eps * max_j (P^T P)_jj (alpha = 0 if that maximum is 0), and form
  * uhat = ubar + sum_j alpha_j (ubar - U_j).
  * U, G: m x Pn row-major (window iterates and their gradients, any order);
