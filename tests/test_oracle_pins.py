@@ -190,6 +190,41 @@ def test_mttkrp_is_multilinear_along_a_line(dims, R):
         assert np.abs(acc - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_line_search_on_the_polynomial_visits_the_same_trials(seed):
+    """More-Thuente on phi(beta) = f(x0 + beta d) evaluated through f and g at
+    every trial, and on the degree-2N polynomial that interpolates phi (its
+    derivative for phi'), end at the same step after the same number of trials
+    with the same termination code: a search on the exact polynomial is the
+    search Section 2.1 runs."""
+    rng = np.random.default_rng(seed)
+    dims, R = (6, 5, 4), 3
+    X = O.DenseTensor(rng.standard_normal(dims))
+    x0 = synth.initial_guess(rng, dims, R)
+    f0, g0 = O.fg(X, x0, R)
+    d = -g0 * 0.05 + 0.1 * rng.standard_normal(x0.size)
+    if g0 @ d >= 0:
+        d = -g0 * 0.05
+    N = len(dims)
+
+    def phi_true(b):
+        f, g = O.fg(X, x0 + b * d, R)
+        return f, float(g @ d), None
+
+    b = np.linspace(-1.0, 2.0, 2 * N + 1)
+    coef = np.polyfit(b, [O.fg(X, x0 + t * d, R)[0] for t in b], 2 * N)
+    dcoef = np.polyder(coef)
+
+    def phi_poly(t):
+        return float(np.polyval(coef, t)), float(np.polyval(dcoef, t)), None
+
+    st, ft, _, _, nt, it = O.more_thuente(phi_true, f0, float(g0 @ d))
+    sp, fp, _, _, np_, ip = O.more_thuente(phi_poly, *phi_poly(0.0)[:2])
+    assert (nt, it) == (np_, ip)
+    assert abs(st - sp) <= 1e-8 * abs(st)
+    assert abs(ft - fp) <= 1e-8 * (abs(ft) + X.norm2)
+
+
 def test_exact_decomposition_has_zero_f_and_g():
     rng = np.random.default_rng(7)
     dims, R = (5, 4, 6), 3
