@@ -323,6 +323,45 @@ def test_normalize_invariants_and_exact_gradient_rescale():
         np.testing.assert_allclose(np.linalg.norm(A, axis=0), lam ** (1 / 3), rtol=1e-12)
 
 
+def test_normalize_carries_mttkrp_gram_and_inverse_by_scales_and_order():
+    """After the normalisation every mode's factor is the old one with columns
+    scaled by s_{n,r} = lambda_r^(1/N) / ||a_r^(n)|| and reordered by decreasing
+    lambda.  Then M^(n), the Grams and the inverse of Gammabar^(n) at the new
+    point follow from the old ones by the same order and the products of the
+    other modes' scales; the accelerated iteration reuses them instead of
+    recomputing.  M^(n) does not depend on A^(n) at all, which is why the
+    sweep's last MTTKRP is the one at the swept point."""
+    rng = np.random.default_rng(23)
+    dims, R = (5, 4, 6), 4
+    N = len(dims)
+    T = rng.standard_normal(dims)
+    F = [A * rng.uniform(0.2, 4.0, size=R) for A in rand_factors(rng, dims, R)]
+    nu = np.stack([np.sqrt(np.sum(A * A, axis=0)) for A in F])
+    lam = np.prod(nu, axis=0)
+    order = np.argsort(-lam, kind="stable")
+    s = lam ** (1.0 / N) / nu
+    un, _, lam_sorted = O.normalize(O.pack(F), dims, R)
+    np.testing.assert_allclose(lam_sorted, lam[order], rtol=1e-13)
+    Fn = O.unpack(un, dims, R)
+    for n in range(N):
+        np.testing.assert_allclose(Fn[n], (F[n] * s[n])[:, order], rtol=1e-12)
+        c = np.prod(np.delete(s, n, axis=0), axis=0)
+        M_old = O.mttkrp_dense(T, F, n)
+        np.testing.assert_allclose(O.mttkrp_dense(T, Fn, n), (M_old * c)[:, order],
+                                   rtol=1e-11, atol=1e-12 * np.abs(M_old).max())
+        G_old = F[n].T @ F[n]
+        np.testing.assert_allclose(O.grams(Fn)[n],
+                                   (G_old * np.outer(s[n], s[n]))[np.ix_(order, order)],
+                                   rtol=1e-11, atol=1e-13 * np.abs(G_old).max())
+        Gi_old = np.linalg.inv(O.gamma_bar(F, n))
+        Gi_new = np.linalg.inv(O.gamma_bar(Fn, n))
+        np.testing.assert_allclose(Gi_new, (Gi_old / np.outer(c, c))[np.ix_(order, order)],
+                                   rtol=1e-8, atol=1e-10 * np.abs(Gi_new).max())
+        F_other = [A.copy() for A in F]
+        F_other[n] = rng.standard_normal(F[n].shape)
+        np.testing.assert_array_equal(O.mttkrp_dense(T, F_other, n), M_old)
+
+
 def test_normalize_zero_column_left_unscaled():
     dims, R = (3, 3), 2
     u = np.arange(1.0, 13.0)
