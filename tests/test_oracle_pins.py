@@ -588,6 +588,61 @@ def test_solve_monotone_and_recovers_planted():
     assert rep.f <= 1e-12 * X.norm2
 
 
+def test_solve_restarting_every_iteration_is_normalised_als(monkeypatch):
+    """When the N-GMRES direction is never a descent direction every iteration
+    restarts from the ALS iterate, so the solve reduces to plain ALS (one sweep
+    and one normalisation per iteration) and each window holds one point."""
+    rng = synth.rng_for(94)
+    prob = synth.dense_problem(rng, (6, 5, 7), 2, 0.5)
+    X = O.DenseTensor(prob.T)
+    u0 = synth.initial_guess(rng, prob.dims, 2)
+    windows = []
+
+    def ascent_step(U, G, ubar, gbar, eps=1e-12):
+        windows.append(len(U))
+        return ubar + gbar, None
+
+    monkeypatch.setattr(O, "ngmres_step", ascent_step)
+    iters = 12
+    u, g, rep = O.cp_solve(X, u0, O.SolveOpts(R=2, tol=0.0, maxit=iters))
+    assert rep.iters == iters and rep.restarts == iters and rep.als_sweeps == iters
+    assert windows == [1] * iters
+    v, _, _ = O.normalize(u0, prob.dims, 2)
+    for _ in range(iters):
+        v, _, _ = O.normalize(O.als_sweep(X, v, 2), prob.dims, 2)
+    np.testing.assert_allclose(u, v, rtol=1e-12, atol=1e-13 * np.abs(v).max())
+
+
+def test_solve_window_grows_to_w_and_slides(monkeypatch):
+    """The window holds the last min(k + 1, w) iterates since the last
+    restart, and a restart leaves only the ALS iterate in it."""
+    rng = synth.rng_for(93)
+    prob = synth.dense_problem(rng, (8, 7, 9), 3, 0.9)
+    X = O.DenseTensor(prob.T)
+    u0 = synth.initial_guess(rng, prob.dims, 3)
+    real = O.ngmres_step
+    windows = []
+
+    def recording_step(U, G, ubar, gbar, eps=1e-12):
+        windows.append(len(U))
+        return real(U, G, ubar, gbar, eps)
+
+    monkeypatch.setattr(O, "ngmres_step", recording_step)
+    w, iters = 3, 10
+    _, _, rep = O.cp_solve(X, u0, O.SolveOpts(R=3, w=w, tol=0.0, maxit=iters))
+    assert rep.iters == iters and len(windows) == iters
+    assert windows[0] == 1
+    resets = 0
+    for prev, n in zip(windows, windows[1:]):
+        if n == 1:
+            resets += 1
+        else:
+            assert n == min(prev + 1, w)
+    assert 2 <= max(windows) <= w
+    # A restart in the last iteration leaves no later window to show it.
+    assert resets in (rep.restarts, rep.restarts - 1)
+
+
 def test_ngmres_beats_als_on_collinear_problem():
     rng = synth.rng_for(95)
     prob = synth.dense_problem(rng, (15, 15, 15), 3, 0.9, paper_l1=1, paper_l2=1)
