@@ -613,6 +613,31 @@ def test_solve_restarting_every_iteration_is_normalised_als(monkeypatch):
     np.testing.assert_allclose(u, v, rtol=1e-12, atol=1e-13 * np.abs(v).max())
 
 
+def test_solve_with_failing_line_search_is_normalised_als(monkeypatch):
+    """A line search that ends without sufficient decrease falls back to
+    beta = 0 (R10), i.e. to the ALS iterate, so if it always does the solve's
+    iterates are plain normalised ALS; every iteration counts as a restart or
+    a line-search failure."""
+    rng = synth.rng_for(92)
+    prob = synth.dense_problem(rng, (6, 7, 5), 2, 0.5)
+    X = O.DenseTensor(prob.T)
+    u0 = synth.initial_guess(rng, prob.dims, 2)
+
+    def failing_search(phi, f0, g0, opts=O.LSOpts()):
+        _, _, extra = phi(0.5)
+        return 0.5, f0 + 1.0, None, extra, 1, 3
+
+    monkeypatch.setattr(O, "more_thuente", failing_search)
+    iters = 10
+    u, _, rep = O.cp_solve(X, u0, O.SolveOpts(R=2, tol=0.0, maxit=iters))
+    assert rep.iters == iters and rep.restarts + rep.ls_failures == iters
+    assert rep.ls_failures > 0
+    v, _, _ = O.normalize(u0, prob.dims, 2)
+    for _ in range(iters):
+        v, _, _ = O.normalize(O.als_sweep(X, v, 2), prob.dims, 2)
+    np.testing.assert_allclose(u, v, rtol=1e-12, atol=1e-13 * np.abs(v).max())
+
+
 def test_solve_window_grows_to_w_and_slides(monkeypatch):
     """The window holds the last min(k + 1, w) iterates since the last
     restart, and a restart leaves only the ALS iterate in it."""
