@@ -549,6 +549,29 @@ def test_laplacian_matches_paper_worked_example():
     assert got == want
 
 
+@pytest.mark.parametrize("d,s", [(1, 6), (2, 4), (3, 3)])
+def test_laplacian_is_the_kronecker_sum_of_1d_laplacians(d, s):
+    """With the first d indices as the grid point and the last d as its
+    neighbour, the tensor viewed as an s^d x s^d matrix is the Kronecker sum
+    of d copies of tridiag(-1, 2, -1), whose eigenvalues are the sums of d
+    values 2 - 2 cos(k pi / (s + 1)), k = 1..s."""
+    lap = synth.laplacian_tensor(d, s)
+    T = np.zeros(lap.dims)
+    T[tuple(lap.coords.T)] = lap.vals
+    A = T.reshape(s ** d, s ** d)
+    L1 = 2 * np.eye(s) - np.eye(s, k=1) - np.eye(s, k=-1)
+    K = np.zeros((s ** d, s ** d))
+    for k in range(d):
+        term = np.ones((1, 1))
+        for m in range(d):
+            term = np.kron(term, L1 if m == k else np.eye(s))
+        K += term
+    np.testing.assert_array_equal(A, K)
+    mu = 2 - 2 * np.cos(np.arange(1, s + 1) * np.pi / (s + 1))
+    sums = np.sort([sum(c) for c in itertools.product(mu, repeat=d)])
+    np.testing.assert_allclose(np.linalg.eigvalsh(A), sums, atol=1e-12)
+
+
 @pytest.mark.parametrize("d,s", [(1, 5), (2, 4), (3, 3)])
 def test_laplacian_nnz_count(d, s):
     lap = synth.laplacian_tensor(d, s)
