@@ -450,7 +450,10 @@ def run_reference(args):
     times = []
     last = None
     for k in range(args.warmup + args.steps):
-        s = cpu_sample(args.cpu_iters)
+        # one BLAS thread, as the cpu_baseline object states
+        s = run_cpu_baseline_subprocess(args.cpu_iters)
+        if "error" in s:
+            return {"impl": "reference", "unavailable": f"oracle sample failed: {s['error']}"}
         if k >= args.warmup:
             times.append(s["est_solve_s"])
             last = s
