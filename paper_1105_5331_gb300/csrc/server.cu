@@ -142,7 +142,6 @@ struct cp_server {
       finish(sl, st);
       return;
     }
-    r->state = REQ_RUNNING;
   }
 
   void finish(Slot& sl, cp_status st) {
@@ -194,6 +193,7 @@ struct cp_server {
           if (!pending.empty() && used + pending.front()->footprint <= budget) {
             r = pending.front();
             pending.pop_front();
+            r->state = REQ_RUNNING;   // under the lock: a cancel from now on is refused
             used += r->footprint;
             peak = std::max(peak, used);
             ++running;
@@ -223,7 +223,14 @@ cp_status cp_server_create(cp_ctx* ctx, size_t hbm_budget_bytes, int max_active,
   s->max_active = max_active;
   CP_TRY(cp_ctx_create(ctx->device, nullptr, &s->wctx));
   s->slots.resize((size_t)max_active);
-  for (auto& sl : s->slots) CP_TRY(sl.res.create());
+  for (auto& sl : s->slots) {
+    const cp_status st = sl.res.create();
+    if (st != CP_OK) {   // release what was made (destroy skips what was not)
+      for (auto& q : s->slots) q.res.destroy();
+      cp_ctx_destroy(s->wctx);
+      return st;
+    }
+  }
   cp_server* raw = s.release();
   raw->worker = std::thread([raw]() { raw->loop(); });
   *out = raw;
