@@ -499,6 +499,110 @@ def test_linesearch_rejects_ascent_direction():
     assert O.more_thuente(quad_phi(1.0, 1.0), 0.0, 1.0)[-1] == -1
 
 
+# Trial selection of More-Thuente, case by case, against interpolants built
+# here by solving their interpolation conditions as linear systems.
+
+def hermite_cubic_min(a, fa, ga, b, fb, gb):
+    """Local minimiser of the cubic with p(a) = fa, p'(a) = ga, p(b) = fb,
+    p'(b) = gb, found from the roots of p' (None if p has none)."""
+    x = np.array([0.0, b - a])
+    V = np.array([[1, x[0], x[0] ** 2, x[0] ** 3], [0, 1, 2 * x[0], 3 * x[0] ** 2],
+                  [1, x[1], x[1] ** 2, x[1] ** 3], [0, 1, 2 * x[1], 3 * x[1] ** 2]])
+    c = np.linalg.solve(V, [fa, ga, fb, gb])
+    for r in np.roots([3 * c[3], 2 * c[2], c[1]]):
+        if abs(r.imag) < 1e-12 and 2 * c[2] + 6 * c[3] * r.real > 0:
+            return a + r.real
+    return None
+
+
+def quad_fgf_min(a, fa, ga, b, fb):
+    """Stationary point of the quadratic with q(a) = fa, q'(a) = ga, q(b) = fb."""
+    h = b - a
+    c = np.linalg.solve([[1, 0, 0], [0, 1, 0], [1, h, h * h]], [fa, ga, fb])
+    return a - c[1] / (2 * c[2])
+
+
+def secant_gg_root(a, ga, b, gb):
+    """Zero of the straight line through (a, ga) and (b, gb)."""
+    m, q = np.linalg.solve([[a, 1], [b, 1]], [ga, gb])
+    return -q / m
+
+
+@pytest.mark.parametrize("t", [(1.0, 0.5, 1.0), (1.0, 0.5, 3.0), (1.0, 3.0, -0.5), (-1.0, 0.7, -1.5)])
+def test_mt_trial_case1_higher_value(t):
+    """f_t > f_l: the minimum is bracketed; the cubic step if it is nearer
+    a_l than the quadratic one, else halfway from the cubic to the quadratic;
+    the new trial becomes the upper end."""
+    lo = (0.0, 0.0, -1.0) if t[0] > 0 else (0.0, 0.0, 1.0)
+    hi = (0.0, 0.0, -1.0)
+    nlo, nhi, nxt, brackt = O.mt_trial(lo, hi, t, False, 0.0, 10.0)
+    ac = hermite_cubic_min(*lo, *t)
+    aq = quad_fgf_min(*lo, t[0], t[1])
+    want = ac if abs(ac - lo[0]) < abs(aq - lo[0]) else ac + 0.5 * (aq - ac)
+    assert brackt and nlo == lo and nhi == t
+    assert nxt == pytest.approx(want, rel=1e-12, abs=1e-14)
+
+
+def test_mt_trial_case1_takes_both_branches():
+    """The case-1 examples above include one that takes the cubic step and
+    one that takes the midpoint, with the cubic and quadratic steps apart, so
+    that exchanging the two interpolants changes the result."""
+    lo = (0.0, 0.0, -1.0)
+    near = []
+    for t in [(1.0, 0.5, 1.0), (1.0, 0.5, 3.0)]:
+        ac, aq = hermite_cubic_min(*lo, *t), quad_fgf_min(*lo, t[0], t[1])
+        assert abs(ac - aq) > 1e-3
+        near.append(abs(ac - lo[0]) < abs(aq - lo[0]))
+    assert sorted(near) == [False, True]
+
+
+@pytest.mark.parametrize("t", [(1.0, -0.2, 0.5), (1.0, -0.6, 0.1), (2.0, -0.5, 3.0)])
+def test_mt_trial_case2_derivative_sign_change(t):
+    """f_t <= f_l, g_t g_l < 0: bracketed; of the cubic and secant steps the
+    one farther from a_t; a_t becomes the lower end and a_l the upper."""
+    lo, hi = (0.0, 0.0, -1.0), (5.0, 9.0, 1.0)
+    nlo, nhi, nxt, brackt = O.mt_trial(lo, hi, t, False, 0.0, 10.0)
+    ac = hermite_cubic_min(*lo, *t)
+    asec = secant_gg_root(lo[0], lo[2], t[0], t[2])
+    want = ac if abs(ac - t[0]) >= abs(asec - t[0]) else asec
+    assert brackt and nlo == t and nhi == lo
+    assert nxt == pytest.approx(want, rel=1e-12, abs=1e-14)
+
+
+@pytest.mark.parametrize("t,brackt", [((1.0, -0.8, -0.3), False), ((1.0, -0.8, -0.3), True),
+                                      ((1.0, -0.55, -0.9), False), ((0.5, -0.4, -0.6), True)])
+def test_mt_trial_case3_derivative_decreases(t, brackt):
+    """f_t <= f_l, same sign, |g_t| <= |g_l|: the cubic step if it lies beyond
+    a_t (else the far bound); not bracketed: the farther of cubic and secant,
+    clipped to [stmin, stmax]; bracketed: the nearer, at most 0.66 of the way
+    to the upper end."""
+    lo, hi, stmax = (0.0, 0.0, -1.0), (2.0, 1.0, 1.0), 10.0
+    nlo, nhi, nxt, b2 = O.mt_trial(lo, hi, t, brackt, 0.0, stmax)
+    ac = hermite_cubic_min(*lo, *t)
+    if ac is None or ac <= t[0]:
+        ac = stmax
+    asec = secant_gg_root(lo[0], lo[2], t[0], t[2])
+    if brackt:
+        want = ac if abs(ac - t[0]) < abs(asec - t[0]) else asec
+        want = min(t[0] + 0.66 * (hi[0] - t[0]), want)
+    else:
+        want = ac if abs(ac - t[0]) > abs(asec - t[0]) else asec
+        want = min(stmax, max(0.0, want))
+    assert b2 == brackt and nlo == t and nhi == hi
+    assert nxt == pytest.approx(want, rel=1e-12, abs=1e-14)
+
+
+def test_mt_trial_case4_derivative_does_not_decrease():
+    """f_t <= f_l, same sign, |g_t| > |g_l|: not bracketed -> the far bound;
+    bracketed -> the cubic step between a_t and the upper end."""
+    lo, t = (0.0, 0.0, -1.0), (1.0, -2.0, -1.5)
+    assert O.mt_trial(lo, (0.0, 0.0, -1.0), t, False, 0.0, 10.0)[2] == 10.0
+    hi = (3.0, 1.0, 2.0)
+    nlo, nhi, nxt, brackt = O.mt_trial(lo, hi, t, True, 0.0, 10.0)
+    assert nlo == t and nhi == hi and brackt
+    assert nxt == pytest.approx(hermite_cubic_min(*t, *hi), rel=1e-12)
+
+
 # --------------------------------------------------------------------------
 # COO sort and segmentation
 # --------------------------------------------------------------------------
