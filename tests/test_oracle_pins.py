@@ -795,6 +795,58 @@ def test_solve_window_grows_to_w_and_slides(monkeypatch):
     assert resets in (rep.restarts, rep.restarts - 1)
 
 
+def test_solve_loop_structure_of_algorithm_1(monkeypatch):
+    """What Algorithm 1 with the readings R6, R8 fixes about the loop, checked
+    on every call of Step II and Step III: the window's newest point is the
+    iterate the ALS step (Step I) started from, the window slides by one, every
+    point in it and every accelerated iterate is normalised (a fixed point of
+    the normalisation), and the search starts at the ALS iterate."""
+    rng = synth.rng_for(91)
+    prob = synth.dense_problem(rng, (8, 7, 9), 3, 0.9)
+    dims, R = prob.dims, 3
+    X = O.DenseTensor(prob.T)
+    u0 = synth.initial_guess(rng, dims, R)
+    real_step, real_search = O.ngmres_step, O.more_thuente
+    calls, searches = [], []
+
+    def recording_step(U, G, ubar, gbar, eps=1e-12):
+        calls.append((np.array(U, copy=True), ubar.copy()))
+        return real_step(U, G, ubar, gbar, eps)
+
+    def recording_search(phi, f0, g0, opts=O.LSOpts()):
+        f_at_0, _, (x0, _) = phi(0.0)
+        _, _, (x1, _) = phi(1.0)
+        searches.append((x0, x1, f0, f_at_0))
+        return real_search(phi, f0, g0, opts)
+
+    monkeypatch.setattr(O, "ngmres_step", recording_step)
+    monkeypatch.setattr(O, "more_thuente", recording_search)
+    w, iters = 3, 14
+    _, _, rep = O.cp_solve(X, u0, O.SolveOpts(R=R, w=w, tol=0.0, maxit=iters))
+    assert rep.iters == iters and len(searches) == iters - rep.restarts >= 4
+
+    def is_normalised(v):
+        return np.allclose(O.normalize(v, dims, R)[0], v, rtol=1e-11, atol=1e-13 * np.abs(v).max())
+
+    for U, ubar in calls:
+        assert all(is_normalised(row) for row in U)
+        ubar_from_newest, _, _ = O.normalize(O.als_sweep(X, U[-1], R), dims, R)
+        np.testing.assert_allclose(ubar, ubar_from_newest, rtol=1e-12, atol=1e-13 * np.abs(ubar).max())
+    slid = 0
+    for (U, _), (V, _) in zip(calls, calls[1:]):
+        if len(V) == 1:
+            continue                                     # a restart
+        keep = U[1:] if len(U) == w else U
+        np.testing.assert_array_equal(V[:-1], keep)
+        slid += len(U) == w
+    assert slid >= 1
+    ubars = {c[1].tobytes() for c in calls}
+    for x0, x1, f0, f_at_0 in searches:
+        assert x0.tobytes() in ubars                      # beta = 0 is the ALS iterate
+        assert f_at_0 == pytest.approx(f0, rel=1e-13)
+        assert is_normalised(x1)                          # beta = 1 is the normalised uhat
+
+
 def test_ngmres_beats_als_on_collinear_problem():
     rng = synth.rng_for(95)
     prob = synth.dense_problem(rng, (15, 15, 15), 3, 0.9, paper_l1=1, paper_l2=1)
