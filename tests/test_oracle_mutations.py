@@ -64,6 +64,21 @@ MUTATIONS = [
      "ac = _cubic_min(at, ft, gt, au, fu, gu)", "ac = _cubic_min(al, fl, gl, au, fu, gu)"),
     ("interval update sign",
      "if gt * (al - at) < 0.0:", "if gt * (al - at) > 0.0:"),
+    ("line search without the psi stage",
+     "if stage == 1 and f <= lo[1] and f > ftest:", "if False:"),
+    ("sufficient decrease with the wrong sign",
+     "ftest = f0 + stp * ftol * g0", "ftest = f0 - stp * ftol * g0"),
+    ("curvature condition without the absolute value",
+     "if f <= ftest and abs(g) <= gtol * (-g0):", "if f <= ftest and g <= gtol * (-g0):"),
+    ("extrapolation upper limit of 2 steps",
+     "xhi = stp + 4.0 * (stp - lo[0])", "xhi = stp + 2.0 * (stp - lo[0])"),
+    ("extrapolation lower limit of 1 step",
+     "xlo = stp + 1.1 * (stp - lo[0])", "xlo = stp + 1.0 * (stp - lo[0])"),
+    ("one evaluation more than maxfev",
+     "if nfev >= opts.maxfev:", "if nfev > opts.maxfev:"),
+    ("lower end mapped back from psi without the ftol term",
+     "lo = (lo_m[0], lo_m[1] + f0 + lo_m[0] * ftol * g0, lo_m[2] + ftol * g0)",
+     "lo = (lo_m[0], lo_m[1] + f0, lo_m[2] + ftol * g0)"),
 ]
 
 

@@ -495,6 +495,137 @@ def test_linesearch_strong_wolfe_on_published_test_functions(case, a0):
     assert nfev <= 20
 
 
+def record_trials(phi):
+    trials = []
+
+    def rec(a):
+        out = phi(a)
+        trials.append(a)
+        return out
+    return rec, trials
+
+
+def test_linesearch_extrapolates_by_four_steps_until_maxfev_or_stpmax():
+    """On phi(b) = -b the slope never flattens, so every trial extrapolates
+    to the upper limit a_t + 4 (a_t - a_l): trials (4^k - 1) / 3 until
+    maxfev ends the search (info 3), or stpmax is reached with sufficient
+    decrease and the slope still below ftol phi'(0) (info 5)."""
+    lin = lambda a: (-a, -1.0, None)
+    rec, trials = record_trials(lin)
+    beta, _, _, _, nfev, info = O.more_thuente(rec, 0.0, -1.0, O.LSOpts(maxfev=5))
+    assert trials == [1.0, 5.0, 21.0, 85.0, 341.0] and (beta, nfev, info) == (341.0, 5, 3)
+    rec, trials = record_trials(lin)
+    beta, _, _, _, nfev, info = O.more_thuente(rec, 0.0, -1.0, O.LSOpts(stpmax=100.0))
+    assert trials == [1.0, 5.0, 21.0, 85.0, 100.0] and (beta, nfev, info) == (100.0, 5, 5)
+
+
+def test_linesearch_extrapolates_at_least_1_1_steps():
+    """phi(b) = (b - 1.05)^2 - 1.05^2: after the unit trial both the cubic and
+    the secant step point to the minimiser 1.05, inside the unbracketed lower
+    limit a_t + 1.1 (a_t - a_l) = 2.1, so the next trial is 2.1."""
+    phi = lambda a: ((a - 1.05) ** 2 - 1.05 ** 2, 2 * (a - 1.05), None)
+    rec, trials = record_trials(phi)
+    O.more_thuente(rec, 0.0, -2.1)
+    assert trials[:2] == [1.0, pytest.approx(2.1, rel=1e-15)]
+
+
+def test_linesearch_first_stage_works_on_psi():
+    """phi(b) = -b + a b^2 + c b^3 with phi(1) between phi(0) + ftol phi'(0)
+    and phi(0): phi is lower at 1 than at 0 (case 3 for phi, extrapolation
+    beyond 2.1) but psi(b) = phi(b) - phi(0) - ftol b phi'(0) is higher
+    (case 1 for psi), so the first stage must bracket in (0, 1) with the case-1
+    step of psi."""
+    mu = 1e-4
+    c = 0.5 - 2 * (1 - 0.5e-4)
+    a = (1 - 0.5e-4) - c
+    phi = lambda b: (-b + a * b * b + c * b ** 3, -1 + 2 * a * b + 3 * c * b * b, None)
+    f1, g1, _ = phi(1.0)
+    assert f1 == pytest.approx(-0.5e-4) and g1 == pytest.approx(-0.5)
+    rec, trials = record_trials(phi)
+    O.more_thuente(rec, 0.0, -1.0, O.LSOpts(ftol=mu))
+    lo = (0.0, 0.0, -1.0 + mu)
+    t = (1.0, f1 + mu, g1 + mu)
+    ac = hermite_cubic_min(*lo, *t)
+    aq = quad_fgf_min(*lo, t[0], t[1])
+    want = ac if abs(ac) < abs(aq) else ac + 0.5 * (aq - ac)
+    assert 0 < want < 1 and trials[1] == pytest.approx(want, rel=1e-12)
+
+
+def psi_step_quartic():
+    """The quartic with phi(0) = 0, phi'(0) = -1, phi(1) = -0.2, phi'(1) = -0.5,
+    phi(5) = -0.25, searched with ftol = gtol = 0.1: the unit trial lies
+    below the sufficient-decrease line and is still steep, so the search
+    extrapolates to 5, where phi is above that line but below phi(1); the
+    trial after it is chosen in the first stage (psi) with the lower end at 1,
+    the one path on which the lower end is mapped back from psi."""
+    A = np.array([[1, 0, 0, 0, 0], [0, 1, 0, 0, 0], [1, 1, 1, 1, 1], [0, 1, 2, 3, 4],
+                  [1, 5, 25, 125, 625]], dtype=float)
+    P = np.polynomial.Polynomial(np.linalg.solve(A, [0, -1, -0.2, -0.5, -0.25]))
+    dP = P.deriv()
+    return (lambda a: (float(P(a)), float(dP(a)))), 0.1, 0.1
+
+
+@pytest.mark.parametrize("case", range(7))
+@pytest.mark.parametrize("a0", [1e-3, 1e-1, 1e0, 1e1, 1e3])
+def test_linesearch_interval_ends_are_evaluated_points(monkeypatch, case, a0):
+    """Every point handed to the trial selection (the two ends and the new
+    trial) is an evaluated trial or 0 with its own phi and phi' (or, all three
+    together, psi and psi' in the first stage)."""
+    fn, mu, eta = (mt_test_functions() + [psi_step_quartic()])[case]
+    f0, g0 = fn(0.0)
+    seen = {0.0: (f0, g0)}
+
+    def phi(a):
+        v, d = fn(a)
+        seen[a] = (v, d)
+        return v, d, None
+
+    real, checked = O.mt_trial, []
+
+    def checking_trial(lo, hi, t, brackt, stmin, stmax):
+        forms = []
+        for a, v, d in (lo, hi, t):
+            fv, fd = seen[a]
+            if v == fv and d == fd:
+                forms.append("phi")
+            elif v == pytest.approx(fv - f0 - a * mu * g0, rel=1e-12, abs=1e-15) and \
+                    d == pytest.approx(fd - mu * g0, rel=1e-12, abs=1e-15):
+                forms.append("psi")
+            else:
+                forms.append("neither")
+        assert len(set(forms)) == 1 and forms[0] != "neither", (lo, hi, t, forms)
+        checked.append(forms[0])
+        return real(lo, hi, t, brackt, stmin, stmax)
+
+    monkeypatch.setattr(O, "mt_trial", checking_trial)
+    O.more_thuente(phi, f0, g0, O.LSOpts(ftol=mu, gtol=eta, stp0=a0, maxfev=40, xtol=1e-12))
+
+
+def test_linesearch_interval_checks_reach_the_first_stage():
+    """Across the cases above the first stage (psi) and the second (phi) are
+    both exercised, and the quartic takes a psi step with its lower end away
+    from 0, so the check above covers the mapping back from psi."""
+    forms = set()
+    for fn, mu, eta in mt_test_functions() + [psi_step_quartic()]:
+        for a0 in [1e-3, 1e-1, 1e0, 1e1, 1e3]:
+            f0, g0 = fn(0.0)
+            real = O.mt_trial
+            try:
+                def spy(lo, hi, t, brackt, stmin, stmax):
+                    a, v, _ = t
+                    if v == fn(a)[0]:
+                        forms.add("phi")
+                    else:
+                        forms.add("psi, lower end at 0" if lo[0] == 0.0 else "psi, lower end inside")
+                    return real(lo, hi, t, brackt, stmin, stmax)
+                O.mt_trial = spy
+                O.more_thuente(lambda a: (*fn(a), None), f0, g0,
+                               O.LSOpts(ftol=mu, gtol=eta, stp0=a0, maxfev=40, xtol=1e-12))
+            finally:
+                O.mt_trial = real
+    assert forms == {"phi", "psi, lower end at 0", "psi, lower end inside"}
+
+
 def test_linesearch_rejects_ascent_direction():
     assert O.more_thuente(quad_phi(1.0, 1.0), 0.0, 1.0)[-1] == -1
 
