@@ -233,8 +233,9 @@ void cp_ls_opts_default(cp_ls_opts* o);
  * polynomial, equal to f0 and g0^T d up to rounding.  On return
  * x = x0 + stp d and f, g are evaluated there (x, g device; f, stp, nfev,
  * info host; nfev counts trials).  info as in More-Thuente: 1 strong Wolfe
- * met, 2 xtol, 3 maxfev, 4 stpmin, 5 stpmax, 6 rounding; if phi'(0) >= 0
- * returns CP_ERR_LINESEARCH.  Synchronous. */
+ * met, 2 xtol, 3 maxfev, 4 stpmin, 5 stpmax, 6 rounding; and 7 when a trial's
+ * phi or phi' is not finite (the search stops at that trial); if
+ * phi'(0) >= 0 returns CP_ERR_LINESEARCH.  Synchronous. */
 cp_status linesearch(cp_ctx* ctx, const cp_tensor* t, int R, const double* x0, double f0,
                      const double* g0, const double* d, const cp_ls_opts* opts, double* x,
                      double* f, double* g, double* stp, int* nfev, int* info,
