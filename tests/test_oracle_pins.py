@@ -978,6 +978,23 @@ def test_solve_loop_structure_of_algorithm_1(monkeypatch):
         assert is_normalised(x1)                          # beta = 1 is the normalised uhat
 
 
+@pytest.mark.parametrize("d,s,R", [(3, 4, 2), (4, 4, 2)])
+def test_solve_test_problem_2_shapes_reach_an_als_fixed_point(d, s, R):
+    """Test Problem II at the paper's N = 6 and N = 8 sizes (s = 4, R = 2,
+    Tables 4-6): the solve converges with f non-increasing, and where the
+    gradient vanishes every ALS mode solve returns its own factor, so the
+    solution is a fixed point of the normalised ALS step."""
+    lap = synth.laplacian_tensor(d, s)
+    X = O.SparseTensor(lap.coords, lap.vals, lap.dims)
+    u0 = synth.initial_guess(synth.rng_for(89), lap.dims, R)
+    u, g, rep = O.cp_solve(X, u0, O.SolveOpts(R=R, tol=1e-10, maxit=3000))
+    assert rep.converged
+    fs = [h[0] for h in rep.history]
+    assert all(b <= a * (1 + 1e-12) + 1e-14 for a, b in zip(fs, fs[1:]))
+    v, _, _ = O.normalize(O.als_sweep(X, u, R), lap.dims, R)
+    assert np.linalg.norm(v - u) <= 1e-9 * np.linalg.norm(u)
+
+
 def test_ngmres_beats_als_on_collinear_problem():
     rng = synth.rng_for(95)
     prob = synth.dense_problem(rng, (15, 15, 15), 3, 0.9, paper_l1=1, paper_l2=1)
