@@ -282,6 +282,29 @@ def test_als_mode_updates_decrease_f_and_zero_the_mode_gradient():
     np.testing.assert_allclose(u1, O.pack(F2), rtol=1e-12)
 
 
+def test_gradient_vanishes_at_an_als_fixed_point():
+    """Plain ALS (one sweep and a normalisation per step) run until it stops
+    moving reaches a point where every mode solve returns its own factor, so
+    each G^(n) = -M^(n) + A^(n) Gammabar^(n) is zero there: the gradient, built
+    independently of the ALS solves, must vanish up to rounding."""
+    rng = synth.rng_for(88)
+    prob = synth.dense_problem(rng, (9, 8, 7), 3, 0.5, eta=0.1)
+    X = O.DenseTensor(prob.T)
+    R = 3
+    u, _, _ = O.normalize(synth.initial_guess(rng, prob.dims, R), prob.dims, R)
+    for _ in range(2000):
+        v, _, _ = O.normalize(O.als_sweep(X, u, R), prob.dims, R)
+        step = np.linalg.norm(v - u) / np.linalg.norm(u)
+        u = v
+        if step < 1e-14:
+            break
+    assert step < 1e-14
+    _, g = O.fg(X, u, R)
+    F = O.unpack(u, prob.dims, R)
+    Mnorm = np.linalg.norm(O.pack([X.mttkrp(F, n) for n in range(3)]))
+    assert np.linalg.norm(g) <= 1e-12 * Mnorm
+
+
 def test_als_recovers_noise_free_planted_tensor():
     rng = np.random.default_rng(10)
     prob = synth.dense_problem(rng, (10, 9, 8), 3, 0.3)
