@@ -23,6 +23,18 @@ MUTATIONS = [
     ("ALS as Jacobi (old factors in every mode)",
      "        M = X.mttkrp(factors, n)\n        factors[n] = als_mode_solve",
      "        M = X.mttkrp(unpack(np.array(u, dtype=np.float64), X.dims, R), n)\n        factors[n] = als_mode_solve"),
+    ("dense MTTKRP pairs the factors with the wrong modes",
+     'expr = letters + "," + ",".join(letters[m] + "z" for m in others)',
+     'expr = letters + "," + ",".join(letters[m] + "z" for m in reversed(others))'),
+    ("COO sort key in the wrong order",
+     "perm = np.lexsort(tuple(coords[:, m] for m in reversed(key_modes))).astype(np.int64)",
+     "perm = np.lexsort(tuple(coords[:, m] for m in key_modes)).astype(np.int64)"),
+    ("COO segment pointers end one short",
+     "seg_ptr = np.concatenate([starts, [rows.size]]).astype(np.int64)",
+     "seg_ptr = np.concatenate([starts, [rows.size - 1]]).astype(np.int64)"),
+    ("Gamma leaves out the last mode",
+     "    for G in grams(factors):\n        out = out * G",
+     "    for G in grams(factors)[:-1]:\n        out = out * G"),
     ("sparse MTTKRP gathers the output mode",
      "w = w * factors[m][coords[:, m]]", "w = w * factors[m][coords[:, n]]"),
     ("normalisation orders by increasing lambda",
