@@ -60,3 +60,18 @@ def test_no_gpu_means_a_cuda_error_not_a_fallback():
     with pytest.raises(cp.CpError) as ei:
         cp.cp_ctx_create(0)
     assert ei.value.status in (1, 4)
+
+
+def test_package_without_its_library_fails_to_import(tmp_path):
+    """A copy of the package without the built library must refuse to import
+    (no CPU fallback path exists)."""
+    import shutil
+    import subprocess
+    import sys
+    src = os.path.join(ROOT, "paper_1105_5331_gb300")
+    dst = tmp_path / "paper_1105_5331_gb300"
+    shutil.copytree(src, dst, ignore=shutil.ignore_patterns("*.so", "_build", "__pycache__", "csrc"))
+    r = subprocess.run([sys.executable, "-c", "import paper_1105_5331_gb300"], cwd=tmp_path,
+                       capture_output=True, text=True, env=dict(os.environ, PYTHONPATH=str(tmp_path)))
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "no CPU fallback" in r.stderr
