@@ -27,6 +27,10 @@
  *    cp_last_error() gives a message for the calling thread's last failure.
  *    Arguments are validated before any work is enqueued.
  *  Threads.  A context may be used by one thread at a time.
+ *  Devices.  A call that takes a context makes the context's device current
+ *    on the calling thread and leaves it current.  A tensor handle belongs to
+ *    the device of the context it was created with; passing it with a
+ *    context of another device fails with CP_ERR_ARG.
  */
 #ifndef CP_GB300_H
 #define CP_GB300_H

@@ -400,15 +400,22 @@ void cp_tensor_destroy(cp_tensor* t) {
   cudaStreamSynchronize(cudaStreamLegacy);
 }
 
-static cp_status check_tensor_R(const cp_tensor* t, int R) {
+// The tensor must live on the context's device: its copies are device
+// arrays of the device it was created on, and a kernel on another device
+// would read that device's memory.
+static cp_status check_tensor_R(const cp_ctx* ctx, const cp_tensor* t, int R) {
   CP_NULLCHECK(t);
+  if (ctx && t->device != ctx->device) {
+    set_error("tensor on device %d, context on device %d", t->device, ctx->device);
+    return CP_ERR_ARG;
+  }
   return check_R(R);
 }
 
 cp_status cp_mttkrp(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, int mode, double* out,
                     cp_precision prec) {
   CP_NULLCHECK(ctx);
-  CP_TRY(check_tensor_R(t, R));
+  CP_TRY(check_tensor_R(ctx, t, R));
   CP_NULLCHECK(u);
   CP_NULLCHECK(out);
   if (mode < 0 || mode >= t->N) {
@@ -428,7 +435,7 @@ cp_status cp_mttkrp(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, int
 cp_status cp_mttkrp_variants(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, const double* d,
                              const int* modes, int nmodes, double* out, cp_precision prec) {
   CP_NULLCHECK(ctx);
-  CP_TRY(check_tensor_R(t, R));
+  CP_TRY(check_tensor_R(ctx, t, R));
   CP_NULLCHECK(u);
   CP_NULLCHECK(d);
   CP_NULLCHECK(modes);
@@ -461,7 +468,7 @@ cp_status cp_mttkrp_variants(cp_ctx* ctx, const cp_tensor* t, int R, const doubl
 cp_status cp_fg(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, double* f, double* g,
                 cp_precision prec) {
   CP_NULLCHECK(ctx);
-  CP_TRY(check_tensor_R(t, R));
+  CP_TRY(check_tensor_R(ctx, t, R));
   CP_NULLCHECK(u);
   CP_NULLCHECK(f);
   CP_TRY(use_device(ctx));
@@ -473,7 +480,7 @@ cp_status cp_fg(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, double*
 cp_status cp_als_sweep(cp_ctx* ctx, const cp_tensor* t, int R, double* u, int normalize,
                        cp_precision prec) {
   CP_NULLCHECK(ctx);
-  CP_TRY(check_tensor_R(t, R));
+  CP_TRY(check_tensor_R(ctx, t, R));
   CP_NULLCHECK(u);
   CP_TRY(use_device(ctx));
   Layout L;
@@ -569,7 +576,7 @@ cp_status linesearch(cp_ctx* ctx, const cp_tensor* t, int R, const double* x0, d
                      const double* g0, const double* d, const cp_ls_opts* opts, double* x,
                      double* f, double* g, double* stp, int* nfev, int* info, cp_precision prec) {
   CP_NULLCHECK(ctx);
-  CP_TRY(check_tensor_R(t, R));
+  CP_TRY(check_tensor_R(ctx, t, R));
   CP_NULLCHECK(x0);
   CP_NULLCHECK(g0);
   CP_NULLCHECK(d);
@@ -634,7 +641,7 @@ cp_status cp_solve(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* opts, d
                    cp_solve_report* rep) {
   CP_NULLCHECK(ctx);
   CP_NULLCHECK(opts);
-  CP_TRY(check_tensor_R(t, opts->R));
+  CP_TRY(check_tensor_R(ctx, t, opts->R));
   CP_NULLCHECK(u);
   if (opts->w < 1 || opts->w > CP_MAX_W) {
     set_error("cp_solve: window w = %d outside [1, %d]", opts->w, CP_MAX_W);

@@ -295,6 +295,10 @@ extern "C" cp_status cp_mttkrp_noalloc(cp_ctx* ctx, const cp_tensor* t, int R, c
     set_error("cp_mttkrp_noalloc: dense tensors only");
     return CP_ERR_UNSUPPORTED;
   }
+  if (t->device != ctx->device) {
+    set_error("cp_mttkrp_noalloc: tensor on device %d, context on device %d", t->device, ctx->device);
+    return CP_ERR_ARG;
+  }
   if (R < 1 || R > CP_MAX_R || mode < 0 || mode >= t->N) {
     set_error("cp_mttkrp_noalloc: R = %d or mode = %d out of range", R, mode);
     return CP_ERR_ARG;

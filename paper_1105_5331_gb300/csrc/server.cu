@@ -386,8 +386,11 @@ cp_status cp_solve_batch(cp_ctx* ctx, int nreq, const cp_tensor* const* tensors,
   std::vector<bool> dev((size_t)nreq);
   cp_status first = CP_OK;
   for (int i = 0; i < nreq; ++i) {
-    if (!tensors[i] || !u[i]) {
-      if (first == CP_OK) first = CP_ERR_ARG;
+    if (!tensors[i] || !u[i] || tensors[i]->device != ctx->device) {
+      if (first == CP_OK) {
+        set_error("cp_solve_batch: request %d: null tensor or iterate, or tensor on another device", i);
+        first = CP_ERR_ARG;
+      }
       continue;
     }
     dev[i] = on_device(u[i]);

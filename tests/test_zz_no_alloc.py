@@ -57,6 +57,31 @@ def test_noalloc_matches_cp_mttkrp_twice(cp, shape, R, dtype):
     ctx.close()
 
 
+def test_noalloc_fewer_ctas_when_the_scratch_is_the_limit(cp):
+    """4000 rows at R = 64 make one partial block 2 048 000 bytes, so only
+    four blocks fit the 8 MiB scratch: the split-K grid shrinks to four CTAs,
+    each taking a quarter of the contraction, instead of two per SM."""
+    ctx = cp.cp_ctx_create(0, torch.cuda.current_stream())
+    shape, R = (4000, 40, 40), 64
+    assert (8 << 20) // (shape[0] * R * 8) == 4
+    rng = np.random.default_rng(4000)
+    T = rng.standard_normal(shape).astype(np.float32)
+    u = torch.from_numpy(synth.initial_guess(rng, shape, R)).cuda()
+    t = cp.cp_tensor_dense(ctx, torch.from_numpy(T).cuda())
+    oracle = O.mttkrp_dense(T.astype(np.float64), O.unpack(u.cpu().numpy(), shape, R), 0).ravel()
+    for call in range(2):
+        ref = torch.empty(shape[0] * R, dtype=torch.float64, device="cuda")
+        got = torch.full_like(ref, float("nan"))
+        cp.cp_mttkrp(ctx, t, R, u, 0, ref)
+        cp.cp_mttkrp_noalloc(ctx, t, R, u, 0, got)
+        cp.cp_ctx_sync(ctx)
+        a = got.cpu().numpy()
+        assert rel(a, ref.cpu().numpy()) <= TOL, call
+        assert rel(a, oracle) <= TOL, call
+    t.close()
+    ctx.close()
+
+
 def test_noalloc_rejects_rows_beyond_the_scratch(cp):
     ctx = cp.cp_ctx_create(0, torch.cuda.current_stream())
     # one partial block of I x R doubles must fit in the 8 MiB scratch
