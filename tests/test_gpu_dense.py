@@ -233,6 +233,102 @@ def test_linesearch_parity(cp, ctx, direction):
     assert rel(g.cpu().numpy(), extra[1]) <= TOL
 
 
+def solve_line_searches(X, u0, R):
+    """(ubar, d, f(ubar), g(ubar)) of every line search of the oracle's
+    solve of the 20x20x20 workload (Algorithm 1, Step III)."""
+    found = []
+    real = O.more_thuente
+
+    def capture(phi, f0, g0, opts=O.LSOpts()):
+        cells = dict(zip(phi.__code__.co_freevars, (c.cell_contents for c in phi.__closure__)))
+        found.append((cells["ubar"], cells["d"]))
+        return real(phi, f0, g0, opts)
+    O.more_thuente = capture
+    try:
+        O.cp_solve(X, u0, O.SolveOpts(R=R, tol=1e-7))
+    finally:
+        O.more_thuente = real
+    return [(ub, d, *O.fg(X, ub, R)) for ub, d in found]
+
+
+def mt_events(phi, f0, g0, opts):
+    """Run the oracle's search and name what chose each trial after the
+    first: 'sel' (the trial selection's step), 'bisect' (midpoint of a
+    bracket that shrank too slowly) or 'fallback' (the best point, when no
+    further progress is possible); also return info."""
+    real, pending, events = O.mt_trial, {}, []
+
+    def spy(lo, hi, t, brackt, stmin, stmax):
+        pending["sel"] = real(lo, hi, t, brackt, stmin, stmax)
+        return pending["sel"]
+
+    def rec(a):
+        if "sel" in pending:
+            lo, hi, nxt, _ = pending.pop("sel")
+            if a == min(max(nxt, opts.stpmin), opts.stpmax):
+                events.append("sel")
+            elif a == lo[0]:
+                events.append("fallback")
+            elif a == lo[0] + 0.5 * (hi[0] - lo[0]):
+                events.append("bisect")
+        return phi(a)
+    O.mt_trial = spy
+    try:
+        out = O.more_thuente(rec, f0, g0, opts)
+    finally:
+        O.mt_trial = real
+    return out, events
+
+
+# (line search of the solve, options, what must happen): options under which
+# the workload's own line searches take each driver rule and each exit code
+LS_CASES = [
+    (11, dict(gtol=1e-6, stp0=9.827, stpmax=12.653), "bisect"),
+    (10, dict(ftol=0.1, stp0=43.869, stpmax=15.443), "bisect"),
+    (11, dict(ftol=0.3, gtol=0.9, xtol=1e-6, stp0=0.423, stpmin=0.1, stpmax=0.3), "bisect"),
+    (1, dict(xtol=0.8), "fallback"),
+    (1, dict(xtol=0.8), "info2"),
+    (0, dict(maxfev=2, gtol=1e-6), "info3"),
+    (0, dict(stpmin=1e3, stp0=1e3), "info4"),
+    (0, dict(stpmax=0.05), "info5"),
+    (2, dict(ftol=0.45, gtol=1e-8, xtol=1e-10, stp0=0.1962), "info6"),
+    (10, dict(ftol=0.45, gtol=1e-8, xtol=1e-6, stp0=0.5303, stpmax=10.0), "info6"),
+]
+
+
+@pytest.mark.parametrize("k,opt,what", LS_CASES, ids=[f"{c[2]}-ls{c[0]}" for c in LS_CASES])
+def test_linesearch_parity_every_driver_rule(cp, ctx, k, opt, what):
+    """The GPU search (on the line polynomial of phi) against the oracle's
+    search (f and g at every trial) on the solve's own search lines, with
+    options that make each More-Thuente driver rule and exit code happen:
+    identical nfev and info, stp, f, x and g within 1e-10."""
+    prob, u0 = synth.workload_dense_small()
+    R = 3
+    X = O.DenseTensor(prob.T)
+    ub, d, fb, gb = solve_line_searches(X, u0, R)[k]
+    ls = O.LSOpts(**opt)
+
+    def phi(beta):
+        x = ub + beta * d
+        fx, gx = O.fg(X, x, R)
+        return fx, float(gx @ d), (x, gx)
+
+    (b, fo, _, extra, nfo, info_o), events = mt_events(phi, fb, float(gb @ d), ls)
+    assert (what in events) if what in ("bisect", "fallback") else info_o == int(what[4:]), (events, info_o)
+    co = cp.cp_ls_opts()
+    for name in ("ftol", "gtol", "xtol", "stpmin", "stpmax", "stp0", "maxfev"):
+        setattr(co, name, getattr(ls, name))
+    t = cp.cp_tensor_dense(ctx, dev(prob.T))
+    x = torch.empty(ub.size, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(x)
+    f, stp, nfev, info = cp.linesearch(ctx, t, R, dev(ub), fb, dev(gb), dev(d), x, g, co)
+    assert (nfev, info) == (nfo, info_o)
+    assert abs(stp - b) <= TOL * abs(b)
+    assert abs(f - fo) <= TOL * abs(fo)
+    assert rel(x.cpu().numpy(), extra[0]) <= TOL
+    assert rel(g.cpu().numpy(), extra[1]) <= TOL
+
+
 def test_linesearch_rejects_ascent(cp, ctx):
     prob, u0 = synth.workload_dense_small()
     X = O.DenseTensor(prob.T)

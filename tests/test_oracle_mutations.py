@@ -91,7 +91,19 @@ MUTATIONS = [
     ("lower end mapped back from psi without the ftol term",
      "lo = (lo_m[0], lo_m[1] + f0 + lo_m[0] * ftol * g0, lo_m[2] + ftol * g0)",
      "lo = (lo_m[0], lo_m[1] + f0, lo_m[2] + ftol * g0)"),
+    ("no bisection of a bracket that shrinks too slowly",
+     "if abs(hi[0] - lo[0]) >= 0.66 * width1:", "if False:"),
+    ("no fall-back to the best point when no progress is possible",
+     "or imax - imin <= xtol * imax):\n            stp = lo[0]",
+     "or imax - imin <= xtol * imax):\n            pass"),
+    ("second stage entered without the slope condition",
+     "if stage == 1 and f <= ftest and g >= min(ftol, gtol) * g0:", "if stage == 1 and f <= ftest:"),
 ]
+# Removing the switch to the second stage altogether is an equivalent
+# mistake, not planted here: after the first trial with psi <= 0 and
+# phi' >= min(ftol, gtol) phi'(0) no later trial can be both no higher than
+# the best point and above the sufficient-decrease line, so the first stage's
+# step on psi is never taken again (test_linesearch_first_stage_cannot_return_after_the_switch).
 
 
 @pytest.mark.slow

@@ -653,6 +653,87 @@ def test_linesearch_rejects_ascent_direction():
     assert O.more_thuente(quad_phi(1.0, 1.0), 0.0, 1.0)[-1] == -1
 
 
+def poly_phi(coeffs):
+    """phi(b) = -b + b^2 (c0 + c1 b + c2 b^2 + ...): phi(0) = 0, phi'(0) = -1."""
+    P = np.polynomial.Polynomial([0.0, -1.0] + [float(c) for c in coeffs])
+    dP = P.deriv()
+    return lambda a: (float(P(a)), float(dP(a)))
+
+
+def test_linesearch_bisects_a_bracket_that_shrinks_too_slowly():
+    """phi = -b + 18 b^2 - 16 b^3 + 20 b^4 - 17 b^5: phi(1) = 4 > phi(0), so
+    the unit trial brackets the minimum in [0, 1].  The next two trials are
+    lower, still descending points near 0, each becoming the lower end while
+    1 stays the upper end.  After the third trial the bracket [a_3, 1] is
+    still wider than 0.66 times the bracket two trials earlier ([0, 1]), so
+    More and Thuente's safeguard replaces the interpolated step by the
+    midpoint of the bracket."""
+    fn = poly_phi([18, -16, 20, -17])
+    rec, trials = record_trials(lambda a: (*fn(a), None))
+    O.more_thuente(rec, 0.0, -1.0)
+    a2, a3 = trials[1], trials[2]
+    assert fn(1.0)[0] > 0.0
+    for prev, a in ((0.0, a2), (a2, a3)):
+        assert fn(a)[0] < fn(prev)[0] and fn(a)[1] < 0.0 and 0.0 < a < 1.0
+    assert 1.0 - a3 >= 0.66 * 1.0
+    assert trials[3] == pytest.approx(a3 + 0.5 * (1.0 - a3), rel=1e-15)
+
+
+def test_linesearch_returns_the_best_point_once_the_interval_is_below_xtol():
+    """phi = -b + 5 b^6 with xtol = 0.8: phi(1) = 4 > 0 brackets the minimum
+    in [0, 1]; the second trial is lower and still descending, so the bracket
+    becomes [a_2, 1], whose width 1 - a_2 is below xtol times its upper end.
+    No further progress is allowed: the next trial is the best point a_2
+    itself, and the search ends there with info 2."""
+    fn = poly_phi([0, 0, 0, 5])
+    rec, trials = record_trials(lambda a: (*fn(a), None))
+    beta, _, _, _, nfev, info = O.more_thuente(rec, 0.0, -1.0, O.LSOpts(xtol=0.8))
+    a2 = trials[1]
+    assert fn(a2)[0] < 0.0 and fn(a2)[1] < 0.0 and 1.0 - a2 <= 0.8
+    assert trials == [1.0, a2, a2] and (beta, nfev, info) == (a2, 3, 2)
+
+
+def test_linesearch_first_stage_cannot_return_after_the_switch():
+    """The second stage starts at the first trial with psi <= 0 and
+    phi' >= min(ftol, gtol) phi'(0).  Such a trial lies past a minimiser and
+    on or below the sufficient-decrease line, and it closes the bracket on
+    that side, so every later trial that is no higher than the best point is
+    also on or below the line: the first stage's step on psi (taken only for
+    trials above the line) cannot occur after the switch.  Checked on random
+    quintics and step options: after the switch, no trial is both no higher
+    than the lower end and above the line."""
+    rng = np.random.default_rng(20)
+    switched_cases = 0
+    for _ in range(400):
+        fn = poly_phi(rng.normal(size=4) * rng.choice([1.0, 5.0, 20.0]))
+        mu, eta = float(rng.choice([1e-4, 0.1, 0.3])), float(rng.choice([1e-3, 1e-2, 0.1, 0.9]))
+        opts = O.LSOpts(ftol=mu, gtol=eta, stp0=float(10 ** rng.uniform(-2, 1)), maxfev=30)
+        seen, state = [], {"switched": False}
+        real = O.mt_trial
+
+        def spy(lo, hi, t, brackt, stmin, stmax):
+            seen.append((lo, t, state["switched"]))
+            return real(lo, hi, t, brackt, stmin, stmax)
+
+        def phi(a):
+            f, g = fn(a)
+            if f <= mu * a * -1.0 and g >= min(mu, eta) * -1.0:
+                state["switched"] = True
+            return f, g, None
+        O.mt_trial = spy
+        try:
+            O.more_thuente(phi, 0.0, -1.0, opts)
+        finally:
+            O.mt_trial = real
+        for lo, t, after in seen:
+            a, f = t[0], fn(t[0])[0]
+            lo_f = fn(lo[0])[0] if lo[0] != 0.0 else 0.0
+            if after and f <= lo_f:
+                assert f <= -mu * a, (a, f, lo)
+        switched_cases += any(after for _, _, after in seen)
+    assert switched_cases >= 20
+
+
 # Trial selection of More-Thuente, case by case, against interpolants built
 # here by solving their interpolation conditions as linear systems.
 
