@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mttkrp-only", default=None, choices=["dense_256", "dense_4way", "sparse"],
+    p.add_argument("--mttkrp-only", default=None, choices=["dense_256", "dense_4way", "sparse", "sparse_scaled"],
                    help="time only cp_mttkrp on that workload (profiling driver)")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--accuracy-report", default=None, choices=["dense_256", "dense_4way"],
@@ -66,7 +66,14 @@ def parse():
     p.add_argument("--serve-fp64-requests", type=int, default=32,
                    help="requests solved by the FP64 path in saturation for the mixed-vs-FP64 figure")
     p.add_argument("--serve-slots", type=int, default=48)
+    p.add_argument("--dimtree", type=int, default=-1, choices=[-1, 0, 1],
+                   help="dimension-tree MTTKRP pairs in the mixed solve: -1 library default, 0 off, 1 on")
+    p.add_argument("--fixed-iters", type=int, default=0,
+                   help="solve-only timing at exactly this many iterations (tolerance out of reach): ms per iteration")
+    p.add_argument("--no-workloads", action="store_true",
+                   help="skip the 20^3, 96^4 and sparse workload blocks of the bench line")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--cpu-c1", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--cpu-iters", type=int, default=1, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -107,45 +114,109 @@ def oracle_iters(name="dense_256"):
 
 
 def cpu_sample(n_iters: int) -> dict:
-    """Time the oracle on the workload: the start-up (normalise + f/g) and
-    n_iters N-GMRES iterations; a full solve is start-up + iters x per-iteration."""
-    import numpy as np  # noqa: F401
+    """Time the oracle on the workload: its start-up (normalise + f/g) and
+    then n_iters N-GMRES iterations of one solve, each timed on its own (an
+    iteration starts at its Step I, the ALS sweep).  A full solve is the
+    start-up plus the oracle's own iteration count times the mean iteration."""
     import synth
     from oracle import cp_oracle as O
     prob, u0 = synth.workload_dense_256()
     X = O.DenseTensor(prob.T)
-    t0 = time.perf_counter()
-    O.cp_solve(X, u0, O.SolveOpts(R=R, tol=TOL), max_iters=0)
-    t_init = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    _, _, rep = O.cp_solve(X, u0, O.SolveOpts(R=R, tol=TOL), max_iters=n_iters)
-    t_run = time.perf_counter() - t0
-    per_iter = max(t_run - t_init, 1e-9) / max(rep.iters, 1)
+    marks = []
+    real = O.als_sweep
+
+    def timed_sweep(*a, **k):
+        marks.append(time.perf_counter())
+        return real(*a, **k)
+    O.als_sweep = timed_sweep
+    try:
+        t0 = time.perf_counter()
+        _, _, rep = O.cp_solve(X, u0, O.SolveOpts(R=R, tol=TOL), max_iters=n_iters)
+        t_end = time.perf_counter()
+    finally:
+        O.als_sweep = real
+    bounds = marks + [t_end]
+    per_iter = [bounds[i + 1] - bounds[i] for i in range(len(marks))]
     full = oracle_iters()
-    est = t_init + (full if full else float("nan")) * per_iter
+    mean = sum(per_iter) / max(len(per_iter), 1)
+    t_init = (marks[0] if marks else t_end) - t0
     return dict(t_init_s=t_init, per_iter_s=per_iter, iters_sampled=rep.iters, oracle_iters=full,
-                est_solve_s=est)
+                est_solve_s=t_init + (full if full else float("nan")) * mean)
 
 
-def run_cpu_baseline_subprocess(n_iters: int) -> dict | None:
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+def cpu_solves_c1(n_solves: int) -> dict:
+    """Whole oracle solves of the 20x20x20 R=3 workload to ||g||/P < 1e-7,
+    each timed from the initial guess to convergence."""
+    import synth
+    from oracle import cp_oracle as O
+    prob, u0 = synth.workload_dense_small()
+    X = O.DenseTensor(prob.T)
+    times, iters = [], None
+    for _ in range(n_solves):
+        t0 = time.perf_counter()
+        _, _, rep = O.cp_solve(X, u0, O.SolveOpts(R=3, tol=TOL))
+        times.append(time.perf_counter() - t0)
+        iters = rep.iters
+    return dict(solves=n_solves, mean_s=sum(times) / len(times), iters=iters)
+
+
+def host_cpu() -> dict:
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:  # noqa: BLE001
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def run_cpu_child(flag: str, n: int, threads: int = 1) -> dict:
+    """Run one CPU timing in a child process with `threads` BLAS threads and
+    no GPU visible; returns its JSON result (or {"error": ...})."""
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t,
                CUDA_VISIBLE_DEVICES="")
     try:
-        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample",
-                              "--cpu-iters", str(n_iters)], capture_output=True, text=True, env=env,
-                             timeout=900)
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), flag, "--cpu-iters", str(n)],
+                             capture_output=True, text=True, env=env, timeout=1800)
         return json.loads(out.stdout.strip().splitlines()[-1])
     except Exception as exc:  # noqa: BLE001
         return {"error": str(exc)[:200]}
 
 
+def run_cpu_baseline_subprocess(n_iters: int) -> dict | None:
+    return run_cpu_child("--cpu-sample", n_iters, 1)
+
+
 def cpu_baseline_obj(s: dict) -> dict:
     val = 1.0 / s["est_solve_s"] if s.get("est_solve_s") and s["est_solve_s"] == s["est_solve_s"] else None
+    per = s.get("per_iter_s") or [0.0]
     return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": (f"oracle start-up + {s.get('iters_sampled')} N-GMRES iteration(s) of this workload "
-                       f"timed ({s.get('t_init_s', 0):.2f} s + {s.get('per_iter_s', 0):.2f} s/iter, numpy "
+                       f"timed ({s.get('t_init_s', 0):.2f} s + {sum(per) / len(per):.2f} s/iter, numpy "
                        f"single thread), extrapolated to the oracle's own {s.get('oracle_iters')} "
-                       f"iterations to tolerance (oracle/workload_iters.json)")}
+                       f"iterations to tolerance (oracle/workload_iters.json)"),
+            "host": host_cpu()}
+
+
+def cpu_c1_block() -> dict:
+    """The oracle's whole solves of the 20x20x20 workload on the host, one
+    BLAS thread and all cores (no extrapolation)."""
+    h = host_cpu()
+    one = run_cpu_child("--cpu-c1", 20, 1)
+    allc = run_cpu_child("--cpu-c1", 20, h["nproc"] or 1)
+    res = {"host": h, "kind": "oracle", "workload": "dense 20x20x20 fp64, R=3, c=0.5, 10% noise, tol 1e-7"}
+    for name, r in (("one_thread", one), ("all_cores", allc)):
+        if "error" in r:
+            res[name] = r
+        else:
+            res[name] = {"solves_per_s": 1.0 / r["mean_s"], "ms_per_solve": 1e3 * r["mean_s"],
+                         "solves_timed": r["solves"], "iters": r["iters"],
+                         "threads": 1 if name == "one_thread" else h["nproc"]}
+    return res
 
 
 # ------------------------------------------------------------------- clocks
@@ -212,9 +283,10 @@ def run_ours(args, rank, world, local_rank):
     import synth
     import paper_1105_5331_gb300 as cp
 
-    cpu = None
+    cpu = cpu_c1 = None
     if rank == 0 and not args.no_cpu_baseline and not args.solve_only:
         cpu = run_cpu_baseline_subprocess(args.cpu_iters)   # before any GPU work
+        cpu_c1 = cpu_c1_block()
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -237,6 +309,11 @@ def run_ours(args, rank, world, local_rank):
         o = cp.cp_solve_opts_default(R)
         o.tol = TOL
         o.prec = p
+        o.dimtree = args.dimtree
+        if args.fixed_iters > 0:
+            o.tol = 1e-30
+            o.maxit = args.fixed_iters
+            o.polish = 0
         return o
 
     def timed_solves(p, n_warm, n_timed, launch_count=None):
@@ -282,6 +359,18 @@ def run_ours(args, rank, world, local_rank):
 
     serving = serving_run(cp, ctx, args) if rank == 0 and not args.solve_only else None
 
+    # the other workloads: the 20^3 plain method, the 96^4 mixed solve with
+    # its errors, the sparse solve with its one-off sort (not in `value`)
+    workloads = None
+    if rank == 0 and not args.solve_only and not args.no_workloads:
+        t.close()
+        workloads = {"dense_20_fp64": c1_block(cp, ctx, stream), "dense_4way_96": c3_block(cp, ctx, stream),
+                     "sparse_20000": c4_block(cp, ctx, stream)}
+        workloads["sparse_20000"]["scaled_2e8"] = sparse_scaled_block(cp, ctx, stream)
+        if cpu_c1 is not None:
+            workloads["dense_20_fp64"]["cpu_oracle"] = cpu_c1
+        t = None
+
     clocks = clk.summary()
     lat = sorted(times)
     res = {
@@ -294,12 +383,14 @@ def run_ours(args, rank, world, local_rank):
                    "precision": args.prec, "l2": "flushed before every timed step: 512 MiB write, then 256 MiB read (cold, clean L2)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "us_per_iteration": 1e6 * sum(times) / max(1, sum(r["iters"] for r in reps)),
         "solve": {"iters": reps[-1]["iters"], "fg_evals": reps[-1]["fg_evals"],
                   "restarts": reps[-1]["restarts"], "ls_failures": reps[-1]["ls_failures"],
                   "mixed_iters": reps[-1]["mixed_iters"], "fp64_iters": reps[-1]["fp64_iters"],
                   "gnorm_over_P": reps[-1]["gnorm_over_P"], "f": reps[-1]["f"]},
         "vs_fp64_path": other_obj,
         "serving": serving,
+        "workloads": workloads,
         "roofline": roof,
         "e2e": e2e,
         "clocks": clocks,
@@ -310,7 +401,8 @@ def run_ours(args, rank, world, local_rank):
             res["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu["error"]}
         else:
             res["cpu_baseline"] = cpu_baseline_obj(cpu)
-    t.close()
+    if t is not None:
+        t.close()
     ctx.close()
     return res
 
@@ -447,26 +539,30 @@ def e2e_run(cp, ctx, prob, u0, prec, n, T_host):
 
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
-    times = []
-    last = None
-    for k in range(args.warmup + args.steps):
-        # one BLAS thread, as the cpu_baseline object states
-        s = run_cpu_baseline_subprocess(args.cpu_iters)
-        if "error" in s:
-            return {"impl": "reference", "unavailable": f"oracle sample failed: {s['error']}"}
-        if k >= args.warmup:
-            times.append(s["est_solve_s"])
-            last = s
-    mean = sum(times) / len(times)
-    value = 1.0 / mean if mean == mean else None
-    cb = cpu_baseline_obj(last)
+    """The FP64 CPU oracle on the host cores (one BLAS thread, in a child
+    process), on the 256^3 workload: one solve's start-up, then warmup +
+    steps N-GMRES iterations of that solve; a step is one iteration, timed
+    on its own.  solves/s = 1 / (start-up + the oracle's own iteration count
+    to tolerance x the mean timed iteration)."""
+    s = run_cpu_baseline_subprocess(args.warmup + args.steps)
+    if "error" in s:
+        return {"impl": "reference", "unavailable": f"oracle sample failed: {s['error']}"}
+    timed = s["per_iter_s"][args.warmup:]
+    mean = sum(timed) / len(timed)
+    full = s.get("oracle_iters")
+    value = 1.0 / (s["t_init_s"] + full * mean) if full else None
+    cb = cpu_baseline_obj(dict(s, per_iter_s=timed))
     cb["value"] = value
+    cb["sample"] = (f"one oracle solve of this workload: start-up {s['t_init_s']:.2f} s, then {args.warmup} "
+                    f"untimed + {args.steps} timed N-GMRES iterations (mean {mean:.2f} s each, numpy single "
+                    f"thread); solves/s = 1 / (start-up + {full} iterations to tolerance x mean), the "
+                    f"oracle's own count (oracle/workload_iters.json)")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * mean,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generator; no dataset)",
             "config": {"workload": WORKLOAD, "dims": list(DIMS), "R": R, "tol": TOL, "w": 20,
-                       "precision": "fp64 (CPU oracle)"},
+                       "precision": "fp64 (CPU oracle)", "step": "one N-GMRES iteration of the oracle"},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -503,6 +599,12 @@ def run_mttkrp_only(args):
 
     import synth
     import paper_1105_5331_gb300 as cp
+    if args.mttkrp_only == "sparse_scaled":
+        dev = torch.device("cuda", 0)
+        stream = torch.cuda.Stream(dev)
+        ctx = cp.cp_ctx_create(0, stream)
+        print(json.dumps({"mttkrp_only": "sparse_scaled", **sparse_scaled_block(cp, ctx, stream)}))
+        return
     sparse = args.mttkrp_only == "sparse"
     if args.mttkrp_only == "dense_256":
         prob, u0 = synth.workload_dense_256()
@@ -561,43 +663,66 @@ def run_mttkrp_only(args):
     print(json.dumps({"mttkrp_only": args.mttkrp_only, "prec": args.prec, **res}))
 
 
-def run_accuracy_report(args):
+def match_factors(prob, um, uf):
+    """Rank-one terms of two solutions matched greedily by congruence (the
+    product over modes of |cos| of the columns); per mode the relative error
+    of the first against the second, column signs matched."""
+    import numpy as np
+    Rk = prob.R
+    As, Bs, off = [], [], 0
+    for n in prob.dims:
+        As.append(um[off:off + n * Rk].reshape(n, Rk))
+        Bs.append(uf[off:off + n * Rk].reshape(n, Rk))
+        off += n * Rk
+    C = np.ones((Rk, Rk))
+    for A, Bf in zip(As, Bs):
+        C *= np.abs((A / np.linalg.norm(A, axis=0)).T @ (Bf / np.linalg.norm(Bf, axis=0)))
+    perm, used = [-1] * Rk, set()
+    for idx in np.argsort(-C, axis=None):
+        r, q = divmod(int(idx), Rk)
+        if perm[r] < 0 and q not in used:
+            perm[r] = q
+            used.add(q)
+    errs = []
+    for A, Bf in zip(As, Bs):
+        Bp = Bf[:, perm]
+        sg = np.sign(np.sum(A * Bp, axis=0))
+        sg[sg == 0] = 1.0
+        errs.append(float(np.linalg.norm(A - Bp * sg) / np.linalg.norm(Bf)))
+    return errs, perm
+
+
+def mixed_vs_fp64(cp, ctx, t, prob, u0, stream, timed=1):
     """The mixed-precision solve (bf16x3 MTTKRP, FP64 polish) and the FP64
-    solve of one workload from the same starting point on the GPU: iterations,
-    time, f and ||grad f||/P of each; at the mixed solution, f and grad f of
-    the mixed evaluation against the FP64 one (the FP64 GPU path matches the
-    FP64 oracle within 1e-10 in the tests); and the mixed solution's factors
-    against the FP64 solution's (per mode, relative Frobenius error with the
-    column signs matched)."""
+    solve of one dense workload from the same start, CUDA-event timed; at the
+    mixed solution, f and grad f of the mixed evaluation against the FP64
+    one; the mixed solution's factors against the FP64 solution's."""
     import numpy as np
     import torch
-
-    import synth
-    import paper_1105_5331_gb300 as cp
-    prob, u0 = synth.workload_dense_4way() if args.accuracy_report == "dense_4way" else synth.workload_dense_256()
     Rk = prob.R
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.Stream(dev)
-    ctx = cp.cp_ctx_create(0, stream)
-    with torch.cuda.stream(stream):
-        T = torch.from_numpy(prob.T).to(dev)
-    stream.synchronize()
-    t = cp.cp_tensor_dense(ctx, T)
-    out = {"accuracy_report": args.accuracy_report, "dims": list(prob.dims), "R": Rk, "tol": TOL}
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {"dims": list(prob.dims), "R": Rk, "tol": TOL}
     sols = {}
+    with torch.cuda.stream(stream):
+        u0d = torch.from_numpy(u0).to(dev)
     for name, prec in (("mixed", cp.CP_MIXED_BF16X3), ("fp64", cp.CP_FP64)):
         o = cp.cp_solve_opts_default(Rk)
         o.tol = TOL
         o.prec = prec
-        with torch.cuda.stream(stream):
-            u = torch.from_numpy(u0).to(dev)
-        stream.synchronize()
-        t0 = time.perf_counter()
-        r = cp.cp_solve(ctx, t, o, u)
-        stream.synchronize()
-        dt = time.perf_counter() - t0
+        times = []
+        for k in range(1 + timed):
+            with torch.cuda.stream(stream):
+                u = u0d.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = cp.cp_solve(ctx, t, o, u)
+            e1.record(stream)
+            e1.synchronize()
+            if k > 0 or timed == 0:
+                times.append(e0.elapsed_time(e1) / 1e3)
         sols[name] = u
-        out[name] = {"s": dt, "iters": r["iters"], "mixed_iters": r["mixed_iters"], "fp64_iters": r["fp64_iters"],
+        out[name] = {"solves_per_s": len(times) / sum(times), "ms_per_solve": 1e3 * sum(times) / len(times),
+                     "iters": r["iters"], "mixed_iters": r["mixed_iters"], "fp64_iters": r["fp64_iters"],
                      "converged": r["converged"], "f": r["f"], "gnorm_over_P": r["gnorm_over_P"]}
     um = sols["mixed"]
     P = um.numel()
@@ -613,33 +738,218 @@ def run_accuracy_report(args):
     out["at_mixed_solution"] = {"f_fp64": f64, "f_mixed_rel_err": abs(fm - f64) / abs(f64),
                                 "g_fp64_over_P": float(np.linalg.norm(g64)) / P,
                                 "g_mixed_err_over_P": float(np.linalg.norm(gm - g64)) / P}
-    # rank-one terms matched greedily by congruence (product over modes of
-    # |cos| of the columns), then per mode the relative error, signs matched
-    a, b = um.cpu().numpy(), sols["fp64"].cpu().numpy()
-    As, Bs, off = [], [], 0
-    for n in prob.dims:
-        As.append(a[off:off + n * Rk].reshape(n, Rk))
-        Bs.append(b[off:off + n * Rk].reshape(n, Rk))
-        off += n * Rk
-    C = np.ones((Rk, Rk))
-    for A, Bf in zip(As, Bs):
-        C *= np.abs((A / np.linalg.norm(A, axis=0)).T @ (Bf / np.linalg.norm(Bf, axis=0)))
-    perm, used = [-1] * Rk, set()
-    for idx in np.argsort(-C, axis=None):
-        r, s = divmod(int(idx), Rk)
-        if perm[r] < 0 and s not in used:
-            perm[r] = s
-            used.add(s)
-    errs = []
-    for A, Bf in zip(As, Bs):
-        Bp = Bf[:, perm]
-        s = np.sign(np.sum(A * Bp, axis=0))
-        s[s == 0] = 1.0
-        errs.append(float(np.linalg.norm(A - Bp * s) / np.linalg.norm(Bf)))
+    errs, perm = match_factors(prob, um.cpu().numpy(), sols["fp64"].cpu().numpy())
     out["factors_rel_err_vs_fp64_solve"] = errs
-    out["term_order_vs_fp64_solve"] = perm
     out["f_rel_diff_vs_fp64_solve"] = abs(out["mixed"]["f"] - out["fp64"]["f"]) / abs(out["fp64"]["f"])
+    out["note"] = ("errors against the FP64 GPU path, which matches the FP64 oracle within 1e-10 per call "
+                   "(tests/test_gpu_dense.py, tests/test_gpu_trajectories.py)")
+    return out, sols
+
+
+def run_accuracy_report(args):
+    """mixed_vs_fp64 on one workload, one JSON line."""
+    import torch
+
+    import synth
+    import paper_1105_5331_gb300 as cp
+    prob, u0 = synth.workload_dense_4way() if args.accuracy_report == "dense_4way" else synth.workload_dense_256()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    ctx = cp.cp_ctx_create(0, stream)
+    with torch.cuda.stream(stream):
+        T = torch.from_numpy(prob.T).to(dev)
+    stream.synchronize()
+    t = cp.cp_tensor_dense(ctx, T)
+    out, _ = mixed_vs_fp64(cp, ctx, t, prob, u0, stream, timed=0)
+    out["accuracy_report"] = args.accuracy_report
     print(json.dumps(out))
+
+
+def c1_block(cp, ctx, stream, n_solves=30):
+    """The 20x20x20 R=3 workload (the paper's plain method, FP64): whole GPU
+    solves to ||g||/P < 1e-7, CUDA-event timed, and the oracle's whole solves
+    on the host cores."""
+    import torch
+    import synth
+    prob, u0 = synth.workload_dense_small()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.stream(stream):
+        T = torch.from_numpy(prob.T).to(dev)
+        u0d = torch.from_numpy(u0).to(dev)
+    stream.synchronize()
+    t = cp.cp_tensor_dense(ctx, T)
+    o = cp.cp_solve_opts_default(3)
+    o.tol = TOL
+    times = []
+    for k in range(3 + n_solves):
+        with torch.cuda.stream(stream):
+            u = u0d.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = cp.cp_solve(ctx, t, o, u)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 3:
+            times.append(e0.elapsed_time(e1) / 1e3)
+    t.close()
+    lat = sorted(times)
+    return {"workload": "dense 20x20x20 fp64, planted R=3, c=0.5, 10% noise; N-GMRES w=20, R=3, fp64, "
+                        "stop ||g||/P < 1e-7",
+            "solves_per_s": len(times) / sum(times), "p50_ms": 1e3 * lat[len(lat) // 2],
+            "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], "solves_timed": len(times),
+            "iters": r["iters"], "converged": r["converged"]}
+
+
+def c3_block(cp, ctx, stream):
+    """The 96^4 R=32 workload: mixed (FP64-polished) and FP64 solves, and the
+    errors of f, grad f and the factors of the mixed solution."""
+    import synth
+    import torch
+    prob, u0 = synth.workload_dense_4way()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.stream(stream):
+        T = torch.from_numpy(prob.T).to(dev)
+    stream.synchronize()
+    t = cp.cp_tensor_dense(ctx, T)
+    del T
+    out, _ = mixed_vs_fp64(cp, ctx, t, prob, u0, stream, timed=1)
+    out["workload"] = "dense 96x96x96x96 fp32, planted R=32, c=0.5, 5% noise; N-GMRES w=20, R=32, stop ||g||/P < 1e-7"
+    t.close()
+    return out
+
+
+def sparse_scaled_on_device(I, nnz, R=10, seed=11055731):
+    """A scaled version of the sparse workload, drawn on the GPU (a host draw
+    of 2e8 distinct coordinates takes minutes): I x I x I, uniform int64
+    coordinates made distinct through their linear index (sorted by it), a
+    planted rank-R model with U(0,1) factors evaluated there plus 1 % noise,
+    FP32 values.  Returns device coords (nnz' x 3), values, nnz' (nnz' may
+    fall a few short of nnz when draws collide)."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    key = torch.randint(0, I * I * I, (nnz,), generator=g, device="cuda", dtype=torch.int64)
+    key = torch.unique(key)
+    coords = torch.stack([key // (I * I), (key // I) % I, key % I], dim=1).contiguous()
+    del key
+    m = torch.ones(coords.shape[0], R, dtype=torch.float64, device="cuda")
+    for n in range(3):
+        A = torch.rand(I, R, generator=g, dtype=torch.float64, device="cuda")
+        m *= A[coords[:, n]]
+    m = m.sum(dim=1)
+    noise = torch.randn(coords.shape[0], generator=g, dtype=torch.float64, device="cuda")
+    vals = (m + 0.01 * torch.linalg.vector_norm(m) * noise / torch.linalg.vector_norm(noise)).to(torch.float32)
+    return coords, vals.contiguous(), int(coords.shape[0])
+
+
+def sparse_scaled_block(cp, ctx, stream, variants=((2_000_000, 200_000_000), (500_000, 200_000_000))):
+    """The sparse MTTKRP at 2e8 nonzeros (kernel timers, every mode, FP32
+    products and FP64): I = 2e6 as planned (the two gathered FP32 factor
+    tables, 2 x 128 MB, exceed the 129 MB L2), and I = 5e5 (2 x 32 MB, L2
+    resident), with the one-off sort and segmentation."""
+    import torch
+    res = {}
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    Rk = 10
+    for I, want in variants:
+        coords, vals, nnz = sparse_scaled_on_device(I, want, Rk)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t = cp.cp_tensor_coo(ctx, (I, I, I), coords, vals)
+        cp.cp_ctx_sync(ctx)
+        build_s = time.perf_counter() - t0
+        del coords, vals
+        u = torch.rand(3 * I * Rk, dtype=torch.float64, device="cuda")
+        out = torch.empty(I * Rk, dtype=torch.float64, device="cuda")
+        blk = {"I": I, "nnz": nnz, "sort_and_segment_s": build_s}
+        for pname, prec, sf in (("fp32_products", cp.CP_MIXED_BF16X3, 4), ("fp64", cp.CP_FP64, 8)):
+            cp.cp_mttkrp(ctx, t, Rk, u, 0, out, prec)
+            cp.cp_ctx_timer_enable(ctx, True)
+            for n in range(3):
+                for _ in range(2):
+                    cp.cp_mttkrp(ctx, t, Rk, u, n, out, prec)
+            ms, launches = cp.cp_ctx_timer_read(ctx, cp.TIMER_COO)
+            cp.cp_ctx_timer_enable(ctx, False)
+            d = ms / 1e3 / max(launches, 1)
+            comp = nnz * 12
+            access = comp + nnz * 2 * Rk * sf
+            blk[pname] = {"avg_kernel_ms": 1e3 * d, "compulsory_GBps": comp / d / 1e9,
+                          "compulsory_frac_of_hbm": comp / d / 1e9 / peak, "access_GBps": access / d / 1e9,
+                          "access_frac_of_hbm": access / d / 1e9 / peak, "launches_timed": launches}
+        t.close()
+        del u, out
+        torch.cuda.empty_cache()
+        res[f"I{I}"] = blk
+    res["bytes"] = ("compulsory = 12 B per nonzero (FP32 value + two int32 coordinates); access = compulsory + "
+                    "the two gathered factor rows (R x 4 B FP32 / R x 8 B FP64 each)")
+    return res
+
+
+def c4_block(cp, ctx, stream, maxit=3000):
+    """The sparse 20000^3 workload (2e6 nonzeros, planted rank 10 + 1 %
+    noise, R=10, w=20): the one-off sort and segmentation, the sparse MTTKRP
+    of every mode (kernel timers; compulsory and access bytes), and FP64 and
+    FP32-product solves."""
+    import torch
+    import synth
+    prob, u0 = synth.workload_sparse()
+    Rk = prob.R
+    dev = torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.stream(stream):
+        coords = torch.from_numpy(prob.coords).to(dev)
+        vals = torch.from_numpy(prob.vals).to(dev)
+        u0d = torch.from_numpy(u0).to(dev)
+    stream.synchronize()
+    build = []
+    for k in range(2):
+        t0 = time.perf_counter()
+        t = cp.cp_tensor_coo(ctx, prob.dims, coords, vals)
+        cp.cp_ctx_sync(ctx)
+        build.append(time.perf_counter() - t0)
+        if k == 0:
+            t.close()
+    nnz = prob.coords.shape[0]
+    N = len(prob.dims)
+    res = {"workload": "sparse 20000^3 COO, 2e6 distinct uniform nonzeros, planted rank-10 U(0,1) + 1% noise, "
+                       "fp32 values; N-GMRES w=20, R=10, stop ||g||/P < 1e-7",
+           "nnz": nnz, "sort_and_segment_s": build[-1],
+           "sort_note": "cp_tensor_coo on device arrays, synchronised: validation, per-mode stable sort, "
+                        "segmentation, work units (second call; the first is warm-up)"}
+    out = torch.empty(max(prob.dims) * Rk, dtype=torch.float64, device=dev)
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    for pname, prec, sf in (("fp64", cp.CP_FP64, 8), ("fp32_products", cp.CP_MIXED_BF16X3, 4)):
+        cp.cp_ctx_timer_enable(ctx, True)
+        for n in range(N):
+            for _ in range(5):
+                cp.cp_mttkrp(ctx, t, Rk, u0d, n, out, prec)
+        ms, launches = cp.cp_ctx_timer_read(ctx, cp.TIMER_COO)
+        cp.cp_ctx_timer_enable(ctx, False)
+        d = ms / 1e3 / max(launches, 1)
+        comp = nnz * (4 + 4 * (N - 1))
+        access = comp + nnz * (N - 1) * Rk * sf
+        res[f"mttkrp_{pname}"] = {"avg_kernel_us": 1e6 * d, "compulsory_GBps": comp / d / 1e9,
+                                  "access_GBps": access / d / 1e9, "compulsory_frac_of_hbm": comp / d / 1e9 / peak,
+                                  "launches_timed": launches}
+    for pname, prec in (("fp64", cp.CP_FP64), ("fp32_products", cp.CP_MIXED_BF16X3)):
+        o = cp.cp_solve_opts_default(Rk)
+        o.tol = TOL
+        o.prec = prec
+        o.maxit = maxit
+        with torch.cuda.stream(stream):
+            u = u0d.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = cp.cp_solve(ctx, t, o, u)
+        e1.record(stream)
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        res[f"solve_{pname}"] = {"solves_per_s": 1.0 / sec, "ms_per_solve": 1e3 * sec, "iters": r["iters"],
+                                 "converged": r["converged"], "f": r["f"], "gnorm_over_P": r["gnorm_over_P"],
+                                 "maxit": maxit}
+    t.close()
+    return res
 
 
 def run_small_kernels(args):
@@ -764,6 +1074,9 @@ def main():
     args = parse()
     if args.cpu_sample:
         print(json.dumps(cpu_sample(args.cpu_iters)))
+        return
+    if args.cpu_c1:
+        print(json.dumps(cpu_solves_c1(args.cpu_iters)))
         return
     if args.kernel_breakdown:
         run_kernel_breakdown(args)

@@ -153,6 +153,18 @@ cp_status cp_mttkrp(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, int
 cp_status cp_mttkrp_variants(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, const double* d,
                              const int* modes, int nmodes, double* out, cp_precision prec);
 
+/* Dimension-tree MTTKRPs of a 3-way dense tensor (no counterpart in the
+ * paper; an exact regrouping of the index sum of Eq. Gn): one pass over T
+ * forms W = T x_c A^(c), W[i_a, i_b, r] = sum_{i_c} T[...] A^(c)[i_c, r],
+ * for `contracted` c = 0 or 2, and the MTTKRPs of the two other modes a < b
+ * follow from W: M^(a)[i, r] = sum_j W[i, j, r] A^(b)[j, r] and
+ * M^(b)[j, r] = sum_i W[i, j, r] A^(a)[i, r].  out: M^(a) (I_a x R) then
+ * M^(b) (I_b x R), row-major doubles.  CP_MIXED_BF16X3 only (W on the
+ * tensor cores with bf16x3 split products and FP32 accumulation; the two
+ * contractions in FP64); CP_ERR_UNSUPPORTED otherwise.  Asynchronous. */
+cp_status cp_mttkrp_dimtree(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, int contracted,
+                            double* out, cp_precision prec);
+
 /* FP64 dense MTTKRP that allocates no device memory (no counterpart in the
  * paper; it exists for callers that cannot allocate while they run: code that
  * enqueues work inside a stream capture it does not own, serving loops with a
@@ -260,6 +272,10 @@ typedef struct {
   cp_ls_opts ls;
   int mixed_maxfev;    /* mixed precision phase: at most this many trials    */
                        /* per line search when > 0 (default 0: ls.maxfev)     */
+  int dimtree;         /* 3-way dense tensors in the mixed phase: the sweep's */
+                       /* M^(2), M^(3) from W = T x_1 A^(1), and M^(1), M^(2) */
+                       /* at ubar from T x_3 A^(3) (see cp_mttkrp_dimtree):  */
+                       /* 1 on; 0 or -1 (default) off                         */
 } cp_solve_opts;
 
 typedef struct {
@@ -267,6 +283,8 @@ typedef struct {
   int mixed_iters, fp64_iters;
   double f, gnorm_over_P, normT2;
   double t_total_s;
+  int ls_trials;       /* line-search trials: evaluations of phi and phi' on  */
+                       /* the line polynomial, summed over all searches       */
 } cp_solve_report;
 
 void cp_solve_opts_default(cp_solve_opts* o, int R);

@@ -31,7 +31,7 @@ EXPORTED = [
     "cp_ctx_create", "cp_ctx_destroy", "cp_last_error", "cp_ctx_sync", "cp_ctx_stream",
     "cp_kernel_launches", "cp_ctx_timer_enable", "cp_ctx_timer_read",
     "cp_tensor_dense", "cp_tensor_coo", "cp_tensor_info", "cp_tensor_sorted_mode",
-    "cp_tensor_destroy", "cp_mttkrp", "cp_mttkrp_variants", "cp_mttkrp_noalloc", "cp_fg", "cp_als_sweep", "cp_normalize",
+    "cp_tensor_destroy", "cp_mttkrp", "cp_mttkrp_variants", "cp_mttkrp_noalloc", "cp_mttkrp_dimtree", "cp_fg", "cp_als_sweep", "cp_normalize",
     "ngmres_step",
     "cp_ls_opts_default", "linesearch", "cp_solve_opts_default", "cp_solve",
     "cp_solve_batch", "cp_server_create", "cp_server_submit", "cp_server_poll", "cp_server_cancel",
@@ -55,7 +55,7 @@ class cp_solve_opts(C.Structure):
     _fields_ = [("R", C.c_int), ("w", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
                 ("eps", C.c_double), ("prec", C.c_int), ("polish", C.c_int),
                 ("mixed_tol_factor", C.c_double), ("ls", cp_ls_opts),
-                ("mixed_maxfev", C.c_int)]
+                ("mixed_maxfev", C.c_int), ("dimtree", C.c_int)]
 
 
 class cp_solve_report(C.Structure):
@@ -63,7 +63,7 @@ class cp_solve_report(C.Structure):
                 ("restarts", C.c_int), ("ls_failures", C.c_int), ("converged", C.c_int),
                 ("mixed_iters", C.c_int), ("fp64_iters", C.c_int),
                 ("f", C.c_double), ("gnorm_over_P", C.c_double), ("normT2", C.c_double),
-                ("t_total_s", C.c_double)]
+                ("t_total_s", C.c_double), ("ls_trials", C.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -92,6 +92,7 @@ def _load():
         "cp_tensor_destroy": (None, [VP]),
         "cp_mttkrp": (I, [VP, VP, I, VP, I, VP, I]),
         "cp_mttkrp_noalloc": (I, [VP, VP, I, VP, I, VP]),
+        "cp_mttkrp_dimtree": (I, [VP, VP, I, VP, I, VP, I]),
         "cp_mttkrp_variants": (I, [VP, VP, I, VP, VP, P, I, VP, I]),
         "cp_fg": (I, [VP, VP, I, VP, VP, VP, I]),
         "cp_als_sweep": (I, [VP, VP, I, VP, I, I]),
@@ -310,6 +311,12 @@ def cp_mttkrp_variants(ctx, t, R: int, u, d, modes, out, prec: int = CP_FP64):
     _check(_lib.cp_mttkrp_variants(_h(ctx), _h(t), int(R), _ptr(u), _ptr(d), ms, len(modes), _ptr(out),
                                    int(prec)))
     return out
+
+
+def cp_mttkrp_dimtree(ctx, t, R: int, u, contracted: int, out, prec: int = 1):
+    """W = T x_contracted A^(contracted), then the MTTKRPs of the other two
+    modes from W (in increasing mode order, back to back in out)."""
+    _check(_lib.cp_mttkrp_dimtree(_h(ctx), _h(t), int(R), _ptr(u), int(contracted), _ptr(out), int(prec)))
 
 
 def cp_mttkrp_noalloc(ctx, t, R: int, u, mode: int, out):

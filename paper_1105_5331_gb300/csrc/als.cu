@@ -430,6 +430,8 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
   if (own32) CP_TRY(f32_copy(ctx, L, u, o32, acc32, u32));
   if (!grams_valid) CP_TRY(grams_of(ctx, ctx->stream, ctx->d_counter, L, u, 0, N, grams));
   const int rows = std::max(1, 32 / R);
+  const bool dtree = ctx->dimtree && want_f32 && N == 3;
+  Parts W{};
   for (int n = 0; n < N; ++n) {
     // aux: (Gram of the mode updated last) -> inverse of Gammabar^(n),
     // overlapped with this mode's MTTKRP on the main stream; the first mode's
@@ -445,10 +447,19 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
       CP_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
     }
     Parts pt;
-    if (n == 0 && m0)
+    if (n == 0 && m0) {
       pt = Parts{m0, 1, 0};
-    else
+    } else if (dtree && n >= 1) {
+      // M^(2) and M^(3) from W = T x_1 A^(1) (A^(1) just updated): M^(2)
+      // with the old A^(3), M^(3) with the A^(2) updated in between
+      if (n == 1) CP_TRY(dimtree_w(ctx, t, L, u32, o32, 0, &W));
+      double* M = nullptr;
+      CP_TRY(ws_alloc(ctx, (void**)&M, sizeof(double) * (size_t)L.dims[n] * R));
+      CP_TRY(dimtree_contract(ctx, t, L, W, 0, n, u, M));
+      pt = Parts{M, 1, 0};
+    } else {
       CP_TRY(mttkrp_parts(ctx, t, L, u, u32, o32, n, prec, &pt));
+    }
     if (!pre) CP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     UpdParams up;
     up.parts = pt;
@@ -465,6 +476,7 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
     CP_LAUNCH_CHECK();
     if (!(n == 0 && m0)) ws_free(ctx, const_cast<void*>(pt.p));
   }
+  if (W.p) ws_free(ctx, const_cast<void*>(W.p));
   CP_TRY(grams_of(ctx, ctx->stream, ctx->d_counter, L, u, N - 1, 1, grams));
   ws_free(ctx, Xinv);
   if (own32) ws_free(ctx, u32);

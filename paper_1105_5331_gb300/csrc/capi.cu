@@ -465,6 +465,39 @@ cp_status cp_mttkrp_variants(cp_ctx* ctx, const cp_tensor* t, int R, const doubl
   return mttkrp_variants_any(ctx, t, L, u, d, modes, nmodes, out, prec);
 }
 
+cp_status cp_mttkrp_dimtree(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, int contracted, double* out,
+                            cp_precision prec) {
+  CP_NULLCHECK(ctx);
+  CP_TRY(check_tensor_R(ctx, t, R));
+  CP_NULLCHECK(u);
+  CP_NULLCHECK(out);
+  if (t->kind != 0 || t->N != 3 || prec != CP_MIXED_BF16X3) {
+    set_error("cp_mttkrp_dimtree: 3-way dense tensors in CP_MIXED_BF16X3 only");
+    return CP_ERR_UNSUPPORTED;
+  }
+  if (contracted != 0 && contracted != 2) {
+    set_error("cp_mttkrp_dimtree: contracted mode %d is not 0 or 2", contracted);
+    return CP_ERR_ARG;
+  }
+  CP_TRY(use_device(ctx));
+  Layout L;
+  L.set(t->N, t->dims, R);
+  cp_tensor* tt = const_cast<cp_tensor*>(t);
+  int64_t acc32 = 0;
+  const F32Off o32 = f32_layout(L, &acc32);
+  float* u32 = nullptr;
+  CP_TRY(ws_alloc(ctx, (void**)&u32, sizeof(float) * (size_t)acc32 + 64));
+  CP_TRY(f32_copy(ctx, L, u, o32, acc32, u32));
+  Parts W;
+  CP_TRY(dimtree_w(ctx, tt, L, u32, o32, contracted, &W));
+  const int a = contracted == 0 ? 1 : 0, b = contracted == 2 ? 1 : 2;
+  CP_TRY(dimtree_contract(ctx, t, L, W, contracted, a, u, out));
+  CP_TRY(dimtree_contract(ctx, t, L, W, contracted, b, u, out + t->dims[a] * R));
+  ws_free(ctx, const_cast<void*>(W.p));
+  ws_free(ctx, u32);
+  return CP_OK;
+}
+
 cp_status cp_fg(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, double* f, double* g,
                 cp_precision prec) {
   CP_NULLCHECK(ctx);
@@ -635,6 +668,7 @@ void cp_solve_opts_default(cp_solve_opts* o, int R) {
   o->mixed_tol_factor = 1.0;
   cp_ls_opts_default(&o->ls);
   o->mixed_maxfev = 0;
+  o->dimtree = -1;
 }
 
 cp_status cp_solve(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* opts, double* u,

@@ -120,6 +120,9 @@ inline FactorPtrs factor_ptrs(const Layout& L, const double* u) {
 // ------------------------------------------------------------------ handles
 struct cp_ctx {
   int device = 0;
+  // solver contexts only: 3-way dense mixed-precision MTTKRP pairs come from
+  // a dimension tree (one pass over T for two modes)
+  bool dimtree = false;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int num_sms = 0;
@@ -259,6 +262,14 @@ cp_status mttkrp_dense_mixed_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L
 cp_status mttkrp_tc_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* a32, const float* d32,
                              const F32Off& o, const int* modes, int nmodes, Parts* out);
 bool tc_variants_supported(const Layout& L);
+// Dimension tree (3-way dense, mixed precision): W = T x_c A^(c) on the
+// tensor cores (partial sums in *W), and the MTTKRP of `mode` (one of the
+// two modes other than c) from W with the other factor taken from u (FP64).
+cp_status prepare_dimtree(cp_ctx* ctx, cp_tensor* t);
+cp_status dimtree_w(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o32, int contracted,
+                    Parts* W);
+cp_status dimtree_contract(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const Parts& W, int contracted,
+                           int mode, const double* u, double* out);
 
 // Normalise src (and gsrc) into dst (and gdst); lambda (R) optional.  With
 // grams (N x R x R, the Grams of src) the column norms come from their

@@ -540,7 +540,7 @@ __global__ void variant_sum_kernel(const float* __restrict__ part, int count, in
 // position c ^ (r & 7), and the lo block follows.
 template <typename TT>
 __global__ void split_tiles_kernel(const TT* __restrict__ src, int64_t I, int64_t Kbar, int64_t ktiles,
-                                   uint8_t* __restrict__ out) {
+                                   uint8_t* __restrict__ out, int transposed = 0) {
   const int64_t total = ktiles * I * 8;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(o & 7);
@@ -554,8 +554,10 @@ __global__ void split_tiles_kernel(const TT* __restrict__ src, int64_t I, int64_
 #pragma unroll
     for (int q = 0; q < 8; q += 2) {
       const int64_t k = kt * kBK + c * 8 + q;
-      const double x0 = k < Kbar ? (double)src[i * Kbar + k] : 0.0;
-      const double x1 = k + 1 < Kbar ? (double)src[i * Kbar + k + 1] : 0.0;
+      // element (i, k) of the I x Kbar matrix: row-major, or stored as its
+      // transpose (Kbar x I row-major)
+      const double x0 = k < Kbar ? (double)(transposed ? src[k * I + i] : src[i * Kbar + k]) : 0.0;
+      const double x1 = k + 1 < Kbar ? (double)(transposed ? src[(k + 1) * I + i] : src[i * Kbar + k + 1]) : 0.0;
       const __nv_bfloat16 h0 = __double2bfloat16(x0), h1 = __double2bfloat16(x1);
       const __nv_bfloat16 l0 = __double2bfloat16(x0 - (double)__bfloat162float(h0));
       const __nv_bfloat16 l1 = __double2bfloat16(x1 - (double)__bfloat162float(h1));
@@ -578,6 +580,10 @@ struct MixedMode {
 // Per-tensor mixed-precision state lives beside the handle (indexed by mode).
 struct TcState {
   MixedMode mode[CP_MAX_N];
+  // planes of T seen as a matrix for the dimension tree: [0] rows over modes
+  // 1..N-1, contraction over mode 0; [1] rows over modes 0..N-2,
+  // contraction over mode N-1
+  void* gemm_tiles[2] = {nullptr, nullptr};
 };
 
 static TcState* tc_state(cp_tensor* t) {
@@ -589,6 +595,9 @@ void tensor_free_mixed(cp_tensor* t, cudaStream_t s) {
     if (t->Ttile[n]) cudaFreeAsync(t->Ttile[n], s);
     t->Ttile[n] = nullptr;
   }
+  if (tc_state(t))
+    for (void*& g : tc_state(t)->gemm_tiles)
+      if (g) cudaFreeAsync(g, s);
   delete tc_state(t);
   t->tc_state = nullptr;
 }
@@ -612,6 +621,30 @@ static cp_status ensure_planes(cp_ctx* ctx, cp_tensor* t, int n) {
                                                                         (uint8_t*)t->Ttile[n]);
   CP_LAUNCH_CHECK();
   mm.ready = true;
+  return CP_OK;
+}
+
+// Planes of T as the matrix of a dimension-tree GEMM (see TcState): which =
+// 0 contracts mode 0 (rows = prod of dims 1..N-1, the transpose of T_(1)),
+// which = 1 contracts mode N-1 (rows = prod of dims 0..N-2, T_(1) itself,
+// the row-major tensor).
+static cp_status ensure_gemm_planes(cp_ctx* ctx, cp_tensor* t, int which) {
+  if (!t->tc_state) t->tc_state = new TcState();
+  void*& tiles = tc_state(t)->gemm_tiles[which];
+  if (tiles) return CP_OK;
+  const int64_t K = which == 0 ? t->dims[0] : t->dims[t->N - 1];
+  const int64_t rows = t->K / K;
+  const int64_t ktiles = (K + kBK - 1) / kBK;
+  CP_CUDA(cudaMallocAsync(&tiles, (size_t)ktiles * 2 * (size_t)rows * 128, ctx->stream));
+  const int64_t work = ktiles * rows * 8;
+  const int64_t blocks = std::min<int64_t>((work + 255) / 256, 16 * (int64_t)ctx->num_sms);
+  if (t->dtype == CP_DTYPE_F64)
+    split_tiles_kernel<double><<<(unsigned)blocks, 256, 0, ctx->stream>>>((const double*)t->Tn[0], rows, K, ktiles,
+                                                                         (uint8_t*)tiles, which == 0);
+  else
+    split_tiles_kernel<float><<<(unsigned)blocks, 256, 0, ctx->stream>>>((const float*)t->Tn[0], rows, K, ktiles,
+                                                                        (uint8_t*)tiles, which == 0);
+  CP_LAUNCH_CHECK();
   return CP_OK;
 }
 
@@ -648,6 +681,15 @@ cp_status prepare_mixed(cp_ctx* ctx, cp_tensor* t) {
   return CP_OK;
 }
 
+cp_status prepare_dimtree(cp_ctx* ctx, cp_tensor* t) {
+  if (t->kind != 0 || t->N != 3) return CP_OK;
+  CP_TRY(ensure_gemm_planes(ctx, t, 0));
+  CP_TRY(ensure_gemm_planes(ctx, t, 1));
+  CP_TRY(set_smem_attr());
+  CP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return CP_OK;
+}
+
 // Padded FP32 copy of the factors of u (one launch for all modes).
 static cp_status factors_f32(cp_ctx* ctx, const Layout& L, const double* u, float** buf, F32Off* o) {
   int64_t total = 0;
@@ -655,6 +697,9 @@ static cp_status factors_f32(cp_ctx* ctx, const Layout& L, const double* u, floa
   CP_TRY(ws_alloc(ctx, (void**)buf, sizeof(float) * (size_t)total + 64));
   return f32_copy(ctx, L, u, *o, total, *buf);
 }
+
+static cp_status tc_plan_launch(cp_ctx* ctx, TcParams& p, const int64_t* work, int64_t work_sum,
+                                const int64_t* mgroups, size_t tab_max, uint32_t stage_bytes, Parts* parts);
 
 // The MTTKRPs of modes[0..nmodes) in one launch of the tensor-core kernel
 // (FP32 factors u32 at offsets o; with nvar > 1 the Khatri-Rao variants of
@@ -729,6 +774,19 @@ static cp_status mttkrp_tc_multi(cp_ctx* ctx, cp_tensor* t, const Layout& L, con
     work[k] = J.ktiles * mt;
     work_sum += work[k];
   }
+  return tc_plan_launch(ctx, p, work, work_sum, mgroups, tab_max, stage_bytes, parts);
+}
+
+// Plan and launch the jobs of p (their tiles, sizes and tables set; p's R,
+// RP, nvar, outc, rs, nother, status and ntm set): shared-memory stages,
+// accumulators, each job's split of its contraction range over its share of
+// the SMs, and the per-job partial sums (gx x I x outc floats, in parts).
+static cp_status tc_plan_launch(cp_ctx* ctx, TcParams& p, const int64_t* work, int64_t work_sum,
+                                const int64_t* mgroups, size_t tab_max, uint32_t stage_bytes, Parts* parts) {
+  const int nmodes = p.njobs;
+  const int RP = p.RP;
+  const int outc = p.outc;
+  const int R = p.R;
   const size_t fixed = 1024 + 256 + 64;          // alignment slack, barriers, TMEM slot
   p.tab_smem = (tab_max <= 96 * 1024 && (size_t)kMaxDynSmem >= fixed + tab_max + 2 * (size_t)stage_bytes) ? 1 : 0;
   const size_t avail = (size_t)kMaxDynSmem - fixed - (p.tab_smem ? tab_max : 0);
@@ -848,6 +906,158 @@ cp_status mttkrp_dense_mixed_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L
   for (int k = 0; k < nmodes; ++k) ws_free(ctx, const_cast<void*>(pts[k].p));
   ws_free(ctx, d32);
   ws_free(ctx, a32);
+  return CP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Dimension tree for 3-way tensors: one pass over T makes
+//   W = T x_c A^(c)   (I_a x I_b x R, FP32; c the first or the last mode),
+// from which the MTTKRPs of the two other modes follow by contracting W with
+// one factor each (a = the slower of them in T's order, b the faster):
+//   M^(a)[i, r] = sum_j W[i, j, r] F_b[j, r],   M^(b)[j, r] = sum_i W[i, j, r] F_a[i, r],
+// the same index sums as Eq. Gn's M^(n) = T_(n) Phibar^(n), regrouped.  W is a
+// GEMM (rows (i_a, i_b), contraction i_c, R columns) on the tensor-core
+// kernel with the one factor as its Khatri-Rao tile; the contractions run in
+// FP64 on W's FP32 values and FP64 factors.
+// ---------------------------------------------------------------------------
+namespace {
+
+// out[a, r] = sum_b W[a B + b, r] F[b, r], W = sum of `count` FP32 partials
+// (pitch A B R).  One block per a; thread t = q R + r takes b = q, q + Q, ...
+// (Q = 256 / R); the Q sums of each r are added in q order.
+__global__ void __launch_bounds__(256) contract_fast_kernel(const float* __restrict__ W, int count, int64_t A,
+                                                            int64_t B, int R, const double* __restrict__ F,
+                                                            double* __restrict__ out) {
+  CP_PDL_ENTRY();
+  __shared__ double red[256];
+  const int Q = 256 / R;
+  const int t = threadIdx.x;
+  const int q = t / R, r = t - (t / R) * R;
+  const int64_t pitch = A * B * R;
+  for (int64_t a = blockIdx.x; a < A; a += gridDim.x) {
+    double acc = 0.0;
+    if (q < Q) {
+      for (int64_t b = q; b < B; b += Q) {
+        const int64_t e = (a * B + b) * R + r;
+        float w = 0.f;
+        for (int c = 0; c < count; ++c) w += __ldg(&W[(int64_t)c * pitch + e]);
+        acc = fma((double)w, F[b * R + r], acc);
+      }
+    }
+    red[t] = acc;
+    __syncthreads();
+    if (t < R) {
+      double sum = 0.0;
+      for (int k = 0; k < Q; ++k) sum += red[k * R + t];
+      out[a * R + t] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+// out[b, r] = sum_a W[a B + b, r] F[a, r].  Block x covers 32 consecutive
+// (b, r) elements (one per lane); warp w takes a = w, w + 8, ...; the eight
+// warp sums are added in warp order.
+__global__ void __launch_bounds__(256) contract_slow_kernel(const float* __restrict__ W, int count, int64_t A,
+                                                            int64_t B, int R, const double* __restrict__ F,
+                                                            double* __restrict__ out) {
+  CP_PDL_ENTRY();
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t BR = B * R;
+  const int64_t pitch = A * BR;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;     // b R + r
+  const bool in = e < BR;
+  const int r = in ? (int)(e % R) : 0;
+  double acc = 0.0;
+  if (in) {
+    for (int64_t a = w; a < A; a += 8) {
+      float x = 0.f;
+      for (int c = 0; c < count; ++c) x += __ldg(&W[(int64_t)c * pitch + a * BR + e]);
+      acc = fma((double)x, F[a * R + r], acc);
+    }
+  }
+  red[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && in) {
+    double sum = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += red[k][lane];
+    out[e] = sum;
+  }
+}
+
+}  // namespace
+
+// W = T x_c A^(c) on the tensor cores: one job, the factor's FP32 copy (row
+// stride rs) as its only table; the partial sums (gx x rows x R FP32) in *W.
+static cp_status tc_gemm_launch(cp_ctx* ctx, cp_tensor* t, int which, const float* F32, int rs, int R, Parts* W) {
+  if ((uintptr_t)F32 & 15u) {
+    set_error("dimension tree: FP32 factor copy must be 16-byte aligned");
+    return CP_ERR_ARG;
+  }
+  CP_TRY(ensure_gemm_planes(ctx, t, which));
+  const int64_t K = which == 0 ? t->dims[0] : t->dims[t->N - 1];
+  const int64_t rows = t->K / K;
+  TcParams p{};
+  p.njobs = 1;
+  p.R = R;
+  p.RP = std::max(16, (R + 15) / 16 * 16);
+  p.nvar = 1;
+  p.outc = R;
+  p.rs = rs;
+  p.nother = 1;
+  p.status = ctx->d_status;
+  p.ntm = 1;
+  const uint32_t stage_bytes = 2u * kTileBytes + 2u * (uint32_t)p.RP * 128u;
+  TcJob& J = p.job[0];
+  J.tiles = (const uint8_t*)tc_state(t)->gemm_tiles[which];
+  J.I = rows;
+  J.Kbar = K;
+  J.ktiles = (K + kBK - 1) / kBK;
+  J.tab[0] = F32;
+  J.dimo[0] = K;
+  J.tab_soff[0] = 0;
+  J.tab_cpy[0] = (uint32_t)((size_t)K * rs * sizeof(float));
+  J.tab_bytes = J.tab_cpy[0];
+  const int64_t mg = (rows + kBM - 1) / kBM;
+  const int64_t work = J.ktiles * mg;
+  return tc_plan_launch(ctx, p, &work, work, &mg, J.tab_cpy[0], stage_bytes, W);
+}
+
+cp_status dimtree_w(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o32, int contracted,
+                    Parts* W) {
+  if (t->kind != 0 || t->N != 3 || (contracted != 0 && contracted != 2)) {
+    set_error("dimension tree: 3-way dense tensors, first or last mode only");
+    return CP_ERR_UNSUPPORTED;
+  }
+  return tc_gemm_launch(ctx, t, contracted == 0 ? 0 : 1, u32 + o32.off[contracted], o32.rs, L.R, W);
+}
+
+cp_status dimtree_contract(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const Parts& W, int contracted,
+                           int mode, const double* u, double* out) {
+  // W's rows: (i_a, i_b) with a < b the two modes other than `contracted`
+  const int a = contracted == 0 ? 1 : 0;
+  const int b = contracted == 2 ? 1 : 2;
+  const int64_t A = t->dims[a], B = t->dims[b];
+  const int R = L.R;
+  if (R > 256 || !W.f32) {
+    set_error("dimension tree: rank %d / partials not supported", R);
+    return CP_ERR_UNSUPPORTED;
+  }
+  if (mode == a) {
+    const unsigned blocks = (unsigned)std::min<int64_t>(A, 8 * (int64_t)ctx->num_sms);
+    (void)launch_pdl(contract_fast_kernel, dim3(blocks), dim3(256), 0, ctx->stream, (const float*)W.p, W.count, A, B,
+                     R, u + L.off[b], out);
+  } else if (mode == b) {
+    const unsigned blocks = (unsigned)((B * R + 31) / 32);
+    (void)launch_pdl(contract_slow_kernel, dim3(blocks), dim3(256), 0, ctx->stream, (const float*)W.p, W.count, A, B,
+                     R, u + L.off[a], out);
+  } else {
+    set_error("dimension tree: mode %d is not one W serves", mode);
+    return CP_ERR_ARG;
+  }
+  CP_LAUNCH_CHECK();
   return CP_OK;
 }
 

@@ -247,6 +247,20 @@ cp_status mttkrp_parts(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double*
 // their start-up, and the shared launch measured slower per iteration.)
 static cp_status mttkrp_parts_multi(cp_ctx* ctx, cp_tensor* t, const Layout& L, const double* u, const float* u32,
                                     const F32Off& o32, const int* modes, int nmodes, cp_precision prec, Parts* out) {
+  if (ctx->dimtree && t->kind == 0 && t->N == 3 && prec == CP_MIXED_BF16X3 && u32 && nmodes == 2 && modes[0] == 0 &&
+      modes[1] == 1) {
+    // M^(1) and M^(2) from one pass: W = T x_3 A^(3), then one contraction each
+    Parts W;
+    CP_TRY(dimtree_w(ctx, t, L, u32, o32, 2, &W));
+    for (int k = 0; k < 2; ++k) {
+      double* M = nullptr;
+      CP_TRY(ws_alloc(ctx, (void**)&M, sizeof(double) * (size_t)L.dims[k] * L.R));
+      CP_TRY(dimtree_contract(ctx, t, L, W, 2, k, u, M));
+      out[k] = Parts{M, 1, 0};
+    }
+    ws_free(ctx, const_cast<void*>(W.p));
+    return CP_OK;
+  }
   for (int k = 0; k < nmodes; ++k) CP_TRY(mttkrp_parts(ctx, t, L, u, u32, o32, modes[k], prec, &out[k]));
   return CP_OK;
 }

@@ -8,11 +8,14 @@
 //   * segments = runs of equal i_n (head flags + exclusive scan);
 //   * work units = segments cut into chunks of at most kUnit nonzeros;
 //   * the other coordinates as int32 planes and the values, in sorted order.
-// MTTKRP: one warp per unit; each lane takes nonzeros of the unit in turn,
-// gathers the factor rows of the other modes, multiplies, and accumulates R
-// partial sums; a butterfly shuffle reduction gives the unit's row sum
-// (fixed order, no atomics); a last kernel adds the units of each segment
-// in order into M.  Rows without nonzeros are zero.
+// MTTKRP: one warp per unit (its nonzeros share one output row).  FP32
+// products: "vector groups" of lanes per nonzero, each lane reading one
+// 16-byte piece of every gathered factor row; FP64 products: a staged form
+// (the warp reads 32 nonzeros' values and coordinates at once, then groups
+// of R lanes gather the rows entry by entry).  Either way the products are
+// summed per lane and the lanes combined by shuffles in a fixed order (no
+// atomics); a last kernel adds the units of each segment in order into M.
+// Rows without nonzeros are zero.
 #include <algorithm>
 #include <vector>
 
@@ -272,73 +275,162 @@ __global__ void table_kernel(const double* __restrict__ A, int64_t I, int R, int
   }
 }
 
-// One warp per work unit.  Lanes map to ranks: with R <= 32 the warp holds
-// G = 32 / R groups of R lanes, group g takes the unit's nonzeros g, g + G,
-// ..., and lane r of a group multiplies the r-th entries of the gathered
-// factor rows (so each row is one coalesced R-wide load and the value and
-// coordinates are broadcast within the group).  The G group sums are added
-// in a fixed order at the end.  For R > 32 one group covers the ranks in
-// chunks of 32.  A group loads the coordinates and rows of kUnroll of its
-// nonzeros before it multiplies and adds them in the same order as one at a
-// time (kUnroll = 4 for FP64 products: 227 instead of 254 us on 2e6
-// nonzeros of rank 10; FP32 products keep more warps resident instead).  Table rows are RP elements apart, a multiple of 32 bytes, so that
-// a row takes whole 32-byte sectors.
-template <typename TT, int NO, int kUnroll>
-__global__ void __launch_bounds__(256) mttkrp_coo_kernel(const int32_t* __restrict__ other,
-                                                         const float* __restrict__ vals, int64_t nnz,
-                                                         const int64_t* __restrict__ unit_start,
-                                                         int64_t nunits, Tables tab, int R, int RP,
-                                                         double* __restrict__ partial) {
+// 16-byte vector types of the factor-row reads.
+template <typename TT>
+struct VecOf;
+template <>
+struct VecOf<float> {
+  using V = float4;
+  static constexpr int kW = 4;
+  __device__ static void put(const V& x, float* d) { d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w; }
+};
+template <>
+struct VecOf<double> {
+  using V = double2;
+  static constexpr int kW = 2;
+  __device__ static void put(const V& x, double* d) { d[0] = x.x; d[1] = x.y; }
+};
+
+// Staged form for R <= 32.  The warp first reads the next 32 nonzeros of its
+// unit lane by lane (coalesced values and coordinates, all in flight at
+// once); then its G = 32 / R groups of R lanes take those nonzeros in turn,
+// kUn per group at a time, each group getting a nonzero's value and
+// coordinates from the lane that read them by shuffle and gathering the
+// factor rows with lane r reading entry r (one contiguous R-wide read per
+// row).  Group g adds the products of its nonzeros in order; the G group
+// sums are added in a fixed order at the end.
+template <typename TT, int NO, int kUn>
+__global__ void __launch_bounds__(256) mttkrp_coo_staged_kernel(const int32_t* __restrict__ other,
+                                                                const float* __restrict__ vals, int64_t nnz,
+                                                                const int64_t* __restrict__ unit_start,
+                                                                int64_t nunits, Tables tab, int R, int RP,
+                                                                double* __restrict__ partial) {
   const int lane = threadIdx.x & 31;
   const int64_t unit = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (unit >= nunits) return;
   const int64_t b = unit_start[unit], e = unit_start[unit + 1];
-  const int G = R <= 32 ? 32 / R : 1;
-  const int g = R <= 32 ? lane / R : 0;
-  const int r0 = R <= 32 ? lane - g * R : lane;
+  const int G = 32 / R;
+  const int g = lane / R;
+  const int r = lane - g * R;
   const bool active = g < G;
-  const int nch = (R + 31) / 32;            // rank chunks handled by this lane (R > 32)
-  TT acc0 = (TT)0, acc1 = (TT)0;
-  if (active) {
-    for (int64_t k0 = b + g; k0 < e; k0 += (int64_t)G * kUnroll) {
-      // kUnroll nonzeros k0, k0 + G, ...: values and rows first (a slot past
-      // the unit reads row 0 with value 0)
-      TT v[kUnroll];
-      const TT* rows[kUnroll][NO];
+  TT acc = (TT)0;
+  for (int64_t base = b; base < e; base += 32) {
+    const int64_t k = base + lane;
+    const bool in = k < e;
+    const float vl = in ? vals[k] : 0.f;
+    int32_t co[NO];
 #pragma unroll
-      for (int q = 0; q < kUnroll; ++q) {
-        const int64_t k = k0 + (int64_t)q * G;
-        const bool in = k < e;
-        v[q] = in ? (TT)vals[k] : (TT)0;
+    for (int j = 0; j < NO; ++j) co[j] = in ? other[(int64_t)j * nnz + k] : 0;
+    const int cnt = (int)min((int64_t)32, e - base);
+    for (int q0 = 0; q0 < cnt; q0 += G * kUn) {
+      TT v[kUn], x[kUn][NO];
 #pragma unroll
-        for (int j = 0; j < NO; ++j)
-          rows[q][j] = (const TT*)tab.A[j] + (in ? (int64_t)other[(int64_t)j * nnz + k] : (int64_t)0) * RP;
-      }
-      if (r0 < R) {
+      for (int u = 0; u < kUn; ++u) {
+        const int q = q0 + u * G + g;               // this group's nonzero
+        const bool use = active && q < cnt;
+        // every lane takes part in every shuffle; the predicate applies after
+        const float vq = __shfl_sync(0xffffffffu, vl, q & 31);
+        v[u] = use ? (TT)vq : (TT)0;
 #pragma unroll
-        for (int q = 0; q < kUnroll; ++q) {
-          TT p = v[q];
-#pragma unroll
-          for (int j = 0; j < NO; ++j) p *= rows[q][j][r0];
-          acc0 += p;
+        for (int j = 0; j < NO; ++j) {
+          const int32_t i = __shfl_sync(0xffffffffu, co[j], q & 31);
+          x[u][j] = use ? ((const TT*)tab.A[j])[(int64_t)i * RP + r] : (TT)0;
         }
       }
-      if (nch > 1 && r0 + 32 < R) {
 #pragma unroll
-        for (int q = 0; q < kUnroll; ++q) {
-          TT p = v[q];
+      for (int u = 0; u < kUn; ++u) {
+        TT p = v[u];
 #pragma unroll
-          for (int j = 0; j < NO; ++j) p *= rows[q][j][r0 + 32];
-          acc1 += p;
-        }
+        for (int j = 0; j < NO - 1; ++j) p *= x[u][j];
+        acc = fma(p, x[u][NO - 1], acc);
       }
     }
   }
   // add the group sums in order: lane r (group 0) gathers groups 1..G-1
-  double s0 = (double)acc0;
-  for (int q = 1; q < G; ++q) s0 += (double)__shfl_sync(0xffffffffu, acc0, (lane + q * R) & 31);
-  if (g == 0 && r0 < R) partial[unit * R + r0] = s0;
-  if (nch > 1 && r0 + 32 < R) partial[unit * R + r0 + 32] = (double)acc1;
+  double s0 = (double)acc;
+  for (int q = 1; q < G; ++q) s0 += (double)__shfl_sync(0xffffffffu, acc, (lane + q * R) & 31);
+  if (g == 0) partial[unit * R + r] = s0;
+}
+
+// Vector-group form.  Each nonzero is handled by LP lanes; lane h of a group
+// owns the row entries [h CH, h CH + CH) (CH = NV 16-byte vectors: NV x 4
+// FP32 or NV x 2 FP64 values), so a warp instruction gathers 32 / LP rows,
+// each as contiguous 16-byte pieces, and all kUn x (N - 1) row reads of a
+// lane are issued before its products.  A unit's nonzeros all belong to one
+// output row: each lane sums its CH ranks over the nonzeros it took, the
+// lanes holding the same ranks are added by a butterfly (a fixed order), and
+// lanes 0..LP-1 write the unit's R sums.  Table rows are RP entries apart, RP
+// a multiple of 32 bytes, so every vector read stays inside its row.
+template <typename TT, int NO, int LP, int NV, int kUn>
+__global__ void __launch_bounds__(256) mttkrp_coo_vgroup_kernel(const int32_t* __restrict__ other,
+                                                                const float* __restrict__ vals, int64_t nnz,
+                                                                const int64_t* __restrict__ unit_start,
+                                                                int64_t nunits, Tables tab, int R, int RP,
+                                                                double* __restrict__ partial) {
+  using VT = VecOf<TT>;
+  using V = typename VT::V;
+  constexpr int kW = VT::kW, kCh = NV * kW, kNpw = 32 / LP;
+  const int lane = threadIdx.x & 31;
+  const int64_t unit = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (unit >= nunits) return;
+  const int64_t b = unit_start[unit], e = unit_start[unit + 1];
+  const int slot = lane / LP;                 // this lane's nonzero within a warp step
+  const int h = lane - slot * LP;             // this lane's chunk of ranks
+  const bool cols = h * kCh < R;
+  TT acc[kCh];
+#pragma unroll
+  for (int l = 0; l < kCh; ++l) acc[l] = (TT)0;
+  for (int64_t k0 = b + slot; k0 < e; k0 += (int64_t)kNpw * kUn) {
+    TT v[kUn];
+    V x[kUn][NO][NV];
+#pragma unroll
+    for (int u = 0; u < kUn; ++u) {
+      const int64_t k = k0 + (int64_t)u * kNpw;
+      const bool in = k < e;
+      v[u] = in ? (TT)vals[k] : (TT)0;
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        if (in && cols) {
+          const int64_t i = other[(int64_t)j * nnz + k];
+          const V* src = reinterpret_cast<const V*>((const TT*)tab.A[j] + i * RP + h * kCh);
+#pragma unroll
+          for (int q = 0; q < NV; ++q) x[u][j][q] = __ldg(src + q);
+        } else {
+#pragma unroll
+          for (int q = 0; q < NV; ++q) x[u][j][q] = V{};
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUn; ++u) {
+#pragma unroll
+      for (int hv = 0; hv < NV; ++hv) {
+        TT p[kW], y[kW];
+#pragma unroll
+        for (int l = 0; l < kW; ++l) p[l] = v[u];
+#pragma unroll
+        for (int j = 0; j < NO - 1; ++j) {
+          VT::put(x[u][j][hv], y);
+#pragma unroll
+          for (int l = 0; l < kW; ++l) p[l] *= y[l];
+        }
+        VT::put(x[u][NO - 1][hv], y);
+#pragma unroll
+        for (int l = 0; l < kW; ++l) acc[hv * kW + l] = fma(p[l], y[l], acc[hv * kW + l]);
+      }
+    }
+  }
+  // lanes h, h + LP, h + 2 LP, ... hold the same ranks: butterfly over them
+#pragma unroll
+  for (int l = 0; l < kCh; ++l) {
+#pragma unroll
+    for (int o = 16; o >= LP; o >>= 1) acc[l] += __shfl_xor_sync(0xffffffffu, acc[l], o);
+  }
+  if (lane < LP && cols) {
+#pragma unroll
+    for (int l = 0; l < kCh; ++l)
+      if (h * kCh + l < R) partial[unit * R + h * kCh + l] = (double)acc[l];
+  }
 }
 
 __global__ void zero_kernel(double* __restrict__ x, int64_t n) {
@@ -525,10 +617,10 @@ void tensor_free_coo(cp_tensor* t) {
   }
 }
 
-// nonzeros in flight per lane group: 4 for FP64 products; FP32 products run
-// fastest one at a time (more warps resident: 40.3 us against 51.2 us with 2)
-template <typename TT>
-constexpr int kCooUnroll() { return sizeof(TT) == 8 ? 4 : 1; }
+// 16-byte vectors per lane and factor row in the vector-group kernel (one:
+// two 16-byte reads of one lane fall into the same 32-byte sector and
+// doubled the L1 sector requests, 43.0 against 28.7 us per mode)
+constexpr int kVecPerLane = 1;
 
 template <typename TT, int NO>
 static cp_status launch_coo(cp_ctx* ctx, const cp_tensor* t, const CooMode& md, const Tables& tab, int R, int RP,
@@ -536,10 +628,32 @@ static cp_status launch_coo(cp_ctx* ctx, const cp_tensor* t, const CooMode& md, 
   const int64_t threads = 256;
   const int64_t blocks = (md.nunits * 32 + threads - 1) / threads;
   if (blocks == 0) return CP_OK;
-  {
-    TimerScope ts(ctx, 2);
-    mttkrp_coo_kernel<TT, NO, kCooUnroll<TT>()><<<(unsigned)blocks, (unsigned)threads, 0, ctx->stream>>>(
-        md.other, md.vals, t->nnz, md.unit_start, md.nunits, tab, R, RP, partial);
+  TimerScope ts(ctx, 2);
+  const dim3 g((unsigned)blocks), bl((unsigned)threads);
+  if (sizeof(TT) == 8 && R <= 32) {
+    // FP64 products: the staged kernel (154 us per mode of the 2e6-nonzero
+    // rank-10 tensor against 175 us for the vector groups; FP64 is the bound)
+    mttkrp_coo_staged_kernel<TT, NO, 4><<<g, bl, 0, ctx->stream>>>(md.other, md.vals, t->nnz, md.unit_start,
+                                                                    md.nunits, tab, R, RP, partial);
+  } else {
+    // FP32 products (and FP64 above rank 32): the vector groups (28.7 us per
+    // mode at 2e6 nonzeros, 2.64 ms at 2e8), lanes per nonzero enough
+    // 16-byte chunks for the R ranks, a power of two
+    constexpr int NV = kVecPerLane;
+    const int ch = NV * 16 / (int)sizeof(TT);
+    int LP = 1;
+    while (LP * ch < R) LP *= 2;
+#define CP_VG(lp) mttkrp_coo_vgroup_kernel<TT, NO, lp, NV, 2><<<g, bl, 0, ctx->stream>>>( \
+    md.other, md.vals, t->nnz, md.unit_start, md.nunits, tab, R, RP, partial)
+    switch (LP) {
+      case 1: CP_VG(1); break;
+      case 2: CP_VG(2); break;
+      case 4: CP_VG(4); break;
+      case 8: CP_VG(8); break;
+      case 16: CP_VG(16); break;
+      default: CP_VG(32); break;
+    }
+#undef CP_VG
   }
   CP_LAUNCH_CHECK();
   return CP_OK;

@@ -110,6 +110,30 @@ ALS_SHAPES = [
 ]
 
 
+def als_sweep_tolerance(X, u, R):
+    """Forward-error bound for two FP64 evaluations of one ALS sweep that
+    differ only in rounding (order of sums, Gauss-Jordan against Cholesky).
+    Mode n solves A^(n) Gammabar^(n) = M^(n); a relative perturbation e of
+    its inputs moves A^(n) by at most kappa(Gammabar^(n)) e to first order.
+    Its inputs carry the summation error of M and the Grams, at most
+    eta = (Kbar + 2R) u relative with u = 2^-53 (recursive summation of Kbar
+    products, R-term Hadamard and solve), plus the error of every factor
+    updated before it, which enters M once and the Grams twice:
+    e_n = kappa_n (eta + 3 sum_{m<n} e_m).  The sweep is held to
+    max(1e-10, 3 max_n e_n); the kappa_n are those of the oracle's sweep."""
+    u_ = 2.0 ** -53
+    F = [A.copy() for A in O.unpack(np.array(u, dtype=np.float64), X.dims, R)]
+    errs = []
+    for n in range(len(F)):
+        Gb = O.gamma_bar(F, n)
+        kappa = np.linalg.cond(Gb)
+        Kbar = int(np.prod([d for m, d in enumerate(X.dims) if m != n]))
+        eta = (Kbar + 2 * R) * u_
+        errs.append(kappa * (eta + 3.0 * sum(errs)))
+        F[n] = O.als_mode_solve(X.mttkrp(F, n), Gb)
+    return max(TOL, 3.0 * max(errs))
+
+
 @pytest.mark.parametrize("shape,R,dtype", ALS_SHAPES)
 @pytest.mark.parametrize("normalize", [False, True])
 def test_als_sweep_parity(cp, ctx, shape, R, dtype, normalize):
@@ -127,9 +151,10 @@ def test_als_sweep_parity(cp, ctx, shape, R, dtype, normalize):
     ud = dev(u)
     cp.cp_als_sweep(ctx, t, R, ud, normalize)
     cp.cp_ctx_sync(ctx)
-    # ALS amplifies rounding by the condition of Gammabar; compare against
-    # that bound as well as the flat tolerance
-    assert rel(ud.cpu().numpy(), ref) <= 1e-8
+    tol = als_sweep_tolerance(X, u, R)
+    err = rel(ud.cpu().numpy(), ref)
+    print("ALS sweep", shape, R, "error", err, "tolerance", tol)
+    assert err <= tol
 
 
 def test_als_sweep_parity_well_conditioned(cp, ctx):

@@ -1,10 +1,21 @@
 """GPU checks of the mixed-precision dense MTTKRP (tcgen05, bf16x3 split
 products, FP32 accumulation) against the FP64 oracle, through the C ABI.
 
-Stated bound: relative Frobenius error of M^(n) <= 5e-5 (each split product
-carries ~2^-17 relative error, the accumulation is FP32); f and g built from
-these MTTKRPs are held to the same relative bound against their FP64 values
-(g is compared relative to ||M||, the scale at which its terms cancel)."""
+Stated bounds:
+  * element by element, |M_gpu - M| <= c (|T_(n)| |Phibar|) with
+    c = 3.01 2^-16 + (2N - 2) 2^-24 + (n_mma + 1) 2^-22: the split products
+    drop at most 3.01 u^2 |ab| (u = 2^-8), the FP32 copies of T and of the
+    factors and the FP32 Khatri-Rao products add (2N - 2) 2^-24, and every
+    tensor-core MMA that adds into an FP32 accumulator is charged two FP32
+    ulps (2^-22) of the CTA's share of |T_(n)| |Phibar|, n_mma of them along
+    one accumulator (12 MMAs per 64-element contraction tile: four 16-deep
+    steps of three split products), one more for the epilogue and the FP32
+    partial;
+  * relative Frobenius error of M^(n) <= 5e-5 (the split errors have random
+    signs and add to ~5e-6 of ||M||);
+  * f and g built from these MTTKRPs are held to the same relative bound
+    against their FP64 values (g relative to ||M||, the scale at which its
+    terms cancel)."""
 import numpy as np
 import pytest
 import torch
@@ -41,6 +52,38 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0)
 
 
+def split_k_tiles_per_cta(I, Kbar):
+    """Contraction tiles (64 elements) one CTA adds for a single-mode launch:
+    the rows form ceil(I / 128) groups and the SMs are shared among them."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ktiles = -(-Kbar // 64)
+    groups = -(-I // 128)
+    target = max(1, sms // groups)
+    return -(-ktiles // target)
+
+
+def elementwise_bound(T, F, n, rows=None):
+    """c (|T_(n)| |Phibar|) for the rows of mode n listed (all if None),
+    |T_(n)| |Phibar| computed by the oracle's MTTKRP of |T| and |A|."""
+    N = T.ndim
+    Tabs = np.abs(np.asarray(T, dtype=np.float64))
+    Fabs = [np.abs(A) for A in F]
+    if rows is not None:
+        Tabs = np.take(Tabs, rows, axis=n)
+        Fabs[n] = Fabs[n][rows]
+    B = O.mttkrp_dense(Tabs, Fabs, n)
+    Kbar = int(np.prod([T.shape[m] for m in range(N) if m != n]))
+    n_mma = 12 * split_k_tiles_per_cta(T.shape[n], Kbar)
+    c = 3.01 * 2.0 ** -16 + (2 * N - 2) * 2.0 ** -24 + (n_mma + 1) * 2.0 ** -22
+    return c * B
+
+
+def check_elementwise(got, ref, bound, what):
+    excess = np.abs(got - ref) - bound
+    worst = np.unravel_index(np.argmax(excess), excess.shape)
+    assert np.all(excess <= 0.0), (what, worst, got[worst], ref[worst], bound[worst])
+
+
 SHAPES = [
     ((20, 20, 20), 3, np.float64),        # tiny, one k-tile group per CTA
     ((7, 5, 3), 1, np.float32),           # K-bar below one tile
@@ -65,8 +108,10 @@ def test_mixed_mttkrp_error_bound(cp, ctx, shape, R, dtype):
         cp.cp_mttkrp(ctx, t, R, ud, n, out, cp.CP_MIXED_BF16X3)
         cp.cp_ctx_sync(ctx)
         ref = O.mttkrp_dense(T.astype(np.float64), F, n)
-        err = rel(out.cpu().numpy().reshape(ref.shape), ref)
+        got = out.cpu().numpy().reshape(ref.shape)
+        err = rel(got, ref)
         assert err <= MIXED_TOL, (shape, R, n, err)
+        check_elementwise(got, ref, elementwise_bound(T, F, n), (shape, R, n))
 
 
 def test_mixed_mttkrp_deterministic(cp, ctx):
@@ -111,7 +156,33 @@ def test_full_size_dense_256_mixed_mttkrp(cp, ctx):
         cp.cp_mttkrp(ctx, t, 16, ud, n, out, cp.CP_MIXED_BF16X3)
         cp.cp_ctx_sync(ctx)
         ref = O.mttkrp_dense(prob.T, F, n)
-        assert rel(out.cpu().numpy().reshape(ref.shape), ref) <= MIXED_TOL
+        got = out.cpu().numpy().reshape(ref.shape)
+        assert rel(got, ref) <= MIXED_TOL
+        check_elementwise(got, ref, elementwise_bound(prob.T, F, n), n)
+
+
+def test_full_size_dense_4way_96_mixed_mttkrp_sampled_rows(cp, ctx):
+    """The 96^4, R=32 workload at full size in the bench's launch
+    configuration: every mode's mixed MTTKRP on the GPU, checked on sampled
+    rows (first, last and six random) that the oracle computes from the
+    tensor sliced along that mode, element by element and in norm."""
+    prob, u0 = synth.workload_dense_4way()
+    R = prob.R
+    t = cp.cp_tensor_dense(ctx, dev(prob.T))
+    ud = dev(u0)
+    F = O.unpack(u0, prob.dims, R)
+    rng = np.random.default_rng(96)
+    for n in range(4):
+        out = torch.empty(prob.dims[n] * R, dtype=torch.float64, device="cuda")
+        cp.cp_mttkrp(ctx, t, R, ud, n, out, cp.CP_MIXED_BF16X3)
+        cp.cp_ctx_sync(ctx)
+        rows = np.unique(np.concatenate([[0, prob.dims[n] - 1], rng.integers(0, prob.dims[n], 6)]))
+        Fs = list(F)
+        Fs[n] = F[n][rows]
+        ref = O.mttkrp_dense(np.take(prob.T, rows, axis=n), Fs, n)
+        got = out.cpu().numpy().reshape(prob.dims[n], R)[rows]
+        assert rel(got, ref) <= MIXED_TOL
+        check_elementwise(got, ref, elementwise_bound(prob.T, F, n, rows), n)
 
 
 # Khatri-Rao variant MTTKRPs (the line search's pass): shapes where every
@@ -267,3 +338,105 @@ def match_terms(A, B):
             perm[r] = s
             used.add(s)
     return perm
+
+
+# Dimension tree (3-way): W = T x_c A^(c) in one tensor-core pass, then the
+# MTTKRPs of the two other modes from W.  W's GEMM has rows over the two
+# other modes and the contraction over mode c, so its accumulation chain is
+# that of a launch with rows = I_a I_b and Kbar = I_c; its split products
+# involve T and one FP32 factor: c = 3.01 2^-16 + 2 2^-24 + (n_mma + 1) 2^-22,
+# applied to |T_(n)| |Phibar| as for the MTTKRP (the FP64 contraction of W
+# with the other factor adds 2^-53 terms).
+DIMTREE_CASES = [((20, 20, 20), 3), ((130, 33, 17), 16), ((96, 80, 70), 16), ((17, 65, 200), 5),
+                 ((40, 30, 20), 64)]
+
+
+def dimtree_bound(T, F, n, contracted):
+    Tabs = np.abs(np.asarray(T, dtype=np.float64))
+    B = O.mttkrp_dense(Tabs, [np.abs(A) for A in F], n)
+    rows = T.size // T.shape[contracted]
+    n_mma = 12 * split_k_tiles_per_cta(rows, T.shape[contracted])
+    c = 3.01 * 2.0 ** -16 + 2 * 2.0 ** -24 + (n_mma + 1) * 2.0 ** -22
+    return c * B
+
+
+@pytest.mark.parametrize("shape,R", DIMTREE_CASES)
+@pytest.mark.parametrize("contracted", [0, 2])
+def test_dimtree_mttkrps_error_bound(cp, ctx, shape, R, contracted):
+    rng = np.random.default_rng(R + contracted)
+    T = rng.standard_normal(shape).astype(np.float32)
+    u = synth.initial_guess(rng, shape, R)
+    F = O.unpack(u, shape, R)
+    t = cp.cp_tensor_dense(ctx, dev(T))
+    others = [m for m in range(3) if m != contracted]
+    out = torch.empty(sum(shape[m] for m in others) * R, dtype=torch.float64, device="cuda")
+    cp.cp_mttkrp_dimtree(ctx, t, R, dev(u), contracted, out)
+    cp.cp_ctx_sync(ctx)
+    got_all = out.cpu().numpy()
+    off = 0
+    for n in others:
+        ref = O.mttkrp_dense(T.astype(np.float64), F, n)
+        got = got_all[off:off + shape[n] * R].reshape(ref.shape)
+        off += shape[n] * R
+        assert rel(got, ref) <= MIXED_TOL, (shape, R, contracted, n)
+        check_elementwise(got, ref, dimtree_bound(T, F, n, contracted), (shape, R, contracted, n))
+
+
+def test_dimtree_full_size_dense_256(cp, ctx):
+    """Both dimension-tree pairs of the 256^3 R=16 workload against the
+    oracle's MTTKRPs, element by element."""
+    prob, u0 = synth.workload_dense_256()
+    t = cp.cp_tensor_dense(ctx, dev(prob.T))
+    F = O.unpack(u0, prob.dims, 16)
+    for contracted in (0, 2):
+        out = torch.empty(2 * 256 * 16, dtype=torch.float64, device="cuda")
+        cp.cp_mttkrp_dimtree(ctx, t, 16, dev(u0), contracted, out)
+        cp.cp_ctx_sync(ctx)
+        got_all = out.cpu().numpy()
+        for k, n in enumerate(m for m in range(3) if m != contracted):
+            ref = O.mttkrp_dense(prob.T, F, n)
+            got = got_all[k * 4096:(k + 1) * 4096].reshape(ref.shape)
+            assert rel(got, ref) <= MIXED_TOL
+            check_elementwise(got, ref, dimtree_bound(prob.T, F, n, contracted), (contracted, n))
+
+
+def test_dimtree_rejects_other_cases(cp, ctx):
+    rng = np.random.default_rng(4)
+    T4 = rng.standard_normal((5, 4, 3, 2)).astype(np.float32)
+    t4 = cp.cp_tensor_dense(ctx, dev(T4))
+    out = torch.empty(1000, dtype=torch.float64, device="cuda")
+    u = dev(synth.initial_guess(rng, T4.shape, 2))
+    with pytest.raises(cp.CpError) as ei:
+        cp.cp_mttkrp_dimtree(ctx, t4, 2, u, 0, out)
+    assert ei.value.status == 11
+    T3 = rng.standard_normal((5, 4, 3)).astype(np.float32)
+    t3 = cp.cp_tensor_dense(ctx, dev(T3))
+    u3 = dev(synth.initial_guess(rng, T3.shape, 2))
+    with pytest.raises(cp.CpError) as ei:
+        cp.cp_mttkrp_dimtree(ctx, t3, 2, u3, 1, out)
+    assert ei.value.status == 1
+    with pytest.raises(cp.CpError) as ei:
+        cp.cp_mttkrp_dimtree(ctx, t3, 2, u3, 0, out, cp.CP_FP64)
+    assert ei.value.status == 11
+
+
+@pytest.mark.parametrize("dimtree", [0, 1])
+def test_mixed_solve_with_and_without_dimension_tree(cp, ctx, dimtree):
+    """The mixed-precision solve of a 3-way problem with the sweep's and
+    ubar's MTTKRP pairs from the dimension tree (1) and from plain passes
+    (0): both meet ||g||/P < 1e-7 by the oracle's own FP64 gradient at the
+    returned point."""
+    rng = synth.rng_for(0, 51)
+    prob = synth.dense_problem(rng, (60, 50, 40), 6, 0.5, eta=0.05, dtype=np.float32)
+    u0 = synth.initial_guess(rng, prob.dims, 6)
+    t = cp.cp_tensor_dense(ctx, dev(prob.T))
+    u = dev(u0)
+    o = cp.cp_solve_opts_default(6)
+    o.prec = cp.CP_MIXED_BF16X3
+    o.dimtree = dimtree
+    rep = cp.cp_solve(ctx, t, o, u)
+    print("dimtree", dimtree, rep)
+    assert rep["converged"]
+    f, g = O.fg(O.DenseTensor(prob.T), u.cpu().numpy(), 6)
+    assert np.linalg.norm(g) / O.n_params(prob.dims, 6) < 1e-7 * 1.01
+    assert abs(f - rep["f"]) <= 1e-10 * f

@@ -162,6 +162,21 @@ def test_sparse_fg_parity(cp, ctx):
     assert rel(g.cpu().numpy(), go) <= TOL
 
 
+def sparse_als_tolerance(X, u, R, nnz):
+    """The first-order bound of the dense ALS parity test with the nonzeros
+    per row in place of Kbar: e_n = kappa(Gammabar^(n)) (eta + 3 sum_{m<n}
+    e_m), eta = (nnz + 2R) 2^-53 (a row sums at most nnz products; the Grams
+    sum I_m <= nnz terms), held to max(1e-10, 3 max e_n)."""
+    F = [A.copy() for A in O.unpack(np.array(u, dtype=np.float64), X.dims, R)]
+    errs = []
+    for n in range(len(F)):
+        Gb = O.gamma_bar(F, n)
+        eta = (max(nnz, max(X.dims)) + 2 * R) * 2.0 ** -53
+        errs.append(np.linalg.cond(Gb) * (eta + 3.0 * sum(errs)))
+        F[n] = O.als_mode_solve(X.mttkrp(F, n), Gb)
+    return max(TOL, 3.0 * max(errs))
+
+
 def test_sparse_als_sweep_tall_factor(cp, ctx):
     """A factor taller than one Gram row chunk (9000 rows): the Grams take
     the chunked path with its fixed-order cross-block sum."""
@@ -179,7 +194,10 @@ def test_sparse_als_sweep_tall_factor(cp, ctx):
     ud = dev(u)
     cp.cp_als_sweep(ctx, t, R, ud, False)
     cp.cp_ctx_sync(ctx)
-    assert rel(ud.cpu().numpy(), ref) <= 1e-8
+    tol = sparse_als_tolerance(X, u, R, nnz)
+    err = rel(ud.cpu().numpy(), ref)
+    print("sparse ALS sweep error", err, "tolerance", tol)
+    assert err <= tol
 
 
 def test_two_way_laplacian_solve_reaches_eckart_young_optimum(cp, ctx):
@@ -214,8 +232,56 @@ def test_laplacian_4way_solve_parity(cp, ctx):
     assert rep["converged"] and rep_o.converged
     f, g = O.fg(X, ud.cpu().numpy(), R)
     assert np.linalg.norm(g) / O.n_params(lap.dims, R) < 1e-7
-    assert abs(rep["f"] - rep_o.f) <= 1e-8 * rep_o.f
+    assert abs(rep["f"] - rep_o.f) <= 1e-10 * rep_o.f + 1e-14 * X.norm2
     print("iterations gpu/oracle", rep["iters"], rep_o.iters)
+
+
+# Test Problem II at the paper's shapes (Section 4, Tables 4-6): the 2d-way
+# Laplacian tensor on an s^d grid, N = 2d.
+TP2_SHAPES = [(2, 8, 6), (2, 16, 3), (3, 4, 2), (3, 8, 5), (4, 4, 2)]
+
+
+@pytest.mark.parametrize("d,s,R", TP2_SHAPES)
+def test_sparse_mttkrp_parity_test_problem_2(cp, ctx, d, s, R):
+    """Every mode's sparse MTTKRP of the N = 4, 6, 8 Laplacian tensors:
+    FP64 within 1e-10 of the oracle, FP32 products within 5e-5."""
+    lap = synth.laplacian_tensor(d, s)
+    u = synth.initial_guess(synth.rng_for(4, 100 + 10 * d + s), lap.dims, R)
+    F = O.unpack(u, lap.dims, R)
+    t = cp.cp_tensor_coo(ctx, lap.dims, dev(lap.coords), dev(lap.vals))
+    ud = dev(u)
+    for n in range(2 * d):
+        ref = O.mttkrp_sparse(lap.coords, lap.vals.astype(np.float64), lap.dims, F, n)
+        out = torch.empty(s * R, dtype=torch.float64, device="cuda")
+        out32 = torch.empty_like(out)
+        cp.cp_mttkrp(ctx, t, R, ud, n, out, cp.CP_FP64)
+        cp.cp_mttkrp(ctx, t, R, ud, n, out32, cp.CP_MIXED_BF16X3)
+        cp.cp_ctx_sync(ctx)
+        assert rel(out.cpu().numpy().reshape(ref.shape), ref) <= TOL, n
+        assert rel(out32.cpu().numpy().reshape(ref.shape), ref) <= 5e-5, n
+
+
+@pytest.mark.parametrize("d,s,R", TP2_SHAPES)
+def test_laplacian_solve_paper_shapes(cp, ctx, d, s, R):
+    """GPU solve against the oracle's solve on Test Problem II at the paper's
+    shapes, from the same seeded start, to ||g||/P < 1e-7: both converge,
+    f agrees within 1e-10 f + 1e-14 ||T||^2, and the oracle's gradient at the
+    GPU's solution meets the tolerance."""
+    lap = synth.laplacian_tensor(d, s)
+    u0 = synth.initial_guess(synth.rng_for(4, 10 * d + s), lap.dims, R)
+    X = O.SparseTensor(lap.coords, lap.vals, lap.dims)
+    uo, _, rep_o = O.cp_solve(X, u0, O.SolveOpts(R=R, tol=1e-7, maxit=5000))
+    t = cp.cp_tensor_coo(ctx, lap.dims, dev(lap.coords), dev(lap.vals))
+    ud = dev(u0)
+    opts = cp.cp_solve_opts_default(R)
+    opts.maxit = 5000
+    rep = cp.cp_solve(ctx, t, opts, ud)
+    print("Test Problem II d=%d s=%d R=%d: iterations gpu/oracle %d/%d, f %.17g / %.17g"
+          % (d, s, R, rep["iters"], rep_o.iters, rep["f"], rep_o.f))
+    assert rep["converged"] and rep_o.converged
+    f, g = O.fg(X, ud.cpu().numpy(), R)
+    assert np.linalg.norm(g) / O.n_params(lap.dims, R) < 1e-7
+    assert abs(rep["f"] - rep_o.f) <= 1e-10 * rep_o.f + 1e-14 * X.norm2
 
 
 def test_full_size_sparse_sort_and_mttkrp(cp, ctx):

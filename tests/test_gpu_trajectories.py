@@ -1,0 +1,134 @@
+"""Full-size fixed-iteration parity of the FP64 solve (Algorithm 1) against the
+FP64 oracle, through the C ABI, on the 256^3 R=16 dense workload, the
+20000^3 2e6-nonzero R=10 sparse workload and the 96^4 R=32 dense workload;
+and the whole 256^3 FP64 solve against the oracle's own solve.
+
+The oracle's trajectories are stored in tests/golden/trajectories.json by
+tests/golden/make_trajectories.py (oracle calls only; the 96^4 oracle takes
+minutes per iteration).  For j = 1..k the GPU solves from the same start with
+maxit = j and must match the oracle after j iterations:
+  * iterations, restarts, ALS sweeps, line-search trials and failed searches
+    exactly;
+  * f within 1e-10 |f| + 1e-14 ||T||^2 (the whole-solve tolerance);
+  * ||g||/P within (1e-10 (||g|| + ||M||) + (2N - 1) b_j 2 ||M||) / P:
+    g = -M + A Gammabar cancels terms of size ||M||, so its absolute error
+    scales with ||M||; and both terms are homogeneous of degree at most 2N - 1
+    in the factors, so an iterate that rounding has moved by b_j (relative,
+    below) moves them by at most (2N - 1) b_j of their size;
+  * after k iterations, the iterate (its norm, and 2000 stored entries) within
+    max(1e-10, b_k) relative, b_k the
+    first-order bound on the movement rounding alone can cause (the ALS
+    sweep bound kappa(Gammabar) (Kbar + 2R) 2^-53, accumulated over the
+    iterations; the golden file stores it)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import cp_oracle as O
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = json.load(open(os.path.join(HERE, "golden", "trajectories.json")))
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def cp():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1105_5331_gb300 as cp
+    return cp
+
+
+@pytest.fixture(scope="module")
+def ctx(cp):
+    c = cp.cp_ctx_create(0, torch.cuda.current_stream())
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def make(cp, ctx, name):
+    if name == "dense_256":
+        prob, u0 = synth.workload_dense_256()
+    elif name == "dense_4way_96":
+        prob, u0 = synth.workload_dense_4way()
+    else:
+        prob, u0 = synth.workload_sparse()
+    if name == "sparse_20000":
+        t = cp.cp_tensor_coo(ctx, prob.dims, dev(prob.coords), dev(prob.vals))
+    else:
+        t = cp.cp_tensor_dense(ctx, dev(prob.T))
+    return prob, u0, t
+
+
+@pytest.mark.parametrize("name", ["dense_256", "sparse_20000", "dense_4way_96"])
+def test_fixed_iteration_trajectory(cp, ctx, name):
+    if name not in GOLDEN:
+        pytest.skip(f"no stored oracle trajectory for {name}")
+    gold = GOLDEN[name]
+    prob, u0, t = make(cp, ctx, name)
+    R, P = gold["R"], gold["P"]
+    assert cp.cp_tensor_info(t)[2] == pytest.approx(gold["normT2"], rel=1e-12)
+    u0d = dev(u0)
+    for step in gold["steps"]:
+        j = step["iters"]
+        u = u0d.clone()
+        o = cp.cp_solve_opts_default(R)
+        o.maxit = j
+        rep = cp.cp_solve(ctx, t, o, u)
+        got = {k: rep[k] for k in ("iters", "restarts", "als_sweeps", "ls_trials", "ls_failures")}
+        want = {k: step[k] for k in got}
+        print(name, j, "f", rep["f"], step["f"], "gn", rep["gnorm_over_P"], step["gnorm_over_P"], got)
+        assert got == want, (j, got, want)
+        assert abs(rep["f"] - step["f"]) <= TOL * abs(step["f"]) + 1e-14 * gold["normT2"], j
+        N = len(gold["dims"])
+        gtol = (TOL * (step["gnorm_over_P"] * P + gold["mnorm_final"])
+                + (2 * N - 1) * step["u_bound"] * 2.0 * gold["mnorm_final"]) / P
+        assert abs(rep["gnorm_over_P"] - step["gnorm_over_P"]) <= gtol, j
+    uk = u.cpu().numpy()
+    idx = np.array(gold["u_index"])
+    ref = np.array(gold["u_sample"])
+    got_u = uk[idx]
+    assert abs(np.linalg.norm(uk) - gold["u_norm"]) <= max(TOL, gold["steps"][-1]["u_bound"]) * gold["u_norm"]
+    err = np.linalg.norm(got_u - ref) / np.linalg.norm(ref)
+    bound = max(TOL, gold["steps"][-1]["u_bound"])
+    print(name, "iterate after", gold["k"], "iterations: error", err, "bound", bound)
+    assert err <= bound
+    t.close()
+
+
+def test_dense_256_fp64_solve_matches_the_oracle_solve(cp, ctx):
+    """The whole FP64 solve of the 256^3 R=16 workload to ||g||/P < 1e-7:
+    the oracle's own solve (oracle/workload_iters.json, written by
+    oracle/workload_iters.py) took 588 iterations with 271 restarts; the GPU
+    must take the same iterations and restarts and reach the same f within
+    1e-10, and the oracle's gradient at the GPU's solution must meet the
+    tolerance.  The line-search trial count and the number of searches that
+    ended without both Wolfe conditions are printed, not asserted: over ~300
+    searches an exit test taken at rounding level (a trial's curvature within
+    an ulp of gtol |phi'(0)|) may go the other way without moving the
+    accepted point, as the matching iterations and f show."""
+    ref = json.load(open(os.path.join(os.path.dirname(HERE), "oracle", "workload_iters.json")))["dense_256"]
+    prob, u0, t = make(cp, ctx, "dense_256")
+    u = dev(u0)
+    o = cp.cp_solve_opts_default(16)
+    rep = cp.cp_solve(ctx, t, o, u)
+    print("GPU iterations, restarts, f, trials, failed searches:", rep["iters"], rep["restarts"], rep["f"],
+          rep["ls_trials"], rep["ls_failures"], "oracle:", ref["iters"], ref["restarts"], ref["f"],
+          ref["fg_evals"] - 1 - ref["iters"], ref["ls_failures"])
+    assert rep["converged"] and ref["converged"]
+    assert (rep["iters"], rep["restarts"]) == (ref["iters"], ref["restarts"])
+    X = O.DenseTensor(prob.T)
+    assert abs(rep["f"] - ref["f"]) <= TOL * ref["f"] + 1e-14 * X.norm2
+    f, g = O.fg(X, u.cpu().numpy(), 16)
+    assert np.linalg.norm(g) / O.n_params(prob.dims, 16) < 1e-7
+    assert abs(f - rep["f"]) <= TOL * f
+    t.close()
