@@ -48,7 +48,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mttkrp-only", default=None, choices=["dense_256", "dense_4way", "sparse", "sparse_scaled"],
+    p.add_argument("--mttkrp-only", default=None,
+                   choices=["dense_256", "dense_4way", "sparse", "sparse_scaled", "dimtree_256"],
                    help="time only cp_mttkrp on that workload (profiling driver)")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--accuracy-report", default=None, choices=["dense_256", "dense_4way"],
@@ -70,6 +71,9 @@ def parse():
                    help="dimension-tree MTTKRP pairs in the mixed solve: -1 library default, 0 off, 1 on")
     p.add_argument("--fixed-iters", type=int, default=0,
                    help="solve-only timing at exactly this many iterations (tolerance out of reach): ms per iteration")
+    p.add_argument("--precision-table", type=int, default=0,
+                   help="solve the first N serving-stream requests alone in FP64 and in mixed precision; "
+                        "one JSON line per request (time, iterations, entries)")
     p.add_argument("--no-workloads", action="store_true",
                    help="skip the 20^3, 96^4 and sparse workload blocks of the bench line")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -592,6 +596,88 @@ def aggregate_replicas(times, world):
     return world * len(times) / total_max, total_max
 
 
+def dimtree_timing(cp, reps=5):
+    """The 256^3 R=16 workload: cp_mttkrp_dimtree (W = T x_c A^(c) on the
+    tensor cores, both other modes' MTTKRPs from W) against two mixed
+    cp_mttkrp calls for the same modes; CUDA events around each call, the
+    tensor-core kernel timed alone by the library timers, L2 flushed before."""
+    import torch
+    import synth
+    prob, u0 = synth.workload_dense_256()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    ctx = cp.cp_ctx_create(0, stream)
+    with torch.cuda.stream(stream):
+        T = torch.from_numpy(prob.T).to(dev)
+        u = torch.from_numpy(u0).to(dev)
+    flush = L2Flush(dev)
+    stream.synchronize()
+    t = cp.cp_tensor_dense(ctx, T)
+    out = torch.empty(2 * 256 * 16, dtype=torch.float64, device=dev)
+    res = {}
+    for c in (0, 2):
+        modes = [m for m in range(3) if m != c]
+        for name, fn in (("dimtree", lambda: cp.cp_mttkrp_dimtree(ctx, t, 16, u, c, out)),
+                         ("two_mttkrps", lambda: [cp.cp_mttkrp(ctx, t, 16, u, m, out[k * 4096:(k + 1) * 4096],
+                                                                cp.CP_MIXED_BF16X3) for k, m in enumerate(modes)])):
+            call = []
+            for k in range(reps + 1):
+                if k == 1:
+                    cp.cp_ctx_timer_enable(ctx, True)
+                flush(stream, k)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                if k > 0:
+                    call.append(e0.elapsed_time(e1) * 1e3)
+            tc_ms, launches = cp.cp_ctx_timer_read(ctx, cp.TIMER_TC)
+            cp.cp_ctx_timer_enable(ctx, False)
+            res[f"c{c}_{name}"] = {"call_us": sum(call) / len(call), "tc_kernel_us_total": 1e3 * tc_ms / reps,
+                                   "tc_launches_per_call": launches / reps}
+    return res
+
+
+def run_precision_table(args):
+    """Each of the first N requests of the serving stream solved alone, FP64
+    and mixed (FP64-polished), from the same start, CUDA-event timed after one
+    warm-up solve of each: the size at which mixed precision starts to pay."""
+    import torch
+    import synth
+    import paper_1105_5331_gb300 as cp
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    ctx = cp.cp_ctx_create(0, stream)
+    reqs = synth.request_stream(args.precision_table, rate_per_s=200.0, config=5)
+    rows = []
+    for r in reqs:
+        prob, u0 = synth.request_problem(r, config=5)
+        with torch.cuda.stream(stream):
+            T = torch.from_numpy(prob.T).to(dev)
+            u0d = torch.from_numpy(u0).to(dev)
+        stream.synchronize()
+        t = cp.cp_tensor_dense(ctx, T)
+        row = {"id": r.request_id, "dims": list(r.dims), "R": r.R, "tol": r.tol, "entries": int(T.numel())}
+        for name, prec in (("fp64", cp.CP_FP64), ("mixed", cp.CP_MIXED_BF16X3)):
+            o = cp.cp_solve_opts_default(r.R)
+            o.tol = r.tol
+            o.prec = prec
+            for k in range(2):
+                with torch.cuda.stream(stream):
+                    u = u0d.clone()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rep = cp.cp_solve(ctx, t, o, u)
+                e1.record(stream)
+                e1.synchronize()
+            row[name] = {"ms": e0.elapsed_time(e1), "iters": rep["iters"], "converged": rep["converged"]}
+        t.close()
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    ctx.close()
+
+
 def run_mttkrp_only(args):
     """cp_mttkrp on every mode of a workload, `reps` launches per mode with an
     L2 flush before each; prints per-mode average times (profiling driver)."""
@@ -599,6 +685,9 @@ def run_mttkrp_only(args):
 
     import synth
     import paper_1105_5331_gb300 as cp
+    if args.mttkrp_only == "dimtree_256":
+        print(json.dumps({"mttkrp_only": "dimtree_256", **dimtree_timing(cp)}))
+        return
     if args.mttkrp_only == "sparse_scaled":
         dev = torch.device("cuda", 0)
         stream = torch.cuda.Stream(dev)
@@ -1089,6 +1178,9 @@ def main():
         return
     if args.mttkrp_only:
         run_mttkrp_only(args)
+        return
+    if args.precision_table:
+        run_precision_table(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

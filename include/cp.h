@@ -161,7 +161,8 @@ cp_status cp_mttkrp_variants(cp_ctx* ctx, const cp_tensor* t, int R, const doubl
  * M^(b)[j, r] = sum_i W[i, j, r] A^(a)[i, r].  out: M^(a) (I_a x R) then
  * M^(b) (I_b x R), row-major doubles.  CP_MIXED_BF16X3 only (W on the
  * tensor cores with bf16x3 split products and FP32 accumulation; the two
- * contractions in FP64); CP_ERR_UNSUPPORTED otherwise.  Asynchronous. */
+ * contractions with FP32 copies of the factors, FP32 sums);
+ * CP_ERR_UNSUPPORTED otherwise.  Asynchronous. */
 cp_status cp_mttkrp_dimtree(cp_ctx* ctx, const cp_tensor* t, int R, const double* u, int contracted,
                             double* out, cp_precision prec);
 
@@ -275,7 +276,7 @@ typedef struct {
   int dimtree;         /* 3-way dense tensors in the mixed phase: the sweep's */
                        /* M^(2), M^(3) from W = T x_1 A^(1), and M^(1), M^(2) */
                        /* at ubar from T x_3 A^(3) (see cp_mttkrp_dimtree):  */
-                       /* 1 on; 0 or -1 (default) off                         */
+                       /* 1 on, 0 off, -1 (default) when prod(dims) >= 2^21  */
 } cp_solve_opts;
 
 typedef struct {

@@ -455,7 +455,7 @@ cp_status als_sweep_v2(cp_ctx* ctx, const cp_tensor* t_in, const Layout& L, doub
       if (n == 1) CP_TRY(dimtree_w(ctx, t, L, u32, o32, 0, &W));
       double* M = nullptr;
       CP_TRY(ws_alloc(ctx, (void**)&M, sizeof(double) * (size_t)L.dims[n] * R));
-      CP_TRY(dimtree_contract(ctx, t, L, W, 0, n, u, M));
+      CP_TRY(dimtree_contract(ctx, t, L, W, 0, n, u32, o32, M));
       pt = Parts{M, 1, 0};
     } else {
       CP_TRY(mttkrp_parts(ctx, t, L, u, u32, o32, n, prec, &pt));

@@ -491,8 +491,8 @@ cp_status cp_mttkrp_dimtree(cp_ctx* ctx, const cp_tensor* t, int R, const double
   Parts W;
   CP_TRY(dimtree_w(ctx, tt, L, u32, o32, contracted, &W));
   const int a = contracted == 0 ? 1 : 0, b = contracted == 2 ? 1 : 2;
-  CP_TRY(dimtree_contract(ctx, t, L, W, contracted, a, u, out));
-  CP_TRY(dimtree_contract(ctx, t, L, W, contracted, b, u, out + t->dims[a] * R));
+  CP_TRY(dimtree_contract(ctx, t, L, W, contracted, a, u32, o32, out));
+  CP_TRY(dimtree_contract(ctx, t, L, W, contracted, b, u32, o32, out + t->dims[a] * R));
   ws_free(ctx, const_cast<void*>(W.p));
   ws_free(ctx, u32);
   return CP_OK;

@@ -263,13 +263,14 @@ cp_status mttkrp_tc_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L, const f
                              const F32Off& o, const int* modes, int nmodes, Parts* out);
 bool tc_variants_supported(const Layout& L);
 // Dimension tree (3-way dense, mixed precision): W = T x_c A^(c) on the
-// tensor cores (partial sums in *W), and the MTTKRP of `mode` (one of the
-// two modes other than c) from W with the other factor taken from u (FP64).
+// tensor cores (in *W), and the MTTKRP of `mode` (one of the two modes other
+// than c) from W and the other factor's FP32 copy (u32, f32_layout), summed
+// in FP32 and written as FP64.
 cp_status prepare_dimtree(cp_ctx* ctx, cp_tensor* t);
 cp_status dimtree_w(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32, const F32Off& o32, int contracted,
                     Parts* W);
 cp_status dimtree_contract(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const Parts& W, int contracted,
-                           int mode, const double* u, double* out);
+                           int mode, const float* u32, const F32Off& o32, double* out);
 
 // Normalise src (and gsrc) into dst (and gdst); lambda (R) optional.  With
 // grams (N x R x R, the Grams of src) the column norms come from their

@@ -922,72 +922,307 @@ cp_status mttkrp_dense_mixed_variants(cp_ctx* ctx, cp_tensor* t, const Layout& L
 // ---------------------------------------------------------------------------
 namespace {
 
-// out[a, r] = sum_b W[a B + b, r] F[b, r], W = sum of `count` FP32 partials
-// (pitch A B R).  One block per a; thread t = q R + r takes b = q, q + Q, ...
-// (Q = 256 / R); the Q sums of each r are added in q order.
-__global__ void __launch_bounds__(256) contract_fast_kernel(const float* __restrict__ W, int count, int64_t A,
-                                                            int64_t B, int R, const double* __restrict__ F,
+// out[a, r] = sum_b W[a B + b, r] F[b, r] in FP32 (W one FP32 buffer, A B x R;
+// F the FP32 factor copy, row stride rs), written as FP64.  One block per a;
+// thread t = q R + r takes b = q, q + Q, ... (Q = 256 / R), kU of them with
+// all their reads issued before the FMAs; the Q sums of each r are added in
+// q order.
+constexpr int kContractU = 8;
+
+__global__ void __launch_bounds__(256) contract_fast_kernel(const float* __restrict__ W, int A, int B, int R,
+                                                            const float* __restrict__ F, int rs,
                                                             double* __restrict__ out) {
   CP_PDL_ENTRY();
-  __shared__ double red[256];
+  __shared__ float red[256];
   const int Q = 256 / R;
   const int t = threadIdx.x;
-  const int q = t / R, r = t - (t / R) * R;
-  const int64_t pitch = A * B * R;
-  for (int64_t a = blockIdx.x; a < A; a += gridDim.x) {
-    double acc = 0.0;
-    if (q < Q) {
-      for (int64_t b = q; b < B; b += Q) {
-        const int64_t e = (a * B + b) * R + r;
-        float w = 0.f;
-        for (int c = 0; c < count; ++c) w += __ldg(&W[(int64_t)c * pitch + e]);
-        acc = fma((double)w, F[b * R + r], acc);
+  const int q = t / R, r = t - q * R;
+  const int nb = q < Q ? (B - q + Q - 1) / Q : 0;       // this thread's b count
+  const int wstep = Q * R, fstep = Q * rs;
+  for (int a = blockIdx.x; a < A; a += gridDim.x) {
+    const float* wp = W + ((size_t)a * B + q) * R + r;
+    const float* fp = F + (size_t)q * rs + r;
+    float acc = 0.f;
+    for (int k0 = 0; k0 < nb; k0 += kContractU) {
+      float w[kContractU], f[kContractU];
+#pragma unroll
+      for (int u = 0; u < kContractU; ++u) {
+        const bool in = k0 + u < nb;
+        w[u] = in ? __ldg(wp + (size_t)(k0 + u) * wstep) : 0.f;
+        f[u] = in ? __ldg(fp + (size_t)(k0 + u) * fstep) : 0.f;
       }
+#pragma unroll
+      for (int u = 0; u < kContractU; ++u) acc = fmaf(w[u], f[u], acc);
     }
     red[t] = acc;
     __syncthreads();
     if (t < R) {
-      double sum = 0.0;
+      float sum = 0.f;
       for (int k = 0; k < Q; ++k) sum += red[k * R + t];
-      out[a * R + t] = sum;
+      out[(size_t)a * R + t] = (double)sum;
     }
     __syncthreads();
   }
 }
 
-// out[b, r] = sum_a W[a B + b, r] F[a, r].  Block x covers 32 consecutive
-// (b, r) elements (one per lane); warp w takes a = w, w + 8, ...; the eight
-// warp sums are added in warp order.
-__global__ void __launch_bounds__(256) contract_slow_kernel(const float* __restrict__ W, int count, int64_t A,
-                                                            int64_t B, int R, const double* __restrict__ F,
-                                                            double* __restrict__ out) {
+// out[b, r] = sum_a W[a B + b, r] F[a, r] in FP32, written as FP64.  Block x
+// covers 32 consecutive (b, r) elements (one per lane); warp w of 32 takes
+// a = w, w + 32, ..., kU of them with all their reads issued before the FMAs;
+// the 32 warp sums are added in warp order.
+__global__ void __launch_bounds__(1024) contract_slow_kernel(const float* __restrict__ W, int A, int B, int R,
+                                                             const float* __restrict__ F, int rs,
+                                                             double* __restrict__ out) {
   CP_PDL_ENTRY();
-  __shared__ double red[8][32];
+  __shared__ float red[32][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t BR = B * R;
-  const int64_t pitch = A * BR;
-  const int64_t e = (int64_t)blockIdx.x * 32 + lane;     // b R + r
+  const int BR = B * R;
+  const int e = blockIdx.x * 32 + lane;                 // b R + r
   const bool in = e < BR;
-  const int r = in ? (int)(e % R) : 0;
-  double acc = 0.0;
-  if (in) {
-    for (int64_t a = w; a < A; a += 8) {
-      float x = 0.f;
-      for (int c = 0; c < count; ++c) x += __ldg(&W[(int64_t)c * pitch + a * BR + e]);
-      acc = fma((double)x, F[a * R + r], acc);
+  const int r = in ? e % R : 0;
+  const int na = in && w < A ? (A - w + 31) / 32 : 0;   // this thread's a count
+  const float* wp = W + (size_t)w * BR + e;
+  const float* fp = F + (size_t)w * rs + r;
+  const size_t wstep = (size_t)32 * BR, fstep = (size_t)32 * rs;
+  float acc = 0.f;
+  for (int k0 = 0; k0 < na; k0 += kContractU) {
+    float x[kContractU], f[kContractU];
+#pragma unroll
+    for (int u = 0; u < kContractU; ++u) {
+      const bool ok = k0 + u < na;
+      x[u] = ok ? __ldg(wp + (k0 + u) * wstep) : 0.f;
+      f[u] = ok ? __ldg(fp + (k0 + u) * fstep) : 0.f;
     }
+#pragma unroll
+    for (int u = 0; u < kContractU; ++u) acc = fmaf(x[u], f[u], acc);
   }
   red[w][lane] = acc;
   __syncthreads();
   if (w == 0 && in) {
-    double sum = 0.0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) sum += red[k][lane];
-    out[e] = sum;
+    float sum = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) sum += red[k][lane];
+    out[e] = (double)sum;
+  }
+}
+
+// W = sum of `count` FP32 partials (pitch n) into one FP32 buffer, in order.
+__global__ void sum_parts_f32_kernel(const float* __restrict__ part, int count, int64_t n, float* __restrict__ out) {
+  CP_PDL_ENTRY();
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int c = 0; c < count; ++c) s += part[(int64_t)c * n + k];
+    out[k] = s;
   }
 }
 
 }  // namespace
+
+// The dimension tree's GEMM W = T_mat F (rows x K, K x R) as a persistent
+// tensor-core kernel: W has many rows and a short contraction (one mode's
+// length), so each CTA (one per SM) takes 128-row tiles m = blockIdx.x,
+// blockIdx.x + gridDim.x, ... with one TMEM accumulator per tile, two of
+// them alternating, so that a tile's epilogue overlaps the next tile's MMAs;
+// the B operand (F split into bf16 hi / lo, all nk contraction tiles) is
+// built once into shared memory, and the tiles of T stream through a ring of
+// stages as in the MTTKRP kernel.  Warps: 0 bulk-copy producer, 1 TMEM and
+// MMA issuer, 2-5 B builders and then the epilogue.  Every wait is bounded.
+struct GemmParams {
+  const uint8_t* tiles;   // pre-tiled hi / lo planes of the rows x K matrix
+  int64_t rows;
+  int K, nk;              // contraction length and tiles of 64
+  const float* F;         // K x rs FP32 (row stride rs floats)
+  int rs, R, RP;
+  int stages;
+  uint32_t ncols;         // TMEM columns (two accumulators of RP)
+  float* W;               // rows x R FP32
+  int* status;
+};
+constexpr int kGemmMaxTiles = 8;        // contraction tiles held in shared memory (K <= 512)
+
+__global__ void __launch_bounds__(kThreads, 1) dimtree_gemm_kernel(const __grid_constant__ GemmParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t b_bytes = (uint32_t)p.RP * 128u;     // one plane of one B tile
+  const uint32_t btile = 2u * b_bytes;                 // hi then lo (a multiple of 1024 bytes)
+  const uint32_t abase = base + (uint32_t)p.nk * btile;
+  const uint32_t stage_bytes = 2u * kTileBytes;        // hi then lo A tile
+  const int S = p.stages;
+  const uint32_t bars = abase + (uint32_t)S * stage_bytes;
+  auto full_bar = [&](int s) { return bars + 8u * (uint32_t)s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (uint32_t)(S + s); };
+  auto accf_bar = [&](int b) { return bars + 16u * (uint32_t)S + 8u * (uint32_t)b; };
+  auto acce_bar = [&](int b) { return bars + 16u * (uint32_t)S + 16u + 8u * (uint32_t)b; };
+  const uint32_t bready_bar = bars + 16u * (uint32_t)S + 32u;
+  const uint32_t tmem_slot = bready_bar + 8u;
+  volatile uint32_t* tmem_slot_ptr = (volatile uint32_t*)(gbase + (tmem_slot - base));
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t mtiles = (p.rows + kBM - 1) / kBM;
+  const int nm = blockIdx.x < mtiles ? (int)((mtiles - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf_bar(b), 1);
+      mbar_init(acce_bar(b), 128);
+    }
+    mbar_init(bready_bar, 128);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_proxy_async();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tmem_slot),
+                 "r"(p.ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot_ptr;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      CP_PDL_WAIT();
+      CP_PDL_TRIGGER();
+      int issued = 0;
+      bool ok = true;
+      for (int j = 0; j < nm && ok; ++j) {
+        const int64_t m = blockIdx.x + (int64_t)j * gridDim.x;
+        const uint32_t blk = 128u * (uint32_t)min((int64_t)kBM, p.rows - m * kBM);
+        for (int kt = 0; kt < p.nk; ++kt) {
+          const int i = j * p.nk + kt;
+          const int s = i % S;
+          if (!mbar_wait(empty_bar(s), (uint32_t)(((i / S) & 1) ^ 1), p.status)) {
+            ok = false;
+            break;
+          }
+          const uint32_t st = abase + (uint32_t)s * stage_bytes;
+          const uint8_t* src = p.tiles + (int64_t)kt * (2 * p.rows * 128) + m * (2 * kBM * 128);
+          mbar_arrive_tx(full_bar(s), 2u * blk);
+          bulk_load(st, src, blk, full_bar(s));
+          bulk_load(st + kTileBytes, src + blk, blk, full_bar(s));
+          ++issued;
+        }
+      }
+      // let copies still in flight land before the CTA can exit
+      for (int i = max(0, issued - S); i < issued; ++i)
+        mbar_wait(full_bar(i % S), (uint32_t)((i / S) & 1), p.status);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0 && mbar_wait(bready_bar, 0u, p.status)) {
+      tc_fence_after();
+      const uint32_t idesc = idesc_bf16(kBM, p.RP);
+      bool ok = true;
+      for (int j = 0; j < nm && ok; ++j) {
+        const int buf = j & 1;
+        if (!mbar_wait(acce_bar(buf), (uint32_t)(((j >> 1) & 1) ^ 1), p.status)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * p.RP);
+        for (int kt = 0; kt < p.nk; ++kt) {
+          const int i = j * p.nk + kt;
+          const int s = i % S;
+          if (!mbar_wait(full_bar(s), (uint32_t)((i / S) & 1), p.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ahi = abase + (uint32_t)s * stage_bytes;
+          const uint32_t alo = ahi + kTileBytes;
+          const uint32_t bhi = base + (uint32_t)kt * btile;
+          const uint32_t blo = bhi + b_bytes;
+#pragma unroll
+          for (int q = 0; q < kBK / 16; ++q) {
+            const uint32_t off = (uint32_t)q * 32u;
+            mma_bf16(d, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, (kt > 0 || q > 0) ? 1u : 0u);
+            mma_bf16(d, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
+            mma_bf16(d, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, 1u);
+          }
+          mma_commit(empty_bar(s));
+        }
+        if (ok) mma_commit(accf_bar(buf));
+      }
+    }
+  } else {
+    // --------------------------------------------- B tiles, then the epilogue
+    CP_PDL_WAIT();      // F is written by the preceding kernel
+    CP_PDL_TRIGGER();
+    // thread t takes groups g = t, t + 128, ... of four columns of one
+    // contraction element (a 16-byte read of F), eight groups in flight
+    const int t = threadIdx.x - 64;              // 0..127
+    const int gpr = p.RP >> 2;                   // column groups per contraction element
+    const int ngroups = p.nk * kBK * gpr;
+    for (int g0 = t; g0 < ngroups; g0 += 128 * 8) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int g = g0 + 128 * u;
+        const int kappa = g / gpr;
+        const int c4 = (g - kappa * gpr) * 4;
+        v[u] = (g < ngroups && kappa < p.K && c4 < p.rs)
+                   ? __ldg(reinterpret_cast<const float4*>(p.F + (int64_t)kappa * p.rs + c4))
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int g = g0 + 128 * u;
+        if (g >= ngroups) break;
+        const int kappa = g / gpr;
+        const int c4 = (g - kappa * gpr) * 4;
+        const int kt = kappa / kBK;
+        const uint32_t kk = (uint32_t)(kappa - kt * kBK);
+        uint8_t* bhi = gbase + (size_t)kt * btile;
+        const float xs[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t c = (uint32_t)(c4 + q);
+          const float x = (int)c < p.R ? xs[q] : 0.f;
+          const __nv_bfloat16 h = __float2bfloat16_rn(x);
+          const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+          const uint32_t off = c * 128u + (((kk >> 3) ^ (c & 7u)) << 4) + (kk & 7u) * 2u;
+          *(__nv_bfloat16*)(bhi + off) = h;
+          *(__nv_bfloat16*)(bhi + b_bytes + off) = l;
+        }
+      }
+    }
+    fence_proxy_async();
+    mbar_arrive(bready_bar);
+    const int qd = warp & 3;                     // TMEM lane quarter of this warp
+    for (int j = 0; j < nm; ++j) {
+      const int buf = j & 1;
+      if (!mbar_wait(accf_bar(buf), (uint32_t)((j >> 1) & 1), p.status)) break;
+      tc_fence_after();
+      const int64_t row = (blockIdx.x + (int64_t)j * gridDim.x) * kBM + qd * 32 + lane;
+      for (int c = 0; c < p.RP; c += 16) {
+        uint32_t v[16];
+        tmem_ld16_async(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * p.RP + c), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < p.rows) {
+          float* out = p.W + row * p.R;
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (c + e < p.R) out[c + e] = __uint_as_float(v[e]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(acce_bar(buf));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.ncols) : "memory");
+  }
+}
 
 // W = T x_c A^(c) on the tensor cores: one job, the factor's FP32 copy (row
 // stride rs) as its only table; the partial sums (gx x rows x R FP32) in *W.
@@ -999,6 +1234,44 @@ static cp_status tc_gemm_launch(cp_ctx* ctx, cp_tensor* t, int which, const floa
   CP_TRY(ensure_gemm_planes(ctx, t, which));
   const int64_t K = which == 0 ? t->dims[0] : t->dims[t->N - 1];
   const int64_t rows = t->K / K;
+  {
+    GemmParams g{};
+    g.tiles = (const uint8_t*)tc_state(t)->gemm_tiles[which];
+    g.rows = rows;
+    g.K = (int)K;
+    g.nk = (int)((K + kBK - 1) / kBK);
+    g.F = F32;
+    g.rs = rs;
+    g.R = R;
+    g.RP = std::max(16, (R + 15) / 16 * 16);
+    const size_t btiles = (size_t)g.nk * 2 * g.RP * 128;
+    const size_t fixed = 1024 + 256;
+    const size_t stages = ((size_t)kMaxDynSmem - fixed - std::min(btiles, (size_t)kMaxDynSmem)) / (2 * kTileBytes);
+    if (g.nk <= kGemmMaxTiles && btiles <= 96 * 1024 && stages >= 2) {
+      g.stages = (int)std::min<size_t>(6, stages);
+      g.ncols = 32;
+      while (g.ncols < (uint32_t)(2 * g.RP)) g.ncols <<= 1;
+      g.status = ctx->d_status;
+      float* Wout = nullptr;
+      CP_TRY(ws_alloc(ctx, (void**)&Wout, sizeof(float) * (size_t)rows * R));
+      g.W = Wout;
+      static bool attr = false;
+      if (!attr) {
+        CP_CUDA(cudaFuncSetAttribute(dimtree_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+        attr = true;
+      }
+      const int64_t mtiles = (rows + kBM - 1) / kBM;
+      const unsigned grid = (unsigned)std::min<int64_t>(mtiles, ctx->num_sms);
+      const size_t smem = fixed + btiles + (size_t)g.stages * 2 * kTileBytes;
+      {
+        TimerScope ts(ctx, 0);
+        (void)launch_pdl(dimtree_gemm_kernel, dim3(grid), dim3(kThreads), smem, ctx->stream, g);
+      }
+      CP_LAUNCH_CHECK();
+      *W = Parts{Wout, 1, 1};
+      return CP_OK;
+    }
+  }
   TcParams p{};
   p.njobs = 1;
   p.R = R;
@@ -1031,28 +1304,42 @@ cp_status dimtree_w(cp_ctx* ctx, cp_tensor* t, const Layout& L, const float* u32
     set_error("dimension tree: 3-way dense tensors, first or last mode only");
     return CP_ERR_UNSUPPORTED;
   }
-  return tc_gemm_launch(ctx, t, contracted == 0 ? 0 : 1, u32 + o32.off[contracted], o32.rs, L.R, W);
+  CP_TRY(tc_gemm_launch(ctx, t, contracted == 0 ? 0 : 1, u32 + o32.off[contracted], o32.rs, L.R, W));
+  if (W->count > 1) {
+    // the split-K form (contractions too long for the persistent kernel):
+    // one FP32 buffer for the contractions
+    const int64_t n = t->K / t->dims[contracted] * L.R;
+    float* one = nullptr;
+    CP_TRY(ws_alloc(ctx, (void**)&one, sizeof(float) * (size_t)n));
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * ctx->num_sms));
+    (void)launch_pdl(sum_parts_f32_kernel, dim3(blocks), dim3(256), 0, ctx->stream, (const float*)W->p, W->count, n,
+                     one);
+    CP_LAUNCH_CHECK();
+    ws_free(ctx, const_cast<void*>(W->p));
+    *W = Parts{one, 1, 1};
+  }
+  return CP_OK;
 }
 
 cp_status dimtree_contract(cp_ctx* ctx, const cp_tensor* t, const Layout& L, const Parts& W, int contracted,
-                           int mode, const double* u, double* out) {
+                           int mode, const float* u32, const F32Off& o32, double* out) {
   // W's rows: (i_a, i_b) with a < b the two modes other than `contracted`
   const int a = contracted == 0 ? 1 : 0;
   const int b = contracted == 2 ? 1 : 2;
   const int64_t A = t->dims[a], B = t->dims[b];
   const int R = L.R;
-  if (R > 256 || !W.f32) {
+  if (R > 256 || !W.f32 || W.count != 1 || (int64_t)A * B * R >= ((int64_t)1 << 31)) {
     set_error("dimension tree: rank %d / partials not supported", R);
     return CP_ERR_UNSUPPORTED;
   }
   if (mode == a) {
     const unsigned blocks = (unsigned)std::min<int64_t>(A, 8 * (int64_t)ctx->num_sms);
-    (void)launch_pdl(contract_fast_kernel, dim3(blocks), dim3(256), 0, ctx->stream, (const float*)W.p, W.count, A, B,
-                     R, u + L.off[b], out);
+    (void)launch_pdl(contract_fast_kernel, dim3(blocks), dim3(256), 0, ctx->stream, (const float*)W.p, (int)A, (int)B,
+                     R, u32 + o32.off[b], o32.rs, out);
   } else if (mode == b) {
     const unsigned blocks = (unsigned)((B * R + 31) / 32);
-    (void)launch_pdl(contract_slow_kernel, dim3(blocks), dim3(256), 0, ctx->stream, (const float*)W.p, W.count, A, B,
-                     R, u + L.off[a], out);
+    (void)launch_pdl(contract_slow_kernel, dim3(blocks), dim3(1024), 0, ctx->stream, (const float*)W.p, (int)A, (int)B,
+                     R, u32 + o32.off[a], o32.rs, out);
   } else {
     set_error("dimension tree: mode %d is not one W serves", mode);
     return CP_ERR_ARG;

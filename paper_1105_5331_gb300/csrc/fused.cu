@@ -255,7 +255,7 @@ static cp_status mttkrp_parts_multi(cp_ctx* ctx, cp_tensor* t, const Layout& L, 
     for (int k = 0; k < 2; ++k) {
       double* M = nullptr;
       CP_TRY(ws_alloc(ctx, (void**)&M, sizeof(double) * (size_t)L.dims[k] * L.R));
-      CP_TRY(dimtree_contract(ctx, t, L, W, 2, k, u, M));
+      CP_TRY(dimtree_contract(ctx, t, L, W, 2, k, u32, o32, M));
       out[k] = Parts{M, 1, 0};
     }
     ws_free(ctx, const_cast<void*>(W.p));

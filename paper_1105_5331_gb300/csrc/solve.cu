@@ -426,9 +426,11 @@ cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts&
   CP_CUDA(cudaMemsetAsync(m.ctl, 0, sizeof(SolveCtl), sub.stream));
   CP_CUDA(cudaMemsetAsync(m.u32, 0, 3 * n32 * sizeof(double), sub.stream));
   if (o.prec != CP_FP64) CP_TRY(prepare_mixed(&sub, t));
-  // dimension tree for the mixed phase of 3-way dense solves (on request;
-  // off by default: 362 against 323 us per iteration on the 256^3 workload)
-  sub.dimtree = o.prec == CP_MIXED_BF16X3 && t->kind == 0 && t->N == 3 && o.dimtree > 0;
+  // dimension tree for the mixed phase of 3-way dense solves: on request, or
+  // by default from 2^21 tensor entries up (256^3, R = 16: the pair of
+  // MTTKRPs in 40 instead of 66 us, 316 against 326 us per iteration)
+  sub.dimtree = o.prec == CP_MIXED_BF16X3 && t->kind == 0 && t->N == 3 &&
+                (o.dimtree > 0 || (o.dimtree < 0 && t->K >= ((int64_t)1 << 21)));
   if (sub.dimtree) CP_TRY(prepare_dimtree(&sub, t));
   return CP_OK;
 }

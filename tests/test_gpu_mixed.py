@@ -341,12 +341,13 @@ def match_terms(A, B):
 
 
 # Dimension tree (3-way): W = T x_c A^(c) in one tensor-core pass, then the
-# MTTKRPs of the two other modes from W.  W's GEMM has rows over the two
-# other modes and the contraction over mode c, so its accumulation chain is
-# that of a launch with rows = I_a I_b and Kbar = I_c; its split products
-# involve T and one FP32 factor: c = 3.01 2^-16 + 2 2^-24 + (n_mma + 1) 2^-22,
-# applied to |T_(n)| |Phibar| as for the MTTKRP (the FP64 contraction of W
-# with the other factor adds 2^-53 terms).
+# MTTKRPs of the two other modes from W.  W's split products involve T and one
+# FP32 factor; its tensor-core accumulation runs over the I_c / 64
+# contraction tiles of a 128-row tile (n_mma = 12 I_c / 64, the kernel keeps
+# each tile's whole contraction in one accumulator); the contraction of W
+# with the other factor's FP32 copy sums I_m products in FP32 (m the mode
+# summed out).  So c = 3.01 2^-16 + 3 2^-24 + (n_mma + 1) 2^-22 + I_m 2^-24,
+# applied to |T_(n)| |Phibar| as for the MTTKRP.
 DIMTREE_CASES = [((20, 20, 20), 3), ((130, 33, 17), 16), ((96, 80, 70), 16), ((17, 65, 200), 5),
                  ((40, 30, 20), 64)]
 
@@ -354,9 +355,9 @@ DIMTREE_CASES = [((20, 20, 20), 3), ((130, 33, 17), 16), ((96, 80, 70), 16), ((1
 def dimtree_bound(T, F, n, contracted):
     Tabs = np.abs(np.asarray(T, dtype=np.float64))
     B = O.mttkrp_dense(Tabs, [np.abs(A) for A in F], n)
-    rows = T.size // T.shape[contracted]
-    n_mma = 12 * split_k_tiles_per_cta(rows, T.shape[contracted])
-    c = 3.01 * 2.0 ** -16 + 2 * 2.0 ** -24 + (n_mma + 1) * 2.0 ** -22
+    n_mma = 12 * -(-T.shape[contracted] // 64)
+    summed = [m for m in range(3) if m not in (n, contracted)][0]
+    c = 3.01 * 2.0 ** -16 + 3 * 2.0 ** -24 + (n_mma + 1) * 2.0 ** -22 + T.shape[summed] * 2.0 ** -24
     return c * B
 
 
