@@ -74,6 +74,9 @@ def parse():
     p.add_argument("--precision-table", type=int, default=0,
                    help="solve the first N serving-stream requests alone in FP64 and in mixed precision; "
                         "one JSON line per request (time, iterations, entries)")
+    p.add_argument("--table-mixed-only", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--mixed-stall", type=int, default=0, help=argparse.SUPPRESS)
+    p.add_argument("--serve-only", action="store_true", help="only the serving stream block (profiling driver)")
     p.add_argument("--no-workloads", action="store_true",
                    help="skip the 20^3, 96^4 and sparse workload blocks of the bench line")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -486,6 +489,7 @@ def serving_run(cp, ctx, args):
         o = cp.cp_solve_opts_default(r.R)
         o.tol = r.tol
         o.prec = prec
+        o.dimtree = args.dimtree
         return o
 
     def run(prec, count, open_loop):
@@ -660,9 +664,12 @@ def run_precision_table(args):
         t = cp.cp_tensor_dense(ctx, T)
         row = {"id": r.request_id, "dims": list(r.dims), "R": r.R, "tol": r.tol, "entries": int(T.numel())}
         for name, prec in (("fp64", cp.CP_FP64), ("mixed", cp.CP_MIXED_BF16X3)):
+            if args.table_mixed_only and prec == cp.CP_FP64:
+                continue
             o = cp.cp_solve_opts_default(r.R)
             o.tol = r.tol
             o.prec = prec
+            o.mixed_stall = args.mixed_stall
             for k in range(2):
                 with torch.cuda.stream(stream):
                     u = u0d.clone()
@@ -1181,6 +1188,13 @@ def main():
         return
     if args.precision_table:
         run_precision_table(args)
+        return
+    if args.serve_only:
+        import torch
+        import paper_1105_5331_gb300 as cp
+        stream = torch.cuda.Stream(torch.device("cuda", 0))
+        ctx = cp.cp_ctx_create(0, stream)
+        print(json.dumps({"serve_only": True, "dimtree": args.dimtree, **serving_run(cp, ctx, args)}))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

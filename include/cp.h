@@ -277,6 +277,9 @@ typedef struct {
                        /* M^(2), M^(3) from W = T x_1 A^(1), and M^(1), M^(2) */
                        /* at ubar from T x_3 A^(3) (see cp_mttkrp_dimtree):  */
                        /* 1 on, 0 off, -1 (default) when prod(dims) >= 2^21  */
+  int mixed_stall;     /* mixed phase: hand over to the FP64 phase after this */
+                       /* many iterations without a new smallest ||g||         */
+                       /* (<= 0: the default, 800)                            */
 } cp_solve_opts;
 
 typedef struct {

@@ -50,6 +50,16 @@ namespace {
 enum { F = 0, FBAR = 1, SLOPE = 3, GD = 4, GG = 5, NSCAL = 8 };
 enum { STOP_RUN = 0, STOP_TOL = 1, STOP_MAXIT = 2, STOP_STALL = 3, STOP_NONFINITE = 4 };
 
+// Iterations of the mixed phase without a new smallest ||g|| before the FP64
+// phase takes over (the safeguard for a tolerance below the mixed-precision
+// noise floor).  On collinear problems N-GMRES's ||g|| plateaus for long
+// stretches, and a handover that comes too early leaves most of the solve to
+// the FP64 phase (a 174 x 164 x 48, R = 18, c = 0.9 request: 115 mixed + 1024
+// FP64 iterations after a false stall at 50, against 325 mixed iterations).
+// Over the first 128 requests of the serving stream, solved alone: 7.0 s in
+// total at 50, 4.2 s at 200, 3.6 s at 400, 3.5 s at 800 (no false stall left).
+constexpr int kMixedStallDefault = 800;
+
 // Stopping test on ||g||/P (shared by the phase start and the loop tail).
 __device__ void ctl_eval(SolveCtl* c, const double* scal, double P, double tol, int maxit, int mixed,
                          int stall, cudaGraphConditionalHandle outer) {
@@ -447,7 +457,7 @@ cp_status Solver::capture_phase(cp_precision pr, bool first, cudaGraph_t* out) {
   const F32Off o32 = f32_layout(L, &acc32);
   const double tol = mixed ? o.tol * (o.mixed_tol_factor > 0 ? o.mixed_tol_factor : 1.0) : o.tol;
   const int maxit = o.maxit;
-  const int stall = 50;
+  const int stall = o.mixed_stall > 0 ? o.mixed_stall : kMixedStallDefault;
   const double Pd = (double)P;
   const int cap = o.w;
   cp_ls_opts lso = o.ls;
