@@ -670,6 +670,7 @@ def run_precision_table(args):
             o.tol = r.tol
             o.prec = prec
             o.mixed_stall = args.mixed_stall
+            o.dimtree = args.dimtree
             for k in range(2):
                 with torch.cuda.stream(stream):
                     u = u0d.clone()
