@@ -62,7 +62,7 @@ def parse():
     p.add_argument("--kernel-breakdown", action="store_true",
                    help="one headline solve under the CUDA profiler (CUPTI): per-kernel launches, device "
                         "time and critical-path share (ncu does not see kernels inside conditional graph bodies)")
-    p.add_argument("--serve-requests", type=int, default=128,
+    p.add_argument("--serve-requests", type=int, default=1024,
                    help="requests of the 200/s Poisson serving stream replayed (0: skip)")
     p.add_argument("--serve-fp64-requests", type=int, default=32,
                    help="requests solved by the FP64 path in saturation for the mixed-vs-FP64 figure")
@@ -471,19 +471,38 @@ def mttkrp_roofline(cp, ctx, t, u, stream, flush, prec):
                             else "fallback 6.8 TB/s - of fallback")}
 
 
+def _gen_request(r):
+    """One request's tensor and initial guess (worker of the generation pool)."""
+    import synth
+    prob, u0 = synth.request_problem(r, config=5)
+    return prob.T, u0
+
+
+def generate_requests(reqs, workers=16):
+    """The requests' tensors, drawn by a pool of spawned processes (about
+    56 ms of host work each), in request order."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(workers, os.cpu_count() or 1)) as pool:
+        return pool.map(_gen_request, reqs, chunksize=8)
+
+
 def serving_run(cp, ctx, args):
     """The serving stream (dense 3-way requests, sides U{16..192}, R U{2..32},
     collinearity {0.5, 0.9}, 1-10 % noise, tol {1e-5, 1e-7}, Poisson arrivals
-    at 200/s): the first `serve_requests` requests replayed open-loop through
-    the request server (p50/p99 time to tolerance), then the same requests all
-    submitted at t=0 (saturation solves/s), mixed and FP64."""
+    at 200/s): the first `serve_requests` requests (default: all 1024)
+    replayed open-loop through the request server (p50/p99 time to
+    tolerance), then the same requests all submitted at t=0 (saturation
+    solves/s); then the first `serve_fp64_requests` in FP64 and in mixed
+    precision, at saturation and one by one (the per-request table)."""
     import numpy as np
     import synth
     n = args.serve_requests
     if n <= 0:
         return None
     reqs = synth.request_stream(n, rate_per_s=200.0, config=5)
-    probs = [synth.request_problem(r, config=5) for r in reqs]   # generated before timing
+    t0 = time.perf_counter()
+    probs = generate_requests(reqs)                           # generated before timing
+    t_gen = time.perf_counter() - t0
 
     def opts(r, prec):
         o = cp.cp_solve_opts_default(r.R)
@@ -497,12 +516,12 @@ def serving_run(cp, ctx, args):
         outs = [np.zeros_like(u0) for _, u0 in probs[:count]]
         t0 = time.perf_counter()
         ids = []
-        for r, (prob, u0), out in zip(reqs[:count], probs[:count], outs):
+        for r, (T, u0), out in zip(reqs[:count], probs[:count], outs):
             if open_loop:
                 delay = r.arrival_s - (time.perf_counter() - t0)
                 if delay > 0:
                     time.sleep(delay)
-            ids.append(cp.cp_server_submit(srv, prob.T, opts(r, prec), u0, out))
+            ids.append(cp.cp_server_submit(srv, T, opts(r, prec), u0, out))
         cp.cp_server_drain(srv, 1800.0)
         wall = time.perf_counter() - t0
         st = cp.cp_server_stats(srv)
@@ -512,14 +531,40 @@ def serving_run(cp, ctx, args):
                 "p99_ms": st["p99_s"] * 1e3, "solves_per_s": count / wall,
                 "peak_admitted_bytes": st["peak_bytes"]}
 
+    def one_by_one(count):
+        """Each request solved alone, FP64 then mixed, wall time of cp_solve
+        (synchronous) after its tensor is made: [id, entries, R, fp64 ms,
+        mixed ms, fp64 iterations, mixed iterations]."""
+        rows = []
+        for r, (T, u0) in zip(reqs[:count], probs[:count]):
+            t = cp.cp_tensor_dense(ctx, T)
+            row = [r.request_id, int(T.size), r.R]
+            ms, its = [], []
+            for prec in (cp.CP_FP64, cp.CP_MIXED_BF16X3):
+                u = np.array(u0, copy=True)
+                cp.cp_solve(ctx, t, opts(r, prec), u)          # warm-up (graph capture, planes)
+                u = np.array(u0, copy=True)
+                t1 = time.perf_counter()
+                rep = cp.cp_solve(ctx, t, opts(r, prec), u)
+                ms.append(1e3 * (time.perf_counter() - t1))
+                its.append(rep["iters"])
+            t.close()
+            rows.append(row + [round(ms[0], 2), round(ms[1], 2)] + its)
+        return rows
+
     res = {"stream": "Poisson 200/s, sides U{16..192}, R U{2..32}, c {0.5,0.9}, noise U(1%,10%), tol {1e-5,1e-7}",
-           "slots": args.serve_slots}
+           "slots": args.serve_slots, "generation_s": t_gen}
     res["open_loop_mixed"] = run(cp.CP_MIXED_BF16X3, n, True)
     res["saturation_mixed"] = run(cp.CP_MIXED_BF16X3, n, False)
     if args.serve_fp64_requests > 0:
         m = min(n, args.serve_fp64_requests)
         res["saturation_fp64"] = run(cp.CP_FP64, m, False)
         res["saturation_mixed_same_requests"] = run(cp.CP_MIXED_BF16X3, m, False)
+        rows = one_by_one(m)
+        res["one_by_one"] = {"columns": ["id", "entries", "R", "fp64_ms", "mixed_ms", "fp64_iters", "mixed_iters"],
+                             "rows": rows,
+                             "mixed_not_slower": sum(1 for x in rows if x[4] <= x[3]),
+                             "fp64_total_ms": sum(x[3] for x in rows), "mixed_total_ms": sum(x[4] for x in rows)}
     return res
 
 

@@ -280,6 +280,8 @@ typedef struct {
   int mixed_stall;     /* mixed phase: hand over to the FP64 phase after this */
                        /* many iterations without a new smallest ||g||         */
                        /* (<= 0: the default, 800)                            */
+  int mixed_min_entries; /* dense tensors with fewer entries run CP_MIXED_BF16X3 */
+                         /* solves in FP64 (0: the default, 4096; -1: never)   */
 } cp_solve_opts;
 
 typedef struct {

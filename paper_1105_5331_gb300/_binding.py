@@ -55,7 +55,8 @@ class cp_solve_opts(C.Structure):
     _fields_ = [("R", C.c_int), ("w", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
                 ("eps", C.c_double), ("prec", C.c_int), ("polish", C.c_int),
                 ("mixed_tol_factor", C.c_double), ("ls", cp_ls_opts),
-                ("mixed_maxfev", C.c_int), ("dimtree", C.c_int), ("mixed_stall", C.c_int)]
+                ("mixed_maxfev", C.c_int), ("dimtree", C.c_int), ("mixed_stall", C.c_int),
+                ("mixed_min_entries", C.c_int)]
 
 
 class cp_solve_report(C.Structure):

@@ -670,6 +670,7 @@ void cp_solve_opts_default(cp_solve_opts* o, int R) {
   o->mixed_maxfev = 0;
   o->dimtree = -1;
   o->mixed_stall = 0;
+  o->mixed_min_entries = 0;
 }
 
 cp_status cp_solve(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* opts, double* u,

@@ -60,6 +60,10 @@ enum { STOP_RUN = 0, STOP_TOL = 1, STOP_MAXIT = 2, STOP_STALL = 3, STOP_NONFINIT
 // total at 50, 4.2 s at 200, 3.6 s at 400, 3.5 s at 800 (no false stall left).
 constexpr int kMixedStallDefault = 800;
 
+// Dense tensors with fewer entries solve in FP64 when mixed precision is
+// asked for (cp_solve_opts.mixed_min_entries).
+constexpr int64_t kMixedMinEntriesDefault = 4096;
+
 // Stopping test on ||g||/P (shared by the phase start and the loop tail).
 __device__ void ctl_eval(SolveCtl* c, const double* scal, double P, double tol, int maxit, int mixed,
                          int stall, cudaGraphConditionalHandle outer) {
@@ -353,6 +357,13 @@ void Solver::release() {
 cp_status Solver::setup(cp_ctx* ctx, const cp_tensor* t_in, const cp_solve_opts& opts, SolverRes* r) {
   t = const_cast<cp_tensor*>(t_in);
   o = opts;
+  // small dense tensors: FP64 throughout (the bf16x3 noise in f costs more
+  // iterations than the tensor cores save: a 9 x 8 x 7, R = 3 solve took 81
+  // mixed iterations against 13 in FP64; every request of the serving stream,
+  // from 58 176 entries up, was faster mixed)
+  const int64_t min_entries = o.mixed_min_entries > 0 ? o.mixed_min_entries
+                              : o.mixed_min_entries == 0 ? kMixedMinEntriesDefault : 0;
+  if (o.prec != CP_FP64 && t->kind == 0 && t->K < min_entries) o.prec = CP_FP64;
   L.set(t->N, t->dims, o.R);
   P = L.P();
   if (r) {

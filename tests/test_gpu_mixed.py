@@ -441,3 +441,26 @@ def test_mixed_solve_with_and_without_dimension_tree(cp, ctx, dimtree):
     f, g = O.fg(O.DenseTensor(prob.T), u.cpu().numpy(), 6)
     assert np.linalg.norm(g) / O.n_params(prob.dims, 6) < 1e-7 * 1.01
     assert abs(f - rep["f"]) <= 1e-10 * f
+
+
+def test_small_dense_tensors_solve_in_fp64_when_mixed_is_asked(cp, ctx):
+    """Below 4096 entries a mixed-precision request runs in FP64 (the bf16x3
+    noise in f costs more iterations there than the tensor cores save);
+    mixed_min_entries = -1 keeps it mixed.  Both meet the tolerance by the
+    oracle's own gradient."""
+    rng = synth.rng_for(0, 7)
+    prob = synth.dense_problem(rng, (9, 8, 7), 3, 0.5, eta=0.05)
+    u0 = synth.initial_guess(rng, prob.dims, 3)
+    t = cp.cp_tensor_dense(ctx, dev(prob.T))
+    X = O.DenseTensor(prob.T)
+    for floor, mixed_expected in ((0, False), (-1, True)):
+        o = cp.cp_solve_opts_default(3)
+        o.prec = cp.CP_MIXED_BF16X3
+        o.tol = 1e-8
+        o.mixed_min_entries = floor
+        u = dev(u0)
+        rep = cp.cp_solve(ctx, t, o, u)
+        assert rep["converged"]
+        assert (rep["mixed_iters"] > 0) == mixed_expected, rep
+        _, g = O.fg(X, u.cpu().numpy(), 3)
+        assert np.linalg.norm(g) / O.n_params(prob.dims, 3) < 1e-8 * 1.01
