@@ -320,6 +320,26 @@ cp_status cp_solve(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* opts, d
 cp_status cp_solve_batch(cp_ctx* ctx, int nreq, const cp_tensor* const* tensors,
                          const cp_solve_opts* opts, double* const* u, cp_solve_report* reps);
 
+/* Many small 3-way dense decompositions in one persistent launch (Algorithm 1
+ * for every request; Steps I-III as for cp_solve).  Each thread-block
+ * cluster of `cluster` CTAs (1, 2, 4 or 8; 0 picks one per request from its
+ * size) runs the whole solve of one request at a time, with cluster barriers
+ * between the dependent steps and no host round trip per iteration, and then
+ * takes the next request from a device queue.
+ * Requests: tensors[i] dense, N = 3, every side <= 256, I_n R <= 8192,
+ * R <= 32, w <= 32 (CP_ERR_UNSUPPORTED otherwise).  opts[i].prec CP_FP64:
+ * FP64 throughout; any mixed precision: a phase with FP32 products and FP32
+ * sums over at most a few hundred terms on the CUDA cores (partial sums,
+ * Grams, solves, window least squares, f and the line search in FP64), then
+ * with opts[i].polish the FP64 phase to tol; the mixed phase ends at
+ * tol * mixed_tol_factor or after mixed_stall iterations without a new
+ * smallest ||g|| (as for cp_solve).  u[i] (host or device, P doubles): the
+ * initial guess in, the solution out; reps (may be NULL): nreq reports.
+ * Returns the first failing status (CP_ERR_MAXIT if a request did not meet
+ * its tol).  Synchronous. */
+cp_status cp_solve_many(cp_ctx* ctx, int nreq, const cp_tensor* const* tensors, const cp_solve_opts* opts,
+                        double* const* u, cp_solve_report* reps, int cluster);
+
 /* Request server (continuous batching).  Requests (dense tensors, each with
  * its own shape, rank, tolerance and precision) wait in arrival order and are
  * admitted while one of `max_active` slots is free and the sum of the device

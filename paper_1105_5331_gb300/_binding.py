@@ -34,7 +34,7 @@ EXPORTED = [
     "cp_tensor_destroy", "cp_mttkrp", "cp_mttkrp_variants", "cp_mttkrp_noalloc", "cp_mttkrp_dimtree", "cp_fg", "cp_als_sweep", "cp_normalize",
     "ngmres_step",
     "cp_ls_opts_default", "linesearch", "cp_solve_opts_default", "cp_solve",
-    "cp_solve_batch", "cp_server_create", "cp_server_submit", "cp_server_poll", "cp_server_cancel",
+    "cp_solve_batch", "cp_solve_many", "cp_server_create", "cp_server_submit", "cp_server_poll", "cp_server_cancel",
     "cp_server_drain", "cp_server_stats", "cp_server_destroy",
 ]
 
@@ -106,6 +106,8 @@ def _load():
         "cp_solve": (I, [VP, VP, C.POINTER(cp_solve_opts), VP, C.POINTER(cp_solve_report)]),
         "cp_solve_batch": (I, [VP, I, C.POINTER(VP), C.POINTER(cp_solve_opts), C.POINTER(VP),
                                C.POINTER(cp_solve_report)]),
+        "cp_solve_many": (I, [VP, I, C.POINTER(VP), C.POINTER(cp_solve_opts), C.POINTER(VP),
+                              C.POINTER(cp_solve_report), I]),
         "cp_server_create": (I, [VP, C.c_size_t, I, C.POINTER(VP)]),
         "cp_server_submit": (I, [VP, I, P, I, VP, C.POINTER(cp_solve_opts), VP, VP, C.POINTER(C.c_uint64)]),
         "cp_server_poll": (I, [VP, C.c_uint64, C.POINTER(I), C.POINTER(I), C.POINTER(cp_solve_report),
@@ -387,6 +389,19 @@ def cp_solve_batch(ctx, tensors, opts_list, us) -> list:
     up = (C.c_void_p * n)(*[_ptr(u) for u in us])
     reps = (cp_solve_report * n)()
     _check(_lib.cp_solve_batch(_h(ctx), n, th, op, up, reps), allow=(8,))
+    return [r.as_dict() for r in reps]
+
+
+def cp_solve_many(ctx, tensors, opts_list, us, cluster: int = 0) -> list:
+    """Solve many small 3-way dense problems in one persistent launch (one
+    thread-block cluster per problem at a time); returns the reports.  A
+    problem that stops at maxit is not an exception."""
+    n = len(tensors)
+    th = (C.c_void_p * n)(*[_h(t) for t in tensors])
+    op = (cp_solve_opts * n)(*opts_list)
+    up = (C.c_void_p * n)(*[_ptr(u) for u in us])
+    reps = (cp_solve_report * n)()
+    _check(_lib.cp_solve_many(_h(ctx), n, th, op, up, reps, int(cluster)), allow=(8,))
     return [r.as_dict() for r in reps]
 
 

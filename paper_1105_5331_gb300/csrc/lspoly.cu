@@ -70,37 +70,6 @@ struct CoefParams {
   int* status;
 };
 
-__device__ void mt_init(MTState& s, double f0, double g0, const cp_ls_opts& o) {
-  s.ftol = o.ftol;
-  s.gtol = o.gtol;
-  s.xtol = o.xtol;
-  s.stpmin = o.stpmin;
-  s.stpmax = o.stpmax;
-  s.maxfev = o.maxfev;
-  s.f0 = f0;
-  s.g0 = g0;
-  s.nfev = 0;
-  s.info = 0;
-  s.done = 0;
-  s.brackt = 0;
-  s.stage = 1;
-  s.lo_a = 0.0; s.lo_f = f0; s.lo_g = g0;
-  s.hi_a = 0.0; s.hi_f = f0; s.hi_g = g0;
-  s.width = o.stpmax - o.stpmin;
-  s.width1 = 2.0 * s.width;
-  s.stp = fmin(fmax(o.stp0, o.stpmin), o.stpmax);
-  s.imin = 0.0;
-  s.imax = s.stp + 4.0 * s.stp;
-  s.stp_eval = s.stp;
-  s.f = f0;
-  s.g = g0;
-  if (!(g0 < 0.0)) {
-    s.info = -1;
-    s.done = 1;
-    s.stp_eval = 0.0;
-  }
-}
-
 // E(beta) coefficients: thread per (r, s), the product of the N quadratics
 // of that entry; block sums, then the last block adds them in block order.
 __global__ void __launch_bounds__(256) ls_epoly_kernel(const double* __restrict__ grams, int N, int R,
@@ -260,7 +229,7 @@ __global__ void __launch_bounds__(256) ls_coef_kernel(const CoefParams p) {
   for (int q = 0; q <= 2 * N; ++q) p.poly[q] = poly[q];
   // More-Thuente on phi, phi' by Horner's rule
   MTState s;
-  mt_init(s, poly[0], poly[1], p.o);
+  mtdev::mt_init(s, poly[0], poly[1], p.o);
   while (!s.done) {
     const double b = s.stp;
     double f = poly[2 * N], g = 2 * N * poly[2 * N];

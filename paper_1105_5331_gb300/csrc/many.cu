@@ -1,0 +1,1581 @@
+// Many small 3-way dense decompositions in one persistent launch: every
+// thread-block cluster runs the whole N-GMRES solve (Algorithm 1: Step I the
+// ALS sweep of Section 2.3, Step II the window least squares of Section 2.1
+// with delta I, Step III the More-Thuente search of Section 2.4 on the line
+// polynomial) of one request at a time, and takes the next request from a
+// device queue when it finishes.  Cross-CTA steps meet at cluster barriers
+// (barrier.cluster with release/acquire), so a request costs no kernel
+// launches per iteration and its iterations never wait on the host.
+//
+// Work split inside a cluster of C CTAs (rank k):
+//   * rows: CTA k owns rows [k I_n / C, (k+1) I_n / C) of every factor, of
+//     every iterate and gradient block, and of M^(n); everything row-wise
+//     (ALS updates, gradients, normalisation, window pushes, N-GMRES
+//     combination) touches only its own rows;
+//   * fibers: the tensor is read as T[j][i3] (j = i1 I2 + i2, the last index
+//     fastest); CTA k owns fibers [k J / C, (k+1) J / C);
+//   * sums (Grams, M^(3), window dots, column norms, slopes, f) are written
+//     as per-CTA partials and added in rank order after a barrier, by every
+//     CTA that needs them (the same order everywhere, so every CTA takes the
+//     same decisions).
+//
+// Passes over T per iteration (one each, all CTAs): Y = T x_3 A^(3) for the
+// sweep's modes 1 and 2; M^(3) of the swept point; Y' = T x_3 Abar^(3) for
+// ubar's modes 1 and 2 (M^(3)(ubar) is the swept M^(3) with the
+// normalisation's column scales); Z = T x_3 [Abar^(3) | D^(3)] for the line
+// polynomial and the accepted point's modes 1 and 2; M^(3) at the accepted
+// point.
+//
+// Precision per request phase: mixed (products and their sums over at most
+// a few hundred terms in FP32 on the CUDA cores, partial sums added in FP64;
+// Grams, solves, window least squares, f and the line search in FP64),
+// then an FP64 phase that restarts the window from the FP64 gradient and runs
+// to tol (the polish); or FP64 throughout.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "cp_internal.cuh"
+#include "linesearch.cuh"
+#include "mt_device.cuh"
+#include "newton.cuh"
+
+namespace cpg {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxR = 32;      // rank limit
+constexpr int kMaxW = 32;      // window limit
+constexpr int kMaxC = 8;       // cluster size limit (portable clusters)
+constexpr int kMaxI = 256;     // side limit
+constexpr int kMaxIR = 8192;   // I_n R limit (the M^(3) accumulators live in shared memory)
+constexpr int kColW = 16;      // columns per register tile in the passes
+constexpr int kBsCols = 32;    // columns of the factor staged at once for Y = T x_3 B
+constexpr int kFib = 64;       // fibers per Khatri-Rao chunk for M^(3)
+constexpr int kFlush = 8;      // chunks between FP64 flushes of the FP32 accumulators
+constexpr int kTile = 128;     // window elements per shared-memory tile
+constexpr int kTileLd = kTile + 1;
+
+enum { STOP_RUN = 0, STOP_TOL = 1, STOP_MAXIT = 2, STOP_STALL = 3, STOP_NONFINITE = 4 };
+enum { PH_MIXED = 1, PH_FP64 = 2, PH_DONE = 3 };
+// scal[] slots
+enum { S_F = 0, S_FBAR = 1, S_BETA = 2, S_ACCEPT = 3, S_PARK = 4, S_NSCAL = 8 };
+
+struct ManyCtl {
+  int iters, fg_evals, als_sweeps, restarts, ls_failures, ls_trials, accepts;
+  int mixed_iters, fp64_iters;
+  int phase;          // PH_*
+  int start;          // 2: normalise the start point, then start a phase; 1: start a phase; 0: iterate
+  int stop;           // STOP_* of the last test
+  int status;         // cp_status of the request
+  int win_start, win_m;
+  int since_best;
+  double best, gn, f;
+};
+
+struct ManyReq {
+  const void* T;      // T[j][i3], J x I3, j = i1 I2 + i2 (modes 1, 2, 3 of the paper)
+  int t64;            // T holds doubles
+  int I1, I2, I3, J, R, P;
+  int off2, off3;     // element offsets of A^(2), A^(3) in an iterate
+  double normT2;
+  double tol, tol_mixed, eps;
+  int maxit, w, polish, stall;
+  cp_ls_opts ls, ls_mixed;
+  double *u, *g, *ub, *gb, *uh, *d, *x, *U, *G;
+  double* Y;          // J x 2R (floats in the mixed phase)
+  double *M1, *M2, *M3, *M3s;   // M^(n) at the current point; the swept point's M^(3)
+  double *V1, *V2;    // line-search variants of modes 1, 2: 4 x I1 x R, 4 x I2 x R
+  double* part;       // kMaxC x part_ld partials: two large regions of big_ld, two of 128 scalars
+  int part_ld, big_ld;
+  double *Gu, *Gs, *Gb, *Gad, *Gdd, *Gx;   // Grams (3 x R x R): u, swept, ubar, ubar^T d, d^T d, x
+  double* scal;
+  ManyCtl* ctl;
+};
+
+struct ManyQueue {
+  int next;
+  int ntasks;
+  unsigned long long budget_ns;   // a cluster parks its request after this long
+};
+
+// Small shared state of one CTA.
+struct EngSh {
+  ManyReq q;
+  ManyCtl c;
+  double A[kMaxR * kMaxR];        // Gammabar and its inverse
+  double A0[kMaxR * kMaxR];       // a copy for the ridge retry
+  double H[kMaxW * kMaxW];
+  double rhs[kMaxW];
+  double alpha[kMaxW];
+  double nu[3 * kMaxR];
+  double scale[3 * kMaxR];
+  double key[kMaxR];
+  double lam[kMaxR];
+  double sc2[3 * kMaxR];          // second set of scales (the other normalisation of a step)
+  double poly[8];
+  double red[kWarps];
+  double bcast[8];
+  int order[kMaxR];
+  int order2[kMaxR];
+  unsigned long long t0;
+  int task;
+  int flag;
+};
+
+// ---------------------------------------------------------------- cluster
+
+__device__ __forceinline__ unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cl_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cl_id() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+// Every thread of every CTA of the cluster; global and shared writes before
+// it are visible to the cluster's threads after it.
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int lo_of(int n, int k, int C) { return (int)(((long long)n * k) / C); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the CTA (fixed order); every thread gets it.
+__device__ double cta_sum(double v, EngSh& sh) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) s += sh.red[w];
+  return s;
+}
+
+// Sum over the cluster's partials part[c * ld + k] in rank order.
+__device__ __forceinline__ double psum(const double* part, int ld, int C, int k) {
+  double s = 0.0;
+  for (int c = 0; c < C; ++c) s += part[(size_t)c * ld + k];
+  return s;
+}
+
+
+__device__ __forceinline__ float fmat(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ------------------------------------------------------------ passes over T
+
+// Y[j][c0 + c] = sum_{i3} T[j][i3] B[i3][c] for the CTA's fibers j, where B
+// is A (I3 x R) or [A | D] (I3 x 2R); Y has row stride ys (AT elements).
+// Lanes own fibers; the factor columns are staged in shared memory (kBsCols
+// at a time) and read as broadcasts, kColW accumulators per lane.
+template <typename TT, typename AT>
+__device__ void pass_y(const TT* __restrict__ T, int J, int I3, int R, const double* __restrict__ A,
+                       const double* __restrict__ D, AT* __restrict__ Y, int ys, int rk, int C, AT* Bs) {
+  const int ncol = D ? 2 * R : R;
+  const int jlo = lo_of(J, rk, C), jhi = lo_of(J, rk + 1, C);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < ncol; c0 += kBsCols) {
+    const int nc = min(kBsCols, ncol - c0);
+    const int ncp = (nc + kColW - 1) / kColW * kColW;
+    __syncthreads();
+    for (int e = threadIdx.x; e < I3 * ncp; e += kThreads) {
+      const int i = e / ncp, c = e - (e / ncp) * ncp;
+      const int cc = c0 + c;
+      double v = 0.0;
+      if (c < nc) v = cc < R ? A[(size_t)i * R + cc] : D[(size_t)i * R + cc - R];
+      Bs[e] = (AT)v;
+    }
+    __syncthreads();
+    for (int jb = jlo + warp * 32; jb < jhi; jb += kThreads) {
+      const int j = jb + lane;
+      const bool ok = j < jhi;
+      const TT* trow = T + (size_t)(ok ? j : jb) * I3;
+      for (int ct = 0; ct < ncp; ct += kColW) {
+        AT acc[kColW];
+#pragma unroll
+        for (int k = 0; k < kColW; ++k) acc[k] = (AT)0;
+        const AT* b = Bs + ct;
+        for (int i = 0; i < I3; ++i) {
+          const AT t = (AT)__ldg(trow + i);
+#pragma unroll
+          for (int k = 0; k < kColW; ++k) acc[k] = fmat(t, b[k], acc[k]);
+          b += ncp;
+        }
+        if (ok) {
+          AT* yrow = Y + (size_t)j * ys + c0 + ct;
+#pragma unroll
+          for (int k = 0; k < kColW; ++k)
+            if (ct + k < nc) yrow[k] = acc[k];
+        }
+      }
+    }
+  }
+}
+
+// The CTA's partial of M^(3)(A, B): out[i3][r] = sum_{j in its fibers}
+// T[j][i3] A[j / I2][r] B[j % I2][r] (I3 x R doubles).  Khatri-Rao rows of
+// kFib fibers at a time in shared memory; lanes own i3 (coalesced reads of
+// T), a warp owns one or two (32-row, kColW-column) output tiles and keeps
+// them in FP32/FP64 registers, added into FP64 shared totals every kFlush
+// chunks.
+template <typename TT, typename AT>
+__device__ void pass_m3(const TT* __restrict__ T, int J, int I2, int I3, int R, const double* __restrict__ A,
+                        const double* __restrict__ B, double* __restrict__ out, int rk, int C, AT* KRs,
+                        double* Ms) {
+  const int Rp = (R + kColW - 1) / kColW * kColW;
+  const int nib = (I3 + 31) / 32, nct = Rp / kColW;
+  const int units = nib * nct;   // at most 2 kWarps (I3 <= 256, R <= 32)
+  const int jlo = lo_of(J, rk, C), jhi = lo_of(J, rk + 1, C);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < I3 * R; e += kThreads) Ms[e] = 0.0;
+  AT acc[2][kColW];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int k = 0; k < kColW; ++k) acc[u][k] = (AT)0;
+  int chunks = 0;
+  for (int j0 = jlo; j0 < jhi; j0 += kFib) {
+    const int nf = min(kFib, jhi - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kFib * Rp; e += kThreads) {
+      const int f = e / Rp, r = e - (e / Rp) * Rp;
+      AT v = (AT)0;
+      if (f < nf && r < R) {
+        const int j = j0 + f;
+        const int i1 = j / I2, i2 = j - (j / I2) * I2;
+        v = (AT)A[(size_t)i1 * R + r] * (AT)B[(size_t)i2 * R + r];
+      }
+      KRs[e] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int unit = warp + u * kWarps;
+      if (unit < units) {
+        const int ib = unit / nct, ct = unit - (unit / nct) * nct;
+        const int i3 = ib * 32 + lane;
+        const bool ok = i3 < I3;
+        const TT* tcol = T + (size_t)j0 * I3 + (ok ? i3 : 0);
+        const AT* b = KRs + ct * kColW;
+        for (int f = 0; f < nf; ++f) {
+          const AT t = ok ? (AT)__ldg(tcol + (size_t)f * I3) : (AT)0;
+#pragma unroll
+          for (int k = 0; k < kColW; ++k) acc[u][k] = fmat(t, b[k], acc[u][k]);
+          b += Rp;
+        }
+      }
+    }
+    if (++chunks == kFlush || j0 + kFib >= jhi) {
+      chunks = 0;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int unit = warp + u * kWarps;
+        if (unit < units) {
+          const int ib = unit / nct, ct = unit - (unit / nct) * nct;
+          const int i3 = ib * 32 + lane;
+          if (i3 < I3) {
+#pragma unroll
+            for (int k = 0; k < kColW; ++k) {
+              const int r = ct * kColW + k;
+              if (r < R) Ms[i3 * R + r] += (double)acc[u][k];
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kColW; ++k) acc[u][k] = (AT)0;
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < I3 * R; e += kThreads) out[e] = Ms[e];
+}
+
+// Rows of M^(1) from Y = T x_3 (.): out[i1][r] = sum_{i2} Y[(i1 I2 + i2) ys + c0 + r] B[i2][r]
+// for the CTA's rows i1 (and the same for the D columns at c0 + R with dv).
+template <typename AT>
+__device__ void contract_m1(const AT* __restrict__ Y, int ys, int c0, int I1, int I2, int R,
+                            const double* __restrict__ B, double* __restrict__ out, int rk, int C) {
+  const int lo = lo_of(I1, rk, C), hi = lo_of(I1, rk + 1, C);
+  for (int e = threadIdx.x; e < (hi - lo) * R; e += kThreads) {
+    const int i1 = lo + e / R, r = e - (e / R) * R;
+    const AT* y = Y + (size_t)i1 * I2 * ys + c0 + r;
+    AT s = (AT)0;
+    for (int i2 = 0; i2 < I2; ++i2) s = fmat(y[(size_t)i2 * ys], (AT)B[(size_t)i2 * R + r], s);
+    out[(size_t)i1 * R + r] = (double)s;
+  }
+}
+
+// Rows of M^(2) from Y: out[i2][r] = sum_{i1} Y[(i1 I2 + i2) ys + c0 + r] A[i1][r]
+// for the CTA's rows i2.
+template <typename AT>
+__device__ void contract_m2(const AT* __restrict__ Y, int ys, int c0, int I1, int I2, int R,
+                            const double* __restrict__ A, double* __restrict__ out, int rk, int C) {
+  const int lo = lo_of(I2, rk, C), hi = lo_of(I2, rk + 1, C);
+  for (int e = threadIdx.x; e < (hi - lo) * R; e += kThreads) {
+    const int i2 = lo + e / R, r = e - (e / R) * R;
+    const AT* y = Y + (size_t)i2 * ys + c0 + r;
+    AT s = (AT)0;
+    for (int i1 = 0; i1 < I1; ++i1) s = fmat(y[(size_t)i1 * I2 * ys], (AT)A[(size_t)i1 * R + r], s);
+    out[(size_t)i2 * R + r] = (double)s;
+  }
+}
+
+// The line search's variants of modes 1 and 2 from Z = T x_3 [Abar^(3) | D^(3)]
+// (row stride 2R): V1[v][i1][r], v = 2 c + b, sums over i2 of Z_c B_b with
+// B_0 = Abar^(2), B_1 = D^(2); V2[v][i2][r], v = 2 c + a, sums over i1 of
+// Z_c A_a with A_0 = Abar^(1), A_1 = D^(1) (c = 0: Abar^(3) columns, 1: D^(3)).
+template <typename AT>
+__device__ void contract_variants(const AT* __restrict__ Z, int I1, int I2, int R, const double* __restrict__ Ab1,
+                                  const double* __restrict__ D1, const double* __restrict__ Ab2,
+                                  const double* __restrict__ D2, double* __restrict__ V1, double* __restrict__ V2,
+                                  int rk, int C) {
+  const int zs = 2 * R;
+  {
+    const int lo = lo_of(I1, rk, C), hi = lo_of(I1, rk + 1, C);
+    for (int e = threadIdx.x; e < (hi - lo) * R; e += kThreads) {
+      const int i1 = lo + e / R, r = e - (e / R) * R;
+      const AT* z = Z + (size_t)i1 * I2 * zs + r;
+      AT s00 = 0, s01 = 0, s10 = 0, s11 = 0;
+      for (int i2 = 0; i2 < I2; ++i2) {
+        const AT za = z[(size_t)i2 * zs], zd = z[(size_t)i2 * zs + R];
+        const AT ba = (AT)Ab2[(size_t)i2 * R + r], bd = (AT)D2[(size_t)i2 * R + r];
+        s00 = fmat(za, ba, s00);
+        s01 = fmat(za, bd, s01);
+        s10 = fmat(zd, ba, s10);
+        s11 = fmat(zd, bd, s11);
+      }
+      const size_t o = (size_t)i1 * R + r, st = (size_t)I1 * R;
+      V1[o] = (double)s00;
+      V1[st + o] = (double)s01;
+      V1[2 * st + o] = (double)s10;
+      V1[3 * st + o] = (double)s11;
+    }
+  }
+  {
+    const int lo = lo_of(I2, rk, C), hi = lo_of(I2, rk + 1, C);
+    for (int e = threadIdx.x; e < (hi - lo) * R; e += kThreads) {
+      const int i2 = lo + e / R, r = e - (e / R) * R;
+      const AT* z = Z + (size_t)i2 * zs + r;
+      AT s00 = 0, s01 = 0, s10 = 0, s11 = 0;
+      for (int i1 = 0; i1 < I1; ++i1) {
+        const AT za = z[(size_t)i1 * I2 * zs], zd = z[(size_t)i1 * I2 * zs + R];
+        const AT aa = (AT)Ab1[(size_t)i1 * R + r], ad = (AT)D1[(size_t)i1 * R + r];
+        s00 = fmat(za, aa, s00);
+        s01 = fmat(za, ad, s01);
+        s10 = fmat(zd, aa, s10);
+        s11 = fmat(zd, ad, s11);
+      }
+      const size_t o = (size_t)i2 * R + r, st = (size_t)I2 * R;
+      V2[o] = (double)s00;
+      V2[st + o] = (double)s01;
+      V2[2 * st + o] = (double)s10;
+      V2[3 * st + o] = (double)s11;
+    }
+  }
+}
+
+// ------------------------------------------------------------ FP64 helpers
+
+// Partial X^T Y over rows [lo, hi) of two I x R row-major matrices.
+__device__ void gram_part(const double* __restrict__ X, const double* __restrict__ Yv, int lo, int hi, int R,
+                          double* __restrict__ out) {
+  for (int e = threadIdx.x; e < R * R; e += kThreads) {
+    const int r = e / R, s = e - (e / R) * R;
+    double acc = 0.0;
+    for (int i = lo; i < hi; ++i) acc = fma(X[(size_t)i * R + r], Yv[(size_t)i * R + s], acc);
+    out[e] = acc;
+  }
+}
+
+// In-place inverse of the SPD matrix A (R x R, shared) by Gauss-Jordan
+// elimination without pivoting; false (the same in every thread) when a
+// pivot is not positive and finite.
+__device__ bool spd_inverse(double* A, int R) {
+  for (int k = 0; k < R; ++k) {
+    __syncthreads();
+    const double p = A[k * R + k];
+    if (!(p > 0.0) || !isfinite(p)) return false;
+    const double ip = recip_nr(p);
+    double v[kMaxR * kMaxR / kThreads];
+    int cnt = 0;
+    for (int e = threadIdx.x; e < R * R; e += kThreads) {
+      const int i = e / R, j = e - (e / R) * R;
+      double a = A[e];
+      if (i == k && j == k)
+        a = ip;
+      else if (i == k)
+        a *= ip;
+      else if (j == k)
+        a = -a * ip;
+      else
+        a = fma(-A[i * R + k] * ip, A[k * R + j], a);
+      v[cnt++] = a;
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int e = threadIdx.x; e < R * R; e += kThreads) A[e] = v[cnt++];
+  }
+  __syncthreads();
+  return true;
+}
+
+// sh.A <- inverse of sh.A0 (Gammabar), retrying once with the ridge
+// 1e-12 trace / R (the reading of the ALS mode solve used throughout).
+__device__ bool gammabar_inverse(int R, EngSh& sh) {
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * R; e += kThreads) sh.A[e] = sh.A0[e];
+  if (spd_inverse(sh.A, R)) return true;
+  double tr = 0.0;
+  for (int r = 0; r < R; ++r) tr += sh.A0[r * R + r];
+  const double ridge = 1e-12 * tr / R;
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * R; e += kThreads) {
+    const int i = e / R, j = e - (e / R) * R;
+    sh.A[e] = sh.A0[e] + (i == j ? ridge : 0.0);
+  }
+  return spd_inverse(sh.A, R);
+}
+
+// sh.A0 = Ga o Gb (Hadamard product of two R x R Grams).
+__device__ void hadamard_into(const double* Ga, const double* Gb, int R, double* out) {
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * R; e += kThreads) out[e] = Ga[e] * Gb[e];
+  __syncthreads();
+}
+
+// Normalisation scales and term order (Section 2.3) from the column sums of
+// squares s[n R + r] of the three factors: nu = ||a_r^(n)||, lambda_r =
+// prod_n nu, scale = lambda^(1/3) / nu (1 for a term with a zero column),
+// order = stable sort by decreasing lambda (NaN last).
+__device__ void norm_scales(const double* s, int R, EngSh& sh, double* scale, int* order) {
+  __syncthreads();
+  for (int t = threadIdx.x; t < 3 * R; t += kThreads) {
+    const double v = s[t];
+    const double y = v > 0.0 ? rsqrt_nr(v) : 0.0;
+    sh.nu[t] = v * y;
+    scale[t] = y;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += kThreads) {
+    double l = 1.0;
+    bool zero = false;
+    for (int n = 0; n < 3; ++n) {
+      l *= sh.nu[n * R + r];
+      if (sh.nu[n * R + r] == 0.0) zero = true;
+    }
+    if (zero) l = 0.0;
+    const double root = cbrt(l);
+    for (int n = 0; n < 3; ++n) scale[n * R + r] = zero ? 1.0 : root * scale[n * R + r];
+    sh.lam[r] = l;
+    sh.key[r] = isnan(l) ? -INFINITY : l;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += kThreads) {
+    int rank = 0;
+    for (int q = 0; q < R; ++q)
+      if (sh.key[q] > sh.key[r] || (sh.key[q] == sh.key[r] && q < r)) ++rank;
+    order[rank] = r;
+  }
+  __syncthreads();
+}
+
+// Grams of the normalised point: out_n[p][q] = G_n[o_p][o_q] s_n[o_p] s_n[o_q].
+__device__ void grams_normalised(const double* G, int R, const double* scale, const int* order, double* out) {
+  for (int e = threadIdx.x; e < 3 * R * R; e += kThreads) {
+    const int n = e / (R * R), pq = e - n * R * R;
+    const int p = pq / R, q = pq - (pq / R) * R;
+    const int op = order[p], oq = order[q];
+    out[e] = G[(size_t)n * R * R + op * R + oq] * scale[n * R + op] * scale[n * R + oq];
+  }
+}
+
+// sum_{r,s} prod_n G_n[r][s] = ||[[A]]||^2 (Eq. fA), by the whole CTA.
+__device__ double model_norm2(const double* G, int R, EngSh& sh) {
+  double part = 0.0;
+  for (int e = threadIdx.x; e < R * R; e += kThreads)
+    part += G[e] * G[(size_t)R * R + e] * G[2 * (size_t)R * R + e];
+  return cta_sum(part, sh);
+}
+
+// Cholesky solve of (H + delta I) alpha = rhs in shared memory by warp 0
+// (m <= 32): the N-GMRES normal equations (Eq. normal with delta I).  alpha
+// = 0 when max diag H = 0.
+__device__ void window_solve(int m, double eps, EngSh& sh) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double dmax = 0.0;
+    for (int j = 0; j < m; ++j) dmax = fmax(dmax, sh.H[j * kMaxW + j]);
+    if (dmax == 0.0) {
+      if (lane < m) sh.alpha[lane] = 0.0;
+    } else {
+      const double delta = eps * dmax;
+      if (lane < m) sh.H[lane * kMaxW + lane] += delta;
+      __syncwarp();
+      // right-looking Cholesky, lower triangle in place (lane = row)
+      // (Newton-refined square roots and reciprocals: each IEEE FP64 divide
+      // or sqrt is a serial chain of ~650 cycles in this one-warp solve)
+      for (int k = 0; k < m; ++k) {
+        const double dk = sqrt_nr(sh.H[k * kMaxW + k]);
+        const double idk = recip_nr(dk);
+        __syncwarp();
+        if (lane == k) {
+          sh.H[k * kMaxW + k] = dk;
+          sh.sc2[k] = idk;
+        }
+        if (lane > k && lane < m) sh.H[lane * kMaxW + k] *= idk;
+        __syncwarp();
+        if (lane > k && lane < m) {
+          const double lk = sh.H[lane * kMaxW + k];
+          for (int j = k + 1; j <= lane; ++j) sh.H[lane * kMaxW + j] -= lk * sh.H[j * kMaxW + k];
+        }
+        __syncwarp();
+      }
+      // L y = rhs, then L^T alpha = y
+      double y = lane < m ? sh.rhs[lane] : 0.0;
+      for (int k = 0; k < m; ++k) {
+        const double yk = __shfl_sync(0xffffffffu, y, k) * sh.sc2[k];
+        if (lane == k) y = yk;
+        if (lane > k && lane < m) y -= sh.H[lane * kMaxW + k] * yk;
+      }
+      double a = y;
+      for (int k = m - 1; k >= 0; --k) {
+        const double ak = __shfl_sync(0xffffffffu, a, k) * sh.sc2[k];
+        if (lane == k) a = ak;
+        if (lane < k) a -= sh.H[k * kMaxW + lane] * ak;
+      }
+      if (lane < m) sh.alpha[lane] = a;
+    }
+  }
+  __syncthreads();
+}
+
+// Window ring slot of window row j (oldest first).
+__device__ __forceinline__ int ring(int start, int j, int w) { return (start + j) % w; }
+
+// ------------------------------------------------------------ request steps
+
+struct Rows {
+  int lo[3], hi[3], off[3], I[3];
+};
+
+__device__ __forceinline__ Rows rows_of(const ManyReq& q, int rk, int C) {
+  Rows w;
+  w.I[0] = q.I1;
+  w.I[1] = q.I2;
+  w.I[2] = q.I3;
+  w.off[0] = 0;
+  w.off[1] = q.off2;
+  w.off[2] = q.off3;
+  for (int n = 0; n < 3; ++n) {
+    w.lo[n] = lo_of(w.I[n], rk, C);
+    w.hi[n] = lo_of(w.I[n], rk + 1, C);
+  }
+  return w;
+}
+
+// f(e, n, i, r) for the CTA's elements of an iterate (its rows of every mode).
+template <class F>
+__device__ __forceinline__ void for_own(const Rows& w, int R, F f) {
+  for (int n = 0; n < 3; ++n) {
+    const int cnt = (w.hi[n] - w.lo[n]) * R;
+    for (int k = threadIdx.x; k < cnt; k += kThreads) {
+      const int i = w.lo[n] + k / R, r = k - (k / R) * R;
+      f(w.off[n] + i * R + r, n, i, r);
+    }
+  }
+}
+
+template <typename AT>
+__device__ void do_pass_y(const ManyReq& q, const double* A, const double* D, int rk, int C, char* big) {
+  const int ys = D ? 2 * q.R : q.R;
+  if (q.t64)
+    pass_y<double, AT>((const double*)q.T, q.J, q.I3, q.R, A, D, (AT*)q.Y, ys, rk, C, (AT*)big);
+  else
+    pass_y<float, AT>((const float*)q.T, q.J, q.I3, q.R, A, D, (AT*)q.Y, ys, rk, C, (AT*)big);
+}
+
+template <typename AT>
+__device__ void do_pass_m3(const ManyReq& q, const double* A, const double* B, double* out, int rk, int C,
+                           char* big) {
+  AT* KRs = (AT*)big;
+  double* Ms = (double*)(big + kFib * kMaxR * sizeof(double));
+  if (q.t64)
+    pass_m3<double, AT>((const double*)q.T, q.J, q.I2, q.I3, q.R, A, B, out, rk, C, KRs, Ms);
+  else
+    pass_m3<float, AT>((const float*)q.T, q.J, q.I2, q.I3, q.R, A, B, out, rk, C, KRs, Ms);
+}
+
+// Gradient rows G^(n) = -M^(n) + A^(n) Gammabar^(n) (Eq. Gn) of the CTA's
+// rows, Gammabar^(n) from the Grams G (3 x R x R) of the point v.
+__device__ void grad_rows(const ManyReq& q, const Rows& w, const double* v, const double* G, const double* M1,
+                          const double* M2, const double* M3, double* g, EngSh& sh) {
+  const int R = q.R, RR = R * R;
+  for (int n = 0; n < 3; ++n) {
+    hadamard_into(G + (size_t)((n + 1) % 3) * RR, G + (size_t)((n + 2) % 3) * RR, R, sh.A0);
+    const double* Mn = n == 0 ? M1 : n == 1 ? M2 : M3;
+    const int cnt = (w.hi[n] - w.lo[n]) * R;
+    for (int k = threadIdx.x; k < cnt; k += kThreads) {
+      const int i = w.lo[n] + k / R, r = k - (k / R) * R;
+      const double* a = v + w.off[n] + (size_t)i * R;
+      double s = -Mn[(size_t)i * R + r];
+      for (int kk = 0; kk < R; ++kk) s = fma(a[kk], sh.A0[kk * R + r], s);
+      g[w.off[n] + (size_t)i * R + r] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// ALS update of the CTA's rows of mode n: dst rows = M rows Gammabar^-1 (sh.A).
+__device__ void als_rows(const double* M, int R, int lo, int hi, double* dst, const EngSh& sh) {
+  __syncthreads();
+  for (int k = threadIdx.x; k < (hi - lo) * R; k += kThreads) {
+    const int i = lo + k / R, r = k - (k / R) * R;
+    const double* m = M + (size_t)i * R;
+    double s = 0.0;
+    for (int kk = 0; kk < R; ++kk) s = fma(m[kk], sh.A[kk * R + r], s);
+    dst[(size_t)i * R + r] = s;
+  }
+  __syncthreads();
+}
+
+// Push the CTA's elements of (u, g) into the window (slot 0 after a reset)
+// and return its partial of ||g||^2.
+__device__ double window_push(const ManyReq& q, const Rows& w, const double* u, const double* g, int slot) {
+  double part = 0.0;
+  double* Us = q.U + (size_t)slot * q.P;
+  double* Gs_ = q.G + (size_t)slot * q.P;
+  for_own(w, q.R, [&](int e, int, int, int) {
+    const double gv = g[e];
+    Us[e] = u[e];
+    Gs_[e] = gv;
+    part = fma(gv, gv, part);
+  });
+  return part;
+}
+
+__device__ __forceinline__ int push_slot(const ManyCtl& c, int w, bool reset) {
+  if (reset) return 0;
+  return c.win_m < w ? (c.win_start + c.win_m) % w : c.win_start;
+}
+
+enum TailKind { T_BEGIN = 0, T_ACCEPT = 1, T_KEEP = 2 };
+
+// End of a phase start or an iteration: ||g||, f, window bookkeeping,
+// counters and the stopping test (the same in every CTA), the park
+// decision (CTA 0's clock), the control block to global memory.  The
+// partials of ||g||^2 (and of <A^(3), M^(3)> for T_BEGIN / T_ACCEPT) are in
+// the scalar region A, slots 2 and 1.  Returns true when the cluster leaves
+// this request (finished or parked).
+__device__ bool tail(EngSh& sh, int rk, int C, int kind, bool reset, unsigned long long t0,
+                     unsigned long long budget) {
+  const ManyReq& q = sh.q;
+  const int SCA = 2 * q.big_ld;
+  if (rk == 0 && threadIdx.x == 0) q.scal[S_PARK] = (gtimer() - t0 > budget) ? 1.0 : 0.0;
+  cl_sync();
+  const double gg = psum(q.part + SCA + 2, q.part_ld, C, 0);
+  double f;
+  if (kind == T_KEEP) {
+    f = sh.bcast[0];
+  } else {
+    const double inner = psum(q.part + SCA + 1, q.part_ld, C, 0);
+    const double model = model_norm2(kind == T_ACCEPT ? q.Gx : q.Gu, q.R, sh);
+    f = 0.5 * (q.normT2 - 2.0 * inner + model);
+  }
+  const bool park = q.scal[S_PARK] != 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ManyCtl& c = sh.c;
+    const bool mixed = c.phase == PH_MIXED;
+    if (reset) {
+      c.win_start = 0;
+      c.win_m = 1;
+    } else if (c.win_m < q.w) {
+      c.win_m += 1;
+    } else {
+      c.win_start = (c.win_start + 1) % q.w;
+    }
+    if (kind == T_BEGIN) {
+      c.best = INFINITY;
+      c.since_best = 0;
+      c.fg_evals += 1;
+      c.start = 0;
+    } else {
+      c.iters += 1;
+      if (mixed)
+        c.mixed_iters += 1;
+      else
+        c.fp64_iters += 1;
+    }
+    const double gn = sqrt(gg) / q.P;
+    c.gn = gn;
+    c.f = f;
+    int stop = STOP_RUN;
+    if (!isfinite(gn))
+      stop = STOP_NONFINITE;
+    else if (gn < (mixed ? q.tol_mixed : q.tol))
+      stop = STOP_TOL;
+    else if (c.iters >= q.maxit)
+      stop = STOP_MAXIT;
+    else if (mixed) {
+      if (gn < c.best) {
+        c.best = gn;
+        c.since_best = 0;
+      } else if (++c.since_best >= q.stall) {
+        stop = STOP_STALL;
+      }
+    }
+    c.stop = stop;
+    if (stop != STOP_RUN) {
+      if (mixed && q.polish && (stop == STOP_TOL || stop == STOP_STALL)) {
+        c.phase = PH_FP64;
+        c.start = 1;
+      } else {
+        c.phase = PH_DONE;
+        if (stop == STOP_NONFINITE) c.status = CP_ERR_NONFINITE;
+      }
+    }
+    if (rk == 0) {
+      *q.ctl = c;
+      q.scal[S_F] = f;
+    }
+  }
+  __syncthreads();
+  return sh.c.phase == PH_DONE || park;
+}
+
+// Phase start: (start == 2) u = normalise(x), x holding the initial guess
+// (R5 of the readings: the solve starts from the normalised guess); f and g
+// at u in this phase's precision; the window becomes {(u, g)}.
+template <typename AT>
+__device__ bool run_start(EngSh& sh, char* big, int rk, int C, unsigned long long t0, unsigned long long budget) {
+  const ManyReq& q = sh.q;
+  const int R = q.R, RR = R * R, ld = q.part_ld;
+  const int BA = 0, BB = q.big_ld, SCA = 2 * q.big_ld;
+  double* my = q.part + (size_t)rk * ld;
+  const Rows w = rows_of(q, rk, C);
+  if (sh.c.start == 2) {
+    for (int n = 0; n < 3; ++n) gram_part(q.x + w.off[n], q.x + w.off[n], w.lo[n], w.hi[n], R, my + BA + n * RR);
+    cl_sync();
+    for (int t = threadIdx.x; t < 3 * R; t += kThreads) {
+      const int n = t / R, r = t - (t / R) * R;
+      sh.sc2[t] = psum(q.part + BA, ld, C, n * RR + r * R + r);
+    }
+    norm_scales(sh.sc2, R, sh, sh.scale, sh.order);
+    for_own(w, R, [&](int e, int n, int i, int r) {
+      const int o = sh.order[r];
+      q.u[e] = q.x[w.off[n] + (size_t)i * R + o] * sh.scale[n * R + o];
+    });
+    if (rk == 0) {
+      for (int e = threadIdx.x; e < 3 * RR; e += kThreads) q.Gx[e] = psum(q.part + BA, ld, C, e);
+      __syncthreads();
+      grams_normalised(q.Gx, R, sh.scale, sh.order, q.Gu);
+    }
+    cl_sync();
+  }
+  const double* u = q.u;
+  do_pass_y<AT>(q, u + q.off3, nullptr, rk, C, big);
+  cl_sync();
+  contract_m1<AT>((const AT*)q.Y, R, 0, q.I1, q.I2, R, u + q.off2, q.M1, rk, C);
+  contract_m2<AT>((const AT*)q.Y, R, 0, q.I1, q.I2, R, u, q.M2, rk, C);
+  do_pass_m3<AT>(q, u, u + q.off2, my + BB, rk, C, big);
+  cl_sync();
+  double inner = 0.0;
+  for (int k = threadIdx.x; k < (w.hi[2] - w.lo[2]) * R; k += kThreads) {
+    const int e = w.lo[2] * R + k;
+    const double m = psum(q.part + BB, ld, C, e);
+    q.M3[e] = m;
+    inner = fma(u[q.off3 + e], m, inner);
+  }
+  inner = cta_sum(inner, sh);
+  grad_rows(q, w, u, q.Gu, q.M1, q.M2, q.M3, q.g, sh);
+  const double gpart = cta_sum(window_push(q, w, u, q.g, 0), sh);
+  if (threadIdx.x == 0) {
+    my[SCA + 1] = inner;
+    my[SCA + 2] = gpart;
+  }
+  return tail(sh, rk, C, T_BEGIN, true, t0, budget);
+}
+
+// The "keep" ends of an iteration: after a restart (reset) or a search that
+// found no acceptable step, u = ubar with its f, g and Grams.
+__device__ bool keep_ubar(EngSh& sh, int rk, int C, bool reset, unsigned long long t0, unsigned long long budget) {
+  const ManyReq& q = sh.q;
+  const Rows w = rows_of(q, rk, C);
+  for_own(w, q.R, [&](int e, int, int, int) {
+    q.u[e] = q.ub[e];
+    q.g[e] = q.gb[e];
+  });
+  if (rk == 0)
+    for (int e = threadIdx.x; e < 3 * q.R * q.R; e += kThreads) q.Gu[e] = q.Gb[e];
+  __syncthreads();
+  const double gpart = cta_sum(window_push(q, w, q.u, q.g, push_slot(sh.c, q.w, reset)), sh);
+  if (threadIdx.x == 0) q.part[(size_t)rk * q.part_ld + 2 * q.big_ld + 2] = gpart;
+  return tail(sh, rk, C, T_KEEP, reset, t0, budget);
+}
+
+// One iteration of Algorithm 1 from u (with g(u), Grams of u, window).
+template <typename AT>
+__device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long t0, unsigned long long budget) {
+  const ManyReq& q = sh.q;
+  const int R = q.R, RR = R * R, ld = q.part_ld;
+  const int BA = 0, BB = q.big_ld, SCA = 2 * q.big_ld, SCB = SCA + 128;
+  double* my = q.part + (size_t)rk * ld;
+  const Rows w = rows_of(q, rk, C);
+  const double* u = q.u;
+  double* sw = q.uh;   // the swept point (unnormalised), later uhat
+  auto fail_spd = [&]() {
+    if (threadIdx.x == 0) {
+      sh.c.status = CP_ERR_NOT_SPD;
+      sh.c.phase = PH_DONE;
+      if (rk == 0) *q.ctl = sh.c;
+    }
+    __syncthreads();
+    return true;
+  };
+
+  // ---- Step I: the ALS sweep (Section 2.3), modes 1 and 2 from Y = T x_3 A^(3)
+  do_pass_y<AT>(q, u + q.off3, nullptr, rk, C, big);
+  cl_sync();
+  hadamard_into(q.Gu + RR, q.Gu + 2 * RR, R, sh.A0);
+  if (!gammabar_inverse(R, sh)) return fail_spd();
+  contract_m1<AT>((const AT*)q.Y, R, 0, q.I1, q.I2, R, u + q.off2, q.M1, rk, C);
+  als_rows(q.M1, R, w.lo[0], w.hi[0], sw, sh);
+  gram_part(sw, sw, w.lo[0], w.hi[0], R, my + BA);
+  cl_sync();
+  __syncthreads();
+  for (int e = threadIdx.x; e < RR; e += kThreads) {
+    const double g1 = psum(q.part + BA, ld, C, e);
+    sh.A0[e] = g1 * q.Gu[2 * RR + e];
+    if (rk == 0) q.Gs[e] = g1;
+  }
+  if (!gammabar_inverse(R, sh)) return fail_spd();
+  contract_m2<AT>((const AT*)q.Y, R, 0, q.I1, q.I2, R, sw, q.M2, rk, C);
+  als_rows(q.M2, R, w.lo[1], w.hi[1], sw + q.off2, sh);
+  gram_part(sw + q.off2, sw + q.off2, w.lo[1], w.hi[1], R, my + BB);
+  cl_sync();
+  if (rk == 0)
+    for (int e = threadIdx.x; e < RR; e += kThreads) q.Gs[RR + e] = psum(q.part + BB, ld, C, e);
+  do_pass_m3<AT>(q, sw, sw + q.off2, my + BA, rk, C, big);
+  cl_sync();
+  for (int k = threadIdx.x; k < (w.hi[2] - w.lo[2]) * R; k += kThreads) {
+    const int e = w.lo[2] * R + k;
+    q.M3s[e] = psum(q.part + BA, ld, C, e);
+  }
+  hadamard_into(q.Gs, q.Gs + RR, R, sh.A0);
+  if (!gammabar_inverse(R, sh)) return fail_spd();
+  als_rows(q.M3s, R, w.lo[2], w.hi[2], sw + q.off3, sh);
+  gram_part(sw + q.off3, sw + q.off3, w.lo[2], w.hi[2], R, my + BB);
+  cl_sync();
+
+  // ---- ubar = normalise(swept) (R3, R4); its Grams and M^(3) follow
+  for (int t = threadIdx.x; t < 3 * R; t += kThreads) {
+    const int n = t / R, r = t - (t / R) * R;
+    sh.sc2[t] = n < 2 ? q.Gs[(size_t)n * RR + r * R + r] : psum(q.part + BB, ld, C, r * R + r);
+  }
+  norm_scales(sh.sc2, R, sh, sh.scale, sh.order);
+  if (rk == 0) {
+    for (int e = threadIdx.x; e < RR; e += kThreads) q.Gs[2 * RR + e] = psum(q.part + BB, ld, C, e);
+    __syncthreads();
+    grams_normalised(q.Gs, R, sh.scale, sh.order, q.Gb);
+  }
+  for_own(w, R, [&](int e, int n, int i, int r) {
+    const int o = sh.order[r];
+    q.ub[e] = sw[w.off[n] + (size_t)i * R + o] * sh.scale[n * R + o];
+  });
+  for (int k = threadIdx.x; k < (w.hi[2] - w.lo[2]) * R; k += kThreads) {
+    const int i = w.lo[2] + k / R, p = k - (k / R) * R;
+    const int o = sh.order[p];
+    q.M3[(size_t)i * R + p] = q.M3s[(size_t)i * R + o] * sh.scale[o] * sh.scale[R + o];
+  }
+  cl_sync();
+
+  // ---- f and g at ubar: modes 1 and 2 from Y' = T x_3 Abar^(3)
+  const double* ub = q.ub;
+  do_pass_y<AT>(q, ub + q.off3, nullptr, rk, C, big);
+  cl_sync();
+  contract_m1<AT>((const AT*)q.Y, R, 0, q.I1, q.I2, R, ub + q.off2, q.M1, rk, C);
+  contract_m2<AT>((const AT*)q.Y, R, 0, q.I1, q.I2, R, ub, q.M2, rk, C);
+  __syncthreads();
+  grad_rows(q, w, ub, q.Gb, q.M1, q.M2, q.M3, q.gb, sh);
+  {
+    double inner = 0.0;
+    for (int k = threadIdx.x; k < (w.hi[2] - w.lo[2]) * R; k += kThreads) {
+      const int e = w.lo[2] * R + k;
+      inner = fma(ub[q.off3 + e], q.M3[e], inner);
+    }
+    inner = cta_sum(inner, sh);
+    if (threadIdx.x == 0) my[SCA] = inner;
+  }
+
+  // ---- Step II: window dots over the CTA's elements (p_j = gbar - g_j)
+  const int m = sh.c.win_m, wstart = sh.c.win_start;
+  const int npairs = m * (m + 1) / 2, ntask = npairs + m;
+  {
+    double* tile = (double*)big;                 // m x kTileLd, then gbar
+    double* gt = tile + (size_t)kMaxW * kTileLd;
+    double acc[3] = {0.0, 0.0, 0.0};
+    int ta[3], tb[3];
+    for (int s = 0; s < 3; ++s) {
+      const int t = threadIdx.x + s * kThreads;
+      ta[s] = -1;
+      tb[s] = -1;
+      if (t < npairs) {
+        int j = 0, rem = t;
+        while (rem >= m - j) {
+          rem -= m - j;
+          ++j;
+        }
+        ta[s] = j;
+        tb[s] = j + rem;
+      } else if (t < ntask) {
+        ta[s] = t - npairs;   // rhs_j: against gbar
+        tb[s] = -2;
+      }
+    }
+    for (int n = 0; n < 3; ++n) {
+      const int e_lo = w.off[n] + w.lo[n] * R, e_hi = w.off[n] + w.hi[n] * R;
+      for (int e0 = e_lo; e0 < e_hi; e0 += kTile) {
+        const int ne = min(kTile, e_hi - e0);
+        __syncthreads();
+        for (int x = threadIdx.x; x < m * kTile; x += kThreads) {
+          const int j = x / kTile, k = x - (x / kTile) * kTile;
+          double v = 0.0;
+          if (k < ne) v = q.gb[e0 + k] - q.G[(size_t)ring(wstart, j, q.w) * q.P + e0 + k];
+          tile[j * kTileLd + k] = v;
+        }
+        for (int k = threadIdx.x; k < kTile; k += kThreads) gt[k] = k < ne ? q.gb[e0 + k] : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+          if (ta[s] >= 0) {
+            const double* a = tile + ta[s] * kTileLd;
+            const double* b = tb[s] == -2 ? gt : tile + tb[s] * kTileLd;
+            double v = acc[s];
+            for (int k = 0; k < ne; ++k) v = fma(a[k], b[k], v);
+            acc[s] = v;
+          }
+        }
+      }
+    }
+    for (int s = 0; s < 3; ++s) {
+      const int t = threadIdx.x + s * kThreads;
+      if (t < ntask) my[BA + t] = t < npairs ? acc[s] : -acc[s];
+    }
+  }
+  cl_sync();
+  // f(ubar); the normal equations, solved in every CTA
+  {
+    const double inner = psum(q.part + SCA, ld, C, 0);
+    const double model = model_norm2(q.Gb, R, sh);
+    if (threadIdx.x == 0) sh.bcast[0] = 0.5 * (q.normT2 - 2.0 * inner + model);
+  }
+  for (int t = threadIdx.x; t < ntask; t += kThreads) {
+    const double v = psum(q.part + BA, ld, C, t);
+    if (t < npairs) {
+      int j = 0, rem = t;
+      while (rem >= m - j) {
+        rem -= m - j;
+        ++j;
+      }
+      const int l = j + rem;
+      sh.H[j * kMaxW + l] = v;
+      sh.H[l * kMaxW + j] = v;
+    } else {
+      sh.rhs[t - npairs] = v;
+    }
+  }
+  window_solve(m, q.eps, sh);
+  // uhat = ubar + sum_j alpha_j (ubar - u_j) (Eq. accel), and its column sums of squares
+  {
+    double cs = 0.0;
+    const int tR = (int)threadIdx.x < 3 * R ? (int)threadIdx.x : -1;
+    for_own(w, R, [&](int e, int, int, int) {
+      const double b = ub[e];
+      double acc = 0.0;
+      for (int j = 0; j < m; ++j) acc += sh.alpha[j] * (b - q.U[(size_t)ring(wstart, j, q.w) * q.P + e]);
+      sw[e] = b + acc;
+    });
+    __syncthreads();
+    if (tR >= 0) {
+      const int n = tR / R, r = tR - (tR / R) * R;
+      for (int i = w.lo[n]; i < w.hi[n]; ++i) {
+        const double v = sw[w.off[n] + (size_t)i * R + r];
+        cs = fma(v, v, cs);
+      }
+      my[SCB + tR] = cs;
+    }
+  }
+  cl_sync();
+  // normalise uhat (R6); d = uhat - ubar, the slope g(ubar)^T d; the line
+  // search's Grams ubar^T d and d^T d
+  for (int t = threadIdx.x; t < 3 * R; t += kThreads) sh.sc2[t] = psum(q.part + SCB, ld, C, t);
+  norm_scales(sh.sc2, R, sh, sh.scale, sh.order);
+  {
+    double sl = 0.0;
+    for_own(w, R, [&](int e, int n, int i, int r) {
+      const int o = sh.order[r];
+      const double dv = sw[w.off[n] + (size_t)i * R + o] * sh.scale[n * R + o] - ub[e];
+      q.d[e] = dv;
+      sl = fma(q.gb[e], dv, sl);
+    });
+    sl = cta_sum(sl, sh);
+    if (threadIdx.x == 0) my[SCA] = sl;
+  }
+  __syncthreads();
+  for (int n = 0; n < 3; ++n) {
+    gram_part(ub + w.off[n], q.d + w.off[n], w.lo[n], w.hi[n], R, my + BB + n * RR);
+    gram_part(q.d + w.off[n], q.d + w.off[n], w.lo[n], w.hi[n], R, my + BB + (3 + n) * RR);
+  }
+  cl_sync();
+  const double slope = psum(q.part + SCA, ld, C, 0);
+  const bool restart = !(slope < 0.0);
+  if (threadIdx.x == 0) {
+    sh.c.als_sweeps += 1;
+    sh.c.fg_evals += 1;
+    if (restart) sh.c.restarts += 1;
+  }
+  __syncthreads();
+  if (restart) return keep_ubar(sh, rk, C, true, t0, budget);   // R7
+
+  // ---- Step III: the line polynomial phi(beta) = f(ubar + beta d)
+  if (rk == 0)
+    for (int e = threadIdx.x; e < 3 * RR; e += kThreads) {
+      q.Gad[e] = psum(q.part + BB, ld, C, e);
+      q.Gdd[e] = psum(q.part + BB, ld, C, 3 * RR + e);
+    }
+  do_pass_y<AT>(q, ub + q.off3, q.d + q.off3, rk, C, big);
+  cl_sync();
+  contract_variants<AT>((const AT*)q.Y, q.I1, q.I2, R, ub, q.d, ub + q.off2, q.d + q.off2, q.V1, q.V2, rk, C);
+  __syncthreads();
+  // <T, [[A_a, B_b, C_c]]> partials: sum over the CTA's rows of mode 1 of A_a V1[2c + b]
+  for (int k8 = 0; k8 < 8; ++k8) {
+    const int a = k8 >> 2, v = k8 & 3;
+    const double* F = a ? q.d : ub;
+    const double* V = q.V1 + (size_t)v * q.I1 * R;
+    double s8 = 0.0;
+    for (int k = threadIdx.x; k < (w.hi[0] - w.lo[0]) * R; k += kThreads) {
+      const int e = w.lo[0] * R + k;
+      s8 = fma(F[e], V[e], s8);
+    }
+    s8 = cta_sum(s8, sh);
+    if (threadIdx.x == 0) my[SCB + k8] = s8;
+  }
+  cl_sync();
+  if (rk == 0) {
+    // E(beta) = ||[[ubar + beta d]]||^2 = sum_{r,s} prod_n (a_n + b_n beta + c_n beta^2)
+    double e7[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int e = threadIdx.x; e < RR; e += kThreads) {
+      const int r = e / R, s2 = e - (e / R) * R;
+      double pc[7] = {1, 0, 0, 0, 0, 0, 0};
+      int deg = 0;
+      for (int n = 0; n < 3; ++n) {
+        const double a0 = q.Gb[(size_t)n * RR + e];
+        const double a1 = q.Gad[(size_t)n * RR + e] + q.Gad[(size_t)n * RR + s2 * R + r];
+        const double a2 = q.Gdd[(size_t)n * RR + e];
+        double nx[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int k = 0; k <= deg; ++k) {
+          nx[k] = fma(pc[k], a0, nx[k]);
+          nx[k + 1] = fma(pc[k], a1, nx[k + 1]);
+          nx[k + 2] = fma(pc[k], a2, nx[k + 2]);
+        }
+        deg += 2;
+        for (int k = 0; k < 7; ++k) pc[k] = nx[k];
+      }
+      for (int k = 0; k < 7; ++k) e7[k] += pc[k];
+    }
+    for (int k = 0; k < 7; ++k) e7[k] = cta_sum(e7[k], sh);
+    if (threadIdx.x == 0) {
+      double poly[7];
+      for (int k = 0; k < 7; ++k) poly[k] = 0.5 * e7[k];
+      for (int k8 = 0; k8 < 8; ++k8) {
+        const int a = k8 >> 2, v = k8 & 3;
+        const int b = v & 1, c = v >> 1;
+        poly[a + b + c] -= psum(q.part + SCB, ld, C, k8);
+      }
+      poly[0] += 0.5 * q.normT2;
+      MTState st;
+      mtdev::mt_init(st, poly[0], poly[1], sh.c.phase == PH_MIXED ? q.ls_mixed : q.ls);
+      while (!st.done) {
+        const double b = st.stp;
+        double f = poly[6], g = 6.0 * poly[6];
+        for (int k = 5; k >= 1; --k) {
+          f = fma(f, b, poly[k]);
+          g = fma(g, b, k * poly[k]);
+        }
+        f = fma(f, b, poly[0]);
+        mtdev::mt_advance(&st, &f, &g);
+      }
+      const bool accept = st.nfev > 0 && (st.info == 1 || st.f <= st.f0 + st.ftol * st.stp_eval * st.g0);
+      q.scal[S_BETA] = st.stp_eval;
+      q.scal[S_ACCEPT] = accept ? 1.0 : 0.0;
+      q.scal[5] = (double)st.nfev;
+      q.scal[6] = (double)st.info;
+      sh.bcast[1] = accept ? 1.0 : 0.0;
+      sh.bcast[2] = st.stp_eval;
+    }
+    __syncthreads();
+    if (sh.bcast[1] != 0.0) {
+      const double beta = sh.bcast[2];
+      for (int e = threadIdx.x; e < 3 * RR; e += kThreads) {
+        const int n = e / RR, rs = e - n * RR;
+        const int r = rs / R, s2 = rs - (rs / R) * R;
+        const double a1 = q.Gad[e] + q.Gad[(size_t)n * RR + s2 * R + r];
+        q.Gx[e] = fma(beta, fma(beta, q.Gdd[e], a1), q.Gb[e]);
+      }
+    }
+  }
+  cl_sync();
+  const double beta = q.scal[S_BETA];
+  const bool accept = q.scal[S_ACCEPT] != 0.0;
+  if (threadIdx.x == 0) {
+    sh.c.ls_trials += (int)q.scal[5];
+    if ((int)q.scal[6] != 1) sh.c.ls_failures += 1;
+    if (accept) {
+      sh.c.accepts += 1;
+      sh.c.fg_evals += 1;
+    }
+  }
+  __syncthreads();
+  if (!accept) return keep_ubar(sh, rk, C, false, t0, budget);   // R10
+
+  // ---- the accepted point x = ubar + beta d: M^(1), M^(2) from the variants
+  for_own(w, R, [&](int e, int, int, int) { q.x[e] = fma(beta, q.d[e], ub[e]); });
+  {
+    const double b2 = beta * beta;
+    const size_t s1 = (size_t)q.I1 * R, s2 = (size_t)q.I2 * R;
+    for (int k = threadIdx.x; k < (w.hi[0] - w.lo[0]) * R; k += kThreads) {
+      const int e = w.lo[0] * R + k;
+      q.M1[e] = q.V1[e] + beta * (q.V1[s1 + e] + q.V1[2 * s1 + e]) + b2 * q.V1[3 * s1 + e];
+    }
+    for (int k = threadIdx.x; k < (w.hi[1] - w.lo[1]) * R; k += kThreads) {
+      const int e = w.lo[1] * R + k;
+      q.M2[e] = q.V2[e] + beta * (q.V2[s2 + e] + q.V2[2 * s2 + e]) + b2 * q.V2[3 * s2 + e];
+    }
+  }
+  cl_sync();
+  do_pass_m3<AT>(q, q.x, q.x + q.off2, my + BA, rk, C, big);
+  cl_sync();
+  double inner = 0.0;
+  for (int k = threadIdx.x; k < (w.hi[2] - w.lo[2]) * R; k += kThreads) {
+    const int e = w.lo[2] * R + k;
+    const double mv = psum(q.part + BA, ld, C, e);
+    q.M3[e] = mv;
+    inner = fma(q.x[q.off3 + e], mv, inner);
+  }
+  inner = cta_sum(inner, sh);
+  grad_rows(q, w, q.x, q.Gx, q.M1, q.M2, q.M3, sw, sh);
+  // u, g = normalise(x, g(x)) (R8), with the scales from x's Grams
+  for (int t = threadIdx.x; t < 3 * R; t += kThreads) {
+    const int n = t / R, r = t - (t / R) * R;
+    sh.sc2[t] = q.Gx[(size_t)n * RR + r * R + r];
+  }
+  norm_scales(sh.sc2, R, sh, sh.scale, sh.order);
+  for_own(w, R, [&](int e, int n, int i, int r) {
+    const int o = sh.order[r];
+    const size_t src = w.off[n] + (size_t)i * R + o;
+    const double sc = sh.scale[n * R + o];
+    q.u[e] = q.x[src] * sc;
+    q.g[e] = sw[src] / sc;
+  });
+  if (rk == 0) grams_normalised(q.Gx, R, sh.scale, sh.order, q.Gu);
+  __syncthreads();
+  const double gpart = cta_sum(window_push(q, w, q.u, q.g, push_slot(sh.c, q.w, false)), sh);
+  if (threadIdx.x == 0) {
+    my[SCA + 1] = inner;
+    my[SCA + 2] = gpart;
+  }
+  return tail(sh, rk, C, T_ACCEPT, false, t0, budget);
+}
+
+// ------------------------------------------------------------------ kernel
+
+// Persistent: each cluster takes requests from the queue (tasks[next++]) and
+// runs their solves; a cluster stops taking new ones once its CTA 0 has run
+// for budget_ns, and parks its current request at the end of the iteration
+// in which that happens (the request's state stays in its buffers).
+__global__ void __launch_bounds__(kThreads, 1)
+    many_kernel(const ManyReq* __restrict__ reqs, const int* __restrict__ tasks, ManyQueue* queue,
+                int* cluster_task) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  EngSh& sh = *reinterpret_cast<EngSh*>(dyn_smem);
+  char* big = reinterpret_cast<char*>(dyn_smem) + (sizeof(EngSh) + 127) / 128 * 128;
+  const int rk = (int)cl_rank(), C = (int)cl_size();
+  const unsigned cid = cl_id();
+  if (threadIdx.x == 0) sh.t0 = gtimer();
+  __syncthreads();
+  const unsigned long long t0 = sh.t0;
+  const unsigned long long budget = queue->budget_ns;
+  const int ntasks = queue->ntasks;
+  for (;;) {
+    if (rk == 0 && threadIdx.x == 0) {
+      int t = ntasks;
+      if (gtimer() - t0 <= budget) t = atomicAdd(&queue->next, 1);
+      cluster_task[cid] = t;
+    }
+    cl_sync();
+    if (threadIdx.x == 0) sh.task = *(volatile int*)&cluster_task[cid];
+    __syncthreads();
+    const int t = sh.task;
+    cl_sync();
+    if (t >= ntasks) break;
+    if (threadIdx.x == 0) {
+      sh.q = reqs[tasks[t]];
+      sh.c = *sh.q.ctl;
+    }
+    __syncthreads();
+    for (;;) {
+      if (sh.c.phase == PH_DONE) break;
+      bool leave;
+      if (sh.c.start)
+        leave = sh.c.phase == PH_MIXED ? run_start<float>(sh, big, rk, C, t0, budget)
+                                       : run_start<double>(sh, big, rk, C, t0, budget);
+      else
+        leave = sh.c.phase == PH_MIXED ? run_iter<float>(sh, big, rk, C, t0, budget)
+                                       : run_iter<double>(sh, big, rk, C, t0, budget);
+      if (leave) break;
+    }
+  }
+}
+
+size_t engine_smem(int I3max, int IRmax) {
+  size_t bigb = std::max<size_t>((size_t)I3max * kBsCols * sizeof(double),
+                                 (size_t)kFib * kMaxR * sizeof(double) + (size_t)IRmax * sizeof(double));
+  bigb = std::max<size_t>(bigb, ((size_t)kMaxW * kTileLd + kTile) * sizeof(double));
+  return (sizeof(EngSh) + 127) / 128 * 128 + bigb;
+}
+
+}  // namespace
+}  // namespace cpg
+
+// ------------------------------------------------------------------- host
+
+namespace cpg {
+
+namespace {
+
+constexpr int kStallDefault = 800;
+
+struct ManyJob {
+  ManyReq q{};
+  void* mem = nullptr;
+  int C = 1;
+  bool done = false;
+  const cp_tensor* t = nullptr;
+  std::chrono::steady_clock::time_point t0;
+  double t_done = 0.0;
+};
+
+int64_t big_ld_of(int I3, int R) {
+  int64_t b = std::max<int64_t>((int64_t)I3 * R, 6 * (int64_t)R * R);
+  b = std::max<int64_t>(b, (int64_t)kMaxW * (kMaxW + 1) / 2 + kMaxW);
+  return (b + 31) / 32 * 32;
+}
+
+// Bytes of one request's state; with base, the pointers of q are set.
+size_t job_layout(ManyReq& q, char* base) {
+  const int64_t P = q.P, R = q.R, RR = R * R;
+  const int64_t big = big_ld_of(q.I3, q.R);
+  const int64_t ld = 2 * big + 256;
+  size_t n = 0;
+  auto take = [&](int64_t cnt) -> double* {
+    double* p = base ? (double*)(base + n * sizeof(double)) : nullptr;
+    n += (size_t)((cnt + 15) / 16 * 16);   // 128-byte aligned pieces
+    return p;
+  };
+  q.u = take(P);
+  q.g = take(P);
+  q.ub = take(P);
+  q.gb = take(P);
+  q.uh = take(P);
+  q.d = take(P);
+  q.x = take(P);
+  q.U = take((int64_t)q.w * P);
+  q.G = take((int64_t)q.w * P);
+  q.Y = take((int64_t)q.J * 2 * R);
+  q.M1 = take(q.I1 * R);
+  q.M2 = take(q.I2 * R);
+  q.M3 = take(q.I3 * R);
+  q.M3s = take(q.I3 * R);
+  q.V1 = take(4 * q.I1 * R);
+  q.V2 = take(4 * q.I2 * R);
+  q.part = take(kMaxC * ld);
+  q.Gu = take(3 * RR);
+  q.Gs = take(3 * RR);
+  q.Gb = take(3 * RR);
+  q.Gad = take(3 * RR);
+  q.Gdd = take(3 * RR);
+  q.Gx = take(3 * RR);
+  q.scal = take(16);
+  q.part_ld = (int)ld;
+  q.big_ld = (int)big;
+  return n * sizeof(double);
+}
+
+// Cluster size for a request of K entries and rank R, before tuning.
+int default_cluster(int64_t K, int R) {
+  const int64_t work = K * (int64_t)std::max(R, 8);
+  if (work < ((int64_t)1 << 20)) return 1;
+  if (work < ((int64_t)1 << 22)) return 2;
+  if (work < ((int64_t)1 << 24)) return 4;
+  return 8;
+}
+
+}  // namespace
+
+// Why a request cannot run on the cluster engine (nullptr when it can).
+const char* many_unsupported(const cp_tensor* t, const cp_solve_opts& o) {
+  if (!t || t->kind != 0 || t->N != 3) return "the engine takes 3-way dense tensors";
+  if (o.R < 1 || o.R > kMaxR) return "rank above 32";
+  if (o.w < 1 || o.w > kMaxW) return "window above 32";
+  for (int n = 0; n < 3; ++n) {
+    if (t->dims[n] < 1 || t->dims[n] > kMaxI) return "a side above 256";
+    if (t->dims[n] * o.R > kMaxIR) return "I_n R above 8192";
+  }
+  if (t->dims[0] * t->dims[1] > (int64_t)1 << 30) return "too many fibers";
+  return nullptr;
+}
+
+cp_status many_solve(cp_ctx* ctx, int nreq, const cp_tensor* const* ts, const cp_solve_opts* opts,
+                     double* const* u, cp_solve_report* reps, int cluster) {
+  if (!ctx || nreq < 0 || (nreq > 0 && (!ts || !opts || !u)) || cluster < 0 || cluster > kMaxC ||
+      (cluster & (cluster - 1))) {
+    set_error("cp_solve_many: bad arguments");
+    return CP_ERR_ARG;
+  }
+  if (nreq == 0) return CP_OK;
+  CP_CUDA(cudaSetDevice(ctx->device));
+  CP_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < nreq; ++i) {
+    if (!ts[i] || !u[i] || ts[i]->device != ctx->device) {
+      set_error("cp_solve_many: request %d: null tensor or iterate, or tensor on another device", i);
+      return CP_ERR_ARG;
+    }
+    const char* why = many_unsupported(ts[i], opts[i]);
+    if (why) {
+      set_error("cp_solve_many: request %d: %s", i, why);
+      return CP_ERR_UNSUPPORTED;
+    }
+    const cp_solve_opts& o = opts[i];
+    if (!(o.tol > 0.0) || o.maxit < 0 || !(o.eps >= 0.0) || o.ls.maxfev < 1) {
+      set_error("cp_solve_many: request %d: bad options", i);
+      return CP_ERR_ARG;
+    }
+  }
+  cudaStream_t s = ctx->stream;
+  std::vector<ManyJob> jobs((size_t)nreq);
+  size_t total = 0;
+  std::vector<size_t> at((size_t)nreq);
+  int I3max = 1, IRmax = 1;
+  for (int i = 0; i < nreq; ++i) {
+    const cp_tensor* t = ts[i];
+    const cp_solve_opts& o = opts[i];
+    ManyReq& q = jobs[i].q;
+    q.T = t->Tn[0];
+    q.t64 = t->dtype == CP_DTYPE_F64 ? 1 : 0;
+    q.I1 = (int)t->dims[0];
+    q.I2 = (int)t->dims[1];
+    q.I3 = (int)t->dims[2];
+    q.J = q.I1 * q.I2;
+    q.R = o.R;
+    q.P = (q.I1 + q.I2 + q.I3) * o.R;
+    q.off2 = q.I1 * o.R;
+    q.off3 = (q.I1 + q.I2) * o.R;
+    q.normT2 = t->norm2;
+    q.tol = o.tol;
+    q.tol_mixed = o.tol * (o.mixed_tol_factor > 0.0 ? o.mixed_tol_factor : 1.0);
+    q.eps = o.eps;
+    q.maxit = o.maxit;
+    q.w = o.w;
+    q.polish = o.polish ? 1 : 0;
+    q.stall = o.mixed_stall > 0 ? o.mixed_stall : kStallDefault;
+    q.ls = o.ls;
+    q.ls_mixed = o.ls;
+    if (o.mixed_maxfev > 0 && o.mixed_maxfev < o.ls.maxfev) q.ls_mixed.maxfev = o.mixed_maxfev;
+    at[i] = total;
+    total += (job_layout(q, nullptr) + 255) / 256 * 256;
+    jobs[i].t = t;
+    jobs[i].C = cluster ? cluster : default_cluster(t->K, o.R);
+    I3max = std::max(I3max, q.I3);
+    for (int n = 0; n < 3; ++n) IRmax = std::max<int>(IRmax, (int)t->dims[n] * o.R);
+  }
+  // one allocation: request states, descriptors, control blocks, queues
+  const size_t ctl_off = total;
+  total += ((size_t)nreq * sizeof(ManyCtl) + 255) / 256 * 256;
+  const size_t req_off = total;
+  total += ((size_t)nreq * sizeof(ManyReq) + 255) / 256 * 256;
+  const size_t q_off = total;
+  int maxclusters = 2 * ctx->num_sms;
+  total += 4 * ((sizeof(ManyQueue) + 64 + (size_t)(nreq + maxclusters) * sizeof(int) + 255) / 256 * 256);
+  char* base = nullptr;
+  CP_CUDA(cudaMallocAsync((void**)&base, total, s));
+  ManyCtl* ctl_d = (ManyCtl*)(base + ctl_off);
+  ManyReq* req_d = (ManyReq*)(base + req_off);
+  std::vector<ManyCtl> ctl_h((size_t)nreq);
+  const auto t0 = std::chrono::steady_clock::now();
+  cp_status st = CP_OK;
+  for (int i = 0; i < nreq; ++i) {
+    ManyReq& q = jobs[i].q;
+    (void)job_layout(q, base + at[i]);
+    q.ctl = ctl_d + i;
+    ManyCtl c{};
+    c.phase = opts[i].prec == CP_FP64 ? PH_FP64 : PH_MIXED;
+    c.start = 2;
+    c.best = INFINITY;
+    c.status = CP_OK;
+    ctl_h[i] = c;
+    jobs[i].t0 = t0;
+    if (st == CP_OK) {
+      const cudaError_t e = cudaMemcpyAsync(q.x, u[i], sizeof(double) * q.P, cudaMemcpyDefault, s);
+      if (e != cudaSuccess) st = cuda_fail(e, "cp_solve_many: initial guess", __FILE__, __LINE__);
+    }
+  }
+  std::vector<ManyReq> req_h((size_t)nreq);
+  for (int i = 0; i < nreq; ++i) req_h[i] = jobs[i].q;
+  if (st == CP_OK) {
+    const cudaError_t e1 = cudaMemcpyAsync(req_d, req_h.data(), sizeof(ManyReq) * nreq, cudaMemcpyHostToDevice, s);
+    const cudaError_t e2 = cudaMemcpyAsync(ctl_d, ctl_h.data(), sizeof(ManyCtl) * nreq, cudaMemcpyHostToDevice, s);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) st = cuda_fail(e1 != cudaSuccess ? e1 : e2, "cp_solve_many: upload",
+                                                             __FILE__, __LINE__);
+  }
+  const size_t smem = engine_smem(I3max, IRmax);
+  if (st == CP_OK) {
+    const cudaError_t e = cudaFuncSetAttribute(many_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) st = cuda_fail(e, "cp_solve_many: shared memory", __FILE__, __LINE__);
+  }
+  // rounds: every cluster size's unfinished requests in one launch each
+  int remaining = nreq;
+  while (st == CP_OK && remaining > 0) {
+    char* qb = base + q_off;
+    for (int C = 1; C <= kMaxC && st == CP_OK; C <<= 1) {
+      std::vector<int> tasks;
+      for (int i = 0; i < nreq; ++i)
+        if (!jobs[i].done && jobs[i].C == C) tasks.push_back(i);
+      if (tasks.empty()) continue;
+      ManyQueue* qd = (ManyQueue*)qb;
+      int* tasks_d = (int*)(qb + sizeof(ManyQueue) + 64);
+      int* ctask_d = tasks_d + nreq;
+      qb += (sizeof(ManyQueue) + 64 + (size_t)(nreq + maxclusters) * sizeof(int) + 255) / 256 * 256;
+      ManyQueue qh{0, (int)tasks.size(), 500ull * 1000 * 1000};
+      cudaLaunchConfig_t cfg{};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cfg.gridDim = dim3((unsigned)C);
+      int active = 0;
+      cudaError_t e = cudaOccupancyMaxActiveClusters(&active, many_kernel, &cfg);
+      if (e != cudaSuccess || active < 1) {
+        st = cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidConfiguration, "cp_solve_many: cluster occupancy",
+                       __FILE__, __LINE__);
+        break;
+      }
+      const int nclusters = std::min<int>({active, (int)tasks.size(), maxclusters});
+      cfg.gridDim = dim3((unsigned)(nclusters * C));
+      e = cudaMemcpyAsync(qd, &qh, sizeof(qh), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tasks_d, tasks.data(), sizeof(int) * tasks.size(), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, many_kernel, (const ManyReq*)req_d, (const int*)tasks_d, qd,
+                                                  ctask_d);
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+      if (e != cudaSuccess) st = cuda_fail(e, "cp_solve_many: launch", __FILE__, __LINE__);
+      // the queue's host copies must outlive the copies: wait per launch
+      if (st == CP_OK) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "cp_solve_many: engine", __FILE__, __LINE__);
+      }
+    }
+    if (st != CP_OK) break;
+    const cudaError_t e = cudaMemcpyAsync(ctl_h.data(), ctl_d, sizeof(ManyCtl) * nreq, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) {
+      const cudaError_t e2 = cudaStreamSynchronize(s);
+      if (e2 != cudaSuccess) st = cuda_fail(e2, "cp_solve_many: control blocks", __FILE__, __LINE__);
+    } else {
+      st = cuda_fail(e, "cp_solve_many: control blocks", __FILE__, __LINE__);
+    }
+    const double now = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    remaining = 0;
+    for (int i = 0; i < nreq; ++i) {
+      if (!jobs[i].done && ctl_h[i].phase == PH_DONE) {
+        jobs[i].done = true;
+        jobs[i].t_done = now;
+      }
+      if (!jobs[i].done) ++remaining;
+    }
+  }
+  cp_status first = st;
+  for (int i = 0; i < nreq && st == CP_OK; ++i) {
+    const ManyCtl& c = ctl_h[i];
+    const cudaError_t e = cudaMemcpyAsync(u[i], jobs[i].q.u, sizeof(double) * jobs[i].q.P, cudaMemcpyDefault, s);
+    if (e != cudaSuccess && first == CP_OK) first = cuda_fail(e, "cp_solve_many: solution", __FILE__, __LINE__);
+    if (reps) {
+      cp_solve_report r{};
+      r.iters = c.iters;
+      r.fg_evals = c.fg_evals;
+      r.als_sweeps = c.als_sweeps;
+      r.restarts = c.restarts;
+      r.ls_failures = c.ls_failures;
+      r.converged = (c.stop == STOP_TOL && c.status == CP_OK) ? 1 : 0;
+      r.mixed_iters = c.mixed_iters;
+      r.fp64_iters = c.fp64_iters;
+      r.f = c.f;
+      r.gnorm_over_P = c.gn;
+      r.normT2 = jobs[i].t->norm2;
+      r.t_total_s = jobs[i].t_done;
+      r.ls_trials = c.ls_trials;
+      reps[i] = r;
+    }
+    if (first == CP_OK) {
+      if (c.status != CP_OK) {
+        set_error("cp_solve_many: request %d: %s", i,
+                  c.status == CP_ERR_NOT_SPD ? "Gammabar not positive definite" : "non-finite gradient");
+        first = (cp_status)c.status;
+      } else if (c.stop != STOP_TOL) {
+        set_error("cp_solve_many: request %d: tol not met after %d iterations (||g||/P = %.3e)", i, c.iters, c.gn);
+        first = CP_ERR_MAXIT;
+      }
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaFreeAsync(base, s);
+  cudaStreamSynchronize(s);
+  return first;
+}
+
+}  // namespace cpg
+
+extern "C" cp_status cp_solve_many(cp_ctx* ctx, int nreq, const cp_tensor* const* tensors, const cp_solve_opts* opts,
+                                   double* const* u, cp_solve_report* reps, int cluster) {
+  return cpg::many_solve(ctx, nreq, tensors, opts, u, reps, cluster);
+}

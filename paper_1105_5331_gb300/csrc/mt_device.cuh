@@ -91,6 +91,40 @@ __device__ inline bool slope_secant_zero(const Pt& p, const Pt& q, double* x) {
   return true;
 }
 
+// A search from phi(0) = f0 and phi'(0) = g0 < 0 (done at once, info -1,
+// when g0 is not negative): first trial stp0 clamped to [stpmin, stpmax],
+// no bracket yet, first stage.
+__device__ inline void mt_init(MTState& s, double f0, double g0, const cp_ls_opts& o) {
+  s.ftol = o.ftol;
+  s.gtol = o.gtol;
+  s.xtol = o.xtol;
+  s.stpmin = o.stpmin;
+  s.stpmax = o.stpmax;
+  s.maxfev = o.maxfev;
+  s.f0 = f0;
+  s.g0 = g0;
+  s.nfev = 0;
+  s.info = 0;
+  s.done = 0;
+  s.brackt = 0;
+  s.stage = 1;
+  s.lo_a = 0.0; s.lo_f = f0; s.lo_g = g0;
+  s.hi_a = 0.0; s.hi_f = f0; s.hi_g = g0;
+  s.width = o.stpmax - o.stpmin;
+  s.width1 = 2.0 * s.width;
+  s.stp = fmin(fmax(o.stp0, o.stpmin), o.stpmax);
+  s.imin = 0.0;
+  s.imax = s.stp + 4.0 * s.stp;
+  s.stp_eval = s.stp;
+  s.f = f0;
+  s.g = g0;
+  if (!(g0 < 0.0)) {
+    s.info = -1;
+    s.done = 1;
+    s.stp_eval = 0.0;
+  }
+}
+
 enum TrialCase { kHigher = 1, kSlopesCross = 2, kFlattening = 3, kSteepening = 4 };
 
 __device__ inline int classify(const Pt& l, const Pt& t) {
