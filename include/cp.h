@@ -340,14 +340,26 @@ cp_status cp_solve_batch(cp_ctx* ctx, int nreq, const cp_tensor* const* tensors,
 cp_status cp_solve_many(cp_ctx* ctx, int nreq, const cp_tensor* const* tensors, const cp_solve_opts* opts,
                         double* const* u, cp_solve_report* reps, int cluster);
 
+/* The cluster size cp_solve_many uses for a request when given 0: the size
+ * chosen for its bucket (ceil log2 of its entries, ceil log2 R, FP64 or
+ * mixed).  The first request of a bucket is timed for a few iterations with
+ * each size, 1, 2, 4 and 8 CTAs (the request itself, from u0, in scratch
+ * buffers); the size with the least SM time per iteration (CTAs x time) is
+ * kept for the rest of the process.  u0: host or device (P doubles).
+ * Synchronous.  CP_ERR_UNSUPPORTED as for cp_solve_many. */
+cp_status cp_many_plan(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* opts, const double* u0, int* cluster);
+
 /* Request server (continuous batching).  Requests (dense tensors, each with
  * its own shape, rank, tolerance and precision) wait in arrival order and are
  * admitted while one of `max_active` slots is free and the sum of the device
  * footprints of the running requests stays within hbm_budget_bytes.  Each
  * admitted request keeps its tensor, factors, N-GMRES window and line-search
- * state on the device and runs on its own stream; requests that arrive while
- * others run are admitted as slots and memory free up.  A worker thread inside
- * the server admits, polls and retires requests. */
+ * state on the device; requests that fit the cluster engine (see
+ * cp_server_set_engine) share its persistent launches (up to `max_active` of
+ * them), the others run on a slot of their own (`max_active` slots, each its
+ * own stream); requests that arrive while others run are admitted as slots and
+ * memory free up.  A worker thread inside the server admits, polls and
+ * retires requests. */
 typedef struct cp_server cp_server;
 
 cp_status cp_server_create(cp_ctx* ctx, size_t hbm_budget_bytes, int max_active, cp_server** out);
@@ -376,6 +388,17 @@ cp_status cp_server_drain(cp_server* s, double timeout_s);
  * Any output may be NULL. */
 cp_status cp_server_stats(cp_server* s, double* p50_s, double* p99_s, double* solves_per_s, int* completed,
                           size_t* peak_bytes);
+
+/* Route requests that fit cp_solve_many's limits (3-way dense, sides <= 256,
+ * I_n R <= 8192, R <= 32, w <= 32) and have at most max_work entries x R
+ * (max_work <= 0: no such limit) to the cluster engine (on = 1: one
+ * persistent launch per round of about 10 ms runs every such running
+ * request, each on a thread-block cluster of the size chosen for its bucket,
+ * see cp_many_plan), the others to a graph slot of their own (tensor-core
+ * MTTKRPs over the whole GPU); on = 0 sends every request to a graph slot.
+ * Default: on, max_work = 2^21.  Applies to requests admitted from then on.
+ * CP_ERR_UNSUPPORTED when the engine could not be set up on this device. */
+cp_status cp_server_set_engine(cp_server* s, int on, long long max_work);
 
 /* Stop the worker after the running requests finish; free everything. */
 void cp_server_destroy(cp_server* s);

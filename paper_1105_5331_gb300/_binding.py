@@ -34,8 +34,8 @@ EXPORTED = [
     "cp_tensor_destroy", "cp_mttkrp", "cp_mttkrp_variants", "cp_mttkrp_noalloc", "cp_mttkrp_dimtree", "cp_fg", "cp_als_sweep", "cp_normalize",
     "ngmres_step",
     "cp_ls_opts_default", "linesearch", "cp_solve_opts_default", "cp_solve",
-    "cp_solve_batch", "cp_solve_many", "cp_server_create", "cp_server_submit", "cp_server_poll", "cp_server_cancel",
-    "cp_server_drain", "cp_server_stats", "cp_server_destroy",
+    "cp_solve_batch", "cp_solve_many", "cp_many_plan", "cp_server_create", "cp_server_submit", "cp_server_poll", "cp_server_cancel",
+    "cp_server_drain", "cp_server_stats", "cp_server_set_engine", "cp_server_destroy",
 ]
 
 
@@ -108,6 +108,7 @@ def _load():
                                C.POINTER(cp_solve_report)]),
         "cp_solve_many": (I, [VP, I, C.POINTER(VP), C.POINTER(cp_solve_opts), C.POINTER(VP),
                               C.POINTER(cp_solve_report), I]),
+        "cp_many_plan": (I, [VP, VP, C.POINTER(cp_solve_opts), VP, C.POINTER(I)]),
         "cp_server_create": (I, [VP, C.c_size_t, I, C.POINTER(VP)]),
         "cp_server_submit": (I, [VP, I, P, I, VP, C.POINTER(cp_solve_opts), VP, VP, C.POINTER(C.c_uint64)]),
         "cp_server_poll": (I, [VP, C.c_uint64, C.POINTER(I), C.POINTER(I), C.POINTER(cp_solve_report),
@@ -116,6 +117,7 @@ def _load():
         "cp_server_drain": (I, [VP, D]),
         "cp_server_stats": (I, [VP, C.POINTER(D), C.POINTER(D), C.POINTER(D), C.POINTER(I),
                                 C.POINTER(C.c_size_t)]),
+        "cp_server_set_engine": (I, [VP, I, C.c_longlong]),
         "cp_server_destroy": (None, [VP]),
     }
     for name, (res, args) in sig.items():
@@ -405,16 +407,26 @@ def cp_solve_many(ctx, tensors, opts_list, us, cluster: int = 0) -> list:
     return [r.as_dict() for r in reps]
 
 
+def cp_many_plan(ctx, t, opts, u0) -> int:
+    """Cluster size cp_solve_many gives this request's bucket (tuned on
+    first use)."""
+    out = C.c_int(0)
+    _check(_lib.cp_many_plan(_h(ctx), _h(t), C.byref(opts), _ptr(u0), C.byref(out)))
+    return out.value
+
+
 class Server:
     """Owning wrapper of a cp_server*."""
 
     def __init__(self, handle):
         self.handle = handle
+        self.buffers = []   # host arrays the worker reads or writes until the server is destroyed
 
     def close(self):
         if self.handle:
             _lib.cp_server_destroy(self.handle)
             self.handle = None
+            self.buffers = []
 
     def __del__(self):
         try:
@@ -436,6 +448,8 @@ def cp_server_submit(server, data, opts: cp_solve_opts, u0, u_out) -> int:
     rid = C.c_uint64()
     _check(_lib.cp_server_submit(_h(server), len(dims), _dims(dims), dtype, _ptr(data), C.byref(opts),
                                  _ptr(u0), _ptr(u_out), C.byref(rid)))
+    if isinstance(server, Server):
+        server.buffers.append(u_out)   # the result is written there later
     return rid.value
 
 
@@ -466,6 +480,13 @@ def cp_server_stats(server) -> dict:
     _check(_lib.cp_server_stats(_h(server), C.byref(p50), C.byref(p99), C.byref(sps), C.byref(n), C.byref(peak)))
     return {"p50_s": p50.value, "p99_s": p99.value, "solves_per_s": sps.value, "completed": n.value,
             "peak_bytes": peak.value}
+
+
+def cp_server_set_engine(server, on: bool, max_work: int = 1 << 21):
+    """Route requests that fit the cluster engine and have at most max_work
+    entries x R to it (on, the default), the rest to graph slots of their
+    own; on=False: every request to a graph slot."""
+    _check(_lib.cp_server_set_engine(_h(server), 1 if on else 0, int(max_work)))
 
 
 def cp_server_destroy(server):

@@ -75,6 +75,8 @@ struct ManyCtl {
   int status;         // cp_status of the request
   int win_start, win_m;
   int since_best;
+  int ysrc;           // T x_3 A^(3)(u) for the next sweep: 0 none, 1 in Y (stride R),
+                      // 2 in Y2 (stride R), 3 the first R columns of Y (stride 2R)
   double best, gn, f;
 };
 
@@ -89,6 +91,7 @@ struct ManyReq {
   cp_ls_opts ls, ls_mixed;
   double *u, *g, *ub, *gb, *uh, *d, *x, *U, *G;
   double* Y;          // J x 2R (floats in the mixed phase)
+  double* Y2;         // J x R: T x_3 A^(3) of the accepted point's normalisation
   double *M1, *M2, *M3, *M3s;   // M^(n) at the current point; the swept point's M^(3)
   double *V1, *V2;    // line-search variants of modes 1, 2: 4 x I1 x R, 4 x I2 x R
   double* part;       // kMaxC x part_ld partials: two large regions of big_ld, two of 128 scalars
@@ -120,6 +123,7 @@ struct EngSh {
   double sc2[3 * kMaxR];          // second set of scales (the other normalisation of a step)
   double poly[8];
   double red[kWarps];
+  double redn[kWarps * 8];
   double bcast[8];
   int order[kMaxR];
   int order2[kMaxR];
@@ -176,6 +180,25 @@ __device__ double cta_sum(double v, EngSh& sh) {
   return s;
 }
 
+// NV sums over the CTA at once (NV <= 8, fixed order); every thread gets them.
+template <int NV>
+__device__ void cta_sums(double* v, EngSh& sh) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh.redn[(threadIdx.x >> 5) * 8 + k] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += sh.redn[w * 8 + k];
+    v[k] = s;
+  }
+}
+
 // Sum over the cluster's partials part[c * ld + k] in rank order.
 __device__ __forceinline__ double psum(const double* part, int ld, int C, int k) {
   double s = 0.0;
@@ -189,16 +212,47 @@ __device__ __forceinline__ double fmat(double a, double b, double c) { return __
 
 // ------------------------------------------------------------ passes over T
 
+// Asynchronous copies global -> shared (cp.async, sm_80 and later): every
+// thread issues its share of a tile, so hundreds of loads are in flight.
+__device__ __forceinline__ void cp_async_el(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_el(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Tiles of T staged per step: 64 bytes of a row (16 floats, 8 doubles) for
+// Y = T x_3 B; 128-byte rows... whole rows of kTF fibers for M^(3).
+template <typename TT>
+struct Stage {
+  static constexpr int kIC = 64 / (int)sizeof(TT);    // i3 per sub-tile in Y = T x_3 B
+  static constexpr int kTF = 128 / (int)sizeof(TT);   // fibers per chunk in M^(3)
+};
+constexpr int kYF = 2 * kThreads;   // fibers per block in Y = T x_3 B
+
 // Y[j][c0 + c] = sum_{i3} T[j][i3] B[i3][c] for the CTA's fibers j, where B
 // is A (I3 x R) or [A | D] (I3 x 2R); Y has row stride ys (AT elements).
-// Lanes own fibers; the factor columns are staged in shared memory (kBsCols
-// at a time) and read as broadcasts, kColW accumulators per lane.
+// Each thread keeps two kColW-column register tiles: fiber t's two column
+// tiles when the staged columns need two (more than kColW), else fibers t and
+// t + kThreads (blocks of kYF fibers).  T arrives in block x kIC sub-tiles,
+// double-buffered by cp.async from every thread, stored with an odd row
+// stride (kIC + 1) so that a warp reading one column of its 32 rows hits 32
+// different banks; the factor columns (kBsCols at a time) are read as
+// broadcasts.
 template <typename TT, typename AT>
-__device__ void pass_y(const TT* __restrict__ T, int J, int I3, int R, const double* __restrict__ A,
-                       const double* __restrict__ D, AT* __restrict__ Y, int ys, int rk, int C, AT* Bs) {
+__device__ __noinline__ void pass_y(const TT* __restrict__ T, int J, int I3, int R, const double* __restrict__ A,
+                                    const double* __restrict__ D, AT* __restrict__ Y, int ys, int rk, int C, AT* Bs,
+                                    TT* Tst) {
+  constexpr int kIC = Stage<TT>::kIC, kLd = kIC + 1;
   const int ncol = D ? 2 * R : R;
   const int jlo = lo_of(J, rk, C), jhi = lo_of(J, rk + 1, C);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nsub = (I3 + kIC - 1) / kIC;
+  TT* const buf1 = Tst + kYF * kLd;
   for (int c0 = 0; c0 < ncol; c0 += kBsCols) {
     const int nc = min(kBsCols, ncol - c0);
     const int ncp = (nc + kColW - 1) / kColW * kColW;
@@ -211,26 +265,81 @@ __device__ void pass_y(const TT* __restrict__ T, int J, int I3, int R, const dou
       Bs[e] = (AT)v;
     }
     __syncthreads();
-    for (int jb = jlo + warp * 32; jb < jhi; jb += kThreads) {
-      const int j = jb + lane;
-      const bool ok = j < jhi;
-      const TT* trow = T + (size_t)(ok ? j : jb) * I3;
-      for (int ct = 0; ct < ncp; ct += kColW) {
-        AT acc[kColW];
-#pragma unroll
-        for (int k = 0; k < kColW; ++k) acc[k] = (AT)0;
-        const AT* b = Bs + ct;
-        for (int i = 0; i < I3; ++i) {
-          const AT t = (AT)__ldg(trow + i);
-#pragma unroll
-          for (int k = 0; k < kColW; ++k) acc[k] = fmat(t, b[k], acc[k]);
-          b += ncp;
+    const bool two = ncp > kColW;            // two column tiles of one fiber
+    const int fb = two ? kThreads : kYF;     // fibers per block
+    for (int jb = jlo; jb < jhi; jb += fb) {
+      const int nrow = min(fb, jhi - jb);
+      auto issue = [&](int sc, TT* dst) {
+        const int i0 = sc * kIC, ni = min(kIC, I3 - i0);
+        for (int e = threadIdx.x; e < fb * kIC; e += kThreads) {
+          const int f = e / kIC, i = e - (e / kIC) * kIC;
+          if (f < nrow && i < ni) cp_async_el(dst + f * kLd + i, T + (size_t)(jb + f) * I3 + i0 + i);
         }
-        if (ok) {
-          AT* yrow = Y + (size_t)j * ys + c0 + ct;
+        cp_async_commit();
+      };
+      AT acc0[kColW], acc1[kColW];
 #pragma unroll
-          for (int k = 0; k < kColW; ++k)
-            if (ct + k < nc) yrow[k] = acc[k];
+      for (int k = 0; k < kColW; ++k) {
+        acc0[k] = (AT)0;
+        acc1[k] = (AT)0;
+      }
+      issue(0, Tst);
+      for (int sc = 0; sc < nsub; ++sc) {
+        if (sc + 1 < nsub) {
+          issue(sc + 1, ((sc + 1) & 1) ? buf1 : Tst);
+          cp_async_wait_one();
+        } else {
+          cp_async_wait_all();
+        }
+        __syncthreads();
+        const int i0 = sc * kIC, ni = min(kIC, I3 - i0);
+        const TT* tbase = ((sc & 1) ? buf1 : Tst) + threadIdx.x * kLd;
+        const AT* b = Bs + (size_t)i0 * ncp;
+        if (two) {
+          for (int i = 0; i < ni; ++i) {
+            const AT t = (AT)tbase[i];
+#pragma unroll
+            for (int k = 0; k < kColW; ++k) {
+              acc0[k] = fmat(t, b[k], acc0[k]);
+              acc1[k] = fmat(t, b[kColW + k], acc1[k]);
+            }
+            b += ncp;
+          }
+        } else {
+          const TT* tb2 = tbase + kThreads * kLd;
+          for (int i = 0; i < ni; ++i) {
+            const AT t0 = (AT)tbase[i], t1 = (AT)tb2[i];
+#pragma unroll
+            for (int k = 0; k < kColW; ++k) {
+              const AT bv = b[k];
+              acc0[k] = fmat(t0, bv, acc0[k]);
+              acc1[k] = fmat(t1, bv, acc1[k]);
+            }
+            b += ncp;
+          }
+        }
+        __syncthreads();   // the buffer is refilled two steps later
+      }
+      const int f0 = threadIdx.x;
+      if (two) {
+        if (f0 < nrow) {
+          AT* yrow = Y + (size_t)(jb + f0) * ys + c0;
+#pragma unroll
+          for (int k = 0; k < kColW; ++k) {
+            if (k < nc) yrow[k] = acc0[k];
+            if (kColW + k < nc) yrow[kColW + k] = acc1[k];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int f = f0 + h * kThreads;
+          if (f < nrow) {
+            AT* yrow = Y + (size_t)(jb + f) * ys + c0;
+#pragma unroll
+            for (int k = 0; k < kColW; ++k)
+              if (k < nc) yrow[k] = h ? acc1[k] : acc0[k];
+          }
         }
       }
     }
@@ -238,81 +347,135 @@ __device__ void pass_y(const TT* __restrict__ T, int J, int I3, int R, const dou
 }
 
 // The CTA's partial of M^(3)(A, B): out[i3][r] = sum_{j in its fibers}
-// T[j][i3] A[j / I2][r] B[j % I2][r] (I3 x R doubles).  Khatri-Rao rows of
-// kFib fibers at a time in shared memory; lanes own i3 (coalesced reads of
-// T), a warp owns one or two (32-row, kColW-column) output tiles and keeps
-// them in FP32/FP64 registers, added into FP64 shared totals every kFlush
-// chunks.
+// T[j][i3] A[j / I2][r] B[j % I2][r] (I3 x R doubles).  T arrives in chunks
+// of kTF whole rows (contiguous in memory), double-buffered by cp.async from
+// every thread; the Khatri-Rao rows of the next chunk are formed (into the
+// other of two shared buffers) from factor entries loaded before the current
+// chunk is processed.  A unit is a 64-row, kColW-column output tile: its
+// lanes own i3 and i3 + 32 (two accumulator rows share every Khatri-Rao
+// read); with u units, kWarps / u warps share a unit and take every
+// (kWarps / u)-th fiber of a chunk.  Register sums are FP32 (or FP64) and
+// are added into FP64 shared totals, one set per fiber group, every kFlush
+// chunks; the groups are added in order at the end.
 template <typename TT, typename AT>
-__device__ void pass_m3(const TT* __restrict__ T, int J, int I2, int I3, int R, const double* __restrict__ A,
-                        const double* __restrict__ B, double* __restrict__ out, int rk, int C, AT* KRs,
+__device__ __noinline__ void pass_m3(const TT* __restrict__ T, int J, int I2, int I3, int R, const double* __restrict__ A,
+                        const double* __restrict__ B, double* __restrict__ out, int rk, int C, TT* Tst, AT* KRs,
                         double* Ms) {
+  constexpr int kTF = Stage<TT>::kTF;
+  constexpr int kKRPer = Stage<float>::kTF * kMaxR / kThreads;   // Khatri-Rao entries per thread
   const int Rp = (R + kColW - 1) / kColW * kColW;
-  const int nib = (I3 + 31) / 32, nct = Rp / kColW;
-  const int units = nib * nct;   // at most 2 kWarps (I3 <= 256, R <= 32)
+  const int nib = (I3 + 63) / 64, nct = Rp / kColW;
+  const int units = nib * nct;   // at most kWarps (I3 <= 256, R <= 32)
+  const int wpu = kWarps / units;
+  const int IR = I3 * R;
   const int jlo = lo_of(J, rk, C), jhi = lo_of(J, rk + 1, C);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int e = threadIdx.x; e < I3 * R; e += kThreads) Ms[e] = 0.0;
-  AT acc[2][kColW];
+  const int grp = warp % wpu;
+  const int unit = warp < units * wpu ? warp / wpu : units;
+  const int ib = unit / nct, ct = unit - (unit / nct) * nct;
+  const int i3a = ib * 64 + lane, i3b = i3a + 32;
+  const bool oka = unit < units && i3a < I3, okb = unit < units && i3b < I3;
+  TT* const buf1 = Tst + kTF * kMaxI;
+  AT* const kr1 = KRs + kTF * kMaxR;
+  for (int e = threadIdx.x; e < wpu * IR; e += kThreads) Ms[e] = 0.0;
+  AT acc0[kColW], acc1[kColW];
 #pragma unroll
-  for (int u = 0; u < 2; ++u)
+  for (int k = 0; k < kColW; ++k) {
+    acc0[k] = (AT)0;
+    acc1[k] = (AT)0;
+  }
+  auto issue = [&](int j0, TT* dst) {
+    const int n = min(kTF, jhi - j0) * I3;
+    const TT* src = T + (size_t)j0 * I3;
+    for (int e = threadIdx.x; e < n; e += kThreads) cp_async_el(dst + e, src + e);
+    cp_async_commit();
+  };
+  double fa[kKRPer], fb[kKRPer];
+  auto load_kr = [&](int j0) {
+    const int nf = min(kTF, jhi - j0);
 #pragma unroll
-    for (int k = 0; k < kColW; ++k) acc[u][k] = (AT)0;
-  int chunks = 0;
-  for (int j0 = jlo; j0 < jhi; j0 += kFib) {
-    const int nf = min(kFib, jhi - j0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < kFib * Rp; e += kThreads) {
+    for (int q = 0; q < kKRPer; ++q) {
+      const int e = threadIdx.x + q * kThreads;
       const int f = e / Rp, r = e - (e / Rp) * Rp;
-      AT v = (AT)0;
+      fa[q] = 0.0;
+      fb[q] = 0.0;
       if (f < nf && r < R) {
         const int j = j0 + f;
         const int i1 = j / I2, i2 = j - (j / I2) * I2;
-        v = (AT)A[(size_t)i1 * R + r] * (AT)B[(size_t)i2 * R + r];
+        fa[q] = A[(size_t)i1 * R + r];
+        fb[q] = B[(size_t)i2 * R + r];
       }
-      KRs[e] = v;
+    }
+  };
+  auto store_kr = [&](AT* dst) {
+#pragma unroll
+    for (int q = 0; q < kKRPer; ++q) {
+      const int e = threadIdx.x + q * kThreads;
+      if (e < kTF * Rp) dst[e] = (AT)fa[q] * (AT)fb[q];
+    }
+  };
+  const int nch = (jhi - jlo + kTF - 1) / kTF;
+  if (nch > 0) {
+    issue(jlo, Tst);
+    load_kr(jlo);
+    store_kr(KRs);
+  }
+  int chunks = 0;
+  for (int c = 0; c < nch; ++c) {
+    const int j0 = jlo + c * kTF;
+    const int nf = min(kTF, jhi - j0);
+    if (c + 1 < nch) {
+      issue(j0 + kTF, ((c + 1) & 1) ? buf1 : Tst);
+      load_kr(j0 + kTF);   // consumed after this chunk's products
+      cp_async_wait_one();
+    } else {
+      cp_async_wait_all();
     }
     __syncthreads();
+    const TT* tb = (c & 1) ? buf1 : Tst;
+    const AT* kb = ((c & 1) ? kr1 : KRs) + ct * kColW;
+    if (unit < units) {
+      const TT* ta = tb + (oka ? i3a : 0);
+      const TT* tb2 = tb + (okb ? i3b : 0);
+      for (int f = grp; f < nf; f += wpu) {
+        const AT t0 = oka ? (AT)ta[f * I3] : (AT)0;
+        const AT t1 = okb ? (AT)tb2[f * I3] : (AT)0;
+        const AT* bf = kb + f * Rp;
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int unit = warp + u * kWarps;
-      if (unit < units) {
-        const int ib = unit / nct, ct = unit - (unit / nct) * nct;
-        const int i3 = ib * 32 + lane;
-        const bool ok = i3 < I3;
-        const TT* tcol = T + (size_t)j0 * I3 + (ok ? i3 : 0);
-        const AT* b = KRs + ct * kColW;
-        for (int f = 0; f < nf; ++f) {
-          const AT t = ok ? (AT)__ldg(tcol + (size_t)f * I3) : (AT)0;
-#pragma unroll
-          for (int k = 0; k < kColW; ++k) acc[u][k] = fmat(t, b[k], acc[u][k]);
-          b += Rp;
+        for (int k = 0; k < kColW; ++k) {
+          const AT bv = bf[k];
+          acc0[k] = fmat(t0, bv, acc0[k]);
+          acc1[k] = fmat(t1, bv, acc1[k]);
         }
       }
     }
-    if (++chunks == kFlush || j0 + kFib >= jhi) {
+    if (c + 1 < nch) store_kr(((c + 1) & 1) ? kr1 : KRs);
+    if (++chunks == kFlush || c + 1 == nch) {
       chunks = 0;
+      if (unit < units) {
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int unit = warp + u * kWarps;
-        if (unit < units) {
-          const int ib = unit / nct, ct = unit - (unit / nct) * nct;
-          const int i3 = ib * 32 + lane;
-          if (i3 < I3) {
-#pragma unroll
-            for (int k = 0; k < kColW; ++k) {
-              const int r = ct * kColW + k;
-              if (r < R) Ms[i3 * R + r] += (double)acc[u][k];
-            }
+        for (int k = 0; k < kColW; ++k) {
+          const int r = ct * kColW + k;
+          if (r < R) {
+            if (oka) Ms[grp * IR + i3a * R + r] += (double)acc0[k];
+            if (okb) Ms[grp * IR + i3b * R + r] += (double)acc1[k];
           }
         }
+      }
 #pragma unroll
-        for (int k = 0; k < kColW; ++k) acc[u][k] = (AT)0;
+      for (int k = 0; k < kColW; ++k) {
+        acc0[k] = (AT)0;
+        acc1[k] = (AT)0;
       }
     }
+    __syncthreads();   // this chunk's buffers are rewritten two chunks on
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < I3 * R; e += kThreads) out[e] = Ms[e];
+  for (int e = threadIdx.x; e < IR; e += kThreads) {
+    double v = 0.0;
+    for (int g = 0; g < wpu; ++g) v += Ms[g * IR + e];
+    out[e] = v;
+  }
 }
 
 // Rows of M^(1) from Y = T x_3 (.): out[i1][r] = sum_{i2} Y[(i1 I2 + i2) ys + c0 + r] B[i2][r]
@@ -421,24 +584,32 @@ __device__ bool spd_inverse(double* A, int R) {
     const double p = A[k * R + k];
     if (!(p > 0.0) || !isfinite(p)) return false;
     const double ip = recip_nr(p);
-    double v[kMaxR * kMaxR / kThreads];
-    int cnt = 0;
-    for (int e = threadIdx.x; e < R * R; e += kThreads) {
-      const int i = e / R, j = e - (e / R) * R;
-      double a = A[e];
-      if (i == k && j == k)
-        a = ip;
-      else if (i == k)
-        a *= ip;
-      else if (j == k)
-        a = -a * ip;
-      else
-        a = fma(-A[i * R + k] * ip, A[k * R + j], a);
-      v[cnt++] = a;
+    constexpr int kPer = kMaxR * kMaxR / kThreads;
+    double v[kPer];
+#pragma unroll
+    for (int c = 0; c < kPer; ++c) {
+      const int e = threadIdx.x + c * kThreads;
+      double a = 0.0;
+      if (e < R * R) {
+        const int i = e / R, j = e - (e / R) * R;
+        a = A[e];
+        if (i == k && j == k)
+          a = ip;
+        else if (i == k)
+          a *= ip;
+        else if (j == k)
+          a = -a * ip;
+        else
+          a = fma(-A[i * R + k] * ip, A[k * R + j], a);
+      }
+      v[c] = a;
     }
     __syncthreads();
-    cnt = 0;
-    for (int e = threadIdx.x; e < R * R; e += kThreads) A[e] = v[cnt++];
+#pragma unroll
+    for (int c = 0; c < kPer; ++c) {
+      const int e = threadIdx.x + c * kThreads;
+      if (e < R * R) A[e] = v[c];
+    }
   }
   __syncthreads();
   return true;
@@ -611,24 +782,34 @@ __device__ __forceinline__ void for_own(const Rows& w, int R, F f) {
   }
 }
 
+// Shared memory of the passes (the large region, 128-byte aligned pieces):
+// Y = T x_3 B: the factor columns (kMaxI x kBsCols) and two staging tiles
+// (256 fibers x 129 bytes... of T); M^(3): two chunks of T rows, the
+// Khatri-Rao rows, the FP64 totals.
+constexpr size_t kBsBytes = (size_t)kMaxI * kBsCols * sizeof(double);
+constexpr size_t kTstBytes = 2 * (size_t)kYF * (Stage<double>::kIC + 1) * sizeof(double) + 256;
+constexpr size_t kTchBytes = 2 * (size_t)Stage<float>::kTF * kMaxI * sizeof(float);
+constexpr size_t kKRBytes = 2 * (size_t)Stage<float>::kTF * kMaxR * sizeof(double);
+
 template <typename AT>
 __device__ void do_pass_y(const ManyReq& q, const double* A, const double* D, int rk, int C, char* big) {
   const int ys = D ? 2 * q.R : q.R;
+  AT* Bs = (AT*)big;
   if (q.t64)
-    pass_y<double, AT>((const double*)q.T, q.J, q.I3, q.R, A, D, (AT*)q.Y, ys, rk, C, (AT*)big);
+    pass_y<double, AT>((const double*)q.T, q.J, q.I3, q.R, A, D, (AT*)q.Y, ys, rk, C, Bs, (double*)(big + kBsBytes));
   else
-    pass_y<float, AT>((const float*)q.T, q.J, q.I3, q.R, A, D, (AT*)q.Y, ys, rk, C, (AT*)big);
+    pass_y<float, AT>((const float*)q.T, q.J, q.I3, q.R, A, D, (AT*)q.Y, ys, rk, C, Bs, (float*)(big + kBsBytes));
 }
 
 template <typename AT>
 __device__ void do_pass_m3(const ManyReq& q, const double* A, const double* B, double* out, int rk, int C,
                            char* big) {
-  AT* KRs = (AT*)big;
-  double* Ms = (double*)(big + kFib * kMaxR * sizeof(double));
+  AT* KRs = (AT*)(big + kTchBytes);
+  double* Ms = (double*)(big + kTchBytes + kKRBytes);
   if (q.t64)
-    pass_m3<double, AT>((const double*)q.T, q.J, q.I2, q.I3, q.R, A, B, out, rk, C, KRs, Ms);
+    pass_m3<double, AT>((const double*)q.T, q.J, q.I2, q.I3, q.R, A, B, out, rk, C, (double*)big, KRs, Ms);
   else
-    pass_m3<float, AT>((const float*)q.T, q.J, q.I2, q.I3, q.R, A, B, out, rk, C, KRs, Ms);
+    pass_m3<float, AT>((const float*)q.T, q.J, q.I2, q.I3, q.R, A, B, out, rk, C, (float*)big, KRs, Ms);
 }
 
 // Gradient rows G^(n) = -M^(n) + A^(n) Gammabar^(n) (Eq. Gn) of the CTA's
@@ -818,15 +999,18 @@ __device__ bool run_start(EngSh& sh, char* big, int rk, int C, unsigned long lon
   if (threadIdx.x == 0) {
     my[SCA + 1] = inner;
     my[SCA + 2] = gpart;
+    sh.c.ysrc = 1;
   }
   return tail(sh, rk, C, T_BEGIN, true, t0, budget);
 }
 
 // The "keep" ends of an iteration: after a restart (reset) or a search that
 // found no acceptable step, u = ubar with its f, g and Grams.
-__device__ bool keep_ubar(EngSh& sh, int rk, int C, bool reset, unsigned long long t0, unsigned long long budget) {
+__device__ bool keep_ubar(EngSh& sh, int rk, int C, bool reset, int ysrc, unsigned long long t0,
+                          unsigned long long budget) {
   const ManyReq& q = sh.q;
   const Rows w = rows_of(q, rk, C);
+  if (threadIdx.x == 0) sh.c.ysrc = ysrc;
   for_own(w, q.R, [&](int e, int, int, int) {
     q.u[e] = q.ub[e];
     q.g[e] = q.gb[e];
@@ -860,11 +1044,17 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
   };
 
   // ---- Step I: the ALS sweep (Section 2.3), modes 1 and 2 from Y = T x_3 A^(3)
-  do_pass_y<AT>(q, u + q.off3, nullptr, rk, C, big);
-  cl_sync();
+  // (kept from the previous iteration when it made u: see ysrc)
+  const int ysrc = sh.c.ysrc;
+  const AT* Ysw = ysrc == 2 ? (const AT*)q.Y2 : (const AT*)q.Y;
+  const int ysw = ysrc == 3 ? 2 * R : R;
+  if (ysrc == 0) {
+    do_pass_y<AT>(q, u + q.off3, nullptr, rk, C, big);
+    cl_sync();
+  }
   hadamard_into(q.Gu + RR, q.Gu + 2 * RR, R, sh.A0);
   if (!gammabar_inverse(R, sh)) return fail_spd();
-  contract_m1<AT>((const AT*)q.Y, R, 0, q.I1, q.I2, R, u + q.off2, q.M1, rk, C);
+  contract_m1<AT>(Ysw, ysw, 0, q.I1, q.I2, R, u + q.off2, q.M1, rk, C);
   als_rows(q.M1, R, w.lo[0], w.hi[0], sw, sh);
   gram_part(sw, sw, w.lo[0], w.hi[0], R, my + BA);
   cl_sync();
@@ -875,7 +1065,7 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
     if (rk == 0) q.Gs[e] = g1;
   }
   if (!gammabar_inverse(R, sh)) return fail_spd();
-  contract_m2<AT>((const AT*)q.Y, R, 0, q.I1, q.I2, R, sw, q.M2, rk, C);
+  contract_m2<AT>(Ysw, ysw, 0, q.I1, q.I2, R, sw, q.M2, rk, C);
   als_rows(q.M2, R, w.lo[1], w.hi[1], sw + q.off2, sh);
   gram_part(sw + q.off2, sw + q.off2, w.lo[1], w.hi[1], R, my + BB);
   cl_sync();
@@ -941,6 +1131,7 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
     double* gt = tile + (size_t)kMaxW * kTileLd;
     double acc[3] = {0.0, 0.0, 0.0};
     int ta[3], tb[3];
+#pragma unroll
     for (int s = 0; s < 3; ++s) {
       const int t = threadIdx.x + s * kThreads;
       ta[s] = -1;
@@ -983,6 +1174,7 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
         }
       }
     }
+#pragma unroll
     for (int s = 0; s < 3; ++s) {
       const int t = threadIdx.x + s * kThreads;
       if (t < ntask) my[BA + t] = t < npairs ? acc[s] : -acc[s];
@@ -1018,6 +1210,7 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
     for_own(w, R, [&](int e, int, int, int) {
       const double b = ub[e];
       double acc = 0.0;
+#pragma unroll 4
       for (int j = 0; j < m; ++j) acc += sh.alpha[j] * (b - q.U[(size_t)ring(wstart, j, q.w) * q.P + e]);
       sw[e] = b + acc;
     });
@@ -1061,7 +1254,8 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
     if (restart) sh.c.restarts += 1;
   }
   __syncthreads();
-  if (restart) return keep_ubar(sh, rk, C, true, t0, budget);   // R7
+  // (after a restart the Y buffer still holds Y' = T x_3 Abar^(3))
+  if (restart) return keep_ubar(sh, rk, C, true, 1, t0, budget);   // R7
 
   // ---- Step III: the line polynomial phi(beta) = f(ubar + beta d)
   if (rk == 0)
@@ -1074,17 +1268,23 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
   contract_variants<AT>((const AT*)q.Y, q.I1, q.I2, R, ub, q.d, ub + q.off2, q.d + q.off2, q.V1, q.V2, rk, C);
   __syncthreads();
   // <T, [[A_a, B_b, C_c]]> partials: sum over the CTA's rows of mode 1 of A_a V1[2c + b]
-  for (int k8 = 0; k8 < 8; ++k8) {
-    const int a = k8 >> 2, v = k8 & 3;
-    const double* F = a ? q.d : ub;
-    const double* V = q.V1 + (size_t)v * q.I1 * R;
-    double s8 = 0.0;
+  {
+    double s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const size_t st1 = (size_t)q.I1 * R;
     for (int k = threadIdx.x; k < (w.hi[0] - w.lo[0]) * R; k += kThreads) {
       const int e = w.lo[0] * R + k;
-      s8 = fma(F[e], V[e], s8);
+      const double fa = ub[e], fd = q.d[e];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const double m = q.V1[v * st1 + e];
+        s8[v] = fma(fa, m, s8[v]);
+        s8[4 + v] = fma(fd, m, s8[4 + v]);
+      }
     }
-    s8 = cta_sum(s8, sh);
-    if (threadIdx.x == 0) my[SCB + k8] = s8;
+    cta_sums<8>(s8, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) my[SCB + k] = s8[k];
   }
   cl_sync();
   if (rk == 0) {
@@ -1092,27 +1292,32 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
     double e7[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int e = threadIdx.x; e < RR; e += kThreads) {
       const int r = e / R, s2 = e - (e / R) * R;
-      double pc[7] = {1, 0, 0, 0, 0, 0, 0};
-      int deg = 0;
+      double qd[3][3];
+#pragma unroll
       for (int n = 0; n < 3; ++n) {
-        const double a0 = q.Gb[(size_t)n * RR + e];
-        const double a1 = q.Gad[(size_t)n * RR + e] + q.Gad[(size_t)n * RR + s2 * R + r];
-        const double a2 = q.Gdd[(size_t)n * RR + e];
-        double nx[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int k = 0; k <= deg; ++k) {
-          nx[k] = fma(pc[k], a0, nx[k]);
-          nx[k + 1] = fma(pc[k], a1, nx[k + 1]);
-          nx[k + 2] = fma(pc[k], a2, nx[k + 2]);
-        }
-        deg += 2;
-        for (int k = 0; k < 7; ++k) pc[k] = nx[k];
+        qd[n][0] = q.Gb[(size_t)n * RR + e];
+        qd[n][1] = q.Gad[(size_t)n * RR + e] + q.Gad[(size_t)n * RR + s2 * R + r];
+        qd[n][2] = q.Gdd[(size_t)n * RR + e];
       }
-      for (int k = 0; k < 7; ++k) e7[k] += pc[k];
+      // the product of the three quadratics, coefficient by coefficient
+      double p4[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) p4[i + j] = fma(qd[0][i], qd[1][j], p4[i + j]);
+      double p6[7] = {0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) p6[i + j] = fma(p4[i], qd[2][j], p6[i + j]);
+#pragma unroll
+      for (int k = 0; k < 7; ++k) e7[k] += p6[k];
     }
-    for (int k = 0; k < 7; ++k) e7[k] = cta_sum(e7[k], sh);
+    cta_sums<7>(e7, sh);
     if (threadIdx.x == 0) {
       double poly[7];
       for (int k = 0; k < 7; ++k) poly[k] = 0.5 * e7[k];
+#pragma unroll
       for (int k8 = 0; k8 < 8; ++k8) {
         const int a = k8 >> 2, v = k8 & 3;
         const int b = v & 1, c = v >> 1;
@@ -1162,7 +1367,8 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
     }
   }
   __syncthreads();
-  if (!accept) return keep_ubar(sh, rk, C, false, t0, budget);   // R10
+  // (Z's first R columns are T x_3 Abar^(3))
+  if (!accept) return keep_ubar(sh, rk, C, false, 3, t0, budget);   // R10
 
   // ---- the accepted point x = ubar + beta d: M^(1), M^(2) from the variants
   for_own(w, R, [&](int e, int, int, int) { q.x[e] = fma(beta, q.d[e], ub[e]); });
@@ -1204,7 +1410,22 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
     q.g[e] = sw[src] / sc;
   });
   if (rk == 0) grams_normalised(q.Gx, R, sh.scale, sh.order, q.Gu);
+  // the next sweep's Y = T x_3 A^(3)(u): u's A^(3) is x's, scaled and
+  // reordered, and T x_3 x^(3) = Z_ubar + beta Z_d (the line-search pass)
+  {
+    const int jlo = lo_of(q.J, rk, C), jhi = lo_of(q.J, rk + 1, C);
+    const AT* Z = (const AT*)q.Y;
+    AT* Y2 = (AT*)q.Y2;
+    const AT b = (AT)beta;
+    for (int k = threadIdx.x; k < (jhi - jlo) * R; k += kThreads) {
+      const int j = jlo + k / R, p = k - (k / R) * R;
+      const int o = sh.order[p];
+      const AT* z = Z + (size_t)j * 2 * R;
+      Y2[(size_t)j * R + p] = fmat(b, z[R + o], z[o]) * (AT)sh.scale[2 * R + o];
+    }
+  }
   __syncthreads();
+  if (threadIdx.x == 0) sh.c.ysrc = 2;
   const double gpart = cta_sum(window_push(q, w, q.u, q.g, push_slot(sh.c, q.w, false)), sh);
   if (threadIdx.x == 0) {
     my[SCA + 1] = inner;
@@ -1263,9 +1484,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-size_t engine_smem(int I3max, int IRmax) {
-  size_t bigb = std::max<size_t>((size_t)I3max * kBsCols * sizeof(double),
-                                 (size_t)kFib * kMaxR * sizeof(double) + (size_t)IRmax * sizeof(double));
+size_t engine_smem() {
+  size_t bigb = std::max<size_t>(kBsBytes + kTstBytes, kTchBytes + kKRBytes + (size_t)kMaxIR * sizeof(double));
   bigb = std::max<size_t>(bigb, ((size_t)kMaxW * kTileLd + kTile) * sizeof(double));
   return (sizeof(EngSh) + 127) / 128 * 128 + bigb;
 }
@@ -1280,16 +1500,8 @@ namespace cpg {
 namespace {
 
 constexpr int kStallDefault = 800;
-
-struct ManyJob {
-  ManyReq q{};
-  void* mem = nullptr;
-  int C = 1;
-  bool done = false;
-  const cp_tensor* t = nullptr;
-  std::chrono::steady_clock::time_point t0;
-  double t_done = 0.0;
-};
+constexpr int kProbeIters = 6;        // iterations a tuning probe runs
+constexpr int kGroups = 4;            // cluster sizes 1, 2, 4, 8
 
 int64_t big_ld_of(int I3, int R) {
   int64_t b = std::max<int64_t>((int64_t)I3 * R, 6 * (int64_t)R * R);
@@ -1318,6 +1530,7 @@ size_t job_layout(ManyReq& q, char* base) {
   q.U = take((int64_t)q.w * P);
   q.G = take((int64_t)q.w * P);
   q.Y = take((int64_t)q.J * 2 * R);
+  q.Y2 = take((int64_t)q.J * R);
   q.M1 = take(q.I1 * R);
   q.M2 = take(q.I2 * R);
   q.M3 = take(q.I3 * R);
@@ -1337,29 +1550,498 @@ size_t job_layout(ManyReq& q, char* base) {
   return n * sizeof(double);
 }
 
-// Cluster size for a request of K entries and rank R, before tuning.
-int default_cluster(int64_t K, int R) {
-  const int64_t work = K * (int64_t)std::max(R, 8);
-  if (work < ((int64_t)1 << 20)) return 1;
-  if (work < ((int64_t)1 << 22)) return 2;
-  if (work < ((int64_t)1 << 24)) return 4;
-  return 8;
+void fill_req(ManyReq& q, const cp_tensor* t, const cp_solve_opts& o) {
+  q = ManyReq{};
+  q.T = t->Tn[0];
+  q.t64 = t->dtype == CP_DTYPE_F64 ? 1 : 0;
+  q.I1 = (int)t->dims[0];
+  q.I2 = (int)t->dims[1];
+  q.I3 = (int)t->dims[2];
+  q.J = q.I1 * q.I2;
+  q.R = o.R;
+  q.P = (q.I1 + q.I2 + q.I3) * o.R;
+  q.off2 = q.I1 * o.R;
+  q.off3 = (q.I1 + q.I2) * o.R;
+  q.normT2 = t->norm2;
+  q.tol = o.tol;
+  q.tol_mixed = o.tol * (o.mixed_tol_factor > 0.0 ? o.mixed_tol_factor : 1.0);
+  q.eps = o.eps;
+  q.maxit = o.maxit;
+  q.w = o.w;
+  q.polish = o.polish ? 1 : 0;
+  q.stall = o.mixed_stall > 0 ? o.mixed_stall : kStallDefault;
+  q.ls = o.ls;
+  q.ls_mixed = o.ls;
+  if (o.mixed_maxfev > 0 && o.mixed_maxfev < o.ls.maxfev) q.ls_mixed.maxfev = o.mixed_maxfev;
+}
+
+ManyCtl initial_ctl(const cp_solve_opts& o) {
+  ManyCtl c{};
+  c.phase = o.prec == CP_FP64 ? PH_FP64 : PH_MIXED;
+  c.start = 2;
+  c.best = INFINITY;
+  c.status = CP_OK;
+  return c;
+}
+
+// Cluster sizes chosen by the tuner, per (device, ceil log2 entries,
+// ceil log2 R, precision) bucket; shared by every context of the process.
+struct TuneKey {
+  int dev, lk, lr, prec;
+  bool operator<(const TuneKey& o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (lk != o.lk) return lk < o.lk;
+    if (lr != o.lr) return lr < o.lr;
+    return prec < o.prec;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+
+int ceil_log2(int64_t v) {
+  int l = 0;
+  while (((int64_t)1 << l) < v) ++l;
+  return l;
+}
+
+TuneKey tune_key(int dev, const cp_tensor* t, const cp_solve_opts& o) {
+  return TuneKey{dev, ceil_log2(t->K), ceil_log2(o.R), o.prec == CP_FP64 ? 0 : 1};
 }
 
 }  // namespace
 
-// Why a request cannot run on the cluster engine (nullptr when it can).
-const char* many_unsupported(const cp_tensor* t, const cp_solve_opts& o) {
-  if (!t || t->kind != 0 || t->N != 3) return "the engine takes 3-way dense tensors";
+// Why a request cannot run on the engine (nullptr when it can).
+const char* many_unsupported_dims(int kind, int N, const int64_t* dims, const cp_solve_opts& o) {
+  if (kind != 0 || N != 3) return "the engine takes 3-way dense tensors";
   if (o.R < 1 || o.R > kMaxR) return "rank above 32";
   if (o.w < 1 || o.w > kMaxW) return "window above 32";
   for (int n = 0; n < 3; ++n) {
-    if (t->dims[n] < 1 || t->dims[n] > kMaxI) return "a side above 256";
-    if (t->dims[n] * o.R > kMaxIR) return "I_n R above 8192";
+    if (dims[n] < 1 || dims[n] > kMaxI) return "a side above 256";
+    if (dims[n] * o.R > kMaxIR) return "I_n R above 8192";
   }
-  if (t->dims[0] * t->dims[1] > (int64_t)1 << 30) return "too many fibers";
   return nullptr;
 }
+
+const char* many_unsupported(const cp_tensor* t, const cp_solve_opts& o) {
+  if (!t) return "no tensor";
+  return many_unsupported_dims(t->kind, t->N, t->dims, o);
+}
+
+// Device bytes of one request's engine state.
+size_t many_state_bytes(const int64_t* dims, const cp_solve_opts& o) {
+  ManyReq q{};
+  q.I1 = (int)dims[0];
+  q.I2 = (int)dims[1];
+  q.I3 = (int)dims[2];
+  q.J = q.I1 * q.I2;
+  q.R = o.R;
+  q.P = (q.I1 + q.I2 + q.I3) * o.R;
+  q.w = o.w;
+  return job_layout(q, nullptr) + 4096;
+}
+
+// The engine: request states, the device descriptor table, the launch
+// rounds.  Not thread-safe (one owner thread).
+struct ManyEngine {
+  struct Job {
+    bool used = false, running = false;
+    bool in_round = false;             // launched in the round in flight
+    ManyReq q{};
+    void* mem = nullptr;
+    int C = 1;
+    const cp_tensor* t = nullptr;
+    int iters = 0;
+  };
+  cp_ctx* ctx = nullptr;
+  int cap = 0;
+  int maxcl[kGroups] = {0, 0, 0, 0};
+  size_t smem = 0;
+  cudaStream_t es = nullptr;
+  cudaStream_t gs[kGroups] = {};
+  cudaEvent_t fork = nullptr, join[kGroups] = {}, round_ev = nullptr, pa = nullptr, pb = nullptr;
+  ManyReq* req_d = nullptr;          // cap + 1 descriptors (the last one for tuning probes)
+  ManyCtl* ctl_d = nullptr;          // cap + 1
+  char* qbuf_d = nullptr;
+  size_t qstride = 0;
+  ManyCtl* ctl_h = nullptr;          // pinned: control blocks read back after a round
+  ManyCtl* ctl_up = nullptr;         // pinned: initial control blocks to upload
+  int* tasks_h = nullptr;            // pinned, kGroups x cap
+  ManyQueue* q_h = nullptr;          // pinned, kGroups
+  std::vector<Job> jobs;
+  bool in_flight = false;
+  int launched_rounds = 0;
+
+  ~ManyEngine() { destroy(); }
+
+  cp_status create(cp_ctx* c, int capacity) {
+    ctx = c;
+    cap = std::max(1, capacity);
+    smem = engine_smem();
+    CP_CUDA(cudaSetDevice(ctx->device));
+    CP_CUDA(cudaFuncSetAttribute(many_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CP_CUDA(cudaStreamCreateWithFlags(&es, cudaStreamNonBlocking));
+    for (int k = 0; k < kGroups; ++k) {
+      CP_CUDA(cudaStreamCreateWithFlags(&gs[k], cudaStreamNonBlocking));
+      CP_CUDA(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming));
+    }
+    CP_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    CP_CUDA(cudaEventCreateWithFlags(&round_ev, cudaEventDisableTiming));
+    CP_CUDA(cudaEventCreate(&pa));
+    CP_CUDA(cudaEventCreate(&pb));
+    for (int k = 0; k < kGroups; ++k) {
+      const int C = 1 << k;
+      cudaLaunchConfig_t cfg{};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)C);
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, many_kernel, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        n = 0;
+      }
+      maxcl[k] = n;
+    }
+    if (maxcl[0] < 1) {
+      set_error("cp_solve_many: the engine kernel cannot be resident");
+      return CP_ERR_CUDA;
+    }
+    const int mx = std::max({maxcl[0], maxcl[1], maxcl[2], maxcl[3], 1});
+    qstride = (sizeof(ManyQueue) + 64 + (size_t)(cap + 1 + mx) * sizeof(int) + 255) / 256 * 256;
+    CP_CUDA(cudaMallocAsync((void**)&req_d, sizeof(ManyReq) * (cap + 1), es));
+    CP_CUDA(cudaMallocAsync((void**)&ctl_d, sizeof(ManyCtl) * (cap + 1), es));
+    CP_CUDA(cudaMallocAsync((void**)&qbuf_d, qstride * (kGroups + 1), es));
+    CP_CUDA(cudaMallocHost((void**)&ctl_h, sizeof(ManyCtl) * (cap + 1)));
+    CP_CUDA(cudaMallocHost((void**)&ctl_up, sizeof(ManyCtl) * (cap + 1)));
+    CP_CUDA(cudaMallocHost((void**)&tasks_h, sizeof(int) * (size_t)(kGroups + 1) * (cap + 1)));
+    CP_CUDA(cudaMallocHost((void**)&q_h, sizeof(ManyQueue) * (kGroups + 1)));
+    jobs.resize((size_t)cap);
+    return CP_OK;
+  }
+
+  void destroy() {
+    if (es) cudaStreamSynchronize(es);
+    for (auto& j : jobs)
+      if (j.mem) cudaFreeAsync(j.mem, es);
+    jobs.clear();
+    if (req_d) cudaFreeAsync(req_d, es);
+    if (ctl_d) cudaFreeAsync(ctl_d, es);
+    if (qbuf_d) cudaFreeAsync(qbuf_d, es);
+    req_d = nullptr;
+    ctl_d = nullptr;
+    qbuf_d = nullptr;
+    if (es) cudaStreamSynchronize(es);
+    if (ctl_h) cudaFreeHost(ctl_h);
+    if (ctl_up) cudaFreeHost(ctl_up);
+    ctl_up = nullptr;
+    if (tasks_h) cudaFreeHost(tasks_h);
+    if (q_h) cudaFreeHost(q_h);
+    ctl_h = nullptr;
+    tasks_h = nullptr;
+    q_h = nullptr;
+    for (int k = 0; k < kGroups; ++k) {
+      if (gs[k]) cudaStreamDestroy(gs[k]);
+      if (join[k]) cudaEventDestroy(join[k]);
+      gs[k] = nullptr;
+      join[k] = nullptr;
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (round_ev) cudaEventDestroy(round_ev);
+    if (pa) cudaEventDestroy(pa);
+    if (pb) cudaEventDestroy(pb);
+    fork = round_ev = pa = pb = nullptr;
+    if (es) cudaStreamDestroy(es);
+    es = nullptr;
+  }
+
+  // One launch of cluster size C over ntasks requests (tasks_h + group
+  // offset already filled) on stream s, queue block g.
+  cp_status launch(int g, int C, int ntasks, unsigned long long budget_ns, cudaStream_t s) {
+    char* qb = qbuf_d + (size_t)g * qstride;
+    ManyQueue* qd = (ManyQueue*)qb;
+    int* tasks_d = (int*)(qb + sizeof(ManyQueue) + 64);
+    int* ctask_d = tasks_d + cap + 1;
+    q_h[g] = ManyQueue{0, ntasks, budget_ns};
+    const int k = C == 1 ? 0 : C == 2 ? 1 : C == 4 ? 2 : 3;
+    const int nclusters = std::min(maxcl[k], ntasks);
+    if (nclusters < 1) {
+      set_error("cp_solve_many: clusters of %d CTAs cannot be resident", C);
+      return CP_ERR_CUDA;
+    }
+    CP_CUDA(cudaMemcpyAsync(qd, &q_h[g], sizeof(ManyQueue), cudaMemcpyHostToDevice, s));
+    CP_CUDA(cudaMemcpyAsync(tasks_d, tasks_h + (size_t)g * (cap + 1), sizeof(int) * ntasks, cudaMemcpyHostToDevice, s));
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(nclusters * C));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CP_CUDA(cudaLaunchKernelEx(&cfg, many_kernel, (const ManyReq*)req_d, (const int*)tasks_d, qd, ctask_d));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return CP_OK;
+  }
+
+  // Cluster size for a request: the tuned one for its bucket.  The first
+  // request of a bucket times kProbeIters iterations of itself with each
+  // cluster size (scratch state, descriptor slot cap); among the sizes whose
+  // time is within 1.5x of the fastest, the one with the least SM time
+  // (C x elapsed) is kept: the fewest CTAs that do not stretch the
+  // request's latency by more than half.
+  cp_status tuned_cluster(const cp_tensor* t, const cp_solve_opts& o, const double* u0, int* out) {
+    const TuneKey key = tune_key(ctx->device, t, o);
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) {
+        *out = it->second;
+        return CP_OK;
+      }
+    }
+    ManyReq q;
+    fill_req(q, t, o);
+    q.maxit = std::min(o.maxit, kProbeIters);
+    q.tol = 0.0;
+    q.tol_mixed = 0.0;
+    void* mem = nullptr;
+    CP_CUDA(cudaMallocAsync(&mem, job_layout(q, nullptr), es));
+    (void)job_layout(q, (char*)mem);
+    q.ctl = ctl_d + cap;
+    const ManyCtl c0 = initial_ctl(o);
+    double best = INFINITY;
+    int bestC = 1;
+    double tms[kGroups] = {INFINITY, INFINITY, INFINITY, INFINITY};
+    cp_status st = CP_OK;
+    for (int pass = 0; pass < 2 && st == CP_OK; ++pass) {
+      for (int k = 0; k < kGroups && st == CP_OK; ++k) {
+        const int C = 1 << k;
+        if (maxcl[k] < 1 || (pass == 0 && k > 0)) continue;   // pass 0: one warm-up launch
+        // the probe uses descriptor and control slot cap and queue block kGroups
+        ctl_up[cap] = c0;
+        char* qb = qbuf_d + (size_t)kGroups * qstride;
+        ManyQueue* qd = (ManyQueue*)qb;
+        int* tasks_d = (int*)(qb + sizeof(ManyQueue) + 64);
+        int* ctask_d = tasks_d + cap + 1;
+        q_h[kGroups] = ManyQueue{0, 1, ~0ull >> 1};
+        tasks_h[(size_t)kGroups * (cap + 1)] = cap;
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)C);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = es;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaMemcpyAsync(q.ctl, &ctl_up[cap], sizeof(ManyCtl), cudaMemcpyHostToDevice, es);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(req_d + cap, &q, sizeof(ManyReq), cudaMemcpyHostToDevice, es);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(q.x, u0, sizeof(double) * q.P, cudaMemcpyDefault, es);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(qd, &q_h[kGroups], sizeof(ManyQueue), cudaMemcpyHostToDevice, es);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(tasks_d, tasks_h + (size_t)kGroups * (cap + 1), sizeof(int), cudaMemcpyHostToDevice, es);
+        if (e == cudaSuccess) e = cudaEventRecord(pa, es);
+        if (e == cudaSuccess)
+          e = cudaLaunchKernelEx(&cfg, many_kernel, (const ManyReq*)req_d, (const int*)tasks_d, qd, ctask_d);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (e == cudaSuccess) e = cudaEventRecord(pb, es);
+        if (e == cudaSuccess) e = cudaEventSynchronize(pb);
+        if (e != cudaSuccess) {
+          st = cuda_fail(e, "cp_solve_many: tuning probe", __FILE__, __LINE__);
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, pa, pb);
+        if (pass == 1) tms[k] = ms;
+      }
+    }
+    cudaFreeAsync(mem, es);
+    if (st != CP_OK) return st;
+    double tmin = INFINITY;
+    for (int k = 0; k < kGroups; ++k) tmin = std::min(tmin, tms[k]);
+    for (int k = 0; k < kGroups; ++k) {
+      const int C = 1 << k;
+      if (tms[k] <= 1.5 * tmin && (double)C * tms[k] < best) {
+        best = (double)C * tms[k];
+        bestC = C;
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune[key] = bestC;
+    }
+    *out = bestC;
+    return CP_OK;
+  }
+
+  // Admit a request (its tensor complete on the device).  cluster: 1, 2, 4,
+  // 8, or 0 for the tuned size.
+  cp_status add(const cp_tensor* t, const cp_solve_opts& o, const double* u0, int cluster, int* slot) {
+    int k = -1;
+    for (int i = 0; i < cap; ++i)
+      if (!jobs[i].used) {
+        k = i;
+        break;
+      }
+    if (k < 0) {
+      set_error("cp_solve_many: engine full");
+      return CP_ERR_BUSY;
+    }
+    int C = cluster;
+    if (C == 0) CP_TRY(tuned_cluster(t, o, u0, &C));
+    Job& j = jobs[k];
+    fill_req(j.q, t, o);
+    void* mem = nullptr;
+    CP_CUDA(cudaMallocAsync(&mem, job_layout(j.q, nullptr), es));
+    (void)job_layout(j.q, (char*)mem);
+    j.q.ctl = ctl_d + k;
+    j.mem = mem;
+    j.C = C;
+    j.t = t;
+    j.used = true;
+    j.running = true;
+    j.iters = 0;
+    // (ctl_h belongs to the round read-back, which may still be in flight)
+    ctl_up[k] = initial_ctl(o);
+    CP_CUDA(cudaMemcpyAsync(j.q.x, u0, sizeof(double) * j.q.P, cudaMemcpyDefault, es));
+    CP_CUDA(cudaMemcpyAsync(ctl_d + k, &ctl_up[k], sizeof(ManyCtl), cudaMemcpyHostToDevice, es));
+    CP_CUDA(cudaMemcpyAsync(req_d + k, &j.q, sizeof(ManyReq), cudaMemcpyHostToDevice, es));
+    // pageable sources above: the copies have been taken before they return
+    *slot = k;
+    return CP_OK;
+  }
+
+  int running() const {
+    int n = 0;
+    for (const auto& j : jobs) n += j.running ? 1 : 0;
+    return n;
+  }
+
+  // Enqueue one round: every running request, grouped by cluster size, one
+  // launch per group on its own stream (least iterations first), then the
+  // control blocks back to the host.  Non-blocking.
+  cp_status launch_round(unsigned long long budget_ns) {
+    CP_CUDA(cudaEventRecord(fork, es));
+    for (int g = 0; g < kGroups; ++g) {
+      const int C = 1 << g;
+      std::vector<int> ids;
+      for (int i = 0; i < cap; ++i)
+        if (jobs[i].running && jobs[i].C == C) ids.push_back(i);
+      if (ids.empty()) continue;
+      std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return jobs[a].iters < jobs[b].iters; });
+      for (int i : ids) jobs[i].in_round = true;
+      std::copy(ids.begin(), ids.end(), tasks_h + (size_t)g * (cap + 1));
+      CP_CUDA(cudaStreamWaitEvent(gs[g], fork, 0));
+      CP_TRY(launch(g, C, (int)ids.size(), budget_ns, gs[g]));
+      CP_CUDA(cudaEventRecord(join[g], gs[g]));
+      CP_CUDA(cudaStreamWaitEvent(es, join[g], 0));
+    }
+    CP_CUDA(cudaMemcpyAsync(ctl_h, ctl_d, sizeof(ManyCtl) * cap, cudaMemcpyDeviceToHost, es));
+    CP_CUDA(cudaEventRecord(round_ev, es));
+    in_flight = true;
+    ++launched_rounds;
+    return CP_OK;
+  }
+
+  // After a round: true when it has finished; `finished` receives the
+  // requests that are done.
+  cp_status poll(bool block, bool* idle, std::vector<int>* finished) {
+    *idle = true;
+    if (!in_flight) return CP_OK;
+    const cudaError_t e = block ? cudaEventSynchronize(round_ev) : cudaEventQuery(round_ev);
+    if (e == cudaErrorNotReady) {
+      *idle = false;
+      return CP_OK;
+    }
+    in_flight = false;
+    if (e != cudaSuccess) return cuda_fail(e, "cp_solve_many: engine round", __FILE__, __LINE__);
+    for (int i = 0; i < cap; ++i) {
+      Job& j = jobs[i];
+      if (!j.running || !j.in_round) continue;   // admitted after the round was launched
+      j.in_round = false;
+      j.iters = ctl_h[i].iters;
+      if (ctl_h[i].phase == PH_DONE) {
+        j.running = false;
+        if (finished) finished->push_back(i);
+      }
+    }
+    return CP_OK;
+  }
+
+  // Result of a finished request: u (host or device), report, status.
+  cp_status result(int k, double* u_out, cp_solve_report* rep, cp_status* status) {
+    const Job& j = jobs[k];
+    const ManyCtl& c = ctl_h[k];
+    CP_CUDA(cudaMemcpyAsync(u_out, j.q.u, sizeof(double) * j.q.P, cudaMemcpyDefault, es));
+    CP_CUDA(cudaStreamSynchronize(es));
+    if (rep) {
+      cp_solve_report r{};
+      r.iters = c.iters;
+      r.fg_evals = c.fg_evals;
+      r.als_sweeps = c.als_sweeps;
+      r.restarts = c.restarts;
+      r.ls_failures = c.ls_failures;
+      r.converged = (c.stop == STOP_TOL && c.status == CP_OK) ? 1 : 0;
+      r.mixed_iters = c.mixed_iters;
+      r.fp64_iters = c.fp64_iters;
+      r.f = c.f;
+      r.gnorm_over_P = c.gn;
+      r.normT2 = j.t->norm2;
+      r.ls_trials = c.ls_trials;
+      *rep = r;
+    }
+    cp_status st = (cp_status)c.status;
+    if (st == CP_OK && c.stop != STOP_TOL) st = CP_ERR_MAXIT;
+    if (status) *status = st;
+    return CP_OK;
+  }
+
+  void release(int k) {
+    Job& j = jobs[k];
+    if (j.mem) cudaFreeAsync(j.mem, es);
+    j = Job();
+  }
+};
+
+ManyEngine* many_engine_create(cp_ctx* ctx, int capacity, cp_status* st) {
+  ManyEngine* e = new ManyEngine();
+  *st = e->create(ctx, capacity);
+  if (*st != CP_OK) {
+    delete e;
+    return nullptr;
+  }
+  return e;
+}
+void many_engine_destroy(ManyEngine* e) { delete e; }
+cp_status many_engine_add(ManyEngine* e, const cp_tensor* t, const cp_solve_opts& o, const double* u0, int* slot) {
+  return e->add(t, o, u0, 0, slot);
+}
+cudaStream_t many_engine_stream(ManyEngine* e) { return e->es; }
+int many_engine_running(ManyEngine* e) { return e->running(); }
+bool many_engine_in_flight(ManyEngine* e) { return e->in_flight; }
+cp_status many_engine_launch(ManyEngine* e, double budget_s) {
+  return e->launch_round((unsigned long long)(budget_s * 1e9));
+}
+cp_status many_engine_poll(ManyEngine* e, bool block, bool* idle, std::vector<int>* finished) {
+  return e->poll(block, idle, finished);
+}
+cp_status many_engine_result(ManyEngine* e, int slot, double* u_out, cp_solve_report* rep, cp_status* st) {
+  return e->result(slot, u_out, rep, st);
+}
+void many_engine_release(ManyEngine* e, int slot) { e->release(slot); }
 
 cp_status many_solve(cp_ctx* ctx, int nreq, const cp_tensor* const* ts, const cp_solve_opts* opts,
                      double* const* u, cp_solve_report* reps, int cluster) {
@@ -1370,7 +2052,6 @@ cp_status many_solve(cp_ctx* ctx, int nreq, const cp_tensor* const* ts, const cp
   }
   if (nreq == 0) return CP_OK;
   CP_CUDA(cudaSetDevice(ctx->device));
-  CP_CUDA(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < nreq; ++i) {
     if (!ts[i] || !u[i] || ts[i]->device != ctx->device) {
       set_error("cp_solve_many: request %d: null tensor or iterate, or tensor on another device", i);
@@ -1387,190 +2068,62 @@ cp_status many_solve(cp_ctx* ctx, int nreq, const cp_tensor* const* ts, const cp
       return CP_ERR_ARG;
     }
   }
-  cudaStream_t s = ctx->stream;
-  std::vector<ManyJob> jobs((size_t)nreq);
-  size_t total = 0;
-  std::vector<size_t> at((size_t)nreq);
-  int I3max = 1, IRmax = 1;
-  for (int i = 0; i < nreq; ++i) {
-    const cp_tensor* t = ts[i];
-    const cp_solve_opts& o = opts[i];
-    ManyReq& q = jobs[i].q;
-    q.T = t->Tn[0];
-    q.t64 = t->dtype == CP_DTYPE_F64 ? 1 : 0;
-    q.I1 = (int)t->dims[0];
-    q.I2 = (int)t->dims[1];
-    q.I3 = (int)t->dims[2];
-    q.J = q.I1 * q.I2;
-    q.R = o.R;
-    q.P = (q.I1 + q.I2 + q.I3) * o.R;
-    q.off2 = q.I1 * o.R;
-    q.off3 = (q.I1 + q.I2) * o.R;
-    q.normT2 = t->norm2;
-    q.tol = o.tol;
-    q.tol_mixed = o.tol * (o.mixed_tol_factor > 0.0 ? o.mixed_tol_factor : 1.0);
-    q.eps = o.eps;
-    q.maxit = o.maxit;
-    q.w = o.w;
-    q.polish = o.polish ? 1 : 0;
-    q.stall = o.mixed_stall > 0 ? o.mixed_stall : kStallDefault;
-    q.ls = o.ls;
-    q.ls_mixed = o.ls;
-    if (o.mixed_maxfev > 0 && o.mixed_maxfev < o.ls.maxfev) q.ls_mixed.maxfev = o.mixed_maxfev;
-    at[i] = total;
-    total += (job_layout(q, nullptr) + 255) / 256 * 256;
-    jobs[i].t = t;
-    jobs[i].C = cluster ? cluster : default_cluster(t->K, o.R);
-    I3max = std::max(I3max, q.I3);
-    for (int n = 0; n < 3; ++n) IRmax = std::max<int>(IRmax, (int)t->dims[n] * o.R);
-  }
-  // one allocation: request states, descriptors, control blocks, queues
-  const size_t ctl_off = total;
-  total += ((size_t)nreq * sizeof(ManyCtl) + 255) / 256 * 256;
-  const size_t req_off = total;
-  total += ((size_t)nreq * sizeof(ManyReq) + 255) / 256 * 256;
-  const size_t q_off = total;
-  int maxclusters = 2 * ctx->num_sms;
-  total += 4 * ((sizeof(ManyQueue) + 64 + (size_t)(nreq + maxclusters) * sizeof(int) + 255) / 256 * 256);
-  char* base = nullptr;
-  CP_CUDA(cudaMallocAsync((void**)&base, total, s));
-  ManyCtl* ctl_d = (ManyCtl*)(base + ctl_off);
-  ManyReq* req_d = (ManyReq*)(base + req_off);
-  std::vector<ManyCtl> ctl_h((size_t)nreq);
+  CP_CUDA(cudaStreamSynchronize(ctx->stream));   // the tensors are complete
   const auto t0 = std::chrono::steady_clock::now();
+  ManyEngine e;
+  CP_TRY(e.create(ctx, nreq));
+  std::vector<int> slot((size_t)nreq, -1);
+  std::vector<double> t_done((size_t)nreq, 0.0);
   cp_status st = CP_OK;
-  for (int i = 0; i < nreq; ++i) {
-    ManyReq& q = jobs[i].q;
-    (void)job_layout(q, base + at[i]);
-    q.ctl = ctl_d + i;
-    ManyCtl c{};
-    c.phase = opts[i].prec == CP_FP64 ? PH_FP64 : PH_MIXED;
-    c.start = 2;
-    c.best = INFINITY;
-    c.status = CP_OK;
-    ctl_h[i] = c;
-    jobs[i].t0 = t0;
-    if (st == CP_OK) {
-      const cudaError_t e = cudaMemcpyAsync(q.x, u[i], sizeof(double) * q.P, cudaMemcpyDefault, s);
-      if (e != cudaSuccess) st = cuda_fail(e, "cp_solve_many: initial guess", __FILE__, __LINE__);
-    }
-  }
-  std::vector<ManyReq> req_h((size_t)nreq);
-  for (int i = 0; i < nreq; ++i) req_h[i] = jobs[i].q;
-  if (st == CP_OK) {
-    const cudaError_t e1 = cudaMemcpyAsync(req_d, req_h.data(), sizeof(ManyReq) * nreq, cudaMemcpyHostToDevice, s);
-    const cudaError_t e2 = cudaMemcpyAsync(ctl_d, ctl_h.data(), sizeof(ManyCtl) * nreq, cudaMemcpyHostToDevice, s);
-    if (e1 != cudaSuccess || e2 != cudaSuccess) st = cuda_fail(e1 != cudaSuccess ? e1 : e2, "cp_solve_many: upload",
-                                                             __FILE__, __LINE__);
-  }
-  const size_t smem = engine_smem(I3max, IRmax);
-  if (st == CP_OK) {
-    const cudaError_t e = cudaFuncSetAttribute(many_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) st = cuda_fail(e, "cp_solve_many: shared memory", __FILE__, __LINE__);
-  }
-  // rounds: every cluster size's unfinished requests in one launch each
-  int remaining = nreq;
-  while (st == CP_OK && remaining > 0) {
-    char* qb = base + q_off;
-    for (int C = 1; C <= kMaxC && st == CP_OK; C <<= 1) {
-      std::vector<int> tasks;
-      for (int i = 0; i < nreq; ++i)
-        if (!jobs[i].done && jobs[i].C == C) tasks.push_back(i);
-      if (tasks.empty()) continue;
-      ManyQueue* qd = (ManyQueue*)qb;
-      int* tasks_d = (int*)(qb + sizeof(ManyQueue) + 64);
-      int* ctask_d = tasks_d + nreq;
-      qb += (sizeof(ManyQueue) + 64 + (size_t)(nreq + maxclusters) * sizeof(int) + 255) / 256 * 256;
-      ManyQueue qh{0, (int)tasks.size(), 500ull * 1000 * 1000};
-      cudaLaunchConfig_t cfg{};
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = (unsigned)C;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.blockDim = dim3(kThreads);
-      cfg.dynamicSmemBytes = smem;
-      cfg.stream = s;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      cfg.gridDim = dim3((unsigned)C);
-      int active = 0;
-      cudaError_t e = cudaOccupancyMaxActiveClusters(&active, many_kernel, &cfg);
-      if (e != cudaSuccess || active < 1) {
-        st = cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidConfiguration, "cp_solve_many: cluster occupancy",
-                       __FILE__, __LINE__);
-        break;
-      }
-      const int nclusters = std::min<int>({active, (int)tasks.size(), maxclusters});
-      cfg.gridDim = dim3((unsigned)(nclusters * C));
-      e = cudaMemcpyAsync(qd, &qh, sizeof(qh), cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(tasks_d, tasks.data(), sizeof(int) * tasks.size(), cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, many_kernel, (const ManyReq*)req_d, (const int*)tasks_d, qd,
-                                                  ctask_d);
-      g_launches.fetch_add(1, std::memory_order_relaxed);
-      if (e != cudaSuccess) st = cuda_fail(e, "cp_solve_many: launch", __FILE__, __LINE__);
-      // the queue's host copies must outlive the copies: wait per launch
-      if (st == CP_OK) {
-        e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = cuda_fail(e, "cp_solve_many: engine", __FILE__, __LINE__);
-      }
-    }
+  for (int i = 0; i < nreq && st == CP_OK; ++i) st = e.add(ts[i], opts[i], u[i], cluster, &slot[i]);
+  while (st == CP_OK && e.running() > 0) {
+    st = e.launch_round(500ull * 1000 * 1000);
     if (st != CP_OK) break;
-    const cudaError_t e = cudaMemcpyAsync(ctl_h.data(), ctl_d, sizeof(ManyCtl) * nreq, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) {
-      const cudaError_t e2 = cudaStreamSynchronize(s);
-      if (e2 != cudaSuccess) st = cuda_fail(e2, "cp_solve_many: control blocks", __FILE__, __LINE__);
-    } else {
-      st = cuda_fail(e, "cp_solve_many: control blocks", __FILE__, __LINE__);
-    }
+    bool idle = false;
+    std::vector<int> fin;
+    st = e.poll(true, &idle, &fin);
     const double now = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    remaining = 0;
-    for (int i = 0; i < nreq; ++i) {
-      if (!jobs[i].done && ctl_h[i].phase == PH_DONE) {
-        jobs[i].done = true;
-        jobs[i].t_done = now;
-      }
-      if (!jobs[i].done) ++remaining;
-    }
+    for (int k : fin) t_done[(size_t)k] = now;   // slot k is request k (added in order)
   }
   cp_status first = st;
   for (int i = 0; i < nreq && st == CP_OK; ++i) {
-    const ManyCtl& c = ctl_h[i];
-    const cudaError_t e = cudaMemcpyAsync(u[i], jobs[i].q.u, sizeof(double) * jobs[i].q.P, cudaMemcpyDefault, s);
-    if (e != cudaSuccess && first == CP_OK) first = cuda_fail(e, "cp_solve_many: solution", __FILE__, __LINE__);
-    if (reps) {
-      cp_solve_report r{};
-      r.iters = c.iters;
-      r.fg_evals = c.fg_evals;
-      r.als_sweeps = c.als_sweeps;
-      r.restarts = c.restarts;
-      r.ls_failures = c.ls_failures;
-      r.converged = (c.stop == STOP_TOL && c.status == CP_OK) ? 1 : 0;
-      r.mixed_iters = c.mixed_iters;
-      r.fp64_iters = c.fp64_iters;
-      r.f = c.f;
-      r.gnorm_over_P = c.gn;
-      r.normT2 = jobs[i].t->norm2;
-      r.t_total_s = jobs[i].t_done;
-      r.ls_trials = c.ls_trials;
-      reps[i] = r;
-    }
+    cp_solve_report r{};
+    cp_status rs = CP_OK;
+    const cp_status c = e.result(slot[i], u[i], &r, &rs);
+    r.t_total_s = t_done[(size_t)slot[i]];
+    if (reps) reps[i] = r;
     if (first == CP_OK) {
-      if (c.status != CP_OK) {
-        set_error("cp_solve_many: request %d: %s", i,
-                  c.status == CP_ERR_NOT_SPD ? "Gammabar not positive definite" : "non-finite gradient");
-        first = (cp_status)c.status;
-      } else if (c.stop != STOP_TOL) {
-        set_error("cp_solve_many: request %d: tol not met after %d iterations (||g||/P = %.3e)", i, c.iters, c.gn);
-        first = CP_ERR_MAXIT;
+      if (c != CP_OK) {
+        first = c;
+      } else if (rs != CP_OK) {
+        if (rs == CP_ERR_MAXIT)
+          set_error("cp_solve_many: request %d: tol not met after %d iterations (||g||/P = %.3e)", i, r.iters,
+                    r.gnorm_over_P);
+        else
+          set_error("cp_solve_many: request %d: %s", i,
+                    rs == CP_ERR_NOT_SPD ? "Gammabar not positive definite" : "non-finite gradient");
+        first = rs;
       }
     }
   }
-  cudaStreamSynchronize(s);
-  cudaFreeAsync(base, s);
-  cudaStreamSynchronize(s);
   return first;
+}
+
+cp_status many_plan(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* o, const double* u0, int* cluster) {
+  if (!ctx || !t || !o || !u0 || !cluster) {
+    set_error("cp_many_plan: bad arguments");
+    return CP_ERR_ARG;
+  }
+  const char* why = many_unsupported(t, *o);
+  if (why) {
+    set_error("cp_many_plan: %s", why);
+    return CP_ERR_UNSUPPORTED;
+  }
+  CP_CUDA(cudaSetDevice(ctx->device));
+  CP_CUDA(cudaStreamSynchronize(ctx->stream));
+  ManyEngine e;
+  CP_TRY(e.create(ctx, 1));
+  return e.tuned_cluster(t, *o, u0, cluster);
 }
 
 }  // namespace cpg
@@ -1578,4 +2131,9 @@ cp_status many_solve(cp_ctx* ctx, int nreq, const cp_tensor* const* ts, const cp
 extern "C" cp_status cp_solve_many(cp_ctx* ctx, int nreq, const cp_tensor* const* tensors, const cp_solve_opts* opts,
                                    double* const* u, cp_solve_report* reps, int cluster) {
   return cpg::many_solve(ctx, nreq, tensors, opts, u, reps, cluster);
+}
+
+extern "C" cp_status cp_many_plan(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* opts, const double* u0,
+                                  int* cluster) {
+  return cpg::many_plan(ctx, t, opts, u0, cluster);
 }

@@ -35,6 +35,20 @@ namespace cpg {
 cp_status solve_impl(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* o, double* u_user, bool user_on_device,
                      cp_solve_report* rep);
 
+// The cluster engine (many.cu).
+struct ManyEngine;
+ManyEngine* many_engine_create(cp_ctx* ctx, int capacity, cp_status* st);
+void many_engine_destroy(ManyEngine* e);
+cp_status many_engine_add(ManyEngine* e, const cp_tensor* t, const cp_solve_opts& o, const double* u0, int* slot);
+int many_engine_running(ManyEngine* e);
+bool many_engine_in_flight(ManyEngine* e);
+cp_status many_engine_launch(ManyEngine* e, double budget_s);
+cp_status many_engine_poll(ManyEngine* e, bool block, bool* idle, std::vector<int>* finished);
+cp_status many_engine_result(ManyEngine* e, int slot, double* u_out, cp_solve_report* rep, cp_status* st);
+void many_engine_release(ManyEngine* e, int slot);
+const char* many_unsupported_dims(int kind, int N, const int64_t* dims, const cp_solve_opts& o);
+size_t many_state_bytes(const int64_t* dims, const cp_solve_opts& o);
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -55,6 +69,8 @@ struct Request {
   double* u_out = nullptr;         // caller's host buffer for the result
   cp_solve_opts opts{};
   size_t footprint = 0;
+  bool engine_ok = false;          // fits the cluster engine
+  long long work = 0;              // entries x R
   Clock::time_point t_submit, t_admit, t_done;
   int state = REQ_PENDING;
   cp_status status = CP_OK;
@@ -99,7 +115,18 @@ size_t request_footprint(int N, const int64_t* dims, cp_dtype dtype, const cp_so
 using namespace cpg;
 
 struct cp_server {
+  // requests on the cluster engine, by engine slot
+  struct EngReq {
+    Request* r = nullptr;
+    cp_tensor* t = nullptr;
+  };
   cp_ctx* ctx = nullptr;        // caller's context (device)
+  ManyEngine* eng = nullptr;    // the cluster engine (3-way dense requests within its limits)
+  bool engine_on = true;
+  long long engine_max_work = 1ll << 21;   // entries x R of the largest request routed to the engine
+  std::vector<EngReq> ereq;
+  int eng_used = 0;
+  double round_s = 0.010;       // engine round length
   cp_ctx* wctx = nullptr;       // worker's own context (stream for uploads)
   size_t budget = 0, used = 0, peak = 0;
   int max_active = 0;
@@ -161,6 +188,11 @@ struct cp_server {
       tensor_release(sl.t, sl.res.stream);
       sl.t = nullptr;
     }
+    sl.req = nullptr;
+    done(r, st);
+  }
+
+  void done(Request* r, cp_status st) {
     r->t_done = Clock::now();
     std::lock_guard<std::mutex> lock(mu);
     r->status = st;
@@ -170,8 +202,39 @@ struct cp_server {
     ++completed;
     latencies.push_back(seconds_since(r->t_submit, r->t_done));
     t_last = r->t_done;
-    sl.req = nullptr;
     cv.notify_all();
+  }
+
+  // Admit r to the cluster engine: its tensor (complete on return), then
+  // its state; it joins the next engine round.
+  void admit_engine(Request* r) {
+    r->t_admit = Clock::now();
+    cp_tensor* t = nullptr;
+    cp_status st = cp_tensor_dense(wctx, r->N, r->dims, r->dtype, r->data.data(), &t);
+    int k = -1;
+    if (st == CP_OK) st = many_engine_add(eng, t, r->opts, r->u0.data(), &k);
+    if (st != CP_OK) {
+      if (t) tensor_release(t, wctx->stream);
+      done(r, st);
+      return;
+    }
+    ereq[(size_t)k].r = r;
+    ereq[(size_t)k].t = t;
+    ++eng_used;
+  }
+
+  void finish_engine(int k) {
+    EngReq& e = ereq[(size_t)k];
+    Request* r = e.r;
+    cp_status rs = CP_OK;
+    cp_status st = many_engine_result(eng, k, r->u_out, &r->rep, &rs);
+    if (st == CP_OK) st = rs;
+    r->rep.t_total_s = seconds_since(r->t_admit, Clock::now());
+    many_engine_release(eng, k);
+    tensor_release(e.t, wctx->stream);
+    e = EngReq();
+    --eng_used;
+    done(r, st);
   }
 
   void loop() {
@@ -184,23 +247,56 @@ struct cp_server {
           progress = true;
         }
       }
-      for (auto& sl : slots) {
-        if (sl.req) continue;
+      if (eng && many_engine_in_flight(eng)) {
+        bool idle = false;
+        std::vector<int> fin;
+        const cp_status st = many_engine_poll(eng, false, &idle, &fin);
+        if (st != CP_OK) {
+          worker_error = st;
+          for (size_t k = 0; k < ereq.size(); ++k)
+            if (ereq[k].r) fin.push_back((int)k);
+        }
+        for (int k : fin) finish_engine(k);
+        if (idle || st != CP_OK) progress = true;
+      }
+      // admission in arrival order: the head request goes to the engine when
+      // it fits it, else to a graph slot; it waits while its kind is full
+      for (;;) {
         Request* r = nullptr;
+        bool to_engine = false;
+        Slot* free_slot = nullptr;
+        for (auto& sl : slots)
+          if (!sl.req) {
+            free_slot = &sl;
+            break;
+          }
         {
           std::lock_guard<std::mutex> lock(mu);
           while (!pending.empty() && pending.front()->state == REQ_CANCELLED) pending.pop_front();
-          if (!pending.empty() && used + pending.front()->footprint <= budget) {
-            r = pending.front();
-            pending.pop_front();
-            r->state = REQ_RUNNING;   // under the lock: a cancel from now on is refused
-            used += r->footprint;
-            peak = std::max(peak, used);
-            ++running;
+          if (!pending.empty()) {
+            Request* h = pending.front();
+            to_engine = eng && engine_on && h->engine_ok && (engine_max_work <= 0 || h->work <= engine_max_work);
+            const bool room = to_engine ? eng_used < (int)ereq.size() : free_slot != nullptr;
+            if (room && used + h->footprint <= budget) {
+              r = h;
+              pending.pop_front();
+              r->state = REQ_RUNNING;   // under the lock: a cancel from now on is refused
+              used += r->footprint;
+              peak = std::max(peak, used);
+              ++running;
+            }
           }
         }
         if (!r) break;
-        admit(sl, r);
+        if (to_engine)
+          admit_engine(r);
+        else
+          admit(*free_slot, r);
+        progress = true;
+      }
+      if (eng && !many_engine_in_flight(eng) && many_engine_running(eng) > 0) {
+        const cp_status st = many_engine_launch(eng, round_s);
+        if (st != CP_OK) worker_error = st;
         progress = true;
       }
       if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -230,6 +326,11 @@ cp_status cp_server_create(cp_ctx* ctx, size_t hbm_budget_bytes, int max_active,
       cp_ctx_destroy(s->wctx);
       return st;
     }
+  }
+  {
+    cp_status est = CP_OK;
+    s->eng = many_engine_create(ctx, max_active, &est);
+    if (s->eng) s->ereq.resize((size_t)max_active);
   }
   cp_server* raw = s.release();
   raw->worker = std::thread([raw]() { raw->loop(); });
@@ -265,7 +366,10 @@ cp_status cp_server_submit(cp_server* s, int N, const int64_t* dims, cp_dtype dt
   r->data.assign((const char*)data, (const char*)data + K * esz);
   r->u0.assign(u0, u0 + sumI * (size_t)opts->R);
   r->u_out = u_out;
-  r->footprint = request_footprint(N, dims, dtype, *opts);
+  r->engine_ok = many_unsupported_dims(0, N, dims, *opts) == nullptr;
+  r->work = (long long)K * opts->R;
+  r->footprint = r->engine_ok ? (size_t)(N + 1) * K * esz + many_state_bytes(dims, *opts)
+                              : request_footprint(N, dims, dtype, *opts);
   if (r->footprint > s->budget) {
     set_error("cp_server_submit: request needs ~%zu bytes, budget %zu", r->footprint, s->budget);
     return CP_ERR_BUSY;
@@ -356,11 +460,47 @@ cp_status cp_server_stats(cp_server* s, double* p50_s, double* p99_s, double* so
   return CP_OK;
 }
 
+cp_status cp_server_set_engine(cp_server* s, int on, long long max_work) {
+  if (!s || on < 0 || on > 1) {
+    set_error("cp_server_set_engine: bad arguments");
+    return CP_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (on && !s->eng) {
+    set_error("cp_server_set_engine: the cluster engine is not available on this device");
+    return CP_ERR_UNSUPPORTED;
+  }
+  s->engine_on = on != 0;
+  s->engine_max_work = max_work;
+  return CP_OK;
+}
+
 void cp_server_destroy(cp_server* s) {
   if (!s) return;
   s->stop.store(true);
   if (s->worker.joinable()) s->worker.join();
   cudaSetDevice(s->ctx->device);
+  if (s->eng) {
+    // engine requests still running finish in further rounds
+    for (;;) {
+      if (many_engine_in_flight(s->eng)) {
+        bool idle = false;
+        std::vector<int> fin;
+        if (many_engine_poll(s->eng, true, &idle, &fin) != CP_OK) break;
+        for (int k : fin) s->finish_engine(k);
+      }
+      if (many_engine_running(s->eng) == 0) break;
+      if (many_engine_launch(s->eng, s->round_s) != CP_OK) break;
+    }
+    for (size_t k = 0; k < s->ereq.size(); ++k)
+      if (s->ereq[k].r) {
+        many_engine_release(s->eng, (int)k);
+        tensor_release(s->ereq[k].t, s->wctx->stream);
+        s->ereq[k] = cp_server::EngReq();
+      }
+    many_engine_destroy(s->eng);
+    s->eng = nullptr;
+  }
   for (auto& sl : s->slots) {
     if (sl.solver)
       while (!sl.solver->poll(true)) {

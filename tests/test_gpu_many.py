@@ -84,7 +84,7 @@ def opts_for(cp, R, prec="fp64", maxit=None):
     return o
 
 
-@pytest.mark.parametrize("cluster", [1, 2, 4])
+@pytest.mark.parametrize("cluster", [0, 1, 2, 4])
 def test_fp64_requests_follow_the_oracle(cp, ctx, oracle_solves, cluster):
     tensors, us, opts = [], [], []
     for (prob, u0, X, uo, rep), case in zip(oracle_solves, CASES):
@@ -231,4 +231,28 @@ def test_unsupported_requests_are_refused(cp, ctx):
         cp.cp_solve_many(ctx, [t], [opts_for(cp, 33)], [dev(synth.initial_guess(rng, (6, 5, 4), 33))])
     assert ei.value.status == 11
     t4.close()
+    t.close()
+
+
+def test_plan_is_tuned_once_per_bucket(cp, ctx):
+    """cp_many_plan: a size in {1, 2, 4, 8}, the same on the second call and
+    for another request of the same bucket (entries and rank within the same
+    powers of two, same precision)."""
+    reqs = serving_like(3, seed=9)
+    prob, u0, R, _ = reqs[0]
+    t = cp.cp_tensor_dense(ctx, dev(prob.T))
+    o = opts_for(cp, R, prec="mixed")
+    c1 = cp.cp_many_plan(ctx, t, o, dev(u0))
+    assert c1 in (1, 2, 4, 8)
+    assert cp.cp_many_plan(ctx, t, o, dev(u0)) == c1
+    # same bucket: one side trimmed by one (entries stay within the power of two)
+    dims = prob.dims
+    K = int(np.prod(dims))
+    lk = int(np.ceil(np.log2(K)))
+    T2 = prob.T[:-1]
+    if int(np.ceil(np.log2(T2.size))) == lk:
+        t2 = cp.cp_tensor_dense(ctx, dev(T2))
+        u2 = synth.initial_guess(np.random.default_rng(1), T2.shape, R)
+        assert cp.cp_many_plan(ctx, t2, o, dev(u2)) == c1
+        t2.close()
     t.close()

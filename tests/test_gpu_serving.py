@@ -74,9 +74,23 @@ def test_batch_equals_solo(cp, ctx, prec_name):
         t.close()
 
 
-def test_server_results_equal_solo_and_stats(cp, ctx):
+def many_solo(cp, ctx, prob, u0, o):
+    t = cp.cp_tensor_dense(ctx, prob.T)
+    u = np.array(u0, copy=True)
+    (rep,) = cp.cp_solve_many(ctx, [t], [o], [u], cluster=0)
+    t.close()
+    return u, rep
+
+
+@pytest.mark.parametrize("engine", [False, True])
+def test_server_results_equal_solo_and_stats(cp, ctx, engine):
+    """Engine off: every request runs on a graph slot and must equal cp_solve;
+    engine on (the default): the requests share the cluster engine's rounds
+    and must equal cp_solve_many of the request alone (the same tuned
+    cluster size)."""
     items = small_requests(12, seed=2)
     srv = cp.cp_server_create(ctx, 8 << 30, 4)
+    cp.cp_server_set_engine(srv, engine)
     outs, ids, opts = [], [], []
     for k, (r, prob, u0) in enumerate(items):
         o = opts_for(cp, r, cp.CP_MIXED_BF16X3 if k % 2 else cp.CP_FP64)
@@ -89,11 +103,44 @@ def test_server_results_equal_solo_and_stats(cp, ctx):
         status, rep, lat = cp.cp_server_poll(srv, rid)
         assert status in (0, 8)
         assert lat > 0
-        u_solo, rep_solo = solo(cp, ctx, prob, u0, o)
+        u_solo, rep_solo = (many_solo if engine else solo)(cp, ctx, prob, u0, o)
         assert np.array_equal(out, u_solo)
         assert rep["iters"] == rep_solo["iters"]
+        if rep["converged"]:
+            _, g = O.fg(O.DenseTensor(prob.T.astype(np.float64)), out, r.R)
+            assert np.linalg.norm(g) / O.n_params(prob.dims, r.R) < o.tol
     st = cp.cp_server_stats(srv)
     assert st["completed"] == 12 and 0 < st["p50_s"] <= st["p99_s"] and st["solves_per_s"] > 0
+    srv.close()
+
+
+def test_server_mixes_engine_and_graph_requests(cp, ctx):
+    """A 4-way request (outside the engine) and 3-way requests in one
+    server: each equals its own path's solo result."""
+    items = small_requests(4, seed=6)
+    rng = synth.rng_for(0, 21)
+    p4 = synth.dense_problem(rng, (9, 8, 7, 6), 3, 0.5, eta=0.05, dtype=np.float32)
+    u4 = synth.initial_guess(rng, p4.dims, 3)
+    srv = cp.cp_server_create(ctx, 8 << 30, 3)
+    o4 = cp.cp_solve_opts_default(3)
+    o4.maxit = 3000
+    out4 = np.zeros_like(u4)
+    id4 = cp.cp_server_submit(srv, p4.T, o4, u4, out4)
+    outs, ids, opts = [], [], []
+    for r, prob, u0 in items:
+        o = opts_for(cp, r, cp.CP_FP64)
+        out = np.zeros_like(u0)
+        ids.append(cp.cp_server_submit(srv, prob.T, o, u0, out))
+        outs.append(out)
+        opts.append(o)
+    cp.cp_server_drain(srv, 600.0)
+    assert cp.cp_server_poll(srv, id4)[0] in (0, 8)
+    u_solo, _ = solo(cp, ctx, p4, u4, o4)
+    assert np.array_equal(out4, u_solo)
+    for (r, prob, u0), rid, out, o in zip(items, ids, outs, opts):
+        assert cp.cp_server_poll(srv, rid)[0] in (0, 8)
+        u_solo, _ = many_solo(cp, ctx, prob, u0, o)
+        assert np.array_equal(out, u_solo)
     srv.close()
 
 
@@ -117,9 +164,12 @@ def test_server_admission_budget(cp, ctx):
 
 def test_server_rejects_request_above_budget(cp, ctx):
     r, prob, u0 = small_requests(1, seed=4)[0]
-    srv = cp.cp_server_create(ctx, 1 << 20, 2)
+    # a budget below the tensor alone (the output buffer stays referenced: an
+    # admitted request would write to it)
+    srv = cp.cp_server_create(ctx, prob.T.nbytes // 2, 2)
+    out = np.zeros_like(u0)
     with pytest.raises(cp.CpError) as ei:
-        cp.cp_server_submit(srv, prob.T, opts_for(cp, r, cp.CP_FP64), u0, np.zeros_like(u0))
+        cp.cp_server_submit(srv, prob.T, opts_for(cp, r, cp.CP_FP64), u0, out)
     assert ei.value.status == 10
     srv.close()
 
