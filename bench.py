@@ -373,6 +373,7 @@ def run_ours(args, rank, world, local_rank):
         t.close()
         workloads = {"dense_20_fp64": c1_block(cp, ctx, stream), "dense_4way_96": c3_block(cp, ctx, stream),
                      "sparse_20000": c4_block(cp, ctx, stream)}
+        workloads["dense_20_fp64"]["many_small"] = many_block(cp, ctx, stream)
         workloads["sparse_20000"]["scaled_2e8"] = sparse_scaled_block(cp, ctx, stream)
         if cpu_c1 is not None:
             workloads["dense_20_fp64"]["cpu_oracle"] = cpu_c1
@@ -492,8 +493,11 @@ def serving_run(cp, ctx, args):
     at 200/s): the first `serve_requests` requests (default: all 1024)
     replayed open-loop through the request server (p50/p99 time to
     tolerance), then the same requests all submitted at t=0 (saturation
-    solves/s); then the first `serve_fp64_requests` in FP64 and in mixed
-    precision, at saturation and one by one (the per-request table)."""
+    solves/s), with the server's default routing (requests up to
+    ENGINE_MAX_WORK entries x R on the cluster engine, the rest on graph
+    slots) and with graph slots only; then the first `serve_fp64_requests`
+    in FP64 and in mixed precision, at saturation and one by one (the
+    per-request table, cp_solve)."""
     import numpy as np
     import synth
     n = args.serve_requests
@@ -511,8 +515,9 @@ def serving_run(cp, ctx, args):
         o.dimtree = args.dimtree
         return o
 
-    def run(prec, count, open_loop):
+    def run(prec, count, open_loop, engine=True):
         srv = cp.cp_server_create(ctx, 64 << 30, args.serve_slots)
+        cp.cp_server_set_engine(srv, engine, ENGINE_MAX_WORK)
         outs = [np.zeros_like(u0) for _, u0 in probs[:count]]
         t0 = time.perf_counter()
         ids = []
@@ -552,10 +557,15 @@ def serving_run(cp, ctx, args):
             rows.append(row + [round(ms[0], 2), round(ms[1], 2)] + its)
         return rows
 
+    routed = sum(1 for r in reqs if r.R * int(np.prod(r.dims)) <= ENGINE_MAX_WORK and max(r.dims) <= 256
+                 and max(r.dims) * r.R <= 8192)
     res = {"stream": "Poisson 200/s, sides U{16..192}, R U{2..32}, c {0.5,0.9}, noise U(1%,10%), tol {1e-5,1e-7}",
-           "slots": args.serve_slots, "generation_s": t_gen}
+           "slots": args.serve_slots, "generation_s": t_gen,
+           "routing": {"cluster_engine_max_entries_x_R": ENGINE_MAX_WORK, "to_cluster_engine": routed,
+                       "to_graph_slots": n - routed}}
     res["open_loop_mixed"] = run(cp.CP_MIXED_BF16X3, n, True)
     res["saturation_mixed"] = run(cp.CP_MIXED_BF16X3, n, False)
+    res["saturation_mixed_graph_slots_only"] = run(cp.CP_MIXED_BF16X3, n, False, engine=False)
     if args.serve_fp64_requests > 0:
         m = min(n, args.serve_fp64_requests)
         res["saturation_fp64"] = run(cp.CP_FP64, m, False)
@@ -566,6 +576,11 @@ def serving_run(cp, ctx, args):
                              "mixed_not_slower": sum(1 for x in rows if x[4] <= x[3]),
                              "fp64_total_ms": sum(x[3] for x in rows), "mixed_total_ms": sum(x[4] for x in rows)}
     return res
+
+
+# Requests up to this many entries x R go to the cluster engine (the server's
+# default routing; larger ones to graph slots with tensor-core MTTKRPs).
+ENGINE_MAX_WORK = 1 << 21
 
 
 def e2e_run(cp, ctx, prob, u0, prec, n, T_host):
@@ -940,6 +955,74 @@ def c1_block(cp, ctx, stream, n_solves=30):
             "solves_per_s": len(times) / sum(times), "p50_ms": 1e3 * lat[len(lat) // 2],
             "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], "solves_timed": len(times),
             "iters": r["iters"], "converged": r["converged"]}
+
+
+def many_block(cp, ctx, stream, n=1024, n_single=30):
+    """Many small decompositions in one persistent launch: n independent
+    problems shaped like the 20x20x20 workload (FP64, R=3, c=0.5, 10 % noise,
+    seeds 1000..1000+n-1), each solved to ||g||/P < 1e-7, by cp_solve_many
+    (every thread-block cluster runs one problem's whole solve at a time) and
+    by cp_solve_batch (one CUDA graph per problem, each on its own stream);
+    wall clock of the call, tensors resident, initial guesses and solutions
+    on the device.  Also the 20^3 workload itself solved alone through
+    cp_solve_many (CUDA-event timed)."""
+    import numpy as np
+    import torch
+    import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ts, u0s, opts = [], [], []
+    for k in range(n):
+        rng = synth.rng_for(1, 1000 + k)
+        prob = synth.dense_problem(rng, (20, 20, 20), 3, 0.5, eta=0.10, dtype=np.float64)
+        with torch.cuda.stream(stream):
+            ts.append(cp.cp_tensor_dense(ctx, torch.from_numpy(prob.T).to(dev)))
+            u0s.append(torch.from_numpy(synth.initial_guess(rng, prob.dims, 3)).to(dev))
+        o = cp.cp_solve_opts_default(3)
+        o.tol = TOL
+        o.prec = cp.CP_FP64
+        opts.append(o)
+    stream.synchronize()
+    out = {"workload": f"{n} independent dense 20x20x20 fp64 problems (planted R=3, c=0.5, 10% noise), "
+                       "N-GMRES w=20, R=3, stop ||g||/P < 1e-7"}
+    for name, fn in (("cp_solve_many", lambda us: cp.cp_solve_many(ctx, ts, opts, us)),
+                     ("cp_solve_batch", lambda us: cp.cp_solve_batch(ctx, ts, opts, us))):
+        for rep in range(2):   # the first call tunes / captures
+            us = [u.clone() for u in u0s]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            reps = fn(us)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        out[name] = {"solves_per_s": n / dt, "wall_s": dt, "converged": sum(r["converged"] for r in reps),
+                     "iters_total": sum(r["iters"] for r in reps)}
+    out["speedup_many_vs_batch"] = out["cp_solve_many"]["solves_per_s"] / out["cp_solve_batch"]["solves_per_s"]
+    # the 20^3 workload alone through the engine
+    prob, u0 = synth.workload_dense_small()
+    with torch.cuda.stream(stream):
+        T = torch.from_numpy(prob.T).to(dev)
+        u0d = torch.from_numpy(u0).to(dev)
+    stream.synchronize()
+    t = cp.cp_tensor_dense(ctx, T)
+    o = cp.cp_solve_opts_default(3)
+    o.tol = TOL
+    o.prec = cp.CP_FP64
+    times = []
+    for k in range(3 + n_single):
+        u = u0d.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        (r,) = cp.cp_solve_many(ctx, [t], [o], [u])
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 3:
+            times.append(e0.elapsed_time(e1) / 1e3)
+    t.close()
+    for x in ts:
+        x.close()
+    lat = sorted(times)
+    out["dense_20_alone"] = {"solves_per_s": len(times) / sum(times), "p50_ms": 1e3 * lat[len(lat) // 2],
+                             "iters": r["iters"], "converged": r["converged"]}
+    return out
 
 
 def c3_block(cp, ctx, stream):

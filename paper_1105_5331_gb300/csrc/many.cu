@@ -712,8 +712,10 @@ __device__ void window_solve(int m, double eps, EngSh& sh) {
       // (Newton-refined square roots and reciprocals: each IEEE FP64 divide
       // or sqrt is a serial chain of ~650 cycles in this one-warp solve)
       for (int k = 0; k < m; ++k) {
-        const double dk = sqrt_nr(sh.H[k * kMaxW + k]);
-        const double idk = recip_nr(dk);
+        // 1/sqrt first: the pivot and its reciprocal from one Newton chain
+        const double hk = sh.H[k * kMaxW + k];
+        const double idk = rsqrt_nr(hk);   // NaN for a pivot <= 0 (not positive definite)
+        const double dk = hk * idk;
         __syncwarp();
         if (lane == k) {
           sh.H[k * kMaxW + k] = dk;
