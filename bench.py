@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--mttkrp-only", default=None,
                    choices=["dense_256", "dense_4way", "sparse", "sparse_scaled", "dimtree_256"],
                    help="time only cp_mttkrp on that workload (profiling driver)")
+    p.add_argument("--many-only", action="store_true",
+                   help="one cp_solve_many call: 16 requests of 48^3, R=8, mixed, 20 iterations each, clusters of "
+                        "2 CTAs (profiling driver for the cluster engine's kernel)")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--accuracy-report", default=None, choices=["dense_256", "dense_4way"],
                    help="mixed (with FP64 polish) against FP64 solves of one workload; one JSON line")
@@ -580,7 +583,7 @@ def serving_run(cp, ctx, args):
 
 # Requests up to this many entries x R go to the cluster engine (the server's
 # default routing; larger ones to graph slots with tensor-core MTTKRPs).
-ENGINE_MAX_WORK = 1 << 21
+ENGINE_MAX_WORK = 1 << 23
 
 
 def e2e_run(cp, ctx, prob, u0, prec, n, T_host):
@@ -743,6 +746,37 @@ def run_precision_table(args):
         t.close()
         rows.append(row)
         print(json.dumps(row), flush=True)
+    ctx.close()
+
+
+def run_many_only(args):
+    """The cluster engine on a small fixed case (profiling driver): 16
+    requests of 48x48x48, planted R=8, c=0.5, 5 % noise, mixed precision,
+    exactly 20 iterations each, clusters of 2 CTAs, one cp_solve_many call;
+    prints its wall time."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1105_5331_gb300 as cp
+    ctx = cp.cp_ctx_create(0, torch.cuda.current_stream())
+    ts, us, opts = [], [], []
+    for k in range(16):
+        rng = synth.rng_for(33, k)
+        prob = synth.dense_problem(rng, (48, 48, 48), 8, 0.5, eta=0.05, dtype=np.float32)
+        ts.append(cp.cp_tensor_dense(ctx, prob.T))
+        us.append(synth.initial_guess(rng, prob.dims, 8))
+        o = cp.cp_solve_opts_default(8)
+        o.prec = cp.CP_MIXED_BF16X3
+        o.tol = 1e-300
+        o.maxit = 20
+        opts.append(o)
+    t0 = time.perf_counter()
+    reps = cp.cp_solve_many(ctx, ts, opts, us, cluster=2)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"many_only": "16 x 48^3 R=8 mixed, 20 iterations, clusters of 2", "wall_s": dt,
+                      "iters": sum(r["iters"] for r in reps)}))
+    for t in ts:
+        t.close()
     ctx.close()
 
 
@@ -1314,6 +1348,9 @@ def main():
         return
     if args.mttkrp_only:
         run_mttkrp_only(args)
+        return
+    if args.many_only:
+        run_many_only(args)
         return
     if args.precision_table:
         run_precision_table(args)

@@ -117,7 +117,7 @@ def _load():
         "cp_server_drain": (I, [VP, D]),
         "cp_server_stats": (I, [VP, C.POINTER(D), C.POINTER(D), C.POINTER(D), C.POINTER(I),
                                 C.POINTER(C.c_size_t)]),
-        "cp_server_set_engine": (I, [VP, I, C.c_longlong]),
+        "cp_server_set_engine": (I, [VP, I, C.c_longlong, I]),
         "cp_server_destroy": (None, [VP]),
     }
     for name, (res, args) in sig.items():
@@ -482,11 +482,12 @@ def cp_server_stats(server) -> dict:
             "peak_bytes": peak.value}
 
 
-def cp_server_set_engine(server, on: bool, max_work: int = 1 << 21):
+def cp_server_set_engine(server, on: bool, max_work: int = 1 << 23, max_ctas: int = 0):
     """Route requests that fit the cluster engine and have at most max_work
     entries x R to it (on, the default), the rest to graph slots of their
-    own; on=False: every request to a graph slot."""
-    _check(_lib.cp_server_set_engine(_h(server), 1 if on else 0, int(max_work)))
+    own; on=False: every request to a graph slot.  max_ctas: CTAs an engine
+    round may use (0: as many as fit)."""
+    _check(_lib.cp_server_set_engine(_h(server), 1 if on else 0, int(max_work), int(max_ctas)))
 
 
 def cp_server_destroy(server):

@@ -173,6 +173,7 @@ void cp_ctx_destroy(cp_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->many) cpg::many_engine_destroy(static_cast<cpg::ManyEngine*>(c->many));
   if (c->own_stream) cudaStreamDestroy(c->stream);
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);

@@ -123,6 +123,7 @@ struct cp_ctx {
   // solver contexts only: 3-way dense mixed-precision MTTKRP pairs come from
   // a dimension tree (one pass over T for two modes)
   bool dimtree = false;
+  void* many = nullptr;             // the cluster engine cp_solve_many keeps between calls
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int num_sms = 0;
@@ -422,5 +423,9 @@ cp_status ws_alloc_on(cp_ctx* ctx, cudaStream_t s, void** p, size_t bytes);
 void ws_free_on(cp_ctx* ctx, cudaStream_t s, void* p);
 
 cp_status read_status(cp_ctx* ctx);
+
+// The cluster engine (many.cu).
+struct ManyEngine;
+void many_engine_destroy(ManyEngine* e);
 
 }  // namespace cpg

@@ -1658,7 +1658,9 @@ struct ManyEngine {
   int cap = 0;
   int maxcl[kGroups] = {0, 0, 0, 0};
   size_t smem = 0;
-  cudaStream_t es = nullptr;
+  cudaStream_t es = nullptr;          // rounds, read-back, results
+  cudaStream_t us = nullptr;          // admissions (allocation, uploads), never behind a round
+  cudaEvent_t up_ev = nullptr;        // the last admission's uploads
   cudaStream_t gs[kGroups] = {};
   cudaEvent_t fork = nullptr, join[kGroups] = {}, round_ev = nullptr, pa = nullptr, pb = nullptr;
   ManyReq* req_d = nullptr;          // cap + 1 descriptors (the last one for tuning probes)
@@ -1672,6 +1674,7 @@ struct ManyEngine {
   std::vector<Job> jobs;
   bool in_flight = false;
   int launched_rounds = 0;
+  int max_ctas = 0;                  // CTAs one round may use (<= 0: as many as fit)
 
   ~ManyEngine() { destroy(); }
 
@@ -1682,6 +1685,8 @@ struct ManyEngine {
     CP_CUDA(cudaSetDevice(ctx->device));
     CP_CUDA(cudaFuncSetAttribute(many_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CP_CUDA(cudaStreamCreateWithFlags(&es, cudaStreamNonBlocking));
+    CP_CUDA(cudaStreamCreateWithFlags(&us, cudaStreamNonBlocking));
+    CP_CUDA(cudaEventCreateWithFlags(&up_ev, cudaEventDisableTiming));
     for (int k = 0; k < kGroups; ++k) {
       CP_CUDA(cudaStreamCreateWithFlags(&gs[k], cudaStreamNonBlocking));
       CP_CUDA(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming));
@@ -1758,20 +1763,28 @@ struct ManyEngine {
     if (pa) cudaEventDestroy(pa);
     if (pb) cudaEventDestroy(pb);
     fork = round_ev = pa = pb = nullptr;
+    if (us) {
+      cudaStreamSynchronize(us);
+      cudaStreamDestroy(us);
+    }
+    if (up_ev) cudaEventDestroy(up_ev);
+    us = nullptr;
+    up_ev = nullptr;
     if (es) cudaStreamDestroy(es);
     es = nullptr;
   }
 
   // One launch of cluster size C over ntasks requests (tasks_h + group
   // offset already filled) on stream s, queue block g.
-  cp_status launch(int g, int C, int ntasks, unsigned long long budget_ns, cudaStream_t s) {
+  cp_status launch(int g, int C, int ntasks, unsigned long long budget_ns, cudaStream_t s, int cta_cap = 0) {
     char* qb = qbuf_d + (size_t)g * qstride;
     ManyQueue* qd = (ManyQueue*)qb;
     int* tasks_d = (int*)(qb + sizeof(ManyQueue) + 64);
     int* ctask_d = tasks_d + cap + 1;
     q_h[g] = ManyQueue{0, ntasks, budget_ns};
     const int k = C == 1 ? 0 : C == 2 ? 1 : C == 4 ? 2 : 3;
-    const int nclusters = std::min(maxcl[k], ntasks);
+    int nclusters = std::min(maxcl[k], ntasks);
+    if (cta_cap > 0) nclusters = std::max(1, std::min(nclusters, cta_cap / C));
     if (nclusters < 1) {
       set_error("cp_solve_many: clusters of %d CTAs cannot be resident", C);
       return CP_ERR_CUDA;
@@ -1907,7 +1920,9 @@ struct ManyEngine {
     Job& j = jobs[k];
     fill_req(j.q, t, o);
     void* mem = nullptr;
-    CP_CUDA(cudaMallocAsync(&mem, job_layout(j.q, nullptr), es));
+    // on the admission stream: a host upload on es would wait for the round
+    // in flight (pageable copies return only when done)
+    CP_CUDA(cudaMallocAsync(&mem, job_layout(j.q, nullptr), us));
     (void)job_layout(j.q, (char*)mem);
     j.q.ctl = ctl_d + k;
     j.mem = mem;
@@ -1918,9 +1933,10 @@ struct ManyEngine {
     j.iters = 0;
     // (ctl_h belongs to the round read-back, which may still be in flight)
     ctl_up[k] = initial_ctl(o);
-    CP_CUDA(cudaMemcpyAsync(j.q.x, u0, sizeof(double) * j.q.P, cudaMemcpyDefault, es));
-    CP_CUDA(cudaMemcpyAsync(ctl_d + k, &ctl_up[k], sizeof(ManyCtl), cudaMemcpyHostToDevice, es));
-    CP_CUDA(cudaMemcpyAsync(req_d + k, &j.q, sizeof(ManyReq), cudaMemcpyHostToDevice, es));
+    CP_CUDA(cudaMemcpyAsync(j.q.x, u0, sizeof(double) * j.q.P, cudaMemcpyDefault, us));
+    CP_CUDA(cudaMemcpyAsync(ctl_d + k, &ctl_up[k], sizeof(ManyCtl), cudaMemcpyHostToDevice, us));
+    CP_CUDA(cudaMemcpyAsync(req_d + k, &j.q, sizeof(ManyReq), cudaMemcpyHostToDevice, us));
+    CP_CUDA(cudaEventRecord(up_ev, us));   // the next round waits for it
     // pageable sources above: the copies have been taken before they return
     *slot = k;
     return CP_OK;
@@ -1936,8 +1952,10 @@ struct ManyEngine {
   // launch per group on its own stream (least iterations first), then the
   // control blocks back to the host.  Non-blocking.
   cp_status launch_round(unsigned long long budget_ns) {
+    CP_CUDA(cudaStreamWaitEvent(es, up_ev, 0));
     CP_CUDA(cudaEventRecord(fork, es));
-    for (int g = 0; g < kGroups; ++g) {
+    int left = max_ctas;   // shared by the groups, larger clusters first
+    for (int g = kGroups - 1; g >= 0; --g) {
       const int C = 1 << g;
       std::vector<int> ids;
       for (int i = 0; i < cap; ++i)
@@ -1947,7 +1965,9 @@ struct ManyEngine {
       for (int i : ids) jobs[i].in_round = true;
       std::copy(ids.begin(), ids.end(), tasks_h + (size_t)g * (cap + 1));
       CP_CUDA(cudaStreamWaitEvent(gs[g], fork, 0));
-      CP_TRY(launch(g, C, (int)ids.size(), budget_ns, gs[g]));
+      const int cap_g = max_ctas > 0 ? std::max(left, C) : 0;
+      CP_TRY(launch(g, C, (int)ids.size(), budget_ns, gs[g], cap_g));
+      if (max_ctas > 0) left -= std::min((int)ids.size(), std::max(1, cap_g / C)) * C;
       CP_CUDA(cudaEventRecord(join[g], gs[g]));
       CP_CUDA(cudaStreamWaitEvent(es, join[g], 0));
     }
@@ -1983,12 +2003,13 @@ struct ManyEngine {
     return CP_OK;
   }
 
-  // Result of a finished request: u (host or device), report, status.
-  cp_status result(int k, double* u_out, cp_solve_report* rep, cp_status* status) {
+  // Result of a finished request: u (host or device), report, status.  With
+  // sync false the copy of u is only enqueued (the caller synchronises es).
+  cp_status result(int k, double* u_out, cp_solve_report* rep, cp_status* status, bool sync = true) {
     const Job& j = jobs[k];
     const ManyCtl& c = ctl_h[k];
     CP_CUDA(cudaMemcpyAsync(u_out, j.q.u, sizeof(double) * j.q.P, cudaMemcpyDefault, es));
-    CP_CUDA(cudaStreamSynchronize(es));
+    if (sync) CP_CUDA(cudaStreamSynchronize(es));
     if (rep) {
       cp_solve_report r{};
       r.iters = c.iters;
@@ -2033,6 +2054,7 @@ cp_status many_engine_add(ManyEngine* e, const cp_tensor* t, const cp_solve_opts
 }
 cudaStream_t many_engine_stream(ManyEngine* e) { return e->es; }
 int many_engine_running(ManyEngine* e) { return e->running(); }
+void many_engine_set_cta_cap(ManyEngine* e, int max_ctas) { e->max_ctas = max_ctas; }
 bool many_engine_in_flight(ManyEngine* e) { return e->in_flight; }
 cp_status many_engine_launch(ManyEngine* e, double budget_s) {
   return e->launch_round((unsigned long long)(budget_s * 1e9));
@@ -2072,8 +2094,25 @@ cp_status many_solve(cp_ctx* ctx, int nreq, const cp_tensor* const* ts, const cp
   }
   CP_CUDA(cudaStreamSynchronize(ctx->stream));   // the tensors are complete
   const auto t0 = std::chrono::steady_clock::now();
-  ManyEngine e;
-  CP_TRY(e.create(ctx, nreq));
+  // the context keeps its engine (streams, pinned buffers, descriptor table)
+  // between calls; a larger batch replaces it
+  ManyEngine* ep = static_cast<ManyEngine*>(ctx->many);
+  if (!ep || ep->cap < nreq) {
+    if (ep) many_engine_destroy(ep);
+    ctx->many = nullptr;
+    cp_status cst = CP_OK;
+    ep = many_engine_create(ctx, std::max(nreq, 64), &cst);
+    if (!ep) return cst;
+    ctx->many = ep;
+  }
+  ManyEngine& e = *ep;
+  struct Release {
+    ManyEngine& e;
+    ~Release() {
+      for (int k = 0; k < e.cap; ++k)
+        if (e.jobs[k].used) e.release(k);
+    }
+  } release_all{e};
   std::vector<int> slot((size_t)nreq, -1);
   std::vector<double> t_done((size_t)nreq, 0.0);
   cp_status st = CP_OK;
@@ -2088,10 +2127,17 @@ cp_status many_solve(cp_ctx* ctx, int nreq, const cp_tensor* const* ts, const cp
     for (int k : fin) t_done[(size_t)k] = now;   // slot k is request k (added in order)
   }
   cp_status first = st;
+  std::vector<cp_solve_report> rr((size_t)nreq);
+  std::vector<cp_status> rst((size_t)nreq, CP_OK), cst((size_t)nreq, CP_OK);
+  for (int i = 0; i < nreq && st == CP_OK; ++i) cst[i] = e.result(slot[i], u[i], &rr[i], &rst[i], false);
+  if (st == CP_OK) {
+    const cudaError_t ce = cudaStreamSynchronize(e.es);
+    if (ce != cudaSuccess) first = cuda_fail(ce, "cp_solve_many: solutions", __FILE__, __LINE__);
+  }
   for (int i = 0; i < nreq && st == CP_OK; ++i) {
-    cp_solve_report r{};
-    cp_status rs = CP_OK;
-    const cp_status c = e.result(slot[i], u[i], &r, &rs);
+    cp_solve_report r = rr[i];
+    const cp_status rs = rst[i];
+    const cp_status c = cst[i];
     r.t_total_s = t_done[(size_t)slot[i]];
     if (reps) reps[i] = r;
     if (first == CP_OK) {
@@ -2123,9 +2169,14 @@ cp_status many_plan(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* o, con
   }
   CP_CUDA(cudaSetDevice(ctx->device));
   CP_CUDA(cudaStreamSynchronize(ctx->stream));
-  ManyEngine e;
-  CP_TRY(e.create(ctx, 1));
-  return e.tuned_cluster(t, *o, u0, cluster);
+  ManyEngine* ep = static_cast<ManyEngine*>(ctx->many);
+  if (!ep) {
+    cp_status cst = CP_OK;
+    ep = many_engine_create(ctx, 64, &cst);
+    if (!ep) return cst;
+    ctx->many = ep;
+  }
+  return ep->tuned_cluster(t, *o, u0, cluster);
 }
 
 }  // namespace cpg

@@ -41,6 +41,7 @@ ManyEngine* many_engine_create(cp_ctx* ctx, int capacity, cp_status* st);
 void many_engine_destroy(ManyEngine* e);
 cp_status many_engine_add(ManyEngine* e, const cp_tensor* t, const cp_solve_opts& o, const double* u0, int* slot);
 int many_engine_running(ManyEngine* e);
+void many_engine_set_cta_cap(ManyEngine* e, int max_ctas);
 bool many_engine_in_flight(ManyEngine* e);
 cp_status many_engine_launch(ManyEngine* e, double budget_s);
 cp_status many_engine_poll(ManyEngine* e, bool block, bool* idle, std::vector<int>* finished);
@@ -123,7 +124,7 @@ struct cp_server {
   cp_ctx* ctx = nullptr;        // caller's context (device)
   ManyEngine* eng = nullptr;    // the cluster engine (3-way dense requests within its limits)
   bool engine_on = true;
-  long long engine_max_work = 1ll << 21;   // entries x R of the largest request routed to the engine
+  long long engine_max_work = 1ll << 23;   // entries x R of the largest request routed to the engine
   std::vector<EngReq> ereq;
   int eng_used = 0;
   double round_s = 0.010;       // engine round length
@@ -330,7 +331,9 @@ cp_status cp_server_create(cp_ctx* ctx, size_t hbm_budget_bytes, int max_active,
   {
     cp_status est = CP_OK;
     s->eng = many_engine_create(ctx, max_active, &est);
-    if (s->eng) s->ereq.resize((size_t)max_active);
+    if (s->eng) {
+      s->ereq.resize((size_t)max_active);
+    }
   }
   cp_server* raw = s.release();
   raw->worker = std::thread([raw]() { raw->loop(); });
@@ -460,7 +463,7 @@ cp_status cp_server_stats(cp_server* s, double* p50_s, double* p99_s, double* so
   return CP_OK;
 }
 
-cp_status cp_server_set_engine(cp_server* s, int on, long long max_work) {
+cp_status cp_server_set_engine(cp_server* s, int on, long long max_work, int max_ctas) {
   if (!s || on < 0 || on > 1) {
     set_error("cp_server_set_engine: bad arguments");
     return CP_ERR_ARG;
@@ -472,6 +475,7 @@ cp_status cp_server_set_engine(cp_server* s, int on, long long max_work) {
   }
   s->engine_on = on != 0;
   s->engine_max_work = max_work;
+  if (s->eng) many_engine_set_cta_cap(s->eng, max_ctas > 0 ? max_ctas : 0);
   return CP_OK;
 }
 
