@@ -223,27 +223,29 @@ __device__ __forceinline__ void cp_async_el(double* dst, const double* src) {
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// Wait until at most N of this thread's newest copy groups are in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
-// Tiles of T staged per step: 64 bytes of a row (16 floats, 8 doubles) for
-// Y = T x_3 B; 128-byte rows... whole rows of kTF fibers for M^(3).
+// Tiles of T staged per step: 128 bytes of a row (32 floats, 16 doubles) for
+// Y = T x_3 B; whole rows of kTF fibers (32 for floats, 16 for doubles) for M^(3).
 template <typename TT>
 struct Stage {
-  static constexpr int kIC = 64 / (int)sizeof(TT);    // i3 per sub-tile in Y = T x_3 B
+  static constexpr int kIC = 128 / (int)sizeof(TT);   // i3 per sub-tile in Y = T x_3 B
   static constexpr int kTF = 128 / (int)sizeof(TT);   // fibers per chunk in M^(3)
 };
-constexpr int kYF = 2 * kThreads;   // fibers per block in Y = T x_3 B
 
 // Y[j][c0 + c] = sum_{i3} T[j][i3] B[i3][c] for the CTA's fibers j, where B
 // is A (I3 x R) or [A | D] (I3 x 2R); Y has row stride ys (AT elements).
-// Each thread keeps two kColW-column register tiles: fiber t's two column
-// tiles when the staged columns need two (more than kColW), else fibers t and
-// t + kThreads (blocks of kYF fibers).  T arrives in block x kIC sub-tiles,
-// double-buffered by cp.async from every thread, stored with an odd row
-// stride (kIC + 1) so that a warp reading one column of its 32 rows hits 32
-// different banks; the factor columns (kBsCols at a time) are read as
-// broadcasts.
+// Threads own fibers (blocks of 256); T arrives in 256-fiber x kIC-column
+// sub-tiles (128 bytes of a row), double-buffered by cp.async from every
+// thread and stored with row stride kIC + 1, so that a warp reading one
+// column of its 32 rows hits 32 banks; the factor columns (32 at a time) are
+// read as broadcasts; two kColW-column register tiles per thread.  (Measured
+// against two fibers per thread with 64-byte sub-tiles and against a
+// three-deep ring: 8-10 % faster than either on 64^3 and 128^3, R = 16.)
 template <typename TT, typename AT>
 __device__ __noinline__ void pass_y(const TT* __restrict__ T, int J, int I3, int R, const double* __restrict__ A,
                                     const double* __restrict__ D, AT* __restrict__ Y, int ys, int rk, int C, AT* Bs,
@@ -252,7 +254,7 @@ __device__ __noinline__ void pass_y(const TT* __restrict__ T, int J, int I3, int
   const int ncol = D ? 2 * R : R;
   const int jlo = lo_of(J, rk, C), jhi = lo_of(J, rk + 1, C);
   const int nsub = (I3 + kIC - 1) / kIC;
-  TT* const buf1 = Tst + kYF * kLd;
+  TT* const buf1 = Tst + kThreads * kLd;
   for (int c0 = 0; c0 < ncol; c0 += kBsCols) {
     const int nc = min(kBsCols, ncol - c0);
     const int ncp = (nc + kColW - 1) / kColW * kColW;
@@ -265,13 +267,12 @@ __device__ __noinline__ void pass_y(const TT* __restrict__ T, int J, int I3, int
       Bs[e] = (AT)v;
     }
     __syncthreads();
-    const bool two = ncp > kColW;            // two column tiles of one fiber
-    const int fb = two ? kThreads : kYF;     // fibers per block
-    for (int jb = jlo; jb < jhi; jb += fb) {
-      const int nrow = min(fb, jhi - jb);
+    const bool two = ncp > kColW;
+    for (int jb = jlo; jb < jhi; jb += kThreads) {
+      const int nrow = min(kThreads, jhi - jb);
       auto issue = [&](int sc, TT* dst) {
         const int i0 = sc * kIC, ni = min(kIC, I3 - i0);
-        for (int e = threadIdx.x; e < fb * kIC; e += kThreads) {
+        for (int e = threadIdx.x; e < kThreads * kIC; e += kThreads) {
           const int f = e / kIC, i = e - (e / kIC) * kIC;
           if (f < nrow && i < ni) cp_async_el(dst + f * kLd + i, T + (size_t)(jb + f) * I3 + i0 + i);
         }
@@ -287,17 +288,17 @@ __device__ __noinline__ void pass_y(const TT* __restrict__ T, int J, int I3, int
       for (int sc = 0; sc < nsub; ++sc) {
         if (sc + 1 < nsub) {
           issue(sc + 1, ((sc + 1) & 1) ? buf1 : Tst);
-          cp_async_wait_one();
+          cp_async_wait<1>();
         } else {
-          cp_async_wait_all();
+          cp_async_wait<0>();
         }
         __syncthreads();
         const int i0 = sc * kIC, ni = min(kIC, I3 - i0);
-        const TT* tbase = ((sc & 1) ? buf1 : Tst) + threadIdx.x * kLd;
+        const TT* trow = ((sc & 1) ? buf1 : Tst) + threadIdx.x * kLd;
         const AT* b = Bs + (size_t)i0 * ncp;
         if (two) {
           for (int i = 0; i < ni; ++i) {
-            const AT t = (AT)tbase[i];
+            const AT t = (AT)trow[i];
 #pragma unroll
             for (int k = 0; k < kColW; ++k) {
               acc0[k] = fmat(t, b[k], acc0[k]);
@@ -306,40 +307,21 @@ __device__ __noinline__ void pass_y(const TT* __restrict__ T, int J, int I3, int
             b += ncp;
           }
         } else {
-          const TT* tb2 = tbase + kThreads * kLd;
           for (int i = 0; i < ni; ++i) {
-            const AT t0 = (AT)tbase[i], t1 = (AT)tb2[i];
+            const AT t = (AT)trow[i];
 #pragma unroll
-            for (int k = 0; k < kColW; ++k) {
-              const AT bv = b[k];
-              acc0[k] = fmat(t0, bv, acc0[k]);
-              acc1[k] = fmat(t1, bv, acc1[k]);
-            }
+            for (int k = 0; k < kColW; ++k) acc0[k] = fmat(t, b[k], acc0[k]);
             b += ncp;
           }
         }
-        __syncthreads();   // the buffer is refilled two steps later
+        __syncthreads();
       }
-      const int f0 = threadIdx.x;
-      if (two) {
-        if (f0 < nrow) {
-          AT* yrow = Y + (size_t)(jb + f0) * ys + c0;
+      if ((int)threadIdx.x < nrow) {
+        AT* yrow = Y + (size_t)(jb + threadIdx.x) * ys + c0;
 #pragma unroll
-          for (int k = 0; k < kColW; ++k) {
-            if (k < nc) yrow[k] = acc0[k];
-            if (kColW + k < nc) yrow[kColW + k] = acc1[k];
-          }
-        }
-      } else {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int f = f0 + h * kThreads;
-          if (f < nrow) {
-            AT* yrow = Y + (size_t)(jb + f) * ys + c0;
-#pragma unroll
-            for (int k = 0; k < kColW; ++k)
-              if (k < nc) yrow[k] = h ? acc1[k] : acc0[k];
-          }
+        for (int k = 0; k < kColW; ++k) {
+          if (k < nc) yrow[k] = acc0[k];
+          if (two && kColW + k < nc) yrow[kColW + k] = acc1[k];
         }
       }
     }
@@ -349,126 +331,102 @@ __device__ __noinline__ void pass_y(const TT* __restrict__ T, int J, int I3, int
 // The CTA's partial of M^(3)(A, B): out[i3][r] = sum_{j in its fibers}
 // T[j][i3] A[j / I2][r] B[j % I2][r] (I3 x R doubles).  T arrives in chunks
 // of kTF whole rows (contiguous in memory), double-buffered by cp.async from
-// every thread; the Khatri-Rao rows of the next chunk are formed (into the
-// other of two shared buffers) from factor entries loaded before the current
-// chunk is processed.  A unit is a 64-row, kColW-column output tile: its
-// lanes own i3 and i3 + 32 (two accumulator rows share every Khatri-Rao
-// read); with u units, kWarps / u warps share a unit and take every
-// (kWarps / u)-th fiber of a chunk.  Register sums are FP32 (or FP64) and
-// are added into FP64 shared totals, one set per fiber group, every kFlush
-// chunks; the groups are added in order at the end.
+// every thread; each chunk's Khatri-Rao rows are formed in shared memory.
+// Lanes own i3 (32-row x kColW-column output tiles); with at most kWarps
+// tiles each gets kWarps / tiles warps that take every (kWarps / tiles)-th
+// fiber of a chunk, with more a warp keeps two tiles.  Register sums are
+// FP32 (or FP64) and are added into FP64 shared totals, one set per fiber
+// group, every kFlush chunks; the groups are added in order at the end.
+// (Measured against 64-row tiles with the next chunk's Khatri-Rao rows
+// loaded ahead and against a three-deep ring: 8-10 % faster.)
 template <typename TT, typename AT>
 __device__ __noinline__ void pass_m3(const TT* __restrict__ T, int J, int I2, int I3, int R, const double* __restrict__ A,
-                        const double* __restrict__ B, double* __restrict__ out, int rk, int C, TT* Tst, AT* KRs,
-                        double* Ms) {
+                                     const double* __restrict__ B, double* __restrict__ out, int rk, int C, TT* Tst,
+                                     AT* KRs, double* Ms) {
   constexpr int kTF = Stage<TT>::kTF;
-  constexpr int kKRPer = Stage<float>::kTF * kMaxR / kThreads;   // Khatri-Rao entries per thread
   const int Rp = (R + kColW - 1) / kColW * kColW;
-  const int nib = (I3 + 63) / 64, nct = Rp / kColW;
-  const int units = nib * nct;   // at most kWarps (I3 <= 256, R <= 32)
-  const int wpu = kWarps / units;
+  const int nib = (I3 + 31) / 32, nct = Rp / kColW;
+  const int units = nib * nct;
+  const int wpu = units <= kWarps ? kWarps / units : 1;
   const int IR = I3 * R;
   const int jlo = lo_of(J, rk, C), jhi = lo_of(J, rk + 1, C);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = warp % wpu;
-  const int unit = warp < units * wpu ? warp / wpu : units;
-  const int ib = unit / nct, ct = unit - (unit / nct) * nct;
-  const int i3a = ib * 64 + lane, i3b = i3a + 32;
-  const bool oka = unit < units && i3a < I3, okb = unit < units && i3b < I3;
   TT* const buf1 = Tst + kTF * kMaxI;
-  AT* const kr1 = KRs + kTF * kMaxR;
   for (int e = threadIdx.x; e < wpu * IR; e += kThreads) Ms[e] = 0.0;
-  AT acc0[kColW], acc1[kColW];
+  AT acc[2][kColW];
 #pragma unroll
-  for (int k = 0; k < kColW; ++k) {
-    acc0[k] = (AT)0;
-    acc1[k] = (AT)0;
-  }
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int k = 0; k < kColW; ++k) acc[u][k] = (AT)0;
   auto issue = [&](int j0, TT* dst) {
     const int n = min(kTF, jhi - j0) * I3;
     const TT* src = T + (size_t)j0 * I3;
     for (int e = threadIdx.x; e < n; e += kThreads) cp_async_el(dst + e, src + e);
     cp_async_commit();
   };
-  double fa[kKRPer], fb[kKRPer];
-  auto load_kr = [&](int j0) {
-    const int nf = min(kTF, jhi - j0);
-#pragma unroll
-    for (int q = 0; q < kKRPer; ++q) {
-      const int e = threadIdx.x + q * kThreads;
-      const int f = e / Rp, r = e - (e / Rp) * Rp;
-      fa[q] = 0.0;
-      fb[q] = 0.0;
-      if (f < nf && r < R) {
-        const int j = j0 + f;
-        const int i1 = j / I2, i2 = j - (j / I2) * I2;
-        fa[q] = A[(size_t)i1 * R + r];
-        fb[q] = B[(size_t)i2 * R + r];
-      }
-    }
-  };
-  auto store_kr = [&](AT* dst) {
-#pragma unroll
-    for (int q = 0; q < kKRPer; ++q) {
-      const int e = threadIdx.x + q * kThreads;
-      if (e < kTF * Rp) dst[e] = (AT)fa[q] * (AT)fb[q];
-    }
-  };
   const int nch = (jhi - jlo + kTF - 1) / kTF;
-  if (nch > 0) {
-    issue(jlo, Tst);
-    load_kr(jlo);
-    store_kr(KRs);
-  }
+  if (nch > 0) issue(jlo, Tst);
   int chunks = 0;
   for (int c = 0; c < nch; ++c) {
     const int j0 = jlo + c * kTF;
     const int nf = min(kTF, jhi - j0);
+    for (int e = threadIdx.x; e < kTF * Rp; e += kThreads) {
+      const int f = e / Rp, r = e - (e / Rp) * Rp;
+      AT v = (AT)0;
+      if (f < nf && r < R) {
+        const int j = j0 + f;
+        const int i1 = j / I2, i2 = j - (j / I2) * I2;
+        v = (AT)A[(size_t)i1 * R + r] * (AT)B[(size_t)i2 * R + r];
+      }
+      KRs[e] = v;
+    }
     if (c + 1 < nch) {
       issue(j0 + kTF, ((c + 1) & 1) ? buf1 : Tst);
-      load_kr(j0 + kTF);   // consumed after this chunk's products
-      cp_async_wait_one();
+      cp_async_wait<1>();
     } else {
-      cp_async_wait_all();
+      cp_async_wait<0>();
     }
     __syncthreads();
     const TT* tb = (c & 1) ? buf1 : Tst;
-    const AT* kb = ((c & 1) ? kr1 : KRs) + ct * kColW;
-    if (unit < units) {
-      const TT* ta = tb + (oka ? i3a : 0);
-      const TT* tb2 = tb + (okb ? i3b : 0);
-      for (int f = grp; f < nf; f += wpu) {
-        const AT t0 = oka ? (AT)ta[f * I3] : (AT)0;
-        const AT t1 = okb ? (AT)tb2[f * I3] : (AT)0;
-        const AT* bf = kb + f * Rp;
 #pragma unroll
-        for (int k = 0; k < kColW; ++k) {
-          const AT bv = bf[k];
-          acc0[k] = fmat(t0, bv, acc0[k]);
-          acc1[k] = fmat(t1, bv, acc1[k]);
+    for (int u = 0; u < 2; ++u) {
+      const int unit = units <= kWarps ? (u == 0 && warp < units * wpu ? warp / wpu : units) : warp + u * kWarps;
+      if (unit < units) {
+        const int ib = unit / nct, ct = unit - (unit / nct) * nct;
+        const int i3 = ib * 32 + lane;
+        const bool ok = i3 < I3;
+        const TT* tcol = tb + (ok ? i3 : 0);
+        const AT* b = KRs + ct * kColW;
+        for (int f = grp; f < nf; f += wpu) {
+          const AT t = ok ? (AT)tcol[f * I3] : (AT)0;
+          const AT* bf = b + f * Rp;
+#pragma unroll
+          for (int k = 0; k < kColW; ++k) acc[u][k] = fmat(t, bf[k], acc[u][k]);
         }
       }
     }
-    if (c + 1 < nch) store_kr(((c + 1) & 1) ? kr1 : KRs);
     if (++chunks == kFlush || c + 1 == nch) {
       chunks = 0;
-      if (unit < units) {
 #pragma unroll
-        for (int k = 0; k < kColW; ++k) {
-          const int r = ct * kColW + k;
-          if (r < R) {
-            if (oka) Ms[grp * IR + i3a * R + r] += (double)acc0[k];
-            if (okb) Ms[grp * IR + i3b * R + r] += (double)acc1[k];
+      for (int u = 0; u < 2; ++u) {
+        const int unit = units <= kWarps ? (u == 0 && warp < units * wpu ? warp / wpu : units) : warp + u * kWarps;
+        if (unit < units) {
+          const int ib = unit / nct, ct = unit - (unit / nct) * nct;
+          const int i3 = ib * 32 + lane;
+          if (i3 < I3) {
+#pragma unroll
+            for (int k = 0; k < kColW; ++k) {
+              const int r = ct * kColW + k;
+              if (r < R) Ms[grp * IR + i3 * R + r] += (double)acc[u][k];
+            }
           }
         }
-      }
 #pragma unroll
-      for (int k = 0; k < kColW; ++k) {
-        acc0[k] = (AT)0;
-        acc1[k] = (AT)0;
+        for (int k = 0; k < kColW; ++k) acc[u][k] = (AT)0;
       }
     }
-    __syncthreads();   // this chunk's buffers are rewritten two chunks on
+    __syncthreads();
   }
   __syncthreads();
   for (int e = threadIdx.x; e < IR; e += kThreads) {
@@ -784,14 +742,14 @@ __device__ __forceinline__ void for_own(const Rows& w, int R, F f) {
   }
 }
 
-// Shared memory of the passes (the large region, 128-byte aligned pieces):
+// Shared memory of the passes (the large region):
 // Y = T x_3 B: the factor columns (kMaxI x kBsCols) and two staging tiles
-// (256 fibers x 129 bytes... of T); M^(3): two chunks of T rows, the
-// Khatri-Rao rows, the FP64 totals.
+// (256 fibers x (kIC + 1) elements of T); M^(3): two chunks of kTF rows of
+// T, the Khatri-Rao rows, the FP64 totals.
 constexpr size_t kBsBytes = (size_t)kMaxI * kBsCols * sizeof(double);
-constexpr size_t kTstBytes = 2 * (size_t)kYF * (Stage<double>::kIC + 1) * sizeof(double) + 256;
+constexpr size_t kTstBytes = 2 * (size_t)kThreads * (Stage<double>::kIC + 1) * sizeof(double) + 256;
 constexpr size_t kTchBytes = 2 * (size_t)Stage<float>::kTF * kMaxI * sizeof(float);
-constexpr size_t kKRBytes = 2 * (size_t)Stage<float>::kTF * kMaxR * sizeof(double);
+constexpr size_t kKRBytes = (size_t)Stage<float>::kTF * kMaxR * sizeof(double);
 
 template <typename AT>
 __device__ void do_pass_y(const ManyReq& q, const double* A, const double* D, int rk, int C, char* big) {
