@@ -420,8 +420,8 @@ def run_ours(args, rank, world, local_rank):
 
 # DRAM bytes (read + write) per launch of mttkrp_tc_kernel, mode 0 of the
 # 256^3 R=16 workload, from one ncu --set full capture of the current kernel
-# (dram__bytes_read.sum 67.178496 MB + dram__bytes_write.sum 0.393472 MB).
-TC_NCU_TRAFFIC = 67571968
+# (dram__bytes_read.sum 67.180800 MB + dram__bytes_write.sum 0.438528 MB).
+TC_NCU_TRAFFIC = 67619328
 
 
 def mttkrp_roofline(cp, ctx, t, u, stream, flush, prec):
@@ -561,7 +561,7 @@ def serving_run(cp, ctx, args):
         return rows
 
     routed = sum(1 for r in reqs if r.R * int(np.prod(r.dims)) <= ENGINE_MAX_WORK and max(r.dims) <= 256
-                 and max(r.dims) * r.R <= 8192)
+                 and max(r.dims) * r.R <= 8192)   # (mixed requests; FP64 ones up to an eighth of it)
     res = {"stream": "Poisson 200/s, sides U{16..192}, R U{2..32}, c {0.5,0.9}, noise U(1%,10%), tol {1e-5,1e-7}",
            "slots": args.serve_slots, "generation_s": t_gen,
            "routing": {"cluster_engine_max_entries_x_R": ENGINE_MAX_WORK, "to_cluster_engine": routed,
