@@ -340,6 +340,13 @@ cp_status cp_solve_batch(cp_ctx* ctx, int nreq, const cp_tensor* const* tensors,
 cp_status cp_solve_many(cp_ctx* ctx, int nreq, const cp_tensor* const* tensors, const cp_solve_opts* opts,
                         double* const* u, cp_solve_report* reps, int cluster);
 
+/* Length of cp_solve_many's launches on this context (default 0.5 s): a
+ * cluster that has run this long finishes its current iteration, leaves its
+ * request's state in device memory and stops; the next launch resumes it
+ * (results are the same whatever the length).  CP_ERR_ARG unless
+ * 0 < seconds <= 3600. */
+cp_status cp_many_set_round(cp_ctx* ctx, double seconds);
+
 /* The cluster size cp_solve_many uses for a request when given 0: the size
  * chosen for its bucket (ceil log2 of its entries, ceil log2 R, FP64 or
  * mixed).  The first request of a bucket is timed for a few iterations with

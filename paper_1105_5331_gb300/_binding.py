@@ -34,7 +34,7 @@ EXPORTED = [
     "cp_tensor_destroy", "cp_mttkrp", "cp_mttkrp_variants", "cp_mttkrp_noalloc", "cp_mttkrp_dimtree", "cp_fg", "cp_als_sweep", "cp_normalize",
     "ngmres_step",
     "cp_ls_opts_default", "linesearch", "cp_solve_opts_default", "cp_solve",
-    "cp_solve_batch", "cp_solve_many", "cp_many_plan", "cp_server_create", "cp_server_submit", "cp_server_poll", "cp_server_cancel",
+    "cp_solve_batch", "cp_solve_many", "cp_many_set_round", "cp_many_plan", "cp_server_create", "cp_server_submit", "cp_server_poll", "cp_server_cancel",
     "cp_server_drain", "cp_server_stats", "cp_server_set_engine", "cp_server_destroy",
 ]
 
@@ -109,6 +109,7 @@ def _load():
         "cp_solve_many": (I, [VP, I, C.POINTER(VP), C.POINTER(cp_solve_opts), C.POINTER(VP),
                               C.POINTER(cp_solve_report), I]),
         "cp_many_plan": (I, [VP, VP, C.POINTER(cp_solve_opts), VP, C.POINTER(I)]),
+        "cp_many_set_round": (I, [VP, D]),
         "cp_server_create": (I, [VP, C.c_size_t, I, C.POINTER(VP)]),
         "cp_server_submit": (I, [VP, I, P, I, VP, C.POINTER(cp_solve_opts), VP, VP, C.POINTER(C.c_uint64)]),
         "cp_server_poll": (I, [VP, C.c_uint64, C.POINTER(I), C.POINTER(I), C.POINTER(cp_solve_report),
@@ -405,6 +406,11 @@ def cp_solve_many(ctx, tensors, opts_list, us, cluster: int = 0) -> list:
     reps = (cp_solve_report * n)()
     _check(_lib.cp_solve_many(_h(ctx), n, th, op, up, reps, int(cluster)), allow=(8,))
     return [r.as_dict() for r in reps]
+
+
+def cp_many_set_round(ctx, seconds: float):
+    """Length of cp_solve_many's launches on this context (default 0.5 s)."""
+    _check(_lib.cp_many_set_round(_h(ctx), float(seconds)))
 
 
 def cp_many_plan(ctx, t, opts, u0) -> int:

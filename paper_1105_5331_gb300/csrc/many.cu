@@ -1633,6 +1633,7 @@ struct ManyEngine {
   bool in_flight = false;
   int launched_rounds = 0;
   int max_ctas = 0;                  // CTAs one round may use (<= 0: as many as fit)
+  unsigned long long round_ns = 500ull * 1000 * 1000;   // cp_solve_many's round length
 
   ~ManyEngine() { destroy(); }
 
@@ -2056,11 +2057,13 @@ cp_status many_solve(cp_ctx* ctx, int nreq, const cp_tensor* const* ts, const cp
   // between calls; a larger batch replaces it
   ManyEngine* ep = static_cast<ManyEngine*>(ctx->many);
   if (!ep || ep->cap < nreq) {
+    const unsigned long long round_ns = ep ? ep->round_ns : 500ull * 1000 * 1000;
     if (ep) many_engine_destroy(ep);
     ctx->many = nullptr;
     cp_status cst = CP_OK;
     ep = many_engine_create(ctx, std::max(nreq, 64), &cst);
     if (!ep) return cst;
+    ep->round_ns = round_ns;
     ctx->many = ep;
   }
   ManyEngine& e = *ep;
@@ -2076,7 +2079,7 @@ cp_status many_solve(cp_ctx* ctx, int nreq, const cp_tensor* const* ts, const cp
   cp_status st = CP_OK;
   for (int i = 0; i < nreq && st == CP_OK; ++i) st = e.add(ts[i], opts[i], u[i], cluster, &slot[i]);
   while (st == CP_OK && e.running() > 0) {
-    st = e.launch_round(500ull * 1000 * 1000);
+    st = e.launch_round(e.round_ns);
     if (st != CP_OK) break;
     bool idle = false;
     std::vector<int> fin;
@@ -2142,6 +2145,21 @@ cp_status many_plan(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* o, con
 extern "C" cp_status cp_solve_many(cp_ctx* ctx, int nreq, const cp_tensor* const* tensors, const cp_solve_opts* opts,
                                    double* const* u, cp_solve_report* reps, int cluster) {
   return cpg::many_solve(ctx, nreq, tensors, opts, u, reps, cluster);
+}
+
+extern "C" cp_status cp_many_set_round(cp_ctx* ctx, double seconds) {
+  if (!ctx || !(seconds > 0.0) || seconds > 3600.0) {
+    cpg::set_error("cp_many_set_round: bad arguments");
+    return CP_ERR_ARG;
+  }
+  if (!ctx->many) {
+    cp_status cst = CP_OK;
+    cpg::ManyEngine* e = cpg::many_engine_create(ctx, 64, &cst);
+    if (!e) return cst;
+    ctx->many = e;
+  }
+  static_cast<cpg::ManyEngine*>(ctx->many)->round_ns = (unsigned long long)(seconds * 1e9);
+  return CP_OK;
 }
 
 extern "C" cp_status cp_many_plan(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* opts, const double* u0,

@@ -256,3 +256,33 @@ def test_plan_is_tuned_once_per_bucket(cp, ctx):
         assert cp.cp_many_plan(ctx, t2, o, dev(u2)) == c1
         t2.close()
     t.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_parking_between_launches_changes_nothing(cp, ctx, prec):
+    """Launches of 20 us: every cluster stops after about one iteration and
+    leaves its request's state in device memory, and the next launch resumes
+    it (window, carried contraction, phase, counters); the results must be
+    bit-identical to launches long enough to finish every solve."""
+    reqs = serving_like(4, seed=13)
+    tensors = [cp.cp_tensor_dense(ctx, dev(p.T)) for p, _, _, _ in reqs]
+    opts = []
+    for _, _, R, tol in reqs:
+        o = opts_for(cp, R, prec=prec)
+        o.tol = tol
+        opts.append(o)
+    us_long = [dev(u0) for _, u0, _, _ in reqs]
+    long_ = cp.cp_solve_many(ctx, tensors, opts, us_long, cluster=2)
+    try:
+        cp.cp_many_set_round(ctx, 20e-6)
+        us_short = [dev(u0) for _, u0, _, _ in reqs]
+        short = cp.cp_solve_many(ctx, tensors, opts, us_short, cluster=2)
+    finally:
+        cp.cp_many_set_round(ctx, 0.5)
+    for a, b, ua, ub in zip(long_, short, us_long, us_short):
+        assert torch.equal(ua, ub)
+        for key in ("iters", "restarts", "ls_trials", "ls_failures", "f", "gnorm_over_P", "mixed_iters", "fp64_iters",
+                    "converged"):
+            assert a[key] == b[key], key
+    for t in tensors:
+        t.close()
