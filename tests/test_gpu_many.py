@@ -286,3 +286,20 @@ def test_parking_between_launches_changes_nothing(cp, ctx, prec):
             assert a[key] == b[key], key
     for t in tensors:
         t.close()
+
+
+def test_not_spd_request_is_reported(cp, ctx):
+    """A zero tensor: the first ALS update zeroes A^(1), so Gammabar^(2) is 0
+    and stays singular after the ridge retry (ridge = 1e-12 trace / R = 0):
+    the request ends with CP_ERR_NOT_SPD, as the oracle's mode solve raises."""
+    T = np.zeros((10, 9, 8), dtype=np.float32)
+    rng = np.random.default_rng(3)
+    u0 = synth.initial_guess(rng, T.shape, 2)
+    X = O.DenseTensor(T.astype(np.float64))
+    with pytest.raises(O.NotSPD):
+        O.cp_solve(X, u0, O.SolveOpts(R=2, tol=1e-7))
+    t = cp.cp_tensor_dense(ctx, dev(T))
+    with pytest.raises(cp.CpError) as ei:
+        cp.cp_solve_many(ctx, [t], [opts_for(cp, 2)], [dev(u0)], cluster=2)
+    assert ei.value.status == 5
+    t.close()

@@ -208,3 +208,30 @@ def test_mixed_solve_polish_certifies_fp64_gradient(cp, ctx):
     _, g = O.fg(O.DenseTensor(prob.T), u, 5)
     assert np.linalg.norm(g) / O.n_params(prob.dims, 5) < 1e-7
     t.close()
+
+
+def test_server_reports_a_failing_engine_request_beside_good_ones(cp, ctx):
+    """A zero tensor (CP_ERR_NOT_SPD after the first sweep) among ordinary
+    requests on the cluster engine: its status is reported, the others
+    converge to their solo results."""
+    items = small_requests(3, seed=8)
+    srv = cp.cp_server_create(ctx, 8 << 30, 4)
+    T0 = np.zeros((10, 9, 8), dtype=np.float32)
+    u00 = synth.initial_guess(np.random.default_rng(3), T0.shape, 2)
+    o0 = cp.cp_solve_opts_default(2)
+    out0 = np.zeros_like(u00)
+    id0 = cp.cp_server_submit(srv, T0, o0, u00, out0)
+    outs, ids, opts = [], [], []
+    for r, prob, u0 in items:
+        o = opts_for(cp, r, cp.CP_FP64)
+        out = np.zeros_like(u0)
+        ids.append(cp.cp_server_submit(srv, prob.T, o, u0, out))
+        outs.append(out)
+        opts.append(o)
+    cp.cp_server_drain(srv, 600.0)
+    assert cp.cp_server_poll(srv, id0)[0] == 5
+    for (r, prob, u0), rid, out, o in zip(items, ids, outs, opts):
+        assert cp.cp_server_poll(srv, rid)[0] in (0, 8)
+        u_solo, _ = many_solo(cp, ctx, prob, u0, o)
+        assert np.array_equal(out, u_solo)
+    srv.close()
