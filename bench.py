@@ -583,7 +583,7 @@ def serving_run(cp, ctx, args):
 
 # Requests up to this many entries x R go to the cluster engine (the server's
 # default routing; larger ones to graph slots with tensor-core MTTKRPs).
-ENGINE_MAX_WORK = 1 << 24
+ENGINE_MAX_WORK = 1 << 26
 
 
 def e2e_run(cp, ctx, prob, u0, prec, n, T_host):

@@ -406,7 +406,7 @@ cp_status cp_server_stats(cp_server* s, double* p50_s, double* p99_s, double* so
  * MTTKRPs over the whole GPU); on = 0 sends every request to a graph slot.
  * An engine round uses at most max_ctas CTAs (each takes a whole SM;
  * <= 0: as many as fit), leaving the rest to the graph slots.  Default: on,
- * max_work = 2^24, no CTA limit.  Applies to requests admitted from then on
+ * max_work = 2^26, no CTA limit.  Applies to requests admitted from then on
  * (the CTA limit to the next round).  CP_ERR_UNSUPPORTED when the engine
  * could not be set up on this device. */
 cp_status cp_server_set_engine(cp_server* s, int on, long long max_work, int max_ctas);

@@ -488,7 +488,7 @@ def cp_server_stats(server) -> dict:
             "peak_bytes": peak.value}
 
 
-def cp_server_set_engine(server, on: bool, max_work: int = 1 << 24, max_ctas: int = 0):
+def cp_server_set_engine(server, on: bool, max_work: int = 1 << 26, max_ctas: int = 0):
     """Route requests that fit the cluster engine and have at most max_work
     entries x R to it (on, the default), the rest to graph slots of their
     own; on=False: every request to a graph slot.  max_ctas: CTAs an engine

@@ -124,7 +124,7 @@ struct cp_server {
   cp_ctx* ctx = nullptr;        // caller's context (device)
   ManyEngine* eng = nullptr;    // the cluster engine (3-way dense requests within its limits)
   bool engine_on = true;
-  long long engine_max_work = 1ll << 24;   // entries x R of the largest request routed to the engine
+  long long engine_max_work = 1ll << 26;   // entries x R of the largest request routed to the engine
   std::vector<EngReq> ereq;
   int eng_used = 0;
   double round_s = 0.010;       // engine round length
