@@ -561,7 +561,7 @@ def serving_run(cp, ctx, args):
         return rows
 
     routed = sum(1 for r in reqs if r.R * int(np.prod(r.dims)) <= ENGINE_MAX_WORK and max(r.dims) <= 256
-                 and max(r.dims) * r.R <= 8192)   # (mixed requests; FP64 ones up to an eighth of it)
+                 and max(r.dims) * r.R <= 8192)   # (mixed requests; FP64 ones up to a 64th of it)
     res = {"stream": "Poisson 200/s, sides U{16..192}, R U{2..32}, c {0.5,0.9}, noise U(1%,10%), tol {1e-5,1e-7}",
            "slots": args.serve_slots, "generation_s": t_gen,
            "routing": {"cluster_engine_max_entries_x_R": ENGINE_MAX_WORK, "to_cluster_engine": routed,

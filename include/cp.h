@@ -398,7 +398,7 @@ cp_status cp_server_stats(cp_server* s, double* p50_s, double* p99_s, double* so
 
 /* Route requests that fit cp_solve_many's limits (3-way dense, sides <= 256,
  * I_n R <= 8192, R <= 32, w <= 32) and have at most max_work entries x R
- * (max_work / 8 for CP_FP64 requests; max_work <= 0: no such limit) to the
+ * (max_work / 64 for CP_FP64 requests; max_work <= 0: no such limit) to the
  * cluster engine (on = 1: one
  * persistent launch per round of about 10 ms runs every such running
  * request, each on a thread-block cluster of the size chosen for its bucket,

@@ -277,8 +277,8 @@ struct cp_server {
           if (!pending.empty()) {
             Request* h = pending.front();
             // FP64 requests compute their passes in FP64 on the engine's
-            // few SMs (2 FP64 FMA per clock per SM): an eighth of the limit
-            const long long mw = h->opts.prec == CP_FP64 ? engine_max_work / 8 : engine_max_work;
+            // few SMs (2 FP64 FMA per clock per SM): a 64th of the limit
+            const long long mw = h->opts.prec == CP_FP64 ? engine_max_work / 64 : engine_max_work;
             to_engine = eng && engine_on && h->engine_ok && (engine_max_work <= 0 || h->work <= mw);
             const bool room = to_engine ? eng_used < (int)ereq.size() : free_slot != nullptr;
             if (room && used + h->footprint <= budget) {
