@@ -52,8 +52,14 @@ def parse():
                    choices=["dense_256", "dense_4way", "sparse", "sparse_scaled", "dimtree_256"],
                    help="time only cp_mttkrp on that workload (profiling driver)")
     p.add_argument("--many-only", action="store_true",
-                   help="one cp_solve_many call: 16 requests of 48^3, R=8, mixed, 20 iterations each, clusters of "
-                        "2 CTAs (profiling driver for the cluster engine's kernel)")
+                   help="cp_solve_many calls on one fixed case (default: 16 requests of 48^3, R=8, mixed, 20 "
+                        "iterations each, clusters of 2 CTAs; profiling driver for the cluster engine's kernel)")
+    p.add_argument("--many-shape", type=int, default=48, help="--many-only: side of the cubic tensors")
+    p.add_argument("--many-rank", type=int, default=8, help="--many-only: planted and fitted rank")
+    p.add_argument("--many-count", type=int, default=16, help="--many-only: requests per call")
+    p.add_argument("--many-iters", type=int, default=20, help="--many-only: iterations per request")
+    p.add_argument("--many-cluster", type=int, default=2, help="--many-only: CTAs per cluster")
+    p.add_argument("--many-prec", default="mixed", choices=["mixed", "fp64"], help="--many-only: precision")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--accuracy-report", default=None, choices=["dense_256", "dense_4way"],
                    help="mixed (with FP64 polish) against FP64 solves of one workload; one JSON line")
@@ -750,31 +756,39 @@ def run_precision_table(args):
 
 
 def run_many_only(args):
-    """The cluster engine on a small fixed case (profiling driver): 16
-    requests of 48x48x48, planted R=8, c=0.5, 5 % noise, mixed precision,
-    exactly 20 iterations each, clusters of 2 CTAs, one cp_solve_many call;
-    prints its wall time."""
+    """The cluster engine on one fixed case (profiling driver): `many-count`
+    requests of a cubic tensor of side `many-shape`, planted rank
+    `many-rank`, c=0.5, 5 % noise, exactly `many-iters` iterations each in
+    `many-prec`, clusters of `many-cluster` CTAs; `reps` cp_solve_many calls
+    from the same start; prints the wall time of each and the best call's
+    time per iteration."""
     import numpy as np
     import torch
     import synth
     import paper_1105_5331_gb300 as cp
+    S, R, n = args.many_shape, args.many_rank, args.many_count
     ctx = cp.cp_ctx_create(0, torch.cuda.current_stream())
-    ts, us, opts = [], [], []
-    for k in range(16):
+    ts, u0s, opts = [], [], []
+    for k in range(n):
         rng = synth.rng_for(33, k)
-        prob = synth.dense_problem(rng, (48, 48, 48), 8, 0.5, eta=0.05, dtype=np.float32)
+        prob = synth.dense_problem(rng, (S, S, S), R, 0.5, eta=0.05, dtype=np.float32)
         ts.append(cp.cp_tensor_dense(ctx, prob.T))
-        us.append(synth.initial_guess(rng, prob.dims, 8))
-        o = cp.cp_solve_opts_default(8)
-        o.prec = cp.CP_MIXED_BF16X3
+        u0s.append(synth.initial_guess(rng, prob.dims, R))
+        o = cp.cp_solve_opts_default(R)
+        o.prec = cp.CP_MIXED_BF16X3 if args.many_prec == "mixed" else cp.CP_FP64
         o.tol = 1e-300
-        o.maxit = 20
+        o.maxit = args.many_iters
         opts.append(o)
-    t0 = time.perf_counter()
-    reps = cp.cp_solve_many(ctx, ts, opts, us, cluster=2)
-    dt = time.perf_counter() - t0
-    print(json.dumps({"many_only": "16 x 48^3 R=8 mixed, 20 iterations, clusters of 2", "wall_s": dt,
-                      "iters": sum(r["iters"] for r in reps)}))
+    walls, iters = [], 0
+    for _ in range(max(1, args.reps)):
+        us = [u.copy() for u in u0s]
+        t0 = time.perf_counter()
+        reps = cp.cp_solve_many(ctx, ts, opts, us, cluster=args.many_cluster)
+        walls.append(time.perf_counter() - t0)
+        iters = max(r["iters"] for r in reps)
+    print(json.dumps({"many_only": f"{n} x {S}^3 R={R} {args.many_prec}, {args.many_iters} iterations, "
+                                   f"clusters of {args.many_cluster}",
+                      "wall_s": walls, "iters": iters, "us_per_iter_best": min(walls) / max(iters, 1) * 1e6}))
     for t in ts:
         t.close()
     ctx.close()

@@ -51,6 +51,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxR = 32;      // rank limit
 constexpr int kMaxW = 32;      // window limit
+constexpr int kHLd = kMaxW + 1; // row stride of the window system in shared memory
 constexpr int kMaxC = 8;       // cluster size limit (portable clusters)
 constexpr int kMaxI = 256;     // side limit
 constexpr int kMaxIR = 8192;   // I_n R limit (the M^(3) accumulators live in shared memory)
@@ -113,7 +114,7 @@ struct EngSh {
   ManyCtl c;
   double A[kMaxR * kMaxR];        // Gammabar and its inverse
   double A0[kMaxR * kMaxR];       // a copy for the ridge retry
-  double H[kMaxW * kMaxW];
+  double H[kMaxW * kHLd];         // window system, rows padded against bank conflicts
   double rhs[kMaxW];
   double alpha[kMaxW];
   double nu[3 * kMaxR];
@@ -127,6 +128,7 @@ struct EngSh {
   double bcast[8];
   int order[kMaxR];
   int order2[kMaxR];
+  double gp[kThreads];            // Gram partials of the row groups
   unsigned long long t0;
   int task;
   int flag;
@@ -418,7 +420,7 @@ __device__ __noinline__ void pass_m3(const TT* __restrict__ T, int J, int I2, in
 #pragma unroll
             for (int k = 0; k < kColW; ++k) {
               const int r = ct * kColW + k;
-              if (r < R) Ms[grp * IR + i3 * R + r] += (double)acc[u][k];
+              if (r < R) Ms[grp * IR + r * I3 + i3] += (double)acc[u][k];
             }
           }
         }
@@ -430,8 +432,9 @@ __device__ __noinline__ void pass_m3(const TT* __restrict__ T, int J, int I2, in
   }
   __syncthreads();
   for (int e = threadIdx.x; e < IR; e += kThreads) {
+    const int i3 = e / R, r = e - (e / R) * R;
     double v = 0.0;
-    for (int g = 0; g < wpu; ++g) v += Ms[g * IR + e];
+    for (int g = 0; g < wpu; ++g) v += Ms[g * IR + r * I3 + i3];
     out[e] = v;
   }
 }
@@ -522,15 +525,40 @@ __device__ void contract_variants(const AT* __restrict__ Z, int I1, int I2, int 
 
 // ------------------------------------------------------------ FP64 helpers
 
-// Partial X^T Y over rows [lo, hi) of two I x R row-major matrices.
+// Partial X^T Y over rows [lo, hi) of two I x R row-major matrices.  For
+// R^2 below the block size and long row ranges the rows are dealt
+// round-robin to up to kThreads / R^2 thread groups of at least 16 rows
+// each (shorter dependent FMA chains) whose sums are added in group order
+// through gp (kThreads doubles of shared memory).
 __device__ void gram_part(const double* __restrict__ X, const double* __restrict__ Yv, int lo, int hi, int R,
-                          double* __restrict__ out) {
-  for (int e = threadIdx.x; e < R * R; e += kThreads) {
-    const int r = e / R, s = e - (e / R) * R;
-    double acc = 0.0;
-    for (int i = lo; i < hi; ++i) acc = fma(X[(size_t)i * R + r], Yv[(size_t)i * R + s], acc);
-    out[e] = acc;
+                          double* __restrict__ out, double* gp) {
+  const int RR = R * R;
+  const int G = min(RR < kThreads ? kThreads / RR : 1, (hi - lo) / 16);
+  if (G <= 1) {
+    for (int e = threadIdx.x; e < RR; e += kThreads) {
+      const int r = e / R, s = e - (e / R) * R;
+      double acc = 0.0;
+      for (int i = lo; i < hi; ++i) acc = fma(X[(size_t)i * R + r], Yv[(size_t)i * R + s], acc);
+      out[e] = acc;
+    }
+    return;
   }
+  const int t = threadIdx.x;
+  double acc = 0.0;
+  if (t < G * RR) {
+    const int g = t / RR, e = t - (t / RR) * RR;
+    const int r = e / R, s = e - (e / R) * R;
+    for (int i = lo + g; i < hi; i += G) acc = fma(X[(size_t)i * R + r], Yv[(size_t)i * R + s], acc);
+  }
+  __syncthreads();
+  gp[t] = acc;
+  __syncthreads();
+  for (int e = t; e < RR; e += kThreads) {
+    double v = 0.0;
+    for (int g = 0; g < G; ++g) v += gp[g * RR + e];
+    out[e] = v;
+  }
+  __syncthreads();
 }
 
 // In-place inverse of the SPD matrix A (R x R, shared) by Gauss-Jordan
@@ -659,31 +687,31 @@ __device__ void window_solve(int m, double eps, EngSh& sh) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     double dmax = 0.0;
-    for (int j = 0; j < m; ++j) dmax = fmax(dmax, sh.H[j * kMaxW + j]);
+    for (int j = 0; j < m; ++j) dmax = fmax(dmax, sh.H[j * kHLd + j]);
     if (dmax == 0.0) {
       if (lane < m) sh.alpha[lane] = 0.0;
     } else {
       const double delta = eps * dmax;
-      if (lane < m) sh.H[lane * kMaxW + lane] += delta;
+      if (lane < m) sh.H[lane * kHLd + lane] += delta;
       __syncwarp();
       // right-looking Cholesky, lower triangle in place (lane = row)
       // (Newton-refined square roots and reciprocals: each IEEE FP64 divide
       // or sqrt is a serial chain of ~650 cycles in this one-warp solve)
       for (int k = 0; k < m; ++k) {
         // 1/sqrt first: the pivot and its reciprocal from one Newton chain
-        const double hk = sh.H[k * kMaxW + k];
+        const double hk = sh.H[k * kHLd + k];
         const double idk = rsqrt_nr(hk);   // NaN for a pivot <= 0 (not positive definite)
         const double dk = hk * idk;
         __syncwarp();
         if (lane == k) {
-          sh.H[k * kMaxW + k] = dk;
+          sh.H[k * kHLd + k] = dk;
           sh.sc2[k] = idk;
         }
-        if (lane > k && lane < m) sh.H[lane * kMaxW + k] *= idk;
+        if (lane > k && lane < m) sh.H[lane * kHLd + k] *= idk;
         __syncwarp();
         if (lane > k && lane < m) {
-          const double lk = sh.H[lane * kMaxW + k];
-          for (int j = k + 1; j <= lane; ++j) sh.H[lane * kMaxW + j] -= lk * sh.H[j * kMaxW + k];
+          const double lk = sh.H[lane * kHLd + k];
+          for (int j = k + 1; j <= lane; ++j) sh.H[lane * kHLd + j] -= lk * sh.H[j * kHLd + k];
         }
         __syncwarp();
       }
@@ -692,13 +720,13 @@ __device__ void window_solve(int m, double eps, EngSh& sh) {
       for (int k = 0; k < m; ++k) {
         const double yk = __shfl_sync(0xffffffffu, y, k) * sh.sc2[k];
         if (lane == k) y = yk;
-        if (lane > k && lane < m) y -= sh.H[lane * kMaxW + k] * yk;
+        if (lane > k && lane < m) y -= sh.H[lane * kHLd + k] * yk;
       }
       double a = y;
       for (int k = m - 1; k >= 0; --k) {
         const double ak = __shfl_sync(0xffffffffu, a, k) * sh.sc2[k];
         if (lane == k) a = ak;
-        if (lane < k) a -= sh.H[k * kMaxW + lane] * ak;
+        if (lane < k) a -= sh.H[k * kHLd + lane] * ak;
       }
       if (lane < m) sh.alpha[lane] = a;
     }
@@ -921,7 +949,7 @@ __device__ bool run_start(EngSh& sh, char* big, int rk, int C, unsigned long lon
   double* my = q.part + (size_t)rk * ld;
   const Rows w = rows_of(q, rk, C);
   if (sh.c.start == 2) {
-    for (int n = 0; n < 3; ++n) gram_part(q.x + w.off[n], q.x + w.off[n], w.lo[n], w.hi[n], R, my + BA + n * RR);
+    for (int n = 0; n < 3; ++n) gram_part(q.x + w.off[n], q.x + w.off[n], w.lo[n], w.hi[n], R, my + BA + n * RR, sh.gp);
     cl_sync();
     for (int t = threadIdx.x; t < 3 * R; t += kThreads) {
       const int n = t / R, r = t - (t / R) * R;
@@ -1016,7 +1044,7 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
   if (!gammabar_inverse(R, sh)) return fail_spd();
   contract_m1<AT>(Ysw, ysw, 0, q.I1, q.I2, R, u + q.off2, q.M1, rk, C);
   als_rows(q.M1, R, w.lo[0], w.hi[0], sw, sh);
-  gram_part(sw, sw, w.lo[0], w.hi[0], R, my + BA);
+  gram_part(sw, sw, w.lo[0], w.hi[0], R, my + BA, sh.gp);
   cl_sync();
   __syncthreads();
   for (int e = threadIdx.x; e < RR; e += kThreads) {
@@ -1027,7 +1055,7 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
   if (!gammabar_inverse(R, sh)) return fail_spd();
   contract_m2<AT>(Ysw, ysw, 0, q.I1, q.I2, R, sw, q.M2, rk, C);
   als_rows(q.M2, R, w.lo[1], w.hi[1], sw + q.off2, sh);
-  gram_part(sw + q.off2, sw + q.off2, w.lo[1], w.hi[1], R, my + BB);
+  gram_part(sw + q.off2, sw + q.off2, w.lo[1], w.hi[1], R, my + BB, sh.gp);
   cl_sync();
   if (rk == 0)
     for (int e = threadIdx.x; e < RR; e += kThreads) q.Gs[RR + e] = psum(q.part + BB, ld, C, e);
@@ -1040,7 +1068,7 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
   hadamard_into(q.Gs, q.Gs + RR, R, sh.A0);
   if (!gammabar_inverse(R, sh)) return fail_spd();
   als_rows(q.M3s, R, w.lo[2], w.hi[2], sw + q.off3, sh);
-  gram_part(sw + q.off3, sw + q.off3, w.lo[2], w.hi[2], R, my + BB);
+  gram_part(sw + q.off3, sw + q.off3, w.lo[2], w.hi[2], R, my + BB, sh.gp);
   cl_sync();
 
   // ---- ubar = normalise(swept) (R3, R4); its Grams and M^(3) follow
@@ -1156,8 +1184,8 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
         ++j;
       }
       const int l = j + rem;
-      sh.H[j * kMaxW + l] = v;
-      sh.H[l * kMaxW + j] = v;
+      sh.H[j * kHLd + l] = v;
+      sh.H[l * kHLd + j] = v;
     } else {
       sh.rhs[t - npairs] = v;
     }
@@ -1202,8 +1230,8 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
   }
   __syncthreads();
   for (int n = 0; n < 3; ++n) {
-    gram_part(ub + w.off[n], q.d + w.off[n], w.lo[n], w.hi[n], R, my + BB + n * RR);
-    gram_part(q.d + w.off[n], q.d + w.off[n], w.lo[n], w.hi[n], R, my + BB + (3 + n) * RR);
+    gram_part(ub + w.off[n], q.d + w.off[n], w.lo[n], w.hi[n], R, my + BB + n * RR, sh.gp);
+    gram_part(q.d + w.off[n], q.d + w.off[n], w.lo[n], w.hi[n], R, my + BB + (3 + n) * RR, sh.gp);
   }
   cl_sync();
   const double slope = psum(q.part + SCA, ld, C, 0);
