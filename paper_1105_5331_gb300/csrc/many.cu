@@ -236,8 +236,11 @@ __device__ __forceinline__ void cp_async_wait() {
 template <typename TT>
 struct Stage {
   static constexpr int kIC = 128 / (int)sizeof(TT);   // i3 per sub-tile in Y = T x_3 B
-  static constexpr int kTF = 128 / (int)sizeof(TT);   // fibers per chunk in M^(3)
+  static constexpr int kTF = 128 / (int)sizeof(TT);   // fibers per chunk in M^(3) at I3 = kMaxI
 };
+// M^(3)'s shared regions: the two T chunks and the Khatri-Rao rows.
+constexpr size_t kTchBytes = 2 * (size_t)Stage<float>::kTF * kMaxI * sizeof(float);
+constexpr size_t kKRBytes = 16384;
 
 // Y[j][c0 + c] = sum_{i3} T[j][i3] B[i3][c] for the CTA's fibers j, where B
 // is A (I3 x R) or [A | D] (I3 x 2R); Y has row stride ys (AT elements).
@@ -338,15 +341,24 @@ __device__ __noinline__ void pass_y(const TT* __restrict__ T, int J, int I3, int
 // tiles each gets kWarps / tiles warps that take every (kWarps / tiles)-th
 // fiber of a chunk, with more a warp keeps two tiles.  Register sums are
 // FP32 (or FP64) and are added into FP64 shared totals, one set per fiber
-// group, every kFlush chunks; the groups are added in order at the end.
-// (Measured against 64-row tiles with the next chunk's Khatri-Rao rows
-// loaded ahead and against a three-deep ring: 8-10 % faster.)
+// group, every kFlush kTF fibers; the groups are added in order at the end.
+// A chunk holds F = kTF 2^k fibers, as many as the two T buffers and the
+// Khatri-Rao rows allow (up to kFlush kTF), so short rows come in longer
+// chunks (fewer barriers and Khatri-Rao builds per fiber); the flush points
+// and each group's fibers do not depend on F.  (Measured against 64-row
+// tiles with the next chunk's Khatri-Rao rows loaded ahead and against a
+// three-deep ring: 8-10 % faster.)
 template <typename TT, typename AT>
 __device__ __noinline__ void pass_m3(const TT* __restrict__ T, int J, int I2, int I3, int R, const double* __restrict__ A,
                                      const double* __restrict__ B, double* __restrict__ out, int rk, int C, TT* Tst,
                                      AT* KRs, double* Ms) {
   constexpr int kTF = Stage<TT>::kTF;
   const int Rp = (R + kColW - 1) / kColW * kColW;
+  int F = kTF;
+  while (2 * F <= kFlush * kTF && 2 * (size_t)(2 * F) * I3 * sizeof(TT) <= kTchBytes &&
+         (size_t)(2 * F) * Rp * sizeof(AT) <= kKRBytes)
+    F *= 2;
+  const int flush_every = kFlush * kTF / F;
   const int nib = (I3 + 31) / 32, nct = Rp / kColW;
   const int units = nib * nct;
   const int wpu = units <= kWarps ? kWarps / units : 1;
@@ -354,7 +366,7 @@ __device__ __noinline__ void pass_m3(const TT* __restrict__ T, int J, int I2, in
   const int jlo = lo_of(J, rk, C), jhi = lo_of(J, rk + 1, C);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = warp % wpu;
-  TT* const buf1 = Tst + kTF * kMaxI;
+  TT* const buf1 = Tst + kTchBytes / 2 / sizeof(TT);
   for (int e = threadIdx.x; e < wpu * IR; e += kThreads) Ms[e] = 0.0;
   AT acc[2][kColW];
 #pragma unroll
@@ -362,18 +374,18 @@ __device__ __noinline__ void pass_m3(const TT* __restrict__ T, int J, int I2, in
 #pragma unroll
     for (int k = 0; k < kColW; ++k) acc[u][k] = (AT)0;
   auto issue = [&](int j0, TT* dst) {
-    const int n = min(kTF, jhi - j0) * I3;
+    const int n = min(F, jhi - j0) * I3;
     const TT* src = T + (size_t)j0 * I3;
     for (int e = threadIdx.x; e < n; e += kThreads) cp_async_el(dst + e, src + e);
     cp_async_commit();
   };
-  const int nch = (jhi - jlo + kTF - 1) / kTF;
+  const int nch = (jhi - jlo + F - 1) / F;
   if (nch > 0) issue(jlo, Tst);
   int chunks = 0;
   for (int c = 0; c < nch; ++c) {
-    const int j0 = jlo + c * kTF;
-    const int nf = min(kTF, jhi - j0);
-    for (int e = threadIdx.x; e < kTF * Rp; e += kThreads) {
+    const int j0 = jlo + c * F;
+    const int nf = min(F, jhi - j0);
+    for (int e = threadIdx.x; e < F * Rp; e += kThreads) {
       const int f = e / Rp, r = e - (e / Rp) * Rp;
       AT v = (AT)0;
       if (f < nf && r < R) {
@@ -384,7 +396,7 @@ __device__ __noinline__ void pass_m3(const TT* __restrict__ T, int J, int I2, in
       KRs[e] = v;
     }
     if (c + 1 < nch) {
-      issue(j0 + kTF, ((c + 1) & 1) ? buf1 : Tst);
+      issue(j0 + F, ((c + 1) & 1) ? buf1 : Tst);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -408,7 +420,7 @@ __device__ __noinline__ void pass_m3(const TT* __restrict__ T, int J, int I2, in
         }
       }
     }
-    if (++chunks == kFlush || c + 1 == nch) {
+    if (++chunks == flush_every || c + 1 == nch) {
       chunks = 0;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -772,12 +784,11 @@ __device__ __forceinline__ void for_own(const Rows& w, int R, F f) {
 
 // Shared memory of the passes (the large region):
 // Y = T x_3 B: the factor columns (kMaxI x kBsCols) and two staging tiles
-// (256 fibers x (kIC + 1) elements of T); M^(3): two chunks of kTF rows of
-// T, the Khatri-Rao rows, the FP64 totals.
+// (256 fibers x (kIC + 1) elements of T); M^(3): two chunks of rows of T
+// (kTF rows of the longest side each, more rows of shorter ones), the
+// Khatri-Rao rows, the FP64 totals.
 constexpr size_t kBsBytes = (size_t)kMaxI * kBsCols * sizeof(double);
 constexpr size_t kTstBytes = 2 * (size_t)kThreads * (Stage<double>::kIC + 1) * sizeof(double) + 256;
-constexpr size_t kTchBytes = 2 * (size_t)Stage<float>::kTF * kMaxI * sizeof(float);
-constexpr size_t kKRBytes = (size_t)Stage<float>::kTF * kMaxR * sizeof(double);
 
 template <typename AT>
 __device__ void do_pass_y(const ManyReq& q, const double* A, const double* D, int rk, int C, char* big) {
