@@ -412,7 +412,21 @@ __device__ __noinline__ void pass_m3(const TT* __restrict__ T, int J, int I2, in
         const bool ok = i3 < I3;
         const TT* tcol = tb + (ok ? i3 : 0);
         const AT* b = KRs + ct * kColW;
-        for (int f = grp; f < nf; f += wpu) {
+        int f = grp;
+        // four fibers at a time, their T values loaded first (the same
+        // order of additions as one at a time)
+        for (; f + 3 * wpu < nf; f += 4 * wpu) {
+          AT t[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) t[q] = ok ? (AT)tcol[(f + q * wpu) * I3] : (AT)0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const AT* bf = b + (f + q * wpu) * Rp;
+#pragma unroll
+            for (int k = 0; k < kColW; ++k) acc[u][k] = fmat(t[q], bf[k], acc[u][k]);
+          }
+        }
+        for (; f < nf; f += wpu) {
           const AT t = ok ? (AT)tcol[f * I3] : (AT)0;
           const AT* bf = b + f * Rp;
 #pragma unroll
