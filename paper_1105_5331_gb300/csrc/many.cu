@@ -57,7 +57,6 @@ constexpr int kMaxI = 256;     // side limit
 constexpr int kMaxIR = 8192;   // I_n R limit (the M^(3) accumulators live in shared memory)
 constexpr int kColW = 16;      // columns per register tile in the passes
 constexpr int kBsCols = 32;    // columns of the factor staged at once for Y = T x_3 B
-constexpr int kFib = 64;       // fibers per Khatri-Rao chunk for M^(3)
 constexpr int kFlush = 8;      // chunks between FP64 flushes of the FP32 accumulators
 constexpr int kTile = 128;     // window elements per shared-memory tile
 constexpr int kTileLd = kTile + 1;
@@ -95,6 +94,7 @@ struct ManyReq {
   double* Y2;         // J x R: T x_3 A^(3) of the accepted point's normalisation
   double *M1, *M2, *M3, *M3s;   // M^(n) at the current point; the swept point's M^(3)
   double *V1, *V2;    // line-search variants of modes 1, 2: 4 x I1 x R, 4 x I2 x R
+  double* K;          // w x w: g_a^T g_b of the window's gradients by ring slot (mixed phase)
   double* part;       // kMaxC x part_ld partials: two large regions of big_ld, two of 128 scalars
   int part_ld, big_ld;
   double *Gu, *Gs, *Gb, *Gad, *Gdd, *Gx;   // Grams (3 x R x R): u, swept, ubar, ubar^T d, d^T d, x
@@ -1136,10 +1136,68 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
     if (threadIdx.x == 0) my[SCA] = inner;
   }
 
-  // ---- Step II: window dots over the CTA's elements (p_j = gbar - g_j)
+  // ---- Step II: window dots over the CTA's elements (p_j = gbar - g_j).
+  // The FP64 phase forms P^T P and P^T gbar directly.  The mixed phase keeps
+  // the window Gram K_jl = g_j^T g_l between iterations and forms only
+  // c_j = gbar^T g_j, gbar^T gbar and the newest entry's row of K (2m + 1
+  // dots instead of m(m + 3)/2); then (P^T P)_jl = gbar^T gbar - c_j - c_l
+  // + K_jl.  The cancellation in that sum costs about u |g|^2 / |p|^2 of
+  // relative accuracy, far below the FP32-level error of the mixed phase's
+  // gradients.
+  constexpr bool kGramKept = sizeof(AT) == sizeof(float);
   const int m = sh.c.win_m, wstart = sh.c.win_start;
   const int npairs = m * (m + 1) / 2, ntask = npairs + m;
-  {
+  if (kGramKept) {
+    // task t < m: gbar . g_t; t = m: gbar . gbar; m < t <= 2m: g_{m-1} . g_{t-m-1}.
+    // Each task's elements are split over S threads (k = s, s + S, ...),
+    // whose sums are added in order at the end.
+    double* tile = (double*)big;                 // m x kTileLd, then gbar
+    double* gt = tile + (size_t)kMaxW * kTileLd;
+    const int nt = 2 * m + 1;
+    const int S = kThreads / nt;
+    const int t = threadIdx.x;
+    const int task = t / S, sidx = t - (t / S) * S;
+    int ta = -1, tb = -1;                        // tile rows; m is gbar
+    if (task < m) {
+      ta = m;
+      tb = task;
+    } else if (task == m) {
+      ta = m;
+      tb = m;
+    } else if (task < nt) {
+      ta = m - 1;
+      tb = task - m - 1;
+    }
+    double acc = 0.0;
+    for (int n = 0; n < 3; ++n) {
+      const int e_lo = w.off[n] + w.lo[n] * R, e_hi = w.off[n] + w.hi[n] * R;
+      for (int e0 = e_lo; e0 < e_hi; e0 += kTile) {
+        const int ne = min(kTile, e_hi - e0);
+        __syncthreads();
+        for (int x = threadIdx.x; x < m * kTile; x += kThreads) {
+          const int j = x / kTile, k = x - (x / kTile) * kTile;
+          tile[j * kTileLd + k] = k < ne ? q.G[(size_t)ring(wstart, j, q.w) * q.P + e0 + k] : 0.0;
+        }
+        for (int k = threadIdx.x; k < kTile; k += kThreads) gt[k] = k < ne ? q.gb[e0 + k] : 0.0;
+        __syncthreads();
+        if (ta >= 0) {
+          const double* a = ta == m ? gt : tile + ta * kTileLd;
+          const double* b = tb == m ? gt : tile + tb * kTileLd;
+          double v = acc;
+          for (int k = sidx; k < ne; k += S) v = fma(a[k], b[k], v);
+          acc = v;
+        }
+      }
+    }
+    __syncthreads();
+    sh.gp[t] = acc;
+    __syncthreads();
+    for (int k = threadIdx.x; k < nt; k += kThreads) {
+      double v = 0.0;
+      for (int s2 = 0; s2 < S; ++s2) v += sh.gp[k * S + s2];
+      my[BA + k] = v;
+    }
+  } else {
     double* tile = (double*)big;                 // m x kTileLd, then gbar
     double* gt = tile + (size_t)kMaxW * kTileLd;
     double acc[3] = {0.0, 0.0, 0.0};
@@ -1200,19 +1258,50 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
     const double model = model_norm2(q.Gb, R, sh);
     if (threadIdx.x == 0) sh.bcast[0] = 0.5 * (q.normT2 - 2.0 * inner + model);
   }
-  for (int t = threadIdx.x; t < ntask; t += kThreads) {
-    const double v = psum(q.part + BA, ld, C, t);
-    if (t < npairs) {
-      int j = 0, rem = t;
-      while (rem >= m - j) {
-        rem -= m - j;
-        ++j;
+  if (kGramKept) {
+    const double gg = psum(q.part + BA, ld, C, m);
+    for (int t = threadIdx.x; t < ntask; t += kThreads) {
+      if (t < npairs) {
+        int j = 0, rem = t;
+        while (rem >= m - j) {
+          rem -= m - j;
+          ++j;
+        }
+        const int l = j + rem;   // j <= l
+        const double kjl = l == m - 1 ? psum(q.part + BA, ld, C, m + 1 + j)
+                                      : q.K[(size_t)ring(wstart, j, q.w) * q.w + ring(wstart, l, q.w)];
+        const double v = gg - psum(q.part + BA, ld, C, j) - psum(q.part + BA, ld, C, l) + kjl;
+        sh.H[j * kHLd + l] = v;
+        sh.H[l * kHLd + j] = v;
+      } else {
+        const int j = t - npairs;
+        sh.rhs[j] = psum(q.part + BA, ld, C, j) - gg;
       }
-      const int l = j + rem;
-      sh.H[j * kHLd + l] = v;
-      sh.H[l * kHLd + j] = v;
-    } else {
-      sh.rhs[t - npairs] = v;
+    }
+    if (rk == 0) {
+      const int sn = ring(wstart, m - 1, q.w);
+      for (int l = threadIdx.x; l < m; l += kThreads) {
+        const int sl = ring(wstart, l, q.w);
+        const double v = psum(q.part + BA, ld, C, m + 1 + l);
+        q.K[(size_t)sn * q.w + sl] = v;
+        q.K[(size_t)sl * q.w + sn] = v;
+      }
+    }
+  } else {
+    for (int t = threadIdx.x; t < ntask; t += kThreads) {
+      const double v = psum(q.part + BA, ld, C, t);
+      if (t < npairs) {
+        int j = 0, rem = t;
+        while (rem >= m - j) {
+          rem -= m - j;
+          ++j;
+        }
+        const int l = j + rem;
+        sh.H[j * kHLd + l] = v;
+        sh.H[l * kHLd + j] = v;
+      } else {
+        sh.rhs[t - npairs] = v;
+      }
     }
   }
   window_solve(m, q.eps, sh);
@@ -1550,6 +1639,7 @@ size_t job_layout(ManyReq& q, char* base) {
   q.M3s = take(q.I3 * R);
   q.V1 = take(4 * q.I1 * R);
   q.V2 = take(4 * q.I2 * R);
+  q.K = take((int64_t)q.w * q.w);
   q.part = take(kMaxC * ld);
   q.Gu = take(3 * RR);
   q.Gs = take(3 * RR);
