@@ -804,14 +804,15 @@ __device__ __forceinline__ void for_own(const Rows& w, int R, F f) {
 constexpr size_t kBsBytes = (size_t)kMaxI * kBsCols * sizeof(double);
 constexpr size_t kTstBytes = 2 * (size_t)kThreads * (Stage<double>::kIC + 1) * sizeof(double) + 256;
 
+// T x_3 A into the Y buffer: row stride ys, columns c0 .. c0 + R - 1.
 template <typename AT>
-__device__ void do_pass_y(const ManyReq& q, const double* A, const double* D, int rk, int C, char* big) {
-  const int ys = D ? 2 * q.R : q.R;
+__device__ void do_pass_y(const ManyReq& q, const double* A, int ys, int c0, int rk, int C, char* big) {
   AT* Bs = (AT*)big;
+  AT* Y = (AT*)q.Y + c0;
   if (q.t64)
-    pass_y<double, AT>((const double*)q.T, q.J, q.I3, q.R, A, D, (AT*)q.Y, ys, rk, C, Bs, (double*)(big + kBsBytes));
+    pass_y<double, AT>((const double*)q.T, q.J, q.I3, q.R, A, nullptr, Y, ys, rk, C, Bs, (double*)(big + kBsBytes));
   else
-    pass_y<float, AT>((const float*)q.T, q.J, q.I3, q.R, A, D, (AT*)q.Y, ys, rk, C, Bs, (float*)(big + kBsBytes));
+    pass_y<float, AT>((const float*)q.T, q.J, q.I3, q.R, A, nullptr, Y, ys, rk, C, Bs, (float*)(big + kBsBytes));
 }
 
 template <typename AT>
@@ -993,7 +994,7 @@ __device__ bool run_start(EngSh& sh, char* big, int rk, int C, unsigned long lon
     cl_sync();
   }
   const double* u = q.u;
-  do_pass_y<AT>(q, u + q.off3, nullptr, rk, C, big);
+  do_pass_y<AT>(q, u + q.off3, R, 0, rk, C, big);
   cl_sync();
   contract_m1<AT>((const AT*)q.Y, R, 0, q.I1, q.I2, R, u + q.off2, q.M1, rk, C);
   contract_m2<AT>((const AT*)q.Y, R, 0, q.I1, q.I2, R, u, q.M2, rk, C);
@@ -1062,7 +1063,7 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
   const AT* Ysw = ysrc == 2 ? (const AT*)q.Y2 : (const AT*)q.Y;
   const int ysw = ysrc == 3 ? 2 * R : R;
   if (ysrc == 0) {
-    do_pass_y<AT>(q, u + q.off3, nullptr, rk, C, big);
+    do_pass_y<AT>(q, u + q.off3, R, 0, rk, C, big);
     cl_sync();
   }
   hadamard_into(q.Gu + RR, q.Gu + 2 * RR, R, sh.A0);
@@ -1118,12 +1119,13 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
   }
   cl_sync();
 
-  // ---- f and g at ubar: modes 1 and 2 from Y' = T x_3 Abar^(3)
+  // ---- f and g at ubar: modes 1 and 2 from Y' = T x_3 Abar^(3), kept in
+  // the first R columns of Y (row stride 2R) for the line search's Z
   const double* ub = q.ub;
-  do_pass_y<AT>(q, ub + q.off3, nullptr, rk, C, big);
+  do_pass_y<AT>(q, ub + q.off3, 2 * R, 0, rk, C, big);
   cl_sync();
-  contract_m1<AT>((const AT*)q.Y, R, 0, q.I1, q.I2, R, ub + q.off2, q.M1, rk, C);
-  contract_m2<AT>((const AT*)q.Y, R, 0, q.I1, q.I2, R, ub, q.M2, rk, C);
+  contract_m1<AT>((const AT*)q.Y, 2 * R, 0, q.I1, q.I2, R, ub + q.off2, q.M1, rk, C);
+  contract_m2<AT>((const AT*)q.Y, 2 * R, 0, q.I1, q.I2, R, ub, q.M2, rk, C);
   __syncthreads();
   grad_rows(q, w, ub, q.Gb, q.M1, q.M2, q.M3, q.gb, sh);
   {
@@ -1357,7 +1359,7 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
   }
   __syncthreads();
   // (after a restart the Y buffer still holds Y' = T x_3 Abar^(3))
-  if (restart) return keep_ubar(sh, rk, C, true, 1, t0, budget);   // R7
+  if (restart) return keep_ubar(sh, rk, C, true, 3, t0, budget);   // R7
 
   // ---- Step III: the line polynomial phi(beta) = f(ubar + beta d)
   if (rk == 0)
@@ -1365,7 +1367,8 @@ __device__ bool run_iter(EngSh& sh, char* big, int rk, int C, unsigned long long
       q.Gad[e] = psum(q.part + BB, ld, C, e);
       q.Gdd[e] = psum(q.part + BB, ld, C, 3 * RR + e);
     }
-  do_pass_y<AT>(q, ub + q.off3, q.d + q.off3, rk, C, big);
+  // Z = T x_3 [Abar^(3) | D^(3)]: the D columns beside Y'
+  do_pass_y<AT>(q, q.d + q.off3, 2 * R, R, rk, C, big);
   cl_sync();
   contract_variants<AT>((const AT*)q.Y, q.I1, q.I2, R, ub, q.d, ub + q.off2, q.d + q.off2, q.V1, q.V2, rk, C);
   __syncthreads();
