@@ -91,6 +91,8 @@ def parse():
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--cpu-c1", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--cpu-iters", type=int, default=1, help=argparse.SUPPRESS)
+    p.add_argument("--cpu-workload", default="dense_256", choices=["dense_256", "sparse_20000"],
+                   help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -121,43 +123,88 @@ class L2Flush:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_iters(name="dense_256"):
+def oracle_solve(name="dense_256"):
+    """The oracle's own solve of a workload (iterations, f/g evaluations, ...)
+    as stored by oracle/workload_iters.py, or None."""
     path = os.path.join(ROOT, "oracle", "workload_iters.json")
     try:
-        return json.load(open(path))[name]["iters"]
+        return json.load(open(path))[name]
     except Exception:
         return None
 
 
-def cpu_sample(n_iters: int) -> dict:
-    """Time the oracle on the workload: its start-up (normalise + f/g) and
+def oracle_iters(name="dense_256"):
+    s = oracle_solve(name)
+    return s["iters"] if s else None
+
+
+def cpu_sample(n_iters: int, name: str = "dense_256") -> dict:
+    """Time the oracle on a workload (dense_256: 256^3 R=16; sparse_20000:
+    20000^3 with 2e6 nonzeros, R=10): its start-up (normalise + f/g) and
     then n_iters N-GMRES iterations of one solve, each timed on its own (an
-    iteration starts at its Step I, the ALS sweep).  A full solve is the
-    start-up plus the oracle's own iteration count times the mean iteration."""
+    iteration starts at its Step I, the ALS sweep), with the time of every
+    ALS sweep and every f/g evaluation inside it."""
     import synth
     from oracle import cp_oracle as O
-    prob, u0 = synth.workload_dense_256()
-    X = O.DenseTensor(prob.T)
-    marks = []
-    real = O.als_sweep
+    if name == "sparse_20000":
+        prob, u0 = synth.workload_sparse()
+        X = O.SparseTensor(prob.coords, prob.vals, prob.dims)
+        Rw = prob.R
+    else:
+        prob, u0 = synth.workload_dense_256()
+        X = O.DenseTensor(prob.T)
+        Rw = R
+    marks, sweeps, fgs = [], [], []
+    real_sweep, real_fg = O.als_sweep, O.fg
 
     def timed_sweep(*a, **k):
         marks.append(time.perf_counter())
-        return real(*a, **k)
-    O.als_sweep = timed_sweep
+        r = real_sweep(*a, **k)
+        sweeps.append(time.perf_counter() - marks[-1])
+        return r
+
+    def timed_fg(*a, **k):
+        t = time.perf_counter()
+        r = real_fg(*a, **k)
+        fgs.append((len(marks), time.perf_counter() - t))
+        return r
+    O.als_sweep, O.fg = timed_sweep, timed_fg
     try:
         t0 = time.perf_counter()
-        _, _, rep = O.cp_solve(X, u0, O.SolveOpts(R=R, tol=TOL), max_iters=n_iters)
+        _, _, rep = O.cp_solve(X, u0, O.SolveOpts(R=Rw, tol=TOL), max_iters=n_iters)
         t_end = time.perf_counter()
     finally:
-        O.als_sweep = real
+        O.als_sweep, O.fg = real_sweep, real_fg
     bounds = marks + [t_end]
     per_iter = [bounds[i + 1] - bounds[i] for i in range(len(marks))]
-    full = oracle_iters()
-    mean = sum(per_iter) / max(len(per_iter), 1)
+    # f/g evaluations of iteration i (1-based: made after its sweep began)
+    fg_n = [sum(1 for k, _ in fgs if k == i + 1) for i in range(len(marks))]
+    fg_t = [sum(d for k, d in fgs if k == i + 1) for i in range(len(marks))]
     t_init = (marks[0] if marks else t_end) - t0
-    return dict(t_init_s=t_init, per_iter_s=per_iter, iters_sampled=rep.iters, oracle_iters=full,
-                est_solve_s=t_init + (full if full else float("nan")) * mean)
+    res = dict(workload=name, t_init_s=t_init, per_iter_s=per_iter, sweep_s=sweeps, fg_count=fg_n, fg_s=fg_t,
+               iters_sampled=rep.iters)
+    res.update(extrapolate(res, 0))
+    return res
+
+
+def extrapolate(s: dict, skip: int) -> dict:
+    """Seconds of a whole oracle solve from a sample: the start-up, plus the
+    oracle's own iteration count times the mean ALS sweep and the rest of an
+    iteration (Step II, normalisations), plus its own count of f/g
+    evaluations after the start-up times the mean evaluation; means over the
+    sampled iterations after the first `skip`.  (Per-iteration times are
+    skewed by the line search: a search may take 1 or 20 evaluations.)"""
+    full = oracle_solve(s["workload"])
+    it = range(skip, len(s["per_iter_s"]))
+    if not full or not it:
+        return dict(oracle_iters=None, oracle_fg_evals=None, est_solve_s=None)
+    sweep = sum(s["sweep_s"][i] for i in it) / len(it)
+    nfg = sum(s["fg_count"][i] for i in it)
+    fg = sum(s["fg_s"][i] for i in it) / max(nfg, 1)
+    rest = sum(s["per_iter_s"][i] - s["sweep_s"][i] - s["fg_s"][i] for i in it) / len(it)
+    est = s["t_init_s"] + full["iters"] * (sweep + rest) + (full["fg_evals"] - 1) * fg
+    return dict(oracle_iters=full["iters"], oracle_fg_evals=full["fg_evals"], mean_sweep_s=sweep,
+                mean_fg_s=fg, mean_rest_s=rest, est_solve_s=est)
 
 
 def cpu_solves_c1(n_solves: int) -> dict:
@@ -189,33 +236,59 @@ def host_cpu() -> dict:
     return {"nproc": os.cpu_count(), "model": model}
 
 
-def run_cpu_child(flag: str, n: int, threads: int = 1) -> dict:
+def run_cpu_child(flag: str, n: int, threads: int = 1, extra=()) -> dict:
     """Run one CPU timing in a child process with `threads` BLAS threads and
     no GPU visible; returns its JSON result (or {"error": ...})."""
     t = str(threads)
     env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t,
                CUDA_VISIBLE_DEVICES="")
     try:
-        out = subprocess.run([sys.executable, os.path.abspath(__file__), flag, "--cpu-iters", str(n)],
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), flag, "--cpu-iters", str(n), *extra],
                              capture_output=True, text=True, env=env, timeout=1800)
         return json.loads(out.stdout.strip().splitlines()[-1])
     except Exception as exc:  # noqa: BLE001
         return {"error": str(exc)[:200]}
 
 
-def run_cpu_baseline_subprocess(n_iters: int) -> dict | None:
-    return run_cpu_child("--cpu-sample", n_iters, 1)
+def run_cpu_baseline_subprocess(n_iters: int, threads: int = 1, name: str = "dense_256") -> dict | None:
+    return run_cpu_child("--cpu-sample", n_iters, threads, ("--cpu-workload", name))
 
 
-def cpu_baseline_obj(s: dict) -> dict:
-    val = 1.0 / s["est_solve_s"] if s.get("est_solve_s") and s["est_solve_s"] == s["est_solve_s"] else None
+def sample_text(s: dict, how: str) -> str:
     per = s.get("per_iter_s") or [0.0]
-    return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle start-up + {s.get('iters_sampled')} N-GMRES iteration(s) of this workload "
-                       f"timed ({s.get('t_init_s', 0):.2f} s + {sum(per) / len(per):.2f} s/iter, numpy "
-                       f"single thread), extrapolated to the oracle's own {s.get('oracle_iters')} "
-                       f"iterations to tolerance (oracle/workload_iters.json)"),
-            "host": host_cpu()}
+    if not s.get("est_solve_s"):
+        return (f"oracle start-up + {len(per)} N-GMRES iteration(s) of this workload timed ({how}); no stored "
+                f"oracle solve to scale to")
+    return (f"oracle start-up + {len(per)} N-GMRES iteration(s) of this workload timed (numpy {how}; "
+            f"start-up {s['t_init_s']:.2f} s, ALS sweep {s['mean_sweep_s']:.2f} s, f/g evaluation "
+            f"{s['mean_fg_s']:.2f} s, rest {s['mean_rest_s']:.3f} s per iteration), scaled to the oracle's own "
+            f"solve of it: {s['oracle_iters']} iterations and {s['oracle_fg_evals']} f/g evaluations "
+            f"(oracle/workload_iters.json)")
+
+
+def cpu_baseline_obj(s: dict, threads: int = 1) -> dict:
+    est = s.get("est_solve_s")
+    how = "single thread" if threads == 1 else f"{threads} BLAS threads"
+    return {"value": 1.0 / est if est else None, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": sample_text(s, how), "host": host_cpu()}
+
+
+def cpu_samples_obj(one: dict, allc: dict | None, nproc: int) -> dict:
+    """cpu_baseline from a one-thread sample, with the all-cores sample of
+    the same workload beside it (the oracle as it stands: its loops do not
+    use more threads, so the two agree)."""
+    if "error" in one:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": one["error"]}
+    res = cpu_baseline_obj(one)
+    if allc is not None:
+        if "error" in allc:
+            res["all_cores"] = {"error": allc["error"]}
+        else:
+            a = cpu_baseline_obj(allc, nproc)
+            res["all_cores"] = {"value": a["value"], "unit": UNIT, "blas_threads": nproc, "sample": a["sample"],
+                                "note": "the oracle's MTTKRP (numpy einsum) runs on one thread whatever "
+                                        "the BLAS thread count; only its small matrix products can use more"}
+    return res
 
 
 def cpu_c1_block() -> dict:
@@ -299,10 +372,16 @@ def run_ours(args, rank, world, local_rank):
     import synth
     import paper_1105_5331_gb300 as cp
 
-    cpu = cpu_c1 = None
+    cpu = cpu_c1 = cpu_c4 = None
     if rank == 0 and not args.no_cpu_baseline and not args.solve_only:
-        cpu = run_cpu_baseline_subprocess(args.cpu_iters)   # before any GPU work
+        nproc = host_cpu()["nproc"] or 1
+        # before any GPU work: the headline workload on one thread and on all
+        # cores, the 20^3 workload as whole solves, the sparse workload
+        cpu = cpu_samples_obj(run_cpu_baseline_subprocess(args.cpu_iters),
+                              run_cpu_baseline_subprocess(args.cpu_iters, nproc), nproc)
         cpu_c1 = cpu_c1_block()
+        if not args.no_workloads and oracle_iters("sparse_20000"):
+            cpu_c4 = cpu_samples_obj(run_cpu_baseline_subprocess(args.cpu_iters, 1, "sparse_20000"), None, 1)
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -386,6 +465,8 @@ def run_ours(args, rank, world, local_rank):
         workloads["sparse_20000"]["scaled_2e8"] = sparse_scaled_block(cp, ctx, stream)
         if cpu_c1 is not None:
             workloads["dense_20_fp64"]["cpu_oracle"] = cpu_c1
+        if cpu_c4 is not None:
+            workloads["sparse_20000"]["cpu_oracle"] = cpu_c4
         t = None
 
     clocks = clk.summary()
@@ -414,10 +495,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
     }
     if cpu is not None:
-        if "error" in cpu:
-            res["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu["error"]}
-        else:
-            res["cpu_baseline"] = cpu_baseline_obj(cpu)
+        res["cpu_baseline"] = cpu
     if t is not None:
         t.close()
     ctx.close()
@@ -619,21 +697,19 @@ def run_reference(args):
     """The FP64 CPU oracle on the host cores (one BLAS thread, in a child
     process), on the 256^3 workload: one solve's start-up, then warmup +
     steps N-GMRES iterations of that solve; a step is one iteration, timed
-    on its own.  solves/s = 1 / (start-up + the oracle's own iteration count
-    to tolerance x the mean timed iteration)."""
+    on its own.  solves/s = 1 / the whole solve's seconds scaled from the
+    timed iterations (extrapolate(): the oracle's own counts of iterations
+    and f/g evaluations times the mean sweep, evaluation and rest)."""
     s = run_cpu_baseline_subprocess(args.warmup + args.steps)
     if "error" in s:
         return {"impl": "reference", "unavailable": f"oracle sample failed: {s['error']}"}
     timed = s["per_iter_s"][args.warmup:]
     mean = sum(timed) / len(timed)
-    full = s.get("oracle_iters")
-    value = 1.0 / (s["t_init_s"] + full * mean) if full else None
-    cb = cpu_baseline_obj(dict(s, per_iter_s=timed))
-    cb["value"] = value
-    cb["sample"] = (f"one oracle solve of this workload: start-up {s['t_init_s']:.2f} s, then {args.warmup} "
-                    f"untimed + {args.steps} timed N-GMRES iterations (mean {mean:.2f} s each, numpy single "
-                    f"thread); solves/s = 1 / (start-up + {full} iterations to tolerance x mean), the "
-                    f"oracle's own count (oracle/workload_iters.json)")
+    est = extrapolate(s, args.warmup)
+    value = 1.0 / est["est_solve_s"] if est.get("est_solve_s") else None
+    cb = cpu_baseline_obj(dict(s, **est))
+    cb["sample"] = (f"one oracle solve of this workload: {args.warmup} untimed + {args.steps} timed N-GMRES "
+                    f"iterations after the start-up (mean {mean:.2f} s each); " + cb["sample"])
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * mean,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -1346,7 +1422,7 @@ def run_kernel_breakdown(args):
 def main():
     args = parse()
     if args.cpu_sample:
-        print(json.dumps(cpu_sample(args.cpu_iters)))
+        print(json.dumps(cpu_sample(args.cpu_iters, args.cpu_workload)))
         return
     if args.cpu_c1:
         print(json.dumps(cpu_solves_c1(args.cpu_iters)))

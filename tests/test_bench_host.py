@@ -53,3 +53,23 @@ def test_clock_summary_reads_nvidia_smi_lines():
     assert clk.summary()["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
     clk.lines = []
     assert clk.summary()["sm_mhz"] is None
+
+
+def test_cpu_sample_is_scaled_by_the_oracle_solve_counts():
+    """The CPU baseline scales a timed sample of oracle iterations to the
+    oracle's own solve: start-up + iterations x (sweep + rest) + (f/g
+    evaluations - 1) x the mean evaluation, the means taken over the sampled
+    iterations after the skipped ones (a line search may take 1 or 20
+    evaluations, so a per-iteration mean would be skewed)."""
+    import bench
+    full = bench.oracle_solve("dense_256")
+    s = {"workload": "dense_256", "t_init_s": 2.0, "per_iter_s": [30.0, 5.0, 7.0],
+         "sweep_s": [1.0, 1.0, 1.0], "fg_count": [20, 3, 5], "fg_s": [28.0, 3.6, 5.6]}
+    e = bench.extrapolate(s, 1)
+    fg = (3.6 + 5.6) / 8
+    rest = ((5.0 - 1.0 - 3.6) + (7.0 - 1.0 - 5.6)) / 2
+    want = 2.0 + full["iters"] * (1.0 + rest) + (full["fg_evals"] - 1) * fg
+    assert abs(e["est_solve_s"] - want) <= 1e-9 * want
+    assert e["oracle_iters"] == full["iters"] and e["oracle_fg_evals"] == full["fg_evals"]
+    assert bench.extrapolate(dict(s, workload="no_such_workload"), 0)["est_solve_s"] is None
+    assert bench.extrapolate(s, 3)["est_solve_s"] is None
