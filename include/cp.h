@@ -351,8 +351,9 @@ cp_status cp_many_set_round(cp_ctx* ctx, double seconds);
  * chosen for its bucket (ceil log2 of its entries, ceil log2 R, FP64 or
  * mixed).  The first request of a bucket is timed for a few iterations with
  * each size, 1, 2, 4 and 8 CTAs (the request itself, from u0, in scratch
- * buffers); the size with the least SM time per iteration (CTAs x time) is
- * kept for the rest of the process.  u0: host or device (P doubles).
+ * buffers); among the sizes within 1.5x of the fastest, the one with the
+ * least SM time per iteration (CTAs x time) is kept for the rest of the
+ * process.  u0: host or device (P doubles).
  * Synchronous.  CP_ERR_UNSUPPORTED as for cp_solve_many. */
 cp_status cp_many_plan(cp_ctx* ctx, const cp_tensor* t, const cp_solve_opts* opts, const double* u0, int* cluster);
 
