@@ -1,6 +1,8 @@
 """CPU checks of bench.py's host logic: the reference arm (the FP64 oracle on
 host cores) prints one JSON line with the contract's keys from rank 0 and
-nothing from other ranks; the clock record is read from nvidia-smi's lines."""
+nothing from other ranks; the clock record is read from nvidia-smi's lines;
+the CPU sample is scaled by the oracle's own solve counts, which are the
+oracle's."""
 import json
 import os
 import subprocess
@@ -73,3 +75,24 @@ def test_cpu_sample_is_scaled_by_the_oracle_solve_counts():
     assert e["oracle_iters"] == full["iters"] and e["oracle_fg_evals"] == full["fg_evals"]
     assert bench.extrapolate(dict(s, workload="no_such_workload"), 0)["est_solve_s"] is None
     assert bench.extrapolate(s, 3)["est_solve_s"] is None
+
+
+def test_stored_oracle_solves_are_the_oracles_own():
+    """oracle/workload_iters.json holds the oracle's own solves (written by
+    oracle/workload_iters.py, which calls only the oracle and the input
+    generators).  The 20^3 entry is recomputed here and must match exactly;
+    every entry must be a converged solve below the tolerance."""
+    import importlib.util
+    import synth
+    spec = importlib.util.spec_from_file_location("wi", os.path.join(ROOT, "oracle", "workload_iters.py"))
+    wi = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(wi)
+    stored = json.load(open(os.path.join(ROOT, "oracle", "workload_iters.json")))
+    prob, u0 = synth.workload_dense_small()
+    got = wi.run("dense_small", prob, u0, 3)
+    for key in ("iters", "fg_evals", "restarts", "ls_failures", "converged"):
+        assert got[key] == stored["dense_small"][key], key
+    for key in ("f", "gnorm_over_P"):   # another host's BLAS may round differently
+        assert abs(got[key] - stored["dense_small"][key]) <= 1e-10 * abs(stored["dense_small"][key]), key
+    for name, rec in stored.items():
+        assert rec["converged"] and rec["gnorm_over_P"] < 1e-7, name
