@@ -9,8 +9,9 @@ with mt_init / mt_advance of csrc/mt_device.cuh.  Here those two functions
 C++ compiler, unchanged: the FP32 seeds of the Newton steps come from IEEE
 host operations, and floating-point contraction is off, so values can differ
 from the device's in the last bits only.  Each search runs on a random
-polynomial of degree 4, 6 or 8 with phi'(0) < 0 under varied options (ftol,
-gtol, xtol, first step, maxfev), and the two searches must make the same
+polynomial of degree 4, 6 or 8 (with phi'(0) < 0 but for a few) under varied
+options (ftol, gtol, xtol, smallest, largest and first step, maxfev) so that
+every exit code occurs, and the two searches must make the same
 trials (within 1e-9 relative), the same number of them, and end with the same
 exit code.  Trials are compared relative to the largest step the search has
 tried so far: a trial near 0 reached from steps of size ~100 is an
@@ -117,12 +118,15 @@ def random_searches(n, seed=20240605):
     for _ in range(n):
         deg = int(rng.choice([4, 6, 8]))
         c = rng.standard_normal(deg + 1) * 10.0 ** rng.uniform(-2, 2, deg + 1)
-        c[1] = -abs(c[1]) - 1e-3
+        # a few lines that do not descend (both sides stop at once, info -1)
+        c[1] = -abs(c[1]) - 1e-3 if rng.uniform() > 0.01 else abs(c[1])
         c[deg] = abs(c[deg]) + 1e-3
         opts = O.LSOpts(ftol=float(rng.choice([1e-4, 1e-3, 0.1, 0.3])),
                         gtol=float(rng.choice([1e-2, 0.1, 0.5, 0.9])),
                         xtol=float(rng.choice([1e-15, 1e-15, 1e-8, 1e-3, 0.1, 0.8])),
-                        stpmin=1e-15, stpmax=float(rng.choice([1e15, 1e15, 2.0, 10.0])),
+                        # a smallest step above the minimiser now and then (info 4)
+                        stpmin=float(rng.choice([1e-15] * 19 + [0.3])),
+                        stpmax=float(rng.choice([1e15, 1e15, 2.0, 10.0])),
                         stp0=float(10.0 ** rng.uniform(-4, 3)),
                         maxfev=int(rng.choice([20, 20, 6, 3])))
         if opts.ftol >= opts.gtol:
@@ -182,5 +186,5 @@ def test_device_search_matches_the_oracle_on_random_lines(harness):
     for k, got, want in differ:
         print("search", k, "host build", got, "oracle", want)
     # every exit code the polynomial lines can produce is reached
-    assert {1, 2, 3, 5}.issubset(infos), infos
+    assert {-1, 1, 2, 3, 4, 5, 6}.issubset(infos), infos
     assert len(differ) <= 0.002 * len(cases), f"{len(differ)} of {len(cases)} searches differ"
